@@ -1,0 +1,370 @@
+"""Python wrapper of the CPU oracle (plain C++17, FP64, history-based).
+
+TEST INFRASTRUCTURE ONLY: imported by `tests/`, `__graft_entry__.smoke()` and the CPU-baseline
+leg of `bench.py`.  The product path never imports this package.
+
+`run(problem, n, seed, ...)` takes a problem dict as written by the seeded generators and returns
+per-bin means and standard errors computed from the exact per-history variance.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MAX_HS = 16
+NCOUNT = 14
+COUNTER_NAMES = ["source", "secondary", "capture", "production", "leak", "census", "lost",
+                 "flight", "collision", "scatter", "surface", "reflect", "ww_split", "ww_kill"]
+KIND = {"PX": 0, "PY": 1, "PZ": 2, "CZ": 3}
+BC = {"interior": 0, "vacuum": 1, "reflect": 2}
+SRC_POS = {"box": 0, "surface_x0": 1}
+SRC_DIR = {"iso": 0, "beam_x": 1, "cos_x": 2}
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with g++ (portable flags only: the same source builds on x86 and Arm)."""
+    src = os.path.join(_HERE, "oracle.cpp")
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= max(os.path.getmtime(src),
+                                               os.path.getmtime(os.path.join(_HERE, "oracle.h")))):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-pthread",
+                           "-ffp-contract=off", "-o", tmp, src])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class OrProblem(C.Structure):
+    _fields_ = [
+        ("G", C.c_int), ("M", C.c_int),
+        ("sigma_t", C.POINTER(C.c_double)), ("sigma_s", C.POINTER(C.c_double)),
+        ("sigma_f", C.POINTER(C.c_double)), ("nu", C.POINTER(C.c_double)),
+        ("chi", C.POINTER(C.c_double)), ("speed", C.POINTER(C.c_double)),
+        ("n_surf", C.c_int), ("surf_kind", C.POINTER(C.c_int)),
+        ("surf_coef", C.POINTER(C.c_double)), ("surf_bc", C.POINTER(C.c_int)),
+        ("n_cell", C.c_int), ("cell_nhs", C.POINTER(C.c_int)),
+        ("cell_hs_surf", C.POINTER(C.c_int)), ("cell_hs_sense", C.POINTER(C.c_int)),
+        ("cell_mat", C.POINTER(C.c_int)),
+        ("has_lattice", C.c_int), ("lat_nx", C.c_int), ("lat_ny", C.c_int),
+        ("lat_x0", C.c_double), ("lat_y0", C.c_double), ("lat_pitch", C.c_double),
+        ("lat_r", C.c_double), ("lat_pin_mat", C.POINTER(C.c_int)), ("lat_matrix", C.c_int),
+        ("src_pos", C.c_int), ("src_dir", C.c_int),
+        ("src_lo", C.c_double * 3), ("src_hi", C.c_double * 3),
+        ("src_group_pdf", C.POINTER(C.c_double)), ("src_t0", C.c_double), ("src_t1", C.c_double),
+        ("n_tally", C.c_int), ("tally_dims", C.POINTER(C.c_int)),
+        ("tally_edges", C.POINTER(C.c_double)), ("t_census", C.c_double),
+        ("ww_on", C.c_int), ("ww_nx", C.c_int), ("ww_ny", C.c_int), ("ww_nz", C.c_int),
+        ("ww_edges", C.POINTER(C.c_double)), ("ww_center", C.POINTER(C.c_double)),
+        ("ww_upper", C.c_double), ("ww_lower", C.c_double), ("ww_split_max", C.c_int),
+    ]
+
+
+class OrEvent(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("root", C.c_uint64), ("k", C.c_uint32),
+                ("kind", C.c_int32), ("outcome", C.c_int32), ("n_child", C.c_int32),
+                ("cell", C.c_int32), ("elem", C.c_int32), ("in_pin", C.c_int32),
+                ("g", C.c_int32),
+                ("x", C.c_double), ("y", C.c_double), ("z", C.c_double),
+                ("ux", C.c_double), ("uy", C.c_double), ("uz", C.c_double),
+                ("t", C.c_double), ("w", C.c_double)]
+
+
+class OrOpts(C.Structure):
+    _fields_ = [("first_history", C.c_uint64), ("n_histories", C.c_uint64),
+                ("seed", C.c_uint64), ("threads", C.c_int),
+                ("log_first", C.c_uint64), ("log_count", C.c_uint64),
+                ("log", C.POINTER(OrEvent)), ("log_cap", C.c_uint64),
+                ("log_n", C.POINTER(C.c_uint64)), ("fixed_bits", C.c_int)]
+
+
+class OrResult(C.Structure):
+    _fields_ = [("s1", C.POINTER(C.c_double)), ("s2", C.POINTER(C.c_double)),
+                ("fixed", C.POINTER(C.c_int64)), ("counters", C.c_int64 * NCOUNT)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.or_run.argtypes = [C.POINTER(OrProblem), C.POINTER(OrOpts), C.POINTER(OrResult)]
+            L.or_run.restype = C.c_int
+            L.or_total_bins.argtypes = [C.POINTER(OrProblem)]
+            L.or_total_bins.restype = C.c_int
+            L.or_philox.argtypes = [C.c_uint32, C.c_uint32, C.POINTER(C.c_uint32),
+                                    C.POINTER(C.c_uint32)]
+            L.or_u01.argtypes = [C.c_uint32, C.c_uint32]
+            L.or_u01.restype = C.c_double
+            L.or_dist_cylinder.argtypes = [C.c_double] * 7 + [C.c_int]
+            L.or_dist_cylinder.restype = C.c_double
+            L.or_dist_plane.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int]
+            L.or_dist_plane.restype = C.c_double
+            L.or_source_sample.argtypes = [C.POINTER(OrProblem), C.c_uint64, C.c_uint64,
+                                           C.POINTER(C.c_double), C.POINTER(C.c_int)]
+            L.or_source_sample.restype = C.c_int
+            L.or_sample_scatter_group.argtypes = [C.POINTER(OrProblem), C.c_int, C.c_int,
+                                                  C.c_double]
+            L.or_sample_scatter_group.restype = C.c_int
+            L.or_child_tag.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32,
+                                       C.c_uint32]
+            L.or_child_tag.restype = C.c_uint64
+            L.or_mlp_param_count.argtypes = [C.c_int]
+            L.or_mlp_param_count.restype = C.c_int
+            L.or_mlp_loss_grad.argtypes = [C.c_int, C.POINTER(C.c_double), C.c_int,
+                                           C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                           C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                           C.POINTER(C.c_double)]
+            L.or_mlp_loss_grad.restype = C.c_double
+            _lib = L
+    return _lib
+
+
+def _dp(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+class Marshalled:
+    """Keeps the numpy buffers alive as long as the ctypes struct that points at them."""
+
+    def __init__(self, prob: dict, ww: dict | None = None):
+        self.keep = []
+        G = prob["G"]
+        mats = prob["materials"]
+        M = len(mats)
+        s = OrProblem()
+        s.G, s.M = G, M
+
+        def dp(x):
+            a, p = _dp(x)
+            self.keep.append(a)
+            return p
+
+        def ip(x):
+            a, p = _ip(x)
+            self.keep.append(a)
+            return p
+
+        s.sigma_t = dp([m["sigma_t"] for m in mats])
+        s.sigma_s = dp([m["sigma_s"] for m in mats])
+        s.sigma_f = dp([m["sigma_f"] for m in mats])
+        s.nu = dp([m["nu"] for m in mats])
+        s.chi = dp([m["chi"] for m in mats])
+        s.speed = dp(prob["speed"])
+        surfs = prob["surfaces"]
+        s.n_surf = len(surfs)
+        s.surf_kind = ip([KIND[x["kind"]] for x in surfs])
+        coef = np.zeros((len(surfs), 3))
+        for i, x in enumerate(surfs):
+            coef[i, : len(x["coef"])] = x["coef"]
+        s.surf_coef = dp(coef)
+        s.surf_bc = ip([BC[x["bc"]] for x in surfs])
+        cells = prob["cells"]
+        s.n_cell = len(cells)
+        hs_s = np.zeros((len(cells), MAX_HS), np.int32)
+        hs_n = np.zeros((len(cells), MAX_HS), np.int32)
+        for i, c in enumerate(cells):
+            for j, (sf, sn) in enumerate(c["halfspaces"]):
+                hs_s[i, j], hs_n[i, j] = sf, sn
+        s.cell_nhs = ip([len(c["halfspaces"]) for c in cells])
+        s.cell_hs_surf = ip(hs_s)
+        s.cell_hs_sense = ip(hs_n)
+        s.cell_mat = ip([c["material"] for c in cells])
+        lat = prob.get("lattice")
+        if lat:
+            s.has_lattice = 1
+            s.lat_nx, s.lat_ny = lat["nx"], lat["ny"]
+            s.lat_x0, s.lat_y0 = lat["x0"], lat["y0"]
+            s.lat_pitch, s.lat_r = lat["pitch"], lat["radius"]
+            s.lat_pin_mat = ip(lat["pin_material"])
+            s.lat_matrix = lat["matrix_material"]
+        else:
+            s.has_lattice = 0
+            s.lat_pin_mat = ip([0])
+        src = prob["source"]
+        s.src_pos = SRC_POS[src["pos"]]
+        s.src_dir = SRC_DIR[src["dir"]]
+        for i in range(3):
+            s.src_lo[i] = src["lo"][i]
+            s.src_hi[i] = src["hi"][i]
+        s.src_group_pdf = dp(src["group_pdf"])
+        s.src_t0, s.src_t1 = src["t0"], src["t1"]
+        tals = prob["tallies"]
+        s.n_tally = len(tals)
+        dims, edges = [], []
+        self.tally_shapes = []
+        for t in tals:
+            n = [len(t[k]) - 1 for k in ("x", "y", "z", "t")]
+            dims += n
+            for k in ("x", "y", "z", "t"):
+                edges += list(t[k])
+            self.tally_shapes.append((n[2], n[1], n[0], G, n[3]))
+        s.tally_dims = ip(dims)
+        s.tally_edges = dp(edges if edges else [0.0])
+        s.t_census = prob["t_census"]
+        if ww is not None:
+            s.ww_on = 1
+            s.ww_nx, s.ww_ny, s.ww_nz = (len(ww[k]) - 1 for k in ("x", "y", "z"))
+            s.ww_edges = dp(list(ww["x"]) + list(ww["y"]) + list(ww["z"]))
+            s.ww_center = dp(ww["center"])
+            s.ww_upper = ww.get("upper", 2.0)
+            s.ww_lower = ww.get("lower", 0.5)
+            s.ww_split_max = ww.get("split_max", 10)
+        else:
+            s.ww_on = 0
+            s.ww_edges = dp([0.0])
+            s.ww_center = dp([0.0])
+        self.s = s
+        self.n_surf = len(surfs)
+
+
+class Result:
+    def __init__(self, shapes, n, s1, s2, fixed, counters, n_surf, events=None):
+        self.n = n
+        self.counters = dict(zip(COUNTER_NAMES, [int(c) for c in counters]))
+        self.s1, self.s2, self.fixed = s1, s2, fixed
+        self.events = events
+        mean = s1 / n
+        var = np.maximum(s2 / n - mean * mean, 0.0) / max(n - 1, 1)
+        self.mean_flat, self.std_flat = mean, np.sqrt(var)
+        self.tallies = []
+        off = 0
+        for shp in shapes:
+            size = int(np.prod(shp))
+            self.tallies.append((mean[off:off + size].reshape(shp),
+                                 np.sqrt(var[off:off + size]).reshape(shp)))
+            off += size
+        self.leak_mean = mean[off:off + n_surf]
+        self.leak_std = np.sqrt(var[off:off + n_surf])
+        self.fixed_tallies = fixed
+
+
+def run(prob: dict, n: int, seed: int = 1, threads: int | None = None, first: int = 0,
+        log_first: int = 0, log_count: int = 0, log_cap: int = 0, ww: dict | None = None,
+        fixed_bits: int = 32) -> Result:
+    L = lib()
+    m = Marshalled(prob, ww)
+    nb = L.or_total_bins(C.byref(m.s))
+    s1 = np.zeros(nb)
+    s2 = np.zeros(nb)
+    fx = np.zeros(nb, np.int64)
+    res = OrResult()
+    res.s1 = s1.ctypes.data_as(C.POINTER(C.c_double))
+    res.s2 = s2.ctypes.data_as(C.POINTER(C.c_double))
+    res.fixed = fx.ctypes.data_as(C.POINTER(C.c_int64))
+    o = OrOpts()
+    o.first_history, o.n_histories, o.seed = first, n, seed
+    o.threads = threads if threads else (os.cpu_count() or 1)
+    o.fixed_bits = fixed_bits
+    events = None
+    log_n = C.c_uint64(0)
+    if log_count > 0:
+        cap = log_cap if log_cap else 64 * log_count
+        events = (OrEvent * cap)()
+        o.log = events
+        o.log_cap = cap
+        o.log_first, o.log_count = log_first, log_count
+        o.log_n = C.pointer(log_n)
+    rc = L.or_run(C.byref(m.s), C.byref(o), C.byref(res))
+    if rc != 0:
+        raise RuntimeError(f"or_run failed: {rc}")
+    ev = None
+    if events is not None:
+        ev = events_to_numpy(events, int(log_n.value))
+    return Result(m.tally_shapes, n, s1, s2, fx, list(res.counters), m.n_surf, ev)
+
+
+EVENT_DTYPE = np.dtype([("tag", np.uint64), ("root", np.uint64), ("k", np.uint32),
+                        ("kind", np.int32), ("outcome", np.int32), ("n_child", np.int32),
+                        ("cell", np.int32), ("elem", np.int32), ("in_pin", np.int32),
+                        ("g", np.int32), ("x", np.float64), ("y", np.float64),
+                        ("z", np.float64), ("ux", np.float64), ("uy", np.float64),
+                        ("uz", np.float64), ("t", np.float64), ("w", np.float64)], align=True)
+
+
+def events_to_numpy(events, n):
+    assert C.sizeof(OrEvent) == EVENT_DTYPE.itemsize
+    buf = np.frombuffer(events, dtype=EVENT_DTYPE, count=len(events))[:n].copy()
+    order = np.lexsort((buf["k"], buf["tag"]))
+    return buf[order]
+
+
+# ----------------------------------------------------------------------------- unit helpers
+
+
+def philox(key, ctr):
+    L = lib()
+    c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    out = (C.c_uint32 * 4)()
+    L.or_philox(int(key[0]) & 0xFFFFFFFF, int(key[1]) & 0xFFFFFFFF, c, out)
+    return [int(v) for v in out]
+
+
+def u01(a, b):
+    return lib().or_u01(a, b)
+
+
+def dist_cylinder(x, y, ux, uy, x0, y0, r, inside):
+    return lib().or_dist_cylinder(x, y, ux, uy, x0, y0, r, int(inside))
+
+
+def dist_plane(pos, u, c, sense):
+    return lib().or_dist_plane(pos, u, c, sense)
+
+
+def source_sample(prob, seed, h):
+    m = Marshalled(prob)
+    out = (C.c_double * 7)()
+    g = C.c_int(0)
+    cell = lib().or_source_sample(C.byref(m.s), seed, h, out, C.byref(g))
+    return list(out), int(g.value), cell
+
+
+def sample_scatter_group(prob, m, g, u):
+    mm = Marshalled(prob)
+    return lib().or_sample_scatter_group(C.byref(mm.s), m, g, u)
+
+
+def child_tag(seed, parent, k, j, marker=0x80000000):
+    return int(lib().or_child_tag(seed, parent, k, j, marker))
+
+
+def mlp_param_count(H=64):
+    return lib().or_mlp_param_count(H)
+
+
+def mlp_loss_grad(params, x, target=None, wt=None, H=64):
+    """FP64 reference MLP (tanh hidden layers): returns (loss, y, grad)."""
+    L = lib()
+    x = np.ascontiguousarray(x, np.float64)
+    n = x.shape[0]
+    p = np.ascontiguousarray(params, np.float64)
+    y = np.zeros(n)
+    grad = np.zeros(p.size)
+    tp = None if target is None else np.ascontiguousarray(target, np.float64)
+    wp = None if wt is None else np.ascontiguousarray(wt, np.float64)
+    dptr = lambda a: a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+    loss = L.or_mlp_loss_grad(H, dptr(p), n, dptr(x), dptr(tp), dptr(wp), dptr(y),
+                              dptr(grad) if tp is not None else None)
+    return loss, y, grad
+
+
+def relative_error(mean, std):
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.where(mean != 0, std / np.abs(mean), math.inf)

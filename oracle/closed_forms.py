@@ -1,0 +1,194 @@
+"""Closed-form and numerically exact solutions that pin the oracle.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  Each function states the mathematics it
+evaluates; none of them runs the random walk.
+
+Units: cross sections 1/cm, lengths cm, speeds cm/s.  All track-length quantities are per source
+particle: a mesh bin's value is the expected total track length (weight x cm) in that bin, i.e.
+the space-time integral of the scalar flux over the bin.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy import integrate, linalg
+from scipy.special import expn
+
+# ------------------------------------------------------------------ P1: beam transmission
+
+
+def beam_transmission(sigma_t: float, L: float) -> float:
+    """Normally incident beam on a pure absorber: uncollided transmission e^{-Sigma_t L}."""
+    return math.exp(-sigma_t * L)
+
+
+def beam_flux_bins(sigma_t: float, edges) -> np.ndarray:
+    """Track length per source particle of a mu=1 beam in [a, b]: (e^{-St a} - e^{-St b})/St."""
+    e = np.asarray(edges, dtype=np.float64)
+    return (np.exp(-sigma_t * e[:-1]) - np.exp(-sigma_t * e[1:])) / sigma_t
+
+
+# ------------------------------------------------------------------ P2: isotropic slab source
+
+
+def slab_leakage(sigma_t: float, L: float, a: float = 1.0):
+    """Pure absorber 0<x<L, isotropic source uniform on [0, a) (one particle in total).
+
+    A particle born at depth d from a face escapes through it uncollided with probability
+    E_2(St d)/2.  Averaging over the source and using d/du E_3(u) = -E_2(u):
+        P_right = [E_3(St (L-a)) - E_3(St L)] / (2 St a)
+        P_left  = [E_3(0) - E_3(St a)] / (2 St a),   E_3(0) = 1/2.
+    """
+    pr = (expn(3, sigma_t * (L - a)) - expn(3, sigma_t * L)) / (2.0 * sigma_t * a)
+    pl = (0.5 - expn(3, sigma_t * a)) / (2.0 * sigma_t * a)
+    return pl, pr
+
+
+def _phi2(u, sigma_t):
+    """Even second antiderivative of K(|u|) = E_1(St |u|) with Phi(0) = Phi'(0) = 0:
+    Phi(u) = |u|/St - (1/2 - E_3(St |u|)) / St^2."""
+    u = np.abs(np.asarray(u, dtype=np.float64))
+    return u / sigma_t - (0.5 - expn(3, sigma_t * u)) / sigma_t**2
+
+
+def slab_flux_bins(sigma_t: float, edges, a: float = 1.0) -> np.ndarray:
+    """Track length per source particle in x-bins of the pure-absorber slab with an isotropic
+    source uniform on [0, a): phi(x) = (1/a) int_0^a E_1(St |x - x'|)/2 dx', integrated over each
+    bin by the double antiderivative:
+        int_xa^xb int_0^a K = Phi(xb) - Phi(xa) - Phi(xb - a) + Phi(xa - a)."""
+    e = np.asarray(edges, dtype=np.float64)
+    xa, xb = e[:-1], e[1:]
+    val = _phi2(xb, sigma_t) - _phi2(xa, sigma_t) - _phi2(xb - a, sigma_t) + _phi2(xa - a, sigma_t)
+    return 0.5 * val / a
+
+
+def slab_flux_bins_quad(sigma_t: float, edges, a: float = 1.0) -> np.ndarray:
+    """The same bin integrals by adaptive quadrature of phi(x) (independent check of the
+    antiderivative algebra).  The inner integral uses int E_1 = -E_2/St."""
+    def phi(x):
+        lo, hi = x - a, x  # x - x' ranges over [x-a, x]
+        def F(u):  # int_0^u E_1(St s) ds for u >= 0
+            return (1.0 - expn(2, sigma_t * u)) / sigma_t
+        if lo >= 0.0:
+            inner = F(hi) - F(lo)
+        elif hi <= 0.0:
+            inner = F(-lo) - F(-hi)
+        else:
+            inner = F(hi) + F(-lo)
+        return 0.5 * inner / a
+    e = np.asarray(edges, dtype=np.float64)
+    out = []
+    for xa, xb in zip(e[:-1], e[1:]):
+        pts = [p for p in (0.0, a) if xa < p < xb]
+        v, _ = integrate.quad(phi, xa, xb, points=pts or None, epsabs=1e-13, epsrel=1e-10,
+                              limit=200)
+        out.append(v)
+    return np.array(out)
+
+
+# ------------------------------------------------------------------ P3 / P4: infinite medium, 1 group
+
+
+def infinite_total_tracklength(sigma_t, sigma_s, nu_sigma_f=0.0):
+    """Steady infinite medium: each unit of track length is removed at rate Sigma_a = St - Ss
+    and replaced at rate nu Sf, so the expected total track length per source is
+    1 / (St - Ss - nu Sf) for a subcritical medium."""
+    return 1.0 / (sigma_t - sigma_s - nu_sigma_f)
+
+
+def infinite_time_bins(sigma_t, sigma_s, nu_sigma_f, v, t_edges):
+    """Time-dependent one-group infinite medium, pulse at t = 0:
+    phi(t) = v exp(-alpha t), alpha = v (St - Ss - nu Sf);
+    int_ta^tb phi dt = (e^{-alpha ta} - e^{-alpha tb}) / (St - Ss - nu Sf).  For a supercritical
+    medium (alpha < 0) the same formula holds."""
+    e = np.asarray(t_edges, dtype=np.float64)
+    sa = sigma_t - sigma_s - nu_sigma_f
+    alpha = v * sa
+    if sa == 0.0:
+        return v * (e[1:] - e[:-1])
+    return (np.exp(-alpha * e[:-1]) - np.exp(-alpha * e[1:])) / sa
+
+
+def infinite_population(sigma_t, sigma_s, nu_sigma_f, v, t):
+    """Expected number of particles alive at time t per source particle: exp(-alpha t)."""
+    return math.exp(-v * (sigma_t - sigma_s - nu_sigma_f) * t)
+
+
+# ------------------------------------------------------------------ P5: multigroup expm
+
+
+def multigroup_operator(mat, speed):
+    """A = V M with M = S^T + chi (nu Sf)^T - diag(St), V = diag(v): d phi/dt = A phi for the
+    volume-integrated group flux phi_g = v_g N_g of an infinite medium."""
+    st = np.asarray(mat["sigma_t"], dtype=np.float64)
+    S = np.asarray(mat["sigma_s"], dtype=np.float64)
+    nsf = np.asarray(mat["nu"], dtype=np.float64) * np.asarray(mat["sigma_f"], dtype=np.float64)
+    chi = np.asarray(mat["chi"], dtype=np.float64)
+    M = S.T + np.outer(chi, nsf) - np.diag(st)
+    return np.diag(np.asarray(speed, dtype=np.float64)) @ M
+
+
+def integrated_flux_vanloan(A, phi0, t):
+    """int_0^t exp(A s) phi0 ds from the block exponential of Van Loan (1978):
+    exp([[A, I], [0, 0]] t) = [[e^{At}, int_0^t e^{As} ds], [0, I]]  (scipy's expm does scaling
+    and squaring with Pade approximants, Higham 2005)."""
+    G = A.shape[0]
+    B = np.zeros((2 * G, 2 * G))
+    B[:G, :G] = A * t
+    B[:G, G:] = np.eye(G) * t
+    E = linalg.expm(B)
+    return E[:G, G:] @ phi0
+
+
+def integrated_flux_eig(A, phi0, t):
+    """Same integral via the eigendecomposition A = W diag(lam) W^-1:
+    int_0^t e^{As} ds = W diag((e^{lam t} - 1)/lam) W^-1."""
+    lam, W = np.linalg.eig(A)
+    f = np.where(np.abs(lam * t) > 1e-12, np.expm1(lam * t) / np.where(lam == 0, 1, lam), t)
+    return np.real(W @ (f * np.linalg.solve(W, phi0.astype(complex))))
+
+
+def multigroup_time_bins(mat, speed, t_edges, g0=0, method="vanloan"):
+    """Per (group, time bin) track length of an infinite medium after a unit pulse in group g0
+    at t = 0: phi(0) = v_g0 e_g0, bins = differences of int_0^t phi."""
+    A = multigroup_operator(mat, speed)
+    G = A.shape[0]
+    phi0 = np.zeros(G)
+    phi0[g0] = speed[g0]
+    f = integrated_flux_vanloan if method == "vanloan" else integrated_flux_eig
+    cum = np.array([f(A, phi0, t) if t > 0 else np.zeros(G) for t in t_edges])
+    return (cum[1:] - cum[:-1]).T  # [G][nt]
+
+
+def multigroup_time_bins_ode(mat, speed, t_edges, g0=0, rtol=1e-12):
+    """Third, independent route: integrate d/dt [phi, Phi] = [A phi, phi] with Radau."""
+    A = multigroup_operator(mat, speed)
+    G = A.shape[0]
+    y0 = np.zeros(2 * G)
+    y0[g0] = speed[g0]
+    te = np.asarray(t_edges, dtype=np.float64)
+
+    def rhs(t, y):
+        return np.concatenate([A @ y[:G], y[:G]])
+
+    def jac(t, y):
+        J = np.zeros((2 * G, 2 * G))
+        J[:G, :G] = A
+        J[G:, :G] = np.eye(G)
+        return J
+
+    sol = integrate.solve_ivp(rhs, (0.0, te[-1]), y0, method="Radau", t_eval=te, rtol=rtol,
+                              atol=1e-30, jac=jac)
+    cum = sol.y[G:].T
+    return (cum[1:] - cum[:-1]).T
+
+
+# ------------------------------------------------------------------ isotropic-flux surface crossings
+
+
+def isotropic_crossings(track_density: float, area: float) -> float:
+    """Expected number of crossings (both directions) of a surface of the given area by a
+    uniform isotropic flux of scalar value `track_density` (track length per unit volume):
+    each one-way partial current is phi/4, so crossings = phi/2 per unit area."""
+    return 0.5 * track_density * area

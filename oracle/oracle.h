@@ -1,0 +1,146 @@
+/*
+ * CPU oracle for the multigroup, time-dependent Monte Carlo random walk.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU-baseline leg of
+ * the benchmark may load this library.  It shares no code, header, table or constant generator
+ * with the CUDA path; the two meet only in the seeded problem dicts.
+ *
+ * What it computes: the analog history-based random walk of the paper's Section 3 problem class
+ * (fixed source, multigroup, quadric CSG of planes and z-cylinders plus a square pin lattice,
+ * time-dependent source, time census, track-length mesh tallies, secondary production), in FP64,
+ * one history at a time, with the per-history variance of every tally bin.  The paper prints no
+ * transport equations; the steps follow textbook multigroup Monte Carlo in the order
+ *   distance to collision -> distance to surface -> distance to census -> move + score ->
+ *   collision (scatter / production / capture) or surface (leak / reflect / transmit).
+ */
+#ifndef MC_ORACLE_H
+#define MC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OR_MAX_HS 16
+
+enum { OR_PX = 0, OR_PY = 1, OR_PZ = 2, OR_CZ = 3 };
+enum { OR_INTERIOR = 0, OR_VACUUM = 1, OR_REFLECT = 2 };
+enum { OR_SRC_BOX = 0, OR_SRC_SURFACE_X0 = 1 };
+enum { OR_DIR_ISO = 0, OR_DIR_BEAM_X = 1, OR_DIR_COS_X = 2 };
+enum { OR_EV_COLLISION = 0, OR_EV_SURFACE = 1, OR_EV_CENSUS = 2, OR_EV_LOST = 3 };
+
+/* counters, summed over all histories */
+enum {
+  OR_C_SOURCE = 0,      /* primaries started */
+  OR_C_SECONDARY,       /* children produced by the production channel */
+  OR_C_CAPTURE,         /* removed by capture */
+  OR_C_PRODUCTION,      /* removed by the production channel (parent absorbed) */
+  OR_C_LEAK,            /* removed through a vacuum surface */
+  OR_C_CENSUS,          /* removed at the census time */
+  OR_C_LOST,            /* removed because no cell contained the particle */
+  OR_C_FLIGHT,          /* flights */
+  OR_C_COLLISION,       /* collisions */
+  OR_C_SCATTER,         /* scatters */
+  OR_C_SURFACE,         /* surface events (including lattice walls and pins) */
+  OR_C_REFLECT,         /* reflections */
+  OR_C_WW_SPLIT,        /* extra particles created by weight-window splitting */
+  OR_C_WW_KILL,         /* particles removed by roulette */
+  OR_NCOUNT
+};
+
+typedef struct {
+  int G, M;
+  const double* sigma_t;   /* [M][G] */
+  const double* sigma_s;   /* [M][G][G], from -> to */
+  const double* sigma_f;   /* [M][G] */
+  const double* nu;        /* [M][G] */
+  const double* chi;       /* [M][G] */
+  const double* speed;     /* [G] */
+  int n_surf;
+  const int* surf_kind;    /* [n_surf] OR_PX.. */
+  const double* surf_coef; /* [n_surf][3]: plane c; or cylinder x0, y0, r */
+  const int* surf_bc;      /* [n_surf] */
+  int n_cell;
+  const int* cell_nhs;     /* [n_cell] */
+  const int* cell_hs_surf; /* [n_cell][OR_MAX_HS] */
+  const int* cell_hs_sense;/* [n_cell][OR_MAX_HS] +1 / -1 */
+  const int* cell_mat;     /* [n_cell], -1 = filled by the lattice */
+  int has_lattice, lat_nx, lat_ny;
+  double lat_x0, lat_y0, lat_pitch, lat_r;
+  const int* lat_pin_mat;  /* [ny][nx], -1 = no pin */
+  int lat_matrix;
+  int src_pos, src_dir;
+  double src_lo[3], src_hi[3];
+  const double* src_group_pdf; /* [G] */
+  double src_t0, src_t1;
+  int n_tally;
+  const int* tally_dims;   /* [n_tally][4]: nx, ny, nz, nt */
+  const double* tally_edges; /* per tally: x[nx+1], y[ny+1], z[nz+1], t[nt+1] */
+  double t_census;
+  /* weight windows: centre w_c per (cell of the ww mesh, group); 0 disables */
+  int ww_on;
+  int ww_nx, ww_ny, ww_nz;
+  const double* ww_edges;  /* x[ww_nx+1], y[ww_ny+1], z[ww_nz+1] */
+  const double* ww_center; /* [ww_nz][ww_ny][ww_nx][G] */
+  double ww_upper, ww_lower; /* split above upper*w_c, roulette below lower*w_c */
+  int ww_split_max;
+} or_problem;
+
+typedef struct {
+  uint64_t tag, root;
+  uint32_t k;
+  int32_t kind, outcome, n_child, cell, elem, in_pin, g;
+  double x, y, z, ux, uy, uz, t, w;
+} or_event;
+
+/* outcome codes: collision 0 scatter, 1 production, 2 capture;
+ * surface 0 transmit, 1 reflect, 2 leak, 3 lattice wall, 4 pin */
+
+typedef struct {
+  uint64_t first_history, n_histories, seed;
+  int threads;
+  uint64_t log_first, log_count; /* histories [log_first, +log_count) are logged */
+  or_event* log;                 /* caller buffer, may be NULL */
+  uint64_t log_cap;
+  uint64_t* log_n;               /* events written (clipped to log_cap) */
+  int fixed_bits;                /* fixed-point scale 2^fixed_bits for the int64 sums */
+} or_opts;
+
+/* Outputs are laid out over all tallies' bins concatenated (tally 0 first, bins in
+ * [z][y][x][g][t] order), followed by n_surf leakage bins.  s1 = sum over histories of the
+ * history's score, s2 = sum of its square; fixed = sum of llrint(score_piece * 2^fixed_bits). */
+typedef struct {
+  double* s1;
+  double* s2;
+  int64_t* fixed;
+  int64_t counters[OR_NCOUNT];
+} or_result;
+
+int or_total_bins(const or_problem* p);
+int or_run(const or_problem* p, const or_opts* o, or_result* r);
+
+/* unit-level entry points used by the tests */
+void or_philox(uint32_t k0, uint32_t k1, const uint32_t ctr[4], uint32_t out[4]);
+double or_u01(uint32_t a, uint32_t b);
+double or_dist_cylinder(double x, double y, double ux, double uy, double x0, double y0, double r,
+                        int inside);
+double or_dist_plane(double pos, double u, double c, int sense);
+/* source sample of history h: writes x,y,z,ux,uy,uz,t and group; returns cell or -1 */
+int or_source_sample(const or_problem* p, uint64_t seed, uint64_t h, double out[7], int* g);
+/* sample a scatter group for material m, group g at uniform u */
+int or_sample_scatter_group(const or_problem* p, int m, int g, double u);
+/* derive the tag of child j produced at event k by a parent */
+uint64_t or_child_tag(uint64_t seed, uint64_t parent, uint32_t k, uint32_t j, uint32_t marker);
+
+/* Reference MLP for the weight-window map: 5 -> H -> H -> H -> 1, tanh hidden units, FP64.
+ * params = [W1 (H x 5), b1 (H), W2 (H x H), b2, W3 (H x H), b3, W4 (1 x H), b4].
+ * Forward over n inputs x[n][5] -> y[n]; loss = mean over n of wt[i] (y - target)^2;
+ * grad receives d loss / d params. */
+int or_mlp_param_count(int H);
+double or_mlp_loss_grad(int H, const double* params, int n, const double* x, const double* target,
+                        const double* wt, double* y, double* grad);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

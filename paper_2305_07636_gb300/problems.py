@@ -1,0 +1,393 @@
+"""Seeded synthetic problem generators for the multigroup time-dependent random walk.
+
+This module only *describes* problems: cross sections, geometry, source, tally meshes
+and census time, as plain Python dicts of numbers.  It contains none of the transport
+arithmetic, so both the CUDA path (through the C ABI) and the CPU oracle consume the same
+dicts without sharing any method code.
+
+The paper (Section 3) states the problem class: fixed-source multigroup transport on
+quadric-surface CSG with a time-dependent source, a time census and time-dependent mesh
+tallies.  The five workloads below are synthetic stand-ins whose shapes follow that
+statement; no benchmark cross-section data is used.
+
+Problem dict layout (all lengths in cm, times in s, cross sections in 1/cm):
+
+    G, speed[G]
+    materials: list of {sigma_t[G], sigma_s[G][G] (from, to), sigma_f[G], nu[G], chi[G]}
+    surfaces:  list of {kind: 'PX'|'PY'|'PZ'|'CZ', coef: [c] or [x0, y0, r],
+                        bc: 'interior'|'vacuum'|'reflect'}
+    cells:     list of {halfspaces: [(surface, +1|-1), ...], material: m (>=0) or -1 (lattice)}
+    lattice:   None or {nx, ny, x0, y0, pitch, radius, pin_material[ny*nx] (-1 = no pin),
+                        matrix_material}
+    source:    {pos: 'box'|'surface_x0', lo[3], hi[3], dir: 'iso'|'beam_x'|'cos_x',
+                group_pdf[G], t0, t1}
+    tallies:   list of {x: edges, y: edges, z: edges, t: edges}  (track-length mesh tallies)
+    t_census:  float (math.inf for steady state)
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+INF = math.inf
+
+# --------------------------------------------------------------------------------------
+# building blocks
+# --------------------------------------------------------------------------------------
+
+
+def material(sigma_t, sigma_s, sigma_f=None, nu=None, chi=None):
+    sigma_t = np.asarray(sigma_t, dtype=np.float64)
+    G = sigma_t.size
+    sigma_s = np.asarray(sigma_s, dtype=np.float64).reshape(G, G)
+    sigma_f = np.zeros(G) if sigma_f is None else np.asarray(sigma_f, dtype=np.float64)
+    nu = np.zeros(G) if nu is None else np.asarray(nu, dtype=np.float64)
+    if chi is None:
+        chi = np.zeros(G)
+        chi[0] = 1.0
+    chi = np.asarray(chi, dtype=np.float64)
+    return {"sigma_t": sigma_t.tolist(), "sigma_s": sigma_s.tolist(),
+            "sigma_f": sigma_f.tolist(), "nu": nu.tolist(), "chi": chi.tolist()}
+
+
+def box_surfaces(lo, hi, bc, axes=(0, 1, 2)):
+    """Planes bounding an axis-aligned box on the requested axes: returns (surfaces, halfspaces)."""
+    kinds = ("PX", "PY", "PZ")
+    surfs, hs = [], []
+    for a in axes:
+        surfs.append({"kind": kinds[a], "coef": [float(lo[a])], "bc": bc})
+        hs.append((len(surfs) - 1, +1))
+        surfs.append({"kind": kinds[a], "coef": [float(hi[a])], "bc": bc})
+        hs.append((len(surfs) - 1, -1))
+    return surfs, hs
+
+
+def source(pos="box", lo=(0, 0, 0), hi=(0, 0, 0), direction="iso", G=1, group=0,
+           group_pdf=None, t0=0.0, t1=0.0):
+    if group_pdf is None:
+        group_pdf = np.zeros(G)
+        group_pdf[group] = 1.0
+    return {"pos": pos, "lo": [float(v) for v in lo], "hi": [float(v) for v in hi],
+            "dir": direction, "group_pdf": [float(v) for v in group_pdf],
+            "t0": float(t0), "t1": float(t1)}
+
+
+def mesh(x=(-INF, INF), y=(-INF, INF), z=(-INF, INF), t=(0.0, INF)):
+    return {"x": [float(v) for v in x], "y": [float(v) for v in y],
+            "z": [float(v) for v in z], "t": [float(v) for v in t]}
+
+
+def problem(name, G, speed, materials, surfaces, cells, src, tallies, t_census=INF,
+            lattice=None):
+    return {"name": name, "G": int(G), "speed": [float(v) for v in speed],
+            "materials": materials, "surfaces": surfaces, "cells": cells,
+            "lattice": lattice, "source": src, "tallies": tallies,
+            "t_census": float(t_census)}
+
+
+def log_time_edges(n_bins, t_lo=1e-9, t_hi=1e-3):
+    """Edges {0} U logspace(t_lo, t_hi, n_bins): n_bins bins, the first one [0, t_lo]."""
+    return [0.0] + np.logspace(math.log10(t_lo), math.log10(t_hi), n_bins).tolist()
+
+
+def log_speeds(G, v_fast=2e9, v_slow=2e5):
+    if G == 1:
+        return [v_fast]
+    return np.logspace(math.log10(v_fast), math.log10(v_slow), G).tolist()
+
+
+def seeded_scatter(rng, G, sigma_t, c_lo, c_hi, upscatter_frac=0.1):
+    """Downscatter-dominant scattering matrix (from, to) with per-group ratio c_g ~ U[c_lo, c_hi].
+
+    Downscatter weights ~U[0,1] for g' >= g; the two slowest groups also get upscatter weights
+    summing to at most `upscatter_frac` of their row.
+    """
+    S = np.zeros((G, G))
+    c = rng.uniform(c_lo, c_hi, G)
+    for g in range(G):
+        wts = np.zeros(G)
+        wts[g:] = rng.uniform(0.0, 1.0, G - g)
+        wts[g] += 1e-3  # keep the self-scatter entry non-empty
+        if G >= 3 and g >= G - 2:
+            up = rng.uniform(0.0, 1.0, g)
+            if up.sum() > 0:
+                up *= upscatter_frac * wts.sum() / up.sum() * rng.uniform(0.2, 1.0)
+            wts[:g] = up
+        S[g] = wts / wts.sum() * c[g] * sigma_t[g]
+    return S
+
+
+# --------------------------------------------------------------------------------------
+# closed-form pin problems (used by the oracle's tests)
+# --------------------------------------------------------------------------------------
+
+
+def slab_problem(L=5.0, sigma_t=1.0, sigma_s=0.5, src_hi=1.0, n_bins=50, direction="iso",
+                 surface_source=False, name="slab"):
+    """Config-1 family: 1D slab 0<x<L, vacuum both ends, one group, steady state."""
+    surfs = [{"kind": "PX", "coef": [0.0], "bc": "vacuum"},
+             {"kind": "PX", "coef": [float(L)], "bc": "vacuum"}]
+    cells = [{"halfspaces": [(0, +1), (1, -1)], "material": 0}]
+    mat = material([sigma_t], [[sigma_s]])
+    if surface_source:
+        src = source("surface_x0", (0, 0, 0), (0, 0, 0), direction, 1)
+    else:
+        src = source("box", (0, 0, 0), (src_hi, 0, 0), direction, 1)
+    tal = [mesh(x=np.linspace(0.0, L, n_bins + 1))]
+    return problem(name, 1, [1.0], [mat], surfs, cells, src, tal)
+
+
+def infinite_medium_1g(sigma_t=1.0, sigma_s=0.5, sigma_f=0.0, nu=0.0, speed=1.0,
+                       t_edges=(0.0, INF), t_census=INF, side=10.0, name="inf1g"):
+    """One-group infinite medium: reflective cube, uniform isotropic pulse source at t=0."""
+    surfs, hs = box_surfaces((0, 0, 0), (side,) * 3, "reflect")
+    cells = [{"halfspaces": hs, "material": 0}]
+    mat = material([sigma_t], [[sigma_s]], [sigma_f], [nu], [1.0])
+    src = source("box", (0, 0, 0), (side,) * 3, "iso", 1)
+    tal = [mesh(x=(0, side), y=(0, side), z=(0, side), t=t_edges)]
+    return problem(name, 1, [speed], [mat], surfs, cells, src, tal, t_census)
+
+
+def azurv1(c=1.1, t_end=20.0, n_tbins=20):
+    """Supercritical AZURV1 stand-in (paper Section 3): c = (sigma_s + nu sigma_f)/sigma_t = 1.1,
+    sigma_t = v = 1, census at t_end mean-free-times."""
+    sigma_s = 0.6
+    sigma_f = 0.2
+    nu = (c - sigma_s) / sigma_f
+    return infinite_medium_1g(1.0, sigma_s, sigma_f, nu, 1.0,
+                              t_edges=np.linspace(0.0, t_end, n_tbins + 1),
+                              t_census=t_end, name="azurv1")
+
+
+# --------------------------------------------------------------------------------------
+# the five workloads
+# --------------------------------------------------------------------------------------
+
+
+def config1(sigma_s=0.5):
+    """1D slab 0<x<5 cm, vacuum, 1 group, sigma_t = 1, isotropic source uniform on [0,1),
+    50 x-bins + left/right leakage (leakage is reported per vacuum surface)."""
+    return slab_problem(5.0, 1.0, sigma_s, 1.0, 50, name="config1")
+
+
+def config2_xs(seed=2, G=7):
+    rng = np.random.default_rng(seed)
+    sigma_t = rng.uniform(0.2, 2.0, G)
+    S = seeded_scatter(rng, G, sigma_t, 0.3, 0.9)
+    return sigma_t, S
+
+
+def config2(seed=2, G=7, n_tbins=100, side=10.0):
+    """Infinite homogeneous medium (reflective 10 cm cube), 7 groups, pulse at t=0 in group 1,
+    no secondary production; 100 log-spaced time bins; census at 1e-3 s."""
+    sigma_t, S = config2_xs(seed, G)
+    surfs, hs = box_surfaces((0, 0, 0), (side,) * 3, "reflect")
+    cells = [{"halfspaces": hs, "material": 0}]
+    mat = material(sigma_t, S)
+    src = source("box", (0, 0, 0), (side,) * 3, "iso", G, 0)
+    t_edges = log_time_edges(n_tbins)
+    tal = [mesh(x=(0, side), y=(0, side), z=(0, side), t=t_edges)]
+    return problem("config2", G, log_speeds(G), [mat], surfs, cells, src, tal, t_edges[-1])
+
+
+def offspring_matrix(mat):
+    """K[g][g'] = (sigma_s[g->g'] + nu sigma_f[g] chi[g']) / sigma_t[g] (mean offspring per
+    collision); used only to scale the synthetic inputs."""
+    st = np.asarray(mat["sigma_t"])
+    S = np.asarray(mat["sigma_s"])
+    F = np.outer(np.asarray(mat["nu"]) * np.asarray(mat["sigma_f"]), np.asarray(mat["chi"]))
+    return (S + F) / st[:, None]
+
+
+def _lattice_materials(rng, G, fissile):
+    sigma_t = rng.uniform(0.3, 2.0, G)
+    while True:
+        S = seeded_scatter(rng, G, sigma_t, 0.3, 0.8)
+        if max(abs(np.linalg.eigvals(S / sigma_t[:, None]))) <= 0.8:
+            break
+    if not fissile:
+        return material(sigma_t, S)
+    # fission in a fraction of sigma_t, fast-peaked spectrum
+    room = sigma_t - S.sum(axis=1)
+    sigma_f = room * rng.uniform(0.2, 0.6, G)
+    nu = rng.uniform(2.3, 2.9, G)
+    chi = np.zeros(G)
+    chi[: max(1, G // 2)] = rng.uniform(0.1, 1.0, max(1, G // 2))
+    chi /= chi.sum()
+    return material(sigma_t, S, sigma_f, nu, chi)
+
+
+def scale_production(mats, target=0.9, rowsum_cap=0.98):
+    """Bisection on one factor lambda multiplying sigma_f of every fissile material so that
+    max_m rho(K_m) = target; asserts every offspring row sum <= rowsum_cap."""
+    def rho(lam):
+        r = 0.0
+        for m in mats:
+            mm = dict(m)
+            mm["sigma_f"] = (np.asarray(m["sigma_f"]) * lam).tolist()
+            r = max(r, max(abs(np.linalg.eigvals(offspring_matrix(mm)))))
+        return r
+    lo, hi = 0.0, 1.0
+    while rho(hi) < target:
+        hi *= 2.0
+        if hi > 1e6:
+            raise ValueError("cannot reach target spectral radius")
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if rho(mid) < target:
+            lo = mid
+        else:
+            hi = mid
+    lam = 0.5 * (lo + hi)
+    out = []
+    for m in mats:
+        mm = dict(m)
+        mm["sigma_f"] = (np.asarray(m["sigma_f"]) * lam).tolist()
+        out.append(mm)
+    rows = max(float(offspring_matrix(m).sum(axis=1).max()) for m in out)
+    return out, lam, rows
+
+
+def config3_materials(seed=3, G=7, target=0.9):
+    for attempt in range(64):
+        rng = np.random.default_rng([seed, attempt])
+        mats = [_lattice_materials(rng, G, True), _lattice_materials(rng, G, True),
+                _lattice_materials(rng, G, False)]
+        scaled, lam, rows = scale_production(mats, target)
+        if rows <= 0.98:
+            return scaled
+    raise RuntimeError("no seeded material set met the offspring row-sum cap")
+
+
+def lattice_problem(n=17, pitch=1.26, radius=0.54, G=7, seed=3, mesh_n=34, n_tbins=50,
+                    mats=None, name="config3"):
+    """2D n x n lattice of z-cylinders in a reflective box (z infinite)."""
+    rng = np.random.default_rng([seed, 1000])
+    if mats is None:
+        mats = config3_materials(seed, G)
+    side = n * pitch
+    surfs, hs = box_surfaces((0, 0, 0), (side, side, 0), "reflect", axes=(0, 1))
+    cells = [{"halfspaces": hs, "material": -1}]
+    pins = np.where(rng.uniform(size=n * n) < 0.25, 1, 0).astype(int)
+    lat = {"nx": n, "ny": n, "x0": 0.0, "y0": 0.0, "pitch": float(pitch),
+           "radius": float(radius), "pin_material": pins.tolist(), "matrix_material": 2}
+    src = source("box", (0, 0, 0), (side, side, 0), "iso", G, 0)
+    t_edges = log_time_edges(n_tbins)
+    tal = [mesh(x=np.linspace(0, side, mesh_n + 1), y=np.linspace(0, side, mesh_n + 1),
+                t=t_edges)]
+    return problem(name, G, log_speeds(G), mats, surfs, cells, src, tal, t_edges[-1], lat)
+
+
+def config3(seed=3):
+    """17x17 lattice of cylinders (r=0.54, pitch 1.26) in a reflective box, 7 groups,
+    3 seeded materials (two pin fills, one matrix), production scaled to spectral radius 0.9,
+    uniform volumetric source, 34x34x7x50 space-group-time mesh."""
+    return lattice_problem(seed=seed)
+
+
+def config4_materials(seed=4, G=7, n_mat=4):
+    rng = np.random.default_rng(seed)
+    mats = []
+    for _ in range(n_mat):
+        sigma_t = rng.uniform(0.5, 3.0, G)
+        S = seeded_scatter(rng, G, sigma_t, 0.3, 0.95)
+        mats.append(material(sigma_t, S))
+    return mats
+
+
+def slab_stack(thickness=200.0, n_layers=40, G=7, seed=4, detector=2.0, ww_bin=5.0,
+               name="config4"):
+    """Deep-penetration x-layered slab stack (infinite in y, z), vacuum both ends, cosine
+    (isotropic-flux) surface source at x=0 in group 1; tally 0 = detector on the last
+    `detector` cm, tally 1 = coarse space-group mesh used to train weight windows."""
+    mats = config4_materials(seed, G)
+    dx = thickness / n_layers
+    xs = [i * dx for i in range(n_layers + 1)]
+    surfs = []
+    for i, x in enumerate(xs):
+        bc = "vacuum" if i in (0, n_layers) else "interior"
+        surfs.append({"kind": "PX", "coef": [float(x)], "bc": bc})
+    cells = [{"halfspaces": [(i, +1), (i + 1, -1)], "material": i % len(mats)}
+             for i in range(n_layers)]
+    src = source("surface_x0", (0, 0, 0), (0, 0, 0), "cos_x", G, 0)
+    n_ww = max(1, int(round(thickness / ww_bin)))
+    tal = [mesh(x=(thickness - detector, thickness)),
+           mesh(x=np.linspace(0.0, thickness, n_ww + 1))]
+    return problem(name, G, log_speeds(G), mats, surfs, cells, src, tal, INF)
+
+
+def config4(seed=4, thickness=200.0):
+    return slab_stack(thickness=thickness, seed=seed)
+
+
+def config5(seed=5, n_problems=256, n_lo=1e4, n_hi=1e6):
+    """256 independent problems of uneven size: types drawn from {1D slab, 2D slab, lattice},
+    G ~ U{1..7}, histories log-uniform in [n_lo, n_hi].  Returns (problems, n_histories)."""
+    rng = np.random.default_rng(seed)
+    probs, nh = [], []
+    for i in range(n_problems):
+        kind = int(rng.integers(0, 3))
+        G = int(rng.integers(1, 8))
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        sub = int(rng.integers(0, 2**31))
+        if kind == 0:
+            probs.append(_slab1d(sub, G, f"p{i}_slab1d"))
+        elif kind == 1:
+            probs.append(_slab2d(sub, G, f"p{i}_slab2d"))
+        else:
+            probs.append(_small_lattice(sub, G, f"p{i}_lattice"))
+        nh.append(n)
+    return probs, nh
+
+
+def _slab1d(seed, G, name):
+    rng = np.random.default_rng(seed)
+    n_layers = int(rng.integers(1, 5))
+    L = float(rng.uniform(2.0, 10.0))
+    xs = np.linspace(0.0, L, n_layers + 1)
+    mats = []
+    for _ in range(n_layers):
+        st = rng.uniform(0.2, 2.0, G)
+        mats.append(material(st, seeded_scatter(rng, G, st, 0.3, 0.9)))
+    surfs = [{"kind": "PX", "coef": [float(x)],
+              "bc": "vacuum" if i in (0, n_layers) else "interior"} for i, x in enumerate(xs)]
+    cells = [{"halfspaces": [(i, +1), (i + 1, -1)], "material": i} for i in range(n_layers)]
+    src = source("box", (0, 0, 0), (L, 0, 0), "iso", G, 0)
+    tal = [mesh(x=np.linspace(0.0, L, 21))]
+    return problem(name, G, log_speeds(G), mats, surfs, cells, src, tal)
+
+
+def _slab2d(seed, G, name):
+    rng = np.random.default_rng(seed)
+    L = float(rng.uniform(2.0, 10.0))
+    surfs = [{"kind": "PX", "coef": [0.0], "bc": "vacuum"},
+             {"kind": "PX", "coef": [L / 2], "bc": "interior"},
+             {"kind": "PX", "coef": [L], "bc": "vacuum"},
+             {"kind": "PY", "coef": [0.0], "bc": "reflect"},
+             {"kind": "PY", "coef": [L / 2], "bc": "interior"},
+             {"kind": "PY", "coef": [L], "bc": "reflect"}]
+    mats, cells = [], []
+    for j in range(2):
+        for i in range(2):
+            st = rng.uniform(0.2, 2.0, G)
+            mats.append(material(st, seeded_scatter(rng, G, st, 0.3, 0.9)))
+            cells.append({"halfspaces": [(i, +1), (i + 1, -1), (3 + j, +1), (4 + j, -1)],
+                          "material": len(mats) - 1})
+    src = source("box", (0, 0, 0), (L, L, 0), "iso", G, 0)
+    tal = [mesh(x=np.linspace(0.0, L, 11), y=np.linspace(0.0, L, 11))]
+    return problem(name, G, log_speeds(G), mats, surfs, cells, src, tal)
+
+
+def _small_lattice(seed, G, name):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 8))
+    mats = config3_materials(int(rng.integers(0, 2**31)), G)
+    p = lattice_problem(n=n, G=G, seed=int(rng.integers(0, 2**31)), mesh_n=2 * n, n_tbins=10,
+                        mats=mats, name=name)
+    return p
+
+
+def by_name(name, **kw):
+    return {"config1": config1, "config2": config2, "config3": config3,
+            "config4": config4}[name](**kw)
