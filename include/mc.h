@@ -1,0 +1,237 @@
+/*
+ * mc.h -- C ABI of libmcgb: GB300 (sm_103a) multigroup, time-dependent Monte Carlo random walk.
+ *
+ * The library implements the transport method whose problem class the MC/DC paper states in
+ * its Section 3: fixed-source multigroup transport on quadric-surface constructive solid geometry
+ * (here planes x/y/z, z-cylinders and a square pin lattice), a time-dependent source, a time
+ * census and time-dependent mesh tallies scored with the track-length estimator (Section 3.1).
+ * Per particle the walk samples the distance to collision, compares it with the distance to the
+ * next surface and to the census, moves the particle and scores its track length into an
+ * (x, y, z, group, time) mesh, then samples the collision: scatter to a new group, secondary
+ * production into a particle bank, or capture.
+ *
+ * Conventions for every entry point:
+ *   - Return value: MC_OK (0) or a negative mc_status.  Nothing aborts, traps or asserts; the
+ *     message of the last failure on the calling thread is returned by mc_last_error().
+ *   - Ownership: every array in a descriptor is copied by mc_problem_create; the caller keeps
+ *     ownership of its memory.  Output buffers are caller-allocated host memory unless an
+ *     argument says "device".
+ *   - Streams: `stream` is a cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream) or NULL
+ *     for the legacy default stream.  mc_run is asynchronous on that stream; device-side errors
+ *     (bank overflow, watchdog) are reported by mc_wait / mc_tally_get, which synchronise.
+ *   - Units: cm, s, 1/cm, cm/s.  Tally values are per source particle.
+ */
+#ifndef MCGB_MC_H
+#define MCGB_MC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------- status codes */
+typedef enum {
+  MC_OK = 0,
+  MC_ERR_INVALID = -1,   /* a descriptor or argument failed validation */
+  MC_ERR_CUDA = -2,      /* a CUDA runtime call failed (message in mc_last_error) */
+  MC_ERR_OOM = -3,       /* device allocation failed */
+  MC_ERR_BANK_FULL = -4, /* the secondary/birth bank overflowed during the run */
+  MC_ERR_TIMEOUT = -5,   /* the device watchdog (iteration or barrier-wait budget) expired */
+  MC_ERR_STATE = -6,     /* call out of order (e.g. tally read before any run) */
+  MC_ERR_LOST = -7       /* particles left the geometry (no cell contains them) */
+} mc_status;
+
+/* ------------------------------------------------------------------------- limits */
+#define MC_MAX_GROUPS 32
+#define MC_MAX_MATERIALS 255
+#define MC_MAX_SURFACES 255
+#define MC_MAX_CELLS 255
+#define MC_MAX_HALFSPACES 16
+#define MC_MAX_LATTICE 255 /* per axis */
+#define MC_MAX_TALLIES 4
+
+/* ------------------------------------------------------------------------- geometry */
+typedef enum { MC_SURF_PX = 0, MC_SURF_PY = 1, MC_SURF_PZ = 2, MC_SURF_CZ = 3 } mc_surface_kind;
+typedef enum { MC_BC_INTERIOR = 0, MC_BC_VACUUM = 1, MC_BC_REFLECT = 2 } mc_boundary;
+
+/* Surface f(x,y,z) = 0.  Planes: f = x - coef[0] (y, z likewise).  Cylinder parallel to z:
+ * f = (x - coef[0])^2 + (y - coef[1])^2 - coef[2]^2.  Reflection is supported on planes only. */
+typedef struct {
+  int kind;       /* mc_surface_kind */
+  double coef[3];
+  int bc;         /* mc_boundary */
+} mc_surface;
+
+/* A cell is the intersection of half-spaces; sense +1 means f >= 0, -1 means f < 0.
+ * material >= 0 fills the cell; material == -1 fills it with the lattice, which must cover the
+ * cell's extent exactly (the lattice's outer walls are the cell's own surfaces). */
+typedef struct {
+  int n_halfspaces;
+  int surface[MC_MAX_HALFSPACES];
+  int sense[MC_MAX_HALFSPACES];
+  int material;
+} mc_cell;
+
+/* Square lattice of nx x ny elements of side `pitch`, lower-left corner (x0, y0); element (i, j)
+ * holds a z-cylinder of `radius` centred in it filled with pin_material[j*nx + i] (or no pin if
+ * that entry is -1) inside matrix_material. */
+typedef struct {
+  int nx, ny;
+  double x0, y0, pitch, radius;
+  const int* pin_material; /* [ny*nx] */
+  int matrix_material;
+} mc_lattice;
+
+/* ------------------------------------------------------------------------- source */
+typedef enum { MC_SRC_BOX = 0, MC_SRC_SURFACE_X0 = 1 } mc_source_pos;
+typedef enum { MC_DIR_ISO = 0, MC_DIR_BEAM_X = 1, MC_DIR_COS_X = 2 } mc_source_dir;
+
+/* Position uniform in the box [lo, hi] (or on the plane x = lo[0] with y, z uniform in
+ * [lo, hi]); direction isotropic, the +x beam, or cosine-distributed into +x (the entering
+ * current of an isotropic angular flux); group from group_pdf; time uniform in [t0, t1]. */
+typedef struct {
+  int pos;  /* mc_source_pos */
+  double lo[3], hi[3];
+  int dir;  /* mc_source_dir */
+  const double* group_pdf; /* [n_groups], non-negative, not necessarily normalised */
+  double t0, t1;
+} mc_source;
+
+/* ------------------------------------------------------------------------- tallies */
+/* Track-length mesh tally over strictly increasing edges (the outermost may be +-inf).
+ * Bins are laid out [z][y][x][group][t]. */
+typedef struct {
+  int nx, ny, nz, nt;
+  const double *x, *y, *z, *t; /* nx+1, ny+1, nz+1, nt+1 edges */
+} mc_mesh_tally;
+
+/* ------------------------------------------------------------------------- problem */
+typedef struct {
+  int n_groups;     /* G */
+  int n_materials;  /* M */
+  const double* sigma_t; /* [M][G] total cross section */
+  const double* sigma_s; /* [M][G][G] scattering, row = from-group, column = to-group */
+  const double* sigma_f; /* [M][G] production cross section */
+  const double* nu;      /* [M][G] mean secondaries per production event (<= 64) */
+  const double* chi;     /* [M][G] secondary group spectrum */
+  const double* speed;   /* [G] group speeds */
+  int n_surfaces;
+  const mc_surface* surfaces;
+  int n_cells;
+  const mc_cell* cells;
+  const mc_lattice* lattice; /* NULL if no cell uses a lattice */
+  mc_source source;
+  int n_tallies;
+  const mc_mesh_tally* tallies;
+  double t_census;           /* final census time; +inf for steady state */
+} mc_problem_desc;
+
+typedef struct mc_problem mc_problem; /* opaque, library-owned */
+
+/* ------------------------------------------------------------------------- run options */
+typedef enum { MC_FP32 = 0, MC_FP64 = 1 } mc_precision;
+typedef enum { MC_TALLY_FIXED64 = 0, MC_TALLY_FP64 = 1 } mc_tally_mode;
+
+typedef struct {
+  int precision;          /* mc_precision: arithmetic of positions/directions/distances */
+  int tally_mode;         /* mc_tally_mode: int64 fixed point (deterministic) or FP64 atomics */
+  int fixed_bits;         /* fixed-point scale 2^fixed_bits (default 32) */
+  int n_batches;          /* statistical batches, >= 2 (default 32) */
+  uint64_t bank_capacity; /* particles in flight (0 = library default) */
+  int block_size;         /* threads per CTA (0 = autotuned default) */
+  int blocks_per_sm;      /* CTAs per SM (0 = as many as fit) */
+  uint64_t max_iterations;/* watchdog: event iterations before MC_ERR_TIMEOUT (0 = 2^20) */
+  int aggregate_atomics;  /* 1 = warp-aggregated tally atomics (default), 0 = one per thread */
+  int ww_enable;          /* 1 = apply the weight-window table set by mc_ww_set_table */
+  uint64_t log_first, log_count; /* log every event of histories [log_first, +log_count) */
+  uint64_t log_capacity;  /* event records kept (0 = 64 per logged history) */
+  uint64_t first_history; /* history indices run are [first_history, first_history + n) */
+} mc_run_opts;
+
+/* Fills the defaults listed above. */
+void mc_run_opts_default(mc_run_opts* o);
+
+/* Event record of the debug log (one per flight of a logged history).  kind: 0 collision,
+ * 1 surface, 2 census, 3 lost.  outcome: collision 0 scatter / 1 production / 2 capture;
+ * surface 0 transmit / 1 reflect / 2 leak / 3 lattice wall / 4 pin.  Position, direction, group,
+ * time and weight are the values at the end of the flight, before the event is handled. */
+typedef struct {
+  uint64_t tag, root;
+  uint32_t k;
+  int32_t kind, outcome, n_child, cell, elem, in_pin, g;
+  double x, y, z, ux, uy, uz, t, w;
+} mc_event;
+
+/* Counters summed over a run, in this order. */
+typedef enum {
+  MC_C_SOURCE = 0, MC_C_SECONDARY, MC_C_CAPTURE, MC_C_PRODUCTION, MC_C_LEAK, MC_C_CENSUS,
+  MC_C_LOST, MC_C_FLIGHT, MC_C_COLLISION, MC_C_SCATTER, MC_C_SURFACE, MC_C_REFLECT,
+  MC_C_WW_SPLIT, MC_C_WW_KILL, MC_C_ITERATIONS, MC_NCOUNTERS
+} mc_counter;
+
+/* ------------------------------------------------------------------------- entry points */
+
+/* Validates `d` on the host (returns MC_ERR_INVALID before touching the GPU), builds the
+ * per-material sampling tables (scatter-group CDFs, channel thresholds, chi CDFs) and the
+ * geometry/tally tables, and uploads them to the current device.  *out receives a handle owned
+ * by the library; release it with mc_problem_destroy. */
+int mc_problem_create(const mc_problem_desc* d, mc_problem** out);
+
+/* Runs n_histories source particles (history indices first_history + 0..n-1, each with its whole lineage of
+ * secondaries) with the given 64-bit seed, asynchronously on `stream`.  Tallies and counters of
+ * the previous run are replaced.  Histories are split into opts->n_batches contiguous batches
+ * whose tallies give the statistical error.  The paper's time census, track-length estimator and
+ * secondary production are Section 3 features; the random walk itself is the textbook analog one.
+ * Returns MC_ERR_INVALID for bad options, MC_ERR_OOM / MC_ERR_CUDA for launch failures. */
+int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts* opts,
+           void* stream);
+
+/* Waits for the last run and returns its device status (MC_OK, MC_ERR_BANK_FULL,
+ * MC_ERR_TIMEOUT, MC_ERR_LOST). */
+int mc_wait(mc_problem* p);
+
+/* Shape of a tally: {nz, ny, nx, G, nt}.  tally_id == n_tallies addresses the leakage tally,
+ * shape {1, 1, n_surfaces, 1, 1}: weight leaving through each vacuum surface. */
+int mc_tally_shape(const mc_problem* p, int tally_id, int64_t shape[5]);
+
+/* Copies the per-source-particle mean and its standard error (from the spread of the batch
+ * means) of every bin of a tally into host arrays of n >= bins elements.  Synchronises. */
+int mc_tally_get(mc_problem* p, int tally_id, double* mean, double* std_err, size_t n);
+
+/* Copies the per-batch means per source particle, out[n_batches][bins] (n >= n_batches * bins),
+ * of a tally, so that the error of any function of several bins (e.g. a total) can be formed
+ * from the spread of the batch values.  Synchronises. */
+int mc_tally_batches(mc_problem* p, int tally_id, double* out, size_t n, int* n_batches);
+
+/* Copies the MC_NCOUNTERS run counters into counters[n]. Synchronises. */
+int mc_counters_get(mc_problem* p, int64_t* counters, size_t n);
+
+/* Copies up to `cap` event records of the last run's logged histories; *n_out receives the
+ * number copied.  Records are in device completion order (sort by (tag, k) to compare). */
+int mc_event_log(mc_problem* p, mc_event* out, size_t cap, size_t* n_out);
+
+/* Device time of the last run's phases, from CUDA events recorded on the run's stream around
+ * the transport kernel and around the batch-statistics kernel (milliseconds).  Synchronises. */
+int mc_run_timing(mc_problem* p, double* transport_ms, double* stats_ms);
+
+/* Bytes of sampling, geometry and tally tables that mc_problem_create copied to the device
+ * (both tracking precisions); 0 for NULL. */
+size_t mc_problem_table_bytes(const mc_problem* p);
+
+/* Releases the problem and its device memory.  NULL is ignored. */
+void mc_problem_destroy(mc_problem* p);
+
+/* Thread-local message describing the last failure ("" if none). */
+const char* mc_last_error(void);
+
+/* Philox4x32-10 (Salmon et al., SC'11) on the device: out[i] = Philox(key = seed, ctr = ctr[i])
+ * for n counters; ctr and out are DEVICE arrays of 4*n uint32 (counter words c0..c3).  This is
+ * the generator every random draw of the walk uses, exposed for verification. */
+int mc_philox(uint64_t seed, const uint32_t* ctr, uint32_t* out, uint64_t n, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCGB_MC_H */

@@ -1,0 +1,768 @@
+// Host half of libmcgb: the C ABI declared in include/mc.h.
+//
+// mc_problem_create validates a problem description, builds the sampling tables (channel
+// thresholds, scatter-group and secondary-spectrum CDFs, geometry and tally tables) once in FP64
+// and packs them into two blobs (FP32 and FP64 tracking) that every CTA stages into shared memory.
+// mc_run zeroes the per-batch tallies, launches the persistent transport kernel cooperatively and
+// the batch-statistics kernel on the caller's stream.  Readback calls synchronise and turn batch
+// sums into per-source-particle means and standard errors.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "mc_internal.h"
+
+namespace mcgb {
+template <typename R>
+cudaError_t launch_transport(const RunParams& P, int grid, int block, size_t smem, cudaStream_t s);
+template <typename R>
+cudaError_t transport_occupancy(int block, size_t smem, int* per_sm);
+cudaError_t launch_batch_stats(const void* tally, int fp64, double inv_scale, uint64_t bins, int nb,
+                               uint64_t n_hist, double* tot, double* s1, double* s2, cudaStream_t s);
+cudaError_t launch_philox(uint64_t seed, const uint4* ctr, uint4* out, uint64_t n, cudaStream_t s);
+}  // namespace mcgb
+
+using namespace mcgb;
+
+// ------------------------------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+static int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? MC_ERR_OOM : MC_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+// ------------------------------------------------------------------------------------------ memory pool
+// Device blocks are recycled across problems instead of returned to the driver, so creating and
+// destroying problems in a loop does not pay cudaMalloc/cudaFree each time.
+namespace {
+struct PoolBlock {
+  int dev;
+  void* ptr;
+};
+std::mutex g_pool_mu;
+std::multimap<size_t, PoolBlock> g_pool;
+
+int pool_alloc(void** out, size_t bytes, int dev) {
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (auto it = g_pool.lower_bound(bytes); it != g_pool.end() && it->first <= 2 * bytes + (1 << 20); ++it) {
+      if (it->second.dev == dev) {
+        *out = it->second.ptr;
+        g_pool.erase(it);
+        return MC_OK;
+      }
+    }
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    // release cached blocks of this device and retry once
+    std::vector<void*> drop;
+    {
+      std::lock_guard<std::mutex> lk(g_pool_mu);
+      for (auto it = g_pool.begin(); it != g_pool.end();) {
+        if (it->second.dev == dev) {
+          drop.push_back(it->second.ptr);
+          it = g_pool.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+    for (void* d : drop) cudaFree(d);
+    e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  }
+  *out = p;
+  return MC_OK;
+}
+
+// a block must be returned with the size it was requested with
+void pool_free(void* p, size_t bytes, int dev) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  g_pool.insert({bytes, PoolBlock{dev, p}});
+}
+
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  int dev = 0;
+  int ensure(size_t want, int device) {
+    if (ptr && bytes >= want && dev == device) return MC_OK;
+    release();
+    int rc = pool_alloc(&ptr, want, device);
+    if (rc != MC_OK) {
+      ptr = nullptr;
+      return rc;
+    }
+    bytes = want;
+    dev = device;
+    return MC_OK;
+  }
+  void release() {
+    pool_free(ptr, bytes, dev);
+    ptr = nullptr;
+    bytes = 0;
+  }
+};
+}  // namespace
+
+// ------------------------------------------------------------------------------------------ problem
+struct HostTally {
+  int n[4];
+  std::vector<double> e[4];
+};
+
+struct mc_problem {
+  int dev = 0;
+  int G = 0, M = 0, n_surf = 0, n_cell = 0, n_tally = 0;
+  int total_bins = 0, leak_offset = 0;
+  std::vector<HostTally> tallies;
+  std::vector<uint8_t> blob[2];  // [0] FP32 tables, [1] FP64 tables
+  DevBuf d_blob[2];
+  DevBuf d_ctl, d_tally, d_stats, d_log, d_banks;
+  // last run
+  int has_run = 0;
+  uint64_t n_hist = 0;
+  int n_batches = 0;
+  cudaStream_t stream = nullptr;
+  uint64_t log_cap = 0;
+  int last_status = MC_OK;
+  int tally_fp64 = 0;
+  double fixed_scale = 1.0;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // transport start, transport end, stats end
+  // weight windows
+  int ww_set = 0, ww_n[3] = {0, 0, 0};
+  DevBuf d_ww;
+};
+
+namespace {
+
+bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
+
+int validate(const mc_problem_desc* d) {
+  if (!d) return fail(MC_ERR_INVALID, "descriptor is NULL");
+  const int G = d->n_groups, M = d->n_materials;
+  if (G < 1 || G > MC_MAX_GROUPS) return fail(MC_ERR_INVALID, "n_groups=%d outside [1,%d]", G, MC_MAX_GROUPS);
+  if (M < 1 || M > MC_MAX_MATERIALS) return fail(MC_ERR_INVALID, "n_materials=%d outside [1,%d]", M, MC_MAX_MATERIALS);
+  if (!d->sigma_t || !d->sigma_s || !d->sigma_f || !d->nu || !d->chi || !d->speed)
+    return fail(MC_ERR_INVALID, "cross-section array is NULL");
+  for (int g = 0; g < G; ++g)
+    if (!(std::isfinite(d->speed[g]) && d->speed[g] > 0.0)) return fail(MC_ERR_INVALID, "speed[%d] must be > 0", g);
+  for (int m = 0; m < M; ++m) {
+    double chi_sum = 0.0;
+    bool any_f = false;
+    for (int g = 0; g < G; ++g) {
+      const double st = d->sigma_t[m * G + g], sf = d->sigma_f[m * G + g], nu = d->nu[m * G + g];
+      const double ch = d->chi[m * G + g];
+      if (!finite_nonneg(st) || !finite_nonneg(sf) || !finite_nonneg(nu) || !finite_nonneg(ch))
+        return fail(MC_ERR_INVALID, "material %d group %d: negative or non-finite data", m, g);
+      if (nu > 64.0) return fail(MC_ERR_INVALID, "material %d group %d: nu above 64", m, g);
+      double ss = 0.0;
+      for (int h = 0; h < G; ++h) {
+        const double v = d->sigma_s[(m * G + g) * G + h];
+        if (!finite_nonneg(v)) return fail(MC_ERR_INVALID, "material %d sigma_s[%d][%d] invalid", m, g, h);
+        ss += v;
+      }
+      if (ss + sf > st * (1.0 + 1e-12))
+        return fail(MC_ERR_INVALID, "material %d group %d: sigma_s + sigma_f exceeds sigma_t", m, g);
+      chi_sum += ch;
+      any_f = any_f || (sf > 0.0 && nu > 0.0);
+    }
+    if (any_f && !(chi_sum > 0.0)) return fail(MC_ERR_INVALID, "material %d produces secondaries but chi sums to 0", m);
+  }
+  if (d->n_surfaces < 1 || d->n_surfaces > MC_MAX_SURFACES || !d->surfaces)
+    return fail(MC_ERR_INVALID, "n_surfaces=%d outside [1,%d]", d->n_surfaces, MC_MAX_SURFACES);
+  for (int s = 0; s < d->n_surfaces; ++s) {
+    const mc_surface& S = d->surfaces[s];
+    if (S.kind < MC_SURF_PX || S.kind > MC_SURF_CZ) return fail(MC_ERR_INVALID, "surface %d: bad kind", s);
+    if (S.bc < MC_BC_INTERIOR || S.bc > MC_BC_REFLECT) return fail(MC_ERR_INVALID, "surface %d: bad bc", s);
+    if (S.kind == MC_SURF_CZ && S.bc == MC_BC_REFLECT)
+      return fail(MC_ERR_INVALID, "surface %d: reflection is supported on planes only", s);
+    for (int i = 0; i < 3; ++i)
+      if (!std::isfinite(S.coef[i])) return fail(MC_ERR_INVALID, "surface %d: non-finite coefficient", s);
+    if (S.kind == MC_SURF_CZ && !(S.coef[2] > 0.0)) return fail(MC_ERR_INVALID, "surface %d: radius must be > 0", s);
+  }
+  if (d->n_cells < 1 || d->n_cells > MC_MAX_CELLS || !d->cells)
+    return fail(MC_ERR_INVALID, "n_cells=%d outside [1,%d]", d->n_cells, MC_MAX_CELLS);
+  bool uses_lattice = false;
+  for (int c = 0; c < d->n_cells; ++c) {
+    const mc_cell& C = d->cells[c];
+    if (C.n_halfspaces < 1 || C.n_halfspaces > MC_MAX_HALFSPACES)
+      return fail(MC_ERR_INVALID, "cell %d: n_halfspaces=%d outside [1,%d]", c, C.n_halfspaces, MC_MAX_HALFSPACES);
+    for (int i = 0; i < C.n_halfspaces; ++i) {
+      if (C.surface[i] < 0 || C.surface[i] >= d->n_surfaces) return fail(MC_ERR_INVALID, "cell %d: bad surface", c);
+      if (C.sense[i] != 1 && C.sense[i] != -1) return fail(MC_ERR_INVALID, "cell %d: sense must be +-1", c);
+    }
+    if (C.material == -1) uses_lattice = true;
+    else if (C.material < 0 || C.material >= M) return fail(MC_ERR_INVALID, "cell %d: bad material", c);
+  }
+  if (uses_lattice) {
+    const mc_lattice* L = d->lattice;
+    if (!L) return fail(MC_ERR_INVALID, "a cell uses the lattice but no lattice is given");
+    if (L->nx < 1 || L->ny < 1 || L->nx > MC_MAX_LATTICE || L->ny > MC_MAX_LATTICE)
+      return fail(MC_ERR_INVALID, "lattice size outside [1,%d]", MC_MAX_LATTICE);
+    if (!(L->pitch > 0.0) || !(L->radius > 0.0) || !(2.0 * L->radius < L->pitch) || !std::isfinite(L->x0) ||
+        !std::isfinite(L->y0))
+      return fail(MC_ERR_INVALID, "lattice needs pitch > 2 radius > 0");
+    if (!L->pin_material) return fail(MC_ERR_INVALID, "lattice pin_material is NULL");
+    for (int i = 0; i < L->nx * L->ny; ++i)
+      if (L->pin_material[i] < -1 || L->pin_material[i] >= M) return fail(MC_ERR_INVALID, "lattice pin %d: bad material", i);
+    if (L->matrix_material < 0 || L->matrix_material >= M) return fail(MC_ERR_INVALID, "lattice matrix material");
+  }
+  const mc_source& S = d->source;
+  if (S.pos < MC_SRC_BOX || S.pos > MC_SRC_SURFACE_X0 || S.dir < MC_DIR_ISO || S.dir > MC_DIR_COS_X)
+    return fail(MC_ERR_INVALID, "source kind");
+  if (!S.group_pdf) return fail(MC_ERR_INVALID, "source group_pdf is NULL");
+  double gs = 0.0;
+  for (int g = 0; g < G; ++g) {
+    if (!finite_nonneg(S.group_pdf[g])) return fail(MC_ERR_INVALID, "source group_pdf[%d] invalid", g);
+    gs += S.group_pdf[g];
+  }
+  if (!(gs > 0.0)) return fail(MC_ERR_INVALID, "source group_pdf sums to 0");
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(S.lo[i]) || !std::isfinite(S.hi[i]) || S.hi[i] < S.lo[i])
+      return fail(MC_ERR_INVALID, "source box must be finite with hi >= lo");
+  if (!std::isfinite(S.t0) || !std::isfinite(S.t1) || S.t1 < S.t0 || S.t0 < 0.0)
+    return fail(MC_ERR_INVALID, "source times need 0 <= t0 <= t1");
+  if (d->n_tallies < 0 || d->n_tallies > MC_MAX_TALLIES || (d->n_tallies > 0 && !d->tallies))
+    return fail(MC_ERR_INVALID, "n_tallies=%d outside [0,%d]", d->n_tallies, MC_MAX_TALLIES);
+  uint64_t bins = 0;
+  for (int t = 0; t < d->n_tallies; ++t) {
+    const mc_mesh_tally& T = d->tallies[t];
+    const int n[4] = {T.nx, T.ny, T.nz, T.nt};
+    const double* e[4] = {T.x, T.y, T.z, T.t};
+    for (int k = 0; k < 4; ++k) {
+      if (n[k] < 1 || n[k] > (1 << 16) || !e[k]) return fail(MC_ERR_INVALID, "tally %d axis %d: bad size", t, k);
+      for (int i = 0; i <= n[k]; ++i) {
+        if (std::isnan(e[k][i])) return fail(MC_ERR_INVALID, "tally %d: NaN edge", t);
+        if ((i > 0 && i < n[k] && !std::isfinite(e[k][i])) || (i > 0 && !(e[k][i] > e[k][i - 1])))
+          return fail(MC_ERR_INVALID, "tally %d axis %d: edges must increase (infinite only at the ends)", t, k);
+      }
+    }
+    bins += (uint64_t)T.nx * T.ny * T.nz * T.nt * G;
+  }
+  if (bins + d->n_surfaces > (1ull << 30)) return fail(MC_ERR_INVALID, "tallies too large");
+  if (!(d->t_census > 0.0)) return fail(MC_ERR_INVALID, "t_census must be > 0 (inf for steady state)");
+  return MC_OK;
+}
+
+// cumulative distribution of a non-negative row (summed in index order), normalised; entries from
+// the last positive one on are exactly 1 so that any u < 1 selects a bin with positive weight
+void cdf_row(const double* row, int n, double* out) {
+  double total = 0.0;
+  for (int i = 0; i < n; ++i) total += row[i];
+  double acc = 0.0;
+  for (int i = 0; i < n; ++i) {
+    acc += row[i];
+    out[i] = total > 0.0 ? acc / total : (i == n - 1 ? 1.0 : 0.0);
+  }
+  int last = n - 1;
+  while (last > 0 && !(row[last] > 0.0)) --last;
+  for (int i = last; i < n; ++i) out[i] = 1.0;
+}
+
+struct Blob {
+  std::vector<uint8_t> b;
+  Blob() : b(sizeof(TableHeader), 0) {}
+  int put(const void* src, size_t bytes) {
+    size_t off = (b.size() + 15) & ~size_t(15);
+    b.resize(off + ((bytes + 15) & ~size_t(15)), 0);
+    if (bytes) std::memcpy(b.data() + off, src, bytes);
+    return (int)off;
+  }
+  template <typename T>
+  int put(const std::vector<T>& v) {
+    return put(v.data(), v.size() * sizeof(T));
+  }
+  TableHeader* hdr() { return reinterpret_cast<TableHeader*>(b.data()); }
+};
+
+template <typename R>
+std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
+  const int G = d->n_groups, M = d->n_materials;
+  Blob B;
+  TableHeader H;
+  std::memset(&H, 0, sizeof(H));
+  H.G = G;
+  H.M = M;
+  H.n_surf = d->n_surfaces;
+  H.n_cell = d->n_cells;
+  H.real_bytes = (int)sizeof(R);
+  H.t_census = d->t_census;
+  for (int i = 0; i < 3; ++i) {
+    H.src_lo[i] = d->source.lo[i];
+    H.src_hi[i] = d->source.hi[i];
+  }
+  H.src_t0 = d->source.t0;
+  H.src_t1 = d->source.t1;
+  H.src_pos = d->source.pos;
+  H.src_dir = d->source.dir;
+  std::vector<R> st(M * G), ss(M * G), ssf(M * G), nu(M * G), scdf(M * G * G), chi(M * G);
+  std::vector<double> tmp(G);
+  for (int m = 0; m < M; ++m) {
+    for (int g = 0; g < G; ++g) {
+      const double* row = d->sigma_s + (m * G + g) * G;
+      double s = 0.0;
+      for (int h = 0; h < G; ++h) s += row[h];
+      st[m * G + g] = (R)d->sigma_t[m * G + g];
+      ss[m * G + g] = (R)s;
+      ssf[m * G + g] = (R)(s + d->sigma_f[m * G + g]);
+      nu[m * G + g] = (R)d->nu[m * G + g];
+      cdf_row(row, G, tmp.data());
+      for (int h = 0; h < G; ++h) scdf[(m * G + g) * G + h] = (R)tmp[h];
+    }
+    cdf_row(d->chi + m * G, G, tmp.data());
+    for (int h = 0; h < G; ++h) chi[m * G + h] = (R)tmp[h];
+  }
+  std::vector<R> v(G), inv_v(G), src(G);
+  for (int g = 0; g < G; ++g) {
+    v[g] = (R)d->speed[g];
+    inv_v[g] = (R)(1.0 / d->speed[g]);
+  }
+  cdf_row(d->source.group_pdf, G, tmp.data());
+  for (int g = 0; g < G; ++g) src[g] = (R)tmp[g];
+  H.o_st = B.put(st);
+  H.o_ss = B.put(ss);
+  H.o_ssf = B.put(ssf);
+  H.o_nu = B.put(nu);
+  H.o_v = B.put(v);
+  H.o_inv_v = B.put(inv_v);
+  H.o_scdf = B.put(scdf);
+  H.o_chi = B.put(chi);
+  H.o_src_cdf = B.put(src);
+  std::vector<int> skind(H.n_surf), sbc(H.n_surf);
+  std::vector<R> scoef(4 * H.n_surf, R(0));
+  for (int s = 0; s < H.n_surf; ++s) {
+    skind[s] = d->surfaces[s].kind;
+    sbc[s] = d->surfaces[s].bc;
+    for (int i = 0; i < 3; ++i) scoef[4 * s + i] = (R)d->surfaces[s].coef[i];
+  }
+  H.o_skind = B.put(skind);
+  H.o_sbc = B.put(sbc);
+  H.o_scoef = B.put(scoef);
+  std::vector<int> nhs(H.n_cell), hs(H.n_cell * MC_MAX_HALFSPACES, 0), cmat(H.n_cell);
+  for (int c = 0; c < H.n_cell; ++c) {
+    const mc_cell& C = d->cells[c];
+    nhs[c] = C.n_halfspaces;
+    for (int i = 0; i < C.n_halfspaces; ++i)
+      hs[c * MC_MAX_HALFSPACES + i] = C.surface[i] | (C.sense[i] < 0 ? (1 << 16) : 0);
+    cmat[c] = C.material;
+    if (C.material < 0) H.has_lat = 1;
+  }
+  H.o_nhs = B.put(nhs);
+  H.o_hs = B.put(hs);
+  H.o_cmat = B.put(cmat);
+  if (d->lattice) {
+    const mc_lattice* L = d->lattice;
+    H.has_lat = 1;
+    H.lat_nx = L->nx;
+    H.lat_ny = L->ny;
+    H.lat_matrix = L->matrix_material;
+    H.lat_x0 = L->x0;
+    H.lat_y0 = L->y0;
+    H.lat_pitch = L->pitch;
+    H.lat_r = L->radius;
+    std::vector<int> pins(L->pin_material, L->pin_material + L->nx * L->ny);
+    H.o_lpin = B.put(pins);
+  } else {
+    H.has_lat = 0;
+    std::vector<int> none(1, -1);
+    H.o_lpin = B.put(none);
+  }
+  H.n_tally = d->n_tallies;
+  int off = 0;
+  for (int t = 0; t < d->n_tallies; ++t) {
+    const mc_mesh_tally& T = d->tallies[t];
+    TallyDesc& D = H.tally[t];
+    D.nx = T.nx;
+    D.ny = T.ny;
+    D.nz = T.nz;
+    D.nt = T.nt;
+    std::vector<R> ex(T.x, T.x + T.nx + 1), ey(T.y, T.y + T.ny + 1), ez(T.z, T.z + T.nz + 1);
+    std::vector<double> et(T.t, T.t + T.nt + 1);
+    D.o_ex = B.put(ex);
+    D.o_ey = B.put(ey);
+    D.o_ez = B.put(ez);
+    D.o_et = B.put(et);
+    D.bin_offset = off;
+    D.n_bins = T.nx * T.ny * T.nz * G * T.nt;
+    off += D.n_bins;
+  }
+  H.leak_offset = off;
+  H.total_bins = off + H.n_surf;
+  B.b.resize((B.b.size() + 15) & ~size_t(15), 0);
+  H.blob_bytes = (int)B.b.size();
+  *B.hdr() = H;
+  return B.b;
+}
+
+int current_device(int* dev) {
+  cudaError_t e = cudaGetDevice(dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  return MC_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------ ABI
+extern "C" {
+
+const char* mc_last_error(void) { return g_err.c_str(); }
+
+void mc_run_opts_default(mc_run_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = MC_FP32;
+  o->tally_mode = MC_TALLY_FIXED64;
+  o->fixed_bits = 32;
+  o->n_batches = 32;
+  o->aggregate_atomics = 1;
+}
+
+int mc_problem_create(const mc_problem_desc* d, mc_problem** out) {
+  g_err.clear();
+  if (!out) return fail(MC_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  int rc = validate(d);
+  if (rc != MC_OK) return rc;
+  mc_problem* p = new mc_problem();
+  p->G = d->n_groups;
+  p->M = d->n_materials;
+  p->n_surf = d->n_surfaces;
+  p->n_cell = d->n_cells;
+  p->n_tally = d->n_tallies;
+  for (int t = 0; t < d->n_tallies; ++t) {
+    const mc_mesh_tally& T = d->tallies[t];
+    HostTally h;
+    h.n[0] = T.nx;
+    h.n[1] = T.ny;
+    h.n[2] = T.nz;
+    h.n[3] = T.nt;
+    p->tallies.push_back(h);
+  }
+  p->blob[0] = build_blob<float>(d);
+  p->blob[1] = build_blob<double>(d);
+  const TableHeader* H = reinterpret_cast<const TableHeader*>(p->blob[0].data());
+  p->total_bins = H->total_bins;
+  p->leak_offset = H->leak_offset;
+  rc = current_device(&p->dev);
+  for (int i = 0; i < 2 && rc == MC_OK; ++i) {
+    rc = p->d_blob[i].ensure(p->blob[i].size(), p->dev);
+    if (rc == MC_OK) {
+      cudaError_t e = cudaMemcpy(p->d_blob[i].ptr, p->blob[i].data(), p->blob[i].size(), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) rc = cuda_fail(e, "upload tables");
+    }
+  }
+  if (rc == MC_OK) rc = p->d_ctl.ensure(sizeof(Ctl), p->dev);
+  for (int i = 0; i < 3 && rc == MC_OK; ++i) {
+    cudaError_t e = cudaEventCreate(&p->ev[i]);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaEventCreate");
+  }
+  if (rc != MC_OK) {
+    mc_problem_destroy(p);
+    return rc;
+  }
+  *out = p;
+  return MC_OK;
+}
+
+void mc_problem_destroy(mc_problem* p) {
+  if (!p) return;
+  if (p->has_run && p->stream) cudaStreamSynchronize(p->stream);
+  p->d_blob[0].release();
+  p->d_blob[1].release();
+  p->d_ctl.release();
+  p->d_tally.release();
+  p->d_stats.release();
+  p->d_log.release();
+  p->d_banks.release();
+  p->d_ww.release();
+  for (int i = 0; i < 3; ++i)
+    if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+  delete p;
+}
+
+int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts* opts, void* stream) {
+  g_err.clear();
+  if (!p) return fail(MC_ERR_INVALID, "problem is NULL");
+  mc_run_opts o;
+  if (opts) o = *opts;
+  else mc_run_opts_default(&o);
+  if (o.precision != MC_FP32 && o.precision != MC_FP64) return fail(MC_ERR_INVALID, "precision");
+  if (o.tally_mode != MC_TALLY_FIXED64 && o.tally_mode != MC_TALLY_FP64) return fail(MC_ERR_INVALID, "tally_mode");
+  if (o.fixed_bits < 0 || o.fixed_bits > 48) return fail(MC_ERR_INVALID, "fixed_bits outside [0,48]");
+  if (o.n_batches < 2 || o.n_batches > 4096) return fail(MC_ERR_INVALID, "n_batches outside [2,4096]");
+  if (n_histories < (uint64_t)o.n_batches) return fail(MC_ERR_INVALID, "need at least n_batches histories");
+  if (n_histories >= (1ull << 32) || o.first_history + n_histories > (1ull << 32))
+    return fail(MC_ERR_INVALID, "history indices must stay below 2^32");
+  if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 256 || o.block_size % 32))
+    return fail(MC_ERR_INVALID, "block_size must be a multiple of 32 in [32,256]");
+  if (o.ww_enable && !p->ww_set) return fail(MC_ERR_STATE, "weight windows enabled but no table set");
+  int dev;
+  int rc = current_device(&dev);
+  if (rc != MC_OK) return rc;
+  if (dev != p->dev) return fail(MC_ERR_STATE, "problem was created on device %d, current is %d", p->dev, dev);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int fp64 = o.precision == MC_FP64;
+  const int lanes = fp64 ? kLanesFP64 : kLanesFP32;
+  uint64_t cap = o.bank_capacity;
+  if (cap == 0) {
+    cap = 1ull << 16;
+    while (cap < 2 * n_histories && cap < (1ull << 22)) cap <<= 1;
+  }
+  if (cap < 1024) return fail(MC_ERR_INVALID, "bank_capacity must be >= 1024");
+  const size_t bank_bytes = (size_t)cap * 16 * lanes;
+  rc = p->d_banks.ensure(4 * bank_bytes, p->dev);
+  if (rc != MC_OK) return rc;
+  const int nb = o.n_batches;
+  const uint64_t bins = (uint64_t)p->total_bins;
+  rc = p->d_tally.ensure((size_t)nb * bins * 8, p->dev);
+  if (rc == MC_OK) rc = p->d_stats.ensure((size_t)3 * bins * 8, p->dev);
+  if (rc != MC_OK) return rc;
+  uint64_t log_cap = 0;
+  if (o.log_count > 0) {
+    log_cap = o.log_capacity ? o.log_capacity : 64 * o.log_count;
+    rc = p->d_log.ensure(log_cap * sizeof(mc_event), p->dev);
+    if (rc != MC_OK) return rc;
+  }
+  RunParams P;
+  std::memset(&P, 0, sizeof(P));
+  char* banks = (char*)p->d_banks.ptr;
+  for (int side = 0; side < 2; ++side)
+    for (int l = 0; l < lanes; ++l) {
+      P.S[side][l] = (uint4*)(banks + (size_t)side * bank_bytes + (size_t)l * cap * 16);
+      P.B[side][l] = (uint4*)(banks + (size_t)(2 + side) * bank_bytes + (size_t)l * cap * 16);
+    }
+  P.cap_s = cap;
+  P.cap_b = cap;
+  P.ctl = (Ctl*)p->d_ctl.ptr;
+  P.tally = p->d_tally.ptr;
+  P.tally_fp64 = o.tally_mode == MC_TALLY_FP64;
+  P.aggregate = o.aggregate_atomics;
+  P.fixed_scale = std::ldexp(1.0, o.fixed_bits);
+  P.n_hist = n_histories;
+  P.hist_per_batch = (n_histories + nb - 1) / nb;
+  P.h_first = o.first_history;
+  P.n_batches = nb;
+  P.blob_bytes = (int)p->blob[fp64].size();
+  P.blob = (const uint4*)p->d_blob[fp64].ptr;
+  P.seed = seed;
+  P.max_iter = o.max_iterations ? o.max_iterations : (1ull << 20);
+  P.spin_limit = 1ull << 22;
+  P.log = o.log_count ? (mc_event*)p->d_log.ptr : nullptr;
+  P.log_cap = log_cap;
+  P.log_first = o.log_first;
+  P.log_count = o.log_count;
+  if (o.ww_enable) {
+    const double* base = (const double*)p->d_ww.ptr;
+    P.ww_on = 1;
+    P.ww_nx = p->ww_n[0];
+    P.ww_ny = p->ww_n[1];
+    P.ww_nz = p->ww_n[2];
+    P.ww_edges = base;
+    P.ww_center = base + (p->ww_n[0] + 1) + (p->ww_n[1] + 1) + (p->ww_n[2] + 1);
+    P.ww_upper = 2.0;
+    P.ww_lower = 0.5;
+    P.ww_split_max = 10;
+  }
+  CK(cudaMemsetAsync(p->d_ctl.ptr, 0, sizeof(Ctl), s));
+  CK(cudaMemsetAsync(p->d_tally.ptr, 0, (size_t)nb * bins * 8, s));
+  if (P.log) CK(cudaMemsetAsync(p->d_log.ptr, 0, log_cap * sizeof(mc_event), s));
+  const int block = o.block_size ? o.block_size : 256;
+  const size_t smem = P.blob_bytes;
+  int per_sm = 0;
+  CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm) : transport_occupancy<float>(block, smem, &per_sm));
+  if (per_sm < 1) return fail(MC_ERR_CUDA, "transport kernel does not fit on an SM (block %d, smem %zu)", block, smem);
+  if (o.blocks_per_sm > 0 && o.blocks_per_sm < per_sm) per_sm = o.blocks_per_sm;
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->dev));
+  const int grid = sms * per_sm;
+  CK(cudaEventRecord(p->ev[0], s));
+  CK(fp64 ? launch_transport<double>(P, grid, block, smem, s) : launch_transport<float>(P, grid, block, smem, s));
+  CK(cudaEventRecord(p->ev[1], s));
+  double* st = (double*)p->d_stats.ptr;
+  CK(launch_batch_stats(P.tally, P.tally_fp64, 1.0 / P.fixed_scale, bins, nb, n_histories, st, st + bins,
+                        st + 2 * bins, s));
+  CK(cudaEventRecord(p->ev[2], s));
+  p->has_run = 1;
+  p->n_hist = n_histories;
+  p->n_batches = nb;
+  p->stream = s;
+  p->log_cap = log_cap;
+  p->last_status = MC_OK;
+  p->tally_fp64 = P.tally_fp64;
+  p->fixed_scale = P.fixed_scale;
+  return MC_OK;
+}
+
+int mc_wait(mc_problem* p) {
+  if (!p) return fail(MC_ERR_INVALID, "problem is NULL");
+  if (!p->has_run) return fail(MC_ERR_STATE, "no run yet");
+  CK(cudaStreamSynchronize(p->stream));
+  int status = 0;
+  CK(cudaMemcpy(&status, (char*)p->d_ctl.ptr + offsetof(Ctl, status), sizeof(int), cudaMemcpyDeviceToHost));
+  p->last_status = status;
+  if (status == MC_ERR_BANK_FULL) return fail(status, "particle bank overflowed; raise bank_capacity");
+  if (status == MC_ERR_TIMEOUT) return fail(status, "device watchdog expired (iteration or barrier budget)");
+  if (status == MC_ERR_LOST) return fail(status, "particles left the geometry");
+  if (status != 0) return fail(MC_ERR_CUDA, "device status %d", status);
+  return MC_OK;
+}
+
+int mc_tally_shape(const mc_problem* p, int tally_id, int64_t shape[5]) {
+  if (!p || !shape) return fail(MC_ERR_INVALID, "NULL argument");
+  if (tally_id < 0 || tally_id > p->n_tally) return fail(MC_ERR_INVALID, "tally_id %d outside [0,%d]", tally_id, p->n_tally);
+  if (tally_id == p->n_tally) {
+    shape[0] = 1;
+    shape[1] = 1;
+    shape[2] = p->n_surf;
+    shape[3] = 1;
+    shape[4] = 1;
+    return MC_OK;
+  }
+  const HostTally& T = p->tallies[tally_id];
+  shape[0] = T.n[2];
+  shape[1] = T.n[1];
+  shape[2] = T.n[0];
+  shape[3] = p->G;
+  shape[4] = T.n[3];
+  return MC_OK;
+}
+
+int mc_tally_get(mc_problem* p, int tally_id, double* mean, double* std_err, size_t n) {
+  int64_t shp[5];
+  int rc = mc_tally_shape(p, tally_id, shp);
+  if (rc != MC_OK) return rc;
+  rc = mc_wait(p);
+  if (rc != MC_OK) return rc;
+  const size_t nbins = (size_t)(shp[0] * shp[1] * shp[2] * shp[3] * shp[4]);
+  if (n < nbins) return fail(MC_ERR_INVALID, "output holds %zu of %zu bins", n, nbins);
+  const TableHeader* H = reinterpret_cast<const TableHeader*>(p->blob[0].data());
+  const size_t first = tally_id == p->n_tally ? (size_t)H->leak_offset : (size_t)H->tally[tally_id].bin_offset;
+  const size_t bins = (size_t)p->total_bins;
+  std::vector<double> tot(nbins), s1(nbins), s2(nbins);
+  const double* st = (const double*)p->d_stats.ptr;
+  CK(cudaMemcpy(tot.data(), st + first, nbins * 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(s1.data(), st + bins + first, nbins * 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(s2.data(), st + 2 * bins + first, nbins * 8, cudaMemcpyDeviceToHost));
+  const double B = (double)p->n_batches;
+  for (size_t i = 0; i < nbins; ++i) {
+    if (mean) mean[i] = tot[i] / (double)p->n_hist;
+    if (std_err) {
+      const double var = (s2[i] - s1[i] * s1[i] / B) / (B * (B - 1.0));
+      std_err[i] = var > 0.0 ? std::sqrt(var) : 0.0;
+    }
+  }
+  return MC_OK;
+}
+
+int mc_tally_batches(mc_problem* p, int tally_id, double* out, size_t n, int* n_batches) {
+  int64_t shp[5];
+  int rc = mc_tally_shape(p, tally_id, shp);
+  if (rc != MC_OK) return rc;
+  rc = mc_wait(p);
+  if (rc != MC_OK) return rc;
+  const size_t nbins = (size_t)(shp[0] * shp[1] * shp[2] * shp[3] * shp[4]);
+  const int nb = p->n_batches;
+  if (n_batches) *n_batches = nb;
+  if (!out) return MC_OK;
+  if (n < nbins * (size_t)nb) return fail(MC_ERR_INVALID, "output holds %zu of %zu values", n, nbins * (size_t)nb);
+  const TableHeader* H = reinterpret_cast<const TableHeader*>(p->blob[0].data());
+  const size_t first = tally_id == p->n_tally ? (size_t)H->leak_offset : (size_t)H->tally[tally_id].bin_offset;
+  const size_t bins = (size_t)p->total_bins;
+  std::vector<int64_t> raw(nbins);
+  for (int j = 0; j < nb; ++j) {
+    CK(cudaMemcpy(raw.data(), (const char*)p->d_tally.ptr + ((size_t)j * bins + first) * 8, nbins * 8,
+                  cudaMemcpyDeviceToHost));
+    const uint64_t lo = ((uint64_t)j * p->n_hist + nb - 1) / nb, hi = ((uint64_t)(j + 1) * p->n_hist + nb - 1) / nb;
+    const double cnt = (double)(hi - lo);
+    for (size_t i = 0; i < nbins; ++i) {
+      double x;
+      if (p->tally_fp64) std::memcpy(&x, &raw[i], 8);
+      else x = (double)raw[i] / p->fixed_scale;
+      out[(size_t)j * nbins + i] = x / cnt;
+    }
+  }
+  return MC_OK;
+}
+
+int mc_counters_get(mc_problem* p, int64_t* counters, size_t n) {
+  if (!p || !counters) return fail(MC_ERR_INVALID, "NULL argument");
+  int rc = mc_wait(p);
+  if (rc != MC_OK && rc != MC_ERR_BANK_FULL && rc != MC_ERR_TIMEOUT && rc != MC_ERR_LOST) return rc;
+  Ctl c;
+  CK(cudaMemcpy(&c, p->d_ctl.ptr, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < n && i < (size_t)MC_NCOUNTERS; ++i)
+    counters[i] = i == MC_C_ITERATIONS ? (int64_t)c.iterations : (int64_t)c.counters[i];
+  return MC_OK;
+}
+
+int mc_event_log(mc_problem* p, mc_event* out, size_t cap, size_t* n_out) {
+  if (!p || !n_out) return fail(MC_ERR_INVALID, "NULL argument");
+  int rc = mc_wait(p);
+  if (rc != MC_OK) return rc;
+  unsigned long long n = 0;
+  CK(cudaMemcpy(&n, (char*)p->d_ctl.ptr + offsetof(Ctl, log_n), sizeof(n), cudaMemcpyDeviceToHost));
+  size_t m = (size_t)std::min<unsigned long long>(n, p->log_cap);
+  if (m > cap) m = cap;
+  if (m && out) CK(cudaMemcpy(out, p->d_log.ptr, m * sizeof(mc_event), cudaMemcpyDeviceToHost));
+  *n_out = m;
+  if (n > p->log_cap) return fail(MC_ERR_BANK_FULL, "event log overflowed (%llu records)", n);
+  return MC_OK;
+}
+
+size_t mc_problem_table_bytes(const mc_problem* p) {
+  return p ? p->blob[0].size() + p->blob[1].size() : 0;
+}
+
+int mc_run_timing(mc_problem* p, double* transport_ms, double* stats_ms) {
+  if (!p) return fail(MC_ERR_INVALID, "problem is NULL");
+  if (!p->has_run) return fail(MC_ERR_STATE, "no run yet");
+  CK(cudaEventSynchronize(p->ev[2]));
+  float a = 0.f, b = 0.f;
+  CK(cudaEventElapsedTime(&a, p->ev[0], p->ev[1]));
+  CK(cudaEventElapsedTime(&b, p->ev[1], p->ev[2]));
+  if (transport_ms) *transport_ms = a;
+  if (stats_ms) *stats_ms = b;
+  return MC_OK;
+}
+
+int mc_philox(uint64_t seed, const uint32_t* ctr, uint32_t* out, uint64_t n, void* stream) {
+  g_err.clear();
+  if (n == 0) return MC_OK;
+  if (!ctr || !out) return fail(MC_ERR_INVALID, "NULL device pointer");
+  if (((uintptr_t)ctr | (uintptr_t)out) & 15) return fail(MC_ERR_INVALID, "arrays must be 16-byte aligned");
+  CK(launch_philox(seed, (const uint4*)ctr, (uint4*)out, n, (cudaStream_t)stream));
+  return MC_OK;
+}
+
+}  // extern "C"

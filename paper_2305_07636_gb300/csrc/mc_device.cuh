@@ -1,0 +1,506 @@
+// Device building blocks of the random walk: Philox4x32-10, uniforms, particle state lanes,
+// geometry distances, track-length DDA scoring, collision / surface / source sampling.
+//
+// The steps follow the problem statement of the MC/DC paper (Section 3: quadric CSG, multigroup,
+// time-dependent source, time census, track-length mesh tallies, secondary production) with the
+// textbook analog random walk; every random number comes from Philox4x32-10 (Salmon et al., SC'11)
+// keyed by the run seed with the counter (particle tag, event index, block), so a history's
+// random numbers do not depend on how the GPU schedules it.
+#pragma once
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include "mc_internal.h"
+
+namespace mcgb {
+
+// ------------------------------------------------------------------------------------------ RNG
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t k0, uint32_t k1, uint4 c) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+template <typename R>
+struct Uni;
+// FP64: 52 random bits from the top 26 bits of two words, plus one half -> open interval (0,1)
+template <>
+struct Uni<double> {
+  static __device__ __forceinline__ double from(uint32_t a, uint32_t b) {
+    return (__uint2double_rn(a >> 6) * 67108864.0 + __uint2double_rn(b >> 6) + 0.5) *
+           (1.0 / 4503599627370496.0);
+  }
+};
+// FP32: 23 random bits of the first word plus one half -> open interval (0,1), exact in float
+template <>
+struct Uni<float> {
+  static __device__ __forceinline__ float from(uint32_t a, uint32_t) {
+    return (__uint2float_rn(a >> 9) + 0.5f) * 1.1920928955078125e-7f;
+  }
+};
+
+template <typename R>
+struct Pair2 {
+  R a, b;
+};
+
+// two uniforms of block `blk` of event `k` of the particle tagged (tlo, thi)
+template <typename R>
+__device__ __forceinline__ Pair2<R> draw(uint64_t seed, uint32_t tlo, uint32_t thi, uint32_t k,
+                                         uint32_t blk) {
+  const uint4 r = philox4x32_10((uint32_t)seed, (uint32_t)(seed >> 32), make_uint4(tlo, thi, k, blk));
+  return {Uni<R>::from(r.x, r.y), Uni<R>::from(r.z, r.w)};
+}
+
+__device__ __forceinline__ uint2 child_tag(uint64_t seed, uint32_t tlo, uint32_t thi, uint32_t k,
+                                           uint32_t j, uint32_t mark) {
+  const uint4 r = philox4x32_10((uint32_t)seed ^ kChildKeyXor, (uint32_t)(seed >> 32),
+                                make_uint4(tlo, thi, k, mark | j));
+  return make_uint2(r.x, r.y);
+}
+
+template <typename R>
+__device__ __forceinline__ R rinf();
+template <>
+__device__ __forceinline__ float rinf<float>() { return CUDART_INF_F; }
+template <>
+__device__ __forceinline__ double rinf<double>() { return CUDART_INF; }
+
+__device__ __forceinline__ float rlog(float u) { return logf(u); }
+__device__ __forceinline__ double rlog(double u) { return log(u); }
+__device__ __forceinline__ float rsqrt_(float v) { return sqrtf(v); }
+__device__ __forceinline__ double rsqrt_(double v) { return sqrt(v); }
+// (cos 2 pi u, sin 2 pi u)
+__device__ __forceinline__ void sincos2pi(float u, float* s, float* c) { sincospif(2.0f * u, s, c); }
+__device__ __forceinline__ void sincos2pi(double u, double* s, double* c) { sincospi(2.0 * u, s, c); }
+
+// ------------------------------------------------------------------------------------------ tables
+template <typename R>
+struct Tab {
+  const TableHeader* h;
+  const R *st, *ss, *ssf, *nu, *v, *inv_v, *scdf, *chi, *src_cdf, *scoef;
+  const int *skind, *sbc, *nhs, *hs, *cmat, *lpin;
+  R lx0, ly0, lp, lr;
+  int G;
+  __device__ explicit Tab(const char* base) {
+    h = reinterpret_cast<const TableHeader*>(base);
+    st = reinterpret_cast<const R*>(base + h->o_st);
+    ss = reinterpret_cast<const R*>(base + h->o_ss);
+    ssf = reinterpret_cast<const R*>(base + h->o_ssf);
+    nu = reinterpret_cast<const R*>(base + h->o_nu);
+    v = reinterpret_cast<const R*>(base + h->o_v);
+    inv_v = reinterpret_cast<const R*>(base + h->o_inv_v);
+    scdf = reinterpret_cast<const R*>(base + h->o_scdf);
+    chi = reinterpret_cast<const R*>(base + h->o_chi);
+    src_cdf = reinterpret_cast<const R*>(base + h->o_src_cdf);
+    scoef = reinterpret_cast<const R*>(base + h->o_scoef);
+    skind = reinterpret_cast<const int*>(base + h->o_skind);
+    sbc = reinterpret_cast<const int*>(base + h->o_sbc);
+    nhs = reinterpret_cast<const int*>(base + h->o_nhs);
+    hs = reinterpret_cast<const int*>(base + h->o_hs);
+    cmat = reinterpret_cast<const int*>(base + h->o_cmat);
+    lpin = reinterpret_cast<const int*>(base + h->o_lpin);
+    lx0 = (R)h->lat_x0;
+    ly0 = (R)h->lat_y0;
+    lp = (R)h->lat_pitch;
+    lr = (R)h->lat_r;
+    G = h->G;
+  }
+};
+
+// ------------------------------------------------------------------------------------------ state
+template <typename R>
+struct Part {
+  R x, y, z, ux, uy, uz;
+  double t, w;
+  uint32_t tlo, thi, k, pk, elem, root;
+};
+
+template <typename R>
+struct Lanes;
+
+// FP32 particle = 4 x 16 B: (x,y,z,ux) (uy,uz,elem,root) (t,w) (tag_lo,tag_hi,k,packed)
+template <>
+struct Lanes<float> {
+  static constexpr int N = kLanesFP32;
+  static __device__ __forceinline__ void load(Part<float>& p, uint4* const* L, uint64_t i) {
+    const float4 a = __ldcs(reinterpret_cast<const float4*>(L[0]) + i);
+    const float4 b = __ldcs(reinterpret_cast<const float4*>(L[1]) + i);
+    const double2 c = __ldcs(reinterpret_cast<const double2*>(L[2]) + i);
+    const uint4 d = __ldcs(L[3] + i);
+    p.x = a.x; p.y = a.y; p.z = a.z; p.ux = a.w;
+    p.uy = b.x; p.uz = b.y; p.elem = __float_as_uint(b.z); p.root = __float_as_uint(b.w);
+    p.t = c.x; p.w = c.y;
+    p.tlo = d.x; p.thi = d.y; p.k = d.z; p.pk = d.w;
+  }
+  static __device__ __forceinline__ void store(const Part<float>& p, uint4* const* L, uint64_t i) {
+    __stcs(reinterpret_cast<float4*>(L[0]) + i, make_float4(p.x, p.y, p.z, p.ux));
+    __stcs(reinterpret_cast<float4*>(L[1]) + i,
+           make_float4(p.uy, p.uz, __uint_as_float(p.elem), __uint_as_float(p.root)));
+    __stcs(reinterpret_cast<double2*>(L[2]) + i, make_double2(p.t, p.w));
+    __stcs(L[3] + i, make_uint4(p.tlo, p.thi, p.k, p.pk));
+  }
+};
+
+// FP64 particle = 6 x 16 B: (x,y) (z,ux) (uy,uz) (t,w) (tag_lo,tag_hi,k,packed) (elem,root,-,-)
+template <>
+struct Lanes<double> {
+  static constexpr int N = kLanesFP64;
+  static __device__ __forceinline__ void load(Part<double>& p, uint4* const* L, uint64_t i) {
+    const double2 a = __ldcs(reinterpret_cast<const double2*>(L[0]) + i);
+    const double2 b = __ldcs(reinterpret_cast<const double2*>(L[1]) + i);
+    const double2 c = __ldcs(reinterpret_cast<const double2*>(L[2]) + i);
+    const double2 d = __ldcs(reinterpret_cast<const double2*>(L[3]) + i);
+    const uint4 e = __ldcs(L[4] + i);
+    const uint4 f = __ldcs(L[5] + i);
+    p.x = a.x; p.y = a.y; p.z = b.x; p.ux = b.y; p.uy = c.x; p.uz = c.y;
+    p.t = d.x; p.w = d.y;
+    p.tlo = e.x; p.thi = e.y; p.k = e.z; p.pk = e.w;
+    p.elem = f.x; p.root = f.y;
+  }
+  static __device__ __forceinline__ void store(const Part<double>& p, uint4* const* L, uint64_t i) {
+    __stcs(reinterpret_cast<double2*>(L[0]) + i, make_double2(p.x, p.y));
+    __stcs(reinterpret_cast<double2*>(L[1]) + i, make_double2(p.z, p.ux));
+    __stcs(reinterpret_cast<double2*>(L[2]) + i, make_double2(p.uy, p.uz));
+    __stcs(reinterpret_cast<double2*>(L[3]) + i, make_double2(p.t, p.w));
+    __stcs(L[4] + i, make_uint4(p.tlo, p.thi, p.k, p.pk));
+    __stcs(L[5] + i, make_uint4(p.elem, p.root, 0u, 0u));
+  }
+};
+
+// ------------------------------------------------------------------------------------------ geometry
+__device__ __forceinline__ int lat_ix(uint32_t elem) { return (int)(elem & 0xFFu); }
+__device__ __forceinline__ int lat_iy(uint32_t elem) { return (int)((elem >> 8) & 0xFFu); }
+__device__ __forceinline__ uint32_t lat_pack(uint32_t elem, int ix, int iy) {
+  return (elem & 0xFFFF0000u) | (uint32_t)ix | ((uint32_t)iy << 8);
+}
+
+template <typename R>
+__device__ __forceinline__ int material_of(const Tab<R>& T, uint32_t pk, uint32_t elem) {
+  const int m = T.cmat[pk_cell(pk)];
+  if (m >= 0) return m;
+  if (pk_pin(pk)) return T.lpin[lat_iy(elem) * T.h->lat_nx + lat_ix(elem)];
+  return T.h->lat_matrix;
+}
+
+// distance to a plane, counted only while the motion leaves the half-space (sense +1: f >= 0)
+template <typename R>
+__device__ __forceinline__ R plane_dist(R pos, R u, R c, int sense) {
+  const bool leaving = sense > 0 ? (u < R(0)) : (u > R(0));
+  if (!leaving) return rinf<R>();
+  const R d = (c - pos) / u;
+  return d > R(0) ? d : R(0);
+}
+
+// distance to a z-cylinder: from inside the far root, from outside the near root when approaching
+template <typename R>
+__device__ __forceinline__ R cyl_dist(R x, R y, R ux, R uy, R x0, R y0, R r, bool inside) {
+  const R a = ux * ux + uy * uy;
+  if (a == R(0)) return rinf<R>();
+  const R dx = x - x0, dy = y - y0;
+  const R b = dx * ux + dy * uy;
+  const R c = dx * dx + dy * dy - r * r;
+  R disc = b * b - a * c;
+  if (inside) {
+    if (disc < R(0)) disc = R(0);
+    const R sq = rsqrt_(disc);
+    const R d = (b <= R(0)) ? (-b + sq) / a : -c / (b + sq);
+    return d > R(0) ? d : R(0);
+  }
+  if (b >= R(0) || disc <= R(0)) return rinf<R>();
+  const R d = c / (-b + rsqrt_(disc));
+  return d > R(0) ? d : R(0);
+}
+
+template <typename R>
+__device__ __forceinline__ R surf_f(const Tab<R>& T, int s, R x, R y, R z) {
+  const R* c = T.scoef + 4 * s;
+  switch (T.skind[s]) {
+    case MC_SURF_PX: return x - c[0];
+    case MC_SURF_PY: return y - c[0];
+    case MC_SURF_PZ: return z - c[0];
+    default: {
+      const R dx = x - c[0], dy = y - c[1];
+      return dx * dx + dy * dy - c[2] * c[2];
+    }
+  }
+}
+
+// first cell containing the point; if skip >= 0 the half-space on surface `skip` is taken to
+// have sense `skip_sense` without evaluating it (the point lies on that surface)
+template <typename R>
+__device__ int locate_cell(const Tab<R>& T, R x, R y, R z, int skip, int skip_sense) {
+  for (int c = 0; c < T.h->n_cell; ++c) {
+    bool ok = true, seen = skip < 0;
+    const int n = T.nhs[c];
+    for (int i = 0; i < n && ok; ++i) {
+      const int e = T.hs[c * MC_MAX_HALFSPACES + i];
+      const int s = e & 0xFFFF, sn = (e >> 16) ? -1 : 1;
+      if (s == skip) {
+        seen = true;
+        ok = sn == skip_sense;
+      } else {
+        const R f = surf_f(T, s, x, y, z);
+        ok = sn > 0 ? (f >= R(0)) : (f < R(0));
+      }
+    }
+    if (ok && seen) return c;
+  }
+  return -1;
+}
+
+template <typename R>
+__device__ __forceinline__ uint32_t pin_inside(const Tab<R>& T, R x, R y, int ix, int iy) {
+  if (T.lpin[iy * T.h->lat_nx + ix] < 0) return 0u;
+  const R dx = x - (T.lx0 + (R(ix) + R(0.5)) * T.lp), dy = y - (T.ly0 + (R(iy) + R(0.5)) * T.lp);
+  return (dx * dx + dy * dy - T.lr * T.lr) < R(0) ? 1u : 0u;
+}
+
+// lattice element and pin sense of a point inside the lattice cell
+template <typename R>
+__device__ __forceinline__ void lattice_locate(const Tab<R>& T, Part<R>& p) {
+  int ix = (int)floor((p.x - T.lx0) / T.lp), iy = (int)floor((p.y - T.ly0) / T.lp);
+  ix = min(max(ix, 0), T.h->lat_nx - 1);
+  iy = min(max(iy, 0), T.h->lat_ny - 1);
+  p.elem = lat_pack(p.elem, ix, iy);
+  p.pk = (p.pk & ~(1u << 13)) | (pin_inside(T, p.x, p.y, ix, iy) << 13);
+}
+
+struct Hit {
+  uint32_t type;
+  int dir;
+  uint32_t surf;
+};
+
+template <typename R>
+__device__ R boundary_distance(const Tab<R>& T, const Part<R>& p, Hit& hit) {
+  R best = rinf<R>();
+  hit = {HIT_CELL, 1, 0};
+  const int c = (int)pk_cell(p.pk);
+  const int n = T.nhs[c];
+  for (int i = 0; i < n; ++i) {
+    const int e = T.hs[c * MC_MAX_HALFSPACES + i];
+    const int s = e & 0xFFFF, sn = (e >> 16) ? -1 : 1;
+    const R* cf = T.scoef + 4 * s;
+    R d;
+    switch (T.skind[s]) {
+      case MC_SURF_PX: d = plane_dist(p.x, p.ux, cf[0], sn); break;
+      case MC_SURF_PY: d = plane_dist(p.y, p.uy, cf[0], sn); break;
+      case MC_SURF_PZ: d = plane_dist(p.z, p.uz, cf[0], sn); break;
+      default: d = cyl_dist(p.x, p.y, p.ux, p.uy, cf[0], cf[1], cf[2], sn < 0); break;
+    }
+    if (d < best) {
+      best = d;
+      hit = {HIT_CELL, 1, (uint32_t)s};
+    }
+  }
+  if (T.cmat[c] < 0) {
+    // lattice: inner element walls in the direction of motion, then the pin
+    const int ix = lat_ix(p.elem), iy = lat_iy(p.elem);
+    const R xlo = T.lx0 + R(ix) * T.lp, ylo = T.ly0 + R(iy) * T.lp;
+    R lbest = rinf<R>();
+    Hit lh = {HIT_LAT_X, 1, 0};
+    if (p.ux > R(0) && ix + 1 < T.h->lat_nx) {
+      R d = (xlo + T.lp - p.x) / p.ux;
+      d = d > R(0) ? d : R(0);
+      if (d < lbest) { lbest = d; lh = {HIT_LAT_X, 1, 0}; }
+    } else if (p.ux < R(0) && ix > 0) {
+      R d = (xlo - p.x) / p.ux;
+      d = d > R(0) ? d : R(0);
+      if (d < lbest) { lbest = d; lh = {HIT_LAT_X, -1, 0}; }
+    }
+    if (p.uy > R(0) && iy + 1 < T.h->lat_ny) {
+      R d = (ylo + T.lp - p.y) / p.uy;
+      d = d > R(0) ? d : R(0);
+      if (d < lbest) { lbest = d; lh = {HIT_LAT_Y, 1, 0}; }
+    } else if (p.uy < R(0) && iy > 0) {
+      R d = (ylo - p.y) / p.uy;
+      d = d > R(0) ? d : R(0);
+      if (d < lbest) { lbest = d; lh = {HIT_LAT_Y, -1, 0}; }
+    }
+    if (T.lpin[iy * T.h->lat_nx + ix] >= 0) {
+      const R d = cyl_dist(p.x, p.y, p.ux, p.uy, xlo + R(0.5) * T.lp, ylo + R(0.5) * T.lp, T.lr,
+                           pk_pin(p.pk) != 0);
+      if (d < lbest) { lbest = d; lh = {HIT_PIN, 1, 0}; }
+    }
+    if (lbest < best) {
+      best = lbest;
+      hit = lh;
+    }
+  }
+  return best;
+}
+
+// i with e[i] <= x < e[i+1] over n bins; -1 below the first edge, n at or above the last
+template <typename E, typename X>
+__device__ __forceinline__ int bin_search(const E* e, int n, X x) {
+  if (!(x >= (X)e[0])) return -1;
+  if (!(x < (X)e[n])) return n;
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if ((X)e[mid] <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------------------------------------ tally atomics
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Warp-aggregated add: lanes that target the same bin are found with match.any; each peer group
+// is reduced by a shuffle tree over the group's ranks and its lowest lane issues one atomic.
+template <typename V>
+__device__ __forceinline__ V peer_reduce(unsigned mask, unsigned peers, V v) {
+  const int lane = threadIdx.x & 31;
+  const unsigned rank = __popc(peers & lanemask_lt());
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned src = __fns(peers, (unsigned)lane, d + 1);
+    const V o = __shfl_sync(mask, v, (src == 0xFFFFFFFFu) ? lane : (int)src);
+    if (src != 0xFFFFFFFFu && (rank & (2 * d - 1)) == 0) v += o;
+  }
+  return v;
+}
+
+__device__ __forceinline__ void add_fixed(unsigned long long* dst, long long v, bool aggregate) {
+  if (aggregate) {
+    const unsigned mask = __activemask();
+    const unsigned peers = __match_any_sync(mask, (unsigned long long)dst);
+    v = peer_reduce(mask, peers, v);
+    if ((peers & lanemask_lt()) == 0u) atomicAdd(dst, (unsigned long long)v);
+  } else {
+    atomicAdd(dst, (unsigned long long)v);
+  }
+}
+
+__device__ __forceinline__ void add_fp64(double* dst, double v, bool aggregate) {
+  if (aggregate) {
+    const unsigned mask = __activemask();
+    const unsigned peers = __match_any_sync(mask, (unsigned long long)dst);
+    v = peer_reduce(mask, peers, v);
+    if ((peers & lanemask_lt()) == 0u) atomicAdd(dst, v);
+  } else {
+    atomicAdd(dst, v);
+  }
+}
+
+// score value w * len into bin `bin` of the particle's batch tally
+template <typename R>
+__device__ __forceinline__ void score(const RunParams& P, uint64_t slot, double w, R len) {
+  if (P.tally_fp64) {
+    add_fp64(reinterpret_cast<double*>(P.tally) + slot, w * (double)len, P.aggregate != 0);
+  } else {
+    long long q;
+    if (sizeof(R) == 4)
+      q = __float2ll_rn((float)w * (float)len * (float)P.fixed_scale);
+    else
+      q = __double2ll_rn(w * (double)len * P.fixed_scale);
+    add_fixed(reinterpret_cast<unsigned long long*>(P.tally) + slot, q, P.aggregate != 0);
+  }
+}
+
+// Track-length estimator over the segment of length l from the particle's position: walk the
+// mesh cells and time bins it crosses (3D DDA plus the time axis) and score w * piece length into
+// each bin it passes through.
+template <typename R>
+__device__ void score_segment(const Tab<R>& T, const RunParams& P, const Part<R>& p, R l,
+                              uint64_t batch_base) {
+  const int g = (int)pk_g(p.pk);
+  const R v = T.v[g];
+  const char* base = reinterpret_cast<const char*>(T.h);
+  for (int ti = 0; ti < T.h->n_tally; ++ti) {
+    const TallyDesc& D = T.h->tally[ti];
+    const R* e[3] = {reinterpret_cast<const R*>(base + D.o_ex), reinterpret_cast<const R*>(base + D.o_ey),
+                     reinterpret_cast<const R*>(base + D.o_ez)};
+    const double* et = reinterpret_cast<const double*>(base + D.o_et);
+    const int n[3] = {D.nx, D.ny, D.nz};
+    const R pos[3] = {p.x, p.y, p.z}, u[3] = {p.ux, p.uy, p.uz};
+    int idx[3], step[3];
+    R sn[3];
+    bool never = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int i = bin_search(e[d], n[d], pos[d]);
+      idx[d] = i;
+      if (u[d] > R(0)) {
+        step[d] = 1;
+        if (i >= n[d]) never = true;
+        sn[d] = (i >= n[d]) ? rinf<R>() : (e[d][i + 1] - pos[d]) / u[d];
+      } else if (u[d] < R(0)) {
+        step[d] = -1;
+        if (i < 0) never = true;
+        sn[d] = (i < 0) ? rinf<R>() : (e[d][i] - pos[d]) / u[d];
+      } else {
+        step[d] = 0;
+        sn[d] = rinf<R>();
+        if (i < 0 || i >= n[d]) never = true;
+      }
+    }
+    if (never) continue;
+    int it = bin_search(et, D.nt, p.t);
+    if (it >= D.nt) continue;
+    R stn = (R)((et[it + 1] - p.t)) * v;
+    R s = R(0);
+    while (s < l) {
+      R nxt = fmin(fmin(sn[0], sn[1]), fmin(sn[2], stn));
+      nxt = fmin(nxt, l);
+      if (nxt > s && idx[0] >= 0 && idx[0] < n[0] && idx[1] >= 0 && idx[1] < n[1] && idx[2] >= 0 &&
+          idx[2] < n[2] && it >= 0) {
+        const int bin = (((idx[2] * n[1] + idx[1]) * n[0] + idx[0]) * T.G + g) * D.nt + it;
+        score(P, batch_base + (uint64_t)(D.bin_offset + bin), p.w, nxt - s);
+      }
+      if (nxt >= l) break;
+      bool out = false;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (sn[d] <= nxt) {
+          idx[d] += step[d];
+          if (idx[d] < 0 || idx[d] >= n[d]) {
+            // left the mesh along this axis, unless it was entering from outside
+            if ((step[d] > 0 && idx[d] >= n[d]) || (step[d] < 0 && idx[d] < 0)) out = true;
+          }
+          sn[d] = out ? rinf<R>() : (e[d][idx[d] + (step[d] > 0 ? 1 : 0)] - pos[d]) / u[d];
+        }
+      }
+      if (stn <= nxt) {
+        ++it;
+        if (it >= D.nt) out = true;
+        else stn = (R)((et[it + 1] - p.t)) * v;
+      }
+      if (out) break;
+      s = nxt;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------ sampling
+template <typename R>
+__device__ __forceinline__ int sample_cdf(const R* cdf, int n, R u) {
+  for (int i = 0; i < n; ++i)
+    if (u < cdf[i]) return i;
+  return n - 1;
+}
+
+template <typename R>
+__device__ __forceinline__ void iso_dir(R mu, R uphi, R& ux, R& uy, R& uz) {
+  R s, c;
+  sincos2pi(uphi, &s, &c);
+  const R sn = rsqrt_(fmax(R(0), R(1) - mu * mu));
+  ux = mu;
+  uy = sn * c;
+  uz = sn * s;
+}
+
+}  // namespace mcgb

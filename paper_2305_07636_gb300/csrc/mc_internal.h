@@ -1,0 +1,107 @@
+// Internal layout shared by the host half (mc_api.cu) and the device half (mc_transport.cu) of
+// libmcgb.  Not part of the public ABI.
+#pragma once
+#include <stdint.h>
+
+#include "../../include/mc.h"
+
+namespace mcgb {
+
+constexpr int kMaxTallies = MC_MAX_TALLIES;
+constexpr int kMaxLanes = 6;      // 16-byte state lanes per particle (FP64 layout)
+constexpr int kLanesFP32 = 4;     // 64 B per particle
+constexpr int kLanesFP64 = 6;     // 96 B per particle
+constexpr uint32_t kSourceEvent = 0xFFFFFFFFu;
+constexpr uint32_t kChildMark = 0x80000000u;
+constexpr uint32_t kSplitMark = 0xC0000000u;
+constexpr uint32_t kChildKeyXor = 0xA5A5A5A5u;
+
+// ---- packed per-particle word (lane 3 .w in FP32, lane 4 .w in FP64)
+//   bits 0-4   group (G <= 32)
+//   bits 5-12  cell index
+//   bit  13    inside the pin of the current lattice element
+//   bits 14-15 pending event: 0 none (needs a flight), 1 collision, 2 surface
+//   bits 16-17 surface hit type: 0 cell surface, 1 lattice x wall, 2 lattice y wall, 3 pin
+//   bit  18    lattice wall direction (1 = +1, 0 = -1)
+//   bits 19-26 index of the crossed cell surface
+enum : uint32_t { PEND_NONE = 0, PEND_COLL = 1, PEND_SURF = 2 };
+enum : uint32_t { HIT_CELL = 0, HIT_LAT_X = 1, HIT_LAT_Y = 2, HIT_PIN = 3 };
+
+__host__ __device__ inline uint32_t pk_g(uint32_t w) { return w & 0x1Fu; }
+__host__ __device__ inline uint32_t pk_cell(uint32_t w) { return (w >> 5) & 0xFFu; }
+__host__ __device__ inline uint32_t pk_pin(uint32_t w) { return (w >> 13) & 1u; }
+__host__ __device__ inline uint32_t pk_pend(uint32_t w) { return (w >> 14) & 3u; }
+__host__ __device__ inline uint32_t pk_hit(uint32_t w) { return (w >> 16) & 3u; }
+__host__ __device__ inline int pk_dir(uint32_t w) { return ((w >> 18) & 1u) ? 1 : -1; }
+__host__ __device__ inline uint32_t pk_surf(uint32_t w) { return (w >> 19) & 0xFFu; }
+__host__ __device__ inline uint32_t pk_make(uint32_t g, uint32_t cell, uint32_t pin) {
+  return (g & 0x1Fu) | ((cell & 0xFFu) << 5) | ((pin & 1u) << 13);
+}
+__host__ __device__ inline uint32_t pk_set_pending(uint32_t w, uint32_t pend, uint32_t hit,
+                                                   int dir, uint32_t surf) {
+  w &= 0x3FFFu;
+  return w | (pend << 14) | (hit << 16) | ((dir > 0 ? 1u : 0u) << 18) | ((surf & 0xFFu) << 19);
+}
+
+// ---- per-problem table blob: header followed by typed arrays, all 16-byte aligned.  `Real`
+// arrays are float in FP32 mode and double in FP64 mode; time edges are always double.
+struct TallyDesc {
+  int nx, ny, nz, nt;
+  int o_ex, o_ey, o_ez, o_et;  // byte offsets of the edge arrays
+  int bin_offset;              // first bin of this tally in the concatenated bin space
+  int n_bins;
+  int pad[2];
+};
+
+struct TableHeader {
+  int G, M, n_surf, n_cell;
+  int has_lat, lat_nx, lat_ny, lat_matrix;
+  int n_tally, total_bins, leak_offset, real_bytes;
+  int src_pos, src_dir, pad0, pad1;
+  double t_census;
+  double src_lo[3], src_hi[3], src_t0, src_t1;
+  double lat_x0, lat_y0, lat_pitch, lat_r;
+  // byte offsets
+  int o_st, o_ss, o_ssf, o_nu;        // [M][G] Real: sigma_t, scatter threshold, scatter+production threshold, nu
+  int o_v, o_inv_v, o_scdf, o_chi;    // [G] Real speed, 1/speed; [M][G][G] scatter CDF; [M][G] chi CDF
+  int o_src_cdf, o_skind, o_sbc, o_scoef;  // [G] Real; [n_surf] int; [n_surf] int; [n_surf][4] Real
+  int o_nhs, o_hs, o_cmat, o_lpin;    // [n_cell] int; [n_cell][16] int (surf | sense<<16); [n_cell] int; [ny*nx] int
+  TallyDesc tally[kMaxTallies];
+  int blob_bytes, pad2, pad3, pad4;
+};
+
+// ---- device control block, one per problem
+struct Ctl {
+  unsigned long long front[3], back[3], birth[3], hstart[3];  // rotated per iteration (mod 3)
+  unsigned int bar_count, bar_gen;
+  int status, pad;
+  unsigned long long counters[MC_NCOUNTERS + 1];
+  unsigned long long log_n;
+  unsigned long long iterations;
+};
+
+struct RunParams {
+  uint4* S[2][kMaxLanes];  // ping-pong transport banks (front: pending collision, back: surface)
+  uint4* B[2][kMaxLanes];  // ping-pong birth banks (sources' children, split copies)
+  uint64_t cap_s, cap_b;
+  Ctl* ctl;
+  void* tally;             // [n_batches][total_bins] int64 (fixed point) or double
+  int tally_fp64, aggregate;
+  double fixed_scale;      // 2^fixed_bits
+  uint64_t n_hist, hist_per_batch, h_first;
+  int n_batches, blob_bytes;
+  uint64_t seed;
+  const uint4* blob;
+  uint64_t max_iter;
+  unsigned long long spin_limit;  // barrier wait budget (polls)
+  mc_event* log;
+  uint64_t log_cap, log_first, log_count;
+  // weight windows (optional)
+  int ww_on, ww_nx, ww_ny, ww_nz;
+  const double* ww_edges;  // x[nx+1], y[ny+1], z[nz+1]
+  const double* ww_center; // [nz][ny][nx][G]
+  double ww_upper, ww_lower;
+  int ww_split_max, pad;
+};
+
+}  // namespace mcgb

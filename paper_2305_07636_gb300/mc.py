@@ -1,0 +1,380 @@
+"""Python binding of libmcgb (include/mc.h): argument marshalling only.
+
+Every step of the random walk runs in the library's CUDA kernels; this module turns the problem
+dicts of `problems.py` into `mc_problem_desc` structs, passes device pointers / stream handles
+through, and converts status codes into exceptions.  There is no CPU fallback: if the library
+cannot be loaded, or the GPU is unavailable, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+# ------------------------------------------------------------------------------ constants (mc.h)
+MC_OK, MC_ERR_INVALID, MC_ERR_CUDA, MC_ERR_OOM = 0, -1, -2, -3
+MC_ERR_BANK_FULL, MC_ERR_TIMEOUT, MC_ERR_STATE, MC_ERR_LOST = -4, -5, -6, -7
+STATUS_NAMES = {0: "MC_OK", -1: "MC_ERR_INVALID", -2: "MC_ERR_CUDA", -3: "MC_ERR_OOM",
+                -4: "MC_ERR_BANK_FULL", -5: "MC_ERR_TIMEOUT", -6: "MC_ERR_STATE",
+                -7: "MC_ERR_LOST"}
+MAX_HALFSPACES = 16
+MC_FP32, MC_FP64 = 0, 1
+MC_TALLY_FIXED64, MC_TALLY_FP64 = 0, 1
+COUNTER_NAMES = ["source", "secondary", "capture", "production", "leak", "census", "lost",
+                 "flight", "collision", "scatter", "surface", "reflect", "ww_split", "ww_kill",
+                 "iterations"]
+NCOUNTERS = len(COUNTER_NAMES)
+KIND = {"PX": 0, "PY": 1, "PZ": 2, "CZ": 3}
+BC = {"interior": 0, "vacuum": 1, "reflect": 2}
+SRC_POS = {"box": 0, "surface_x0": 1}
+SRC_DIR = {"iso": 0, "beam_x": 1, "cos_x": 2}
+
+
+class McError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+# ------------------------------------------------------------------------------ structs (mc.h)
+DP = C.POINTER(C.c_double)
+IP = C.POINTER(C.c_int)
+
+
+class mc_surface(C.Structure):
+    _fields_ = [("kind", C.c_int), ("coef", C.c_double * 3), ("bc", C.c_int)]
+
+
+class mc_cell(C.Structure):
+    _fields_ = [("n_halfspaces", C.c_int), ("surface", C.c_int * MAX_HALFSPACES),
+                ("sense", C.c_int * MAX_HALFSPACES), ("material", C.c_int)]
+
+
+class mc_lattice(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("x0", C.c_double), ("y0", C.c_double),
+                ("pitch", C.c_double), ("radius", C.c_double), ("pin_material", IP),
+                ("matrix_material", C.c_int)]
+
+
+class mc_source(C.Structure):
+    _fields_ = [("pos", C.c_int), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("dir", C.c_int), ("group_pdf", DP), ("t0", C.c_double), ("t1", C.c_double)]
+
+
+class mc_mesh_tally(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("nt", C.c_int),
+                ("x", DP), ("y", DP), ("z", DP), ("t", DP)]
+
+
+class mc_problem_desc(C.Structure):
+    _fields_ = [("n_groups", C.c_int), ("n_materials", C.c_int),
+                ("sigma_t", DP), ("sigma_s", DP), ("sigma_f", DP), ("nu", DP), ("chi", DP),
+                ("speed", DP), ("n_surfaces", C.c_int), ("surfaces", C.POINTER(mc_surface)),
+                ("n_cells", C.c_int), ("cells", C.POINTER(mc_cell)),
+                ("lattice", C.POINTER(mc_lattice)), ("source", mc_source),
+                ("n_tallies", C.c_int), ("tallies", C.POINTER(mc_mesh_tally)),
+                ("t_census", C.c_double)]
+
+
+class mc_run_opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("tally_mode", C.c_int), ("fixed_bits", C.c_int),
+                ("n_batches", C.c_int), ("bank_capacity", C.c_uint64),
+                ("block_size", C.c_int), ("blocks_per_sm", C.c_int),
+                ("max_iterations", C.c_uint64), ("aggregate_atomics", C.c_int),
+                ("ww_enable", C.c_int), ("log_first", C.c_uint64), ("log_count", C.c_uint64),
+                ("log_capacity", C.c_uint64), ("first_history", C.c_uint64)]
+
+
+class mc_event(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("root", C.c_uint64), ("k", C.c_uint32),
+                ("kind", C.c_int32), ("outcome", C.c_int32), ("n_child", C.c_int32),
+                ("cell", C.c_int32), ("elem", C.c_int32), ("in_pin", C.c_int32),
+                ("g", C.c_int32),
+                ("x", C.c_double), ("y", C.c_double), ("z", C.c_double),
+                ("ux", C.c_double), ("uy", C.c_double), ("uz", C.c_double),
+                ("t", C.c_double), ("w", C.c_double)]
+
+
+EVENT_DTYPE = np.dtype([("tag", np.uint64), ("root", np.uint64), ("k", np.uint32),
+                        ("kind", np.int32), ("outcome", np.int32), ("n_child", np.int32),
+                        ("cell", np.int32), ("elem", np.int32), ("in_pin", np.int32),
+                        ("g", np.int32), ("x", np.float64), ("y", np.float64),
+                        ("z", np.float64), ("ux", np.float64), ("uy", np.float64),
+                        ("uz", np.float64), ("t", np.float64), ("w", np.float64)], align=True)
+
+# every entry point declared in include/mc.h, with its ctypes signature
+SIGNATURES = {
+    "mc_run_opts_default": (None, [C.POINTER(mc_run_opts)]),
+    "mc_problem_create": (C.c_int, [C.POINTER(mc_problem_desc), C.POINTER(C.c_void_p)]),
+    "mc_run": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.POINTER(mc_run_opts), C.c_void_p]),
+    "mc_wait": (C.c_int, [C.c_void_p]),
+    "mc_tally_shape": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64)]),
+    "mc_tally_get": (C.c_int, [C.c_void_p, C.c_int, DP, DP, C.c_size_t]),
+    "mc_counters_get": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_size_t]),
+    "mc_tally_batches": (C.c_int, [C.c_void_p, C.c_int, DP, C.c_size_t, C.POINTER(C.c_int)]),
+    "mc_event_log": (C.c_int, [C.c_void_p, C.POINTER(mc_event), C.c_size_t,
+                               C.POINTER(C.c_size_t)]),
+    "mc_run_timing": (C.c_int, [C.c_void_p, DP, DP]),
+    "mc_problem_table_bytes": (C.c_size_t, [C.c_void_p]),
+    "mc_problem_destroy": (None, [C.c_void_p]),
+    "mc_last_error": (C.c_char_p, []),
+    "mc_philox": (C.c_int, [C.c_uint64, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib(build_if_missing: bool = True):
+    """Loads libmcgb.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            L = C.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().mc_last_error().decode(errors="replace")
+
+
+def check(rc: int):
+    if rc != MC_OK:
+        raise McError(rc, last_error())
+    return rc
+
+
+def run_opts(**kw) -> mc_run_opts:
+    o = mc_run_opts()
+    lib().mc_run_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp32": MC_FP32, "fp64": MC_FP64}[v]
+        if k == "tally_mode" and isinstance(v, str):
+            v = {"fixed": MC_TALLY_FIXED64, "fp64": MC_TALLY_FP64}[v]
+        setattr(o, k, v)
+    return o
+
+
+# ------------------------------------------------------------------------------ marshalling
+class _Desc:
+    """Builds an mc_problem_desc from a problem dict; keeps the arrays alive while in use."""
+
+    def __init__(self, prob: dict):
+        self.keep = []
+        G = int(prob["G"])
+        mats = prob["materials"]
+        d = mc_problem_desc()
+        d.n_groups, d.n_materials = G, len(mats)
+
+        def dp(x):
+            a = np.ascontiguousarray(np.asarray(x, dtype=np.float64).ravel())
+            self.keep.append(a)
+            return a.ctypes.data_as(DP)
+
+        def ip(x):
+            a = np.ascontiguousarray(np.asarray(x, dtype=np.int32).ravel())
+            self.keep.append(a)
+            return a.ctypes.data_as(IP)
+
+        d.sigma_t = dp([m["sigma_t"] for m in mats])
+        d.sigma_s = dp([m["sigma_s"] for m in mats])
+        d.sigma_f = dp([m["sigma_f"] for m in mats])
+        d.nu = dp([m["nu"] for m in mats])
+        d.chi = dp([m["chi"] for m in mats])
+        d.speed = dp(prob["speed"])
+        surfs = prob["surfaces"]
+        sa = (mc_surface * len(surfs))()
+        for i, s in enumerate(surfs):
+            sa[i].kind = KIND[s["kind"]]
+            sa[i].bc = BC[s["bc"]]
+            for j, c in enumerate(s["coef"]):
+                sa[i].coef[j] = c
+        self.keep.append(sa)
+        d.n_surfaces, d.surfaces = len(surfs), sa
+        cells = prob["cells"]
+        ca = (mc_cell * len(cells))()
+        for i, c in enumerate(cells):
+            hs = c["halfspaces"]
+            if len(hs) > MAX_HALFSPACES:
+                raise McError(MC_ERR_INVALID, f"cell {i} has more than {MAX_HALFSPACES} half-spaces")
+            ca[i].n_halfspaces = len(hs)
+            for j, (s, sn) in enumerate(hs):
+                ca[i].surface[j] = s
+                ca[i].sense[j] = sn
+            ca[i].material = c["material"]
+        self.keep.append(ca)
+        d.n_cells, d.cells = len(cells), ca
+        lat = prob.get("lattice")
+        if lat:
+            L = mc_lattice()
+            L.nx, L.ny = lat["nx"], lat["ny"]
+            L.x0, L.y0, L.pitch, L.radius = lat["x0"], lat["y0"], lat["pitch"], lat["radius"]
+            L.pin_material = ip(lat["pin_material"])
+            L.matrix_material = lat["matrix_material"]
+            self.keep.append(L)
+            d.lattice = C.pointer(L)
+        src = prob["source"]
+        d.source.pos = SRC_POS[src["pos"]]
+        d.source.dir = SRC_DIR[src["dir"]]
+        for i in range(3):
+            d.source.lo[i] = src["lo"][i]
+            d.source.hi[i] = src["hi"][i]
+        d.source.group_pdf = dp(src["group_pdf"])
+        d.source.t0, d.source.t1 = src["t0"], src["t1"]
+        tals = prob["tallies"]
+        ta = (mc_mesh_tally * max(1, len(tals)))()
+        for i, t in enumerate(tals):
+            ta[i].nx, ta[i].ny = len(t["x"]) - 1, len(t["y"]) - 1
+            ta[i].nz, ta[i].nt = len(t["z"]) - 1, len(t["t"]) - 1
+            ta[i].x, ta[i].y, ta[i].z, ta[i].t = dp(t["x"]), dp(t["y"]), dp(t["z"]), dp(t["t"])
+        self.keep.append(ta)
+        d.n_tallies, d.tallies = len(tals), ta
+        d.t_census = prob["t_census"]
+        self.desc = d
+
+
+def problem_create(prob: dict) -> int:
+    """mc_problem_create: returns the opaque handle (an int)."""
+    m = _Desc(prob)
+    h = C.c_void_p()
+    check(lib().mc_problem_create(C.byref(m.desc), C.byref(h)))
+    return h.value
+
+
+def problem_destroy(h: int):
+    lib().mc_problem_destroy(C.c_void_p(h))
+
+
+def run(h: int, n_histories: int, seed: int, opts: mc_run_opts | None = None, stream=None):
+    """mc_run: asynchronous on `stream` (a torch.cuda.Stream, a raw handle or None)."""
+    s = _stream_handle(stream)
+    check(lib().mc_run(C.c_void_p(h), int(n_histories), int(seed) & (2**64 - 1),
+                       C.byref(opts) if opts is not None else None, C.c_void_p(s)))
+
+
+def wait(h: int):
+    check(lib().mc_wait(C.c_void_p(h)))
+
+
+def tally_shape(h: int, tally_id: int):
+    shp = (C.c_int64 * 5)()
+    check(lib().mc_tally_shape(C.c_void_p(h), tally_id, shp))
+    return tuple(int(v) for v in shp)
+
+
+def tally_get(h: int, tally_id: int):
+    shp = tally_shape(h, tally_id)
+    n = int(np.prod(shp))
+    mean = np.zeros(n)
+    err = np.zeros(n)
+    check(lib().mc_tally_get(C.c_void_p(h), tally_id, mean.ctypes.data_as(DP),
+                             err.ctypes.data_as(DP), n))
+    return mean.reshape(shp), err.reshape(shp)
+
+
+def tally_batches(h: int, tally_id: int) -> np.ndarray:
+    """mc_tally_batches: per-batch per-source-particle means, shape (n_batches, *tally shape)."""
+    shp = tally_shape(h, tally_id)
+    nb = C.c_int(0)
+    check(lib().mc_tally_batches(C.c_void_p(h), tally_id, None, 0, C.byref(nb)))
+    out = np.zeros((nb.value, int(np.prod(shp))))
+    check(lib().mc_tally_batches(C.c_void_p(h), tally_id, out.ctypes.data_as(DP), out.size,
+                                 C.byref(nb)))
+    return out.reshape((nb.value,) + shp)
+
+
+def counters_get(h: int) -> dict:
+    c = (C.c_int64 * NCOUNTERS)()
+    check(lib().mc_counters_get(C.c_void_p(h), c, NCOUNTERS))
+    return dict(zip(COUNTER_NAMES, [int(v) for v in c]))
+
+
+def event_log(h: int, cap: int) -> np.ndarray:
+    buf = (mc_event * max(1, cap))()
+    n = C.c_size_t(0)
+    check(lib().mc_event_log(C.c_void_p(h), buf, cap, C.byref(n)))
+    assert C.sizeof(mc_event) == EVENT_DTYPE.itemsize
+    ev = np.frombuffer(buf, dtype=EVENT_DTYPE, count=max(1, cap))[: n.value].copy()
+    return ev[np.lexsort((ev["k"], ev["tag"]))]
+
+
+def run_timing(h: int):
+    """mc_run_timing: (transport_ms, stats_ms) of the last run."""
+    a, b = C.c_double(0), C.c_double(0)
+    check(lib().mc_run_timing(C.c_void_p(h), C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def philox(seed: int, ctr_dev_ptr: int, out_dev_ptr: int, n: int, stream=None):
+    """mc_philox on device arrays of 4*n uint32 words."""
+    check(lib().mc_philox(int(seed) & (2**64 - 1), C.c_void_p(ctr_dev_ptr),
+                          C.c_void_p(out_dev_ptr), int(n), C.c_void_p(_stream_handle(stream))))
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class Problem:
+    """Owning wrapper around an mc_problem handle."""
+
+    def __init__(self, prob: dict):
+        self.prob = prob
+        self.h = problem_create(prob)
+        self.n_tallies = len(prob["tallies"])
+
+    def run(self, n_histories, seed=1, stream=None, **opts):
+        self.opts = run_opts(**opts)
+        run(self.h, n_histories, seed, self.opts, stream)
+        return self
+
+    def wait(self):
+        wait(self.h)
+
+    def tally(self, i=0):
+        return tally_get(self.h, i)
+
+    def tally_batches(self, i=0):
+        return tally_batches(self.h, i)
+
+    def leakage(self):
+        return tally_get(self.h, self.n_tallies)
+
+    def counters(self):
+        return counters_get(self.h)
+
+    def table_bytes(self):
+        return int(lib().mc_problem_table_bytes(C.c_void_p(self.h)))
+
+    def timing(self):
+        return run_timing(self.h)
+
+    def events(self, cap):
+        return event_log(self.h, cap)
+
+    def close(self):
+        if self.h:
+            problem_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,230 @@
+"""CUDA path (through the C ABI) against the CPU oracle and the closed forms.
+
+- RNG: the device Philox4x32-10 equals the oracle's bit for bit.
+- Replay: in FP64 tracking the GPU reproduces the oracle's event sequence history by history:
+  the same (tag, event index) set, identical integer fields, positions/directions/times within
+  1e-9 relative.
+- Statistics: FP32-tracking tallies agree with the oracle within 4 sigma of the combined
+  statistical error, bin by bin, on every bin both sides sample to better than 10% relative error.
+- Conservation: every particle started ends exactly once (integer counters).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import closed_forms as CF
+from paper_2305_07636_gb300 import mc
+from paper_2305_07636_gb300 import problems as P
+
+pytestmark = pytest.mark.gpu
+
+THREADS = 16
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    if not _t.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    return _t
+
+
+def combined_z(mg, sg, mo, so, rel_max=0.1):
+    mg, sg, mo, so = (np.asarray(a, dtype=np.float64).ravel() for a in (mg, sg, mo, so))
+    ok = (sg > 0) & (so > 0) & (sg < rel_max * np.abs(mg)) & (so < rel_max * np.abs(mo))
+    return (mg[ok] - mo[ok]) / np.sqrt(sg[ok] ** 2 + so[ok] ** 2)
+
+
+def check_z(z, min_bins, bar=4.0):
+    assert z.size >= min_bins, f"only {z.size} comparable bins"
+    assert np.all(np.abs(z) < bar), f"max |z| = {np.abs(z).max():.2f} over {z.size} bins"
+
+
+def conserved(c):
+    started = c["source"] + c["secondary"] + c["ww_split"]
+    ended = c["capture"] + c["production"] + c["leak"] + c["census"] + c["lost"] + c["ww_kill"]
+    return started == ended
+
+
+# ----------------------------------------------------------------------------- RNG
+
+
+def test_device_philox_equals_oracle(torch):
+    rng = np.random.default_rng(5)
+    n = 4096
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    d_ctr = torch.from_numpy(ctr.view(np.int32)).cuda()
+    d_out = torch.zeros_like(d_ctr)
+    seed = 0x0123456789ABCDEF
+    mc.philox(seed, d_ctr.data_ptr(), d_out.data_ptr(), n)
+    torch.cuda.synchronize()
+    out = d_out.cpu().numpy().view(np.uint32)
+    for i in range(0, n, 7):
+        assert oracle.philox((seed & 0xFFFFFFFF, seed >> 32), ctr[i]) == [int(v) for v in out[i]]
+
+
+# ----------------------------------------------------------------------------- replay
+
+
+REPLAY_FLOAT = ["x", "y", "z", "ux", "uy", "uz", "t", "w"]
+REPLAY_INT = ["kind", "outcome", "n_child", "cell", "elem", "in_pin", "g", "root"]
+
+
+def compare_logs(ev_g, ev_o):
+    kg = set(zip(ev_g["tag"].tolist(), ev_g["k"].tolist()))
+    ko = set(zip(ev_o["tag"].tolist(), ev_o["k"].tolist()))
+    assert kg == ko, f"event sets differ: gpu-only {len(kg - ko)}, oracle-only {len(ko - kg)}"
+    assert len(ev_g) == len(ev_o)
+    for f in REPLAY_INT:
+        bad = np.nonzero(ev_g[f] != ev_o[f])[0]
+        assert bad.size == 0, f"{f} differs at {bad[:5]}"
+    for f in REPLAY_FLOAT:
+        a, b = ev_g[f], ev_o[f]
+        scale = np.maximum(np.maximum(np.abs(a), np.abs(b)), 1.0)
+        rel = np.abs(a - b) / scale
+        assert rel.max() <= 1e-9, f"{f}: max relative difference {rel.max():.3e}"
+
+
+def _replay_case(name):
+    if name == "azurv1":
+        return P.azurv1(t_end=5.0), 2000
+    if name == "config4_thin":
+        return P.slab_stack(thickness=20.0, n_layers=4, name="thin"), 10000
+    return P.by_name(name), 10000
+
+
+@pytest.mark.parametrize("name", ["config1", "config2", "config3", "azurv1", "config4_thin"])
+def test_fp64_replay_first_histories(torch, name):
+    prob, n = _replay_case(name)
+    seed = 77
+    o = oracle.run(prob, n, seed=seed, threads=THREADS, log_first=0, log_count=n,
+                   log_cap=200 * n)
+    p = mc.Problem(prob)
+    p.run(n, seed, precision="fp64", log_first=0, log_count=n, log_capacity=200 * n,
+          bank_capacity=1 << 18)
+    ev = p.events(200 * n)
+    compare_logs(ev, o.events)
+    c = p.counters()
+    for k in oracle.COUNTER_NAMES:
+        assert c[k] == o.counters[k], k
+    p.close()
+
+
+# ----------------------------------------------------------------------------- statistics
+
+
+@pytest.mark.parametrize("name,n_or,n_gpu,min_bins", [
+    ("config1", 400_000, 4_000_000, 45),
+    ("config2", 400_000, 4_000_000, 200),
+    ("config3", 100_000, 2_000_000, 2000),
+])
+def test_fp32_tallies_match_oracle(torch, name, n_or, n_gpu, min_bins):
+    prob = P.by_name(name)
+    o = oracle.run(prob, n_or, seed=3, threads=THREADS)
+    p = mc.Problem(prob)
+    p.run(n_gpu, 4, precision="fp32")
+    for t in range(len(prob["tallies"])):
+        mg, sg = p.tally(t)
+        mo, so = o.tallies[t]
+        check_z(combined_z(mg, sg, mo, so), min_bins)
+    lg, lgs = p.leakage()
+    if np.any(o.leak_mean > 0):
+        check_z(combined_z(lg, lgs, o.leak_mean, o.leak_std), 1)
+    assert conserved(p.counters())
+    p.close()
+
+
+def test_fp32_fixed_vs_fp64_tally_modes_agree(torch):
+    prob = P.config2()
+    p = mc.Problem(prob)
+    p.run(1_000_000, 9, tally_mode="fixed")
+    mf, sf = p.tally(0)
+    p.run(1_000_000, 9, tally_mode="fp64")
+    md, sd = p.tally(0)
+    # same histories, same seed: the two accumulations differ only by rounding
+    assert np.allclose(mf, md, rtol=1e-6, atol=1e-12)
+    p.close()
+
+
+def test_gpu_slab_closed_forms(torch):
+    p = mc.Problem(P.config1(sigma_s=0.0))
+    p.run(4_000_000, 21)
+    m, s = p.tally(0)
+    exact = CF.slab_flux_bins(1.0, np.linspace(0, 5, 51))
+    z = (m.ravel() - exact) / s.ravel()
+    assert np.all(np.abs(z) < 4)
+    lm, ls = p.leakage()
+    pl, pr = CF.slab_leakage(1.0, 5.0)
+    assert abs(lm.ravel()[0] - pl) < 4 * ls.ravel()[0]
+    assert abs(lm.ravel()[1] - pr) < 4 * ls.ravel()[1]
+    p.close()
+    p = mc.Problem(P.slab_problem(5.0, 1.0, 0.0, direction="beam_x", surface_source=True))
+    p.run(4_000_000, 22)
+    lm, ls = p.leakage()
+    assert abs(lm.ravel()[1] - math.exp(-5.0)) < 4 * ls.ravel()[1]
+    p.close()
+
+
+def test_gpu_azurv1_population(torch):
+    prob = P.azurv1()
+    p = mc.Problem(prob)
+    n = 50_000
+    p.run(n, 23, bank_capacity=1 << 21)
+    c = p.counters()
+    assert conserved(c)
+    te = prob["tallies"][0]["t"]
+    m, s = p.tally(0)
+    z = (m.ravel() - CF.infinite_time_bins(1.0, 0.6, 0.5, 1.0, te)) / s.ravel()
+    assert np.all(np.abs(z) < 4)
+    assert c["census"] / n == pytest.approx(math.exp(2.0), rel=0.05)
+    p.close()
+
+
+# ----------------------------------------------------------------------------- errors
+
+
+def test_device_errors_are_status_codes(torch):
+    prob = P.azurv1()
+    p = mc.Problem(prob)
+    with pytest.raises(mc.McError) as e:
+        p.run(20_000, 1, bank_capacity=1024)
+        p.wait()
+    assert e.value.code == mc.MC_ERR_BANK_FULL
+    with pytest.raises(mc.McError) as e:
+        p.run(20_000, 1, max_iterations=3, bank_capacity=1 << 20)
+        p.wait()
+    assert e.value.code == mc.MC_ERR_TIMEOUT
+    # the context is still healthy
+    p.run(2_000, 1, bank_capacity=1 << 20)
+    p.wait()
+    assert conserved(p.counters())
+    p.close()
+
+
+# ----------------------------------------------------------------------------- full size
+
+
+def test_config2_full_size_fp32_against_expm(torch):
+    """1e7 histories in the benchmark's launch configuration: tallies within 4 sigma of the
+    matrix exponential, exact conservation, and a sampled window of histories replayed in FP64
+    against the oracle computing just those histories."""
+    prob = P.config2()
+    p = mc.Problem(prob)
+    n = 10_000_000
+    p.run(n, 2)
+    m, s = p.tally(0)
+    exact = CF.multigroup_time_bins(prob["materials"][0], prob["speed"], prob["tallies"][0]["t"])
+    m2, s2 = m.reshape(7, -1), s.reshape(7, -1)
+    ok = (s2 > 0) & (s2 < 0.1 * np.abs(m2))
+    z = (m2[ok] - exact[ok]) / s2[ok]
+    assert ok.sum() > 400 and np.all(np.abs(z) < 4), np.abs(z).max()
+    assert conserved(p.counters())
+    first, cnt = 5_000_000, 300
+    p.run(n, 2, precision="fp64", log_first=first, log_count=cnt, log_capacity=200 * cnt)
+    ev = p.events(200 * cnt)
+    o = oracle.run(prob, cnt, seed=2, threads=THREADS, first=first, log_first=first,
+                   log_count=cnt, log_cap=200 * cnt)
+    compare_logs(ev, o.events)
+    p.close()
