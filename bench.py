@@ -162,6 +162,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
+    ap.add_argument("--algorithm", default="event", choices=["event", "history"])
+    ap.add_argument("--no-flush", action="store_true", help="skip the L2 flush between steps")
+    ap.add_argument("--opt", action="append", default=[],
+                    help="extra mc_run_opts field as key=value (e.g. block_size=128)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -182,7 +186,8 @@ def main():
         n = args.histories
     seed = 2
     p = mc.Problem(prob)
-    opts = mc.run_opts(first_history=rank * n)
+    extra = {k: int(v) for k, v in (o.split("=", 1) for o in args.opt)}
+    opts = mc.run_opts(first_history=rank * n, algorithm=args.algorithm, **extra)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -202,11 +207,11 @@ def main():
     transport_ms = []
     wall0 = time.perf_counter()
     for k in range(args.steps):
-        flush.zero_()
+        if not args.no_flush:
+            flush.zero_()
         ev_s[k].record(stream)
         mc.run(p.h, n, seed + 100 + k, opts, stream)
         ev_e[k].record(stream)
-        transport_ms.append(None)
     barrier()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
@@ -223,6 +228,8 @@ def main():
     # statistics, roofline and counters from the last timed run
     tr_ms, st_ms = p.timing()
     c = p.counters()
+    tr_t, tr_w, tr_s, tr_drain = p.trace()
+    drain_ms = float((tr_ms * 1e6 - tr_t[tr_drain][0]) / 1e6) if tr_drain.any() else 0.0
     per_batch = p.tally_batches(0).reshape(opts.n_batches, -1).sum(axis=1)
     total = per_batch.mean()
     rel = per_batch.std(ddof=1) / math.sqrt(len(per_batch)) / abs(total)
@@ -254,6 +261,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "histories_per_step": n, "tracking": "fp32",
+                   "algorithm": args.algorithm, "run_opts": extra,
                    "tally": "int64 fixed point 2^-32", "batches": opts.n_batches,
                    "l2": "flushed (256 MB write) before every timed step"},
         "fom": {"value": fom, "unit": "1/s", "tally": "total flux (all groups and time bins)",
@@ -263,11 +271,15 @@ def main():
                      "kernel": "k_transport<float>", "kernel_ms": tr_ms,
                      "algorithmic_bytes": algo_bytes, "peak_kind": peak_kind},
         "counters": {k: c[k] for k in ("flight", "collision", "surface", "census", "iterations")},
+        "algorithm": args.algorithm,
+        "trace": {"iterations": int(len(tr_t)), "history_style_iterations": int(tr_drain.sum()),
+                  "ms_in_history_style_tail": drain_ms},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
         "wall_s": wall,
+        "step_ms": [round(x, 4) for x in step_ms],
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(prob)

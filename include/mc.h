@@ -133,6 +133,11 @@ typedef struct mc_problem mc_problem; /* opaque, library-owned */
 /* ------------------------------------------------------------------------- run options */
 typedef enum { MC_FP32 = 0, MC_FP64 = 1 } mc_precision;
 typedef enum { MC_TALLY_FIXED64 = 0, MC_TALLY_FP64 = 1 } mc_tally_mode;
+/* Event-based: every iteration advances each live particle by one event and one flight and
+ * writes it back to the bank partitioned by its next event (collisions, surfaces).
+ * History-based: each thread carries its particle from source to death without write-back.
+ * Both draw the same random numbers per particle and give identical fixed-point tallies. */
+typedef enum { MC_ALG_EVENT = 0, MC_ALG_HISTORY = 1 } mc_algorithm;
 
 typedef struct {
   int precision;          /* mc_precision: arithmetic of positions/directions/distances */
@@ -148,6 +153,9 @@ typedef struct {
   uint64_t log_first, log_count; /* log every event of histories [log_first, +log_count) */
   uint64_t log_capacity;  /* event records kept (0 = 64 per logged history) */
   uint64_t first_history; /* history indices run are [first_history, first_history + n) */
+  int algorithm;          /* mc_algorithm (default MC_ALG_EVENT) */
+  uint64_t drain_threshold; /* event mode: once every history is sourced and at most this many
+                               particles remain, finish them history-style (0 = 2 per thread) */
 } mc_run_opts;
 
 /* Fills the defaults listed above. */
@@ -188,8 +196,9 @@ int mc_problem_create(const mc_problem_desc* d, mc_problem** out);
 int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts* opts,
            void* stream);
 
-/* Waits for the last run and returns its device status (MC_OK, MC_ERR_BANK_FULL,
- * MC_ERR_TIMEOUT, MC_ERR_LOST). */
+/* Waits for the runs issued so far and returns the first device error any of them raised since
+ * the previous mc_wait (MC_OK, MC_ERR_BANK_FULL, MC_ERR_TIMEOUT, MC_ERR_LOST), so that back-to-back
+ * runs cannot hide a failed one. */
 int mc_wait(mc_problem* p);
 
 /* Shape of a tally: {nz, ny, nx, G, nt}.  tally_id == n_tallies addresses the leakage tally,
@@ -211,6 +220,13 @@ int mc_counters_get(mc_problem* p, int64_t* counters, size_t n);
 /* Copies up to `cap` event records of the last run's logged histories; *n_out receives the
  * number copied.  Records are in device completion order (sort by (tag, k) to compare). */
 int mc_event_log(mc_problem* p, mc_event* out, size_t cap, size_t* n_out);
+
+/* Per-iteration trace of the last run's persistent kernel: t_ns[i] (%globaltimer, ns, relative
+ * to kernel start), items[i] (particles handled in iteration i), sources[i] (new histories
+ * among them; bit 63 set when the iteration ran history-style).  *n_out = iterations recorded
+ * (at most cap and at most 65536).  Synchronises. */
+int mc_trace_get(mc_problem* p, uint64_t* t_ns, uint64_t* items, uint64_t* sources, size_t cap,
+                 size_t* n_out);
 
 /* Device time of the last run's phases, from CUDA events recorded on the run's stream around
  * the transport kernel and around the batch-statistics kernel (milliseconds).  Synchronises. */

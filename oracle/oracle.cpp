@@ -309,7 +309,11 @@ double dist_cyl(double x, double y, double ux, double uy, double x0, double y0, 
     return d > 0.0 ? d : 0.0;
   }
   if (b >= 0.0 || disc <= 0.0) return INF;
-  double d = c / (-b + std::sqrt(disc));
+  // a grazing line whose chord inside the cylinder, 2 sqrt(disc) / a, is shorter than 1e-12 cm
+  // does not enter it (otherwise rounding can bounce a particle in and out on the spot)
+  double sq = std::sqrt(disc);
+  if (2.0 * sq < 1e-12 * a) return INF;
+  double d = c / (-b + sq);
   return d > 0.0 ? d : 0.0;
 }
 

@@ -26,12 +26,14 @@ template <typename R>
 cudaError_t launch_transport(const RunParams& P, int grid, int block, size_t smem, cudaStream_t s);
 template <typename R>
 cudaError_t transport_occupancy(int block, size_t smem, int* per_sm);
-cudaError_t launch_batch_stats(const void* tally, int fp64, double inv_scale, uint64_t bins, int nb,
-                               uint64_t n_hist, double* tot, double* s1, double* s2, cudaStream_t s);
+cudaError_t launch_batch_stats(const void* tally, int fp64, uint64_t bins, int nb, uint64_t n_hist,
+                               void* out, cudaStream_t s);
 cudaError_t launch_philox(uint64_t seed, const uint4* ctr, uint4* out, uint64_t n, cudaStream_t s);
 }  // namespace mcgb
 
 using namespace mcgb;
+
+static const uint64_t kTraceCap = 65536;
 
 // ------------------------------------------------------------------------------------------ errors
 static thread_local std::string g_err;
@@ -148,7 +150,8 @@ struct mc_problem {
   std::vector<HostTally> tallies;
   std::vector<uint8_t> blob[2];  // [0] FP32 tables, [1] FP64 tables
   DevBuf d_blob[2];
-  DevBuf d_ctl, d_tally, d_stats, d_log, d_banks;
+  DevBuf d_ctl, d_tally, d_stats, d_log, d_banks, d_trace;
+  DevBuf d_sticky;  // first device error of any run since the last mc_wait (not reset by mc_run)
   // last run
   int has_run = 0;
   uint64_t n_hist = 0;
@@ -326,6 +329,17 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
   H.src_t1 = d->source.t1;
   H.src_pos = d->source.pos;
   H.src_dir = d->source.dir;
+  for (int i = 0; i < 3; ++i) {
+    H.src_lo_f[i] = (float)d->source.lo[i];
+    H.src_hi_f[i] = (float)d->source.hi[i];
+  }
+  H.src_t0_f = (float)d->source.t0;
+  H.src_t1_f = (float)d->source.t1;
+  H.has_census = std::isfinite(d->t_census) ? 1 : 0;
+  if (H.has_census) {
+    H.tc_hi = (float)d->t_census;
+    H.tc_lo = (float)(d->t_census - (double)H.tc_hi);
+  }
   std::vector<R> st(M * G), ss(M * G), ssf(M * G), nu(M * G), scdf(M * G * G), chi(M * G);
   std::vector<double> tmp(G);
   for (int m = 0; m < M; ++m) {
@@ -409,10 +423,12 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
     D.nt = T.nt;
     std::vector<R> ex(T.x, T.x + T.nx + 1), ey(T.y, T.y + T.ny + 1), ez(T.z, T.z + T.nz + 1);
     std::vector<double> et(T.t, T.t + T.nt + 1);
+    std::vector<float> etf(T.t, T.t + T.nt + 1);
     D.o_ex = B.put(ex);
     D.o_ey = B.put(ey);
     D.o_ez = B.put(ez);
     D.o_et = B.put(et);
+    D.o_etf = B.put(etf);
     D.bin_offset = off;
     D.n_bins = T.nx * T.ny * T.nz * G * T.nt;
     off += D.n_bins;
@@ -483,6 +499,11 @@ int mc_problem_create(const mc_problem_desc* d, mc_problem** out) {
     }
   }
   if (rc == MC_OK) rc = p->d_ctl.ensure(sizeof(Ctl), p->dev);
+  if (rc == MC_OK) rc = p->d_sticky.ensure(16, p->dev);
+  if (rc == MC_OK) {
+    cudaError_t e = cudaMemset(p->d_sticky.ptr, 0, 16);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemset");
+  }
   for (int i = 0; i < 3 && rc == MC_OK; ++i) {
     cudaError_t e = cudaEventCreate(&p->ev[i]);
     if (e != cudaSuccess) rc = cuda_fail(e, "cudaEventCreate");
@@ -505,6 +526,8 @@ void mc_problem_destroy(mc_problem* p) {
   p->d_stats.release();
   p->d_log.release();
   p->d_banks.release();
+  p->d_trace.release();
+  p->d_sticky.release();
   p->d_ww.release();
   for (int i = 0; i < 3; ++i)
     if (p->ev[i]) cudaEventDestroy(p->ev[i]);
@@ -527,6 +550,7 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 256 || o.block_size % 32))
     return fail(MC_ERR_INVALID, "block_size must be a multiple of 32 in [32,256]");
   if (o.ww_enable && !p->ww_set) return fail(MC_ERR_STATE, "weight windows enabled but no table set");
+  if (o.algorithm != MC_ALG_EVENT && o.algorithm != MC_ALG_HISTORY) return fail(MC_ERR_INVALID, "algorithm");
   int dev;
   int rc = current_device(&dev);
   if (rc != MC_OK) return rc;
@@ -565,13 +589,24 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   P.cap_s = cap;
   P.cap_b = cap;
   P.ctl = (Ctl*)p->d_ctl.ptr;
+  P.sticky = (int*)p->d_sticky.ptr;
   P.tally = p->d_tally.ptr;
   P.tally_fp64 = o.tally_mode == MC_TALLY_FP64;
   P.aggregate = o.aggregate_atomics;
   P.fixed_scale = std::ldexp(1.0, o.fixed_bits);
+  P.fixed_scale_f = (float)P.fixed_scale;
+  P.history_mode = o.algorithm == MC_ALG_HISTORY;
+  rc = p->d_trace.ensure((size_t)3 * kTraceCap * 8, p->dev);
+  if (rc != MC_OK) return rc;
+  P.trace = (unsigned long long*)p->d_trace.ptr;
+  P.trace_cap = kTraceCap;
   P.n_hist = n_histories;
   P.hist_per_batch = (n_histories + nb - 1) / nb;
   P.h_first = o.first_history;
+  {
+    const double mg = std::floor(4294967296.0 * (double)nb / (double)n_histories);
+    P.batch_magic = mg >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)mg;
+  }
   P.n_batches = nb;
   P.blob_bytes = (int)p->blob[fp64].size();
   P.blob = (const uint4*)p->d_blob[fp64].ptr;
@@ -598,7 +633,7 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   CK(cudaMemsetAsync(p->d_tally.ptr, 0, (size_t)nb * bins * 8, s));
   if (P.log) CK(cudaMemsetAsync(p->d_log.ptr, 0, log_cap * sizeof(mc_event), s));
   const int block = o.block_size ? o.block_size : 256;
-  const size_t smem = P.blob_bytes;
+  const size_t smem = P.blob_bytes + (size_t)(block / 32) * 64 * 16 * lanes;  // tables + warp queues
   int per_sm = 0;
   CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm) : transport_occupancy<float>(block, smem, &per_sm));
   if (per_sm < 1) return fail(MC_ERR_CUDA, "transport kernel does not fit on an SM (block %d, smem %zu)", block, smem);
@@ -606,12 +641,11 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->dev));
   const int grid = sms * per_sm;
+  P.drain_threshold = o.drain_threshold ? o.drain_threshold : (uint64_t)2 * grid * block;
   CK(cudaEventRecord(p->ev[0], s));
   CK(fp64 ? launch_transport<double>(P, grid, block, smem, s) : launch_transport<float>(P, grid, block, smem, s));
   CK(cudaEventRecord(p->ev[1], s));
-  double* st = (double*)p->d_stats.ptr;
-  CK(launch_batch_stats(P.tally, P.tally_fp64, 1.0 / P.fixed_scale, bins, nb, n_histories, st, st + bins,
-                        st + 2 * bins, s));
+  CK(launch_batch_stats(P.tally, P.tally_fp64, bins, nb, n_histories, p->d_stats.ptr, s));
   CK(cudaEventRecord(p->ev[2], s));
   p->has_run = 1;
   p->n_hist = n_histories;
@@ -629,7 +663,9 @@ int mc_wait(mc_problem* p) {
   if (!p->has_run) return fail(MC_ERR_STATE, "no run yet");
   CK(cudaStreamSynchronize(p->stream));
   int status = 0;
-  CK(cudaMemcpy(&status, (char*)p->d_ctl.ptr + offsetof(Ctl, status), sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&status, p->d_sticky.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+  if (status != 0) CK(cudaMemset(p->d_sticky.ptr, 0, sizeof(int)));
+  if (status == 0) status = p->last_status;  // an error already reported stays the run's status
   p->last_status = status;
   if (status == MC_ERR_BANK_FULL) return fail(status, "particle bank overflowed; raise bank_capacity");
   if (status == MC_ERR_TIMEOUT) return fail(status, "device watchdog expired (iteration or barrier budget)");
@@ -669,18 +705,39 @@ int mc_tally_get(mc_problem* p, int tally_id, double* mean, double* std_err, siz
   const TableHeader* H = reinterpret_cast<const TableHeader*>(p->blob[0].data());
   const size_t first = tally_id == p->n_tally ? (size_t)H->leak_offset : (size_t)H->tally[tally_id].bin_offset;
   const size_t bins = (size_t)p->total_bins;
-  std::vector<double> tot(nbins), s1(nbins), s2(nbins);
-  const double* st = (const double*)p->d_stats.ptr;
-  CK(cudaMemcpy(tot.data(), st + first, nbins * 8, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(s1.data(), st + bins + first, nbins * 8, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(s2.data(), st + 2 * bins + first, nbins * 8, cudaMemcpyDeviceToHost));
   const double B = (double)p->n_batches;
-  for (size_t i = 0; i < nbins; ++i) {
-    if (mean) mean[i] = tot[i] / (double)p->n_hist;
-    if (std_err) {
-      const double var = (s2[i] - s1[i] * s1[i] / B) / (B * (B - 1.0));
-      std_err[i] = var > 0.0 ? std::sqrt(var) : 0.0;
+  const double N = (double)p->n_hist;
+  const double nbar = N / B;  // mean batch size
+  const char* st = (const char*)p->d_stats.ptr;
+  std::vector<double> mv(nbins), sv(nbins);
+  if (p->tally_fp64) {
+    std::vector<double> tot(nbins), s1(nbins), s2(nbins);
+    CK(cudaMemcpy(tot.data(), st + 8 * first, nbins * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(s1.data(), st + 8 * (bins + first), nbins * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(s2.data(), st + 8 * (2 * bins + first), nbins * 8, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < nbins; ++i) {
+      mv[i] = tot[i] / N;
+      sv[i] = (s2[i] - s1[i] * s1[i] / B) / (B * (B - 1.0));
     }
+  } else {
+    std::vector<long long> sum(nbins);
+    std::vector<unsigned long long> lo(nbins), hi(nbins);
+    CK(cudaMemcpy(sum.data(), st + 8 * first, nbins * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(lo.data(), st + 8 * (bins + first), nbins * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(hi.data(), st + 8 * (2 * bins + first), nbins * 8, cudaMemcpyDeviceToHost));
+    const double q = 1.0 / p->fixed_scale;
+    for (size_t i = 0; i < nbins; ++i) {
+      // batch means m_b = T_b q / nbar: S1 = sum m_b, S2 = sum m_b^2 (exact integer sums scaled once)
+      const double s1 = (double)sum[i] * q / nbar;
+      const double sq = ((double)hi[i] * 18446744073709551616.0 + (double)lo[i]) * q * q;
+      const double s2 = sq / (nbar * nbar);
+      mv[i] = (double)sum[i] * q / N;
+      sv[i] = (s2 - s1 * s1 / B) / (B * (B - 1.0));
+    }
+  }
+  for (size_t i = 0; i < nbins; ++i) {
+    if (mean) mean[i] = mv[i];
+    if (std_err) std_err[i] = sv[i] > 0.0 ? std::sqrt(sv[i]) : 0.0;
   }
   return MC_OK;
 }
@@ -728,8 +785,9 @@ int mc_counters_get(mc_problem* p, int64_t* counters, size_t n) {
 
 int mc_event_log(mc_problem* p, mc_event* out, size_t cap, size_t* n_out) {
   if (!p || !n_out) return fail(MC_ERR_INVALID, "NULL argument");
-  int rc = mc_wait(p);
-  if (rc != MC_OK) return rc;
+  if (!p->has_run) return fail(MC_ERR_STATE, "no run yet");
+  // the log is most useful after a failed run, so it is copied whatever the run's status
+  CK(cudaStreamSynchronize(p->stream));
   unsigned long long n = 0;
   CK(cudaMemcpy(&n, (char*)p->d_ctl.ptr + offsetof(Ctl, log_n), sizeof(n), cudaMemcpyDeviceToHost));
   size_t m = (size_t)std::min<unsigned long long>(n, p->log_cap);
@@ -742,6 +800,26 @@ int mc_event_log(mc_problem* p, mc_event* out, size_t cap, size_t* n_out) {
 
 size_t mc_problem_table_bytes(const mc_problem* p) {
   return p ? p->blob[0].size() + p->blob[1].size() : 0;
+}
+
+int mc_trace_get(mc_problem* p, uint64_t* t_ns, uint64_t* items, uint64_t* sources, size_t cap,
+                 size_t* n_out) {
+  if (!p || !n_out) return fail(MC_ERR_INVALID, "NULL argument");
+  if (!p->has_run) return fail(MC_ERR_STATE, "no run yet");
+  CK(cudaStreamSynchronize(p->stream));
+  Ctl c;
+  CK(cudaMemcpy(&c, p->d_ctl.ptr, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  size_t n = (size_t)std::min<unsigned long long>(c.iterations, kTraceCap);
+  if (n > cap) n = cap;
+  std::vector<unsigned long long> buf(3 * n);
+  if (n) CK(cudaMemcpy(buf.data(), p->d_trace.ptr, 3 * n * 8, cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < n; ++i) {
+    if (t_ns) t_ns[i] = buf[3 * i] - c.t_start;
+    if (items) items[i] = buf[3 * i + 1];
+    if (sources) sources[i] = buf[3 * i + 2];
+  }
+  *n_out = n;
+  return MC_OK;
 }
 
 int mc_run_timing(mc_problem* p, double* transport_ms, double* stats_ms) {

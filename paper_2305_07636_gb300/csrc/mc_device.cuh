@@ -38,11 +38,13 @@ struct Uni<double> {
            (1.0 / 4503599627370496.0);
   }
 };
-// FP32: 23 random bits of the first word plus one half -> open interval (0,1), exact in float
+// FP32: 23 random bits of the first word plus one half -> open interval (0,1), exact in float:
+// (m + 1/2) 2^-23 is formed as the float 1 + m 2^-23 (bit pattern) minus (1 - 2^-24); the
+// subtraction is exact (Sterbenz), so no integer-to-float conversion is needed.
 template <>
 struct Uni<float> {
   static __device__ __forceinline__ float from(uint32_t a, uint32_t) {
-    return (__uint2float_rn(a >> 9) + 0.5f) * 1.1920928955078125e-7f;
+    return __fsub_rn(__uint_as_float(0x3F800000u | (a >> 9)), 0.99999994039535522461f);
   }
 };
 
@@ -73,7 +75,7 @@ __device__ __forceinline__ float rinf<float>() { return CUDART_INF_F; }
 template <>
 __device__ __forceinline__ double rinf<double>() { return CUDART_INF; }
 
-__device__ __forceinline__ float rlog(float u) { return logf(u); }
+__device__ __forceinline__ float rlog(float u) { return __logf(u); }
 __device__ __forceinline__ double rlog(double u) { return log(u); }
 __device__ __forceinline__ float rsqrt_(float v) { return sqrtf(v); }
 __device__ __forceinline__ double rsqrt_(double v) { return sqrt(v); }
@@ -116,36 +118,72 @@ struct Tab {
 };
 
 // ------------------------------------------------------------------------------------------ state
+// Particle time.  FP64 tracking keeps a double (the oracle's arithmetic).  FP32 tracking keeps
+// an unevaluated sum of two floats (hi + lo): additions use the exact two-sum of Knuth, so the
+// clock carries about 48 significant bits and the census comparison keeps FP64-class resolution
+// without the FP64 pipe, which on this GPU runs at 1/64 of the FP32 rate.
 template <typename R>
-struct Part {
-  R x, y, z, ux, uy, uz;
-  double t, w;
+struct Part;
+
+template <>
+struct Part<float> {
+  float x, y, z, ux, uy, uz;
+  float th, tl;  // time = th + tl
+  double w;
   uint32_t tlo, thi, k, pk, elem, root;
+  __device__ __forceinline__ float time() const { return th + tl; }
+  __device__ __forceinline__ double time_d() const { return (double)th + (double)tl; }
+  __device__ __forceinline__ void advance(float l, float v, float inv_v) {
+    const float b = __fmul_rn(l, inv_v);
+    const float s = __fadd_rn(th, b);
+    const float bb = __fsub_rn(s, th);
+    const float err = __fadd_rn(__fsub_rn(th, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    const float lo = __fadd_rn(tl, err);
+    th = __fadd_rn(s, lo);
+    tl = __fsub_rn(lo, __fsub_rn(th, s));
+  }
+  // v (t_census - t), with the census time given as hi + lo
+  __device__ __forceinline__ float census_distance(float tch, float tcl, float v) const {
+    return __fadd_rn(__fsub_rn(tch, th), __fsub_rn(tcl, tl)) * v;
+  }
 };
 
+template <>
+struct Part<double> {
+  double x, y, z, ux, uy, uz;
+  double t;
+  double w;
+  uint32_t tlo, thi, k, pk, elem, root;
+  __device__ __forceinline__ double time() const { return t; }
+  __device__ __forceinline__ double time_d() const { return t; }
+  __device__ __forceinline__ void advance(double l, double v, double) { t += l / v; }
+  __device__ __forceinline__ double census_distance(double tc, double, double v) const {
+    return v * (tc - t);
+  }
+};
+
+// packed 16-byte lanes; the same layout in global banks and in the shared-memory queue
 template <typename R>
 struct Lanes;
 
-// FP32 particle = 4 x 16 B: (x,y,z,ux) (uy,uz,elem,root) (t,w) (tag_lo,tag_hi,k,packed)
+// FP32 particle = 4 x 16 B: (x,y,z,ux) (uy,uz,elem,root) (t_hi,t_lo,w) (tag_lo,tag_hi,k,packed)
 template <>
 struct Lanes<float> {
   static constexpr int N = kLanesFP32;
-  static __device__ __forceinline__ void load(Part<float>& p, uint4* const* L, uint64_t i) {
-    const float4 a = __ldcs(reinterpret_cast<const float4*>(L[0]) + i);
-    const float4 b = __ldcs(reinterpret_cast<const float4*>(L[1]) + i);
-    const double2 c = __ldcs(reinterpret_cast<const double2*>(L[2]) + i);
-    const uint4 d = __ldcs(L[3] + i);
-    p.x = a.x; p.y = a.y; p.z = a.z; p.ux = a.w;
-    p.uy = b.x; p.uz = b.y; p.elem = __float_as_uint(b.z); p.root = __float_as_uint(b.w);
-    p.t = c.x; p.w = c.y;
-    p.tlo = d.x; p.thi = d.y; p.k = d.z; p.pk = d.w;
+  static __device__ __forceinline__ void pack(const Part<float>& p, uint4 v[N]) {
+    v[0] = make_uint4(__float_as_uint(p.x), __float_as_uint(p.y), __float_as_uint(p.z), __float_as_uint(p.ux));
+    v[1] = make_uint4(__float_as_uint(p.uy), __float_as_uint(p.uz), p.elem, p.root);
+    const unsigned long long wb = (unsigned long long)__double_as_longlong(p.w);
+    v[2] = make_uint4(__float_as_uint(p.th), __float_as_uint(p.tl), (uint32_t)wb, (uint32_t)(wb >> 32));
+    v[3] = make_uint4(p.tlo, p.thi, p.k, p.pk);
   }
-  static __device__ __forceinline__ void store(const Part<float>& p, uint4* const* L, uint64_t i) {
-    __stcs(reinterpret_cast<float4*>(L[0]) + i, make_float4(p.x, p.y, p.z, p.ux));
-    __stcs(reinterpret_cast<float4*>(L[1]) + i,
-           make_float4(p.uy, p.uz, __uint_as_float(p.elem), __uint_as_float(p.root)));
-    __stcs(reinterpret_cast<double2*>(L[2]) + i, make_double2(p.t, p.w));
-    __stcs(L[3] + i, make_uint4(p.tlo, p.thi, p.k, p.pk));
+  static __device__ __forceinline__ void unpack(const uint4 v[N], Part<float>& p) {
+    p.x = __uint_as_float(v[0].x); p.y = __uint_as_float(v[0].y); p.z = __uint_as_float(v[0].z);
+    p.ux = __uint_as_float(v[0].w); p.uy = __uint_as_float(v[1].x); p.uz = __uint_as_float(v[1].y);
+    p.elem = v[1].z; p.root = v[1].w;
+    p.th = __uint_as_float(v[2].x); p.tl = __uint_as_float(v[2].y);
+    p.w = __longlong_as_double((long long)(((unsigned long long)v[2].w << 32) | v[2].z));
+    p.tlo = v[3].x; p.thi = v[3].y; p.k = v[3].z; p.pk = v[3].w;
   }
 };
 
@@ -153,27 +191,89 @@ struct Lanes<float> {
 template <>
 struct Lanes<double> {
   static constexpr int N = kLanesFP64;
-  static __device__ __forceinline__ void load(Part<double>& p, uint4* const* L, uint64_t i) {
-    const double2 a = __ldcs(reinterpret_cast<const double2*>(L[0]) + i);
-    const double2 b = __ldcs(reinterpret_cast<const double2*>(L[1]) + i);
-    const double2 c = __ldcs(reinterpret_cast<const double2*>(L[2]) + i);
-    const double2 d = __ldcs(reinterpret_cast<const double2*>(L[3]) + i);
-    const uint4 e = __ldcs(L[4] + i);
-    const uint4 f = __ldcs(L[5] + i);
-    p.x = a.x; p.y = a.y; p.z = b.x; p.ux = b.y; p.uy = c.x; p.uz = c.y;
-    p.t = d.x; p.w = d.y;
-    p.tlo = e.x; p.thi = e.y; p.k = e.z; p.pk = e.w;
-    p.elem = f.x; p.root = f.y;
+  static __device__ __forceinline__ uint4 d2(double a, double b) {
+    const unsigned long long x = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long y = (unsigned long long)__double_as_longlong(b);
+    return make_uint4((uint32_t)x, (uint32_t)(x >> 32), (uint32_t)y, (uint32_t)(y >> 32));
   }
-  static __device__ __forceinline__ void store(const Part<double>& p, uint4* const* L, uint64_t i) {
-    __stcs(reinterpret_cast<double2*>(L[0]) + i, make_double2(p.x, p.y));
-    __stcs(reinterpret_cast<double2*>(L[1]) + i, make_double2(p.z, p.ux));
-    __stcs(reinterpret_cast<double2*>(L[2]) + i, make_double2(p.uy, p.uz));
-    __stcs(reinterpret_cast<double2*>(L[3]) + i, make_double2(p.t, p.w));
-    __stcs(L[4] + i, make_uint4(p.tlo, p.thi, p.k, p.pk));
-    __stcs(L[5] + i, make_uint4(p.elem, p.root, 0u, 0u));
+  static __device__ __forceinline__ double lo(const uint4& v) {
+    return __longlong_as_double((long long)(((unsigned long long)v.y << 32) | v.x));
+  }
+  static __device__ __forceinline__ double hi(const uint4& v) {
+    return __longlong_as_double((long long)(((unsigned long long)v.w << 32) | v.z));
+  }
+  static __device__ __forceinline__ void pack(const Part<double>& p, uint4 v[N]) {
+    v[0] = d2(p.x, p.y);
+    v[1] = d2(p.z, p.ux);
+    v[2] = d2(p.uy, p.uz);
+    v[3] = d2(p.t, p.w);
+    v[4] = make_uint4(p.tlo, p.thi, p.k, p.pk);
+    v[5] = make_uint4(p.elem, p.root, 0u, 0u);
+  }
+  static __device__ __forceinline__ void unpack(const uint4 v[N], Part<double>& p) {
+    p.x = lo(v[0]); p.y = hi(v[0]); p.z = lo(v[1]); p.ux = hi(v[1]); p.uy = lo(v[2]); p.uz = hi(v[2]);
+    p.t = lo(v[3]); p.w = hi(v[3]);
+    p.tlo = v[4].x; p.thi = v[4].y; p.k = v[4].z; p.pk = v[4].w;
+    p.elem = v[5].x; p.root = v[5].y;
   }
 };
+
+// Global bank access: 16-byte vector loads and stores, lane-major SoA.  Loads go through L2 only
+// (ld.global.cg): the banks are rewritten by other SMs between grid-barrier iterations and the
+// per-SM L1 is not coherent, so an L1-cached load could return a line from an earlier iteration.
+// Each slot is read once per iteration, so L1 would not help anyway.
+template <typename R>
+__device__ __forceinline__ void bank_load(Part<R>& p, uint4* const* L, uint64_t i) {
+  uint4 v[Lanes<R>::N];
+#pragma unroll
+  for (int l = 0; l < Lanes<R>::N; ++l) v[l] = __ldcg(L[l] + i);
+  Lanes<R>::unpack(v, p);
+}
+template <typename R>
+__device__ __forceinline__ void bank_store(const Part<R>& p, uint4* const* L, uint64_t i) {
+  uint4 v[Lanes<R>::N];
+  Lanes<R>::pack(p, v);
+#pragma unroll
+  for (int l = 0; l < Lanes<R>::N; ++l) __stcs(L[l] + i, v[l]);
+}
+// shared-memory queue access: lane l of slot i at q[l * cap + i]
+template <typename R>
+__device__ __forceinline__ void queue_load(Part<R>& p, const uint4* q, unsigned cap, unsigned i) {
+  uint4 v[Lanes<R>::N];
+#pragma unroll
+  for (int l = 0; l < Lanes<R>::N; ++l) v[l] = q[l * cap + i];
+  Lanes<R>::unpack(v, p);
+}
+template <typename R>
+__device__ __forceinline__ void queue_store(const Part<R>& p, uint4* q, unsigned cap, unsigned i) {
+  uint4 v[Lanes<R>::N];
+  Lanes<R>::pack(p, v);
+#pragma unroll
+  for (int l = 0; l < Lanes<R>::N; ++l) q[l * cap + i] = v[l];
+}
+
+// Round-to-nearest double -> float on the integer pipes (positive normal weights; smaller
+// magnitudes flush to 0, larger saturate to infinity).  The hardware conversion runs on the slow
+// FP64 pipe of this GPU.
+__device__ __forceinline__ float weight_to_float(double w) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(w) + (1ull << 28);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  if (e < -126) return 0.0f;
+  if (e > 127) return CUDART_INF_F;
+  return __uint_as_float(((uint32_t)(e + 127) << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu));
+}
+
+// Non-negative float -> nearest int64 (ties up), from the float's bits: the hardware float-to-
+// int64 conversion also runs on the slow FP64 pipe.
+__device__ __forceinline__ long long float_to_fixed(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const int e = (int)(b >> 23) - 127;  // f = 1.m 2^e
+  if ((b >> 31) || e < -1) return 0ll;
+  const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+  if (e >= 23) return e >= 62 ? 0x7FFFFFFFFFFFFFFFll : (long long)(m << (e - 23));
+  const int sh = 23 - e;  // 1 .. 24
+  return (long long)((m + (1ull << (sh - 1))) >> sh);
+}
 
 // ------------------------------------------------------------------------------------------ geometry
 __device__ __forceinline__ int lat_ix(uint32_t elem) { return (int)(elem & 0xFFu); }
@@ -215,7 +315,12 @@ __device__ __forceinline__ R cyl_dist(R x, R y, R ux, R uy, R x0, R y0, R r, boo
     return d > R(0) ? d : R(0);
   }
   if (b >= R(0) || disc <= R(0)) return rinf<R>();
-  const R d = c / (-b + rsqrt_(disc));
+  // A grazing line whose chord inside the cylinder, 2 sqrt(disc) / a, is shorter than eps does
+  // not enter it: otherwise rounding can put a tangentially moving particle inside with a zero
+  // exit distance and bounce it in and out on the spot.  eps = 2e-5 cm (FP32), 1e-12 cm (FP64).
+  const R sq = rsqrt_(disc);
+  if (R(2) * sq < (sizeof(R) == 4 ? R(2e-5) : R(1e-12)) * a) return rinf<R>();
+  const R d = c / (-b + sq);
   return d > R(0) ? d : R(0);
 }
 
@@ -360,14 +465,15 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 // Warp-aggregated add: lanes that target the same bin are found with match.any; each peer group
-// is reduced by a shuffle tree over the group's ranks and its lowest lane issues one atomic.
+// is reduced by a shuffle tree over the group's ranks and its lowest lane issues one atomic.  The
+// tree runs only as deep as the largest group needs, so a warp without shared bins pays one
+// match and one vote.
 template <typename V>
-__device__ __forceinline__ V peer_reduce(unsigned mask, unsigned peers, V v) {
+__device__ __forceinline__ V peer_reduce(unsigned mask, unsigned peers, V v, unsigned depth) {
   const int lane = threadIdx.x & 31;
   const unsigned rank = __popc(peers & lanemask_lt());
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const unsigned src = __fns(peers, (unsigned)lane, d + 1);
+  for (unsigned d = 1; d < depth; d <<= 1) {
+    const unsigned src = __fns(peers, (unsigned)lane, (int)d + 1);
     const V o = __shfl_sync(mask, v, (src == 0xFFFFFFFFu) ? lane : (int)src);
     if (src != 0xFFFFFFFFu && (rank & (2 * d - 1)) == 0) v += o;
   }
@@ -378,7 +484,8 @@ __device__ __forceinline__ void add_fixed(unsigned long long* dst, long long v, 
   if (aggregate) {
     const unsigned mask = __activemask();
     const unsigned peers = __match_any_sync(mask, (unsigned long long)dst);
-    v = peer_reduce(mask, peers, v);
+    const unsigned depth = __reduce_max_sync(mask, (unsigned)__popc(peers));
+    if (depth > 1) v = peer_reduce(mask, peers, v, depth);
     if ((peers & lanemask_lt()) == 0u) atomicAdd(dst, (unsigned long long)v);
   } else {
     atomicAdd(dst, (unsigned long long)v);
@@ -389,59 +496,79 @@ __device__ __forceinline__ void add_fp64(double* dst, double v, bool aggregate) 
   if (aggregate) {
     const unsigned mask = __activemask();
     const unsigned peers = __match_any_sync(mask, (unsigned long long)dst);
-    v = peer_reduce(mask, peers, v);
+    const unsigned depth = __reduce_max_sync(mask, (unsigned)__popc(peers));
+    if (depth > 1) v = peer_reduce(mask, peers, v, depth);
     if ((peers & lanemask_lt()) == 0u) atomicAdd(dst, v);
   } else {
     atomicAdd(dst, v);
   }
 }
 
-// score value w * len into bin `bin` of the particle's batch tally
+// Scorer for one flight: the weight factor is converted once per flight, not per piece.
 template <typename R>
-__device__ __forceinline__ void score(const RunParams& P, uint64_t slot, double w, R len) {
-  if (P.tally_fp64) {
-    add_fp64(reinterpret_cast<double*>(P.tally) + slot, w * (double)len, P.aggregate != 0);
-  } else {
-    long long q;
-    if (sizeof(R) == 4)
-      q = __float2ll_rn((float)w * (float)len * (float)P.fixed_scale);
-    else
-      q = __double2ll_rn(w * (double)len * P.fixed_scale);
-    add_fixed(reinterpret_cast<unsigned long long*>(P.tally) + slot, q, P.aggregate != 0);
+struct Scorer {
+  const RunParams& P;
+  double w;        // FP64 tallies
+  float wscale;    // fixed-point tallies: w * 2^bits
+  __device__ Scorer(const RunParams& P_, double w_)
+      : P(P_), w(w_), wscale(sizeof(R) == 4 ? weight_to_float(w_) * P_.fixed_scale_f : 0.0f) {}
+  __device__ __forceinline__ void operator()(uint64_t slot, R len) const {
+    if (P.tally_fp64) {
+      add_fp64(reinterpret_cast<double*>(P.tally) + slot, w * (double)len, P.aggregate != 0);
+    } else {
+      const long long q = sizeof(R) == 4 ? float_to_fixed(wscale * (float)len)
+                                         : __double2ll_rn(w * (double)len * P.fixed_scale);
+      add_fixed(reinterpret_cast<unsigned long long*>(P.tally) + slot, q, P.aggregate != 0);
+    }
   }
+};
+
+template <typename R>
+__device__ __forceinline__ const R* time_edges(const char* base, const TallyDesc& D);
+template <>
+__device__ __forceinline__ const float* time_edges<float>(const char* base, const TallyDesc& D) {
+  return reinterpret_cast<const float*>(base + D.o_etf);
+}
+template <>
+__device__ __forceinline__ const double* time_edges<double>(const char* base, const TallyDesc& D) {
+  return reinterpret_cast<const double*>(base + D.o_et);
 }
 
 // Track-length estimator over the segment of length l from the particle's position: walk the
 // mesh cells and time bins it crosses (3D DDA plus the time axis) and score w * piece length into
-// each bin it passes through.
+// each bin it passes through.  Crossing distances are measured from the segment start, so rounding
+// does not accumulate along the walk.
 template <typename R>
 __device__ void score_segment(const Tab<R>& T, const RunParams& P, const Part<R>& p, R l,
                               uint64_t batch_base) {
   const int g = (int)pk_g(p.pk);
   const R v = T.v[g];
   const char* base = reinterpret_cast<const char*>(T.h);
+  const Scorer<R> score(P, p.w);
+  const R t0 = p.time();
   for (int ti = 0; ti < T.h->n_tally; ++ti) {
     const TallyDesc& D = T.h->tally[ti];
     const R* e[3] = {reinterpret_cast<const R*>(base + D.o_ex), reinterpret_cast<const R*>(base + D.o_ey),
                      reinterpret_cast<const R*>(base + D.o_ez)};
-    const double* et = reinterpret_cast<const double*>(base + D.o_et);
+    const R* et = time_edges<R>(base, D);
     const int n[3] = {D.nx, D.ny, D.nz};
     const R pos[3] = {p.x, p.y, p.z}, u[3] = {p.ux, p.uy, p.uz};
     int idx[3], step[3];
-    R sn[3];
+    R sn[3], inv[3];
     bool never = false;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const int i = bin_search(e[d], n[d], pos[d]);
       idx[d] = i;
+      inv[d] = R(1) / u[d];
       if (u[d] > R(0)) {
         step[d] = 1;
         if (i >= n[d]) never = true;
-        sn[d] = (i >= n[d]) ? rinf<R>() : (e[d][i + 1] - pos[d]) / u[d];
+        sn[d] = (i >= n[d]) ? rinf<R>() : (e[d][i + 1] - pos[d]) * inv[d];
       } else if (u[d] < R(0)) {
         step[d] = -1;
         if (i < 0) never = true;
-        sn[d] = (i < 0) ? rinf<R>() : (e[d][i] - pos[d]) / u[d];
+        sn[d] = (i < 0) ? rinf<R>() : (e[d][i] - pos[d]) * inv[d];
       } else {
         step[d] = 0;
         sn[d] = rinf<R>();
@@ -449,17 +576,19 @@ __device__ void score_segment(const Tab<R>& T, const RunParams& P, const Part<R>
       }
     }
     if (never) continue;
-    int it = bin_search(et, D.nt, p.t);
+    int it = bin_search(et, D.nt, t0);
     if (it >= D.nt) continue;
-    R stn = (R)((et[it + 1] - p.t)) * v;
+    R stn = (et[it + 1] - t0) * v;
+    const uint64_t gbase = batch_base + (uint64_t)D.bin_offset + (uint64_t)g * D.nt;
+    const int gstride = T.G * D.nt;
     R s = R(0);
     while (s < l) {
       R nxt = fmin(fmin(sn[0], sn[1]), fmin(sn[2], stn));
       nxt = fmin(nxt, l);
       if (nxt > s && idx[0] >= 0 && idx[0] < n[0] && idx[1] >= 0 && idx[1] < n[1] && idx[2] >= 0 &&
           idx[2] < n[2] && it >= 0) {
-        const int bin = (((idx[2] * n[1] + idx[1]) * n[0] + idx[0]) * T.G + g) * D.nt + it;
-        score(P, batch_base + (uint64_t)(D.bin_offset + bin), p.w, nxt - s);
+        const int cell = (idx[2] * n[1] + idx[1]) * n[0] + idx[0];
+        score(gbase + (uint64_t)cell * gstride + it, nxt - s);
       }
       if (nxt >= l) break;
       bool out = false;
@@ -467,17 +596,14 @@ __device__ void score_segment(const Tab<R>& T, const RunParams& P, const Part<R>
       for (int d = 0; d < 3; ++d) {
         if (sn[d] <= nxt) {
           idx[d] += step[d];
-          if (idx[d] < 0 || idx[d] >= n[d]) {
-            // left the mesh along this axis, unless it was entering from outside
-            if ((step[d] > 0 && idx[d] >= n[d]) || (step[d] < 0 && idx[d] < 0)) out = true;
-          }
-          sn[d] = out ? rinf<R>() : (e[d][idx[d] + (step[d] > 0 ? 1 : 0)] - pos[d]) / u[d];
+          if (idx[d] < 0 || idx[d] >= n[d]) out = true;  // left the mesh along this axis
+          else sn[d] = (e[d][idx[d] + (step[d] > 0 ? 1 : 0)] - pos[d]) * inv[d];
         }
       }
       if (stn <= nxt) {
         ++it;
         if (it >= D.nt) out = true;
-        else stn = (R)((et[it + 1] - p.t)) * v;
+        else stn = (et[it + 1] - t0) * v;
       }
       if (out) break;
       s = nxt;

@@ -16,6 +16,7 @@ constexpr uint32_t kChildMark = 0x80000000u;
 constexpr uint32_t kSplitMark = 0xC0000000u;
 constexpr uint32_t kChildKeyXor = 0xA5A5A5A5u;
 
+// ---- `elem` word: bits 0-7 lattice x index, 8-15 lattice y index, 16-31 statistical batch
 // ---- packed per-particle word (lane 3 .w in FP32, lane 4 .w in FP64)
 //   bits 0-4   group (G <= 32)
 //   bits 5-12  cell index
@@ -50,7 +51,8 @@ struct TallyDesc {
   int o_ex, o_ey, o_ez, o_et;  // byte offsets of the edge arrays
   int bin_offset;              // first bin of this tally in the concatenated bin space
   int n_bins;
-  int pad[2];
+  int o_etf;                   // time edges rounded to float (FP32 tracking)
+  int pad;
 };
 
 struct TableHeader {
@@ -61,6 +63,10 @@ struct TableHeader {
   double t_census;
   double src_lo[3], src_hi[3], src_t0, src_t1;
   double lat_x0, lat_y0, lat_pitch, lat_r;
+  // float copies for FP32 tracking (no double->float conversion on the device)
+  float src_lo_f[4], src_hi_f[4];
+  float src_t0_f, src_t1_f, tc_hi, tc_lo;  // census time as the float pair hi + lo
+  int has_census, pad5, pad6, pad7;
   // byte offsets
   int o_st, o_ss, o_ssf, o_nu;        // [M][G] Real: sigma_t, scatter threshold, scatter+production threshold, nu
   int o_v, o_inv_v, o_scdf, o_chi;    // [G] Real speed, 1/speed; [M][G][G] scatter CDF; [M][G] chi CDF
@@ -73,11 +79,13 @@ struct TableHeader {
 // ---- device control block, one per problem
 struct Ctl {
   unsigned long long front[3], back[3], birth[3], hstart[3];  // rotated per iteration (mod 3)
+  unsigned long long next[3];                                 // dynamic item claim counters
   unsigned int bar_count, bar_gen;
   int status, pad;
   unsigned long long counters[MC_NCOUNTERS + 1];
   unsigned long long log_n;
   unsigned long long iterations;
+  unsigned long long t_start, t_end;  // %globaltimer at kernel start / end (ns)
 };
 
 struct RunParams {
@@ -85,10 +93,18 @@ struct RunParams {
   uint4* B[2][kMaxLanes];  // ping-pong birth banks (sources' children, split copies)
   uint64_t cap_s, cap_b;
   Ctl* ctl;
+  int* sticky;             // first error of any run since the host last read it
   void* tally;             // [n_batches][total_bins] int64 (fixed point) or double
   int tally_fp64, aggregate;
   double fixed_scale;      // 2^fixed_bits
+  float fixed_scale_f;
+  int history_mode;        // 1: every iteration runs its particles to completion (no write-back)
+  uint64_t drain_threshold;// event mode: finish the run history-style once all histories are
+                           // sourced and at most this many particles remain
+  unsigned long long* trace;  // per iteration: globaltimer, items, sources|drain<<63
+  uint64_t trace_cap;
   uint64_t n_hist, hist_per_batch, h_first;
+  uint32_t batch_magic, pad_bm;  // floor(2^32 nb / N) (clamped), for the batch index
   int n_batches, blob_bytes;
   uint64_t seed;
   const uint4* blob;

@@ -5,11 +5,17 @@
 //   [handle its pending event: collision or surface]  ->  [flight: distance to collision /
 //   surface / census, move, track-length scoring]  ->  [append to the next bank, partitioned by
 //   the kind of its new pending event: collisions from the front, surfaces from the back]
-// so that in the next iteration warps take homogeneous work (all collisions, then all surfaces,
-// then births).  Newly sourced histories fill the room left by particles that died; secondaries
-// and weight-window copies go to a birth bank that the next iteration transports.  Iterations are
-// separated by a grid barrier whose wait is bounded; the device status word reports overflow,
-// lost particles and watchdog expiry instead of hanging or trapping.
+// so that in the next iteration the claimed chunks of work are homogeneous (collisions, then
+// surfaces, then births, then new sources).  Inside a CTA the two halves are compacted through a
+// shared-memory queue: all threads handle claimed events, the survivors are packed into the
+// queue, and the queue is flown by the first threads of the CTA, so flights run on full warps
+// even though collisions kill particles.  Newly sourced histories fill the room left by particles
+// that died; secondaries and weight-window copies go to a birth bank that the next iteration
+// transports.  Once every history is sourced and few particles remain, the iteration runs
+// history-style (particles stay in the queue until they die) so the tail costs one grid barrier
+// per generation instead of one per event.  Iterations are separated by a grid barrier whose wait
+// is bounded; the device status word reports overflow, lost particles and watchdog expiry instead
+// of hanging or trapping.
 #include <cuda_runtime.h>
 
 #include "mc_device.cuh"
@@ -27,13 +33,17 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
   return *(volatile const unsigned long long*)p;
 }
 
-__device__ __forceinline__ void set_status(Ctl* ctl, int code) { atomicCAS(&ctl->status, 0, code); }
+// records a device error in the run's status word and in the problem's sticky error word
+__device__ __forceinline__ void set_status(const RunParams& P, int code) {
+  atomicCAS(&P.ctl->status, 0, code);
+  atomicCAS(P.sticky, 0, code);
+}
 
 // Sense-reversing grid barrier for a cooperative (co-resident) grid.  The spin is bounded by
 // `limit` polls; on expiry the block records MC_ERR_TIMEOUT and leaves.  A waiting block also
 // leaves as soon as any block has posted an error status, so one failing block cannot leave the
 // others spinning; every block then stops at the top of its next iteration.
-__device__ void grid_barrier(Ctl* ctl, unsigned long long limit) {
+__device__ void grid_barrier(const RunParams& P, Ctl* ctl, unsigned long long limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned gen = ld_acquire(&ctl->bar_gen);
@@ -48,7 +58,7 @@ __device__ void grid_barrier(Ctl* ctl, unsigned long long limit) {
       while (ld_acquire(&ctl->bar_gen) == gen) {
         if (ld_volatile_int(&ctl->status) != 0) break;
         if (++polls > limit) {
-          set_status(ctl, MC_ERR_TIMEOUT);
+          set_status(P, MC_ERR_TIMEOUT);
           break;
         }
         __nanosleep(64);
@@ -80,7 +90,7 @@ __device__ void log_event(const RunParams& P, const Tab<R>& T, const Part<R>& p,
   e.g = (int)pk_g(p.pk);
   e.x = p.x; e.y = p.y; e.z = p.z;
   e.ux = p.ux; e.uy = p.uy; e.uz = p.uz;
-  e.t = p.t; e.w = p.w;
+  e.t = p.time_d(); e.w = p.w;
   P.log[i] = e;
 }
 
@@ -96,10 +106,10 @@ __device__ __forceinline__ void append_birth(const RunParams& P, uint4* const* B
                                              const Part<R>& c) {
   const unsigned long long i = atomicAdd(counter, 1ull);
   if (i >= P.cap_b) {
-    set_status(P.ctl, MC_ERR_BANK_FULL);
+    set_status(P, MC_ERR_BANK_FULL);
     return;
   }
-  Lanes<R>::store(c, Bout, i);
+  bank_store(c, Bout, i);
 }
 
 // weight-window test after a collision or surface event (split above, roulette below)
@@ -198,7 +208,7 @@ __device__ bool do_surface(const RunParams& P, const Tab<R>& T, Part<R>& p, uint
     const int s = (int)pk_surf(p.pk);
     const int bcnd = T.sbc[s];
     if (bcnd == MC_BC_VACUUM) {
-      score(P, batch_base + (uint64_t)(T.h->leak_offset + s), p.w, R(1));
+      Scorer<R>(P, p.w)(batch_base + (uint64_t)(T.h->leak_offset + s), R(1));
       bump(bc, MC_C_LEAK);
       log_event(P, T, p, 1, 2, 0);
       return false;
@@ -221,7 +231,7 @@ __device__ bool do_surface(const RunParams& P, const Tab<R>& T, Part<R>& p, uint
       const int nc = locate_cell(T, p.x, p.y, p.z, s, -old_sense);
       if (nc < 0) {
         bump(bc, MC_C_LOST);
-        set_status(P.ctl, MC_ERR_LOST);
+        set_status(P, MC_ERR_LOST);
         return false;
       }
       p.pk = (p.pk & ~(0xFFu << 5)) | ((uint32_t)nc << 5);
@@ -255,10 +265,10 @@ __device__ bool do_flight(const RunParams& P, const Tab<R>& T, Part<R>& p, Block
   Hit hit;
   const R ds = boundary_distance(T, p, hit);
   R dt = rinf<R>();
-  const double tc = T.h->t_census;
-  if (tc < CUDART_INF) {
-    const double d = (double)T.v[g] * (tc - p.t);
-    dt = d > 0.0 ? (R)d : R(0);
+  if (T.h->has_census) {
+    const R d = sizeof(R) == 4 ? (R)p.census_distance((R)T.h->tc_hi, (R)T.h->tc_lo, T.v[g])
+                               : (R)p.census_distance((R)T.h->t_census, R(0), T.v[g]);
+    dt = d > R(0) ? d : R(0);
   }
   bump(bc, MC_C_FLIGHT);
   uint32_t pend;
@@ -276,17 +286,14 @@ __device__ bool do_flight(const RunParams& P, const Tab<R>& T, Part<R>& p, Block
   if (!(l < rinf<R>())) {
     bump(bc, MC_C_LOST);
     log_event(P, T, p, 3, 0, 0);
-    set_status(P.ctl, MC_ERR_LOST);
+    set_status(P, MC_ERR_LOST);
     return false;
   }
   score_segment(T, P, p, l, batch_base);
   p.x += l * p.ux;
   p.y += l * p.uy;
   p.z += l * p.uz;
-  if (sizeof(R) == 8)
-    p.t += (double)l / (double)T.v[g];
-  else
-    p.t += (double)(l * T.inv_v[g]);
+  p.advance(l, T.v[g], T.inv_v[g]);
   if (pend == 0) {
     bump(bc, MC_C_CENSUS);
     log_event(P, T, p, 2, 0, 0);
@@ -294,6 +301,38 @@ __device__ bool do_flight(const RunParams& P, const Tab<R>& T, Part<R>& p, Block
   }
   p.pk = pk_set_pending(p.pk, pend, hit.type, hit.dir, hit.surf);
   return true;
+}
+
+// source box and time in the tracking precision (float copies are made on the host)
+__device__ __forceinline__ void source_box(const TableHeader* H, float lo[3], float hi[3]) {
+  for (int i = 0; i < 3; ++i) {
+    lo[i] = H->src_lo_f[i];
+    hi[i] = H->src_hi_f[i];
+  }
+}
+__device__ __forceinline__ void source_box(const TableHeader* H, double lo[3], double hi[3]) {
+  for (int i = 0; i < 3; ++i) {
+    lo[i] = H->src_lo[i];
+    hi[i] = H->src_hi[i];
+  }
+}
+__device__ __forceinline__ void source_time(const TableHeader* H, Part<float>& p, float u) {
+  p.th = H->src_t0_f + (H->src_t1_f - H->src_t0_f) * u;
+  p.tl = 0.0f;
+}
+__device__ __forceinline__ void source_time(const TableHeader* H, Part<double>& p, double u) {
+  p.t = H->src_t0 + (H->src_t1 - H->src_t0) * u;
+}
+
+// statistical batch of history h (and of all its descendants): floor(h_rel nb / N), from a
+// 32-bit reciprocal estimate corrected by exact 64-bit products (no 64-bit division)
+__device__ __forceinline__ uint32_t batch_of(const RunParams& P, uint64_t h) {
+  const uint32_t hr = (uint32_t)(h - P.h_first);
+  const unsigned long long num = (unsigned long long)hr * (unsigned long long)P.n_batches;
+  uint32_t q = __umulhi(hr, P.batch_magic);
+  while ((unsigned long long)(q + 1) * P.n_hist <= num) ++q;
+  while (q > 0 && (unsigned long long)q * P.n_hist > num) --q;
+  return q;
 }
 
 // Source particle of history h (event index kSourceEvent, blocks 0..3)
@@ -305,13 +344,14 @@ __device__ bool make_source(const RunParams& P, const Tab<R>& T, uint64_t h, Par
   const Pair2<R> b1 = draw<R>(P.seed, tlo, thi, kSourceEvent, 1);
   const Pair2<R> b2 = draw<R>(P.seed, tlo, thi, kSourceEvent, 2);
   const Pair2<R> b3 = draw<R>(P.seed, tlo, thi, kSourceEvent, 3);
-  const R lo0 = (R)H->src_lo[0], lo1 = (R)H->src_lo[1], lo2 = (R)H->src_lo[2];
+  R lo[3], hi[3];
+  source_box(H, lo, hi);
   if (H->src_pos == MC_SRC_BOX)
-    p.x = lo0 + ((R)H->src_hi[0] - lo0) * b0.a;
+    p.x = lo[0] + (hi[0] - lo[0]) * b0.a;
   else
-    p.x = lo0;
-  p.y = lo1 + ((R)H->src_hi[1] - lo1) * b0.b;
-  p.z = lo2 + ((R)H->src_hi[2] - lo2) * b1.a;
+    p.x = lo[0];
+  p.y = lo[1] + (hi[1] - lo[1]) * b0.b;
+  p.z = lo[2] + (hi[2] - lo[2]) * b1.a;
   if (H->src_dir == MC_DIR_BEAM_X) {
     p.ux = R(1);
     p.uy = R(0);
@@ -321,13 +361,13 @@ __device__ bool make_source(const RunParams& P, const Tab<R>& T, uint64_t h, Par
     iso_dir(mu, b2.a, p.ux, p.uy, p.uz);
   }
   const int g = sample_cdf(T.src_cdf, T.G, b2.b);
-  p.t = H->src_t0 + (H->src_t1 - H->src_t0) * (double)b3.a;
+  source_time(H, p, b3.a);
   p.w = 1.0;
   p.tlo = tlo;
   p.thi = thi;
   p.k = 0;
   p.root = (uint32_t)h;
-  p.elem = 0;
+  p.elem = batch_of(P, h) << 16;
   const int c = locate_cell(T, p.x, p.y, p.z, -1, 0);
   p.pk = pk_make((uint32_t)g, (uint32_t)(c < 0 ? 0 : c), 0u);
   if (c < 0) return false;
@@ -336,24 +376,56 @@ __device__ bool make_source(const RunParams& P, const Tab<R>& T, uint64_t h, Par
 }
 
 // ------------------------------------------------------------------------------------------ kernel
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Handles the pending event of a particle loaded from the bank; on survival it is ready to fly.
 template <typename R>
-__global__ void __launch_bounds__(256) k_transport(RunParams P) {
+__device__ __forceinline__ bool handle_pending(const RunParams& P, const Tab<R>& T, Part<R>& p, uint4* const* Bout,
+                                               unsigned long long* bcount, BlockCounters* bc, uint64_t bins) {
+  const uint32_t pend = pk_pend(p.pk);
+  const uint64_t bbase = (uint64_t)(p.elem >> 16) * bins;
+  const bool alive = pend == PEND_COLL ? do_collision(P, T, p, Bout, bcount, bc)
+                                       : do_surface(P, T, p, Bout, bcount, bc, bbase);
+  if (alive) {
+    p.k += 1;
+    p.pk = pk_set_pending(p.pk, PEND_NONE, 0, 1, 0);
+  }
+  return alive;
+}
+
+// Items a warp claims per atomic on the iteration's work counter (processed 32 at a time).
+constexpr unsigned kClaim = 128;
+constexpr unsigned kWarpQ = 64;  // per-warp flight queue slots
+
+// dynamic shared memory: [table blob][per-warp flight queues: warps x Lanes<R>::N x kWarpQ]
+template <typename R>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_transport(RunParams P) {
   extern __shared__ __align__(16) char smem[];
   __shared__ BlockCounters bc;
+  __shared__ int s_status;
   for (int i = threadIdx.x; i < P.blob_bytes / 16; i += blockDim.x)
     reinterpret_cast<uint4*>(smem)[i] = P.blob[i];
   if (threadIdx.x < MC_NCOUNTERS) bc.c[threadIdx.x] = 0u;
   __syncthreads();
   const Tab<R> T(smem);
-  Ctl* ctl = P.ctl;
   const int lane = threadIdx.x & 31;
-  const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  uint4* wq = reinterpret_cast<uint4*>(smem + P.blob_bytes) + (threadIdx.x >> 5) * (Lanes<R>::N * kWarpQ);
+  Ctl* ctl = P.ctl;
+  const unsigned lt = lanemask_lt();
   const uint64_t bins = (uint64_t)T.h->total_bins;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t_start = globaltimer();
 
   for (uint64_t it = 0;; ++it) {
     const int cur = (int)(it % 3), nxt = (int)((it + 1) % 3), old = (int)((it + 2) % 3);
-    if (ld_volatile_int(&ctl->status) != 0) break;
+    // the status word can change at any time (another CTA may post an error): read it once per
+    // CTA so that every thread of the CTA takes the same branch
+    if (threadIdx.x == 0) s_status = ld_volatile_int(&ctl->status);
+    __syncthreads();
+    if (s_status != 0) break;
     // the counters cannot exceed the banks (overflow stops the run above); clamp regardless
     uint64_t nF = ld_volatile_u64(&ctl->front[cur]);
     uint64_t nS = ld_volatile_u64(&ctl->back[cur]);
@@ -362,117 +434,184 @@ __global__ void __launch_bounds__(256) k_transport(RunParams P) {
     nF = nF < P.cap_s ? nF : P.cap_s;
     nS = nS < P.cap_s - nF ? nS : P.cap_s - nF;
     const uint64_t h0 = ld_volatile_u64(&ctl->hstart[cur]);
-    const uint64_t room = P.cap_s - nF - nS;
-    const uint64_t nBt = nB < room ? nB : room;  // births transported now; the rest wait
     const uint64_t left = P.n_hist - h0;
+    // history-style iterations never write survivors back, so the transport bank is all room
+    const uint64_t room = P.history_mode ? P.cap_s : P.cap_s - nF - nS;
+    const uint64_t nBt = nB < room ? nB : room;  // births transported now; the rest wait
     const uint64_t room2 = room - nBt;
     const uint64_t nSrc = left < room2 ? left : room2;
     const uint64_t W = nF + nS + nB + nSrc;
     if (W == 0) break;
     if (it >= P.max_iter) {
-      set_status(ctl, MC_ERR_TIMEOUT);
+      set_status(P, MC_ERR_TIMEOUT);
       break;
     }
+    const bool drain = P.history_mode || (nSrc == left && W <= P.drain_threshold);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       ctl->front[old] = 0ull;
       ctl->back[old] = 0ull;
       ctl->birth[old] = 0ull;
+      ctl->next[old] = 0ull;
       ctl->hstart[nxt] = h0 + nSrc;
       ctl->iterations = it + 1;
+      if (P.trace && it < P.trace_cap) {
+        P.trace[3 * it] = globaltimer();
+        P.trace[3 * it + 1] = W;
+        P.trace[3 * it + 2] = nSrc | (drain ? (1ull << 63) : 0ull);
+      }
     }
     uint4* const* Sin = P.S[it & 1];
     uint4* const* Sout = P.S[(it + 1) & 1];
     uint4* const* Bin = P.B[it & 1];
     uint4* const* Bout = P.B[(it + 1) & 1];
     unsigned long long* bcount = &ctl->birth[nxt];
+    unsigned long long* claim = &ctl->next[cur];
 
-    for (uint64_t base = gwarp * 32; base < W; base += nwarps * 32) {
-      const uint64_t item = base + lane;
-      bool alive = false;
+    // Warp loop with a per-warp flight queue in shared memory.  (A) While fewer than 32
+    // particles are queued, the warp takes the next 32 items of its claimed range, handles their
+    // pending events on all lanes, and packs the survivors into the queue.  (B) The warp flies up
+    // to 32 queued particles on full lanes and appends the survivors to the next bank (or, in
+    // history-style iterations, handles their next event and queues them again).  The queue
+    // count is warp-uniform and lives in a register; only __syncwarp orders the queue accesses.
+    unsigned qn = 0;
+    uint64_t rbeg = 0, rend = 0;  // the warp's claimed item range
+    bool exhausted = false;
+    while (true) {
+      while (qn < 32u && !(exhausted && rbeg >= rend)) {
+        if (rbeg >= rend) {
+          unsigned long long b = 0;
+          if (lane == 0) b = atomicAdd(claim, (unsigned long long)kClaim);
+          b = __shfl_sync(0xFFFFFFFFu, b, 0);
+          rbeg = b;
+          rend = b + kClaim < W ? b + kClaim : W;
+          if (b + kClaim >= W) exhausted = true;
+          if (rbeg >= rend) break;
+        }
+        const uint64_t item = rbeg + lane;
+        rbeg = rbeg + 32 < rend ? rbeg + 32 : rend;
+        Part<R> p;
+        bool ready = false;
+        if (item < rend) {
+          if (item < nF + nS) {
+            bank_load(p, Sin, item < nF ? item : P.cap_s - 1 - (item - nF));
+            ready = handle_pending(P, T, p, Bout, bcount, &bc, bins);
+          } else if (item < nF + nS + nB) {
+            const uint64_t j = item - nF - nS;
+            bank_load(p, Bin, j);
+            if (j >= nBt) append_birth(P, Bout, bcount, p);  // waits for room
+            else ready = true;
+          } else {
+            const uint64_t h = P.h_first + h0 + (item - nF - nS - nB);
+            bump(&bc, MC_C_SOURCE);
+            ready = make_source(P, T, h, p);
+            if (!ready) {
+              bump(&bc, MC_C_LOST);
+              set_status(P, MC_ERR_LOST);
+            }
+          }
+        }
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, ready);
+        if (ready) queue_store(p, wq, kWarpQ, qn + __popc(m & lt));
+        qn += __popc(m);
+        __syncwarp();
+      }
+      if (qn == 0u) break;  // the warp's items are exhausted and nothing is left to fly
+      const unsigned nfly = qn < 32u ? qn : 32u;
       Part<R> p;
-      if (item < W) {
-        bool carry = false;
-        bool have = true;
-        if (item < nF) {
-          Lanes<R>::load(p, Sin, item);
-        } else if (item < nF + nS) {
-          Lanes<R>::load(p, Sin, P.cap_s - 1 - (item - nF));
-        } else if (item < nF + nS + nB) {
-          const uint64_t j = item - nF - nS;
-          Lanes<R>::load(p, Bin, j);
-          carry = j >= nBt;
-        } else {
-          const uint64_t h = P.h_first + h0 + (item - nF - nS - nB);
-          bump(&bc, MC_C_SOURCE);
-          have = make_source(P, T, h, p);
-          if (!have) {
-            bump(&bc, MC_C_LOST);
-            set_status(ctl, MC_ERR_LOST);
-          }
+      const bool have = (unsigned)lane < nfly;
+      if (have) queue_load(p, wq, kWarpQ, qn - nfly + lane);
+      __syncwarp();
+      qn -= nfly;
+      bool out = false, again = false;
+      if (have) {
+        bool alive = do_flight(P, T, p, &bc, (uint64_t)(p.elem >> 16) * bins);
+        if (alive && p.k + 1 >= P.max_iter) {
+          // a particle that never ends (e.g. a reflective void without census) cannot keep the
+          // warp busy forever in history-style iterations: the same budget as the iteration
+          // watchdog ends it with MC_ERR_TIMEOUT
+          set_status(P, MC_ERR_TIMEOUT);
+          alive = false;
         }
-        if (carry) {
-          append_birth(P, Bout, bcount, p);
-        } else if (have) {
-          const uint64_t batch = ((uint64_t)(p.root - (uint32_t)P.h_first) * (uint64_t)P.n_batches) / P.n_hist;
-          const uint64_t bbase = batch * bins;
-          const uint32_t pend = pk_pend(p.pk);
-          alive = true;
-          if (pend == PEND_COLL) alive = do_collision(P, T, p, Bout, bcount, &bc);
-          else if (pend == PEND_SURF) alive = do_surface(P, T, p, Bout, bcount, &bc, bbase);
-          if (alive) {
-            if (pend != PEND_NONE) p.k += 1;
-            p.pk = pk_set_pending(p.pk, PEND_NONE, 0, 1, 0);
-            alive = do_flight(P, T, p, &bc, bbase);
-          }
+        if (alive) {
+          if (drain) again = handle_pending(P, T, p, Bout, bcount, &bc, bins);
+          else out = true;
         }
+      }
+      if (drain) {
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, again);
+        if (again) queue_store(p, wq, kWarpQ, qn + __popc(m & lt));
+        qn += __popc(m);
+        __syncwarp();
+        continue;
       }
       // append survivors, partitioned by their pending event: one atomic per warp per side
-      const bool wF = alive && pk_pend(p.pk) == PEND_COLL;
-      const bool wS = alive && pk_pend(p.pk) == PEND_SURF;
+      const bool wF = out && pk_pend(p.pk) == PEND_COLL;
+      const bool wS = out && pk_pend(p.pk) == PEND_SURF;
       const unsigned mF = __ballot_sync(0xFFFFFFFFu, wF), mS = __ballot_sync(0xFFFFFFFFu, wS);
-      unsigned long long bF = 0, bS = 0;
-      if (lane == 0) {
-        if (mF) bF = atomicAdd(&ctl->front[nxt], (unsigned long long)__popc(mF));
-        if (mS) bS = atomicAdd(&ctl->back[nxt], (unsigned long long)__popc(mS));
-      }
-      bF = __shfl_sync(0xFFFFFFFFu, bF, 0);
-      bS = __shfl_sync(0xFFFFFFFFu, bS, 0);
-      const unsigned lt = lanemask_lt();
-      // front + back <= items transported <= cap_s, so the two regions never meet
-      if (wF) {
-        const uint64_t i = bF + __popc(mF & lt);
-        if (i < P.cap_s) Lanes<R>::store(p, Sout, i);
-        else set_status(ctl, MC_ERR_BANK_FULL);
-      }
-      if (wS) {
-        const uint64_t i = bS + __popc(mS & lt);
-        if (i < P.cap_s) Lanes<R>::store(p, Sout, P.cap_s - 1 - i);
-        else set_status(ctl, MC_ERR_BANK_FULL);
+      if (mF | mS) {
+        unsigned long long bF = 0, bS = 0;
+        if (lane == 0) {
+          if (mF) bF = atomicAdd(&ctl->front[nxt], (unsigned long long)__popc(mF));
+          if (mS) bS = atomicAdd(&ctl->back[nxt], (unsigned long long)__popc(mS));
+        }
+        bF = __shfl_sync(0xFFFFFFFFu, bF, 0);
+        bS = __shfl_sync(0xFFFFFFFFu, bS, 0);
+        // front + back <= items transported <= cap_s, so the two regions never meet
+        if (wF) {
+          const uint64_t i = bF + __popc(mF & lt);
+          if (i < P.cap_s) bank_store(p, Sout, i);
+          else set_status(P, MC_ERR_BANK_FULL);
+        }
+        if (wS) {
+          const uint64_t i = bS + __popc(mS & lt);
+          if (i < P.cap_s) bank_store(p, Sout, P.cap_s - 1 - i);
+          else set_status(P, MC_ERR_BANK_FULL);
+        }
       }
     }
-    grid_barrier(ctl, P.spin_limit);
+    grid_barrier(P, ctl, P.spin_limit);
   }
   __syncthreads();
   if (threadIdx.x < MC_NCOUNTERS && bc.c[threadIdx.x])
     atomicAdd(&ctl->counters[threadIdx.x], (unsigned long long)bc.c[threadIdx.x]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t_end = globaltimer();
 }
 
 // ------------------------------------------------------------------------------------------ stats
-// Per bin: total over batches, and sum / sum of squares of the per-history batch means.
-// History h belongs to batch floor(h nb / N), so batch j holds ceil((j+1)N/nb) - ceil(jN/nb) >= 1
-// histories when N >= nb.
-__global__ void k_batch_stats(const void* tally, int fp64, double inv_scale, uint64_t bins, int nb,
-                              uint64_t n_hist, double* tot, double* s1, double* s2) {
+// Batch statistics of every bin.  Fixed-point tallies: the exact integer sum over batches of the
+// batch totals T_b and the exact 128-bit sum of T_b^2 (integer pipes only; the final
+// floating-point arithmetic happens once per bin at readback).  FP64 tallies: sum of T_b and of
+// the batch means and their squares, with the mean batch size.
+__global__ void k_batch_stats_fixed(const long long* tally, uint64_t bins, int nb, long long* sum,
+                                    unsigned long long* sq_lo, unsigned long long* sq_hi) {
+  for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < bins;
+       b += (uint64_t)gridDim.x * blockDim.x) {
+    long long s = 0;
+    unsigned long long lo = 0, hi = 0;
+    for (int j = 0; j < nb; ++j) {
+      const long long x = __ldcs(tally + (uint64_t)j * bins + b);
+      s += x;
+      const unsigned long long ux = (unsigned long long)(x < 0 ? -x : x);
+      const unsigned long long plo = ux * ux, phi = __umul64hi(ux, ux);
+      const unsigned long long nlo = lo + plo;
+      hi += phi + (nlo < lo ? 1ull : 0ull);
+      lo = nlo;
+    }
+    sum[b] = s;
+    sq_lo[b] = lo;
+    sq_hi[b] = hi;
+  }
+}
+
+__global__ void k_batch_stats_fp64(const double* tally, uint64_t bins, int nb, double inv_nbar,
+                                   double* tot, double* s1, double* s2) {
   for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < bins;
        b += (uint64_t)gridDim.x * blockDim.x) {
     double t = 0.0, a = 0.0, q = 0.0;
     for (int j = 0; j < nb; ++j) {
-      const uint64_t i = (uint64_t)j * bins + b;
-      const double x = fp64 ? reinterpret_cast<const double*>(tally)[i]
-                            : (double)reinterpret_cast<const long long*>(tally)[i] * inv_scale;
+      const double x = __ldcs(tally + (uint64_t)j * bins + b);
       t += x;
-      const uint64_t lo = ((uint64_t)j * n_hist + nb - 1) / nb, hi = ((uint64_t)(j + 1) * n_hist + nb - 1) / nb;
-      const double m = x / (double)(hi - lo);
+      const double m = x * inv_nbar;
       a += m;
       q += m * m;
     }
@@ -510,13 +649,22 @@ template cudaError_t launch_transport<double>(const RunParams&, int, int, size_t
 template cudaError_t transport_occupancy<float>(int, size_t, int*);
 template cudaError_t transport_occupancy<double>(int, size_t, int*);
 
-cudaError_t launch_batch_stats(const void* tally, int fp64, double inv_scale, uint64_t bins, int nb,
-                               uint64_t n_hist, double* tot, double* s1, double* s2, cudaStream_t s) {
+cudaError_t launch_batch_stats(const void* tally, int fp64, uint64_t bins, int nb, uint64_t n_hist,
+                               void* out, cudaStream_t s) {
   const int block = 256;
   uint64_t g = (bins + block - 1) / block;
   if (g > 152 * 8) g = 152 * 8;
   if (g < 1) g = 1;
-  k_batch_stats<<<(unsigned)g, block, 0, s>>>(tally, fp64, inv_scale, bins, nb, n_hist, tot, s1, s2);
+  if (fp64) {
+    double* o = reinterpret_cast<double*>(out);
+    k_batch_stats_fp64<<<(unsigned)g, block, 0, s>>>(reinterpret_cast<const double*>(tally), bins, nb,
+                                                     (double)nb / (double)n_hist, o, o + bins, o + 2 * bins);
+  } else {
+    char* o = reinterpret_cast<char*>(out);
+    k_batch_stats_fixed<<<(unsigned)g, block, 0, s>>>(
+        reinterpret_cast<const long long*>(tally), bins, nb, reinterpret_cast<long long*>(o),
+        reinterpret_cast<unsigned long long*>(o + 8 * bins), reinterpret_cast<unsigned long long*>(o + 16 * bins));
+  }
   return cudaGetLastError();
 }
 

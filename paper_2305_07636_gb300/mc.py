@@ -87,7 +87,8 @@ class mc_run_opts(C.Structure):
                 ("block_size", C.c_int), ("blocks_per_sm", C.c_int),
                 ("max_iterations", C.c_uint64), ("aggregate_atomics", C.c_int),
                 ("ww_enable", C.c_int), ("log_first", C.c_uint64), ("log_count", C.c_uint64),
-                ("log_capacity", C.c_uint64), ("first_history", C.c_uint64)]
+                ("log_capacity", C.c_uint64), ("first_history", C.c_uint64),
+                ("algorithm", C.c_int), ("drain_threshold", C.c_uint64)]
 
 
 class mc_event(C.Structure):
@@ -120,6 +121,8 @@ SIGNATURES = {
     "mc_event_log": (C.c_int, [C.c_void_p, C.POINTER(mc_event), C.c_size_t,
                                C.POINTER(C.c_size_t)]),
     "mc_run_timing": (C.c_int, [C.c_void_p, DP, DP]),
+    "mc_trace_get": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+                               C.POINTER(C.c_uint64), C.c_size_t, C.POINTER(C.c_size_t)]),
     "mc_problem_table_bytes": (C.c_size_t, [C.c_void_p]),
     "mc_problem_destroy": (None, [C.c_void_p]),
     "mc_last_error": (C.c_char_p, []),
@@ -161,6 +164,8 @@ def run_opts(**kw) -> mc_run_opts:
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = {"fp32": MC_FP32, "fp64": MC_FP64}[v]
+        if k == "algorithm" and isinstance(v, str):
+            v = {"event": 0, "history": 1}[v]
         if k == "tally_mode" and isinstance(v, str):
             v = {"fixed": MC_TALLY_FIXED64, "fp64": MC_TALLY_FP64}[v]
         setattr(o, k, v)
@@ -295,9 +300,13 @@ def tally_batches(h: int, tally_id: int) -> np.ndarray:
     return out.reshape((nb.value,) + shp)
 
 
-def counters_get(h: int) -> dict:
+def counters_get(h: int, allow_error: bool = False) -> dict:
+    """mc_counters_get.  The library returns the counters even after a device error (bank
+    overflow, watchdog); unless allow_error, the run's status is then raised here."""
     c = (C.c_int64 * NCOUNTERS)()
     check(lib().mc_counters_get(C.c_void_p(h), c, NCOUNTERS))
+    if not allow_error:
+        check(lib().mc_wait(C.c_void_p(h)))
     return dict(zip(COUNTER_NAMES, [int(v) for v in c]))
 
 
@@ -315,6 +324,18 @@ def run_timing(h: int):
     a, b = C.c_double(0), C.c_double(0)
     check(lib().mc_run_timing(C.c_void_p(h), C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def trace_get(h: int, cap: int = 65536):
+    """mc_trace_get: per-iteration (t_ns, items, sources, drain) arrays of the last run."""
+    t = np.zeros(cap, np.uint64)
+    w = np.zeros(cap, np.uint64)
+    s = np.zeros(cap, np.uint64)
+    n = C.c_size_t(0)
+    u64p = lambda a: a.ctypes.data_as(C.POINTER(C.c_uint64))
+    check(lib().mc_trace_get(C.c_void_p(h), u64p(t), u64p(w), u64p(s), cap, C.byref(n)))
+    k = n.value
+    return t[:k], w[:k], s[:k] & ((1 << 63) - 1), (s[:k] >> 63).astype(bool)
 
 
 def philox(seed: int, ctr_dev_ptr: int, out_dev_ptr: int, n: int, stream=None):
@@ -361,6 +382,9 @@ class Problem:
 
     def table_bytes(self):
         return int(lib().mc_problem_table_bytes(C.c_void_p(self.h)))
+
+    def trace(self):
+        return trace_get(self.h)
 
     def timing(self):
         return run_timing(self.h)

@@ -143,6 +143,13 @@ def test_cylinder_distance_cases():
     assert math.isinf(d(-2.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0))    # parallel to the axis
     # oblique chord: from (-2, 0.6) along +x hits x = -0.8
     assert d(-2.0, 0.6, 1.0, 0.0, 0.0, 0.0, 1.0, 0) == pytest.approx(1.2, abs=1e-14)
+    # grazing lines, on a cylinder small enough that the discriminant is resolved: a chord of
+    # 5e-13 cm (below 1e-12) is not entered, a chord of 1e-11 cm is
+    r = 1e-6
+    y = math.sqrt(r * r - 6.25e-26)
+    assert math.isinf(d(-1.5e-6, y, 1.0, 0.0, 0.0, 0.0, r, 0))
+    y = math.sqrt(r * r - 2.5e-23)
+    assert d(-1.5e-6, y, 1.0, 0.0, 0.0, 0.0, r, 0) == pytest.approx(1.5e-6 - 5e-12, abs=1e-16)
     # a 3D direction with a z component: distance scales by 1/sqrt(ux^2+uy^2) of the xy speed
     s = 0.6
     assert d(-2.0, 0.0, s, 0.0, 0.0, 0.0, 1.0, 0) == pytest.approx(1.0 / s, abs=1e-14)
