@@ -156,6 +156,8 @@ typedef struct {
   int algorithm;          /* mc_algorithm (default MC_ALG_EVENT) */
   uint64_t drain_threshold; /* event mode: once every history is sourced and at most this many
                                particles remain, finish them history-style (0 = 2 per thread) */
+  int tally_stripes;      /* copies of the batch tallies that CTAs score into round-robin, summed
+                             by the statistics (0 = up to 16 within a 64 MB budget) */
 } mc_run_opts;
 
 /* Fills the defaults listed above. */

@@ -26,8 +26,8 @@ template <typename R>
 cudaError_t launch_transport(const RunParams& P, int grid, int block, size_t smem, cudaStream_t s);
 template <typename R>
 cudaError_t transport_occupancy(int block, size_t smem, int* per_sm);
-cudaError_t launch_batch_stats(const void* tally, int fp64, uint64_t bins, int nb, uint64_t n_hist,
-                               void* out, cudaStream_t s);
+cudaError_t launch_batch_stats(const void* tally, int fp64, uint64_t bins, int nb, int stripes,
+                               uint64_t n_hist, void* out, cudaStream_t s);
 cudaError_t launch_philox(uint64_t seed, const uint4* ctr, uint4* out, uint64_t n, cudaStream_t s);
 }  // namespace mcgb
 
@@ -160,6 +160,7 @@ struct mc_problem {
   uint64_t log_cap = 0;
   int last_status = MC_OK;
   int tally_fp64 = 0;
+  uint32_t stripes = 1;
   double fixed_scale = 1.0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // transport start, transport end, stats end
   // weight windows
@@ -569,7 +570,14 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   if (rc != MC_OK) return rc;
   const int nb = o.n_batches;
   const uint64_t bins = (uint64_t)p->total_bins;
-  rc = p->d_tally.ensure((size_t)nb * bins * 8, p->dev);
+  // small tallies get up to 16 copies (within a 64 MB budget) to spread same-bin atomics
+  uint32_t stripes = o.tally_stripes > 0 ? (uint32_t)o.tally_stripes : 1u;
+  if (o.tally_stripes <= 0) {
+    const double copy_bytes = (double)nb * (double)bins * 8.0;
+    stripes = (uint32_t)std::max(1.0, std::min(16.0, std::floor(64.0 * 1048576.0 / copy_bytes)));
+  }
+  if (stripes > 256) return fail(MC_ERR_INVALID, "tally_stripes above 256");
+  rc = p->d_tally.ensure((size_t)stripes * nb * bins * 8, p->dev);
   if (rc == MC_OK) rc = p->d_stats.ensure((size_t)3 * bins * 8, p->dev);
   if (rc != MC_OK) return rc;
   uint64_t log_cap = 0;
@@ -591,6 +599,8 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   P.ctl = (Ctl*)p->d_ctl.ptr;
   P.sticky = (int*)p->d_sticky.ptr;
   P.tally = p->d_tally.ptr;
+  P.tally_stripes = stripes;
+  P.stripe_stride = (uint64_t)nb * bins;
   P.tally_fp64 = o.tally_mode == MC_TALLY_FP64;
   P.aggregate = o.aggregate_atomics;
   P.fixed_scale = std::ldexp(1.0, o.fixed_bits);
@@ -630,7 +640,7 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
     P.ww_split_max = 10;
   }
   CK(cudaMemsetAsync(p->d_ctl.ptr, 0, sizeof(Ctl), s));
-  CK(cudaMemsetAsync(p->d_tally.ptr, 0, (size_t)nb * bins * 8, s));
+  CK(cudaMemsetAsync(p->d_tally.ptr, 0, (size_t)stripes * nb * bins * 8, s));
   if (P.log) CK(cudaMemsetAsync(p->d_log.ptr, 0, log_cap * sizeof(mc_event), s));
   const int block = o.block_size ? o.block_size : 256;
   const size_t smem = P.blob_bytes + (size_t)(block / 32) * 64 * 16 * lanes;  // tables + warp queues
@@ -645,7 +655,7 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   CK(cudaEventRecord(p->ev[0], s));
   CK(fp64 ? launch_transport<double>(P, grid, block, smem, s) : launch_transport<float>(P, grid, block, smem, s));
   CK(cudaEventRecord(p->ev[1], s));
-  CK(launch_batch_stats(P.tally, P.tally_fp64, bins, nb, n_histories, p->d_stats.ptr, s));
+  CK(launch_batch_stats(P.tally, P.tally_fp64, bins, nb, (int)stripes, n_histories, p->d_stats.ptr, s));
   CK(cudaEventRecord(p->ev[2], s));
   p->has_run = 1;
   p->n_hist = n_histories;
@@ -654,6 +664,7 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   p->log_cap = log_cap;
   p->last_status = MC_OK;
   p->tally_fp64 = P.tally_fp64;
+  p->stripes = stripes;
   p->fixed_scale = P.fixed_scale;
   return MC_OK;
 }
@@ -756,10 +767,25 @@ int mc_tally_batches(mc_problem* p, int tally_id, double* out, size_t n, int* n_
   const TableHeader* H = reinterpret_cast<const TableHeader*>(p->blob[0].data());
   const size_t first = tally_id == p->n_tally ? (size_t)H->leak_offset : (size_t)H->tally[tally_id].bin_offset;
   const size_t bins = (size_t)p->total_bins;
-  std::vector<int64_t> raw(nbins);
+  std::vector<int64_t> raw(nbins), part(nbins);
   for (int j = 0; j < nb; ++j) {
-    CK(cudaMemcpy(raw.data(), (const char*)p->d_tally.ptr + ((size_t)j * bins + first) * 8, nbins * 8,
-                  cudaMemcpyDeviceToHost));
+    for (uint32_t c = 0; c < p->stripes; ++c) {
+      CK(cudaMemcpy(c ? part.data() : raw.data(),
+                    (const char*)p->d_tally.ptr + ((size_t)c * nb * bins + (size_t)j * bins + first) * 8, nbins * 8,
+                    cudaMemcpyDeviceToHost));
+      if (c)
+        for (size_t i = 0; i < nbins; ++i) {
+          if (p->tally_fp64) {
+            double a, b;
+            std::memcpy(&a, &raw[i], 8);
+            std::memcpy(&b, &part[i], 8);
+            a += b;
+            std::memcpy(&raw[i], &a, 8);
+          } else {
+            raw[i] += part[i];
+          }
+        }
+    }
     const uint64_t lo = ((uint64_t)j * p->n_hist + nb - 1) / nb, hi = ((uint64_t)(j + 1) * p->n_hist + nb - 1) / nb;
     const double cnt = (double)(hi - lo);
     for (size_t i = 0; i < nbins; ++i) {

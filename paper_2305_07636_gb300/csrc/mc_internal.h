@@ -94,6 +94,9 @@ struct RunParams {
   uint64_t cap_s, cap_b;
   Ctl* ctl;
   int* sticky;             // first error of any run since the host last read it
+  uint32_t tally_stripes;  // copies of the batch tallies; CTA b scores into copy b % stripes
+  uint32_t pad_ts;
+  uint64_t stripe_stride;  // elements per copy (n_batches * total_bins)
   void* tally;             // [n_batches][total_bins] int64 (fixed point) or double
   int tally_fp64, aggregate;
   double fixed_scale;      // 2^fixed_bits

@@ -385,9 +385,10 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 // Handles the pending event of a particle loaded from the bank; on survival it is ready to fly.
 template <typename R>
 __device__ __forceinline__ bool handle_pending(const RunParams& P, const Tab<R>& T, Part<R>& p, uint4* const* Bout,
-                                               unsigned long long* bcount, BlockCounters* bc, uint64_t bins) {
+                                               unsigned long long* bcount, BlockCounters* bc, uint64_t bins,
+                                               uint64_t stripe_off) {
   const uint32_t pend = pk_pend(p.pk);
-  const uint64_t bbase = (uint64_t)(p.elem >> 16) * bins;
+  const uint64_t bbase = stripe_off + (uint64_t)(p.elem >> 16) * bins;
   const bool alive = pend == PEND_COLL ? do_collision(P, T, p, Bout, bcount, bc)
                                        : do_surface(P, T, p, Bout, bcount, bc, bbase);
   if (alive) {
@@ -417,6 +418,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_transport(RunPa
   Ctl* ctl = P.ctl;
   const unsigned lt = lanemask_lt();
   const uint64_t bins = (uint64_t)T.h->total_bins;
+  // small tallies are striped over several copies so that hot bins are not one L2 address
+  const uint64_t stripe_off = (uint64_t)(blockIdx.x % P.tally_stripes) * P.stripe_stride;
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t_start = globaltimer();
 
   for (uint64_t it = 0;; ++it) {
@@ -494,7 +497,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_transport(RunPa
         if (item < rend) {
           if (item < nF + nS) {
             bank_load(p, Sin, item < nF ? item : P.cap_s - 1 - (item - nF));
-            ready = handle_pending(P, T, p, Bout, bcount, &bc, bins);
+            ready = handle_pending(P, T, p, Bout, bcount, &bc, bins, stripe_off);
           } else if (item < nF + nS + nB) {
             const uint64_t j = item - nF - nS;
             bank_load(p, Bin, j);
@@ -524,7 +527,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_transport(RunPa
       qn -= nfly;
       bool out = false, again = false;
       if (have) {
-        bool alive = do_flight(P, T, p, &bc, (uint64_t)(p.elem >> 16) * bins);
+        bool alive = do_flight(P, T, p, &bc, stripe_off + (uint64_t)(p.elem >> 16) * bins);
         if (alive && p.k + 1 >= P.max_iter) {
           // a particle that never ends (e.g. a reflective void without census) cannot keep the
           // warp busy forever in history-style iterations: the same budget as the iteration
@@ -533,7 +536,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_transport(RunPa
           alive = false;
         }
         if (alive) {
-          if (drain) again = handle_pending(P, T, p, Bout, bcount, &bc, bins);
+          if (drain) again = handle_pending(P, T, p, Bout, bcount, &bc, bins, stripe_off);
           else out = true;
         }
       }
@@ -582,14 +585,16 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_transport(RunPa
 // batch totals T_b and the exact 128-bit sum of T_b^2 (integer pipes only; the final
 // floating-point arithmetic happens once per bin at readback).  FP64 tallies: sum of T_b and of
 // the batch means and their squares, with the mean batch size.
-__global__ void k_batch_stats_fixed(const long long* tally, uint64_t bins, int nb, long long* sum,
+__global__ void k_batch_stats_fixed(const long long* tally, uint64_t bins, int nb, int stripes, long long* sum,
                                     unsigned long long* sq_lo, unsigned long long* sq_hi) {
+  const uint64_t stride = (uint64_t)nb * bins;
   for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < bins;
        b += (uint64_t)gridDim.x * blockDim.x) {
     long long s = 0;
     unsigned long long lo = 0, hi = 0;
     for (int j = 0; j < nb; ++j) {
-      const long long x = __ldcs(tally + (uint64_t)j * bins + b);
+      long long x = 0;
+      for (int c = 0; c < stripes; ++c) x += __ldcs(tally + c * stride + (uint64_t)j * bins + b);
       s += x;
       const unsigned long long ux = (unsigned long long)(x < 0 ? -x : x);
       const unsigned long long plo = ux * ux, phi = __umul64hi(ux, ux);
@@ -603,13 +608,15 @@ __global__ void k_batch_stats_fixed(const long long* tally, uint64_t bins, int n
   }
 }
 
-__global__ void k_batch_stats_fp64(const double* tally, uint64_t bins, int nb, double inv_nbar,
+__global__ void k_batch_stats_fp64(const double* tally, uint64_t bins, int nb, int stripes, double inv_nbar,
                                    double* tot, double* s1, double* s2) {
+  const uint64_t stride = (uint64_t)nb * bins;
   for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < bins;
        b += (uint64_t)gridDim.x * blockDim.x) {
     double t = 0.0, a = 0.0, q = 0.0;
     for (int j = 0; j < nb; ++j) {
-      const double x = __ldcs(tally + (uint64_t)j * bins + b);
+      double x = 0.0;
+      for (int c = 0; c < stripes; ++c) x += __ldcs(tally + c * stride + (uint64_t)j * bins + b);
       t += x;
       const double m = x * inv_nbar;
       a += m;
@@ -649,20 +656,20 @@ template cudaError_t launch_transport<double>(const RunParams&, int, int, size_t
 template cudaError_t transport_occupancy<float>(int, size_t, int*);
 template cudaError_t transport_occupancy<double>(int, size_t, int*);
 
-cudaError_t launch_batch_stats(const void* tally, int fp64, uint64_t bins, int nb, uint64_t n_hist,
-                               void* out, cudaStream_t s) {
+cudaError_t launch_batch_stats(const void* tally, int fp64, uint64_t bins, int nb, int stripes,
+                               uint64_t n_hist, void* out, cudaStream_t s) {
   const int block = 256;
   uint64_t g = (bins + block - 1) / block;
   if (g > 152 * 8) g = 152 * 8;
   if (g < 1) g = 1;
   if (fp64) {
     double* o = reinterpret_cast<double*>(out);
-    k_batch_stats_fp64<<<(unsigned)g, block, 0, s>>>(reinterpret_cast<const double*>(tally), bins, nb,
+    k_batch_stats_fp64<<<(unsigned)g, block, 0, s>>>(reinterpret_cast<const double*>(tally), bins, nb, stripes,
                                                      (double)nb / (double)n_hist, o, o + bins, o + 2 * bins);
   } else {
     char* o = reinterpret_cast<char*>(out);
     k_batch_stats_fixed<<<(unsigned)g, block, 0, s>>>(
-        reinterpret_cast<const long long*>(tally), bins, nb, reinterpret_cast<long long*>(o),
+        reinterpret_cast<const long long*>(tally), bins, nb, stripes, reinterpret_cast<long long*>(o),
         reinterpret_cast<unsigned long long*>(o + 8 * bins), reinterpret_cast<unsigned long long*>(o + 16 * bins));
   }
   return cudaGetLastError();

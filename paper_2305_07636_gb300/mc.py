@@ -88,7 +88,8 @@ class mc_run_opts(C.Structure):
                 ("max_iterations", C.c_uint64), ("aggregate_atomics", C.c_int),
                 ("ww_enable", C.c_int), ("log_first", C.c_uint64), ("log_count", C.c_uint64),
                 ("log_capacity", C.c_uint64), ("first_history", C.c_uint64),
-                ("algorithm", C.c_int), ("drain_threshold", C.c_uint64)]
+                ("algorithm", C.c_int), ("drain_threshold", C.c_uint64),
+                ("tally_stripes", C.c_int)]
 
 
 class mc_event(C.Structure):
