@@ -148,7 +148,8 @@ typedef struct {
   int block_size;         /* threads per CTA (0 = autotuned default) */
   int blocks_per_sm;      /* CTAs per SM (0 = as many as fit) */
   uint64_t max_iterations;/* watchdog: event iterations before MC_ERR_TIMEOUT (0 = 2^20) */
-  int aggregate_atomics;  /* 1 = warp-aggregated tally atomics (default), 0 = one per thread */
+  int aggregate_atomics;  /* 1 = warp-aggregated tally atomics, 0 = one atomic per score,
+                             -1 = auto (default): aggregate a small tally that is not striped */
   int ww_enable;          /* 1 = apply the weight-window table set by mc_ww_set_table */
   uint64_t log_first, log_count; /* log every event of histories [log_first, +log_count) */
   uint64_t log_capacity;  /* event records kept (0 = 64 per logged history) */
@@ -174,11 +175,12 @@ typedef struct {
   double x, y, z, ux, uy, uz, t, w;
 } mc_event;
 
-/* Counters summed over a run, in this order. */
+/* Counters summed over a run, in this order.  MC_C_SCORES counts track-length tally updates
+ * (one per mesh cell and time bin a flight crosses). */
 typedef enum {
   MC_C_SOURCE = 0, MC_C_SECONDARY, MC_C_CAPTURE, MC_C_PRODUCTION, MC_C_LEAK, MC_C_CENSUS,
   MC_C_LOST, MC_C_FLIGHT, MC_C_COLLISION, MC_C_SCATTER, MC_C_SURFACE, MC_C_REFLECT,
-  MC_C_WW_SPLIT, MC_C_WW_KILL, MC_C_ITERATIONS, MC_NCOUNTERS
+  MC_C_WW_SPLIT, MC_C_WW_KILL, MC_C_ITERATIONS, MC_C_SCORES, MC_NCOUNTERS
 } mc_counter;
 
 /* ------------------------------------------------------------------------- entry points */

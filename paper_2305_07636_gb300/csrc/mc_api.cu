@@ -23,9 +23,9 @@
 
 namespace mcgb {
 template <typename R>
-cudaError_t launch_transport(const RunParams& P, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_transport(const RunParams& P, int grid, int block, size_t smem, cudaStream_t s, bool wide);
 template <typename R>
-cudaError_t transport_occupancy(int block, size_t smem, int* per_sm);
+cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide);
 cudaError_t launch_batch_stats(const void* tally, int fp64, uint64_t bins, int nb, int stripes,
                                uint64_t n_hist, void* out, cudaStream_t s);
 cudaError_t launch_philox(uint64_t seed, const uint4* ctr, uint4* out, uint64_t n, cudaStream_t s);
@@ -462,7 +462,7 @@ void mc_run_opts_default(mc_run_opts* o) {
   o->tally_mode = MC_TALLY_FIXED64;
   o->fixed_bits = 32;
   o->n_batches = 32;
-  o->aggregate_atomics = 1;
+  o->aggregate_atomics = -1;
 }
 
 int mc_problem_create(const mc_problem_desc* d, mc_problem** out) {
@@ -577,6 +577,8 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
     stripes = (uint32_t)std::max(1.0, std::min(16.0, std::floor(64.0 * 1048576.0 / copy_bytes)));
   }
   if (stripes > 256) return fail(MC_ERR_INVALID, "tally_stripes above 256");
+  if ((double)stripes * nb * (double)bins >= 4294967296.0)
+    return fail(MC_ERR_INVALID, "tally bins x batches x stripes must stay below 2^32");
   rc = p->d_tally.ensure((size_t)stripes * nb * bins * 8, p->dev);
   if (rc == MC_OK) rc = p->d_stats.ensure((size_t)3 * bins * 8, p->dev);
   if (rc != MC_OK) return rc;
@@ -602,7 +604,10 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   P.tally_stripes = stripes;
   P.stripe_stride = (uint64_t)nb * bins;
   P.tally_fp64 = o.tally_mode == MC_TALLY_FP64;
-  P.aggregate = o.aggregate_atomics;
+  // auto: aggregate only a small tally that could not be striped (many lanes per hot bin)
+  P.aggregate = o.aggregate_atomics >= 0
+                    ? o.aggregate_atomics
+                    : (stripes == 1 && (double)nb * (double)bins * 8.0 < 32.0 * 1048576.0 ? 1 : 0);
   P.fixed_scale = std::ldexp(1.0, o.fixed_bits);
   P.fixed_scale_f = (float)P.fixed_scale;
   P.history_mode = o.algorithm == MC_ALG_HISTORY;
@@ -643,9 +648,13 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   CK(cudaMemsetAsync(p->d_tally.ptr, 0, (size_t)stripes * nb * bins * 8, s));
   if (P.log) CK(cudaMemsetAsync(p->d_log.ptr, 0, log_cap * sizeof(mc_event), s));
   const int block = o.block_size ? o.block_size : 256;
-  const size_t smem = P.blob_bytes + (size_t)(block / 32) * 64 * 16 * lanes;  // tables + warp queues
+  // tables + per-warp flight queues (64 slots) + per-warp tally staging (128 x 12 B)
+  const size_t smem = P.blob_bytes + (size_t)(block / 32) * (64 * 16 * lanes + 128 * 12);
   int per_sm = 0;
-  CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm) : transport_occupancy<float>(block, smem, &per_sm));
+  // blocks_per_sm == 2 selects the 128-register build of the kernel, otherwise the 80-register one
+  const bool wide = o.blocks_per_sm == 2;
+  CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm, wide)
+          : transport_occupancy<float>(block, smem, &per_sm, wide));
   if (per_sm < 1) return fail(MC_ERR_CUDA, "transport kernel does not fit on an SM (block %d, smem %zu)", block, smem);
   if (o.blocks_per_sm > 0 && o.blocks_per_sm < per_sm) per_sm = o.blocks_per_sm;
   int sms = 0;
@@ -653,7 +662,7 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   const int grid = sms * per_sm;
   P.drain_threshold = o.drain_threshold ? o.drain_threshold : (uint64_t)2 * grid * block;
   CK(cudaEventRecord(p->ev[0], s));
-  CK(fp64 ? launch_transport<double>(P, grid, block, smem, s) : launch_transport<float>(P, grid, block, smem, s));
+  CK(fp64 ? launch_transport<double>(P, grid, block, smem, s, wide) : launch_transport<float>(P, grid, block, smem, s, wide));
   CK(cudaEventRecord(p->ev[1], s));
   CK(launch_batch_stats(P.tally, P.tally_fp64, bins, nb, (int)stripes, n_histories, p->d_stats.ptr, s));
   CK(cudaEventRecord(p->ev[2], s));

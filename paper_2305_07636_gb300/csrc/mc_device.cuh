@@ -534,81 +534,145 @@ __device__ __forceinline__ const double* time_edges<double>(const char* base, co
   return reinterpret_cast<const double*>(base + D.o_et);
 }
 
+// Per-warp staging buffer of tally scores in shared memory: slot index and the score's bits
+// (int64 fixed point or double).
+constexpr unsigned kStage = 128;
+struct Stage {
+  uint32_t* slot;
+  unsigned long long* val;
+};
+
+// Adds the n staged scores with all 32 lanes converged, 32 at a time, so that the match-based
+// warp aggregation sees whole warps.  Must be called by all lanes with a warp-uniform n.
+__device__ __forceinline__ void stage_flush(const RunParams& P, const Stage& S, unsigned n) {
+  __syncwarp();
+  const int lane = threadIdx.x & 31;
+  for (unsigned b = 0; b < n; b += 32) {
+    const unsigned i = b + lane;
+    if (i < n) {
+      const uint32_t slot = S.slot[i];
+      const unsigned long long v = S.val[i];
+      if (P.tally_fp64)
+        add_fp64(reinterpret_cast<double*>(P.tally) + slot, __longlong_as_double((long long)v), P.aggregate != 0);
+      else
+        add_fixed(reinterpret_cast<unsigned long long*>(P.tally) + slot, (long long)v, P.aggregate != 0);
+    }
+  }
+  __syncwarp();
+}
+
 // Track-length estimator over the segment of length l from the particle's position: walk the
 // mesh cells and time bins it crosses (3D DDA plus the time axis) and score w * piece length into
 // each bin it passes through.  Crossing distances are measured from the segment start, so rounding
 // does not accumulate along the walk.
+//
+// The walk runs in warp-uniform rounds: each round every lane still walking emits at most one
+// piece into the warp's staging buffer (ballot prefix), and the buffer is flushed with converged
+// lanes whenever it could overflow and at the end.  Lanes cross different numbers of bins, so
+// issuing the atomics inside each lane's own loop would leave most lanes idle at every atomic.
+// Called by all 32 lanes; `active` lanes have a segment.
 template <typename R>
-__device__ void score_segment(const Tab<R>& T, const RunParams& P, const Part<R>& p, R l,
-                              uint64_t batch_base) {
+__device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Part<R>& p, R l,
+                                   uint64_t batch_base, bool active, const Stage& S, unsigned& pieces) {
+  const unsigned lt = lanemask_lt();
+  const int lane = threadIdx.x & 31;
   const int g = (int)pk_g(p.pk);
-  const R v = T.v[g];
+  const R v = active ? T.v[g] : R(1);
   const char* base = reinterpret_cast<const char*>(T.h);
-  const Scorer<R> score(P, p.w);
-  const R t0 = p.time();
+  const R t0 = active ? p.time() : R(0);
+  const double w = active ? p.w : 0.0;
+  const float wscale = sizeof(R) == 4 ? weight_to_float(w) * P.fixed_scale_f : 0.0f;
+  unsigned n_st = 0;
   for (int ti = 0; ti < T.h->n_tally; ++ti) {
     const TallyDesc& D = T.h->tally[ti];
     const R* e[3] = {reinterpret_cast<const R*>(base + D.o_ex), reinterpret_cast<const R*>(base + D.o_ey),
                      reinterpret_cast<const R*>(base + D.o_ez)};
     const R* et = time_edges<R>(base, D);
     const int n[3] = {D.nx, D.ny, D.nz};
-    const R pos[3] = {p.x, p.y, p.z}, u[3] = {p.ux, p.uy, p.uz};
-    int idx[3], step[3];
-    R sn[3], inv[3];
-    bool never = false;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int i = bin_search(e[d], n[d], pos[d]);
-      idx[d] = i;
-      inv[d] = R(1) / u[d];
-      if (u[d] > R(0)) {
-        step[d] = 1;
-        if (i >= n[d]) never = true;
-        sn[d] = (i >= n[d]) ? rinf<R>() : (e[d][i + 1] - pos[d]) * inv[d];
-      } else if (u[d] < R(0)) {
-        step[d] = -1;
-        if (i < 0) never = true;
-        sn[d] = (i < 0) ? rinf<R>() : (e[d][i] - pos[d]) * inv[d];
-      } else {
-        step[d] = 0;
-        sn[d] = rinf<R>();
-        if (i < 0 || i >= n[d]) never = true;
-      }
-    }
-    if (never) continue;
-    int it = bin_search(et, D.nt, t0);
-    if (it >= D.nt) continue;
-    R stn = (et[it + 1] - t0) * v;
-    const uint64_t gbase = batch_base + (uint64_t)D.bin_offset + (uint64_t)g * D.nt;
-    const int gstride = T.G * D.nt;
-    R s = R(0);
-    while (s < l) {
-      R nxt = fmin(fmin(sn[0], sn[1]), fmin(sn[2], stn));
-      nxt = fmin(nxt, l);
-      if (nxt > s && idx[0] >= 0 && idx[0] < n[0] && idx[1] >= 0 && idx[1] < n[1] && idx[2] >= 0 &&
-          idx[2] < n[2] && it >= 0) {
-        const int cell = (idx[2] * n[1] + idx[1]) * n[0] + idx[0];
-        score(gbase + (uint64_t)cell * gstride + it, nxt - s);
-      }
-      if (nxt >= l) break;
-      bool out = false;
+    R pos[3], u[3], sn[3], inv[3], stn = R(0), s = R(0);
+    int idx[3], step[3], it = 0;
+    bool live = active;
+    if (live) {
+      pos[0] = p.x; pos[1] = p.y; pos[2] = p.z;
+      u[0] = p.ux; u[1] = p.uy; u[2] = p.uz;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        if (sn[d] <= nxt) {
-          idx[d] += step[d];
-          if (idx[d] < 0 || idx[d] >= n[d]) out = true;  // left the mesh along this axis
-          else sn[d] = (e[d][idx[d] + (step[d] > 0 ? 1 : 0)] - pos[d]) * inv[d];
+        const int i = bin_search(e[d], n[d], pos[d]);
+        idx[d] = i;
+        inv[d] = R(1) / u[d];
+        if (u[d] > R(0)) {
+          step[d] = 1;
+          if (i >= n[d]) live = false;
+          sn[d] = (i >= n[d]) ? rinf<R>() : (e[d][i + 1] - pos[d]) * inv[d];
+        } else if (u[d] < R(0)) {
+          step[d] = -1;
+          if (i < 0) live = false;
+          sn[d] = (i < 0) ? rinf<R>() : (e[d][i] - pos[d]) * inv[d];
+        } else {
+          step[d] = 0;
+          sn[d] = rinf<R>();
+          if (i < 0 || i >= n[d]) live = false;
         }
       }
-      if (stn <= nxt) {
-        ++it;
-        if (it >= D.nt) out = true;
-        else stn = (et[it + 1] - t0) * v;
+      it = bin_search(et, D.nt, t0);
+      if (it >= D.nt) live = false;
+      else stn = (et[it + 1] - t0) * v;
+    }
+    const uint64_t gbase = batch_base + (uint64_t)D.bin_offset + (uint64_t)g * D.nt;
+    const int gstride = T.G * D.nt;
+    while (__any_sync(0xFFFFFFFFu, live)) {
+      bool emit = false;
+      uint32_t slot = 0;
+      unsigned long long val = 0;
+      if (live) {
+        R nxt = fmin(fmin(sn[0], sn[1]), fmin(sn[2], stn));
+        nxt = fmin(nxt, l);
+        if (nxt > s && idx[0] >= 0 && idx[0] < n[0] && idx[1] >= 0 && idx[1] < n[1] && idx[2] >= 0 &&
+            idx[2] < n[2] && it >= 0) {
+          const int cell = (idx[2] * n[1] + idx[1]) * n[0] + idx[0];
+          const R len = nxt - s;
+          emit = true;
+          slot = (uint32_t)(gbase + (uint64_t)cell * gstride + it);
+          if (P.tally_fp64)
+            val = (unsigned long long)__double_as_longlong(w * (double)len);
+          else
+            val = (unsigned long long)(sizeof(R) == 4 ? float_to_fixed(wscale * (float)len)
+                                                      : __double2ll_rn(w * (double)len * P.fixed_scale));
+        }
+        if (nxt >= l) {
+          live = false;
+        } else {
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            if (sn[d] <= nxt) {
+              idx[d] += step[d];
+              if (idx[d] < 0 || idx[d] >= n[d]) live = false;  // left the mesh along this axis
+              else sn[d] = (e[d][idx[d] + (step[d] > 0 ? 1 : 0)] - pos[d]) * inv[d];
+            }
+          }
+          if (stn <= nxt) {
+            ++it;
+            if (it >= D.nt) live = false;
+            else stn = (et[it + 1] - t0) * v;
+          }
+          s = nxt;
+        }
       }
-      if (out) break;
-      s = nxt;
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, emit);
+      if (emit) {
+        const unsigned i = n_st + __popc(m & lt);
+        S.slot[i] = slot;
+        S.val[i] = val;
+      }
+      n_st += __popc(m);
+      pieces += __popc(m);  // warp-uniform count, added to the CTA counters at kernel end
+      if (n_st > kStage - 32) {
+        stage_flush(P, S, n_st);
+        n_st = 0;
+      }
     }
   }
+  stage_flush(P, S, n_st);
 }
 
 // ------------------------------------------------------------------------------------------ sampling

@@ -251,18 +251,17 @@ __device__ bool do_surface(const RunParams& P, const Tab<R>& T, Part<R>& p, uint
   return weight_window(P, T, p, Bout, bcount, bc);
 }
 
-// Flight k: distance to collision, surface and census; move; score; set the pending event.
-// Returns false if the particle ends here (census or lost).
+// Flight k, first half: distance to collision, to the nearest surface and to census; chooses the
+// event and the flight length l.  Returns false if no event is reachable (the particle is lost).
 template <typename R>
-__device__ bool do_flight(const RunParams& P, const Tab<R>& T, Part<R>& p, BlockCounters* bc,
-                          uint64_t batch_base) {
+__device__ bool flight_plan(const RunParams& P, const Tab<R>& T, Part<R>& p, BlockCounters* bc, R& l,
+                            uint32_t& pend, Hit& hit) {
   const int G = T.G;
   const int g = (int)pk_g(p.pk);
   const int m = material_of(T, p.pk, p.elem);
   const R St = T.st[m * G + g];
   const R u = draw<R>(P.seed, p.tlo, p.thi, p.k, 0).a;
   const R dc = St > R(0) ? -rlog(u) / St : rinf<R>();
-  Hit hit;
   const R ds = boundary_distance(T, p, hit);
   R dt = rinf<R>();
   if (T.h->has_census) {
@@ -271,8 +270,6 @@ __device__ bool do_flight(const RunParams& P, const Tab<R>& T, Part<R>& p, Block
     dt = d > R(0) ? d : R(0);
   }
   bump(bc, MC_C_FLIGHT);
-  uint32_t pend;
-  R l;
   if (dc < ds && dc < dt) {
     pend = PEND_COLL;
     l = dc;
@@ -280,7 +277,7 @@ __device__ bool do_flight(const RunParams& P, const Tab<R>& T, Part<R>& p, Block
     pend = PEND_SURF;
     l = ds;
   } else {
-    pend = 0;
+    pend = PEND_NONE;  // census
     l = dt;
   }
   if (!(l < rinf<R>())) {
@@ -289,12 +286,20 @@ __device__ bool do_flight(const RunParams& P, const Tab<R>& T, Part<R>& p, Block
     set_status(P, MC_ERR_LOST);
     return false;
   }
-  score_segment(T, P, p, l, batch_base);
+  return true;
+}
+
+// Flight k, second half (after the segment was scored): move, advance the clock, set the pending
+// event.  Returns false if the particle ends at the census.
+template <typename R>
+__device__ bool flight_finish(const RunParams& P, const Tab<R>& T, Part<R>& p, BlockCounters* bc, R l,
+                              uint32_t pend, const Hit& hit) {
+  const int g = (int)pk_g(p.pk);
   p.x += l * p.ux;
   p.y += l * p.uy;
   p.z += l * p.uz;
   p.advance(l, T.v[g], T.inv_v[g]);
-  if (pend == 0) {
+  if (pend == PEND_NONE) {
     bump(bc, MC_C_CENSUS);
     log_event(P, T, p, 2, 0, 0);
     return false;
@@ -403,8 +408,8 @@ constexpr unsigned kClaim = 128;
 constexpr unsigned kWarpQ = 64;  // per-warp flight queue slots
 
 // dynamic shared memory: [table blob][per-warp flight queues: warps x Lanes<R>::N x kWarpQ]
-template <typename R>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_transport(RunParams P) {
+template <typename R, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
   extern __shared__ __align__(16) char smem[];
   __shared__ BlockCounters bc;
   __shared__ int s_status;
@@ -414,9 +419,15 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_transport(RunPa
   __syncthreads();
   const Tab<R> T(smem);
   const int lane = threadIdx.x & 31;
-  uint4* wq = reinterpret_cast<uint4*>(smem + P.blob_bytes) + (threadIdx.x >> 5) * (Lanes<R>::N * kWarpQ);
+  const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  uint4* wq = reinterpret_cast<uint4*>(smem + P.blob_bytes) + warp * (Lanes<R>::N * kWarpQ);
+  // per-warp tally staging buffers follow the queues: values (8 B) then slots (4 B)
+  char* stage_base = smem + P.blob_bytes + (size_t)nwarp * Lanes<R>::N * kWarpQ * 16;
+  const Stage stage{reinterpret_cast<uint32_t*>(stage_base + (size_t)nwarp * kStage * 8) + warp * kStage,
+                    reinterpret_cast<unsigned long long*>(stage_base) + warp * kStage};
   Ctl* ctl = P.ctl;
   const unsigned lt = lanemask_lt();
+  unsigned scored = 0;  // tally updates issued by this warp
   const uint64_t bins = (uint64_t)T.h->total_bins;
   // small tallies are striped over several copies so that hot bins are not one L2 address
   const uint64_t stripe_off = (uint64_t)(blockIdx.x % P.tally_stripes) * P.stripe_stride;
@@ -526,8 +537,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_transport(RunPa
       __syncwarp();
       qn -= nfly;
       bool out = false, again = false;
-      if (have) {
-        bool alive = do_flight(P, T, p, &bc, stripe_off + (uint64_t)(p.elem >> 16) * bins);
+      R l = R(0);
+      uint32_t pend = PEND_NONE;
+      Hit hit;
+      const bool flies = have && flight_plan(P, T, p, &bc, l, pend, hit);
+      score_segment_warp(T, P, p, l, stripe_off + (uint64_t)(p.elem >> 16) * bins, flies, stage, scored);
+      if (flies) {
+        bool alive = flight_finish(P, T, p, &bc, l, pend, hit);
         if (alive && p.k + 1 >= P.max_iter) {
           // a particle that never ends (e.g. a reflective void without census) cannot keep the
           // warp busy forever in history-style iterations: the same budget as the iteration
@@ -574,6 +590,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_transport(RunPa
     }
     grid_barrier(P, ctl, P.spin_limit);
   }
+  if ((threadIdx.x & 31) == 0 && scored) atomicAdd(&bc.c[MC_C_SCORES], scored);
   __syncthreads();
   if (threadIdx.x < MC_NCOUNTERS && bc.c[threadIdx.x])
     atomicAdd(&ctl->counters[threadIdx.x], (unsigned long long)bc.c[threadIdx.x]);
@@ -635,26 +652,34 @@ __global__ void k_philox(uint64_t seed, const uint4* ctr, uint4* out, uint64_t n
 }
 
 // ------------------------------------------------------------------------------------------ launchers
+// Two register budgets of the same kernel: 3 CTAs of 256 threads per SM (80 registers) or 2 CTAs
+// (128 registers, no spills); `wide` selects the second.
 template <typename R>
-cudaError_t launch_transport(const RunParams& P, int grid, int block, size_t smem, cudaStream_t s) {
-  void* args[] = {const_cast<RunParams*>(&P)};
-  return cudaLaunchCooperativeKernel((const void*)k_transport<R>, grid, block, args, smem, s);
+static const void* transport_fn(bool wide) {
+  if (sizeof(R) == 8) return (const void*)k_transport<R, 2>;
+  return wide ? (const void*)k_transport<R, 2> : (const void*)k_transport<R, 3>;
 }
 
 template <typename R>
-cudaError_t transport_occupancy(int block, size_t smem, int* per_sm) {
+cudaError_t launch_transport(const RunParams& P, int grid, int block, size_t smem, cudaStream_t s, bool wide) {
+  void* args[] = {const_cast<RunParams*>(&P)};
+  return cudaLaunchCooperativeKernel(transport_fn<R>(wide), grid, block, args, smem, s);
+}
+
+template <typename R>
+cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide) {
+  const void* f = transport_fn<R>(wide);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute((const void*)k_transport<R>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, (const void*)k_transport<R>, block, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, f, block, smem);
 }
 
-template cudaError_t launch_transport<float>(const RunParams&, int, int, size_t, cudaStream_t);
-template cudaError_t launch_transport<double>(const RunParams&, int, int, size_t, cudaStream_t);
-template cudaError_t transport_occupancy<float>(int, size_t, int*);
-template cudaError_t transport_occupancy<double>(int, size_t, int*);
+template cudaError_t launch_transport<float>(const RunParams&, int, int, size_t, cudaStream_t, bool);
+template cudaError_t launch_transport<double>(const RunParams&, int, int, size_t, cudaStream_t, bool);
+template cudaError_t transport_occupancy<float>(int, size_t, int*, bool);
+template cudaError_t transport_occupancy<double>(int, size_t, int*, bool);
 
 cudaError_t launch_batch_stats(const void* tally, int fp64, uint64_t bins, int nb, int stripes,
                                uint64_t n_hist, void* out, cudaStream_t s) {

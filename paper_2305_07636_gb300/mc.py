@@ -27,7 +27,7 @@ MC_FP32, MC_FP64 = 0, 1
 MC_TALLY_FIXED64, MC_TALLY_FP64 = 0, 1
 COUNTER_NAMES = ["source", "secondary", "capture", "production", "leak", "census", "lost",
                  "flight", "collision", "scatter", "surface", "reflect", "ww_split", "ww_kill",
-                 "iterations"]
+                 "iterations", "scores"]
 NCOUNTERS = len(COUNTER_NAMES)
 KIND = {"PX": 0, "PY": 1, "PZ": 2, "CZ": 3}
 BC = {"interior": 0, "vacuum": 1, "reflect": 2}
