@@ -1,0 +1,78 @@
+"""The C-ABI library loads without a GPU, exports every entry point that include/mc.h declares,
+and rejects invalid problem descriptions on the host before touching CUDA.  No compute calls."""
+import ctypes as C
+import math
+import os
+import re
+
+import pytest
+
+from paper_2305_07636_gb300 import mc
+from paper_2305_07636_gb300 import problems as P
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "mc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(mc_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for core in ("mc_problem_create", "mc_run", "mc_tally_get", "mc_problem_destroy",
+                 "mc_wait", "mc_counters_get", "mc_event_log", "mc_philox"):
+        assert core in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = C.CDLL(mc._build.build())
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    assert set(declared_functions()) <= set(mc.SIGNATURES)
+
+
+def test_run_opts_defaults():
+    o = mc.run_opts()
+    assert (o.precision, o.tally_mode, o.fixed_bits, o.n_batches) == (0, 0, 32, 32)
+    assert o.aggregate_atomics == -1 and o.algorithm == 0
+
+
+def _bad(mutator):
+    prob = P.config1()
+    mutator(prob)
+    with pytest.raises(mc.McError) as e:
+        mc.problem_create(prob)
+    assert e.value.code == mc.MC_ERR_INVALID
+    return str(e.value)
+
+
+@pytest.mark.parametrize("case", [
+    lambda p: p["materials"][0].__setitem__("sigma_s", [[1.5]]),          # channels exceed sigma_t
+    lambda p: p["materials"][0].__setitem__("sigma_t", [-1.0]),
+    lambda p: p["materials"][0].__setitem__("nu", [100.0]),
+    lambda p: p.__setitem__("speed", [0.0]),
+    lambda p: p["surfaces"][0].__setitem__("kind", "CZ") or p["surfaces"][0].__setitem__("coef", [0, 0, 1]) or p["surfaces"][0].__setitem__("bc", "reflect"),
+    lambda p: p["cells"][0].__setitem__("halfspaces", [(7, 1)]),
+    lambda p: p["cells"][0].__setitem__("material", -1),                    # lattice fill, no lattice
+    lambda p: p["source"].__setitem__("group_pdf", [0.0]),
+    lambda p: p["tallies"][0].__setitem__("x", [0.0, 2.0, 1.0]),           # edges not increasing
+    lambda p: p.__setitem__("t_census", 0.0),
+])
+def test_invalid_descriptions_are_rejected_on_the_host(case):
+    assert _bad(case)
+
+
+def test_no_gpu_means_a_loud_error_not_a_fallback():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(mc.McError) as e:
+        mc.problem_create(P.config1())
+    assert e.value.code in (mc.MC_ERR_CUDA, mc.MC_ERR_OOM)
+    assert math.isfinite(len(str(e.value)))
