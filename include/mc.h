@@ -246,6 +246,34 @@ void mc_problem_destroy(mc_problem* p);
 /* Thread-local message describing the last failure ("" if none). */
 const char* mc_last_error(void);
 
+/* ------------------------------------------------------------------------- allocation-free run */
+/* Bytes of the library's static device scratch used by mc_run_static. */
+#define MC_STATIC_SCRATCH_BYTES (32u << 20)
+
+/* mc_run for callers that cannot allocate device memory: code that runs while a CUDA graph is
+ * being captured (cudaMalloc is not allowed then), applications that hand all device memory to
+ * their own pool or allocator up front, and allocator or memory-pressure callbacks that must not
+ * re-enter the allocator.  This call takes no memory from cudaMalloc, cudaFree or any allocating
+ * library: its control block, particle banks (32768 particles each), batch tallies and statistics
+ * live in one MC_STATIC_SCRATCH_BYTES array that the library declares at file scope, reserved on
+ * every GPU that loads the library until the process exits.  The paper has no counterpart; it is
+ * an interface for such callers only.
+ *   p            problem from mc_problem_create (created beforehand, outside the restricted code)
+ *   n_histories, seed, opts   as for mc_run; opts may not ask for an event log, more than 32768
+ *                particles in flight, or tally_stripes > 1 (MC_ERR_INVALID)
+ *   mean, std_err  DEVICE arrays of at least the problem's total bin count (every mesh tally's
+ *                bins in tally order, then the leakage bins), caller-allocated; they receive the
+ *                per-source-particle mean and standard error, or NaN in every entry if the run
+ *                failed on the device (bank overflow, watchdog, lost particle)
+ * The tallies must fit the scratch: (n_batches + 3) x bins x 8 bytes plus the banks; larger
+ * problems are rejected with MC_ERR_INVALID and a message giving the bytes needed.  Asynchronous on
+ * `stream`.  The first call on a device looks up the array's device address (a runtime query, no
+ * allocation) with that device current; make that first call before any stream capture.  Every
+ * call shares the one array, which keeps the last call's contents (the call clears what must start
+ * at zero): calls that overlap on the GPU, e.g. on two streams, race and corrupt each other. */
+int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts* opts,
+                  double* mean, double* std_err, void* stream);
+
 /* Philox4x32-10 (Salmon et al., SC'11) on the device: out[i] = Philox(key = seed, ctr = ctr[i])
  * for n counters; ctr and out are DEVICE arrays of 4*n uint32 (counter words c0..c3).  This is
  * the generator every random draw of the walk uses, exposed for verification. */

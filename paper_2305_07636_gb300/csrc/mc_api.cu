@@ -879,3 +879,179 @@ int mc_philox(uint64_t seed, const uint32_t* ctr, uint32_t* out, uint64_t n, voi
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------ static scratch
+// Run entry point for callers that cannot allocate device memory (see mc_run_static in mc.h).
+// All of its scratch lives in this file-scope array, which the CUDA runtime reserves on every
+// device that loads this module and keeps until the process exits.
+static __device__ __align__(256) unsigned char g_static_scratch[MC_STATIC_SCRATCH_BYTES];
+
+namespace {
+constexpr uint64_t kStaticBank = 32768;  // particles in flight per bank
+std::mutex g_static_mu;
+void* g_static_ptr[64] = {nullptr};
+
+// Device address of g_static_scratch on `dev` (current): looked up once per device.  The host-side
+// name of the array is only a stand-in, never a device address.
+int static_scratch(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= 64) return fail(MC_ERR_STATE, "device %d outside the supported range", dev);
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+    g_static_ptr[dev] = ptr;
+  }
+  *out = (unsigned char*)g_static_ptr[dev];
+  return MC_OK;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Per-bin mean and standard error from the batch statistics, or NaN everywhere if the run failed.
+__global__ void k_static_finalize(const Ctl* ctl, const void* stats, int fp64, uint64_t bins, double n_hist,
+                                  double nb, double inv_scale, double* mean, double* std_err) {
+  const bool bad = ctl->status != 0;
+  const double nan = __longlong_as_double(0x7FF8000000000000ll);
+  const double nbar = n_hist / nb;
+  for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < bins;
+       b += (uint64_t)gridDim.x * blockDim.x) {
+    double m, var;
+    if (fp64) {
+      const double* st = reinterpret_cast<const double*>(stats);
+      m = st[b] / n_hist;
+      var = (st[2 * bins + b] - st[bins + b] * st[bins + b] / nb) / (nb * (nb - 1.0));
+    } else {
+      const long long* sum = reinterpret_cast<const long long*>(stats);
+      const unsigned long long* lo = reinterpret_cast<const unsigned long long*>(sum + bins);
+      const unsigned long long* hi = lo + bins;
+      const double s1 = (double)sum[b] * inv_scale / nbar;
+      const double sq = ((double)hi[b] * 18446744073709551616.0 + (double)lo[b]) * inv_scale * inv_scale;
+      m = (double)sum[b] * inv_scale / n_hist;
+      var = (sq / (nbar * nbar) - s1 * s1 / nb) / (nb * (nb - 1.0));
+    }
+    mean[b] = bad ? nan : m;
+    std_err[b] = bad ? nan : (var > 0.0 ? sqrt(var) : 0.0);
+  }
+}
+}  // namespace
+
+extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts* opts,
+                             double* mean, double* std_err, void* stream) {
+  g_err.clear();
+  if (!p) return fail(MC_ERR_INVALID, "problem is NULL");
+  if (!mean || !std_err) return fail(MC_ERR_INVALID, "mean and std_err must be device arrays");
+  mc_run_opts o;
+  if (opts) o = *opts;
+  else mc_run_opts_default(&o);
+  if (o.precision != MC_FP32 && o.precision != MC_FP64) return fail(MC_ERR_INVALID, "precision");
+  if (o.tally_mode != MC_TALLY_FIXED64 && o.tally_mode != MC_TALLY_FP64) return fail(MC_ERR_INVALID, "tally_mode");
+  if (o.fixed_bits < 0 || o.fixed_bits > 48) return fail(MC_ERR_INVALID, "fixed_bits outside [0,48]");
+  if (o.n_batches < 2 || o.n_batches > 4096) return fail(MC_ERR_INVALID, "n_batches outside [2,4096]");
+  if (n_histories < (uint64_t)o.n_batches) return fail(MC_ERR_INVALID, "need at least n_batches histories");
+  if (n_histories >= (1ull << 32) || o.first_history + n_histories > (1ull << 32))
+    return fail(MC_ERR_INVALID, "history indices must stay below 2^32");
+  if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 256 || o.block_size % 32))
+    return fail(MC_ERR_INVALID, "block_size must be a multiple of 32 in [32,256]");
+  if (o.algorithm != MC_ALG_EVENT && o.algorithm != MC_ALG_HISTORY) return fail(MC_ERR_INVALID, "algorithm");
+  if (o.log_count > 0) return fail(MC_ERR_INVALID, "mc_run_static keeps no event log");
+  if (o.ww_enable && !p->ww_set) return fail(MC_ERR_STATE, "weight windows enabled but no table set");
+  if (o.bank_capacity > kStaticBank)
+    return fail(MC_ERR_INVALID, "bank_capacity %llu exceeds the static limit of %llu particles",
+                (unsigned long long)o.bank_capacity, (unsigned long long)kStaticBank);
+  if (o.tally_stripes > 1) return fail(MC_ERR_INVALID, "mc_run_static keeps a single tally copy");
+  int dev;
+  int rc = current_device(&dev);
+  if (rc != MC_OK) return rc;
+  if (dev != p->dev) return fail(MC_ERR_STATE, "problem was created on device %d, current is %d", p->dev, dev);
+  const int fp64 = o.precision == MC_FP64;
+  const int lanes = fp64 ? kLanesFP64 : kLanesFP32;
+  const uint64_t cap = kStaticBank;
+  const int nb = o.n_batches;
+  const uint64_t bins = (uint64_t)p->total_bins;
+  // layout: [control block][sticky word][4 particle banks][batch tallies][batch statistics]
+  const size_t off_sticky = align256(sizeof(Ctl));
+  const size_t off_banks = off_sticky + 256;
+  const size_t bank_bytes = (size_t)cap * 16 * lanes;
+  const size_t off_tally = align256(off_banks + 4 * bank_bytes);
+  const size_t tally_bytes = (size_t)nb * bins * 8;
+  const size_t off_stats = align256(off_tally + tally_bytes);
+  const size_t need = off_stats + (size_t)3 * bins * 8;
+  if (need > (size_t)MC_STATIC_SCRATCH_BYTES)
+    return fail(MC_ERR_INVALID,
+                "%d batches x %llu bins need %zu bytes of scratch; the static scratch holds %zu (use mc_run)", nb,
+                (unsigned long long)bins, need, (size_t)MC_STATIC_SCRATCH_BYTES);
+  unsigned char* base = nullptr;
+  rc = static_scratch(dev, &base);
+  if (rc != MC_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  RunParams P;
+  std::memset(&P, 0, sizeof(P));
+  for (int side = 0; side < 2; ++side)
+    for (int l = 0; l < lanes; ++l) {
+      P.S[side][l] = (uint4*)(base + off_banks + (size_t)side * bank_bytes + (size_t)l * cap * 16);
+      P.B[side][l] = (uint4*)(base + off_banks + (size_t)(2 + side) * bank_bytes + (size_t)l * cap * 16);
+    }
+  P.cap_s = cap;
+  P.cap_b = cap;
+  P.ctl = (Ctl*)base;
+  P.sticky = (int*)(base + off_sticky);
+  P.tally = base + off_tally;
+  P.tally_stripes = 1;
+  P.stripe_stride = (uint64_t)nb * bins;
+  P.tally_fp64 = o.tally_mode == MC_TALLY_FP64;
+  P.aggregate = o.aggregate_atomics >= 0 ? o.aggregate_atomics : 1;
+  P.fixed_scale = std::ldexp(1.0, o.fixed_bits);
+  P.fixed_scale_f = (float)P.fixed_scale;
+  P.history_mode = o.algorithm == MC_ALG_HISTORY;
+  P.trace = nullptr;
+  P.trace_cap = 0;
+  P.n_hist = n_histories;
+  P.hist_per_batch = (n_histories + nb - 1) / nb;
+  P.h_first = o.first_history;
+  {
+    const double mg = std::floor(4294967296.0 * (double)nb / (double)n_histories);
+    P.batch_magic = mg >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)mg;
+  }
+  P.n_batches = nb;
+  P.blob_bytes = (int)p->blob[fp64].size();
+  P.blob = (const uint4*)p->d_blob[fp64].ptr;
+  P.seed = seed;
+  P.max_iter = o.max_iterations ? o.max_iterations : (1ull << 20);
+  P.spin_limit = 1ull << 22;
+  if (o.ww_enable) {
+    const double* wb = (const double*)p->d_ww.ptr;
+    P.ww_on = 1;
+    P.ww_nx = p->ww_n[0];
+    P.ww_ny = p->ww_n[1];
+    P.ww_nz = p->ww_n[2];
+    P.ww_edges = wb;
+    P.ww_center = wb + (p->ww_n[0] + 1) + (p->ww_n[1] + 1) + (p->ww_n[2] + 1);
+    P.ww_upper = 2.0;
+    P.ww_lower = 0.5;
+    P.ww_split_max = 10;
+  }
+  // the array keeps the previous call's contents: clear what must start at zero
+  CK(cudaMemsetAsync(base, 0, off_banks, s));
+  CK(cudaMemsetAsync(base + off_tally, 0, tally_bytes, s));
+  const int block = o.block_size ? o.block_size : 256;
+  const size_t smem = P.blob_bytes + (size_t)(block / 32) * (64 * 16 * lanes + 128 * 12);
+  const bool wide = o.blocks_per_sm == 2;
+  int per_sm = 0;
+  CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm, wide)
+          : transport_occupancy<float>(block, smem, &per_sm, wide));
+  if (per_sm < 1) return fail(MC_ERR_CUDA, "transport kernel does not fit on an SM (block %d, smem %zu)", block, smem);
+  if (o.blocks_per_sm > 0 && o.blocks_per_sm < per_sm) per_sm = o.blocks_per_sm;
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = sms * per_sm;
+  P.drain_threshold = o.drain_threshold ? o.drain_threshold : (uint64_t)2 * grid * block;
+  CK(fp64 ? launch_transport<double>(P, grid, block, smem, s, wide)
+          : launch_transport<float>(P, grid, block, smem, s, wide));
+  CK(launch_batch_stats(P.tally, P.tally_fp64, bins, nb, 1, n_histories, base + off_stats, s));
+  unsigned g = (unsigned)std::min<uint64_t>((bins + 255) / 256, 1024);
+  k_static_finalize<<<g ? g : 1, 256, 0, s>>>((const Ctl*)base, base + off_stats, P.tally_fp64, bins,
+                                              (double)n_histories, (double)nb, 1.0 / P.fixed_scale, mean, std_err);
+  CK(cudaGetLastError());
+  return MC_OK;
+}

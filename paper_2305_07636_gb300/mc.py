@@ -128,6 +128,8 @@ SIGNATURES = {
     "mc_problem_destroy": (None, [C.c_void_p]),
     "mc_last_error": (C.c_char_p, []),
     "mc_philox": (C.c_int, [C.c_uint64, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]),
+    "mc_run_static": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.POINTER(mc_run_opts),
+                                C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -318,6 +320,15 @@ def event_log(h: int, cap: int) -> np.ndarray:
     assert C.sizeof(mc_event) == EVENT_DTYPE.itemsize
     ev = np.frombuffer(buf, dtype=EVENT_DTYPE, count=max(1, cap))[: n.value].copy()
     return ev[np.lexsort((ev["k"], ev["tag"]))]
+
+
+def run_static(h: int, n_histories: int, seed: int, opts: mc_run_opts | None, mean_dev_ptr: int,
+               err_dev_ptr: int, stream=None):
+    """mc_run_static: the run for callers that cannot allocate device memory; writes the
+    per-bin mean and standard error into the given device arrays (NaN if the run failed)."""
+    check(lib().mc_run_static(C.c_void_p(h), int(n_histories), int(seed) & (2**64 - 1),
+                              C.byref(opts) if opts is not None else None, C.c_void_p(mean_dev_ptr),
+                              C.c_void_p(err_dev_ptr), C.c_void_p(_stream_handle(stream))))
 
 
 def run_timing(h: int):
