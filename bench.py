@@ -238,6 +238,10 @@ def main():
     peak, peak_kind = peaks()
     algo_bytes = c["flight"] * BYTES_PER_FLIGHT
     achieved = algo_bytes / (tr_ms / 1000.0) / 1e9
+    # tally scoring against the L2 atomic roofline, measured live on the tally's footprint
+    tally_elems = sum(int(np.prod(mc.tally_shape(p.h, t))) for t in range(len(prob["tallies"]) + 1))
+    atom_peak = mc.atomic_peak(max(1, tally_elems * opts.n_batches * 16))
+    atom_rate = c["scores"] / (tr_ms / 1000.0)
 
     # end to end through the public API with host buffers
     e2e_times = []
@@ -269,7 +273,11 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "k_transport<float>", "kernel_ms": tr_ms,
-                     "algorithmic_bytes": algo_bytes, "peak_kind": peak_kind},
+                     "algorithmic_bytes": algo_bytes, "peak_kind": peak_kind,
+                     "l2_atomic": {"achieved": atom_rate / 1e9, "peak": atom_peak / 1e9,
+                                   "unit": "G atomics/s", "frac": atom_rate / atom_peak,
+                                   "scores_per_flight": c["scores"] / c["flight"],
+                                   "peak_kind": "measured live (mc_atomic_peak, random 64-bit adds)"}},
         "counters": {k: c[k] for k in ("flight", "collision", "surface", "census", "iterations")},
         "algorithm": args.algorithm,
         "trace": {"iterations": int(len(tr_t)), "history_style_iterations": int(tr_drain.sum()),

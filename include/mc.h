@@ -274,6 +274,12 @@ const char* mc_last_error(void);
 int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts* opts,
                   double* mean, double* std_err, void* stream);
 
+/* Measures the device's L2 atomic throughput for the scoring access pattern: 64-bit atomic adds
+ * to pseudo-random slots of a zeroed array of `span` elements (1 .. 2^27), issued by 8 CTAs of
+ * 256 threads per SM; *atomics_per_s receives adds per second.  Allocates and frees its array.
+ * Used as the atomic roofline of track-length scoring. */
+int mc_atomic_peak(uint64_t span, double* atomics_per_s);
+
 /* Philox4x32-10 (Salmon et al., SC'11) on the device: out[i] = Philox(key = seed, ctr = ctr[i])
  * for n counters; ctr and out are DEVICE arrays of 4*n uint32 (counter words c0..c3).  This is
  * the generator every random draw of the walk uses, exposed for verification. */

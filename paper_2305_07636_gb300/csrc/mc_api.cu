@@ -29,6 +29,8 @@ cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide);
 cudaError_t launch_batch_stats(const void* tally, int fp64, uint64_t bins, int nb, int stripes,
                                uint64_t n_hist, void* out, cudaStream_t s);
 cudaError_t launch_philox(uint64_t seed, const uint4* ctr, uint4* out, uint64_t n, cudaStream_t s);
+cudaError_t launch_atomic_probe(unsigned long long* a, unsigned long long span, int grid, int iters, unsigned salt,
+                                cudaStream_t s);
 }  // namespace mcgb
 
 using namespace mcgb;
@@ -866,6 +868,37 @@ int mc_run_timing(mc_problem* p, double* transport_ms, double* stats_ms) {
   CK(cudaEventElapsedTime(&b, p->ev[1], p->ev[2]));
   if (transport_ms) *transport_ms = a;
   if (stats_ms) *stats_ms = b;
+  return MC_OK;
+}
+
+int mc_atomic_peak(uint64_t span, double* atomics_per_s) {
+  g_err.clear();
+  if (!atomics_per_s || span < 1 || span > (1ull << 27)) return fail(MC_ERR_INVALID, "span outside [1, 2^27]");
+  int dev, sms = 0;
+  int rc = current_device(&dev);
+  if (rc != MC_OK) return rc;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  DevBuf buf;
+  rc = buf.ensure(span * 8, dev);
+  if (rc != MC_OK) return rc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMemset(buf.ptr, 0, span * 8);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int grid = sms * 8, iters = 256;
+  if (e == cudaSuccess) e = launch_atomic_probe((unsigned long long*)buf.ptr, span, grid, iters, 1u, 0);  // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(e0, 0);
+  for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+    e = launch_atomic_probe((unsigned long long*)buf.ptr, span, grid, iters, 2u + r, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  buf.release();
+  if (e != cudaSuccess) return cuda_fail(e, "atomic probe");
+  *atomics_per_s = 3.0 * grid * 256.0 * iters / (ms * 1e-3);
   return MC_OK;
 }
 

@@ -645,6 +645,22 @@ __global__ void k_batch_stats_fp64(const double* tally, uint64_t bins, int nb, i
   }
 }
 
+// L2 atomic throughput probe: 64-bit adds to pseudo-random slots of an array of `span` elements
+// (the access pattern of tally scoring), `iters` per thread.
+__global__ void k_atomic_probe(unsigned long long* a, unsigned long long span, int iters, unsigned salt) {
+  unsigned long long x = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) * 2654435761ull + salt;
+  for (int i = 0; i < iters; ++i) {
+    x = x * 6364136223846793005ull + 1442695040888963407ull;
+    atomicAdd(a + ((x >> 20) % span), 1ull);
+  }
+}
+
+cudaError_t launch_atomic_probe(unsigned long long* a, unsigned long long span, int grid, int iters, unsigned salt,
+                                cudaStream_t s) {
+  k_atomic_probe<<<grid, 256, 0, s>>>(a, span, iters, salt);
+  return cudaGetLastError();
+}
+
 __global__ void k_philox(uint64_t seed, const uint4* ctr, uint4* out, uint64_t n) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x)

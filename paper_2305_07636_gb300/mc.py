@@ -128,6 +128,7 @@ SIGNATURES = {
     "mc_problem_destroy": (None, [C.c_void_p]),
     "mc_last_error": (C.c_char_p, []),
     "mc_philox": (C.c_int, [C.c_uint64, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]),
+    "mc_atomic_peak": (C.c_int, [C.c_uint64, DP]),
     "mc_run_static": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.POINTER(mc_run_opts),
                                 C.c_void_p, C.c_void_p, C.c_void_p]),
 }
@@ -329,6 +330,13 @@ def run_static(h: int, n_histories: int, seed: int, opts: mc_run_opts | None, me
     check(lib().mc_run_static(C.c_void_p(h), int(n_histories), int(seed) & (2**64 - 1),
                               C.byref(opts) if opts is not None else None, C.c_void_p(mean_dev_ptr),
                               C.c_void_p(err_dev_ptr), C.c_void_p(_stream_handle(stream))))
+
+
+def atomic_peak(span: int) -> float:
+    """mc_atomic_peak: 64-bit atomic adds per second over `span` random slots."""
+    v = C.c_double(0)
+    check(lib().mc_atomic_peak(int(span), C.byref(v)))
+    return v.value
 
 
 def run_timing(h: int):
