@@ -236,6 +236,53 @@ int mc_trace_get(mc_problem* p, uint64_t* t_ns, uint64_t* items, uint64_t* sourc
  * the transport kernel and around the batch-statistics kernel (milliseconds).  Synchronises. */
 int mc_run_timing(mc_problem* p, double* transport_ms, double* stats_ms);
 
+/* Weight windows (variance reduction for deep penetration; the paper's runs are analog or use
+ * implicit capture, §3).  Sets the window-centre table w_c over an (x, y, z) mesh and all groups:
+ * edges = x[nx+1], y[ny+1], z[nz+1] (increasing), centre[nz][ny][nx][G] (host arrays, copied;
+ * 0 disables windows in a cell).  With opts->ww_enable, after every collision or surface event a
+ * particle of weight w in a cell with centre w_c is split into k = min(ceil(w / w_c), 10) copies
+ * of weight w / k if w > 2 w_c, or rouletted (kept with probability w / w_c at weight w_c, using
+ * the event's u_ww draw) if w < w_c / 2.  Both keep every tally unbiased.  Weighted runs should
+ * use FP64 tallies (weights can span many decades). */
+int mc_ww_set_table(mc_problem* p, int nx, int ny, int nz, const double* edges, const double* centre);
+
+/* ------------------------------------------------------------------------- importance network */
+/* A 5 -> 64 -> 64 -> 64 -> 1 perceptron (tanh hidden units, linear output) mapping a phase-space
+ * point (x, y, z, group, t, each scaled to [-1, 1]) to the log of a weight-window centre.  FP32
+ * master parameters with Adam state; the forward and backward passes run on the tensor cores in
+ * BF16 with FP32 accumulation.  Parameter order: W1[64][5], b1[64], W2[64][64], b2[64],
+ * W3[64][64], b3[64], W4[64], b4 (mc_mlp_param_count() values).  The paper has no such network:
+ * it is this library's learned variance reduction for deep-penetration problems. */
+typedef struct mc_mlp mc_mlp;
+int mc_mlp_param_count(void);
+/* Creates a network on the current device with all parameters 0. */
+int mc_mlp_create(mc_mlp** out);
+void mc_mlp_destroy(mc_mlp* m);
+/* Copies n == mc_mlp_param_count() parameters from / to host memory (set resets the Adam state). */
+int mc_mlp_set_params(mc_mlp* m, const double* params, size_t n);
+int mc_mlp_get_params(mc_mlp* m, double* params, size_t n);
+/* y[i] = net(x[i]) for n points; x DEVICE [n][5] float, y DEVICE [n] float. */
+int mc_mlp_forward(mc_mlp* m, const float* x, float* y, int n, void* stream);
+/* loss = (1/n) sum_i wt[i] (net(x[i]) - target[i])^2 and grad = d loss / d params (DEVICE arrays;
+ * wt may be NULL for unit weights; grad has mc_mlp_param_count() floats; both are overwritten). */
+int mc_mlp_loss_grad(mc_mlp* m, const float* x, const float* target, const float* wt, int n, float* grad,
+                     float* loss, void* stream);
+/* `epochs` full-batch Adam steps (beta 0.9 / 0.999) at learning rate lr on the DEVICE arrays,
+ * continuing the network's Adam state; *last_loss (DEVICE, may be NULL) gets the last epoch's loss.
+ * One CTA runs all epochs; the set is limited to 2^20 points. */
+int mc_mlp_train(mc_mlp* m, const float* x, const float* target, const float* wt, int n, int epochs, float lr,
+                 float* last_loss, void* stream);
+/* One learning round of the weight windows from the problem's last run (synchronous):
+ *   1. from mesh tally `tally_id` (its time bins summed) take the flux phi of every (cell, group)
+ *      resolved to a relative error below 0.5; target = log(phi / phi_ref), phi_ref = the flux of the
+ *      source point's cell in the source's main group, weight = 1 / relative variance (capped);
+ *   2. train the network on these targets on the GPU (`epochs` Adam steps at `lr`);
+ *   3. evaluate it on every (cell, group) of that tally's spatial mesh and set the window centres
+ *      w_c = phi_ref-normalised exp(net) as the problem's weight-window table (the forward-flux
+ *      weight windows of the MAGIC method, learned instead of tabulated).
+ * info (host, may be NULL) receives {training points, final loss, target scale, phi_ref}. */
+int mc_ww_learn(mc_problem* p, mc_mlp* m, int tally_id, int epochs, float lr, double info[4]);
+
 /* Bytes of sampling, geometry and tally tables that mc_problem_create copied to the device
  * (both tracking precisions); 0 for NULL. */
 size_t mc_problem_table_bytes(const mc_problem* p);

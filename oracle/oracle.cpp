@@ -498,7 +498,11 @@ Particle source_particle(const Prob& P, uint64_t seed, uint64_t h) {
 bool weight_window(const Prob& P, uint64_t seed, Particle& q, uint32_t k_used,
                    std::vector<Particle>& stack, Acc& acc) {
   if (!P.ww) return true;
-  int ix = bin_of(P.ww_e[0], q.x), iy = bin_of(P.ww_e[1], q.y), iz = bin_of(P.ww_e[2], q.z);
+  // the window of the cell the particle moves into: a particle on a window-mesh edge (e.g. just
+  // after crossing a layer plane that is also a mesh plane) is looked up 1e-9 cm ahead
+  const double ah = 1e-9;
+  int ix = bin_of(P.ww_e[0], q.x + ah * q.ux), iy = bin_of(P.ww_e[1], q.y + ah * q.uy),
+      iz = bin_of(P.ww_e[2], q.z + ah * q.uz);
   if (ix < 0 || iy < 0 || iz < 0) return true;
   double wc = P.ww_c[((iz * P.ww_n[1] + iy) * P.ww_n[0] + ix) * P.G + q.g];
   if (!(wc > 0.0)) return true;

@@ -167,6 +167,8 @@ struct mc_problem {
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // transport start, transport end, stats end
   // weight windows
   int ww_set = 0, ww_n[3] = {0, 0, 0};
+  double src_center[3] = {0.0, 0.0, 0.0};  // reference point of the source (box centre / surface point)
+  int src_group = 0;                        // the source's most likely group
   DevBuf d_ww;
 };
 
@@ -486,8 +488,14 @@ int mc_problem_create(const mc_problem_desc* d, mc_problem** out) {
     h.n[1] = T.ny;
     h.n[2] = T.nz;
     h.n[3] = T.nt;
+    const double* e[4] = {T.x, T.y, T.z, T.t};
+    for (int k = 0; k < 4; ++k) h.e[k].assign(e[k], e[k] + h.n[k] + 1);
     p->tallies.push_back(h);
   }
+  for (int i = 0; i < 3; ++i) p->src_center[i] = 0.5 * (d->source.lo[i] + d->source.hi[i]);
+  if (d->source.pos == MC_SRC_SURFACE_X0) p->src_center[0] = d->source.lo[0];
+  for (int g = 1; g < p->G; ++g)
+    if (d->source.group_pdf[g] > d->source.group_pdf[p->src_group]) p->src_group = g;
   p->blob[0] = build_blob<float>(d);
   p->blob[1] = build_blob<double>(d);
   const TableHeader* H = reinterpret_cast<const TableHeader*>(p->blob[0].data());
@@ -835,6 +843,35 @@ int mc_event_log(mc_problem* p, mc_event* out, size_t cap, size_t* n_out) {
   return MC_OK;
 }
 
+int mc_ww_set_table(mc_problem* p, int nx, int ny, int nz, const double* edges, const double* centre) {
+  g_err.clear();
+  if (!p || !edges || !centre) return fail(MC_ERR_INVALID, "NULL argument");
+  if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny * nz > (1 << 24))
+    return fail(MC_ERR_INVALID, "weight-window mesh size");
+  const int n[3] = {nx, ny, nz};
+  const double* e = edges;
+  for (int d = 0; d < 3; ++d) {
+    for (int i = 1; i <= n[d]; ++i)
+      if (!(e[i] > e[i - 1])) return fail(MC_ERR_INVALID, "weight-window edges must increase");
+    e += n[d] + 1;
+  }
+  const size_t cells = (size_t)nx * ny * nz * p->G;
+  for (size_t i = 0; i < cells; ++i)
+    if (!(centre[i] >= 0.0) || !std::isfinite(centre[i]))
+      return fail(MC_ERR_INVALID, "weight-window centres must be finite and >= 0 (0 disables a cell)");
+  const size_t n_edges = (size_t)(nx + 1) + (ny + 1) + (nz + 1);
+  if (p->has_run) CK(cudaStreamSynchronize(p->stream));
+  int rc = p->d_ww.ensure((n_edges + cells) * sizeof(double), p->dev);
+  if (rc != MC_OK) return rc;
+  CK(cudaMemcpy(p->d_ww.ptr, edges, n_edges * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy((double*)p->d_ww.ptr + n_edges, centre, cells * sizeof(double), cudaMemcpyHostToDevice));
+  p->ww_n[0] = nx;
+  p->ww_n[1] = ny;
+  p->ww_n[2] = nz;
+  p->ww_set = 1;
+  return MC_OK;
+}
+
 size_t mc_problem_table_bytes(const mc_problem* p) {
   return p ? p->blob[0].size() + p->blob[1].size() : 0;
 }
@@ -1086,5 +1123,249 @@ extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t
   k_static_finalize<<<g ? g : 1, 256, 0, s>>>((const Ctl*)base, base + off_stats, P.tally_fp64, bins,
                                               (double)n_histories, (double)nb, 1.0 / P.fixed_scale, mean, std_err);
   CK(cudaGetLastError());
+  return MC_OK;
+}
+
+// ------------------------------------------------------------------------------------------ importance network
+namespace mcgb {
+size_t mlp_param_count();
+size_t mlp_weights_bytes();
+cudaError_t mlp_refresh(const float* master, void* Wg, cudaStream_t s);
+cudaError_t mlp_forward(const void* Wg, const float* x, float* y, int n, cudaStream_t s);
+cudaError_t mlp_loss_grad(const void* Wg, const float* x, const float* tgt, const float* wt, int n, float* grad,
+                          float* loss, cudaStream_t s);
+cudaError_t mlp_train(float* master, float* m1, float* m2, void* Wg, const float* x, const float* tgt, const float* wt,
+                      int n, int epochs, float lr, long long step0, float* last_loss, cudaStream_t s);
+cudaError_t mlp_centres(const float* y, int n, double scale, double ymin, double ymax, double ref, double* centre,
+                        cudaStream_t s);
+}  // namespace mcgb
+
+struct mc_mlp {
+  int dev = 0;
+  DevBuf master, m1, m2, wg, data, aux;
+  long long steps = 0;
+};
+
+extern "C" {
+
+int mc_mlp_param_count(void) { return (int)mlp_param_count(); }
+
+int mc_mlp_create(mc_mlp** out) {
+  g_err.clear();
+  if (!out) return fail(MC_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  mc_mlp* m = new mc_mlp();
+  int rc = current_device(&m->dev);
+  const size_t np = mlp_param_count();
+  if (rc == MC_OK) rc = m->master.ensure(np * 4, m->dev);
+  if (rc == MC_OK) rc = m->m1.ensure(np * 4, m->dev);
+  if (rc == MC_OK) rc = m->m2.ensure(np * 4, m->dev);
+  if (rc == MC_OK) rc = m->wg.ensure(mlp_weights_bytes(), m->dev);
+  if (rc == MC_OK) {
+    cudaError_t e = cudaMemset(m->master.ptr, 0, np * 4);
+    if (e == cudaSuccess) e = cudaMemset(m->m1.ptr, 0, np * 4);
+    if (e == cudaSuccess) e = cudaMemset(m->m2.ptr, 0, np * 4);
+    if (e == cudaSuccess) e = cudaMemset(m->wg.ptr, 0, mlp_weights_bytes());
+    if (e == cudaSuccess) e = mlp_refresh((const float*)m->master.ptr, m->wg.ptr, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) rc = cuda_fail(e, "mc_mlp_create");
+  }
+  if (rc != MC_OK) {
+    mc_mlp_destroy(m);
+    return rc;
+  }
+  *out = m;
+  return MC_OK;
+}
+
+void mc_mlp_destroy(mc_mlp* m) {
+  if (!m) return;
+  cudaDeviceSynchronize();
+  m->master.release();
+  m->m1.release();
+  m->m2.release();
+  m->wg.release();
+  m->data.release();
+  m->aux.release();
+  delete m;
+}
+
+int mc_mlp_set_params(mc_mlp* m, const double* params, size_t n) {
+  g_err.clear();
+  const size_t np = mlp_param_count();
+  if (!m || !params || n != np) return fail(MC_ERR_INVALID, "expected %zu parameters", np);
+  std::vector<float> f(np);
+  for (size_t i = 0; i < np; ++i) {
+    if (!std::isfinite(params[i])) return fail(MC_ERR_INVALID, "parameter %zu is not finite", i);
+    f[i] = (float)params[i];
+  }
+  CK(cudaMemcpy(m->master.ptr, f.data(), np * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemset(m->m1.ptr, 0, np * 4));
+  CK(cudaMemset(m->m2.ptr, 0, np * 4));
+  CK(mlp_refresh((const float*)m->master.ptr, m->wg.ptr, 0));
+  CK(cudaDeviceSynchronize());
+  m->steps = 0;
+  return MC_OK;
+}
+
+int mc_mlp_get_params(mc_mlp* m, double* params, size_t n) {
+  g_err.clear();
+  const size_t np = mlp_param_count();
+  if (!m || !params || n < np) return fail(MC_ERR_INVALID, "expected room for %zu parameters", np);
+  std::vector<float> f(np);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(f.data(), m->master.ptr, np * 4, cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < np; ++i) params[i] = f[i];
+  return MC_OK;
+}
+
+int mc_mlp_forward(mc_mlp* m, const float* x, float* y, int n, void* stream) {
+  g_err.clear();
+  if (!m || !x || !y || n < 0) return fail(MC_ERR_INVALID, "bad argument");
+  if (n == 0) return MC_OK;
+  CK(mlp_forward(m->wg.ptr, x, y, n, (cudaStream_t)stream));
+  return MC_OK;
+}
+
+int mc_mlp_loss_grad(mc_mlp* m, const float* x, const float* target, const float* wt, int n, float* grad,
+                     float* loss, void* stream) {
+  g_err.clear();
+  if (!m || !x || !target || !grad || !loss || n < 1) return fail(MC_ERR_INVALID, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(grad, 0, mlp_param_count() * 4, s));
+  CK(cudaMemsetAsync(loss, 0, 4, s));
+  CK(mlp_loss_grad(m->wg.ptr, x, target, wt, n, grad, loss, s));
+  return MC_OK;
+}
+
+int mc_mlp_train(mc_mlp* m, const float* x, const float* target, const float* wt, int n, int epochs, float lr,
+                 float* last_loss, void* stream) {
+  g_err.clear();
+  if (!m || !x || !target || n < 1 || epochs < 0 || !(lr > 0.f)) return fail(MC_ERR_INVALID, "bad argument");
+  CK(mlp_train((float*)m->master.ptr, (float*)m->m1.ptr, (float*)m->m2.ptr, m->wg.ptr, x, target, wt, n, epochs, lr,
+               m->steps, last_loss, (cudaStream_t)stream));
+  m->steps += epochs;
+  return MC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// scaled coordinate in [-1, 1] of bin i of an edge list (0 on axes without finite extent)
+double scaled_centre(const std::vector<double>& e, int i) {
+  const int n = (int)e.size() - 1;
+  double lo = e[0], hi = e[n];
+  if (!std::isfinite(lo)) lo = n > 1 ? e[1] : 0.0;
+  if (!std::isfinite(hi)) hi = n > 1 ? e[n - 1] : 0.0;
+  if (!(hi > lo)) return 0.0;
+  double a = e[i], b = e[i + 1];
+  if (!std::isfinite(a)) a = b;
+  if (!std::isfinite(b)) b = a;
+  const double c = 0.5 * (a + b);
+  const double v = 2.0 * (c - lo) / (hi - lo) - 1.0;
+  return v < -1.0 ? -1.0 : (v > 1.0 ? 1.0 : v);
+}
+
+int bin_of_point(const std::vector<double>& e, double v) {
+  const int n = (int)e.size() - 1;
+  for (int i = 0; i < n; ++i)
+    if (v >= e[i] && v < e[i + 1]) return i;
+  return v < e[0] ? 0 : n - 1;
+}
+}  // namespace
+
+extern "C" int mc_ww_learn(mc_problem* p, mc_mlp* m, int tally_id, int epochs, float lr, double info[4]) {
+  g_err.clear();
+  if (!p || !m) return fail(MC_ERR_INVALID, "NULL argument");
+  if (tally_id < 0 || tally_id >= p->n_tally) return fail(MC_ERR_INVALID, "tally_id must name a mesh tally");
+  int64_t shp[5];
+  int rc = mc_tally_shape(p, tally_id, shp);
+  if (rc != MC_OK) return rc;
+  const int nz = (int)shp[0], ny = (int)shp[1], nx = (int)shp[2], G = (int)shp[3], nt = (int)shp[4];
+  const size_t nbin = (size_t)nz * ny * nx * G * nt;
+  std::vector<double> mean(nbin), err(nbin);
+  rc = mc_tally_get(p, tally_id, mean.data(), err.data(), nbin);
+  if (rc != MC_OK) return rc;
+  const HostTally& T = p->tallies[tally_id];
+  const size_t ncell = (size_t)nz * ny * nx * G;
+  std::vector<double> phi(ncell, 0.0), var(ncell, 0.0);
+  for (size_t c = 0; c < ncell; ++c)
+    for (int it = 0; it < nt; ++it) {
+      phi[c] += mean[c * nt + it];
+      var[c] += err[c * nt + it] * err[c * nt + it];
+    }
+  const int rx = bin_of_point(T.e[0], p->src_center[0]), ry = bin_of_point(T.e[1], p->src_center[1]),
+            rz = bin_of_point(T.e[2], p->src_center[2]);
+  const double phi_ref = phi[(((size_t)rz * ny + ry) * nx + rx) * G + p->src_group];
+  if (!(phi_ref > 0.0)) return fail(MC_ERR_STATE, "the source cell of tally %d has no flux yet", tally_id);
+  std::vector<float> xs, tg, wt, xall;
+  double scale = 1.0;
+  for (int iz = 0; iz < nz; ++iz)
+    for (int iy = 0; iy < ny; ++iy)
+      for (int ix = 0; ix < nx; ++ix)
+        for (int g = 0; g < G; ++g) {
+          const float pt[5] = {(float)scaled_centre(T.e[0], ix), (float)scaled_centre(T.e[1], iy),
+                               (float)scaled_centre(T.e[2], iz), G > 1 ? (float)(2.0 * g / (G - 1) - 1.0) : 0.f, 0.f};
+          xall.insert(xall.end(), pt, pt + 5);
+          const size_t c = (((size_t)iz * ny + iy) * nx + ix) * G + g;
+          if (!(phi[c] > 0.0)) continue;
+          const double rel = std::sqrt(var[c]) / phi[c];
+          if (!(rel < 0.5)) continue;
+          const double target = std::log(phi[c] / phi_ref);
+          xs.insert(xs.end(), pt, pt + 5);
+          tg.push_back((float)target);
+          wt.push_back((float)std::min(1.0 / std::max(rel * rel, 1e-12), 1e4));
+          scale = std::max(scale, std::fabs(target));
+        }
+  const int n = (int)tg.size();
+  if (n < 2) return fail(MC_ERR_STATE, "tally %d resolves fewer than two bins", tally_id);
+  if (n > (1 << 20)) return fail(MC_ERR_INVALID, "too many training points");
+  double wsum = 0.0;
+  for (float w : wt) wsum += w;
+  for (int i = 0; i < n; ++i) {
+    tg[i] = (float)(tg[i] / scale);
+    wt[i] = (float)(wt[i] * n / wsum);
+  }
+  const int nall = (int)(xall.size() / 5);
+  // device: [x n*5][target n][weight n][loss 1] and [all points nall*5][y nall]
+  rc = m->data.ensure(((size_t)n * 7 + 4) * 4, m->dev);
+  if (rc == MC_OK) rc = m->aux.ensure((size_t)nall * 6 * 4, m->dev);
+  if (rc != MC_OK) return rc;
+  float* dx = (float*)m->data.ptr;
+  float* dt = dx + (size_t)n * 5;
+  float* dw = dt + n;
+  float* dl = dw + n;
+  float* dall = (float*)m->aux.ptr;
+  float* dy = dall + (size_t)nall * 5;
+  CK(cudaMemcpy(dx, xs.data(), (size_t)n * 5 * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dt, tg.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dw, wt.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dall, xall.data(), (size_t)nall * 5 * 4, cudaMemcpyHostToDevice));
+  CK(mlp_train((float*)m->master.ptr, (float*)m->m1.ptr, (float*)m->m2.ptr, m->wg.ptr, dx, dt, dw, n, epochs, lr,
+               m->steps, dl, 0));
+  m->steps += epochs;
+  CK(mlp_forward(m->wg.ptr, dall, dy, nall, 0));
+  // the window table lives on the tally's spatial mesh
+  const size_t n_edges = (size_t)(nx + 1) + (ny + 1) + (nz + 1);
+  if (p->has_run) CK(cudaStreamSynchronize(p->stream));
+  rc = p->d_ww.ensure((n_edges + (size_t)nall) * sizeof(double), p->dev);
+  if (rc != MC_OK) return rc;
+  std::vector<double> edges;
+  for (int d = 0; d < 3; ++d) edges.insert(edges.end(), T.e[d].begin(), T.e[d].end());
+  CK(cudaMemcpy(p->d_ww.ptr, edges.data(), n_edges * sizeof(double), cudaMemcpyHostToDevice));
+  // window centres relative to the source particle's weight 1 at phi_ref
+  CK(mlp_centres(dy, nall, scale, -700.0, 50.0, 1.0, (double*)p->d_ww.ptr + n_edges, 0));
+  float loss = 0.f;
+  CK(cudaMemcpy(&loss, dl, 4, cudaMemcpyDeviceToHost));
+  p->ww_n[0] = nx;
+  p->ww_n[1] = ny;
+  p->ww_n[2] = nz;
+  p->ww_set = 1;
+  if (info) {
+    info[0] = n;
+    info[1] = loss;
+    info[2] = scale;
+    info[3] = phi_ref;
+  }
   return MC_OK;
 }

@@ -120,8 +120,12 @@ __device__ bool weight_window(const RunParams& P, const Tab<R>& T, Part<R>& p, u
   const double* ex = P.ww_edges;
   const double* ey = ex + P.ww_nx + 1;
   const double* ez = ey + P.ww_ny + 1;
-  const int ix = bin_search(ex, P.ww_nx, (double)p.x), iy = bin_search(ey, P.ww_ny, (double)p.y),
-            iz = bin_search(ez, P.ww_nz, (double)p.z);
+  // the window of the cell the particle moves into: a particle on a window-mesh edge (e.g. just
+  // after crossing a layer plane that is also a mesh plane) is looked up 1e-9 cm ahead
+  const double ah = 1e-9;
+  const int ix = bin_search(ex, P.ww_nx, (double)p.x + ah * (double)p.ux),
+            iy = bin_search(ey, P.ww_ny, (double)p.y + ah * (double)p.uy),
+            iz = bin_search(ez, P.ww_nz, (double)p.z + ah * (double)p.uz);
   if (ix < 0 || ix >= P.ww_nx || iy < 0 || iy >= P.ww_ny || iz < 0 || iz >= P.ww_nz) return true;
   const double wc = __ldg(P.ww_center + ((size_t)(iz * P.ww_ny + iy) * P.ww_nx + ix) * T.G + pk_g(p.pk));
   if (!(wc > 0.0)) return true;

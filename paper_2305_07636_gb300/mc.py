@@ -129,6 +129,18 @@ SIGNATURES = {
     "mc_last_error": (C.c_char_p, []),
     "mc_philox": (C.c_int, [C.c_uint64, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]),
     "mc_atomic_peak": (C.c_int, [C.c_uint64, DP]),
+    "mc_ww_set_table": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, DP, DP]),
+    "mc_mlp_param_count": (C.c_int, []),
+    "mc_mlp_create": (C.c_int, [C.POINTER(C.c_void_p)]),
+    "mc_mlp_destroy": (None, [C.c_void_p]),
+    "mc_mlp_set_params": (C.c_int, [C.c_void_p, DP, C.c_size_t]),
+    "mc_mlp_get_params": (C.c_int, [C.c_void_p, DP, C.c_size_t]),
+    "mc_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "mc_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                   C.c_void_p, C.c_void_p]),
+    "mc_mlp_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_float,
+                               C.c_void_p, C.c_void_p]),
+    "mc_ww_learn": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_float, DP]),
     "mc_run_static": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.POINTER(mc_run_opts),
                                 C.c_void_p, C.c_void_p, C.c_void_p]),
 }
@@ -332,6 +344,15 @@ def run_static(h: int, n_histories: int, seed: int, opts: mc_run_opts | None, me
                               C.c_void_p(err_dev_ptr), C.c_void_p(_stream_handle(stream))))
 
 
+def ww_set_table(h: int, ww: dict):
+    """mc_ww_set_table from {x, y, z: edges, center: [nz][ny][nx][G]}."""
+    edges = np.ascontiguousarray(np.concatenate([np.asarray(ww[k], np.float64) for k in "xyz"]))
+    centre = np.ascontiguousarray(np.asarray(ww["center"], np.float64).ravel())
+    n = [len(ww[k]) - 1 for k in "xyz"]
+    check(lib().mc_ww_set_table(C.c_void_p(h), n[0], n[1], n[2], edges.ctypes.data_as(DP),
+                                centre.ctypes.data_as(DP)))
+
+
 def atomic_peak(span: int) -> float:
     """mc_atomic_peak: 64-bit atomic adds per second over `span` random slots."""
     v = C.c_double(0)
@@ -391,6 +412,9 @@ class Problem:
     def tally(self, i=0):
         return tally_get(self.h, i)
 
+    def set_weight_windows(self, ww):
+        ww_set_table(self.h, ww)
+
     def tally_batches(self, i=0):
         return tally_batches(self.h, i)
 
@@ -422,3 +446,59 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+class Mlp:
+    """Owning wrapper around an mc_mlp handle (the weight-window importance network).  Device
+    arrays are passed as raw pointers (e.g. torch tensors' data_ptr())."""
+
+    def __init__(self, params=None):
+        h = C.c_void_p()
+        check(lib().mc_mlp_create(C.byref(h)))
+        self.h = h.value
+        self.n_params = int(lib().mc_mlp_param_count())
+        if params is not None:
+            self.set_params(params)
+
+    def set_params(self, params):
+        a = np.ascontiguousarray(np.asarray(params, np.float64).ravel())
+        check(lib().mc_mlp_set_params(C.c_void_p(self.h), a.ctypes.data_as(DP), a.size))
+
+    def get_params(self):
+        a = np.zeros(self.n_params)
+        check(lib().mc_mlp_get_params(C.c_void_p(self.h), a.ctypes.data_as(DP), a.size))
+        return a
+
+    def forward(self, x_ptr, y_ptr, n, stream=None):
+        check(lib().mc_mlp_forward(C.c_void_p(self.h), C.c_void_p(x_ptr), C.c_void_p(y_ptr), int(n),
+                                   C.c_void_p(_stream_handle(stream))))
+
+    def loss_grad(self, x_ptr, t_ptr, w_ptr, n, g_ptr, l_ptr, stream=None):
+        check(lib().mc_mlp_loss_grad(C.c_void_p(self.h), C.c_void_p(x_ptr), C.c_void_p(t_ptr),
+                                     C.c_void_p(w_ptr), int(n), C.c_void_p(g_ptr), C.c_void_p(l_ptr),
+                                     C.c_void_p(_stream_handle(stream))))
+
+    def train(self, x_ptr, t_ptr, w_ptr, n, epochs, lr, loss_ptr=0, stream=None):
+        check(lib().mc_mlp_train(C.c_void_p(self.h), C.c_void_p(x_ptr), C.c_void_p(t_ptr),
+                                 C.c_void_p(w_ptr), int(n), int(epochs), float(lr),
+                                 C.c_void_p(loss_ptr), C.c_void_p(_stream_handle(stream))))
+
+    def close(self):
+        if self.h:
+            lib().mc_mlp_destroy(C.c_void_p(self.h))
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ww_learn(problem_h: int, mlp: "Mlp", tally_id: int, epochs: int, lr: float) -> dict:
+    """mc_ww_learn: one learning round of the weight windows from the problem's last run."""
+    info = np.zeros(4)
+    check(lib().mc_ww_learn(C.c_void_p(problem_h), C.c_void_p(mlp.h), int(tally_id), int(epochs),
+                            float(lr), info.ctypes.data_as(DP)))
+    return {"points": int(info[0]), "loss": float(info[1]), "scale": float(info[2]),
+            "phi_ref": float(info[3])}

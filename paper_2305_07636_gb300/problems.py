@@ -388,6 +388,42 @@ def _small_lattice(seed, G, name):
     return p
 
 
+def exponential_ww(prob, decay, nx=None, ref=1.0):
+    """Weight-window centres w_c = ref * exp(-decay * x) on an x-mesh (edges from the problem's
+    second tally, or nx equal bins over the slab), all groups alike: a fixed, seeded-free input."""
+    if nx is None:
+        xe = np.asarray(prob["tallies"][1]["x"], dtype=np.float64)
+    else:
+        L = prob["surfaces"][-1]["coef"][0]
+        xe = np.linspace(0.0, L, nx + 1)
+    xc = 0.5 * (xe[:-1] + xe[1:])
+    G = prob["G"]
+    centre = np.repeat((ref * np.exp(-decay * xc))[:, None], G, axis=1)  # [nx][G]
+    return {"x": xe.tolist(), "y": [-INF, INF], "z": [-INF, INF], "center": centre.tolist()}
+
+
+def bf16_round(a):
+    """Round to the nearest bfloat16 value (ties to even), returned as float64."""
+    f = np.ascontiguousarray(np.asarray(a, np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def mlp_init(seed=7, H=64, n_in=5, bf16=True):
+    """Seeded Xavier-uniform initial parameters of the 5 -> H -> H -> H -> 1 importance network in
+    the order W1, b1, W2, b2, W3, b3, W4, b4 (biases zero); optionally rounded to bfloat16 so that
+    a BF16 copy of them is exact."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_in, fan_out in ((n_in, H), (H, H), (H, H), (H, 1)):
+        lim = math.sqrt(6.0 / (fan_in + fan_out))
+        parts.append(rng.uniform(-lim, lim, fan_in * fan_out))
+        parts.append(np.zeros(fan_out))
+    p = np.concatenate(parts)
+    return bf16_round(p) if bf16 else p
+
+
 def by_name(name, **kw):
     return {"config1": config1, "config2": config2, "config3": config3,
             "config4": config4}[name](**kw)

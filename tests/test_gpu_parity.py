@@ -302,3 +302,32 @@ def test_tangent_pin_crossing_terminates(torch):
     c = p.counters()
     assert conserved(c) and c["flight"] < 10_000
     p.close()
+
+
+# ----------------------------------------------------------------------------- weight windows
+
+
+def test_weight_window_fp64_replay_and_unbiasedness(torch):
+    """A seeded exponential window table (an input, like the cross sections) given to both sides:
+    the FP64 GPU walk replays the oracle's event sequence with splitting and roulette, and the
+    FP32 GPU tallies with windows agree with the oracle's analog tallies within 4 sigma."""
+    prob = P.slab_stack(thickness=8.0, n_layers=4, detector=2.0, ww_bin=1.0, name="thin")
+    ww = P.exponential_ww(prob, decay=0.8)
+    n = 3000
+    o = oracle.run(prob, n, seed=77, threads=THREADS, log_first=0, log_count=n, log_cap=400 * n,
+                   ww=ww)
+    p = mc.Problem(prob)
+    p.set_weight_windows(ww)
+    p.run(n, 77, precision="fp64", tally_mode="fp64", ww_enable=1, log_first=0, log_count=n,
+          log_capacity=400 * n, bank_capacity=1 << 18)
+    compare_logs(p.events(400 * n), o.events)
+    c = p.counters()
+    for k in oracle.COUNTER_NAMES:
+        assert c[k] == o.counters[k], k
+    a = oracle.run(prob, 2_000_000, seed=5, threads=THREADS)
+    p.run(2_000_000, 6, tally_mode="fp64", ww_enable=1)
+    assert conserved(p.counters())
+    mg, sg = p.tally(1)
+    mo, so = a.tallies[1]
+    check_z(combined_z(mg, sg, mo, so), 20)
+    p.close()
