@@ -159,6 +159,7 @@ typedef struct {
                                particles remain, finish them history-style (0 = 2 per thread) */
   int tally_stripes;      /* copies of the batch tallies that CTAs score into round-robin, summed
                              by the statistics (0 = up to 16 within a 64 MB budget) */
+  int batch_unit;         /* mc_run_batch: histories per work unit a warp claims (0 = tuned or 128) */
 } mc_run_opts;
 
 /* Fills the defaults listed above. */
@@ -320,6 +321,46 @@ const char* mc_last_error(void);
  * at zero): calls that overlap on the GPU, e.g. on two streams, race and corrupt each other. */
 int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts* opts,
                   double* mean, double* std_err, void* stream);
+
+/* ------------------------------------------------------------------------- batched launch */
+/* Runs n independent problems (n <= 65536) in one persistent launch, replayed from a CUDA graph
+ * that the library captures once per launch shape.  Problem i runs histories [0, n_hist[i]) with
+ * the seed `seed + i`: exactly the particles that mc_run(ps[i], n_hist[i], seed + i, o) transports,
+ * so fixed-point tallies and event counters equal those of n separate runs bit for bit.
+ *   Scheduling: the histories of every problem are cut into work units of o->batch_unit
+ *   consecutive histories, problems in ascending order of n_hist (short problems finish first).
+ *   Every warp of the grid claims units one at a time, stages the unit's problem tables in its own
+ *   slice of shared memory (only when the problem changes), and carries the unit's particles and
+ *   all their secondaries to completion; a warp claims the next unit of the same problem before its
+ *   lanes run dry.  Secondaries and weight-window copies wait in a warp-private stack of
+ *   o->bank_capacity particles (0 = 2048) in device memory; no CTA waits for another, so the
+ *   launch has no grid barrier.
+ *   Options apply to every problem (precision, tally_mode, fixed_bits, n_batches, ww_enable,
+ *   aggregate_atomics, max_iterations as the per-particle event budget); algorithm, event logging,
+ *   first_history, tally_stripes and drain_threshold do not apply.  block_size, blocks_per_sm and
+ *   batch_unit left at 0 take the configuration mc_batch_tune stored for a batch of the same
+ *   shape, else 256 threads, as many CTAs per SM as fit, 128 histories.
+ *   Results are read per problem with mc_tally_get, mc_tally_batches, mc_counters_get; mc_wait on
+ *   a problem returns that problem's device error (bank overflow, watchdog, lost particle), which
+ *   stops its remaining units but not the other problems'.  mc_run_timing on a problem gives the
+ *   span from its first claimed unit to its last finished particle (device clock) as transport
+ *   time.
+ *   Asynchronous on `stream`, unless per_problem_wall_s is non-NULL: then the call synchronises and
+ *   writes, for each problem, the seconds from the start of the launch until its last particle
+ *   finished.  The problems must live on the current device and be distinct. */
+int mc_run_batch(mc_problem* const* ps, int n, const uint64_t* n_hist, uint64_t seed,
+                 const mc_run_opts* o, void* stream, double* per_problem_wall_s);
+
+/* Autotuner of mc_run_batch: runs the batch (seed, o) under each candidate configuration (block
+ * size 128 or 256; the 80- or 128-register build of the kernel; units of 32 to 512 histories),
+ * times each launch with CUDA events (best of two after a warm-up), and stores the fastest for
+ * every later batch of the same shape (problem count, precision, tally mode, batches, and per
+ * problem its group count, geometry kind, bin count and history count rounded to a power of 2).
+ * tuned (nullable) receives a copy of o with block_size, blocks_per_sm and batch_unit set;
+ * best_ms (nullable) the launch time of that configuration, in ms.  Synchronises.  The tallies
+ * left behind are those of the last candidate run. */
+int mc_batch_tune(mc_problem* const* ps, int n, const uint64_t* n_hist, uint64_t seed,
+                  const mc_run_opts* o, void* stream, mc_run_opts* tuned, double* best_ms);
 
 /* Measures the device's L2 atomic throughput for the scoring access pattern: 64-bit atomic adds
  * to pseudo-random slots of a zeroed array of `span` elements (1 .. 2^27), issued by 8 CTAs of

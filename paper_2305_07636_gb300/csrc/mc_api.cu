@@ -19,7 +19,7 @@
 #include <string>
 #include <vector>
 
-#include "mc_internal.h"
+#include "mc_host.h"
 
 namespace mcgb {
 template <typename R>
@@ -40,7 +40,9 @@ static const uint64_t kTraceCap = 65536;
 // ------------------------------------------------------------------------------------------ errors
 static thread_local std::string g_err;
 
-static int fail(int code, const char* fmt, ...) {
+namespace mcgb {
+
+int fail(int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -50,27 +52,26 @@ static int fail(int code, const char* fmt, ...) {
   return code;
 }
 
-static int cuda_fail(cudaError_t e, const char* what) {
+int cuda_fail(cudaError_t e, const char* what) {
   return fail(e == cudaErrorMemoryAllocation ? MC_ERR_OOM : MC_ERR_CUDA, "%s: %s", what,
               cudaGetErrorString(e));
 }
 
-#define CK(call)                                  \
-  do {                                            \
-    cudaError_t e_ = (call);                      \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-  } while (0)
+int current_device(int* dev) {
+  cudaError_t e = cudaGetDevice(dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  return MC_OK;
+}
 
 // ------------------------------------------------------------------------------------------ memory pool
 // Device blocks are recycled across problems instead of returned to the driver, so creating and
 // destroying problems in a loop does not pay cudaMalloc/cudaFree each time.
-namespace {
 struct PoolBlock {
   int dev;
   void* ptr;
 };
-std::mutex g_pool_mu;
-std::multimap<size_t, PoolBlock> g_pool;
+static std::mutex g_pool_mu;
+static std::multimap<size_t, PoolBlock> g_pool;
 
 int pool_alloc(void** out, size_t bytes, int dev) {
   {
@@ -115,62 +116,7 @@ void pool_free(void* p, size_t bytes, int dev) {
   g_pool.insert({bytes, PoolBlock{dev, p}});
 }
 
-struct DevBuf {
-  void* ptr = nullptr;
-  size_t bytes = 0;
-  int dev = 0;
-  int ensure(size_t want, int device) {
-    if (ptr && bytes >= want && dev == device) return MC_OK;
-    release();
-    int rc = pool_alloc(&ptr, want, device);
-    if (rc != MC_OK) {
-      ptr = nullptr;
-      return rc;
-    }
-    bytes = want;
-    dev = device;
-    return MC_OK;
-  }
-  void release() {
-    pool_free(ptr, bytes, dev);
-    ptr = nullptr;
-    bytes = 0;
-  }
-};
-}  // namespace
-
-// ------------------------------------------------------------------------------------------ problem
-struct HostTally {
-  int n[4];
-  std::vector<double> e[4];
-};
-
-struct mc_problem {
-  int dev = 0;
-  int G = 0, M = 0, n_surf = 0, n_cell = 0, n_tally = 0;
-  int total_bins = 0, leak_offset = 0;
-  std::vector<HostTally> tallies;
-  std::vector<uint8_t> blob[2];  // [0] FP32 tables, [1] FP64 tables
-  DevBuf d_blob[2];
-  DevBuf d_ctl, d_tally, d_stats, d_log, d_banks, d_trace;
-  DevBuf d_sticky;  // first device error of any run since the last mc_wait (not reset by mc_run)
-  // last run
-  int has_run = 0;
-  uint64_t n_hist = 0;
-  int n_batches = 0;
-  cudaStream_t stream = nullptr;
-  uint64_t log_cap = 0;
-  int last_status = MC_OK;
-  int tally_fp64 = 0;
-  uint32_t stripes = 1;
-  double fixed_scale = 1.0;
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // transport start, transport end, stats end
-  // weight windows
-  int ww_set = 0, ww_n[3] = {0, 0, 0};
-  double src_center[3] = {0.0, 0.0, 0.0};  // reference point of the source (box centre / surface point)
-  int src_group = 0;                        // the source's most likely group
-  DevBuf d_ww;
-};
+}  // namespace mcgb
 
 namespace {
 
@@ -446,15 +392,55 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
   return B.b;
 }
 
-int current_device(int* dev) {
-  cudaError_t e = cudaGetDevice(dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  return MC_OK;
-}
-
 }  // namespace
 
 // ------------------------------------------------------------------------------------------ ABI
+namespace mcgb {
+
+void fill_run_params(const mc_problem* p, const mc_run_opts& o, uint64_t n_histories, uint64_t seed,
+                     uint32_t stripes, RunParams& P) {
+  const int fp64 = o.precision == MC_FP64;
+  const int nb = o.n_batches;
+  const uint64_t bins = (uint64_t)p->total_bins;
+  P.ctl = (Ctl*)p->d_ctl.ptr;
+  P.sticky = (int*)p->d_sticky.ptr;
+  P.tally = p->d_tally.ptr;
+  P.tally_stripes = stripes;
+  P.stripe_stride = (uint64_t)nb * bins;
+  P.tally_fp64 = o.tally_mode == MC_TALLY_FP64;
+  // auto: aggregate only a small tally that could not be striped (many lanes per hot bin)
+  P.aggregate = o.aggregate_atomics >= 0
+                    ? o.aggregate_atomics
+                    : (stripes == 1 && (double)nb * (double)bins * 8.0 < 32.0 * 1048576.0 ? 1 : 0);
+  P.fixed_scale = std::ldexp(1.0, o.fixed_bits);
+  P.fixed_scale_f = (float)P.fixed_scale;
+  P.n_hist = n_histories;
+  P.hist_per_batch = (n_histories + nb - 1) / nb;
+  {
+    const double mg = std::floor(4294967296.0 * (double)nb / (double)n_histories);
+    P.batch_magic = mg >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)mg;
+  }
+  P.n_batches = nb;
+  P.blob_bytes = (int)p->blob[fp64].size();
+  P.blob = (const uint4*)p->d_blob[fp64].ptr;
+  P.seed = seed;
+  P.max_iter = o.max_iterations ? o.max_iterations : (1ull << 20);
+  if (o.ww_enable) {
+    const double* base = (const double*)p->d_ww.ptr;
+    P.ww_on = 1;
+    P.ww_nx = p->ww_n[0];
+    P.ww_ny = p->ww_n[1];
+    P.ww_nz = p->ww_n[2];
+    P.ww_edges = base;
+    P.ww_center = base + (p->ww_n[0] + 1) + (p->ww_n[1] + 1) + (p->ww_n[2] + 1);
+    P.ww_upper = 2.0;
+    P.ww_lower = 0.5;
+    P.ww_split_max = 10;
+  }
+}
+
+}  // namespace mcgb
+
 extern "C" {
 
 const char* mc_last_error(void) { return g_err.c_str(); }
@@ -610,50 +596,18 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   P.cap_b = cap;
   P.ctl = (Ctl*)p->d_ctl.ptr;
   P.sticky = (int*)p->d_sticky.ptr;
-  P.tally = p->d_tally.ptr;
-  P.tally_stripes = stripes;
-  P.stripe_stride = (uint64_t)nb * bins;
-  P.tally_fp64 = o.tally_mode == MC_TALLY_FP64;
-  // auto: aggregate only a small tally that could not be striped (many lanes per hot bin)
-  P.aggregate = o.aggregate_atomics >= 0
-                    ? o.aggregate_atomics
-                    : (stripes == 1 && (double)nb * (double)bins * 8.0 < 32.0 * 1048576.0 ? 1 : 0);
-  P.fixed_scale = std::ldexp(1.0, o.fixed_bits);
-  P.fixed_scale_f = (float)P.fixed_scale;
+  fill_run_params(p, o, n_histories, seed, stripes, P);
   P.history_mode = o.algorithm == MC_ALG_HISTORY;
   rc = p->d_trace.ensure((size_t)3 * kTraceCap * 8, p->dev);
   if (rc != MC_OK) return rc;
   P.trace = (unsigned long long*)p->d_trace.ptr;
   P.trace_cap = kTraceCap;
-  P.n_hist = n_histories;
-  P.hist_per_batch = (n_histories + nb - 1) / nb;
   P.h_first = o.first_history;
-  {
-    const double mg = std::floor(4294967296.0 * (double)nb / (double)n_histories);
-    P.batch_magic = mg >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)mg;
-  }
-  P.n_batches = nb;
-  P.blob_bytes = (int)p->blob[fp64].size();
-  P.blob = (const uint4*)p->d_blob[fp64].ptr;
-  P.seed = seed;
-  P.max_iter = o.max_iterations ? o.max_iterations : (1ull << 20);
   P.spin_limit = 1ull << 22;
   P.log = o.log_count ? (mc_event*)p->d_log.ptr : nullptr;
   P.log_cap = log_cap;
   P.log_first = o.log_first;
   P.log_count = o.log_count;
-  if (o.ww_enable) {
-    const double* base = (const double*)p->d_ww.ptr;
-    P.ww_on = 1;
-    P.ww_nx = p->ww_n[0];
-    P.ww_ny = p->ww_n[1];
-    P.ww_nz = p->ww_n[2];
-    P.ww_edges = base;
-    P.ww_center = base + (p->ww_n[0] + 1) + (p->ww_n[1] + 1) + (p->ww_n[2] + 1);
-    P.ww_upper = 2.0;
-    P.ww_lower = 0.5;
-    P.ww_split_max = 10;
-  }
   CK(cudaMemsetAsync(p->d_ctl.ptr, 0, sizeof(Ctl), s));
   CK(cudaMemsetAsync(p->d_tally.ptr, 0, (size_t)stripes * nb * bins * 8, s));
   if (P.log) CK(cudaMemsetAsync(p->d_log.ptr, 0, log_cap * sizeof(mc_event), s));
@@ -677,6 +631,7 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   CK(launch_batch_stats(P.tally, P.tally_fp64, bins, nb, (int)stripes, n_histories, p->d_stats.ptr, s));
   CK(cudaEventRecord(p->ev[2], s));
   p->has_run = 1;
+  p->batched = 0;
   p->n_hist = n_histories;
   p->n_batches = nb;
   p->stream = s;
@@ -899,6 +854,15 @@ int mc_trace_get(mc_problem* p, uint64_t* t_ns, uint64_t* items, uint64_t* sourc
 int mc_run_timing(mc_problem* p, double* transport_ms, double* stats_ms) {
   if (!p) return fail(MC_ERR_INVALID, "problem is NULL");
   if (!p->has_run) return fail(MC_ERR_STATE, "no run yet");
+  if (p->batched) {
+    // part of a batched launch: first claimed unit to last finished particle, device clock
+    CK(cudaStreamSynchronize(p->stream));
+    Ctl c;
+    CK(cudaMemcpy(&c, p->d_ctl.ptr, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    if (transport_ms) *transport_ms = c.t_end > c.t_start ? (double)(c.t_end - c.t_start) * 1e-6 : 0.0;
+    if (stats_ms) *stats_ms = 0.0;
+    return MC_OK;
+  }
   CK(cudaEventSynchronize(p->ev[2]));
   float a = 0.f, b = 0.f;
   CK(cudaEventElapsedTime(&a, p->ev[0], p->ev[1]));

@@ -89,7 +89,7 @@ class mc_run_opts(C.Structure):
                 ("ww_enable", C.c_int), ("log_first", C.c_uint64), ("log_count", C.c_uint64),
                 ("log_capacity", C.c_uint64), ("first_history", C.c_uint64),
                 ("algorithm", C.c_int), ("drain_threshold", C.c_uint64),
-                ("tally_stripes", C.c_int)]
+                ("tally_stripes", C.c_int), ("batch_unit", C.c_int)]
 
 
 class mc_event(C.Structure):
@@ -143,6 +143,10 @@ SIGNATURES = {
     "mc_ww_learn": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_float, DP]),
     "mc_run_static": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.POINTER(mc_run_opts),
                                 C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mc_run_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_uint64), C.c_uint64,
+                               C.POINTER(mc_run_opts), C.c_void_p, DP]),
+    "mc_batch_tune": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_uint64), C.c_uint64,
+                                C.POINTER(mc_run_opts), C.c_void_p, C.POINTER(mc_run_opts), DP]),
 }
 
 _lib = None
@@ -342,6 +346,41 @@ def run_static(h: int, n_histories: int, seed: int, opts: mc_run_opts | None, me
     check(lib().mc_run_static(C.c_void_p(h), int(n_histories), int(seed) & (2**64 - 1),
                               C.byref(opts) if opts is not None else None, C.c_void_p(mean_dev_ptr),
                               C.c_void_p(err_dev_ptr), C.c_void_p(_stream_handle(stream))))
+
+
+def _batch_args(handles, n_hist):
+    n = len(handles)
+    if len(n_hist) != n:
+        raise ValueError("one history count per problem")
+    hs = (C.c_void_p * n)(*[C.c_void_p(h) for h in handles])
+    ns = (C.c_uint64 * n)(*[int(v) for v in n_hist])
+    return n, hs, ns
+
+
+def run_batch(handles, n_hist, seed: int, opts: mc_run_opts | None = None, stream=None,
+              wall: bool = False):
+    """mc_run_batch: the problems (handles) in one persistent launch; problem i uses seed + i.
+    With wall=True it synchronises and returns each problem's completion time (s) since the
+    launch started, else None."""
+    n, hs, ns = _batch_args(handles, n_hist)
+    out = np.zeros(n) if wall else None
+    check(lib().mc_run_batch(hs, n, ns, int(seed) & (2**64 - 1),
+                             C.byref(opts) if opts is not None else None,
+                             C.c_void_p(_stream_handle(stream)),
+                             out.ctypes.data_as(DP) if wall else None))
+    return out
+
+
+def batch_tune(handles, n_hist, seed: int, opts: mc_run_opts | None = None, stream=None):
+    """mc_batch_tune: times the candidate configurations and stores the fastest for batches of
+    this shape; returns (tuned options, its launch time in ms)."""
+    n, hs, ns = _batch_args(handles, n_hist)
+    tuned = mc_run_opts()
+    ms = C.c_double(0.0)
+    check(lib().mc_batch_tune(hs, n, ns, int(seed) & (2**64 - 1),
+                              C.byref(opts) if opts is not None else None,
+                              C.c_void_p(_stream_handle(stream)), C.byref(tuned), C.byref(ms)))
+    return tuned, ms.value
 
 
 def ww_set_table(h: int, ww: dict):
