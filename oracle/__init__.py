@@ -113,6 +113,9 @@ def lib():
             L.or_source_sample.argtypes = [C.POINTER(OrProblem), C.c_uint64, C.c_uint64,
                                            C.POINTER(C.c_double), C.POINTER(C.c_int)]
             L.or_source_sample.restype = C.c_int
+            L.or_find_cell.argtypes = [C.POINTER(OrProblem), C.c_double, C.c_double, C.c_double,
+                                       C.c_int, C.c_int, C.c_double, C.c_double, C.c_double]
+            L.or_find_cell.restype = C.c_int
             L.or_sample_scatter_group.argtypes = [C.POINTER(OrProblem), C.c_int, C.c_int,
                                                   C.c_double]
             L.or_sample_scatter_group.restype = C.c_int
@@ -334,6 +337,13 @@ def source_sample(prob, seed, h):
     g = C.c_int(0)
     cell = lib().or_source_sample(C.byref(m.s), seed, h, out, C.byref(g))
     return list(out), int(g.value), cell
+
+
+def find_cell(prob, x, y, z, skip=-1, skip_sense=0, u=(0.0, 0.0, 0.0)):
+    """Cell of a point; skip/skip_sense: the surface just crossed and the sense taken on it;
+    u: the direction of flight."""
+    m = Marshalled(prob)
+    return int(lib().or_find_cell(C.byref(m.s), x, y, z, skip, skip_sense, *[float(v) for v in u]))
 
 
 def sample_scatter_group(prob, m, g, u):

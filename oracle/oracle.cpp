@@ -243,20 +243,63 @@ double surf_f(const Prob& P, int s, double x, double y, double z) {
 // sense +1 <=> f >= 0, sense -1 <=> f < 0
 bool sense_ok(double f, int sense) { return sense > 0 ? f >= 0.0 : f < 0.0; }
 
-int find_cell(const Prob& P, double x, double y, double z, int skip_surf, int skip_sense) {
-  for (int c = 0; c < P.n_cell; ++c) {
-    bool ok = true;
-    bool has_skip = skip_surf < 0;
-    for (int i = 0; i < P.nhs[c] && ok; ++i) {
-      int s = P.hs_surf[c * OR_MAX_HS + i], sn = P.hs_sense[c * OR_MAX_HS + i];
-      if (s == skip_surf) {
-        has_skip = true;
-        ok = (sn == skip_sense);
-      } else {
-        ok = sense_ok(surf_f(P, s, x, y, z), sn);
-      }
+// size of the terms surf_f subtracts: what its rounding error is relative to
+double surf_terms(const Prob& P, int s, double x, double y, double z) {
+  const double* c = &P.scoef[3 * s];
+  switch (P.skind[s]) {
+    case OR_PX: return 1.0 + std::fabs(x) + std::fabs(c[0]);
+    case OR_PY: return 1.0 + std::fabs(y) + std::fabs(c[0]);
+    case OR_PZ: return 1.0 + std::fabs(z) + std::fabs(c[0]);
+    default: {
+      double dx = x - c[0], dy = y - c[1];
+      return 1.0 + dx * dx + dy * dy + c[2] * c[2];
     }
-    if (ok && has_skip) return c;
+  }
+}
+
+// normal component of the direction on surface s: which side a point on s is heading into
+double surf_dir(const Prob& P, int s, double x, double y, double ux, double uy, double uz) {
+  const double* c = &P.scoef[3 * s];
+  switch (P.skind[s]) {
+    case OR_PX: return ux;
+    case OR_PY: return uy;
+    case OR_PZ: return uz;
+    default: return (x - c[0]) * ux + (y - c[1]) * uy;
+  }
+}
+
+// The cell a point is in.  When the point was reached by crossing skip_surf, that surface's sense
+// is given (skip_sense) rather than evaluated, only cells bounded by it qualify, and the
+// direction of flight settles the other surfaces:
+//   - a point lying exactly on another surface belongs to the side the particle is moving into
+//     (the + side if it moves along the surface);
+//   - if no cell holds the point -- a crossing next to where two surfaces meet can land a rounding
+//     error outside the neighbouring surface -- a cell that holds it to within 1e-12 of the size
+//     of each surface function's terms is accepted, the first in cell order.
+// Without a crossing, a point on a surface is on its + side.
+int find_cell(const Prob& P, double x, double y, double z, int skip_surf, int skip_sense, double ux,
+              double uy, double uz) {
+  const int passes = skip_surf < 0 ? 1 : 2;
+  for (int pass = 0; pass < passes; ++pass) {
+    for (int c = 0; c < P.n_cell; ++c) {
+      bool ok = true;
+      bool has_skip = skip_surf < 0;
+      for (int i = 0; i < P.nhs[c] && ok; ++i) {
+        int s = P.hs_surf[c * OR_MAX_HS + i], sn = P.hs_sense[c * OR_MAX_HS + i];
+        if (s == skip_surf) {
+          has_skip = true;
+          ok = (sn == skip_sense);
+        } else if (pass == 0) {
+          double f = surf_f(P, s, x, y, z);
+          if (f == 0.0) f = surf_dir(P, s, x, y, ux, uy, uz);
+          ok = sense_ok(f, sn);
+        } else {
+          double f = surf_f(P, s, x, y, z), tol = 1e-12 * surf_terms(P, s, x, y, z);
+          ok = sn > 0 ? f >= -tol : f < tol;
+        }
+      }
+      if (ok && has_skip) return c;
+    }
   }
   return -1;
 }
@@ -488,7 +531,7 @@ Particle source_particle(const Prob& P, uint64_t seed, uint64_t h) {
   q.t = P.t0 + (P.t1 - P.t0) * b3.a;
   q.w = 1.0;
   q.k = 0;
-  q.cell = find_cell(P, q.x, q.y, q.z, -1, 0);
+  q.cell = find_cell(P, q.x, q.y, q.z, -1, 0, 0.0, 0.0, 0.0);
   q.ix = q.iy = q.in_pin = 0;
   if (q.cell >= 0 && P.cmat[q.cell] < 0) lattice_locate(P, q);
   return q;
@@ -618,7 +661,7 @@ void transport(const Prob& P, uint64_t seed, Particle q, std::vector<Particle>& 
           int old_sense = 0;
           for (int i = 0; i < P.nhs[q.cell]; ++i)
             if (P.hs_surf[q.cell * OR_MAX_HS + i] == s) old_sense = P.hs_sense[q.cell * OR_MAX_HS + i];
-          int nc = find_cell(P, q.x, q.y, q.z, s, -old_sense);
+          int nc = find_cell(P, q.x, q.y, q.z, s, -old_sense, q.ux, q.uy, q.uz);
           rec.outcome = 0;
           if (nc < 0) {
             acc.cnt[OR_C_LOST]++;
@@ -767,6 +810,12 @@ double or_dist_cylinder(double x, double y, double ux, double uy, double x0, dou
 
 double or_dist_plane(double pos, double u, double c, int sense) {
   return dist_plane(pos, u, c, sense);
+}
+
+int or_find_cell(const or_problem* p, double x, double y, double z, int skip, int skip_sense, double ux,
+                 double uy, double uz) {
+  Prob P = copy_problem(p);
+  return find_cell(P, x, y, z, skip, skip_sense, ux, uy, uz);
 }
 
 int or_source_sample(const or_problem* p, uint64_t seed, uint64_t h, double out[7], int* g) {

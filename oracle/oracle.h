@@ -127,6 +127,11 @@ double or_dist_cylinder(double x, double y, double ux, double uy, double x0, dou
 double or_dist_plane(double pos, double u, double c, int sense);
 /* source sample of history h: writes x,y,z,ux,uy,uz,t and group; returns cell or -1 */
 int or_source_sample(const or_problem* p, uint64_t seed, uint64_t h, double out[7], int* g);
+/* cell of the point (x, y, z); skip >= 0: the point was reached by crossing surface `skip`,
+ * flying along (ux, uy, uz), and lies on it with sense skip_sense afterwards; -1 if no cell
+ * holds it */
+int or_find_cell(const or_problem* p, double x, double y, double z, int skip, int skip_sense, double ux,
+                 double uy, double uz);
 /* sample a scatter group for material m, group g at uniform u */
 int or_sample_scatter_group(const or_problem* p, int m, int g, double u);
 /* derive the tag of child j produced at event k by a parent */

@@ -338,25 +338,71 @@ __device__ __forceinline__ R surf_f(const Tab<R>& T, int s, R x, R y, R z) {
   }
 }
 
-// first cell containing the point; if skip >= 0 the half-space on surface `skip` is taken to
-// have sense `skip_sense` without evaluating it (the point lies on that surface)
+// rounding scale of surf_f at a point: the magnitude of the terms it subtracts
 template <typename R>
-__device__ int locate_cell(const Tab<R>& T, R x, R y, R z, int skip, int skip_sense) {
-  for (int c = 0; c < T.h->n_cell; ++c) {
-    bool ok = true, seen = skip < 0;
-    const int n = T.nhs[c];
-    for (int i = 0; i < n && ok; ++i) {
-      const int e = T.hs[c * MC_MAX_HALFSPACES + i];
-      const int s = e & 0xFFFF, sn = (e >> 16) ? -1 : 1;
-      if (s == skip) {
-        seen = true;
-        ok = sn == skip_sense;
-      } else {
-        const R f = surf_f(T, s, x, y, z);
-        ok = sn > 0 ? (f >= R(0)) : (f < R(0));
-      }
+__device__ __forceinline__ R surf_scale(const Tab<R>& T, int s, R x, R y, R z) {
+  const R* c = T.scoef + 4 * s;
+  switch (T.skind[s]) {
+    case MC_SURF_PX: return R(1) + fabs(x) + fabs(c[0]);
+    case MC_SURF_PY: return R(1) + fabs(y) + fabs(c[0]);
+    case MC_SURF_PZ: return R(1) + fabs(z) + fabs(c[0]);
+    default: {
+      const R dx = x - c[0], dy = y - c[1];
+      return R(1) + dx * dx + dy * dy + c[2] * c[2];
     }
-    if (ok && seen) return c;
+  }
+}
+
+// normal component of the direction on surface s (the side a point on s is moving into)
+template <typename R>
+__device__ __forceinline__ R surf_dir(const Tab<R>& T, int s, R x, R y, R ux, R uy, R uz) {
+  const R* c = T.scoef + 4 * s;
+  switch (T.skind[s]) {
+    case MC_SURF_PX: return ux;
+    case MC_SURF_PY: return uy;
+    case MC_SURF_PZ: return uz;
+    default: return (x - c[0]) * ux + (y - c[1]) * uy;
+  }
+}
+
+// First cell containing the point.  If skip >= 0 the point was reached by crossing surface
+// `skip`: the half-space on it is taken to have sense `skip_sense` without evaluating it, and the
+// other half-spaces are tested with the direction (ux, uy, uz):
+//  - a point exactly on another surface (f == 0, e.g. a corner where the crossed plane meets a
+//    second one) is on the side the direction points into (the + side when moving along it);
+//    the plain f >= 0 convention could send such a particle back and forth between two cells in
+//    zero-length flights forever;
+//  - if no cell contains the point, one that contains it within the rounding tolerance (1e-5
+//    relative in FP32, 1e-12 in FP64, of surf_scale) is taken, the first in cell order: a
+//    crossing next to a reflecting wall can round to just outside the wall.
+// Without a crossing (skip < 0) a point on a surface is on its + side.
+template <typename R>
+__device__ int locate_cell(const Tab<R>& T, R x, R y, R z, int skip, int skip_sense, R ux = R(0), R uy = R(0),
+                           R uz = R(0)) {
+  const R eps = sizeof(R) == 4 ? R(1e-5) : R(1e-12);
+  for (int pass = 0; pass < (skip >= 0 ? 2 : 1); ++pass) {
+    for (int c = 0; c < T.h->n_cell; ++c) {
+      bool ok = true, seen = skip < 0;
+      const int n = T.nhs[c];
+      for (int i = 0; i < n && ok; ++i) {
+        const int e = T.hs[c * MC_MAX_HALFSPACES + i];
+        const int s = e & 0xFFFF, sn = (e >> 16) ? -1 : 1;
+        if (s == skip) {
+          seen = true;
+          ok = sn == skip_sense;
+        } else {
+          const R f = surf_f(T, s, x, y, z);
+          if (pass == 0) {
+            const R d = f != R(0) ? f : surf_dir(T, s, x, y, ux, uy, uz);
+            ok = sn > 0 ? (d >= R(0)) : (d < R(0));
+          } else {
+            const R tol = eps * surf_scale(T, s, x, y, z);
+            ok = sn > 0 ? (f >= -tol) : (f < tol);
+          }
+        }
+      }
+      if (ok && seen) return c;
+    }
   }
   return -1;
 }

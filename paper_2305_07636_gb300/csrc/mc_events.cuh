@@ -219,7 +219,7 @@ __device__ bool do_surface(const RunParams& P, const Tab<R>& T, Part<R>& p, uint
         const int e = T.hs[c * MC_MAX_HALFSPACES + i];
         if ((e & 0xFFFF) == s) old_sense = (e >> 16) ? -1 : 1;
       }
-      const int nc = locate_cell(T, p.x, p.y, p.z, s, -old_sense);
+      const int nc = locate_cell(T, p.x, p.y, p.z, s, -old_sense, p.ux, p.uy, p.uz);
       if (nc < 0) {
         bump(bc, MC_C_LOST);
         set_status(P, MC_ERR_LOST);

@@ -180,3 +180,36 @@ def test_batch_argument_errors(torch):
     assert e.value.code == mc.MC_ERR_STATE
     for p in ps:
         p.close()
+
+
+@pytest.mark.parametrize("algorithm", ["event", "history"])
+def test_corner_crossing_terminates(torch, algorithm):
+    """FP32 regression: history 218025 of the 2D slab that is problem 32 of the uneven workload
+    (seed 538) flies exactly onto the point where the four cells meet, heading into the cell it
+    is not in.  The corner is resolved by the direction of flight, so the history ends normally
+    instead of crossing back and forth between two cells in zero-length flights until the
+    per-particle watchdog stops it."""
+    prob = P.config5()[0][32]
+    assert prob["name"] == "p32_slab2d"
+    p = mc.Problem(prob)
+    p.run(2, 538, first_history=218024, n_batches=2, algorithm=algorithm)
+    p.wait()
+    c = p.counters()
+    assert conserved(c) and c["flight"] < 10_000, c
+    p.close()
+
+
+def test_full_uneven_workload_runs_clean(torch):
+    """The whole 256-problem workload (about 5.5e7 histories) on three seeds: no problem loses a
+    particle or overflows (this caught crossings next to a reflecting wall that rounded to just
+    outside it), and every problem conserves particles."""
+    probs, nh = P.config5()
+    ps = [mc.Problem(q) for q in probs]
+    hs = [p.h for p in ps]
+    for seed in (5, 6, 105):
+        mc.run_batch(hs, nh, seed)
+        for p, q in zip(ps, probs):
+            p.wait()
+            assert conserved(p.counters()), (seed, q["name"])
+    for p in ps:
+        p.close()

@@ -155,6 +155,36 @@ def test_cylinder_distance_cases():
     assert d(-2.0, 0.0, s, 0.0, 0.0, 0.0, 1.0, 0) == pytest.approx(1.0 / s, abs=1e-14)
 
 
+def test_cell_after_a_crossing_next_to_a_wall():
+    """Four cells of a square cut by interior planes x = L/2 and y = L/2 (surfaces 1 and 4;
+    cells 0: x<h y<h, 1: x>h y<h, 2: x<h y>h, 3: x>h y>h), reflecting walls y = 0 and y = L
+    (3 and 5).  After crossing x = L/2: a point exactly on y = L/2 (the corner) goes to the side
+    the particle is moving into, the + side when it moves along the plane; a point rounded to
+    just outside the wall y = 0 is put in the cell beyond the crossed plane, within 1e-12 of the
+    terms' size; farther out it is lost; away from a crossing no tolerance applies."""
+    prob = P.config5(seed=5, n_problems=3)[0][1]  # the 2D slab kind
+    assert prob["name"].endswith("slab2d")
+    L = prob["surfaces"][2]["coef"][0]
+    h = L / 2
+    fc = oracle.find_cell
+    assert fc(prob, h, 1e-3, 0.0, 1, +1, (0.6, 0.8, 0.0)) == 1   # plainly in the lower right cell
+    assert fc(prob, h, h - 1e-13, 0.0, 1, +1, (0.6, 0.8, 0.0)) == 1
+    assert fc(prob, h, h + 1e-13, 0.0, 1, +1, (0.6, -0.8, 0.0)) == 3
+    # exactly at the corner: the direction decides (this is what ends the back-and-forth of a
+    # particle sitting on the corner between cells 1 and 2 and heading into cell 0)
+    assert fc(prob, h, h, 0.0, 1, -1, (-0.3, -0.9, 0.3)) == 0
+    assert fc(prob, h, h, 0.0, 1, -1, (-0.3, 0.9, 0.3)) == 2
+    assert fc(prob, h, h, 0.0, 4, -1, (-0.3, -0.9, 0.3)) == 0     # the same corner via y = h
+    assert fc(prob, h, h, 0.0, 4, -1, (0.3, -0.9, 0.3)) == 1
+    assert fc(prob, h, h, 0.0, 1, +1, (0.6, 0.0, 0.8)) == 3       # along y = h: the + side
+    assert fc(prob, h, -1e-13, 0.0, 1, +1, (0.6, -0.8, 0.0)) == 1  # rounded past the wall y = 0
+    assert fc(prob, h, L + 1e-13, 0.0, 1, -1, (-0.6, 0.8, 0.0)) == 2  # past y = L, towards -x
+    assert fc(prob, h, -1e-9, 0.0, 1, +1, (0.6, -0.8, 0.0)) == -1   # beyond rounding: lost
+    assert fc(prob, 1.0, -1e-13, 0.0) == -1                  # not a crossing: exact test only
+    assert fc(prob, 1.0, 1e-13, 0.0) == 0
+    assert fc(prob, h, h, 0.0) == 3                          # not a crossing: the + sides
+
+
 # ----------------------------------------------------------------------------- transport closed forms
 
 
