@@ -46,7 +46,34 @@ def workload(name):
         return P.config1(), 10_000_000, "config1: 1-group slab, 1e7 histories"
     if name == "config3":
         return P.config3(), 10_000_000, "config3: 17x17 pin lattice, 7 groups, 1e7 histories"
+    if name == "config5":
+        probs, nh = P.config5()
+        return (probs, nh), sum(nh), (f"config5: {len(probs)} independent problems (1D/2D slab, "
+                                      f"pin lattice; 1-7 groups), {sum(nh)} histories in all, "
+                                      f"{min(nh)}-{max(nh)} per problem")
     raise SystemExit(f"unknown workload {name}")
+
+
+def oracle_batch_sample(probs, nh, threads, target_s, seed):
+    """The oracle over every problem of a batch with its history count scaled by one factor, sized
+    to about target_s seconds; returns (histories, seconds, factor)."""
+    import oracle
+    frac = 1e-3
+    t0 = time.perf_counter()
+    n0 = 0
+    for i, (q, n) in enumerate(zip(probs, nh)):
+        m = max(32, int(n * frac))
+        oracle.run(q, m, seed=seed + i, threads=threads)
+        n0 += m
+    dt = time.perf_counter() - t0
+    frac = min(1.0, frac * target_s / max(dt, 1e-3))
+    t0 = time.perf_counter()
+    n1 = 0
+    for i, (q, n) in enumerate(zip(probs, nh)):
+        m = max(32, int(n * frac))
+        oracle.run(q, m, seed=seed + 1000 + i, threads=threads)
+        n1 += m
+    return n1, time.perf_counter() - t0, frac
 
 
 def peaks():
@@ -125,6 +152,8 @@ def run_reference(args):
     import oracle
     prob, n_full, desc = workload(args.workload)
     threads = os.cpu_count() or 1
+    if args.workload == "config5":
+        return run_reference_batch(args, prob, n_full, desc, threads)
     probe = 20000
     t0 = time.perf_counter()
     oracle.run(prob, probe, seed=1, threads=threads)
@@ -149,6 +178,164 @@ def run_reference(args):
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+def run_reference_batch(args, batch, n_full, desc, threads):
+    probs, nh = batch
+    oracle_batch_sample(probs, nh, threads, 1.0, 7)  # warm-up
+    hist, secs = 0, 0.0
+    frac = 1.0
+    for k in range(args.steps):
+        n, dt, frac = oracle_batch_sample(probs, nh, threads, args.ref_step_seconds / 2, 100 + 10 * k)
+        hist += n
+        secs += dt
+    value = hist / secs
+    sample = (f"every problem of the batch with its histories scaled by {frac:.2e}, FP64 C++ oracle, "
+              f"{threads} threads, problems one after another")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * secs / max(1, args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "sample_fraction": frac},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def pct(a, q):
+    return float(np.percentile(np.asarray(a, dtype=np.float64), q))
+
+
+def bench_batch(args, torch, mc, batch, n_total, desc, world, local):
+    """One step = one batched launch (mc_run_batch) of all problems, after the autotuner has
+    chosen the configuration (untimed).  The sequential comparison runs the same problems, same
+    seeds, one mc_run after another on the same stream."""
+    probs, nh = batch
+    ps = [mc.Problem(q) for q in probs]
+    hs = [p.h for p in ps]
+    stream = torch.cuda.current_stream()
+    seed = 5
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    t0 = time.perf_counter()
+    tuned, tune_ms = mc.batch_tune(hs, nh, seed, None, stream)
+    tune_s = time.perf_counter() - t0
+    for w in range(args.warmup):
+        flush.zero_()
+        mc.run_batch(hs, nh, seed + w, None, stream)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for k in range(args.steps):
+        if not args.no_flush:
+            flush.zero_()
+        ev_s[k].record(stream)
+        mc.run_batch(hs, nh, seed + 100 + k, None, stream)
+        ev_e[k].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    for p in ps:
+        p.wait()
+    step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps)]
+    ms_per_step = sum(step_ms) / len(step_ms)
+    value = n_total / (ms_per_step / 1000.0)
+    # per-problem completion times since the launch started (device clock), untimed extra step
+    wall = mc.run_batch(hs, nh, seed + 100, None, stream, wall=True)
+    cs = [p.counters() for p in ps]
+    flights = sum(c["flight"] for c in cs)
+    scores = sum(c["scores"] for c in cs)
+    kernel_ms = 1000.0 * float(wall.max())
+
+    # sequential: the same problems and seeds, one mc_run each, shortest first
+    order = np.argsort(nh, kind="stable")
+    seq_steps = max(1, min(args.steps, 3))
+    seq_ms, seq_done = [], None
+    for k in range(seq_steps + 1):
+        flush.zero_()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(ps) + 1)]
+        evs[0].record(stream)
+        for j, i in enumerate(order):
+            mc.run(ps[i].h, nh[i], seed + 100 + i, None, stream)
+            evs[j + 1].record(stream)
+        torch.cuda.synchronize()
+        if k == 0:
+            continue  # warm-up
+        done = np.array([evs[0].elapsed_time(evs[j + 1]) for j in range(len(ps))]) / 1000.0
+        seq_ms.append(1000.0 * done[-1])
+        seq_done = np.empty(len(ps))
+        seq_done[order] = done
+    seq_value = n_total / (statistics.mean(seq_ms) / 1000.0)
+
+    peak, peak_kind = peaks()
+    algo_bytes = flights * BYTES_PER_FLIGHT
+    achieved = algo_bytes / (kernel_ms / 1000.0) / 1e9
+    atom_peak = mc.atomic_peak(1 << 24)
+
+    # end to end through the public API with host buffers: create every problem (tables to the
+    # device), one batched launch, read every tally and leakage back, destroy
+    e2e_times, h2d, d2h = [], 0, 0
+    for k in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        qs = [mc.Problem(q) for q in probs]
+        mc.run_batch([q.h for q in qs], nh, seed + 500 + k, None, stream)
+        h2d, d2h = 0, 0
+        for q, pr in zip(qs, probs):
+            for t in range(len(pr["tallies"])):
+                m, e = q.tally(t)
+                d2h += 3 * 8 * m.size
+            lm, ls = q.leakage()
+            d2h += 3 * 8 * lm.size
+            h2d += q.table_bytes()
+        for q in qs:
+            q.close()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_value = n_total / statistics.median(e2e_times) if e2e_times else None
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "histories_per_step": n_total, "tracking": "fp32",
+                   "tally": "int64 fixed point 2^-32", "batches": 32,
+                   "launch": "mc_run_batch (one persistent launch replayed from a CUDA graph)",
+                   "tuned": {"block_size": tuned.block_size, "blocks_per_sm": tuned.blocks_per_sm,
+                             "batch_unit": tuned.batch_unit},
+                   "l2": "flushed (256 MB write) before every timed step"},
+        "batch": {"problems": len(ps), "autotune_s": tune_s, "tuned_launch_ms": tune_ms,
+                  "per_problem_wall_s": {"p50": pct(wall, 50), "p99": pct(wall, 99),
+                                         "max": float(wall.max())},
+                  "sequential": {"value": seq_value, "ms_per_step": statistics.mean(seq_ms),
+                                 "per_problem_wall_s": {"p50": pct(seq_done, 50),
+                                                        "p99": pct(seq_done, 99),
+                                                        "max": float(seq_done.max())},
+                                 "launch": "one mc_run per problem, shortest first, same stream"},
+                  "speedup_vs_sequential": value / seq_value},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_transport_batch<float>", "kernel_ms": kernel_ms,
+                     "algorithmic_bytes": algo_bytes, "peak_kind": peak_kind,
+                     "l2_atomic": {"achieved": scores / (kernel_ms / 1000.0) / 1e9,
+                                   "peak": atom_peak / 1e9, "unit": "G atomics/s",
+                                   "frac": scores / (kernel_ms / 1000.0) / atom_peak,
+                                   "peak_kind": "measured live (mc_atomic_peak, random 64-bit adds)"}},
+        "counters": {"flight": flights, "scores": scores},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+        "step_ms": [round(x, 4) for x in step_ms],
+    }
+    if not args.no_cpu_baseline and world == 1:
+        n, dt, frac = oracle_batch_sample(probs, nh, os.cpu_count() or 1, 10.0, 9)
+        line["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": os.cpu_count() or 1,
+                                "kind": "oracle",
+                                "sample": f"every problem with its histories scaled by {frac:.2e}"}
+    print(json.dumps(line), flush=True)
+    for p in ps:
+        p.close()
 
 
 def main():
@@ -182,6 +369,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     prob, n, desc = workload(args.workload)
+    if args.workload == "config5":
+        if world > 1:
+            raise SystemExit("the batched workload runs on one GPU")
+        return bench_batch(args, torch, mc, prob, n, desc, world, local)
     if args.histories:
         n = args.histories
     seed = 2
