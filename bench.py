@@ -46,6 +46,10 @@ def workload(name):
         return P.config1(), 10_000_000, "config1: 1-group slab, 1e7 histories"
     if name == "config3":
         return P.config3(), 10_000_000, "config3: 17x17 pin lattice, 7 groups, 1e7 histories"
+    if name == "config4":
+        return P.config4(), 1_000_000, ("config4: 200 cm stack of 40 layers (4 seeded materials, Sigma_t "
+                                        "0.5-3, c 0.3-0.95), 7 groups, cosine surface source at x=0, "
+                                        "detector 198-200 cm; learned weight windows")
     if name == "config5":
         probs, nh = P.config5()
         return (probs, nh), sum(nh), (f"config5: {len(probs)} independent problems (1D/2D slab, "
@@ -338,6 +342,136 @@ def bench_batch(args, torch, mc, batch, n_total, desc, world, local):
         p.close()
 
 
+def detector_stats(p, nb=32):
+    """Detector total (tally 0, all bins) per batch: mean and standard error per source history."""
+    b = p.tally_batches(0).reshape(nb, -1).sum(axis=1)
+    return float(b.mean()), float(b.std(ddof=1) / math.sqrt(len(b))), int(np.count_nonzero(b))
+
+
+def learn_windows(mc, P, p, prob, rounds, n0, n_round, seed, extrap=(1.0, 80.0), epochs=3000):
+    """Analog run, then `rounds` refinement rounds: learn the windows from the last run's
+    training tally (tally 1), run with them.  Returns the network and a per-round record."""
+    p.run(n0, seed, tally_mode="fp64")
+    p.wait()
+    net = mc.Mlp(P.mlp_init(seed=4))
+    xs = np.asarray(prob["tallies"][1]["x"])
+    log = []
+    for r in range(rounds):
+        t0 = time.perf_counter()
+        info = mc.ww_learn(p.h, net, 1, epochs, 3e-3, *extrap)
+        learn_s = time.perf_counter() - t0
+        p.run(n_round, seed + 1 + r, tally_mode="fp64", ww_enable=1, bank_capacity=1 << 25)
+        p.wait()
+        m, s, _ = detector_stats(p)
+        mean, err = p.tally(1)
+        ok = ((err < 0.5 * np.abs(mean)) & (mean > 0)).reshape(len(xs) - 1, -1)
+        depth = float(xs[1:][ok.any(axis=1)].max()) if ok.any() else 0.0
+        log.append({"round": r + 1, "resolved_points": info["points"],
+                    "extrapolated_points": info["extrapolated"], "loss": info["loss"],
+                    "learn_s": learn_s, "run_ms": p.timing()[0], "detector": m,
+                    "detector_rel": s / m if m > 0 else None, "resolved_depth_cm": depth})
+    return net, log
+
+
+def timed_fom(torch, mc, p, n, seed, stream, **opts):
+    """One run timed with CUDA events: detector mean, relative error, seconds, FOM."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    o = mc.run_opts(tally_mode="fp64", **opts)
+    e0.record(stream)
+    mc.run(p.h, n, seed, o, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    p.wait()
+    t = e0.elapsed_time(e1) / 1000.0
+    m, s, nz = detector_stats(p)
+    rel = s / m if m > 0 else None
+    return {"histories": n, "seconds": t, "detector": m, "std_err": s, "rel_err": rel,
+            "batches_scoring": nz, "fom": 1.0 / (rel * rel * t) if rel else 0.0,
+            "histories_per_s": n / t}
+
+
+def bench_learned_ww(args, torch, mc):
+    """Learned weight windows on the 200 cm stack: 5 refinement rounds from an analog start,
+    then a measurement run with the final windows; analog and an exponential (non-learned) window
+    table on the same GPU for comparison; the same pipeline on a 10 cm stack that analog can
+    score, for the analog FOM ratio and the bias check."""
+    from paper_2305_07636_gb300 import problems as P
+    stream = torch.cuda.current_stream()
+    prob = P.config4()
+    p = mc.Problem(prob)
+    t0 = time.perf_counter()
+    net, rounds = learn_windows(mc, P, p, prob, 5, 4_000_000, 1_000_000, 4)
+    learn_total = time.perf_counter() - t0
+    for w in range(args.warmup):
+        mc.run(p.h, 200_000, 50 + w, mc.run_opts(tally_mode="fp64", ww_enable=1, bank_capacity=1 << 25), stream)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    steps = [timed_fom(torch, mc, p, 2_000_000, 100 + k, stream, ww_enable=1, bank_capacity=1 << 25)
+             for k in range(args.steps)]
+    clk = clocks.stop()
+    sec = sum(x["seconds"] for x in steps)
+    mean = float(np.mean([x["detector"] for x in steps]))
+    # the steps are independent: pool them (variance of the mean of K estimates)
+    se = math.sqrt(sum(x["std_err"] ** 2 for x in steps)) / len(steps)
+    rel = se / mean if mean > 0 else None
+    learned = {"histories": sum(x["histories"] for x in steps), "seconds": sec, "detector": mean,
+               "std_err": se, "rel_err": rel, "fom": 1.0 / (rel * rel * sec) if rel else 0.0,
+               "seconds_to_5pct": sec * (rel / 0.05) ** 2 if rel else None}
+    c = p.counters()
+    # analog on the same problem: no history reaches the detector
+    n_an = 100_000_000
+    analog = timed_fom(torch, mc, p, n_an, 7, stream)
+    analog["upper_bound_note"] = ("no score in %d histories: fewer than 3 in %d histories reach the "
+                                  "detector at 95%% confidence" % (n_an, n_an))
+    # non-learned windows: one exponential in x for all groups, decay fitted to the analog flux
+    p.run(4_000_000, 4, tally_mode="fp64")
+    fm, fe = p.tally(1)
+    xs = np.asarray(prob["tallies"][1]["x"])
+    tot = fm.reshape(len(xs) - 1, -1).sum(axis=1)
+    ok = tot > 0
+    xc = 0.5 * (xs[:-1] + xs[1:])
+    decay = float(-np.polyfit(xc[ok], np.log(tot[ok]), 1)[0])
+    p.set_weight_windows(P.exponential_ww(prob, decay))
+    try:
+        expo = timed_fom(torch, mc, p, 2_000_000, 9, stream, ww_enable=1, bank_capacity=1 << 25)
+    except mc.McError as e:
+        expo = {"failed": str(e)}
+    expo["decay_per_cm"] = decay
+    p.close()
+    # thin variant: analog scores, so analog FOM and the bias check are measured
+    thin = P.slab_stack(thickness=10.0, n_layers=5, detector=2.0, ww_bin=1.0, name="thin")
+    q = mc.Problem(thin)
+    an = timed_fom(torch, mc, q, 100_000_000, 11, stream)
+    net2, rounds2 = learn_windows(mc, P, q, thin, 5, 4_000_000, 1_000_000, 12)
+    lw = timed_fom(torch, mc, q, 2_000_000, 13, stream, ww_enable=1, bank_capacity=1 << 25)
+    z = (lw["detector"] - an["detector"]) / math.hypot(lw["std_err"], an["std_err"])
+    q.close()
+    net.close()
+    net2.close()
+    value = learned["histories"] / sec
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * sec / len(steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload("config4")[2], "histories_per_step": 2_000_000,
+                   "tracking": "fp32", "tally": "fp64 atomics", "batches": 32,
+                   "windows": "MLP 5-64-64-64-1 (BF16 tensor cores, FP32 accumulate), 5 rounds "
+                              "from a 4e6-history analog run, 1e6 histories per round, "
+                              "extrapolation slope 1.0 over 80 e-folds",
+                   "l2": "inputs (particle banks) larger than L2 between steps"},
+        "fom": {"learned": learned, "analog": analog, "exponential_ww": expo,
+                "thin_10cm": {"analog": an, "learned": lw, "fom_ratio": lw["fom"] / an["fom"] if an["fom"] else None,
+                              "z_learned_vs_analog": z, "rounds": rounds2},
+                "unit": "1/s", "tally": "detector flux, last 2 cm, all groups"},
+        "rounds": rounds, "learning_s": learn_total,
+        "counters": {k: c[k] for k in ("flight", "ww_split", "ww_kill", "scores")},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+        "step_ms": [round(1000 * x["seconds"], 3) for x in steps],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -369,6 +503,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     prob, n, desc = workload(args.workload)
+    if args.workload == "config4":
+        if world > 1:
+            raise SystemExit("the learned-window workload runs on one GPU")
+        return bench_learned_ww(args, torch, mc)
     if args.workload == "config5":
         if world > 1:
             raise SystemExit("the batched workload runs on one GPU")

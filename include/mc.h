@@ -177,11 +177,14 @@ typedef struct {
 } mc_event;
 
 /* Counters summed over a run, in this order.  MC_C_SCORES counts track-length tally updates
- * (one per mesh cell and time bin a flight crosses). */
+ * (one per mesh cell and time bin a flight crosses).  MC_C_WW_HELD counts weight-window splits
+ * not made because the particle store was more than half full: a split is optional (the particle
+ * keeps its weight, which is unbiased), so bad windows slow a run down instead of overflowing
+ * it; a run with held splits is no longer independent of the GPU's schedule. */
 typedef enum {
   MC_C_SOURCE = 0, MC_C_SECONDARY, MC_C_CAPTURE, MC_C_PRODUCTION, MC_C_LEAK, MC_C_CENSUS,
   MC_C_LOST, MC_C_FLIGHT, MC_C_COLLISION, MC_C_SCATTER, MC_C_SURFACE, MC_C_REFLECT,
-  MC_C_WW_SPLIT, MC_C_WW_KILL, MC_C_ITERATIONS, MC_C_SCORES, MC_NCOUNTERS
+  MC_C_WW_SPLIT, MC_C_WW_KILL, MC_C_ITERATIONS, MC_C_SCORES, MC_C_WW_HELD, MC_NCOUNTERS
 } mc_counter;
 
 /* ------------------------------------------------------------------------- entry points */
@@ -277,12 +280,25 @@ int mc_mlp_train(mc_mlp* m, const float* x, const float* target, const float* wt
  *   1. from mesh tally `tally_id` (its time bins summed) take the flux phi of every (cell, group)
  *      resolved to a relative error below 0.5; target = log(phi / phi_ref), phi_ref = the flux of the
  *      source point's cell in the source's main group, weight = 1 / relative variance (capped);
- *   2. train the network on these targets on the GPU (`epochs` Adam steps at `lr`);
- *   3. evaluate it on every (cell, group) of that tally's spatial mesh and set the window centres
+ *   2. if extrap_slope > 0, continue the windows past the resolved region along x: for every x line
+ *      of the mesh (fixed y, z cell) and each group with r >= 3 resolved cells, fit a
+ *      least-squares line to the targets of its outermost max(3, r/4) resolved cells; take the
+ *      flattest of these slopes that fall away from the resolved region as the line's common
+ *      slope (deep in a medium all groups decay at the common asymptotic rate); from each group's
+ *      outermost resolved cell, lower the target at extrap_slope (in (0, 1]) times that slope until
+ *      it has fallen by extrap_efolds, then hold it to the end of the line.  These extra targets
+ *      have weight 4 (a 50% relative error) and are clamped at -700.  The windows then reach past
+ *      the depth the last run resolved, so that each round resolves deeper, and extrap_efolds
+ *      bounds how far a wrong slope can take them from the flux.  (A table whose splitting
+ *      overflows the bank shows as MC_ERR_BANK_FULL on the next run: learn again with less.)
+ *   3. train the network on these targets on the GPU (`epochs` Adam steps at `lr`);
+ *   4. evaluate it on every (cell, group) of that tally's spatial mesh and set the window centres
  *      w_c = phi_ref-normalised exp(net) as the problem's weight-window table (the forward-flux
  *      weight windows of the MAGIC method, learned instead of tabulated).
- * info (host, may be NULL) receives {training points, final loss, target scale, phi_ref}. */
-int mc_ww_learn(mc_problem* p, mc_mlp* m, int tally_id, int epochs, float lr, double info[4]);
+ * info (host, may be NULL) receives {resolved training points, final loss, target scale, phi_ref,
+ * extrapolated training points}. */
+int mc_ww_learn(mc_problem* p, mc_mlp* m, int tally_id, int epochs, float lr, double extrap_slope,
+                double extrap_efolds, double info[5]);
 
 /* Bytes of sampling, geometry and tally tables that mc_problem_create copied to the device
  * (both tracking precisions); 0 for NULL. */

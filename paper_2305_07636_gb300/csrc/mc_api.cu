@@ -1238,10 +1238,13 @@ int bin_of_point(const std::vector<double>& e, double v) {
 }
 }  // namespace
 
-extern "C" int mc_ww_learn(mc_problem* p, mc_mlp* m, int tally_id, int epochs, float lr, double info[4]) {
+extern "C" int mc_ww_learn(mc_problem* p, mc_mlp* m, int tally_id, int epochs, float lr, double extrap_slope,
+                           double extrap_efolds, double info[5]) {
   g_err.clear();
   if (!p || !m) return fail(MC_ERR_INVALID, "NULL argument");
   if (tally_id < 0 || tally_id >= p->n_tally) return fail(MC_ERR_INVALID, "tally_id must name a mesh tally");
+  if (!(extrap_slope >= 0.0 && extrap_slope <= 1.0)) return fail(MC_ERR_INVALID, "extrap_slope outside [0,1]");
+  if (!(extrap_efolds >= 0.0 && extrap_efolds <= 700.0)) return fail(MC_ERR_INVALID, "extrap_efolds outside [0,700]");
   int64_t shp[5];
   int rc = mc_tally_shape(p, tally_id, shp);
   if (rc != MC_OK) return rc;
@@ -1264,25 +1267,111 @@ extern "C" int mc_ww_learn(mc_problem* p, mc_mlp* m, int tally_id, int epochs, f
   if (!(phi_ref > 0.0)) return fail(MC_ERR_STATE, "the source cell of tally %d has no flux yet", tally_id);
   std::vector<float> xs, tg, wt, xall;
   double scale = 1.0;
+  auto point = [&](int ix, int iy, int iz, int g, float* pt) {
+    pt[0] = (float)scaled_centre(T.e[0], ix);
+    pt[1] = (float)scaled_centre(T.e[1], iy);
+    pt[2] = (float)scaled_centre(T.e[2], iz);
+    pt[3] = G > 1 ? (float)(2.0 * g / (G - 1) - 1.0) : 0.f;
+    pt[4] = 0.f;
+  };
+  auto add = [&](const float* pt, double target, double w) {
+    xs.insert(xs.end(), pt, pt + 5);
+    tg.push_back((float)target);
+    wt.push_back((float)w);
+    scale = std::max(scale, std::fabs(target));
+  };
+  int n_extra = 0;
   for (int iz = 0; iz < nz; ++iz)
-    for (int iy = 0; iy < ny; ++iy)
-      for (int ix = 0; ix < nx; ++ix)
-        for (int g = 0; g < G; ++g) {
-          const float pt[5] = {(float)scaled_centre(T.e[0], ix), (float)scaled_centre(T.e[1], iy),
-                               (float)scaled_centre(T.e[2], iz), G > 1 ? (float)(2.0 * g / (G - 1) - 1.0) : 0.f, 0.f};
+    for (int iy = 0; iy < ny; ++iy) {
+      // resolved cells of every group's x line; then one common slope per side: the flattest of
+      // the groups' fitted slopes (deep in a medium every group decays at the common asymptotic
+      // rate, which no group's near-source rate undercuts)
+      std::vector<std::vector<int>> rix(G);
+      std::vector<std::vector<double>> rt(G);
+      for (int g = 0; g < G; ++g)
+        for (int ix = 0; ix < nx; ++ix) {
+          float pt[5];
+          point(ix, iy, iz, g, pt);
           xall.insert(xall.end(), pt, pt + 5);
           const size_t c = (((size_t)iz * ny + iy) * nx + ix) * G + g;
           if (!(phi[c] > 0.0)) continue;
           const double rel = std::sqrt(var[c]) / phi[c];
           if (!(rel < 0.5)) continue;
           const double target = std::log(phi[c] / phi_ref);
-          xs.insert(xs.end(), pt, pt + 5);
-          tg.push_back((float)target);
-          wt.push_back((float)std::min(1.0 / std::max(rel * rel, 1e-12), 1e4));
-          scale = std::max(scale, std::fabs(target));
+          add(pt, target, std::min(1.0 / std::max(rel * rel, 1e-12), 1e4));
+          rix[g].push_back(ix);
+          rt[g].push_back(target);
         }
+      if (!(extrap_slope > 0.0)) continue;
+      for (int side = 0; side < 2; ++side) {
+        // least-squares line through the k outermost resolved cells of each group on this side
+        std::vector<double> fa(G, 0.0), fb(G, 0.0);
+        std::vector<char> fit(G, 0);
+        double common = 0.0;
+        bool any = false;
+        for (int g = 0; g < G; ++g) {
+          const int nr = (int)rix[g].size();
+          if (nr < 3) continue;
+          const int k = std::max(3, nr / 4);
+          double sx = 0, sy = 0, sxx = 0, sxy = 0;
+          bool finite = true;
+          for (int j = 0; j < k; ++j) {
+            const int q = side ? nr - 1 - j : j;
+            const double xc = 0.5 * (T.e[0][rix[g][q]] + T.e[0][rix[g][q] + 1]);
+            finite = finite && std::isfinite(xc);
+            sx += xc;
+            sy += rt[g][q];
+            sxx += xc * xc;
+            sxy += xc * rt[g][q];
+          }
+          const double den = k * sxx - sx * sx;
+          if (!finite || !(den > 0.0) || !std::isfinite(den)) continue;
+          const double a = (k * sxy - sx * sy) / den;
+          if (side ? !(a < 0.0) : !(a > 0.0)) continue;  // not falling away from the resolved cells
+          fa[g] = a;
+          fb[g] = (sy - a * sx) / k;
+          fit[g] = 1;
+          common = any ? (side ? std::max(common, a) : std::min(common, a)) : a;
+          any = true;
+        }
+        if (!any) continue;
+        // each group continues from its own outermost resolved cell with extrap_slope times the
+        // common slope until the windows have fallen by extrap_efolds, then stays constant
+        const double slope = extrap_slope * common;
+        for (int g = 0; g < G; ++g) {
+          if (!fit[g]) continue;
+          const int nr = (int)rix[g].size();
+          const int edge = side ? rix[g][nr - 1] : rix[g][0];
+          const double xe = 0.5 * (T.e[0][edge] + T.e[0][edge + 1]);
+          const double ye = fa[g] * xe + fb[g];
+          const int from = side ? edge + 1 : 0, to = side ? nx : edge;
+          for (int ix = from; ix < to; ++ix) {
+            const double xc = 0.5 * (T.e[0][ix] + T.e[0][ix + 1]);
+            if (!std::isfinite(xc)) continue;
+            const double drop = std::min(std::fabs(slope * (xc - xe)), extrap_efolds);
+            float pt[5];
+            point(ix, iy, iz, g, pt);
+            add(pt, std::max(ye - drop, -700.0), 4.0);  // the weight of a 50% relative error
+            ++n_extra;
+          }
+        }
+      }
+    }
+  // xall is in [z][y][g][x] order here; the window table wants [z][y][x][g]
+  {
+    std::vector<float> re(xall.size());
+    for (int iz = 0; iz < nz; ++iz)
+      for (int iy = 0; iy < ny; ++iy)
+        for (int g = 0; g < G; ++g)
+          for (int ix = 0; ix < nx; ++ix) {
+            const size_t from = ((((size_t)iz * ny + iy) * G + g) * nx + ix) * 5;
+            const size_t to = ((((size_t)iz * ny + iy) * nx + ix) * G + g) * 5;
+            std::copy(xall.begin() + from, xall.begin() + from + 5, re.begin() + to);
+          }
+    xall.swap(re);
+  }
   const int n = (int)tg.size();
-  if (n < 2) return fail(MC_ERR_STATE, "tally %d resolves fewer than two bins", tally_id);
+  if (n - n_extra < 2) return fail(MC_ERR_STATE, "tally %d resolves fewer than two bins", tally_id);
   if (n > (1 << 20)) return fail(MC_ERR_INVALID, "too many training points");
   double wsum = 0.0;
   for (float w : wt) wsum += w;
@@ -1326,10 +1415,11 @@ extern "C" int mc_ww_learn(mc_problem* p, mc_mlp* m, int tally_id, int epochs, f
   p->ww_n[2] = nz;
   p->ww_set = 1;
   if (info) {
-    info[0] = n;
+    info[0] = n - n_extra;
     info[1] = loss;
     info[2] = scale;
     info[3] = phi_ref;
+    info[4] = n_extra;
   }
   return MC_OK;
 }

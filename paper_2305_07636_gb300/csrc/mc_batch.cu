@@ -103,7 +103,10 @@ __global__ void __launch_bounds__(256, MINB)
   const int n_items = (int)bh->n_items;
   if (lane == 0) atomicMin(&bh->t0, globaltimer());
   if (lane < MC_NCOUNTERS) bc->c[lane] = 0u;
-  if (lane == 0) *sc = 0ull;
+  if (lane == 0) {
+    *sc = 0ull;
+    bc->hold_at = cap / 2;  // weight-window splits are held while the warp's stack is half full
+  }
 
   unsigned long long u0 = 0;
   if (lane == 0) u0 = atomicAdd(&bh->next_unit, 1ull);

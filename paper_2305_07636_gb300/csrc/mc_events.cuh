@@ -82,8 +82,12 @@ __device__ void log_event(const RunParams& P, const Tab<R>& T, const Part<R>& p,
 }
 
 // ------------------------------------------------------------------------------------------ counters
-struct BlockCounters {
+// per-CTA (per-warp in the batched kernel) event counters, and the birth count above which a
+// weight-window split is held (half the birth store, less the births that wait to be stored again
+// in this iteration)
+struct __align__(16) BlockCounters {
   unsigned int c[MC_NCOUNTERS];
+  unsigned long long hold_at;
 };
 __device__ __forceinline__ void bump(BlockCounters* bc, int i, unsigned v = 1u) { atomicAdd(&bc->c[i], v); }
 
@@ -117,6 +121,12 @@ __device__ bool weight_window(const RunParams& P, const Tab<R>& T, Part<R>& p, u
   const double wc = __ldg(P.ww_center + ((size_t)(iz * P.ww_ny + iy) * P.ww_nx + ix) * T.G + pk_g(p.pk));
   if (!(wc > 0.0)) return true;
   if (p.w > P.ww_upper * wc) {
+    // a split is optional: while the birth store is more than half full the particle keeps its
+    // weight (unbiased), so windows far below the flux cannot overflow the store
+    if (*reinterpret_cast<volatile unsigned long long*>(bcount) >= bc->hold_at) {
+      bump(bc, MC_C_WW_HELD);
+      return true;
+    }
     int n = (int)ceil(p.w / wc);
     if (n > P.ww_split_max) n = P.ww_split_max;
     p.w = p.w / n;

@@ -79,6 +79,10 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
       break;
     }
     const bool drain = P.history_mode || (nSrc == left && W <= P.drain_threshold);
+    // splits are held once the births of this iteration, with the nB - nBt waiting births that
+    // are stored again below, would fill half the birth store
+    if (threadIdx.x == 0) bc.hold_at = P.cap_b / 2 > nB - nBt ? P.cap_b / 2 - (nB - nBt) : 0ull;
+    __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       ctl->front[old] = 0ull;
       ctl->back[old] = 0ull;

@@ -27,7 +27,7 @@ MC_FP32, MC_FP64 = 0, 1
 MC_TALLY_FIXED64, MC_TALLY_FP64 = 0, 1
 COUNTER_NAMES = ["source", "secondary", "capture", "production", "leak", "census", "lost",
                  "flight", "collision", "scatter", "surface", "reflect", "ww_split", "ww_kill",
-                 "iterations", "scores"]
+                 "iterations", "scores", "ww_held"]
 NCOUNTERS = len(COUNTER_NAMES)
 KIND = {"PX": 0, "PY": 1, "PZ": 2, "CZ": 3}
 BC = {"interior": 0, "vacuum": 1, "reflect": 2}
@@ -140,7 +140,8 @@ SIGNATURES = {
                                    C.c_void_p, C.c_void_p]),
     "mc_mlp_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_float,
                                C.c_void_p, C.c_void_p]),
-    "mc_ww_learn": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_float, DP]),
+    "mc_ww_learn": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_float, C.c_double,
+                              C.c_double, DP]),
     "mc_run_static": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.POINTER(mc_run_opts),
                                 C.c_void_p, C.c_void_p, C.c_void_p]),
     "mc_run_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_uint64), C.c_uint64,
@@ -534,10 +535,13 @@ class Mlp:
             pass
 
 
-def ww_learn(problem_h: int, mlp: "Mlp", tally_id: int, epochs: int, lr: float) -> dict:
-    """mc_ww_learn: one learning round of the weight windows from the problem's last run."""
-    info = np.zeros(4)
+def ww_learn(problem_h: int, mlp: "Mlp", tally_id: int, epochs: int, lr: float,
+             extrap_slope: float = 0.0, extrap_efolds: float = 0.0) -> dict:
+    """mc_ww_learn: one learning round of the weight windows from the problem's last run
+    (extrap_slope > 0 continues the windows past the resolved depth)."""
+    info = np.zeros(5)
     check(lib().mc_ww_learn(C.c_void_p(problem_h), C.c_void_p(mlp.h), int(tally_id), int(epochs),
-                            float(lr), info.ctypes.data_as(DP)))
+                            float(lr), float(extrap_slope), float(extrap_efolds),
+                            info.ctypes.data_as(DP)))
     return {"points": int(info[0]), "loss": float(info[1]), "scale": float(info[2]),
-            "phi_ref": float(info[3])}
+            "phi_ref": float(info[3]), "extrapolated": int(info[4])}

@@ -318,7 +318,9 @@ def slab_stack(thickness=200.0, n_layers=40, G=7, seed=4, detector=2.0, ww_bin=5
 
 
 def config4(seed=4, thickness=200.0):
-    return slab_stack(thickness=thickness, seed=seed)
+    """200 cm deep-penetration stack of 40 layers (4 seeded materials), detector on the last 2 cm,
+    window-training mesh of 2 cm cells."""
+    return slab_stack(thickness=thickness, seed=seed, ww_bin=2.0)
 
 
 def config5(seed=5, n_problems=256, n_lo=1e4, n_hi=1e6):

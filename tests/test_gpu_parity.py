@@ -331,3 +331,30 @@ def test_weight_window_fp64_replay_and_unbiasedness(torch):
     mo, so = a.tallies[1]
     check_z(combined_z(mg, sg, mo, so), 20)
     p.close()
+
+
+def test_held_splits_stay_unbiased_and_bad_windows_cannot_overflow(torch):
+    """A weight-window split is optional: while the particle store is more than half full it is
+    held (the particle keeps its weight).  (1) The same windows (exp(-1.1 x), close to the flux
+    of this stack) with a store of 1024 particles, where splits are held, and with a large store,
+    where none are: the detector tallies agree within 4 sigma.  (2) Windows falling far faster
+    than the flux (exp(-2.5 x)) with a store of 4096 particles: the run ends without overflow and
+    conserves particles.  (Such windows make the estimate heavy-tailed, so its mean is not tested.)"""
+    prob = P.slab_stack(thickness=10.0, n_layers=5, detector=2.0, ww_bin=1.0, name="thin")
+    p = mc.Problem(prob)
+    p.set_weight_windows(P.exponential_ww(prob, decay=1.1))
+    p.run(400_000, 3, tally_mode="fp64", ww_enable=1, bank_capacity=1 << 22)
+    c = p.counters()
+    assert c["ww_held"] == 0 and c["ww_split"] > 0
+    mr, sr = p.tally(0)
+    p.run(400_000, 4, tally_mode="fp64", ww_enable=1, bank_capacity=1 << 10)
+    c = p.counters()
+    assert c["ww_held"] > 0 and conserved(c), c
+    mh, sh = p.tally(0)
+    z = (mh.sum() - mr.sum()) / np.hypot(np.sqrt((sh ** 2).sum()), np.sqrt((sr ** 2).sum()))
+    assert abs(z) < 4.0, (mh.sum(), mr.sum(), z)
+    p.set_weight_windows(P.exponential_ww(prob, decay=2.5))
+    p.run(4_000, 5, tally_mode="fp64", ww_enable=1, bank_capacity=1 << 12)
+    c = p.counters()
+    assert c["ww_held"] > 0 and conserved(c), c
+    p.close()
