@@ -569,7 +569,7 @@ def main():
     achieved = algo_bytes / (tr_ms / 1000.0) / 1e9
     # tally scoring against the L2 atomic roofline, measured live on the tally's footprint
     tally_elems = sum(int(np.prod(mc.tally_shape(p.h, t))) for t in range(len(prob["tallies"]) + 1))
-    atom_peak = mc.atomic_peak(max(1, tally_elems * opts.n_batches * 16))
+    atom_peak = mc.atomic_peak(min(1 << 27, max(1, tally_elems * opts.n_batches * 16)))
     atom_rate = c["scores"] / (tr_ms / 1000.0)
 
     # end to end through the public API with host buffers

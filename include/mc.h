@@ -146,7 +146,10 @@ typedef struct {
   int n_batches;          /* statistical batches, >= 2 (default 32) */
   uint64_t bank_capacity; /* particles in flight (0 = library default) */
   int block_size;         /* threads per CTA (0 = autotuned default) */
-  int blocks_per_sm;      /* CTAs per SM (0 = as many as fit) */
+  int blocks_per_sm;      /* CTAs per SM: 2 selects the 128-register build of the kernel (2 CTAs of
+                             256 per SM), another value caps the 80-register build (3 per SM);
+                             0 = the 128-register build when a tally has several time bins, else
+                             the 80-register build, as many CTAs as fit */
   uint64_t max_iterations;/* watchdog: event iterations before MC_ERR_TIMEOUT (0 = 2^20) */
   int aggregate_atomics;  /* 1 = warp-aggregated tally atomics, 0 = one atomic per score,
                              -1 = auto (default): aggregate a small tally that is not striped */

@@ -23,9 +23,10 @@
 
 namespace mcgb {
 template <typename R>
-cudaError_t launch_transport(const RunParams& P, int grid, int block, size_t smem, cudaStream_t s, bool wide);
+cudaError_t launch_transport(const RunParams& P, int grid, int block, size_t smem, cudaStream_t s, bool wide,
+                             bool deal);
 template <typename R>
-cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide);
+cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide, bool deal);
 cudaError_t launch_batch_stats(const void* tally, int fp64, uint64_t bins, int nb, int stripes,
                                uint64_t n_hist, void* out, cudaStream_t s);
 cudaError_t launch_philox(uint64_t seed, const uint4* ctr, uint4* out, uint64_t n, cudaStream_t s);
@@ -382,6 +383,7 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
     D.o_etf = B.put(etf);
     D.bin_offset = off;
     D.n_bins = T.nx * T.ny * T.nz * G * T.nt;
+    D.deal = deals_time_pieces(T.nx, T.ny, T.nz, T.nt) ? 1 : 0;
     off += D.n_bins;
   }
   H.leak_offset = off;
@@ -476,6 +478,7 @@ int mc_problem_create(const mc_problem_desc* d, mc_problem** out) {
     h.n[3] = T.nt;
     const double* e[4] = {T.x, T.y, T.z, T.t};
     for (int k = 0; k < 4; ++k) h.e[k].assign(e[k], e[k] + h.n[k] + 1);
+    p->deal = p->deal || deals_time_pieces(T.nx, T.ny, T.nz, T.nt);
     p->tallies.push_back(h);
   }
   for (int i = 0; i < 3; ++i) p->src_center[i] = 0.5 * (d->source.lo[i] + d->source.hi[i]);
@@ -615,10 +618,13 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   // tables + per-warp flight queues (64 slots) + per-warp tally staging (128 x 12 B)
   const size_t smem = P.blob_bytes + (size_t)(block / 32) * (64 * 16 * lanes + 128 * 12);
   int per_sm = 0;
-  // blocks_per_sm == 2 selects the 128-register build of the kernel, otherwise the 80-register one
-  const bool wide = o.blocks_per_sm == 2;
-  CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm, wide)
-          : transport_occupancy<float>(block, smem, &per_sm, wide));
+  // blocks_per_sm == 2 selects the 128-register build of the kernel, any other explicit value the
+  // 80-register one; 0 takes the 128-register build when a tally deals its time pieces out over the
+  // warp (that walk needs the registers) and the 80-register build otherwise
+  const bool deal = p->deal;
+  const bool wide = o.blocks_per_sm == 2 || (o.blocks_per_sm == 0 && deal);
+  CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm, wide, deal)
+          : transport_occupancy<float>(block, smem, &per_sm, wide, deal));
   if (per_sm < 1) return fail(MC_ERR_CUDA, "transport kernel does not fit on an SM (block %d, smem %zu)", block, smem);
   if (o.blocks_per_sm > 0 && o.blocks_per_sm < per_sm) per_sm = o.blocks_per_sm;
   int sms = 0;
@@ -626,7 +632,8 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   const int grid = sms * per_sm;
   P.drain_threshold = o.drain_threshold ? o.drain_threshold : (uint64_t)2 * grid * block;
   CK(cudaEventRecord(p->ev[0], s));
-  CK(fp64 ? launch_transport<double>(P, grid, block, smem, s, wide) : launch_transport<float>(P, grid, block, smem, s, wide));
+  CK(fp64 ? launch_transport<double>(P, grid, block, smem, s, wide, deal)
+          : launch_transport<float>(P, grid, block, smem, s, wide, deal));
   CK(cudaEventRecord(p->ev[1], s));
   CK(launch_batch_stats(P.tally, P.tally_fp64, bins, nb, (int)stripes, n_histories, p->d_stats.ptr, s));
   CK(cudaEventRecord(p->ev[2], s));
@@ -1070,18 +1077,19 @@ extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t
   CK(cudaMemsetAsync(base + off_tally, 0, tally_bytes, s));
   const int block = o.block_size ? o.block_size : 256;
   const size_t smem = P.blob_bytes + (size_t)(block / 32) * (64 * 16 * lanes + 128 * 12);
-  const bool wide = o.blocks_per_sm == 2;
   int per_sm = 0;
-  CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm, wide)
-          : transport_occupancy<float>(block, smem, &per_sm, wide));
+  const bool deal = p->deal;
+  const bool wide = o.blocks_per_sm == 2 || (o.blocks_per_sm == 0 && deal);
+  CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm, wide, deal)
+          : transport_occupancy<float>(block, smem, &per_sm, wide, deal));
   if (per_sm < 1) return fail(MC_ERR_CUDA, "transport kernel does not fit on an SM (block %d, smem %zu)", block, smem);
   if (o.blocks_per_sm > 0 && o.blocks_per_sm < per_sm) per_sm = o.blocks_per_sm;
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int grid = sms * per_sm;
   P.drain_threshold = o.drain_threshold ? o.drain_threshold : (uint64_t)2 * grid * block;
-  CK(fp64 ? launch_transport<double>(P, grid, block, smem, s, wide)
-          : launch_transport<float>(P, grid, block, smem, s, wide));
+  CK(fp64 ? launch_transport<double>(P, grid, block, smem, s, wide, deal)
+          : launch_transport<float>(P, grid, block, smem, s, wide, deal));
   CK(launch_batch_stats(P.tally, P.tally_fp64, bins, nb, 1, n_histories, base + off_stats, s));
   unsigned g = (unsigned)std::min<uint64_t>((bins + 255) / 256, 1024);
   k_static_finalize<<<g ? g : 1, 256, 0, s>>>((const Ctl*)base, base + off_stats, P.tally_fp64, bins,

@@ -81,7 +81,7 @@ __device__ __forceinline__ void warp_copy16(void* dst, const void* src, size_t b
   for (size_t i = lane; i < bytes / 16; i += 32) d[i] = __ldg(s + i);
 }
 
-template <typename R, int MINB>
+template <typename R, int MINB, bool DEAL>
 __global__ void __launch_bounds__(256, MINB)
     k_transport_batch(BatchHeader* bh, const BatchItem* items, unsigned long long* t_done, uint4* stacks,
                       int slot_bytes) {
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(256, MINB)
       uint32_t pend = PEND_NONE;
       Hit hit;
       const bool flies = have && flight_plan(P, T, p, bc, l, pend, hit);
-      score_segment_warp(T, P, p, l, (uint64_t)(p.elem >> 16) * bins, flies, stage, scored);
+      score_segment_warp<R, DEAL>(T, P, p, l, (uint64_t)(p.elem >> 16) * bins, flies, stage, scored);
       if (flies) {
         bool alive = flight_finish(P, T, p, bc, l, pend, hit);
         if (alive && p.k + 1 >= P.max_iter) {
@@ -278,11 +278,16 @@ __global__ void k_batch_stats_multi(const BatchHeader* bh, const BatchItem* item
   }
 }
 
-// the two register budgets of the batched kernel (FP64 tracking has only the wide one)
+// the two register budgets of the batched kernel (FP64 tracking has only the wide one), each with
+// and without the time-bin dealing of the scoring walk
 template <typename R>
-static const void* batch_fn(bool wide) {
-  if constexpr (sizeof(R) == 8) return (const void*)k_transport_batch<R, 2>;
-  else return wide ? (const void*)k_transport_batch<R, 2> : (const void*)k_transport_batch<R, 3>;
+static const void* batch_fn(bool wide, bool deal) {
+  if constexpr (sizeof(R) == 8)
+    return deal ? (const void*)k_transport_batch<R, 2, true> : (const void*)k_transport_batch<R, 2, false>;
+  else if (deal)
+    return wide ? (const void*)k_transport_batch<R, 2, true> : (const void*)k_transport_batch<R, 3, true>;
+  else
+    return wide ? (const void*)k_transport_batch<R, 2, false> : (const void*)k_transport_batch<R, 3, false>;
 }
 
 }  // namespace mcgb
@@ -299,7 +304,7 @@ struct BatchConfig {
 // list and header (uploaded by every call from pinned staging), per-problem completion times,
 // and the warp stacks.
 struct BatchPlan {
-  int dev = 0, n = 0, block = 0, wide = 0, fp64 = 0, grid = 0;
+  int dev = 0, n = 0, block = 0, wide = 0, fp64 = 0, deal = 0, grid = 0;
   size_t slot_bytes = 0, smem = 0;
   uint64_t stack_cap = 0;
   DevBuf d_items, d_head, d_tdone, d_stacks;
@@ -334,8 +339,8 @@ constexpr size_t kMaxPlans = 4;
 constexpr uint64_t kDefaultStack = 2048;
 
 template <typename R>
-cudaError_t batch_occupancy(int block, size_t smem, bool wide, int* per_sm) {
-  const void* f = batch_fn<R>(wide);
+cudaError_t batch_occupancy(int block, size_t smem, bool wide, bool deal, int* per_sm) {
+  const void* f = batch_fn<R>(wide, deal);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -351,7 +356,7 @@ int capture(BatchPlan* pl) {
   unsigned long long* tdone = (unsigned long long*)pl->d_tdone.ptr;
   uint4* stacks = (uint4*)pl->d_stacks.ptr;
   int slot = (int)pl->slot_bytes;
-  const void* f = pl->fp64 ? batch_fn<double>(pl->wide) : batch_fn<float>(pl->wide);
+  const void* f = pl->fp64 ? batch_fn<double>(pl->wide, pl->deal) : batch_fn<float>(pl->wide, pl->deal);
   void* args[] = {&bh, &items, &tdone, &stacks, &slot};
   CK(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
   k_batch_clear<<<dim3((unsigned)pl->n, 16), 256, 0, pl->cap_stream>>>(bh, items, tdone);
@@ -376,10 +381,11 @@ int capture(BatchPlan* pl) {
 
 // The plan of a launch shape, created (and its graph captured) on first use.  Caller holds
 // g_batch_mu.
-int get_plan(int dev, int n, const BatchConfig& c, int fp64, size_t slot, uint64_t stack_cap, BatchPlan** out) {
+int get_plan(int dev, int n, const BatchConfig& c, int fp64, int deal, size_t slot, uint64_t stack_cap,
+             BatchPlan** out) {
   for (auto& pl : g_plans)
     if (pl->dev == dev && pl->n == n && pl->block == c.block && pl->wide == c.wide && pl->fp64 == fp64 &&
-        pl->slot_bytes == slot && pl->stack_cap == stack_cap) {
+        pl->deal == deal && pl->slot_bytes == slot && pl->stack_cap == stack_cap) {
       pl->last_use = ++g_plan_clock;
       *out = pl.get();
       return MC_OK;
@@ -399,13 +405,14 @@ int get_plan(int dev, int n, const BatchConfig& c, int fp64, size_t slot, uint64
   pl->block = c.block;
   pl->wide = c.wide;
   pl->fp64 = fp64;
+  pl->deal = deal;
   pl->slot_bytes = slot;
   pl->stack_cap = stack_cap;
   const size_t wb = fp64 ? batch_warp_bytes<double>(slot) : batch_warp_bytes<float>(slot);
   pl->smem = (size_t)(c.block / 32) * wb;
   int per_sm = 0;
-  CK(fp64 ? batch_occupancy<double>(c.block, pl->smem, c.wide, &per_sm)
-          : batch_occupancy<float>(c.block, pl->smem, c.wide, &per_sm));
+  CK(fp64 ? batch_occupancy<double>(c.block, pl->smem, c.wide, deal, &per_sm)
+          : batch_occupancy<float>(c.block, pl->smem, c.wide, deal, &per_sm));
   if (per_sm < 1)
     return fail(MC_ERR_INVALID, "batched kernel does not fit on an SM (block %d, %zu B shared memory)", c.block,
                 pl->smem);
@@ -495,8 +502,10 @@ int mc_run_batch(mc_problem* const* ps, int n, const uint64_t* n_hist, uint64_t 
       return fail(MC_ERR_INVALID, "a problem appears twice in the batch");
   }
   size_t slot = 0;
+  int deal = 0;  // some problem has a tally whose time pieces are dealt out over the warp
   for (int i = 0; i < n; ++i) {
     mc_problem* p = ps[i];
+    deal = deal || p->deal;
     if (!p) return fail(MC_ERR_INVALID, "problem %d is NULL", i);
     if (p->dev != dev) return fail(MC_ERR_STATE, "problem %d was created on device %d, current is %d", i, p->dev, dev);
     if (n_hist[i] < (uint64_t)nb) return fail(MC_ERR_INVALID, "problem %d: need at least n_batches histories", i);
@@ -532,7 +541,7 @@ int mc_run_batch(mc_problem* const* ps, int n, const uint64_t* n_hist, uint64_t 
 
   std::lock_guard<std::mutex> lk(g_batch_mu);
   BatchPlan* pl = nullptr;
-  rc = get_plan(dev, n, c, fp64, slot, stack_cap, &pl);
+  rc = get_plan(dev, n, c, fp64, deal, slot, stack_cap, &pl);
   if (rc != MC_OK) return rc;
   CK(cudaEventSynchronize(pl->uploaded));  // the staging buffers are free again
   uint64_t units = 0;

@@ -607,19 +607,28 @@ __device__ __forceinline__ void stage_flush(const RunParams& P, const Stage& S, 
   __syncwarp();
 }
 
-// Track-length estimator over the segment of length l from the particle's position: walk the
-// mesh cells and time bins it crosses (3D DDA plus the time axis) and score w * piece length into
-// each bin it passes through.  Crossing distances are measured from the segment start, so rounding
-// does not accumulate along the walk.
+// Track-length estimator over the segment of length l from the particle's position: score
+// w * piece length into every (mesh cell, time bin) the segment passes through.  Crossing
+// distances are measured from the segment start, so rounding does not accumulate along the walk.
 //
-// The walk runs in warp-uniform rounds: each round every lane still walking emits at most one
-// piece into the warp's staging buffer (ballot prefix), and the buffer is flushed with converged
-// lanes whenever it could overflow and at the end.  Lanes cross different numbers of bins, so
-// issuing the atomics inside each lane's own loop would leave most lanes idle at every atomic.
+// The walk runs in warp-uniform rounds.  Normally every round each walking lane emits one piece:
+// the part of its segment up to the next crossing of a mesh plane or time edge.  A tally whose
+// time axis is much finer than its spatial mesh (TallyDesc::deal; then flights cross many more
+// time edges than planes, and the lane with the most crossings sets the number of rounds) instead
+// takes one mesh cell per lane per round: the lane's sub-segment
+// [s, e) in that cell spans time bins it, it+1, ..., whose edges inside it, at distances
+// D_k = (t_k - t0) v, are found by binary search; the pieces of all lanes are then dealt out over
+// the warp (prefix sum of the counts; piece q goes to lane q mod 32, which finds its owner by a
+// 5-step shuffle search and fetches the owner's sub-segment by shuffles), so a lane whose flight
+// crosses many time bins does not keep the other 31 waiting.  Pieces go to the warp's staging
+// buffer, which is flushed with converged lanes whenever it could overflow and at the end.
 // Called by all 32 lanes; `active` lanes have a segment.
-template <typename R>
+// DEAL = false compiles only the one-piece-per-round walk (for runs whose tallies have a single
+// time bin), which keeps the kernel's register footprint down.
+template <typename R, bool DEAL>
 __device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Part<R>& p, R l,
                                    uint64_t batch_base, bool active, const Stage& S, unsigned& pieces) {
+  constexpr unsigned kAll = 0xFFFFFFFFu;
   const unsigned lt = lanemask_lt();
   const int lane = threadIdx.x & 31;
   const int g = (int)pk_g(p.pk);
@@ -628,14 +637,39 @@ __device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Pa
   const R t0 = active ? p.time() : R(0);
   const double w = active ? p.w : 0.0;
   const float wscale = sizeof(R) == 4 ? weight_to_float(w) * P.fixed_scale_f : 0.0f;
+  const bool fp32_fixed = sizeof(R) == 4 && !P.tally_fp64;
   unsigned n_st = 0;
+  // stages one piece per lane (those with emit), flushing when the buffer could overflow
+  auto stage = [&](bool emit, uint32_t slot, R len, double pw, float pws) {
+    unsigned long long val = 0;
+    if (emit) {
+      if (P.tally_fp64)
+        val = (unsigned long long)__double_as_longlong(pw * (double)len);
+      else
+        val = (unsigned long long)(sizeof(R) == 4 ? float_to_fixed(pws * (float)len)
+                                                  : __double2ll_rn(pw * (double)len * P.fixed_scale));
+    }
+    const unsigned m = __ballot_sync(kAll, emit);
+    if (emit) {
+      const unsigned i = n_st + __popc(m & lt);
+      S.slot[i] = slot;
+      S.val[i] = val;
+    }
+    n_st += __popc(m);
+    pieces += __popc(m);  // warp-uniform count, added to the counters at the end
+    if (n_st > kStage - 32) {
+      stage_flush(P, S, n_st);
+      n_st = 0;
+    }
+  };
   for (int ti = 0; ti < T.h->n_tally; ++ti) {
     const TallyDesc& D = T.h->tally[ti];
     const R* e[3] = {reinterpret_cast<const R*>(base + D.o_ex), reinterpret_cast<const R*>(base + D.o_ey),
                      reinterpret_cast<const R*>(base + D.o_ez)};
     const R* et = time_edges<R>(base, D);
     const int n[3] = {D.nx, D.ny, D.nz};
-    R pos[3], u[3], sn[3], inv[3], stn = R(0), s = R(0);
+    const int nt = D.nt;
+    R pos[3], u[3], sn[3], inv[3], s = R(0), stn = rinf<R>();  // stn: distance to time edge it+1
     int idx[3], step[3], it = 0;
     bool live = active;
     if (live) {
@@ -660,61 +694,140 @@ __device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Pa
           if (i < 0 || i >= n[d]) live = false;
         }
       }
-      it = bin_search(et, D.nt, t0);
-      if (it >= D.nt) live = false;
+      it = bin_search(et, nt, t0);  // -1 before the first edge; then D_it <= s < D_it+1
+      if (it >= nt) live = false;
       else stn = (et[it + 1] - t0) * v;
     }
-    const uint64_t gbase = batch_base + (uint64_t)D.bin_offset + (uint64_t)g * D.nt;
-    const int gstride = T.G * D.nt;
-    while (__any_sync(0xFFFFFFFFu, live)) {
-      bool emit = false;
-      uint32_t slot = 0;
-      unsigned long long val = 0;
-      if (live) {
-        R nxt = fmin(fmin(sn[0], sn[1]), fmin(sn[2], stn));
-        nxt = fmin(nxt, l);
-        if (nxt > s && idx[0] >= 0 && idx[0] < n[0] && idx[1] >= 0 && idx[1] < n[1] && idx[2] >= 0 &&
-            idx[2] < n[2] && it >= 0) {
-          const int cell = (idx[2] * n[1] + idx[1]) * n[0] + idx[0];
-          const R len = nxt - s;
-          emit = true;
-          slot = (uint32_t)(gbase + (uint64_t)cell * gstride + it);
-          if (P.tally_fp64)
-            val = (unsigned long long)__double_as_longlong(w * (double)len);
-          else
-            val = (unsigned long long)(sizeof(R) == 4 ? float_to_fixed(wscale * (float)len)
-                                                      : __double2ll_rn(w * (double)len * P.fixed_scale));
+    const uint32_t gbase = (uint32_t)(batch_base + (uint64_t)D.bin_offset + (uint64_t)g * nt);
+    const int gstride = T.G * nt;
+    if (!DEAL || !D.deal) {
+      while (__any_sync(kAll, live)) {
+        bool emit = false;
+        uint32_t slot = 0;
+        R len = R(0);
+        if (live) {
+          const R nxt = fmin(fmin(fmin(sn[0], sn[1]), fmin(sn[2], stn)), l);
+          if (nxt > s && idx[0] >= 0 && idx[0] < n[0] && idx[1] >= 0 && idx[1] < n[1] && idx[2] >= 0 &&
+              idx[2] < n[2] && it >= 0) {
+            emit = true;
+            slot = gbase + (uint32_t)(((idx[2] * n[1] + idx[1]) * n[0] + idx[0]) * gstride + it);
+            len = nxt - s;
+          }
+          if (nxt >= l) {
+            live = false;
+          } else {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+              if (sn[d] <= nxt) {
+                idx[d] += step[d];
+                if (idx[d] < 0 || idx[d] >= n[d]) live = false;  // left the mesh along this axis
+                else sn[d] = (e[d][idx[d] + (step[d] > 0 ? 1 : 0)] - pos[d]) * inv[d];
+              }
+            }
+            if (stn <= nxt) {
+              ++it;
+              if (it >= nt) live = false;
+              else stn = (et[it + 1] - t0) * v;
+            }
+            s = nxt;
+          }
         }
-        if (nxt >= l) {
-          live = false;
+        stage(emit, slot, len, w, wscale);
+      }
+      continue;
+    }
+    while (__any_sync(kAll, live)) {
+      // this lane's sub-segment [s, e) in mesh cell idx, and the last time edge klt before e:
+      // it spans time bins max(it, 0) .. min(klt, nt - 1)
+      R end = s;
+      int klt = it;
+      unsigned cnt = 0;
+      uint32_t cbase = 0;
+      if (live) {
+        end = fmin(fmin(fmin(sn[0], sn[1]), sn[2]), l);
+        if (stn < end) {
+          int lo = it + 1, hi = nt;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((et[mid] - t0) * v < end) lo = mid;
+            else hi = mid - 1;
+          }
+          klt = lo;
+        }
+        const int first = it > 0 ? it : 0, last = klt < nt - 1 ? klt : nt - 1;
+        if (end > s && last >= first && idx[0] >= 0 && idx[0] < n[0] && idx[1] >= 0 && idx[1] < n[1] &&
+            idx[2] >= 0 && idx[2] < n[2]) {
+          cnt = (unsigned)(last - first + 1);
+          cbase = gbase + (uint32_t)(((idx[2] * n[1] + idx[1]) * n[0] + idx[0]) * gstride);
+        }
+      }
+      if (__all_sync(kAll, cnt <= 1u)) {
+        const int bin = it > 0 ? it : 0;
+        const R lo = bin == it ? s : (et[bin] - t0) * v;
+        const R hi = bin < klt ? (et[bin + 1] - t0) * v : end;
+        stage(cnt == 1u && hi > lo, cbase + (uint32_t)bin, hi - lo, w, wscale);
+      } else {
+        unsigned incl = cnt;  // inclusive prefix sum of the counts over the warp
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const unsigned o = __shfl_up_sync(kAll, incl, d);
+          if (lane >= d) incl += o;
+        }
+        const unsigned total = __shfl_sync(kAll, incl, 31);
+        for (unsigned q0 = 0; q0 < total; q0 += 32) {
+          const unsigned q = q0 + (unsigned)lane;
+          int o = 0;  // owner: the first lane whose inclusive count exceeds q
+#pragma unroll
+          for (int b = 16; b >= 1; b >>= 1) {
+            const unsigned pv = __shfl_sync(kAll, incl, o + b - 1);
+            if (pv <= q) o += b;
+          }
+          o = o < 31 ? o : 31;
+          const unsigned on = __shfl_sync(kAll, cnt, o), oincl = __shfl_sync(kAll, incl, o);
+          const int oit = __shfl_sync(kAll, it, o), oklt = __shfl_sync(kAll, klt, o);
+          const R os = __shfl_sync(kAll, s, o), oe = __shfl_sync(kAll, end, o);
+          const R ot0 = __shfl_sync(kAll, t0, o), ov = __shfl_sync(kAll, v, o);
+          const uint32_t ocb = __shfl_sync(kAll, cbase, o);
+          double ow = 0.0;
+          float ows = 0.0f;
+          if (fp32_fixed) ows = __shfl_sync(kAll, wscale, o);
+          else ow = __shfl_sync(kAll, w, o);
+          const int bin = (oit > 0 ? oit : 0) + (int)(q - (oincl - on));
+          const bool mine = q < total;
+          const int eb = mine ? bin : 0;  // an in-range edge index for lanes without a piece
+          const R lo = eb == oit ? os : (et[eb] - ot0) * ov;
+          const R hi = eb < oklt ? (et[eb + 1] - ot0) * ov : oe;
+          stage(mine && hi > lo, ocb + (uint32_t)bin, hi - lo, ow, ows);
+        }
+      }
+      // advance along the walk (lane-local)
+      if (live) {
+        if (klt >= nt) {
+          live = false;  // the time mesh ended inside this sub-segment
         } else {
+          const R dn = klt == it ? stn : (et[klt + 1] - t0) * v;  // distance to edge klt+1
+          if (dn <= end) {
+            it = klt + 1;
+            if (it >= nt) live = false;
+            else stn = (et[it + 1] - t0) * v;
+          } else if (klt != it) {
+            it = klt;
+            stn = dn;
+          }
+        }
+        if (end >= l) {
+          live = false;
+        } else if (live) {
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
-            if (sn[d] <= nxt) {
+            if (sn[d] <= end) {
               idx[d] += step[d];
               if (idx[d] < 0 || idx[d] >= n[d]) live = false;  // left the mesh along this axis
               else sn[d] = (e[d][idx[d] + (step[d] > 0 ? 1 : 0)] - pos[d]) * inv[d];
             }
           }
-          if (stn <= nxt) {
-            ++it;
-            if (it >= D.nt) live = false;
-            else stn = (et[it + 1] - t0) * v;
-          }
-          s = nxt;
         }
-      }
-      const unsigned m = __ballot_sync(0xFFFFFFFFu, emit);
-      if (emit) {
-        const unsigned i = n_st + __popc(m & lt);
-        S.slot[i] = slot;
-        S.val[i] = val;
-      }
-      n_st += __popc(m);
-      pieces += __popc(m);  // warp-uniform count, added to the CTA counters at kernel end
-      if (n_st > kStage - 32) {
-        stage_flush(P, S, n_st);
-        n_st = 0;
+        s = end;
       }
     }
   }

@@ -52,8 +52,12 @@ struct TallyDesc {
   int bin_offset;              // first bin of this tally in the concatenated bin space
   int n_bins;
   int o_etf;                   // time edges rounded to float (FP32 tracking)
-  int pad;
+  int deal;                    // 1: the scoring walk deals this tally's time pieces out over the warp
 };
+
+// A tally's time pieces are dealt out over the warp when its time axis is much finer than its
+// spatial mesh (flights then cross many more time edges than mesh planes).
+inline bool deals_time_pieces(int nx, int ny, int nz, int nt) { return nt >= 4 * (nx + ny + nz); }
 
 struct TableHeader {
   int G, M, n_surf, n_cell;

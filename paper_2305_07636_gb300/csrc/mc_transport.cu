@@ -26,7 +26,7 @@ namespace mcgb {
 constexpr unsigned kClaim = 128;
 
 // dynamic shared memory: [table blob][per-warp flight queues: warps x Lanes<R>::N x kWarpQ]
-template <typename R, int MINB>
+template <typename R, int MINB, bool DEAL>
 __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
   extern __shared__ __align__(16) char smem[];
   __shared__ BlockCounters bc;
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
       uint32_t pend = PEND_NONE;
       Hit hit;
       const bool flies = have && flight_plan(P, T, p, &bc, l, pend, hit);
-      score_segment_warp(T, P, p, l, stripe_off + (uint64_t)(p.elem >> 16) * bins, flies, stage, scored);
+      score_segment_warp<R, DEAL>(T, P, p, l, stripe_off + (uint64_t)(p.elem >> 16) * bins, flies, stage, scored);
       if (flies) {
         bool alive = flight_finish(P, T, p, &bc, l, pend, hit);
         if (alive && p.k + 1 >= P.max_iter) {
@@ -259,22 +259,25 @@ __global__ void k_philox(uint64_t seed, const uint4* ctr, uint4* out, uint64_t n
 
 // ------------------------------------------------------------------------------------------ launchers
 // Two register budgets of the same kernel: 3 CTAs of 256 threads per SM (80 registers) or 2 CTAs
-// (128 registers, no spills); `wide` selects the second.
+// (128 registers, no spills); `wide` selects the second.  `deal` selects the build whose scoring
+// can deal time-bin pieces out over the warp (tallies with more than one time bin).
 template <typename R>
-static const void* transport_fn(bool wide) {
-  if constexpr (sizeof(R) == 8) return (const void*)k_transport<R, 2>;
-  else return wide ? (const void*)k_transport<R, 2> : (const void*)k_transport<R, 3>;
+static const void* transport_fn(bool wide, bool deal) {
+  if constexpr (sizeof(R) == 8) return deal ? (const void*)k_transport<R, 2, true> : (const void*)k_transport<R, 2, false>;
+  else if (deal) return wide ? (const void*)k_transport<R, 2, true> : (const void*)k_transport<R, 3, true>;
+  else return wide ? (const void*)k_transport<R, 2, false> : (const void*)k_transport<R, 3, false>;
 }
 
 template <typename R>
-cudaError_t launch_transport(const RunParams& P, int grid, int block, size_t smem, cudaStream_t s, bool wide) {
+cudaError_t launch_transport(const RunParams& P, int grid, int block, size_t smem, cudaStream_t s, bool wide,
+                             bool deal) {
   void* args[] = {const_cast<RunParams*>(&P)};
-  return cudaLaunchCooperativeKernel(transport_fn<R>(wide), grid, block, args, smem, s);
+  return cudaLaunchCooperativeKernel(transport_fn<R>(wide, deal), grid, block, args, smem, s);
 }
 
 template <typename R>
-cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide) {
-  const void* f = transport_fn<R>(wide);
+cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide, bool deal) {
+  const void* f = transport_fn<R>(wide, deal);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -282,10 +285,10 @@ cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide) 
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, f, block, smem);
 }
 
-template cudaError_t launch_transport<float>(const RunParams&, int, int, size_t, cudaStream_t, bool);
-template cudaError_t launch_transport<double>(const RunParams&, int, int, size_t, cudaStream_t, bool);
-template cudaError_t transport_occupancy<float>(int, size_t, int*, bool);
-template cudaError_t transport_occupancy<double>(int, size_t, int*, bool);
+template cudaError_t launch_transport<float>(const RunParams&, int, int, size_t, cudaStream_t, bool, bool);
+template cudaError_t launch_transport<double>(const RunParams&, int, int, size_t, cudaStream_t, bool, bool);
+template cudaError_t transport_occupancy<float>(int, size_t, int*, bool, bool);
+template cudaError_t transport_occupancy<double>(int, size_t, int*, bool, bool);
 
 cudaError_t launch_batch_stats(const void* tally, int fp64, uint64_t bins, int nb, int stripes,
                                uint64_t n_hist, void* out, cudaStream_t s) {
