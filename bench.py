@@ -485,6 +485,7 @@ def main():
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     ap.add_argument("--algorithm", default="event", choices=["event", "history"])
     ap.add_argument("--no-flush", action="store_true", help="skip the L2 flush between steps")
+    ap.add_argument("--no-tune", action="store_true", help="skip the kernel autotuner (library defaults)")
     ap.add_argument("--opt", action="append", default=[],
                     help="extra mc_run_opts field as key=value (e.g. block_size=128)")
     args = ap.parse_args()
@@ -525,6 +526,12 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    tuned = None
+    if not extra and not args.no_tune:
+        # the kernel configuration for this problem, picked by the library's autotuner (untimed)
+        t_opts, tune_ms = mc.run_tune(p.h, n, seed, opts, stream)
+        tuned = {"block_size": t_opts.block_size, "blocks_per_sm": t_opts.blocks_per_sm,
+                 "candidate_ms": tune_ms}
     for w in range(args.warmup):
         flush.zero_()
         mc.run(p.h, n, seed + w, opts, stream)
@@ -594,7 +601,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "histories_per_step": n, "tracking": "fp32",
-                   "algorithm": args.algorithm, "run_opts": extra,
+                   "algorithm": args.algorithm, "run_opts": extra, "tuned": tuned,
                    "tally": "int64 fixed point 2^-32", "batches": opts.n_batches,
                    "l2": "flushed (256 MB write) before every timed step"},
         "fom": {"value": fom, "unit": "1/s", "tally": "total flux (all groups and time bins)",

@@ -146,10 +146,12 @@ typedef struct {
   int n_batches;          /* statistical batches, >= 2 (default 32) */
   uint64_t bank_capacity; /* particles in flight (0 = library default) */
   int block_size;         /* threads per CTA (0 = autotuned default) */
-  int blocks_per_sm;      /* CTAs per SM: 2 selects the 128-register build of the kernel (2 CTAs of
-                             256 per SM), another value caps the 80-register build (3 per SM);
-                             0 = the 128-register build when a tally has several time bins, else
-                             the 80-register build, as many CTAs as fit */
+  int blocks_per_sm;      /* CTAs per SM, counted in 256-thread CTAs (the cap is blocks_per_sm x
+                             256 / block_size CTAs): 2 selects the 128-register build of the kernel
+                             (2 x 256 threads per SM), another value the 80-register build (3 x 256
+                             fit); 0 = mc_run_tune's choice if it ran, else the 128-register build
+                             when a tally deals its time pieces out over the warp and the 80-register
+                             build otherwise, as many CTAs as fit */
   uint64_t max_iterations;/* watchdog: event iterations before MC_ERR_TIMEOUT (0 = 2^20) */
   int aggregate_atomics;  /* 1 = warp-aggregated tally atomics, 0 = one atomic per score,
                              -1 = auto (default): aggregate a small tally that is not striped */
@@ -206,6 +208,15 @@ int mc_problem_create(const mc_problem_desc* d, mc_problem** out);
  * Returns MC_ERR_INVALID for bad options, MC_ERR_OOM / MC_ERR_CUDA for launch failures. */
 int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts* opts,
            void* stream);
+
+/* Autotuner of mc_run for one problem: runs n_histories with each candidate configuration (256 or
+ * 128 threads per CTA; the 80-register build at 3 CTAs of 256 per SM, or the 128-register build at
+ * 2), times each run with CUDA events (best of two after a warm-up) and stores the fastest in the
+ * problem; later mc_run calls on it whose block_size and blocks_per_sm are both 0 use it.  tuned
+ * (nullable) receives a copy of opts with those two fields set, best_ms (nullable) its time.
+ * Synchronises; the tallies left behind are those of the last candidate. */
+int mc_run_tune(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts* opts, void* stream,
+                mc_run_opts* tuned, double* best_ms);
 
 /* Waits for the runs issued so far and returns the first device error any of them raised since
  * the previous mc_wait (MC_OK, MC_ERR_BANK_FULL, MC_ERR_TIMEOUT, MC_ERR_LOST), so that back-to-back

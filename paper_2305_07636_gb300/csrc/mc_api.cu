@@ -540,6 +540,10 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   mc_run_opts o;
   if (opts) o = *opts;
   else mc_run_opts_default(&o);
+  if (o.block_size == 0 && o.blocks_per_sm == 0 && p->tuned_block) {
+    o.block_size = p->tuned_block;  // the configuration mc_run_tune found for this problem
+    o.blocks_per_sm = p->tuned_bps;
+  }
   if (o.precision != MC_FP32 && o.precision != MC_FP64) return fail(MC_ERR_INVALID, "precision");
   if (o.tally_mode != MC_TALLY_FIXED64 && o.tally_mode != MC_TALLY_FP64) return fail(MC_ERR_INVALID, "tally_mode");
   if (o.fixed_bits < 0 || o.fixed_bits > 48) return fail(MC_ERR_INVALID, "fixed_bits outside [0,48]");
@@ -626,7 +630,7 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm, wide, deal)
           : transport_occupancy<float>(block, smem, &per_sm, wide, deal));
   if (per_sm < 1) return fail(MC_ERR_CUDA, "transport kernel does not fit on an SM (block %d, smem %zu)", block, smem);
-  if (o.blocks_per_sm > 0 && o.blocks_per_sm < per_sm) per_sm = o.blocks_per_sm;
+  if (o.blocks_per_sm > 0) per_sm = std::min(per_sm, std::max(1, o.blocks_per_sm * 256 / block));
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->dev));
   const int grid = sms * per_sm;
@@ -647,6 +651,62 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   p->tally_fp64 = P.tally_fp64;
   p->stripes = stripes;
   p->fixed_scale = P.fixed_scale;
+  return MC_OK;
+}
+
+int mc_run_tune(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts* opts, void* stream,
+                mc_run_opts* tuned, double* best_ms) {
+  if (!p) return fail(MC_ERR_INVALID, "problem is NULL");
+  mc_run_opts o;
+  if (opts) o = *opts;
+  else mc_run_opts_default(&o);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(ce, "cudaEventCreate");
+  }
+  int best_block = 0, best_bps = 0, rc = MC_OK;
+  float best_t = 0.f;
+  const int cands[4][2] = {{256, 0}, {256, 2}, {128, 0}, {128, 2}};  // 80- / 128-register builds
+  p->tuned_block = 0;
+  for (int c = 0; c < 4 && rc == MC_OK; ++c) {
+    mc_run_opts k = o;
+    k.block_size = cands[c][0];
+    k.blocks_per_sm = cands[c][1] ? 2 : 3;  // 128-register build at 2 x 256 threads per SM, else 80 at 3
+    if (o.precision == MC_FP64 && cands[c][1] == 0) continue;  // FP64 tracking has one build
+    rc = mc_run(p, n_histories, seed, &k, stream);  // warm-up
+    float t = -1.f;
+    for (int rep = 0; rep < 2 && rc == MC_OK; ++rep) {
+      ce = cudaEventRecord(e0, s);
+      if (ce == cudaSuccess) rc = mc_run(p, n_histories, seed, &k, stream);
+      if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+      if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+      if (ce != cudaSuccess && rc == MC_OK) rc = cuda_fail(ce, "timing a candidate");
+      if (t < 0.f || ms < t) t = ms;
+    }
+    if (rc == MC_OK) rc = mc_wait(p);  // a candidate that failed on the device fails the tuning
+    if (rc == MC_OK && (best_block == 0 || t < best_t)) {
+      best_block = k.block_size;
+      best_bps = k.blocks_per_sm;
+      best_t = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != MC_OK) return rc;
+  p->tuned_block = best_block;
+  p->tuned_bps = best_bps;
+  if (tuned) {
+    *tuned = o;
+    tuned->block_size = best_block;
+    tuned->blocks_per_sm = best_bps;
+  }
+  if (best_ms) *best_ms = best_t;
   return MC_OK;
 }
 
@@ -1083,7 +1143,7 @@ extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t
   CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm, wide, deal)
           : transport_occupancy<float>(block, smem, &per_sm, wide, deal));
   if (per_sm < 1) return fail(MC_ERR_CUDA, "transport kernel does not fit on an SM (block %d, smem %zu)", block, smem);
-  if (o.blocks_per_sm > 0 && o.blocks_per_sm < per_sm) per_sm = o.blocks_per_sm;
+  if (o.blocks_per_sm > 0) per_sm = std::min(per_sm, std::max(1, o.blocks_per_sm * 256 / block));
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int grid = sms * per_sm;

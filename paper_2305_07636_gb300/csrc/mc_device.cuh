@@ -623,6 +623,14 @@ __device__ __forceinline__ void stage_flush(const RunParams& P, const Stage& S, 
 // crosses many time bins does not keep the other 31 waiting.  Pieces go to the warp's staging
 // buffer, which is flushed with converged lanes whenever it could overflow and at the end.
 // Called by all 32 lanes; `active` lanes have a segment.
+// Score bits of a piece in the modes that need FP64 arithmetic (FP64 tallies, or fixed point
+// with FP64 tracking).  Not inlined, so that the FP32 fixed-point path carries no FP64 pipe work
+// (this GPU runs FP64 at 1/64 of the FP32 rate).
+static __device__ __noinline__ unsigned long long score_bits_fp64(const RunParams& P, double w, double len) {
+  if (P.tally_fp64) return (unsigned long long)__double_as_longlong(w * len);
+  return (unsigned long long)__double2ll_rn(w * len * P.fixed_scale);
+}
+
 // DEAL = false compiles only the one-piece-per-round walk (for runs whose tallies have a single
 // time bin), which keeps the kernel's register footprint down.
 template <typename R, bool DEAL>
@@ -643,11 +651,8 @@ __device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Pa
   auto stage = [&](bool emit, uint32_t slot, R len, double pw, float pws) {
     unsigned long long val = 0;
     if (emit) {
-      if (P.tally_fp64)
-        val = (unsigned long long)__double_as_longlong(pw * (double)len);
-      else
-        val = (unsigned long long)(sizeof(R) == 4 ? float_to_fixed(pws * (float)len)
-                                                  : __double2ll_rn(pw * (double)len * P.fixed_scale));
+      if (fp32_fixed) val = (unsigned long long)float_to_fixed(pws * (float)len);
+      else val = score_bits_fp64(P, pw, (double)len);
     }
     const unsigned m = __ballot_sync(kAll, emit);
     if (emit) {

@@ -144,6 +144,8 @@ SIGNATURES = {
                               C.c_double, DP]),
     "mc_run_static": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.POINTER(mc_run_opts),
                                 C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mc_run_tune": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.POINTER(mc_run_opts), C.c_void_p,
+                              C.POINTER(mc_run_opts), DP]),
     "mc_run_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_uint64), C.c_uint64,
                                C.POINTER(mc_run_opts), C.c_void_p, DP]),
     "mc_batch_tune": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_uint64), C.c_uint64,
@@ -288,6 +290,17 @@ def run(h: int, n_histories: int, seed: int, opts: mc_run_opts | None = None, st
     s = _stream_handle(stream)
     check(lib().mc_run(C.c_void_p(h), int(n_histories), int(seed) & (2**64 - 1),
                        C.byref(opts) if opts is not None else None, C.c_void_p(s)))
+
+
+def run_tune(h: int, n_histories: int, seed: int, opts: mc_run_opts | None = None, stream=None):
+    """mc_run_tune: times the kernel configurations on this problem and keeps the fastest for later
+    runs with default block_size / blocks_per_sm; returns (tuned options, its time in ms)."""
+    tuned = mc_run_opts()
+    ms = C.c_double(0.0)
+    check(lib().mc_run_tune(C.c_void_p(h), int(n_histories), int(seed) & (2**64 - 1),
+                            C.byref(opts) if opts is not None else None,
+                            C.c_void_p(_stream_handle(stream)), C.byref(tuned), C.byref(ms)))
+    return tuned, ms.value
 
 
 def wait(h: int):

@@ -358,3 +358,21 @@ def test_held_splits_stay_unbiased_and_bad_windows_cannot_overflow(torch):
     c = p.counters()
     assert c["ww_held"] > 0 and conserved(c), c
     p.close()
+
+
+def test_run_tuner_picks_a_configuration_that_changes_nothing_but_time(torch):
+    """mc_run_tune times the kernel builds and block sizes on the problem and keeps the fastest;
+    a later default run uses it, and since the schedule does not change any particle's walk the
+    fixed-point tallies and counters equal those of a run with the library defaults."""
+    prob = P.config3()
+    p = mc.Problem(prob)
+    p.run(200_000, 8, tally_stripes=1)
+    ref = (p.tally_batches(0), p.counters())
+    tuned, ms = mc.run_tune(p.h, 200_000, 9)
+    assert (tuned.block_size, tuned.blocks_per_sm) in ((256, 3), (256, 2), (128, 3), (128, 2)) and ms > 0
+    p.run(200_000, 8, tally_stripes=1)
+    b, c = p.tally_batches(0), p.counters()
+    assert np.array_equal(b, ref[0])
+    ref[1].pop("iterations"), c.pop("iterations")
+    assert c == ref[1]
+    p.close()
