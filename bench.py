@@ -38,6 +38,34 @@ UNIT = "histories/s"
 BYTES_PER_FLIGHT = 136  # 64 B state read + 64 B state write + 8 B tally update per event
 
 
+def source_digest():
+    """Digest of the CUDA sources and the ABI header: identifies the kernels a profile was taken on."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2305_07636_gb300", "csrc", "*")))
+    for f in files + [os.path.join(ROOT, "include", "mc.h")]:
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(summary):
+    """DRAM bytes (read + write) per launch from a committed ncu summary under profiles/, or None
+    when the summary was taken on other kernel sources than these."""
+    import re
+    try:
+        with open(os.path.join(ROOT, "profiles", summary)) as f:
+            text = f.read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    d = re.search(r"source_digest:\s*([0-9a-f]+)", text)
+    if m and d and d.group(1) == source_digest():
+        return float(m.group(1))
+    return None
+
+
 def workload(name):
     from paper_2305_07636_gb300 import problems as P
     if name == "config2":
@@ -319,7 +347,7 @@ def bench_batch(args, torch, mc, batch, n_total, desc, world, local):
                                  "launch": "one mc_run per problem, shortest first, same stream"},
                   "speedup_vs_sequential": value / seq_value},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": profiled_traffic("k_transport_batch_config5.md"),
                      "kernel": "k_transport_batch<float>", "kernel_ms": kernel_ms,
                      "algorithmic_bytes": algo_bytes, "peak_kind": peak_kind,
                      "l2_atomic": {"achieved": scores / (kernel_ms / 1000.0) / 1e9,
@@ -607,7 +635,8 @@ def main():
         "fom": {"value": fom, "unit": "1/s", "tally": "total flux (all groups and time bins)",
                 "rel_err_per_step": rel, "seconds_to_5pct": t_5pct},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": profiled_traffic(f"k_transport_{args.workload}_1e7.md") if n == 10_000_000 else None,
                      "kernel": "k_transport<float>", "kernel_ms": tr_ms,
                      "algorithmic_bytes": algo_bytes, "peak_kind": peak_kind,
                      "l2_atomic": {"achieved": atom_rate / 1e9, "peak": atom_peak / 1e9,

@@ -358,7 +358,9 @@ int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t seed, cons
  * the seed `seed + i`: exactly the particles that mc_run(ps[i], n_hist[i], seed + i, o) transports,
  * so fixed-point tallies and event counters equal those of n separate runs bit for bit.
  *   Scheduling: the histories of every problem are cut into work units of o->batch_unit
- *   consecutive histories, problems in ascending order of n_hist (short problems finish first).
+ *   consecutive histories; problems are ordered by geometry kind (plain cells, then lattices, so
+ *   that concurrent warps mostly run the same code) and by ascending n_hist within a kind (short
+ *   problems finish first).
  *   Every warp of the grid claims units one at a time, stages the unit's problem tables in its own
  *   slice of shared memory (only when the problem changes), and carries the unit's particles and
  *   all their secondaries to completion; a warp claims the next unit of the same problem before its

@@ -32,7 +32,7 @@
 
 namespace mcgb {
 
-// one problem of a batch, in claim order (ascending history count)
+// one problem of a batch, in claim order (geometry kind, then ascending history count)
 struct __align__(16) BatchItem {
   RunParams P;          // the problem's run parameters; births use the claiming warp's stack
   void* stats;          // [3][bins] statistics output (the problem's own buffer)
@@ -537,7 +537,14 @@ int mc_run_batch(mc_problem* const* ps, int n, const uint64_t* n_hist, uint64_t 
   }
   std::vector<int> ord(n);
   std::iota(ord.begin(), ord.end(), 0);
-  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return n_hist[a] < n_hist[b]; });
+  // claim order: problems of one geometry kind together (plain cells, then lattices), so that the
+  // warps of an SM mostly run the same code (mixing them stalled the kernel on instruction
+  // fetch), and shortest first within a kind
+  auto kind = [&](int i) { return reinterpret_cast<const TableHeader*>(ps[i]->blob[0].data())->has_lat; };
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+    if (kind(a) != kind(b)) return kind(a) < kind(b);
+    return n_hist[a] < n_hist[b];
+  });
 
   std::lock_guard<std::mutex> lk(g_batch_mu);
   BatchPlan* pl = nullptr;

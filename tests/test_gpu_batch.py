@@ -122,9 +122,12 @@ def test_batch_wall_times(torch):
     ps = [mc.Problem(q) for q in probs]
     wall = mc.run_batch([p.h for p in ps], nh, 1, wall=True)
     assert np.all(np.isfinite(wall)) and np.all(wall > 0)
-    order = np.argsort(nh, kind="stable")
-    # problems are scheduled in ascending size: the smallest finishes before the largest
-    assert wall[order[0]] <= wall[order[-1]]
+    # within a geometry kind problems are scheduled in ascending size: the smallest finishes
+    # before the largest
+    for lattice in (False, True):
+        idx = [i for i, q in enumerate(probs) if q["name"].endswith("lattice") == lattice]
+        order = sorted(idx, key=lambda i: nh[i])
+        assert wall[order[0]] <= wall[order[-1]]
     for p in ps:
         assert p.timing()[0] > 0.0
         assert conserved(p.counters())
