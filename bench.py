@@ -38,19 +38,30 @@ UNIT = "histories/s"
 BYTES_PER_FLIGHT = 136  # 64 B state read + 64 B state write + 8 B tally update per event
 
 
-def source_digest():
-    """Digest of the CUDA sources and the ABI header: identifies the kernels a profile was taken on."""
-    import glob
+KERNEL_SOURCES = {
+    "k_transport": ["mc_transport.cu", "mc_events.cuh", "mc_device.cuh", "mc_internal.h"],
+    "k_transport_batch": ["mc_batch.cu", "mc_events.cuh", "mc_device.cuh", "mc_internal.h", "mc_host.h"],
+}
+
+
+def source_digest(kernel):
+    """Digest of the sources a kernel is compiled from (comments removed) and of the ABI header:
+    identifies the kernel build an ncu summary was taken on."""
     import hashlib
+    import re
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_2305_07636_gb300", "csrc", "*")))
+    files = [os.path.join(ROOT, "paper_2305_07636_gb300", "csrc", f) for f in KERNEL_SOURCES[kernel]]
     for f in files + [os.path.join(ROOT, "include", "mc.h")]:
-        with open(f, "rb") as fh:
-            h.update(os.path.basename(f).encode() + b"\0" + fh.read())
+        with open(f) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        text = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+        h.update(os.path.basename(f).encode() + b"\0" + text.encode())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(summary):
+def profiled_traffic(summary, kernel):
     """DRAM bytes (read + write) per launch from a committed ncu summary under profiles/, or None
     when the summary was taken on other kernel sources than these."""
     import re
@@ -61,7 +72,7 @@ def profiled_traffic(summary):
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     d = re.search(r"source_digest:\s*([0-9a-f]+)", text)
-    if m and d and d.group(1) == source_digest():
+    if m and d and d.group(1) == source_digest(kernel):
         return float(m.group(1))
     return None
 
@@ -347,7 +358,7 @@ def bench_batch(args, torch, mc, batch, n_total, desc, world, local):
                                  "launch": "one mc_run per problem, shortest first, same stream"},
                   "speedup_vs_sequential": value / seq_value},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic("k_transport_batch_config5.md"),
+                     "frac": achieved / peak, "traffic": profiled_traffic("k_transport_batch_config5.md", "k_transport_batch"),
                      "kernel": "k_transport_batch<float>", "kernel_ms": kernel_ms,
                      "algorithmic_bytes": algo_bytes, "peak_kind": peak_kind,
                      "l2_atomic": {"achieved": scores / (kernel_ms / 1000.0) / 1e9,
@@ -636,7 +647,7 @@ def main():
                 "rel_err_per_step": rel, "seconds_to_5pct": t_5pct},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": profiled_traffic(f"k_transport_{args.workload}_1e7.md") if n == 10_000_000 else None,
+                     "traffic": profiled_traffic(f"k_transport_{args.workload}_1e7.md", "k_transport") if n == 10_000_000 else None,
                      "kernel": "k_transport<float>", "kernel_ms": tr_ms,
                      "algorithmic_bytes": algo_bytes, "peak_kind": peak_kind,
                      "l2_atomic": {"achieved": atom_rate / 1e9, "peak": atom_peak / 1e9,
