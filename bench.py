@@ -201,7 +201,9 @@ def run_reference(args):
     t0 = time.perf_counter()
     oracle.run(prob, probe, seed=1, threads=threads)
     per = (time.perf_counter() - t0) / probe
-    n = int(max(probe, min(n_full, args.ref_step_seconds / per)))
+    # each step is a bounded sample: the whole --steps K run stays within about 2.5 minutes
+    step_s = min(args.ref_step_seconds, 150.0 / max(1, args.steps))
+    n = int(max(probe, min(n_full, step_s / per)))
     for w in range(args.warmup):
         oracle.run(prob, min(n, probe), seed=100 + w, threads=threads)
     times = []
@@ -229,7 +231,8 @@ def run_reference_batch(args, batch, n_full, desc, threads):
     hist, secs = 0, 0.0
     frac = 1.0
     for k in range(args.steps):
-        n, dt, frac = oracle_batch_sample(probs, nh, threads, args.ref_step_seconds / 2, 100 + 10 * k)
+        n, dt, frac = oracle_batch_sample(probs, nh, threads, min(args.ref_step_seconds, 150.0 / max(1, args.steps)) / 2,
+                                          100 + 10 * k)
         hist += n
         secs += dt
     value = hist / secs
