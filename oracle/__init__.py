@@ -29,6 +29,7 @@ KIND = {"PX": 0, "PY": 1, "PZ": 2, "CZ": 3}
 BC = {"interior": 0, "vacuum": 1, "reflect": 2}
 SRC_POS = {"box": 0, "surface_x0": 1}
 SRC_DIR = {"iso": 0, "beam_x": 1, "cos_x": 2}
+ESTIMATOR = {"track": 0, "crossing": 1}
 
 
 def build(force: bool = False) -> str:
@@ -67,6 +68,7 @@ class OrProblem(C.Structure):
         ("ww_on", C.c_int), ("ww_nx", C.c_int), ("ww_ny", C.c_int), ("ww_nz", C.c_int),
         ("ww_edges", C.POINTER(C.c_double)), ("ww_center", C.POINTER(C.c_double)),
         ("ww_upper", C.c_double), ("ww_lower", C.c_double), ("ww_split_max", C.c_int),
+        ("tally_est", C.POINTER(C.c_int)),
     ]
 
 
@@ -85,7 +87,8 @@ class OrOpts(C.Structure):
                 ("seed", C.c_uint64), ("threads", C.c_int),
                 ("log_first", C.c_uint64), ("log_count", C.c_uint64),
                 ("log", C.POINTER(OrEvent)), ("log_cap", C.c_uint64),
-                ("log_n", C.POINTER(C.c_uint64)), ("fixed_bits", C.c_int)]
+                ("log_n", C.POINTER(C.c_uint64)), ("fixed_bits", C.c_int),
+                ("implicit_capture", C.c_int), ("wr_cutoff", C.c_double), ("wr_survival", C.c_double)]
 
 
 class OrResult(C.Structure):
@@ -212,13 +215,17 @@ class Marshalled:
         s.n_tally = len(tals)
         dims, edges = [], []
         self.tally_shapes = []
+        est = []
         for t in tals:
             n = [len(t[k]) - 1 for k in ("x", "y", "z", "t")]
             dims += n
             for k in ("x", "y", "z", "t"):
                 edges += list(t[k])
-            self.tally_shapes.append((n[2], n[1], n[0], G, n[3]))
+            est.append(ESTIMATOR[t.get("estimator", "track")])
+            # a time-crossing tally holds one value per time point (nt + 1 of them)
+            self.tally_shapes.append((n[2], n[1], n[0], G, n[3] + (1 if est[-1] == 1 else 0)))
         s.tally_dims = ip(dims)
+        s.tally_est = ip(est if est else [0])
         s.tally_edges = dp(edges if edges else [0.0])
         s.t_census = prob["t_census"]
         if ww is not None:
@@ -260,7 +267,11 @@ class Result:
 
 def run(prob: dict, n: int, seed: int = 1, threads: int | None = None, first: int = 0,
         log_first: int = 0, log_count: int = 0, log_cap: int = 0, ww: dict | None = None,
-        fixed_bits: int = 32) -> Result:
+        fixed_bits: int = 32, implicit_capture: bool = False, wr_cutoff: float = 0.25,
+        wr_survival: float = 0.5) -> Result:
+    """Runs histories [first, first + n) of the problem; implicit_capture selects the collision
+    without a capture channel (weight times the non-capture probability) and the weight-cutoff
+    roulette below wr_cutoff (survivors get wr_survival)."""
     L = lib()
     m = Marshalled(prob, ww)
     nb = L.or_total_bins(C.byref(m.s))
@@ -275,6 +286,8 @@ def run(prob: dict, n: int, seed: int = 1, threads: int | None = None, first: in
     o.first_history, o.n_histories, o.seed = first, n, seed
     o.threads = threads if threads else (os.cpu_count() or 1)
     o.fixed_bits = fixed_bits
+    o.implicit_capture = 1 if implicit_capture else 0
+    o.wr_cutoff, o.wr_survival = wr_cutoff, wr_survival
     events = None
     log_n = C.c_uint64(0)
     if log_count > 0:

@@ -115,6 +115,13 @@ def infinite_population(sigma_t, sigma_s, nu_sigma_f, v, t):
     return math.exp(-v * (sigma_t - sigma_s - nu_sigma_f) * t)
 
 
+def infinite_point_flux(sigma_t, sigma_s, nu_sigma_f, v, t_points):
+    """One-group infinite medium after a unit pulse at t = 0: the flux at the instants t,
+    phi(t) = v exp(-alpha t) (what the time-crossing estimator measures)."""
+    t = np.asarray(t_points, dtype=np.float64)
+    return v * np.exp(-v * (sigma_t - sigma_s - nu_sigma_f) * t)
+
+
 # ------------------------------------------------------------------ P5: multigroup expm
 
 
@@ -159,6 +166,26 @@ def multigroup_time_bins(mat, speed, t_edges, g0=0, method="vanloan"):
     f = integrated_flux_vanloan if method == "vanloan" else integrated_flux_eig
     cum = np.array([f(A, phi0, t) if t > 0 else np.zeros(G) for t in t_edges])
     return (cum[1:] - cum[:-1]).T  # [G][nt]
+
+
+def multigroup_point_flux(mat, speed, t_points, g0=0, method="expm"):
+    """Group flux of an infinite medium at the instants t after a unit pulse in group g0:
+    phi(t) = exp(A t) phi(0), phi(0) = v_g0 e_g0 -> [G][n_points].  method 'expm': scipy's
+    scaling and squaring (Higham 2005); 'eig': the eigendecomposition of A."""
+    A = multigroup_operator(mat, speed)
+    G = A.shape[0]
+    phi0 = np.zeros(G)
+    phi0[g0] = speed[g0]
+    out = []
+    if method == "expm":
+        for t in t_points:
+            out.append(linalg.expm(A * t) @ phi0)
+    else:
+        lam, W = np.linalg.eig(A)
+        c = np.linalg.solve(W, phi0.astype(complex))
+        for t in t_points:
+            out.append(np.real(W @ (np.exp(lam * t) * c)))
+    return np.array(out).T
 
 
 def multigroup_time_bins_ode(mat, speed, t_edges, g0=0, rtol=1e-12):

@@ -16,6 +16,10 @@
 //   5. collision: scatter (g' by CDF of the Sigma_s row, isotropic), production
 //      (floor(nu + xi) children, g' ~ chi, isotropic; parent absorbed) or capture;
 //      surface: leak (vacuum), reflect (flip the normal component) or move to the next cell.
+// Variants used by the paper's Section 3 runs: the time-crossing estimator (the flux at time
+// points t_j: every particle alive at t_j scores w v into the mesh cell it occupies then) and
+// implicit capture (no capture channel; the weight carries the survival probability, and a
+// weight-cutoff roulette ends histories).
 // Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
 // as 1, 2, 3", SC'11) keyed by the seed, with the counter (tag, event index, block).
 #include "oracle.h"
@@ -78,9 +82,17 @@ uint64_t child_tag(uint64_t seed, uint64_t parent, uint32_t k, uint32_t j, uint3
 
 // ---------------------------------------------------------------- problem copy
 struct Tally {
-  std::vector<double> e[4];  // x, y, z, t edges
+  std::vector<double> e[4];  // x, y, z, t edges (time points for a time-crossing tally)
   int n[4];
+  int est;     // OR_EST_TRACK or OR_EST_CROSSING
+  int nval;    // values per (cell, group) along time: n[3] bins, or n[3] + 1 points
   int offset;  // first bin in the concatenated output
+};
+
+// how one history is transported: analog, or with implicit capture and a weight cutoff
+struct Physics {
+  bool implicit;
+  double cutoff, survival;
 };
 
 struct Prob {
@@ -194,8 +206,10 @@ Prob copy_problem(const or_problem* p) {
       T.e[d].assign(e, e + T.n[d] + 1);
       e += T.n[d] + 1;
     }
+    T.est = p->tally_est ? p->tally_est[t] : OR_EST_TRACK;
+    T.nval = T.est == OR_EST_CROSSING ? T.n[3] + 1 : T.n[3];
     T.offset = off;
-    off += T.n[0] * T.n[1] * T.n[2] * G * T.n[3];
+    off += T.n[0] * T.n[1] * T.n[2] * G * T.nval;
     P.tallies.push_back(T);
   }
   P.total_bins = off;
@@ -439,14 +453,17 @@ struct Acc {
     std::memset(cnt, 0, sizeof(cnt));
     fscale = std::ldexp(1.0, fixed_bits);
   }
-  void add(int bin, double v) {
+  // adds score v to the history's bin; the fixed-point sum counts fx (the score itself, or the
+  // weight of a time-crossing score, whose flux w v can exceed the fixed-point range)
+  void add(int bin, double v, double fx) {
     if (!mark[bin]) {
       mark[bin] = 1;
       touched.push_back(bin);
     }
     hist[bin] += v;
-    fixed[bin] += (int64_t)std::llrint(v * fscale);
+    fixed[bin] += (int64_t)std::llrint(fx * fscale);
   }
+  void add(int bin, double v) { add(bin, v, v); }
   void end_history() {
     for (int b : touched) {
       s1[b] += hist[b];
@@ -464,6 +481,23 @@ void score_segment(const Prob& P, const Particle& q, double l, Acc& acc) {
   double v = P.v[q.g];
   double p0[3] = {q.x, q.y, q.z}, u[3] = {q.ux, q.uy, q.uz};
   for (const Tally& T : P.tallies) {
+    if (T.est == OR_EST_CROSSING) {
+      // time-crossing estimator: the flight spans the times [t, t + l / v); at every time point
+      // t_j inside that span the particle contributes w v to the flux of the cell it is in
+      double t_end = q.t + l / v;
+      for (int j = 0; j <= T.n[3]; ++j) {
+        double tj = T.e[3][j];
+        if (!(tj >= q.t && tj < t_end)) continue;
+        double s = (tj - q.t) * v;
+        int ix = bin_of(T.e[0], p0[0] + s * u[0]);
+        int iy = bin_of(T.e[1], p0[1] + s * u[1]);
+        int iz = bin_of(T.e[2], p0[2] + s * u[2]);
+        if (ix < 0 || iy < 0 || iz < 0) continue;
+        int bin = (((iz * T.n[1] + iy) * T.n[0] + ix) * P.G + q.g) * T.nval + j;
+        acc.add(T.offset + bin, q.w * v, q.w);
+      }
+      continue;
+    }
     std::vector<double> cuts;
     cuts.push_back(0.0);
     cuts.push_back(l);
@@ -488,7 +522,7 @@ void score_segment(const Prob& P, const Particle& q, double l, Acc& acc) {
       int iz = bin_of(T.e[2], p0[2] + m * u[2]);
       int it = bin_of(T.e[3], q.t + m / v);
       if (ix < 0 || iy < 0 || iz < 0 || it < 0) continue;
-      int bin = (((iz * T.n[1] + iy) * T.n[0] + ix) * P.G + q.g) * T.n[3] + it;
+      int bin = (((iz * T.n[1] + iy) * T.n[0] + ix) * P.G + q.g) * T.nval + it;
       acc.add(T.offset + bin, q.w * (b - a));
     }
   }
@@ -578,8 +612,8 @@ struct Logger {
   uint64_t first, count;
 };
 
-void transport(const Prob& P, uint64_t seed, Particle q, std::vector<Particle>& stack, Acc& acc,
-               const Logger& lg) {
+void transport(const Prob& P, const Physics& ph, uint64_t seed, Particle q, std::vector<Particle>& stack,
+               Acc& acc, const Logger& lg) {
   const int G = P.G;
   while (true) {
     int m = material(P, q);
@@ -684,14 +718,33 @@ void transport(const Prob& P, uint64_t seed, Particle q, std::vector<Particle>& 
     } else {
       acc.cnt[OR_C_COLLISION]++;
       double Ss = P.ss_tot[m * G + q.g], Sf = P.sf[m * G + q.g];
+      // analog: the channel is drawn over Sigma_t (scatter, production, capture).  Implicit
+      // capture: it is drawn over Sigma_s + Sigma_f only, and the weight takes the factor
+      // (Sigma_s + Sigma_f) / Sigma_t, the probability that the collision is not a capture
       double xi = b0.b * St;
+      if (ph.implicit) {
+        double keep = Ss + Sf;
+        xi = b0.b * keep;
+        if (keep > 0.0) q.w *= keep / St;
+        else xi = INF;  // a pure absorber: the weight would be zero, the particle is captured
+      }
       if (xi < Ss) {
         acc.cnt[OR_C_SCATTER]++;
         Pair b1 = draw(seed, q.tag, k, 1), b2 = draw(seed, q.tag, k, 2);
         q.g = sample_cdf(&P.scat_cdf[(m * G + q.g) * G], G, b1.a);
         isotropic(2.0 * b1.b - 1.0, b2.a, q.ux, q.uy, q.uz);
         rec.outcome = 0;
-        alive = weight_window(P, seed, q, k, stack, acc);
+        if (ph.implicit && q.w < ph.cutoff) {
+          // weight cutoff: survive with probability w / w_s at weight w_s (unbiased)
+          double u = draw(seed, q.tag, k, 3).b;
+          if (u < q.w / ph.survival) {
+            q.w = ph.survival;
+          } else {
+            acc.cnt[OR_C_WW_KILL]++;
+            alive = false;
+          }
+        }
+        if (alive) alive = weight_window(P, seed, q, k, stack, acc);
       } else if (xi < Ss + Sf) {
         acc.cnt[OR_C_PRODUCTION]++;
         Pair b3 = draw(seed, q.tag, k, 3);
@@ -720,7 +773,8 @@ void transport(const Prob& P, uint64_t seed, Particle q, std::vector<Particle>& 
   }
 }
 
-void run_range(const Prob& P, uint64_t seed, uint64_t h0, uint64_t h1, Acc& acc, const Logger& lg) {
+void run_range(const Prob& P, const Physics& ph, uint64_t seed, uint64_t h0, uint64_t h1, Acc& acc,
+               const Logger& lg) {
   std::vector<Particle> stack;
   for (uint64_t h = h0; h < h1; ++h) {
     Particle q = source_particle(P, seed, h);
@@ -732,7 +786,7 @@ void run_range(const Prob& P, uint64_t seed, uint64_t h0, uint64_t h1, Acc& acc,
       while (!stack.empty()) {
         Particle c = stack.back();
         stack.pop_back();
-        transport(P, seed, c, stack, acc, lg);
+        transport(P, ph, seed, c, stack, acc, lg);
       }
     }
     acc.end_history();
@@ -747,7 +801,8 @@ int or_total_bins(const or_problem* p) {
   int off = 0;
   for (int t = 0; t < p->n_tally; ++t) {
     const int* d = &p->tally_dims[4 * t];
-    off += d[0] * d[1] * d[2] * p->G * d[3];
+    const int nval = (p->tally_est && p->tally_est[t] == OR_EST_CROSSING) ? d[3] + 1 : d[3];
+    off += d[0] * d[1] * d[2] * p->G * nval;
   }
   return off + p->n_surf;
 }
@@ -761,12 +816,13 @@ int or_run(const or_problem* p, const or_opts* o, or_result* r) {
   if (nt < 1) nt = 1;
   std::vector<Acc> accs(nt);
   Logger lg{o->log != nullptr, o->log_first, o->log_count};
+  Physics ph{o->implicit_capture != 0, o->wr_cutoff, o->wr_survival};
   std::vector<std::thread> th;
   for (int i = 0; i < nt; ++i) {
     accs[i].init(nb, o->fixed_bits);
     uint64_t h0 = o->first_history + n * (uint64_t)i / (uint64_t)nt;
     uint64_t h1 = o->first_history + n * (uint64_t)(i + 1) / (uint64_t)nt;
-    th.emplace_back([&, i, h0, h1] { run_range(P, o->seed, h0, h1, accs[i], lg); });
+    th.emplace_back([&, i, h0, h1] { run_range(P, ph, o->seed, h0, h1, accs[i], lg); });
   }
   for (auto& t : th) t.join();
   for (int b = 0; b < nb; ++b) {

@@ -8,8 +8,10 @@
  * What it computes: the analog history-based random walk of the paper's Section 3 problem class
  * (fixed source, multigroup, quadric CSG of planes and z-cylinders plus a square pin lattice,
  * time-dependent source, time census, track-length mesh tallies, secondary production), in FP64,
- * one history at a time, with the per-history variance of every tally bin.  The paper prints no
- * transport equations; the steps follow textbook multigroup Monte Carlo in the order
+ * one history at a time, with the per-history variance of every tally bin.  Two variants the
+ * paper's Section 3 runs use: the time-crossing estimator of the flux at time points (the
+ * multigroup pulse and C5G7 transients) and implicit capture (the Kobayashi transient).  The
+ * paper prints no transport equations; the steps follow textbook multigroup Monte Carlo in order
  *   distance to collision -> distance to surface -> distance to census -> move + score ->
  *   collision (scatter / production / capture) or surface (leak / reflect / transmit).
  */
@@ -28,6 +30,8 @@ enum { OR_INTERIOR = 0, OR_VACUUM = 1, OR_REFLECT = 2 };
 enum { OR_SRC_BOX = 0, OR_SRC_SURFACE_X0 = 1 };
 enum { OR_DIR_ISO = 0, OR_DIR_BEAM_X = 1, OR_DIR_COS_X = 2 };
 enum { OR_EV_COLLISION = 0, OR_EV_SURFACE = 1, OR_EV_CENSUS = 2, OR_EV_LOST = 3 };
+/* tally estimators: track length over time bins, or the time-crossing estimator at time points */
+enum { OR_EST_TRACK = 0, OR_EST_CROSSING = 1 };
 
 /* counters, summed over all histories */
 enum {
@@ -44,7 +48,7 @@ enum {
   OR_C_SURFACE,         /* surface events (including lattice walls and pins) */
   OR_C_REFLECT,         /* reflections */
   OR_C_WW_SPLIT,        /* extra particles created by weight-window splitting */
-  OR_C_WW_KILL,         /* particles removed by roulette */
+  OR_C_WW_KILL,         /* particles removed by roulette (weight windows or weight cutoff) */
   OR_NCOUNT
 };
 
@@ -84,6 +88,9 @@ typedef struct {
   const double* ww_center; /* [ww_nz][ww_ny][ww_nx][G] */
   double ww_upper, ww_lower; /* split above upper*w_c, roulette below lower*w_c */
   int ww_split_max;
+  /* per tally: OR_EST_TRACK (nt time bins between the nt+1 edges) or OR_EST_CROSSING (values at
+   * the nt+1 time points themselves); NULL means every tally is a track-length tally */
+  const int* tally_est;
 } or_problem;
 
 typedef struct {
@@ -104,11 +111,19 @@ typedef struct {
   uint64_t log_cap;
   uint64_t* log_n;               /* events written (clipped to log_cap) */
   int fixed_bits;                /* fixed-point scale 2^fixed_bits for the int64 sums */
+  /* implicit capture: collisions never capture; the weight is multiplied by the non-capture
+   * probability (Sigma_s + Sigma_f) / Sigma_t and the channel is drawn among scatter and
+   * production; a particle whose weight falls below wr_cutoff after a scatter survives a
+   * roulette with probability w / wr_survival at weight wr_survival */
+  int implicit_capture;
+  double wr_cutoff, wr_survival;
 } or_opts;
 
 /* Outputs are laid out over all tallies' bins concatenated (tally 0 first, bins in
- * [z][y][x][g][t] order), followed by n_surf leakage bins.  s1 = sum over histories of the
- * history's score, s2 = sum of its square; fixed = sum of llrint(score_piece * 2^fixed_bits). */
+ * [z][y][x][g][t] order; a time-crossing tally has nt+1 time values), followed by n_surf leakage
+ * bins.  s1 = sum over histories of the history's score, s2 = sum of its square; fixed = sum of
+ * llrint(score_piece * 2^fixed_bits), where a time-crossing score piece counts its weight w
+ * (its flux score is w v). */
 typedef struct {
   double* s1;
   double* s2;

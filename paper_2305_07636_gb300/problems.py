@@ -21,7 +21,9 @@ Problem dict layout (all lengths in cm, times in s, cross sections in 1/cm):
                         matrix_material}
     source:    {pos: 'box'|'surface_x0', lo[3], hi[3], dir: 'iso'|'beam_x'|'cos_x',
                 group_pdf[G], t0, t1}
-    tallies:   list of {x: edges, y: edges, z: edges, t: edges}  (track-length mesh tallies)
+    tallies:   list of {x: edges, y: edges, z: edges, t: edges, estimator: 'track'|'crossing'}
+               'track': track-length estimator over the nt time bins between the t edges;
+               'crossing': time-crossing estimator of the flux at the nt+1 time points t
     t_census:  float (math.inf for steady state)
 """
 from __future__ import annotations
@@ -73,9 +75,16 @@ def source(pos="box", lo=(0, 0, 0), hi=(0, 0, 0), direction="iso", G=1, group=0,
             "t0": float(t0), "t1": float(t1)}
 
 
-def mesh(x=(-INF, INF), y=(-INF, INF), z=(-INF, INF), t=(0.0, INF)):
+def mesh(x=(-INF, INF), y=(-INF, INF), z=(-INF, INF), t=(0.0, INF), estimator="track"):
     return {"x": [float(v) for v in x], "y": [float(v) for v in y],
-            "z": [float(v) for v in z], "t": [float(v) for v in t]}
+            "z": [float(v) for v in z], "t": [float(v) for v in t], "estimator": estimator}
+
+
+def with_tallies(prob, tallies):
+    """A copy of the problem with its tally list replaced."""
+    q = dict(prob)
+    q["tallies"] = list(tallies)
+    return q
 
 
 def problem(name, G, speed, materials, surfaces, cells, src, tallies, t_census=INF,
@@ -189,6 +198,18 @@ def config2(seed=2, G=7, n_tbins=100, side=10.0):
     t_edges = log_time_edges(n_tbins)
     tal = [mesh(x=(0, side), y=(0, side), z=(0, side), t=t_edges)]
     return problem("config2", G, log_speeds(G), [mat], surfs, cells, src, tal, t_edges[-1])
+
+
+def config2_crossing(seed=2, G=7, n_tbins=100, side=10.0):
+    """Config 2 with the flux tallied by the time-crossing estimator at the 101 time points
+    {0} U logspace(1e-9, 1e-3, 100) (the paper tallies its multigroup pulse this way), next to the
+    track-length tally over the 100 bins between them."""
+    prob = config2(seed, G, n_tbins, side)
+    tl = prob["tallies"][0]
+    cross = mesh(x=tl["x"], y=tl["y"], z=tl["z"], t=tl["t"], estimator="crossing")
+    q = with_tallies(prob, [tl, cross])
+    q["name"] = "config2_crossing"
+    return q
 
 
 def offspring_matrix(mat):
