@@ -4,7 +4,8 @@
  * The library implements the transport method whose problem class the MC/DC paper states in
  * its Section 3: fixed-source multigroup transport on quadric-surface constructive solid geometry
  * (here planes x/y/z, z-cylinders and a square pin lattice), a time-dependent source, a time
- * census and time-dependent mesh tallies scored with the track-length estimator (Section 3.1).
+ * census and time-dependent mesh tallies scored with the track-length estimator (Section 3.1) or
+ * the time-crossing estimator, with analog collisions or implicit capture (Section 3's runs).
  * Per particle the walk samples the distance to collision, compares it with the distance to the
  * next surface and to the census, moves the particle and scores its track length into an
  * (x, y, z, group, time) mesh, then samples the collision: scatter to a new group, secondary
@@ -100,11 +101,26 @@ typedef struct {
 } mc_source;
 
 /* ------------------------------------------------------------------------- tallies */
-/* Track-length mesh tally over strictly increasing edges (the outermost may be +-inf).
- * Bins are laid out [z][y][x][group][t]. */
+/* Estimators of a mesh tally (both appear in the paper's Section 3 runs).
+ *   MC_EST_TRACK_LENGTH: the track-length estimator of the flux integrated over each of the nt time
+ *     bins between the nt+1 time edges t (and over each mesh cell): a flight scores w x (its
+ *     length inside the cell and time bin).  Per source particle, units cm (flux x volume x time).
+ *   MC_EST_TIME_CROSSING: the time-crossing estimator of the flux at each of the nt+1 time points t
+ *     themselves (the paper's multigroup pulse and C5G7 transients): a particle alive at t_j scores
+ *     w v_g into the mesh cell it occupies at t_j, i.e. a flight over [t_a, t_b) scores every
+ *     t_j with t_a <= t_j < t_b.  Per source particle, units cm^3/s (flux x volume).  The
+ *     device accumulates the weight w (int64 fixed point stays in range for fast groups); the
+ *     readback multiplies by v_g.  A point at or after the census time gets no score: the census
+ *     ends every particle there. */
+typedef enum { MC_EST_TRACK_LENGTH = 0, MC_EST_TIME_CROSSING = 1 } mc_estimator;
+
+/* Mesh tally over strictly increasing edges (the outermost spatial edges may be +-inf; the time
+ * points of a time-crossing tally must be finite).  Values are laid out [z][y][x][group][t]: nt
+ * time bins (track length) or nt+1 time points (time crossing). */
 typedef struct {
   int nx, ny, nz, nt;
   const double *x, *y, *z, *t; /* nx+1, ny+1, nz+1, nt+1 edges */
+  int estimator;               /* mc_estimator (0 = track length) */
 } mc_mesh_tally;
 
 /* ------------------------------------------------------------------------- problem */
@@ -165,6 +181,18 @@ typedef struct {
   int tally_stripes;      /* copies of the batch tallies that CTAs score into round-robin, summed
                              by the statistics (0 = up to 16 within a 64 MB budget) */
   int batch_unit;         /* mc_run_batch: histories per work unit a warp claims (0 = tuned or 128) */
+  /* Implicit capture (survival biasing; the paper's Kobayashi transient runs with it): a collision
+   * never captures.  Its channel is drawn among scatter and production with probabilities
+   * Sigma_s / (Sigma_s + Sigma_f) and Sigma_f / (Sigma_s + Sigma_f), and the weight (of the scattered
+   * particle or of each of the floor(nu + xi) secondaries) is multiplied by the non-capture
+   * probability (Sigma_s + Sigma_f) / Sigma_t; where that is 0 the collision captures as in the
+   * analog walk.  After a scatter, a weight below wr_cutoff survives a roulette with probability
+   * w / wr_survival at weight wr_survival (the u_spare draw of the collision), which ends histories
+   * without bias; roulette kills count as MC_C_WW_KILL.  Needs 0 <= wr_cutoff < wr_survival.  Every
+   * tally stays unbiased; FP64 or fixed-point tallies both work (weights stay near 1). */
+  int implicit_capture;   /* 0 = analog (default), 1 = implicit capture */
+  double wr_cutoff;       /* weight cutoff (default 0.25) */
+  double wr_survival;     /* survival weight of the roulette (default 0.5) */
 } mc_run_opts;
 
 /* Fills the defaults listed above. */
@@ -181,8 +209,10 @@ typedef struct {
   double x, y, z, ux, uy, uz, t, w;
 } mc_event;
 
-/* Counters summed over a run, in this order.  MC_C_SCORES counts track-length tally updates
- * (one per mesh cell and time bin a flight crosses).  MC_C_WW_HELD counts weight-window splits
+/* Counters summed over a run, in this order.  MC_C_SCORES counts tally updates (track length: one
+ * per mesh cell and time bin a flight crosses; time crossing: one per time point a flight spans).
+ * MC_C_WW_KILL counts particles removed by a roulette (weight windows or the implicit-capture
+ * weight cutoff).  MC_C_WW_HELD counts weight-window splits
  * not made because the particle store was more than half full: a split is optional (the particle
  * keeps its weight, which is unbiased), so bad windows slow a run down instead of overflowing
  * it; a run with held splits is no longer independent of the GPU's schedule. */
@@ -223,12 +253,14 @@ int mc_run_tune(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run
  * runs cannot hide a failed one. */
 int mc_wait(mc_problem* p);
 
-/* Shape of a tally: {nz, ny, nx, G, nt}.  tally_id == n_tallies addresses the leakage tally,
- * shape {1, 1, n_surfaces, 1, 1}: weight leaving through each vacuum surface. */
+/* Shape of a tally: {nz, ny, nx, G, nt} (track length) or {nz, ny, nx, G, nt + 1} (time
+ * crossing).  tally_id == n_tallies addresses the leakage tally, shape {1, 1, n_surfaces, 1, 1}:
+ * weight leaving through each vacuum surface. */
 int mc_tally_shape(const mc_problem* p, int tally_id, int64_t shape[5]);
 
 /* Copies the per-source-particle mean and its standard error (from the spread of the batch
- * means) of every bin of a tally into host arrays of n >= bins elements.  Synchronises. */
+ * means) of every bin of a tally into host arrays of n >= bins elements (time-crossing bins
+ * already multiplied by their group speed).  Synchronises. */
 int mc_tally_get(mc_problem* p, int tally_id, double* mean, double* std_err, size_t n);
 
 /* Copies the per-batch means per source particle, out[n_batches][bins] (n >= n_batches * bins),

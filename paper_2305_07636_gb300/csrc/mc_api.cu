@@ -74,6 +74,14 @@ struct PoolBlock {
 static std::mutex g_pool_mu;
 static std::multimap<size_t, PoolBlock> g_pool;
 
+int check_implicit_opts(const mc_run_opts& o) {
+  if (o.implicit_capture != 0 && o.implicit_capture != 1) return fail(MC_ERR_INVALID, "implicit_capture must be 0 or 1");
+  if (o.implicit_capture &&
+      !(std::isfinite(o.wr_cutoff) && std::isfinite(o.wr_survival) && o.wr_cutoff >= 0.0 && o.wr_survival > o.wr_cutoff))
+    return fail(MC_ERR_INVALID, "implicit capture needs 0 <= wr_cutoff < wr_survival (finite)");
+  return MC_OK;
+}
+
 int pool_alloc(void** out, size_t bytes, int dev) {
   {
     std::lock_guard<std::mutex> lk(g_pool_mu);
@@ -215,15 +223,20 @@ int validate(const mc_problem_desc* d) {
     const mc_mesh_tally& T = d->tallies[t];
     const int n[4] = {T.nx, T.ny, T.nz, T.nt};
     const double* e[4] = {T.x, T.y, T.z, T.t};
+    if (T.estimator != MC_EST_TRACK_LENGTH && T.estimator != MC_EST_TIME_CROSSING)
+      return fail(MC_ERR_INVALID, "tally %d: unknown estimator %d", t, T.estimator);
+    const bool crossing = T.estimator == MC_EST_TIME_CROSSING;
     for (int k = 0; k < 4; ++k) {
       if (n[k] < 1 || n[k] > (1 << 16) || !e[k]) return fail(MC_ERR_INVALID, "tally %d axis %d: bad size", t, k);
       for (int i = 0; i <= n[k]; ++i) {
         if (std::isnan(e[k][i])) return fail(MC_ERR_INVALID, "tally %d: NaN edge", t);
         if ((i > 0 && i < n[k] && !std::isfinite(e[k][i])) || (i > 0 && !(e[k][i] > e[k][i - 1])))
           return fail(MC_ERR_INVALID, "tally %d axis %d: edges must increase (infinite only at the ends)", t, k);
+        if (k == 3 && crossing && !std::isfinite(e[k][i]))
+          return fail(MC_ERR_INVALID, "tally %d: time-crossing points must be finite", t);
       }
     }
-    bins += (uint64_t)T.nx * T.ny * T.nz * T.nt * G;
+    bins += (uint64_t)T.nx * T.ny * T.nz * (T.nt + (crossing ? 1 : 0)) * G;
   }
   if (bins + d->n_surfaces > (1ull << 30)) return fail(MC_ERR_INVALID, "tallies too large");
   if (!(d->t_census > 0.0)) return fail(MC_ERR_INVALID, "t_census must be > 0 (inf for steady state)");
@@ -382,8 +395,10 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
     D.o_et = B.put(et);
     D.o_etf = B.put(etf);
     D.bin_offset = off;
-    D.n_bins = T.nx * T.ny * T.nz * G * T.nt;
-    D.deal = deals_time_pieces(T.nx, T.ny, T.nz, T.nt) ? 1 : 0;
+    D.est = T.estimator;
+    D.nval = T.nt + (T.estimator == MC_EST_TIME_CROSSING ? 1 : 0);
+    D.n_bins = T.nx * T.ny * T.nz * G * D.nval;
+    D.deal = (T.estimator == MC_EST_TRACK_LENGTH && deals_time_pieces(T.nx, T.ny, T.nz, T.nt)) ? 1 : 0;
     off += D.n_bins;
   }
   H.leak_offset = off;
@@ -427,6 +442,9 @@ void fill_run_params(const mc_problem* p, const mc_run_opts& o, uint64_t n_histo
   P.blob = (const uint4*)p->d_blob[fp64].ptr;
   P.seed = seed;
   P.max_iter = o.max_iterations ? o.max_iterations : (1ull << 20);
+  P.implicit = o.implicit_capture;
+  P.wr_cutoff = o.wr_cutoff;
+  P.wr_survival = o.wr_survival;
   if (o.ww_enable) {
     const double* base = (const double*)p->d_ww.ptr;
     P.ww_on = 1;
@@ -455,6 +473,8 @@ void mc_run_opts_default(mc_run_opts* o) {
   o->fixed_bits = 32;
   o->n_batches = 32;
   o->aggregate_atomics = -1;
+  o->wr_cutoff = 0.25;
+  o->wr_survival = 0.5;
 }
 
 int mc_problem_create(const mc_problem_desc* d, mc_problem** out) {
@@ -476,9 +496,11 @@ int mc_problem_create(const mc_problem_desc* d, mc_problem** out) {
     h.n[1] = T.ny;
     h.n[2] = T.nz;
     h.n[3] = T.nt;
+    h.est = T.estimator;
+    h.nval = T.nt + (T.estimator == MC_EST_TIME_CROSSING ? 1 : 0);
     const double* e[4] = {T.x, T.y, T.z, T.t};
     for (int k = 0; k < 4; ++k) h.e[k].assign(e[k], e[k] + h.n[k] + 1);
-    p->deal = p->deal || deals_time_pieces(T.nx, T.ny, T.nz, T.nt);
+    p->deal = p->deal || (T.estimator == MC_EST_TRACK_LENGTH && deals_time_pieces(T.nx, T.ny, T.nz, T.nt));
     p->tallies.push_back(h);
   }
   for (int i = 0; i < 3; ++i) p->src_center[i] = 0.5 * (d->source.lo[i] + d->source.hi[i]);
@@ -555,6 +577,7 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
     return fail(MC_ERR_INVALID, "block_size must be a multiple of 32 in [32,256]");
   if (o.ww_enable && !p->ww_set) return fail(MC_ERR_STATE, "weight windows enabled but no table set");
   if (o.algorithm != MC_ALG_EVENT && o.algorithm != MC_ALG_HISTORY) return fail(MC_ERR_INVALID, "algorithm");
+  if (check_implicit_opts(o) != MC_OK) return MC_ERR_INVALID;
   int dev;
   int rc = current_device(&dev);
   if (rc != MC_OK) return rc;
@@ -742,7 +765,7 @@ int mc_tally_shape(const mc_problem* p, int tally_id, int64_t shape[5]) {
   shape[1] = T.n[1];
   shape[2] = T.n[0];
   shape[3] = p->G;
-  shape[4] = T.n[3];
+  shape[4] = T.nval;
   return MC_OK;
 }
 
@@ -787,9 +810,11 @@ int mc_tally_get(mc_problem* p, int tally_id, double* mean, double* std_err, siz
       sv[i] = (s2 - s1 * s1 / B) / (B * (B - 1.0));
     }
   }
+  const char* blob64 = reinterpret_cast<const char*>(p->blob[1].data());
   for (size_t i = 0; i < nbins; ++i) {
-    if (mean) mean[i] = mv[i];
-    if (std_err) std_err[i] = sv[i] > 0.0 ? std::sqrt(sv[i]) : 0.0;
+    const double f = bin_value_factor(blob64, first + i);
+    if (mean) mean[i] = mv[i] * f;
+    if (std_err) std_err[i] = (sv[i] > 0.0 ? std::sqrt(sv[i]) : 0.0) * f;
   }
   return MC_OK;
 }
@@ -829,11 +854,12 @@ int mc_tally_batches(mc_problem* p, int tally_id, double* out, size_t n, int* n_
     }
     const uint64_t lo = ((uint64_t)j * p->n_hist + nb - 1) / nb, hi = ((uint64_t)(j + 1) * p->n_hist + nb - 1) / nb;
     const double cnt = (double)(hi - lo);
+    const char* blob64 = reinterpret_cast<const char*>(p->blob[1].data());
     for (size_t i = 0; i < nbins; ++i) {
       double x;
       if (p->tally_fp64) std::memcpy(&x, &raw[i], 8);
       else x = (double)raw[i] / p->fixed_scale;
-      out[(size_t)j * nbins + i] = x / cnt;
+      out[(size_t)j * nbins + i] = x / cnt * bin_value_factor(blob64, first + i);
     }
   }
   return MC_OK;
@@ -1011,7 +1037,7 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 // Per-bin mean and standard error from the batch statistics, or NaN everywhere if the run failed.
 __global__ void k_static_finalize(const Ctl* ctl, const void* stats, int fp64, uint64_t bins, double n_hist,
-                                  double nb, double inv_scale, double* mean, double* std_err) {
+                                  double nb, double inv_scale, const char* blob64, double* mean, double* std_err) {
   const bool bad = ctl->status != 0;
   const double nan = __longlong_as_double(0x7FF8000000000000ll);
   const double nbar = n_hist / nb;
@@ -1031,8 +1057,9 @@ __global__ void k_static_finalize(const Ctl* ctl, const void* stats, int fp64, u
       m = (double)sum[b] * inv_scale / n_hist;
       var = (sq / (nbar * nbar) - s1 * s1 / nb) / (nb * (nb - 1.0));
     }
-    mean[b] = bad ? nan : m;
-    std_err[b] = bad ? nan : (var > 0.0 ? sqrt(var) : 0.0);
+    const double f = bin_value_factor(blob64, b);  // v_g for time-crossing bins
+    mean[b] = bad ? nan : m * f;
+    std_err[b] = bad ? nan : (var > 0.0 ? sqrt(var) : 0.0) * f;
   }
 }
 }  // namespace
@@ -1055,6 +1082,7 @@ extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t
   if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 256 || o.block_size % 32))
     return fail(MC_ERR_INVALID, "block_size must be a multiple of 32 in [32,256]");
   if (o.algorithm != MC_ALG_EVENT && o.algorithm != MC_ALG_HISTORY) return fail(MC_ERR_INVALID, "algorithm");
+  if (check_implicit_opts(o) != MC_OK) return MC_ERR_INVALID;
   if (o.log_count > 0) return fail(MC_ERR_INVALID, "mc_run_static keeps no event log");
   if (o.ww_enable && !p->ww_set) return fail(MC_ERR_STATE, "weight windows enabled but no table set");
   if (o.bank_capacity > kStaticBank)
@@ -1120,6 +1148,9 @@ extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t
   P.seed = seed;
   P.max_iter = o.max_iterations ? o.max_iterations : (1ull << 20);
   P.spin_limit = 1ull << 22;
+  P.implicit = o.implicit_capture;
+  P.wr_cutoff = o.wr_cutoff;
+  P.wr_survival = o.wr_survival;
   if (o.ww_enable) {
     const double* wb = (const double*)p->d_ww.ptr;
     P.ww_on = 1;
@@ -1153,7 +1184,8 @@ extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t
   CK(launch_batch_stats(P.tally, P.tally_fp64, bins, nb, 1, n_histories, base + off_stats, s));
   unsigned g = (unsigned)std::min<uint64_t>((bins + 255) / 256, 1024);
   k_static_finalize<<<g ? g : 1, 256, 0, s>>>((const Ctl*)base, base + off_stats, P.tally_fp64, bins,
-                                              (double)n_histories, (double)nb, 1.0 / P.fixed_scale, mean, std_err);
+                                              (double)n_histories, (double)nb, 1.0 / P.fixed_scale,
+                                              (const char*)p->d_blob[1].ptr, mean, std_err);
   CK(cudaGetLastError());
   return MC_OK;
 }

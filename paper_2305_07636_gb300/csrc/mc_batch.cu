@@ -341,7 +341,9 @@ constexpr uint64_t kDefaultStack = 2048;
 template <typename R>
 cudaError_t batch_occupancy(int block, size_t smem, bool wide, bool deal, int* per_sm) {
   const void* f = batch_fn<R>(wide, deal);
-  if (smem > 48 * 1024) {
+  // opt in for the exact size: the default limit (48 KB less the kernel's static shared memory)
+  // can be exceeded by a dynamic size just under 48 KB
+  {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
@@ -488,6 +490,7 @@ int mc_run_batch(mc_problem* const* ps, int n, const uint64_t* n_hist, uint64_t 
     return fail(MC_ERR_INVALID, "block_size must be a multiple of 32 in [32,256]");
   if (o.batch_unit < 0 || o.batch_unit > (1 << 20)) return fail(MC_ERR_INVALID, "batch_unit outside [0,2^20]");
   if (o.blocks_per_sm < 0) return fail(MC_ERR_INVALID, "blocks_per_sm < 0");
+  if (check_implicit_opts(o) != MC_OK) return MC_ERR_INVALID;
   const uint64_t stack_cap = o.bank_capacity ? o.bank_capacity : kDefaultStack;
   if (stack_cap < 64 || stack_cap > (1ull << 24)) return fail(MC_ERR_INVALID, "bank_capacity outside [64,2^24]");
   int dev;

@@ -674,6 +674,51 @@ __device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Pa
     const R* et = time_edges<R>(base, D);
     const int n[3] = {D.nx, D.ny, D.nz};
     const int nt = D.nt;
+    if (D.est == MC_EST_TIME_CROSSING) {
+      // Time-crossing estimator: at every time point t_j with t0 <= t_j < t0 + l / v the particle
+      // scores its weight into the mesh cell it occupies at t_j (the readback multiplies by v_g).
+      // One point per lane per warp-uniform round.
+      bool live = active;
+      int j = 0;
+      R dj = R(0);  // distance along the flight to point j
+      if (live) {
+        int lo = 0, hi = nt + 1;  // first point at or after the flight's start
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (et[mid] < t0) lo = mid + 1;
+          else hi = mid;
+        }
+        j = lo;
+        if (j > nt) live = false;
+        else {
+          dj = (et[j] - t0) * v;
+          live = dj < l;
+        }
+      }
+      const uint32_t cb = (uint32_t)(batch_base + (uint64_t)D.bin_offset + (uint64_t)g * D.nval);
+      const int cs = T.G * D.nval;
+      while (__any_sync(kAll, live)) {
+        bool emit = false;
+        uint32_t slot = 0;
+        if (live) {
+          const R sd = dj > R(0) ? dj : R(0);
+          const int ix = bin_search(e[0], n[0], p.x + sd * p.ux), iy = bin_search(e[1], n[1], p.y + sd * p.uy),
+                    iz = bin_search(e[2], n[2], p.z + sd * p.uz);
+          if (ix >= 0 && ix < n[0] && iy >= 0 && iy < n[1] && iz >= 0 && iz < n[2]) {
+            emit = true;
+            slot = cb + (uint32_t)(((iz * n[1] + iy) * n[0] + ix) * cs + j);
+          }
+          ++j;
+          if (j > nt) live = false;
+          else {
+            dj = (et[j] - t0) * v;
+            live = dj < l;
+          }
+        }
+        stage(emit, slot, R(1), w, wscale);
+      }
+      continue;
+    }
     R pos[3], u[3], sn[3], inv[3], s = R(0), stn = rinf<R>();  // stn: distance to time edge it+1
     int idx[3], step[3], it = 0;
     bool live = active;

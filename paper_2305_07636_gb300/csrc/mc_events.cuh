@@ -161,7 +161,21 @@ __device__ bool do_collision(const RunParams& P, const Tab<R>& T, Part<R>& p, ui
   const int g = (int)pk_g(p.pk);
   const int m = material_of(T, p.pk, p.elem);
   const R St = T.st[m * G + g];
-  const R xi = draw<R>(P.seed, p.tlo, p.thi, p.k, 0).b * St;
+  const R keep = T.ssf[m * G + g];  // Sigma_s + Sigma_f: the part of Sigma_t that is not capture
+  const R u0 = draw<R>(P.seed, p.tlo, p.thi, p.k, 0).b;
+  // analog: the channel is drawn over Sigma_t.  Implicit capture: over Sigma_s + Sigma_f, and the
+  // surviving weight takes the non-capture probability (Sigma_s + Sigma_f) / Sigma_t; a collision
+  // whose non-capture probability is 0 captures as in the analog walk
+  R xi = u0 * St;
+  double wkeep = 1.0;
+  if (P.implicit) {
+    if (keep > R(0)) {
+      xi = u0 * keep;
+      wkeep = (double)keep / (double)St;
+    } else {
+      xi = rinf<R>();
+    }
+  }
   bump(bc, MC_C_COLLISION);
   if (xi < T.ss[m * G + g]) {
     bump(bc, MC_C_SCATTER);
@@ -171,14 +185,28 @@ __device__ bool do_collision(const RunParams& P, const Tab<R>& T, Part<R>& p, ui
     log_event(P, T, p, 0, 0, 0);
     p.pk = (p.pk & ~0x1Fu) | (uint32_t)ng;
     iso_dir(R(2) * b1.b - R(1), b2.a, p.ux, p.uy, p.uz);
+    if (P.implicit) {
+      p.w *= wkeep;
+      if (p.w < P.wr_cutoff) {
+        // weight cutoff: survive with probability w / w_s at weight w_s (unbiased)
+        const R u = draw<R>(P.seed, p.tlo, p.thi, p.k, 3).b;
+        if ((double)u < p.w / P.wr_survival) {
+          p.w = P.wr_survival;
+        } else {
+          bump(bc, MC_C_WW_KILL);
+          return false;
+        }
+      }
+    }
     return weight_window(P, T, p, Bout, bcount, bc);
   }
-  if (xi < T.ssf[m * G + g]) {
+  if (xi < keep) {
     bump(bc, MC_C_PRODUCTION);
     const R u = draw<R>(P.seed, p.tlo, p.thi, p.k, 3).a;
     const int n = (int)floor(T.nu[m * G + g] + u);
     for (int j = 0; j < n; ++j) {
       Part<R> c = p;
+      c.w = p.w * wkeep;
       const uint2 t = child_tag(P.seed, p.tlo, p.thi, p.k, (uint32_t)j, kChildMark);
       c.tlo = t.x;
       c.thi = t.y;

@@ -16,6 +16,8 @@ int fail(int code, const char* fmt, ...);
 // maps a CUDA error to MC_ERR_OOM / MC_ERR_CUDA with its message
 int cuda_fail(cudaError_t e, const char* what);
 int current_device(int* dev);
+// validates the implicit-capture fields of run options (MC_OK or MC_ERR_INVALID with a message)
+int check_implicit_opts(const mc_run_opts& o);
 
 // device blocks are recycled across problems instead of returned to the driver; a block must be
 // returned with the size it was requested with
@@ -47,6 +49,8 @@ struct DevBuf {
 
 struct HostTally {
   int n[4];
+  int est = MC_EST_TRACK_LENGTH;
+  int nval = 0;  // values along time per (cell, group): n[3] bins or n[3] + 1 points
   std::vector<double> e[4];
 };
 

@@ -53,6 +53,9 @@ struct TallyDesc {
   int n_bins;
   int o_etf;                   // time edges rounded to float (FP32 tracking)
   int deal;                    // 1: the scoring walk deals this tally's time pieces out over the warp
+  int est;                     // MC_EST_TRACK_LENGTH or MC_EST_TIME_CROSSING
+  int nval;                    // values per (cell, group) along time: nt bins or nt + 1 points
+  int pad0, pad1;
 };
 
 // A tally's time pieces are dealt out over the warp when its time axis is much finer than its
@@ -79,6 +82,22 @@ struct TableHeader {
   TallyDesc tally[kMaxTallies];
   int blob_bytes, pad2, pad3, pad4;
 };
+
+// Factor that turns a bin's accumulated score into the tally value: v_g for a time-crossing bin
+// (the device accumulates the weight w of a particle at a time point; its flux score is w v_g),
+// 1 otherwise.  `blob` is the FP64 table blob (speeds stored as double).
+__host__ __device__ inline double bin_value_factor(const char* blob, uint64_t bin) {
+  const TableHeader* H = reinterpret_cast<const TableHeader*>(blob);
+  for (int t = 0; t < H->n_tally; ++t) {
+    const TallyDesc& D = H->tally[t];
+    if (bin >= (uint64_t)D.bin_offset && bin < (uint64_t)D.bin_offset + (uint64_t)D.n_bins) {
+      if (D.est != MC_EST_TIME_CROSSING) return 1.0;
+      const int g = (int)(((bin - (uint64_t)D.bin_offset) / (uint64_t)D.nval) % (uint64_t)H->G);
+      return reinterpret_cast<const double*>(blob + H->o_v)[g];
+    }
+  }
+  return 1.0;
+}
 
 // ---- device control block, one per problem
 struct Ctl {
@@ -124,7 +143,9 @@ struct RunParams {
   const double* ww_edges;  // x[nx+1], y[ny+1], z[nz+1]
   const double* ww_center; // [nz][ny][nx][G]
   double ww_upper, ww_lower;
-  int ww_split_max, pad;
+  int ww_split_max;
+  int implicit;            // implicit capture with a weight-cutoff roulette
+  double wr_cutoff, wr_survival;
 };
 
 }  // namespace mcgb

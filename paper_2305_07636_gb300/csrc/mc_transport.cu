@@ -278,7 +278,9 @@ cudaError_t launch_transport(const RunParams& P, int grid, int block, size_t sme
 template <typename R>
 cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide, bool deal) {
   const void* f = transport_fn<R>(wide, deal);
-  if (smem > 48 * 1024) {
+  // opt in for the exact size: the default limit (48 KB less the kernel's static shared memory)
+  // can be exceeded by a dynamic size just under 48 KB
+  {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }

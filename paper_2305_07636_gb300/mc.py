@@ -68,7 +68,10 @@ class mc_source(C.Structure):
 
 class mc_mesh_tally(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("nt", C.c_int),
-                ("x", DP), ("y", DP), ("z", DP), ("t", DP)]
+                ("x", DP), ("y", DP), ("z", DP), ("t", DP), ("estimator", C.c_int)]
+
+
+ESTIMATOR = {"track": 0, "crossing": 1}  # mc_estimator
 
 
 class mc_problem_desc(C.Structure):
@@ -89,7 +92,8 @@ class mc_run_opts(C.Structure):
                 ("ww_enable", C.c_int), ("log_first", C.c_uint64), ("log_count", C.c_uint64),
                 ("log_capacity", C.c_uint64), ("first_history", C.c_uint64),
                 ("algorithm", C.c_int), ("drain_threshold", C.c_uint64),
-                ("tally_stripes", C.c_int), ("batch_unit", C.c_int)]
+                ("tally_stripes", C.c_int), ("batch_unit", C.c_int),
+                ("implicit_capture", C.c_int), ("wr_cutoff", C.c_double), ("wr_survival", C.c_double)]
 
 
 class mc_event(C.Structure):
@@ -267,6 +271,7 @@ class _Desc:
             ta[i].nx, ta[i].ny = len(t["x"]) - 1, len(t["y"]) - 1
             ta[i].nz, ta[i].nt = len(t["z"]) - 1, len(t["t"]) - 1
             ta[i].x, ta[i].y, ta[i].z, ta[i].t = dp(t["x"]), dp(t["y"]), dp(t["z"]), dp(t["t"])
+            ta[i].estimator = ESTIMATOR[t.get("estimator", "track")]
         self.keep.append(ta)
         d.n_tallies, d.tallies = len(tals), ta
         d.t_census = prob["t_census"]
