@@ -121,6 +121,18 @@ def oracle_batch_sample(probs, nh, threads, frac, seed):
     return n1, time.perf_counter() - t0
 
 
+def launches_per_run(prob):
+    """Kernels one mc_run launches: transport and batch statistics, plus the range-walk
+    reconstruction when a track-length tally's time axis is much finer than its mesh (the
+    library's rule: nt >= 3 and nt >= 4 (nx + ny + nz))."""
+    n = 2
+    for t in prob["tallies"]:
+        nx, ny, nz, nt = (len(t[k]) - 1 for k in ("x", "y", "z", "t"))
+        if t.get("estimator", "track") == "track" and nt >= 3 and nt >= 4 * (nx + ny + nz):
+            return n + 1
+    return n
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -664,7 +676,7 @@ def main():
                   "ms_in_history_style_tail": drain_ms},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": launches_per_run(prob) * args.steps,
         "clocks": clk,
         "wall_s": wall,
         "step_ms": [round(x, 4) for x in step_ms],

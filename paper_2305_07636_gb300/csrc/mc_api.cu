@@ -24,10 +24,12 @@
 namespace mcgb {
 template <typename R>
 cudaError_t launch_transport(const RunParams& P, int grid, int block, size_t smem, cudaStream_t s, bool wide,
-                             bool deal);
+                             bool range);
 template <typename R>
-cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide, bool deal);
-cudaError_t launch_batch_stats(const void* tally, int fp64, uint64_t bins, int nb, int stripes,
+cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide, bool range);
+cudaError_t launch_reconstruct(void* tally, const char* blob64, uint64_t rows, uint64_t row, int nb, int stripes,
+                               int fp64, cudaStream_t s);
+cudaError_t launch_batch_stats(const void* tally, int fp64, uint64_t bins, uint64_t row, int nb, int stripes,
                                uint64_t n_hist, void* out, cudaStream_t s);
 cudaError_t launch_philox(uint64_t seed, const uint4* ctr, uint4* out, uint64_t n, cudaStream_t s);
 cudaError_t launch_atomic_probe(unsigned long long* a, unsigned long long span, int grid, int iters, unsigned salt,
@@ -237,6 +239,7 @@ int validate(const mc_problem_desc* d) {
       }
     }
     bins += (uint64_t)T.nx * T.ny * T.nz * (T.nt + (crossing ? 1 : 0)) * G;
+    if (!crossing && ranges_time_bins(T.nx, T.ny, T.nz, T.nt)) bins += (uint64_t)T.nx * T.ny * T.nz * (T.nt + 1) * G;
   }
   if (bins + d->n_surfaces > (1ull << 30)) return fail(MC_ERR_INVALID, "tallies too large");
   if (!(d->t_census > 0.0)) return fail(MC_ERR_INVALID, "t_census must be > 0 (inf for steady state)");
@@ -378,7 +381,7 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
     H.o_lpin = B.put(none);
   }
   H.n_tally = d->n_tallies;
-  int off = 0;
+  int off = 0, doff = 0;
   for (int t = 0; t < d->n_tallies; ++t) {
     const mc_mesh_tally& T = d->tallies[t];
     TallyDesc& D = H.tally[t];
@@ -398,11 +401,14 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
     D.est = T.estimator;
     D.nval = T.nt + (T.estimator == MC_EST_TIME_CROSSING ? 1 : 0);
     D.n_bins = T.nx * T.ny * T.nz * G * D.nval;
-    D.deal = (T.estimator == MC_EST_TRACK_LENGTH && deals_time_pieces(T.nx, T.ny, T.nz, T.nt)) ? 1 : 0;
+    D.range = (T.estimator == MC_EST_TRACK_LENGTH && ranges_time_bins(T.nx, T.ny, T.nz, T.nt)) ? 1 : 0;
+    D.diff_offset = doff;
+    if (D.range) doff += T.nx * T.ny * T.nz * G * (T.nt + 1);
     off += D.n_bins;
   }
   H.leak_offset = off;
   H.total_bins = off + H.n_surf;
+  H.total_diff = doff;
   B.b.resize((B.b.size() + 15) & ~size_t(15), 0);
   H.blob_bytes = (int)B.b.size();
   *B.hdr() = H;
@@ -423,7 +429,8 @@ void fill_run_params(const mc_problem* p, const mc_run_opts& o, uint64_t n_histo
   P.sticky = (int*)p->d_sticky.ptr;
   P.tally = p->d_tally.ptr;
   P.tally_stripes = stripes;
-  P.stripe_stride = (uint64_t)nb * bins;
+  P.row = p->row;
+  P.stripe_stride = (uint64_t)nb * p->row;
   P.tally_fp64 = o.tally_mode == MC_TALLY_FP64;
   // auto: aggregate only a small tally that could not be striped (many lanes per hot bin)
   P.aggregate = o.aggregate_atomics >= 0
@@ -500,7 +507,7 @@ int mc_problem_create(const mc_problem_desc* d, mc_problem** out) {
     h.nval = T.nt + (T.estimator == MC_EST_TIME_CROSSING ? 1 : 0);
     const double* e[4] = {T.x, T.y, T.z, T.t};
     for (int k = 0; k < 4; ++k) h.e[k].assign(e[k], e[k] + h.n[k] + 1);
-    p->deal = p->deal || (T.estimator == MC_EST_TRACK_LENGTH && deals_time_pieces(T.nx, T.ny, T.nz, T.nt));
+    p->range = p->range || (T.estimator == MC_EST_TRACK_LENGTH && ranges_time_bins(T.nx, T.ny, T.nz, T.nt));
     p->tallies.push_back(h);
   }
   for (int i = 0; i < 3; ++i) p->src_center[i] = 0.5 * (d->source.lo[i] + d->source.hi[i]);
@@ -512,6 +519,9 @@ int mc_problem_create(const mc_problem_desc* d, mc_problem** out) {
   const TableHeader* H = reinterpret_cast<const TableHeader*>(p->blob[0].data());
   p->total_bins = H->total_bins;
   p->leak_offset = H->leak_offset;
+  p->row = (uint64_t)H->total_bins + (uint64_t)H->total_diff;
+  for (int t = 0; t < H->n_tally; ++t)
+    if (H->tally[t].range) p->range_rows += (uint64_t)H->tally[t].nx * H->tally[t].ny * H->tally[t].nz * H->G;
   rc = current_device(&p->dev);
   for (int i = 0; i < 2 && rc == MC_OK; ++i) {
     rc = p->d_blob[i].ensure(p->blob[i].size(), p->dev);
@@ -598,14 +608,15 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   const uint64_t bins = (uint64_t)p->total_bins;
   // small tallies get up to 16 copies (within a 64 MB budget) to spread same-bin atomics
   uint32_t stripes = o.tally_stripes > 0 ? (uint32_t)o.tally_stripes : 1u;
+  const uint64_t row = p->row;  // bins, then the range walk's difference slots
   if (o.tally_stripes <= 0) {
-    const double copy_bytes = (double)nb * (double)bins * 8.0;
+    const double copy_bytes = (double)nb * (double)row * 8.0;
     stripes = (uint32_t)std::max(1.0, std::min(16.0, std::floor(64.0 * 1048576.0 / copy_bytes)));
   }
   if (stripes > 256) return fail(MC_ERR_INVALID, "tally_stripes above 256");
-  if ((double)stripes * nb * (double)bins >= 4294967296.0)
+  if ((double)stripes * nb * (double)row >= 4294967296.0)
     return fail(MC_ERR_INVALID, "tally bins x batches x stripes must stay below 2^32");
-  rc = p->d_tally.ensure((size_t)stripes * nb * bins * 8, p->dev);
+  rc = p->d_tally.ensure((size_t)stripes * nb * row * 8, p->dev);
   if (rc == MC_OK) rc = p->d_stats.ensure((size_t)3 * bins * 8, p->dev);
   if (rc != MC_OK) return rc;
   uint64_t log_cap = 0;
@@ -639,19 +650,19 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   P.log_first = o.log_first;
   P.log_count = o.log_count;
   CK(cudaMemsetAsync(p->d_ctl.ptr, 0, sizeof(Ctl), s));
-  CK(cudaMemsetAsync(p->d_tally.ptr, 0, (size_t)stripes * nb * bins * 8, s));
+  CK(cudaMemsetAsync(p->d_tally.ptr, 0, (size_t)stripes * nb * row * 8, s));
   if (P.log) CK(cudaMemsetAsync(p->d_log.ptr, 0, log_cap * sizeof(mc_event), s));
   const int block = o.block_size ? o.block_size : 256;
   // tables + per-warp flight queues (64 slots) + per-warp tally staging (128 x 12 B)
   const size_t smem = P.blob_bytes + (size_t)(block / 32) * (64 * 16 * lanes + 128 * 12);
   int per_sm = 0;
   // blocks_per_sm == 2 selects the 128-register build of the kernel, any other explicit value the
-  // 80-register one; 0 takes the 128-register build when a tally deals its time pieces out over the
-  // warp (that walk needs the registers) and the 80-register build otherwise
-  const bool deal = p->deal;
-  const bool wide = o.blocks_per_sm == 2 || (o.blocks_per_sm == 0 && deal);
-  CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm, wide, deal)
-          : transport_occupancy<float>(block, smem, &per_sm, wide, deal));
+  // 80-register one; 0 takes the 128-register build when a tally is scored by the range walk
+  // (that walk needs the registers) and the 80-register build otherwise
+  const bool range = p->range;
+  const bool wide = o.blocks_per_sm == 2 || (o.blocks_per_sm == 0 && range);
+  CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm, wide, range)
+          : transport_occupancy<float>(block, smem, &per_sm, wide, range));
   if (per_sm < 1) return fail(MC_ERR_CUDA, "transport kernel does not fit on an SM (block %d, smem %zu)", block, smem);
   if (o.blocks_per_sm > 0) per_sm = std::min(per_sm, std::max(1, o.blocks_per_sm * 256 / block));
   int sms = 0;
@@ -659,10 +670,12 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   const int grid = sms * per_sm;
   P.drain_threshold = o.drain_threshold ? o.drain_threshold : (uint64_t)2 * grid * block;
   CK(cudaEventRecord(p->ev[0], s));
-  CK(fp64 ? launch_transport<double>(P, grid, block, smem, s, wide, deal)
-          : launch_transport<float>(P, grid, block, smem, s, wide, deal));
+  CK(fp64 ? launch_transport<double>(P, grid, block, smem, s, wide, range)
+          : launch_transport<float>(P, grid, block, smem, s, wide, range));
   CK(cudaEventRecord(p->ev[1], s));
-  CK(launch_batch_stats(P.tally, P.tally_fp64, bins, nb, (int)stripes, n_histories, p->d_stats.ptr, s));
+  if (p->range)
+    CK(launch_reconstruct(P.tally, (const char*)p->d_blob[1].ptr, p->range_rows, row, nb, (int)stripes, P.tally_fp64, s));
+  CK(launch_batch_stats(P.tally, P.tally_fp64, bins, row, nb, (int)stripes, n_histories, p->d_stats.ptr, s));
   CK(cudaEventRecord(p->ev[2], s));
   p->has_run = 1;
   p->batched = 0;
@@ -837,8 +850,8 @@ int mc_tally_batches(mc_problem* p, int tally_id, double* out, size_t n, int* n_
   for (int j = 0; j < nb; ++j) {
     for (uint32_t c = 0; c < p->stripes; ++c) {
       CK(cudaMemcpy(c ? part.data() : raw.data(),
-                    (const char*)p->d_tally.ptr + ((size_t)c * nb * bins + (size_t)j * bins + first) * 8, nbins * 8,
-                    cudaMemcpyDeviceToHost));
+                    (const char*)p->d_tally.ptr + ((size_t)c * nb * p->row + (size_t)j * p->row + first) * 8,
+                    nbins * 8, cudaMemcpyDeviceToHost));
       if (c)
         for (size_t i = 0; i < nbins; ++i) {
           if (p->tally_fp64) {
@@ -1103,13 +1116,13 @@ extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t
   const size_t off_banks = off_sticky + 256;
   const size_t bank_bytes = (size_t)cap * 16 * lanes;
   const size_t off_tally = align256(off_banks + 4 * bank_bytes);
-  const size_t tally_bytes = (size_t)nb * bins * 8;
+  const size_t tally_bytes = (size_t)nb * p->row * 8;
   const size_t off_stats = align256(off_tally + tally_bytes);
   const size_t need = off_stats + (size_t)3 * bins * 8;
   if (need > (size_t)MC_STATIC_SCRATCH_BYTES)
     return fail(MC_ERR_INVALID,
                 "%d batches x %llu bins need %zu bytes of scratch; the static scratch holds %zu (use mc_run)", nb,
-                (unsigned long long)bins, need, (size_t)MC_STATIC_SCRATCH_BYTES);
+                (unsigned long long)p->row, need, (size_t)MC_STATIC_SCRATCH_BYTES);
   unsigned char* base = nullptr;
   rc = static_scratch(dev, &base);
   if (rc != MC_OK) return rc;
@@ -1127,7 +1140,8 @@ extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t
   P.sticky = (int*)(base + off_sticky);
   P.tally = base + off_tally;
   P.tally_stripes = 1;
-  P.stripe_stride = (uint64_t)nb * bins;
+  P.row = p->row;
+  P.stripe_stride = (uint64_t)nb * p->row;
   P.tally_fp64 = o.tally_mode == MC_TALLY_FP64;
   P.aggregate = o.aggregate_atomics >= 0 ? o.aggregate_atomics : 1;
   P.fixed_scale = std::ldexp(1.0, o.fixed_bits);
@@ -1169,19 +1183,21 @@ extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t
   const int block = o.block_size ? o.block_size : 256;
   const size_t smem = P.blob_bytes + (size_t)(block / 32) * (64 * 16 * lanes + 128 * 12);
   int per_sm = 0;
-  const bool deal = p->deal;
-  const bool wide = o.blocks_per_sm == 2 || (o.blocks_per_sm == 0 && deal);
-  CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm, wide, deal)
-          : transport_occupancy<float>(block, smem, &per_sm, wide, deal));
+  const bool range = p->range;
+  const bool wide = o.blocks_per_sm == 2 || (o.blocks_per_sm == 0 && range);
+  CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm, wide, range)
+          : transport_occupancy<float>(block, smem, &per_sm, wide, range));
   if (per_sm < 1) return fail(MC_ERR_CUDA, "transport kernel does not fit on an SM (block %d, smem %zu)", block, smem);
   if (o.blocks_per_sm > 0) per_sm = std::min(per_sm, std::max(1, o.blocks_per_sm * 256 / block));
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int grid = sms * per_sm;
   P.drain_threshold = o.drain_threshold ? o.drain_threshold : (uint64_t)2 * grid * block;
-  CK(fp64 ? launch_transport<double>(P, grid, block, smem, s, wide, deal)
-          : launch_transport<float>(P, grid, block, smem, s, wide, deal));
-  CK(launch_batch_stats(P.tally, P.tally_fp64, bins, nb, 1, n_histories, base + off_stats, s));
+  CK(fp64 ? launch_transport<double>(P, grid, block, smem, s, wide, range)
+          : launch_transport<float>(P, grid, block, smem, s, wide, range));
+  if (p->range)
+    CK(launch_reconstruct(P.tally, (const char*)p->d_blob[1].ptr, p->range_rows, p->row, nb, 1, P.tally_fp64, s));
+  CK(launch_batch_stats(P.tally, P.tally_fp64, bins, p->row, nb, 1, n_histories, base + off_stats, s));
   unsigned g = (unsigned)std::min<uint64_t>((bins + 255) / 256, 1024);
   k_static_finalize<<<g ? g : 1, 256, 0, s>>>((const Ctl*)base, base + off_stats, P.tally_fp64, bins,
                                               (double)n_histories, (double)nb, 1.0 / P.fixed_scale,

@@ -41,6 +41,8 @@ struct __align__(16) BatchItem {
   uint64_t n_units;     // work units of the problem
   int caller_index;     // position in the caller's list
   int pad;
+  const char* blob64;   // the problem's FP64 tables on the device (range-walk reconstruction)
+  uint64_t range_rows;  // its (tally, cell, group) rows scored by the range walk
 };
 
 struct BatchHeader {
@@ -81,7 +83,7 @@ __device__ __forceinline__ void warp_copy16(void* dst, const void* src, size_t b
   for (size_t i = lane; i < bytes / 16; i += 32) d[i] = __ldg(s + i);
 }
 
-template <typename R, int MINB, bool DEAL>
+template <typename R, int MINB, bool RANGE>
 __global__ void __launch_bounds__(256, MINB)
     k_transport_batch(BatchHeader* bh, const BatchItem* items, unsigned long long* t_done, uint4* stacks,
                       int slot_bytes) {
@@ -124,7 +126,7 @@ __global__ void __launch_bounds__(256, MINB)
     __syncwarp();
     const RunParams& P = *wP;
     const Tab<R> T(blob);
-    const uint64_t bins = (uint64_t)T.h->total_bins;
+    const uint64_t row = P.row;  // tally elements per batch: bins, then difference slots
     const uint64_t ufirst = __ldg(&items[j].unit_first);
     unsigned scored = 0;
     uint64_t hn = 0, he = 0;  // histories of the claimed units still to start
@@ -205,14 +207,14 @@ __global__ void __launch_bounds__(256, MINB)
       uint32_t pend = PEND_NONE;
       Hit hit;
       const bool flies = have && flight_plan(P, T, p, bc, l, pend, hit);
-      score_segment_warp<R, DEAL>(T, P, p, l, (uint64_t)(p.elem >> 16) * bins, flies, stage, scored);
+      score_segment_warp<R, RANGE>(T, P, p, l, (uint64_t)(p.elem >> 16) * row, flies, stage, scored);
       if (flies) {
         bool alive = flight_finish(P, T, p, bc, l, pend, hit);
         if (alive && p.k + 1 >= P.max_iter) {
           set_status(P, MC_ERR_TIMEOUT);  // the per-particle event budget
           alive = false;
         }
-        if (alive) again = handle_pending(P, T, p, wP->B[0], sc, bc, bins, 0);
+        if (alive) again = handle_pending(P, T, p, wP->B[0], sc, bc, row, 0);
       }
       const unsigned m = __ballot_sync(0xFFFFFFFFu, again);
       if (again) queue_store(p, wq, kWarpQ, qn + __popc(m & lt));
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(256, MINB)
 // (blockIdx.x = problem), the per-problem completion times and the claim counter.
 __global__ void k_batch_clear(BatchHeader* bh, const BatchItem* items, unsigned long long* t_done) {
   const BatchItem& it = items[blockIdx.x];
-  const uint64_t words = (uint64_t)it.P.n_batches * it.bins;
+  const uint64_t words = (uint64_t)it.P.n_batches * it.P.row;
   long long* t = reinterpret_cast<long long*>(it.P.tally);
   for (uint64_t i = (uint64_t)blockIdx.y * blockDim.x + threadIdx.x; i < words; i += (uint64_t)gridDim.y * blockDim.x)
     t[i] = 0;
@@ -259,6 +261,19 @@ __global__ void k_batch_clear(BatchHeader* bh, const BatchItem* items, unsigned 
   }
 }
 
+// Range-walk reconstruction of every problem that has range rows (blockIdx.x = problem,
+// blockIdx.y strides over its (batch, row) pairs, one warp each).
+__global__ void k_batch_reconstruct_multi(const BatchHeader* bh, const BatchItem* items) {
+  const BatchItem& it = items[blockIdx.x];
+  const uint64_t rows = it.range_rows;
+  if (rows == 0) return;
+  const int nb = it.P.n_batches;
+  const uint64_t warps = (uint64_t)gridDim.y * (blockDim.x >> 5);
+  for (uint64_t wi = (uint64_t)blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5); wi < (uint64_t)nb * rows;
+       wi += warps)
+    reconstruct_warp(it.P.tally, it.blob64, it.P.row, nb, 1, bh->tally_fp64, (int)(wi / rows), wi % rows);
+}
+
 // Batch statistics of every problem (blockIdx.x = problem, blockIdx.y strides over its bins).
 __global__ void k_batch_stats_multi(const BatchHeader* bh, const BatchItem* items) {
   const BatchItem& it = items[blockIdx.x];
@@ -267,11 +282,11 @@ __global__ void k_batch_stats_multi(const BatchHeader* bh, const BatchItem* item
   for (uint64_t b = (uint64_t)blockIdx.y * blockDim.x + threadIdx.x; b < bins; b += (uint64_t)gridDim.y * blockDim.x) {
     if (bh->tally_fp64) {
       double* o = reinterpret_cast<double*>(it.stats);
-      stats_bin_fp64(reinterpret_cast<const double*>(it.P.tally), bins, nb, 1, (double)nb / (double)it.P.n_hist, b,
+      stats_bin_fp64(reinterpret_cast<const double*>(it.P.tally), it.P.row, nb, 1, (double)nb / (double)it.P.n_hist, b,
                      o[b], o[bins + b], o[2 * bins + b]);
     } else {
       char* o = reinterpret_cast<char*>(it.stats);
-      stats_bin_fixed(reinterpret_cast<const long long*>(it.P.tally), bins, nb, 1, b,
+      stats_bin_fixed(reinterpret_cast<const long long*>(it.P.tally), it.P.row, nb, 1, b,
                       reinterpret_cast<long long*>(o)[b], reinterpret_cast<unsigned long long*>(o + 8 * bins)[b],
                       reinterpret_cast<unsigned long long*>(o + 16 * bins)[b]);
     }
@@ -279,12 +294,12 @@ __global__ void k_batch_stats_multi(const BatchHeader* bh, const BatchItem* item
 }
 
 // the two register budgets of the batched kernel (FP64 tracking has only the wide one), each with
-// and without the time-bin dealing of the scoring walk
+// and without the range walk of the scoring
 template <typename R>
-static const void* batch_fn(bool wide, bool deal) {
+static const void* batch_fn(bool wide, bool range) {
   if constexpr (sizeof(R) == 8)
-    return deal ? (const void*)k_transport_batch<R, 2, true> : (const void*)k_transport_batch<R, 2, false>;
-  else if (deal)
+    return range ? (const void*)k_transport_batch<R, 2, true> : (const void*)k_transport_batch<R, 2, false>;
+  else if (range)
     return wide ? (const void*)k_transport_batch<R, 2, true> : (const void*)k_transport_batch<R, 3, true>;
   else
     return wide ? (const void*)k_transport_batch<R, 2, false> : (const void*)k_transport_batch<R, 3, false>;
@@ -304,7 +319,7 @@ struct BatchConfig {
 // list and header (uploaded by every call from pinned staging), per-problem completion times,
 // and the warp stacks.
 struct BatchPlan {
-  int dev = 0, n = 0, block = 0, wide = 0, fp64 = 0, deal = 0, grid = 0;
+  int dev = 0, n = 0, block = 0, wide = 0, fp64 = 0, range = 0, grid = 0;
   size_t slot_bytes = 0, smem = 0;
   uint64_t stack_cap = 0;
   DevBuf d_items, d_head, d_tdone, d_stacks;
@@ -339,8 +354,8 @@ constexpr size_t kMaxPlans = 4;
 constexpr uint64_t kDefaultStack = 2048;
 
 template <typename R>
-cudaError_t batch_occupancy(int block, size_t smem, bool wide, bool deal, int* per_sm) {
-  const void* f = batch_fn<R>(wide, deal);
+cudaError_t batch_occupancy(int block, size_t smem, bool wide, bool range, int* per_sm) {
+  const void* f = batch_fn<R>(wide, range);
   // opt in for the exact size: the default limit (48 KB less the kernel's static shared memory)
   // can be exceeded by a dynamic size just under 48 KB
   {
@@ -358,12 +373,16 @@ int capture(BatchPlan* pl) {
   unsigned long long* tdone = (unsigned long long*)pl->d_tdone.ptr;
   uint4* stacks = (uint4*)pl->d_stacks.ptr;
   int slot = (int)pl->slot_bytes;
-  const void* f = pl->fp64 ? batch_fn<double>(pl->wide, pl->deal) : batch_fn<float>(pl->wide, pl->deal);
+  const void* f = pl->fp64 ? batch_fn<double>(pl->wide, pl->range) : batch_fn<float>(pl->wide, pl->range);
   void* args[] = {&bh, &items, &tdone, &stacks, &slot};
   CK(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
   k_batch_clear<<<dim3((unsigned)pl->n, 16), 256, 0, pl->cap_stream>>>(bh, items, tdone);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaLaunchKernel(f, pl->grid, pl->block, args, pl->smem, pl->cap_stream);
+  if (e == cudaSuccess && pl->range) {
+    k_batch_reconstruct_multi<<<dim3((unsigned)pl->n, 4), 256, 0, pl->cap_stream>>>(bh, items);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) {
     k_batch_stats_multi<<<dim3((unsigned)pl->n, 8), 256, 0, pl->cap_stream>>>(bh, items);
     e = cudaGetLastError();
@@ -383,11 +402,11 @@ int capture(BatchPlan* pl) {
 
 // The plan of a launch shape, created (and its graph captured) on first use.  Caller holds
 // g_batch_mu.
-int get_plan(int dev, int n, const BatchConfig& c, int fp64, int deal, size_t slot, uint64_t stack_cap,
+int get_plan(int dev, int n, const BatchConfig& c, int fp64, int range, size_t slot, uint64_t stack_cap,
              BatchPlan** out) {
   for (auto& pl : g_plans)
     if (pl->dev == dev && pl->n == n && pl->block == c.block && pl->wide == c.wide && pl->fp64 == fp64 &&
-        pl->deal == deal && pl->slot_bytes == slot && pl->stack_cap == stack_cap) {
+        pl->range == range && pl->slot_bytes == slot && pl->stack_cap == stack_cap) {
       pl->last_use = ++g_plan_clock;
       *out = pl.get();
       return MC_OK;
@@ -407,14 +426,14 @@ int get_plan(int dev, int n, const BatchConfig& c, int fp64, int deal, size_t sl
   pl->block = c.block;
   pl->wide = c.wide;
   pl->fp64 = fp64;
-  pl->deal = deal;
+  pl->range = range;
   pl->slot_bytes = slot;
   pl->stack_cap = stack_cap;
   const size_t wb = fp64 ? batch_warp_bytes<double>(slot) : batch_warp_bytes<float>(slot);
   pl->smem = (size_t)(c.block / 32) * wb;
   int per_sm = 0;
-  CK(fp64 ? batch_occupancy<double>(c.block, pl->smem, c.wide, deal, &per_sm)
-          : batch_occupancy<float>(c.block, pl->smem, c.wide, deal, &per_sm));
+  CK(fp64 ? batch_occupancy<double>(c.block, pl->smem, c.wide, range, &per_sm)
+          : batch_occupancy<float>(c.block, pl->smem, c.wide, range, &per_sm));
   if (per_sm < 1)
     return fail(MC_ERR_INVALID, "batched kernel does not fit on an SM (block %d, %zu B shared memory)", c.block,
                 pl->smem);
@@ -505,16 +524,16 @@ int mc_run_batch(mc_problem* const* ps, int n, const uint64_t* n_hist, uint64_t 
       return fail(MC_ERR_INVALID, "a problem appears twice in the batch");
   }
   size_t slot = 0;
-  int deal = 0;  // some problem has a tally whose time pieces are dealt out over the warp
+  int range = 0;  // some problem has a tally scored by the range walk
   for (int i = 0; i < n; ++i) {
     mc_problem* p = ps[i];
-    deal = deal || p->deal;
     if (!p) return fail(MC_ERR_INVALID, "problem %d is NULL", i);
+    range = range || p->range;
     if (p->dev != dev) return fail(MC_ERR_STATE, "problem %d was created on device %d, current is %d", i, p->dev, dev);
     if (n_hist[i] < (uint64_t)nb) return fail(MC_ERR_INVALID, "problem %d: need at least n_batches histories", i);
     if (n_hist[i] >= (1ull << 32)) return fail(MC_ERR_INVALID, "problem %d: history indices must stay below 2^32", i);
     if (o.ww_enable && !p->ww_set) return fail(MC_ERR_STATE, "problem %d: weight windows enabled but no table set", i);
-    if ((double)nb * (double)p->total_bins >= 4294967296.0)
+    if ((double)nb * (double)p->row >= 4294967296.0)
       return fail(MC_ERR_INVALID, "problem %d: tally bins x batches must stay below 2^32", i);
     slot = std::max(slot, p->blob[fp64].size());
   }
@@ -534,7 +553,7 @@ int mc_run_batch(mc_problem* const* ps, int n, const uint64_t* n_hist, uint64_t 
   for (int i = 0; i < n; ++i) {
     mc_problem* p = ps[i];
     const uint64_t bins = (uint64_t)p->total_bins;
-    rc = p->d_tally.ensure((size_t)nb * bins * 8, dev);
+    rc = p->d_tally.ensure((size_t)nb * p->row * 8, dev);
     if (rc == MC_OK) rc = p->d_stats.ensure((size_t)3 * bins * 8, dev);
     if (rc != MC_OK) return rc;
   }
@@ -551,7 +570,7 @@ int mc_run_batch(mc_problem* const* ps, int n, const uint64_t* n_hist, uint64_t 
 
   std::lock_guard<std::mutex> lk(g_batch_mu);
   BatchPlan* pl = nullptr;
-  rc = get_plan(dev, n, c, fp64, deal, slot, stack_cap, &pl);
+  rc = get_plan(dev, n, c, fp64, range, slot, stack_cap, &pl);
   if (rc != MC_OK) return rc;
   CK(cudaEventSynchronize(pl->uploaded));  // the staging buffers are free again
   uint64_t units = 0;
@@ -563,6 +582,8 @@ int mc_run_batch(mc_problem* const* ps, int n, const uint64_t* n_hist, uint64_t 
     it.P.history_mode = 1;
     it.stats = ps[i]->d_stats.ptr;
     it.bins = (uint64_t)ps[i]->total_bins;
+    it.blob64 = (const char*)ps[i]->d_blob[1].ptr;
+    it.range_rows = ps[i]->range_rows;
     it.unit_first = units;
     it.n_units = (n_hist[i] + (uint64_t)c.unit - 1) / (uint64_t)c.unit;
     it.caller_index = i;

@@ -607,22 +607,6 @@ __device__ __forceinline__ void stage_flush(const RunParams& P, const Stage& S, 
   __syncwarp();
 }
 
-// Track-length estimator over the segment of length l from the particle's position: score
-// w * piece length into every (mesh cell, time bin) the segment passes through.  Crossing
-// distances are measured from the segment start, so rounding does not accumulate along the walk.
-//
-// The walk runs in warp-uniform rounds.  Normally every round each walking lane emits one piece:
-// the part of its segment up to the next crossing of a mesh plane or time edge.  A tally whose
-// time axis is much finer than its spatial mesh (TallyDesc::deal; then flights cross many more
-// time edges than planes, and the lane with the most crossings sets the number of rounds) instead
-// takes one mesh cell per lane per round: the lane's sub-segment
-// [s, e) in that cell spans time bins it, it+1, ..., whose edges inside it, at distances
-// D_k = (t_k - t0) v, are found by binary search; the pieces of all lanes are then dealt out over
-// the warp (prefix sum of the counts; piece q goes to lane q mod 32, which finds its owner by a
-// 5-step shuffle search and fetches the owner's sub-segment by shuffles), so a lane whose flight
-// crosses many time bins does not keep the other 31 waiting.  Pieces go to the warp's staging
-// buffer, which is flushed with converged lanes whenever it could overflow and at the end.
-// Called by all 32 lanes; `active` lanes have a segment.
 // Score bits of a piece in the modes that need FP64 arithmetic (FP64 tallies, or fixed point
 // with FP64 tracking).  Not inlined, so that the FP32 fixed-point path carries no FP64 pipe work
 // (this GPU runs FP64 at 1/64 of the FP32 rate).
@@ -631,14 +615,32 @@ static __device__ __noinline__ unsigned long long score_bits_fp64(const RunParam
   return (unsigned long long)__double2ll_rn(w * len * P.fixed_scale);
 }
 
-// DEAL = false compiles only the one-piece-per-round walk (for runs whose tallies have a single
-// time bin), which keeps the kernel's register footprint down.
-template <typename R, bool DEAL>
+// Track-length estimator over the segment of length l from the particle's position: score
+// w * piece length into every (mesh cell, time bin) the segment passes through.  Crossing
+// distances are measured from the segment start, so rounding does not accumulate along the walk.
+// The walk runs in warp-uniform rounds; pieces go to the warp's staging buffer, which is flushed
+// with converged lanes whenever it could overflow and at the end.  Called by all 32 lanes;
+// `active` lanes have a segment.
+//
+// Plain walk: every round each walking lane emits one piece, the part of its segment up to the
+// next crossing of a mesh plane or time edge.
+//
+// Range walk (TallyDesc::range, a time axis much finer than the spatial mesh, so that a flight
+// crosses many more time edges than planes): every round each lane takes one mesh cell.  Its
+// sub-segment [s, e) there spans time bins first..last, found by binary search over the edge
+// distances D_k = (t_k - t0) v.  A bin strictly inside that span is crossed in full, and the
+// track length of a full bin k is the constant v (t_{k+1} - t_k): the lane scores the two end bins
+// as pieces and the run of full bins first+1 .. last-1 as two difference marks, +w at first+1 and
+// -w at last, in the tally's difference slots.  A reconstruction pass after the run turns the
+// running sum of the marks into w v (t_{k+1} - t_k) per bin.  A lane thus makes at most four
+// updates per cell, however many time bins its flight crosses.
+//
+// RANGE = false compiles only the plain walk, which keeps the kernel's register footprint down.
+template <typename R, bool RANGE>
 __device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Part<R>& p, R l,
                                    uint64_t batch_base, bool active, const Stage& S, unsigned& pieces) {
   constexpr unsigned kAll = 0xFFFFFFFFu;
   const unsigned lt = lanemask_lt();
-  const int lane = threadIdx.x & 31;
   const int g = (int)pk_g(p.pk);
   const R v = active ? T.v[g] : R(1);
   const char* base = reinterpret_cast<const char*>(T.h);
@@ -647,13 +649,8 @@ __device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Pa
   const float wscale = sizeof(R) == 4 ? weight_to_float(w) * P.fixed_scale_f : 0.0f;
   const bool fp32_fixed = sizeof(R) == 4 && !P.tally_fp64;
   unsigned n_st = 0;
-  // stages one piece per lane (those with emit), flushing when the buffer could overflow
-  auto stage = [&](bool emit, uint32_t slot, R len, double pw, float pws) {
-    unsigned long long val = 0;
-    if (emit) {
-      if (fp32_fixed) val = (unsigned long long)float_to_fixed(pws * (float)len);
-      else val = score_bits_fp64(P, pw, (double)len);
-    }
+  // stages one value per lane (those with emit), flushing when the buffer could overflow
+  auto stage_bits = [&](bool emit, uint32_t slot, unsigned long long val) {
     const unsigned m = __ballot_sync(kAll, emit);
     if (emit) {
       const unsigned i = n_st + __popc(m & lt);
@@ -667,6 +664,16 @@ __device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Pa
       n_st = 0;
     }
   };
+  // the score of a piece of length len (or, with len = +-1, a difference mark of +-w)
+  auto score_val = [&](bool emit, R len) -> unsigned long long {
+    if (!emit) return 0ull;
+    if (fp32_fixed) {
+      const long long q = float_to_fixed(wscale * fabsf((float)len));
+      return (unsigned long long)(len < R(0) ? -q : q);
+    }
+    return score_bits_fp64(P, w, (double)len);
+  };
+  auto stage = [&](bool emit, uint32_t slot, R len) { stage_bits(emit, slot, score_val(emit, len)); };
   for (int ti = 0; ti < T.h->n_tally; ++ti) {
     const TallyDesc& D = T.h->tally[ti];
     const R* e[3] = {reinterpret_cast<const R*>(base + D.o_ex), reinterpret_cast<const R*>(base + D.o_ey),
@@ -715,7 +722,7 @@ __device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Pa
             live = dj < l;
           }
         }
-        stage(emit, slot, R(1), w, wscale);
+        stage(emit, slot, R(1));
       }
       continue;
     }
@@ -750,7 +757,7 @@ __device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Pa
     }
     const uint32_t gbase = (uint32_t)(batch_base + (uint64_t)D.bin_offset + (uint64_t)g * nt);
     const int gstride = T.G * nt;
-    if (!DEAL || !D.deal) {
+    if (!RANGE || !D.range) {
       while (__any_sync(kAll, live)) {
         bool emit = false;
         uint32_t slot = 0;
@@ -782,17 +789,21 @@ __device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Pa
             s = nxt;
           }
         }
-        stage(emit, slot, len, w, wscale);
+        stage(emit, slot, len);
       }
       continue;
     }
+    // difference slots of this (group, cell): nt + 1 marks per (cell, group) after the batch row's
+    // bins; mark k belongs to bin k
+    const uint32_t dbase = (uint32_t)(batch_base + (uint64_t)T.h->total_bins + (uint64_t)D.diff_offset +
+                                      (uint64_t)g * (nt + 1));
+    const int dstride = T.G * (nt + 1);
     while (__any_sync(kAll, live)) {
-      // this lane's sub-segment [s, e) in mesh cell idx, and the last time edge klt before e:
+      // this lane's sub-segment [s, end) in mesh cell idx, and the last time edge klt before end:
       // it spans time bins max(it, 0) .. min(klt, nt - 1)
       R end = s;
-      int klt = it;
-      unsigned cnt = 0;
-      uint32_t cbase = 0;
+      int klt = it, first = 0, last = -1;
+      uint32_t cell = 0;
       if (live) {
         end = fmin(fmin(fmin(sn[0], sn[1]), sn[2]), l);
         if (stn < end) {
@@ -804,50 +815,31 @@ __device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Pa
           }
           klt = lo;
         }
-        const int first = it > 0 ? it : 0, last = klt < nt - 1 ? klt : nt - 1;
-        if (end > s && last >= first && idx[0] >= 0 && idx[0] < n[0] && idx[1] >= 0 && idx[1] < n[1] &&
-            idx[2] >= 0 && idx[2] < n[2]) {
-          cnt = (unsigned)(last - first + 1);
-          cbase = gbase + (uint32_t)(((idx[2] * n[1] + idx[1]) * n[0] + idx[0]) * gstride);
+        if (end > s && idx[0] >= 0 && idx[0] < n[0] && idx[1] >= 0 && idx[1] < n[1] && idx[2] >= 0 &&
+            idx[2] < n[2]) {
+          first = it > 0 ? it : 0;
+          last = klt < nt - 1 ? klt : nt - 1;
+          cell = (uint32_t)((idx[2] * n[1] + idx[1]) * n[0] + idx[0]);
         }
       }
-      if (__all_sync(kAll, cnt <= 1u)) {
-        const int bin = it > 0 ? it : 0;
-        const R lo = bin == it ? s : (et[bin] - t0) * v;
-        const R hi = bin < klt ? (et[bin + 1] - t0) * v : end;
-        stage(cnt == 1u && hi > lo, cbase + (uint32_t)bin, hi - lo, w, wscale);
-      } else {
-        unsigned incl = cnt;  // inclusive prefix sum of the counts over the warp
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const unsigned o = __shfl_up_sync(kAll, incl, d);
-          if (lane >= d) incl += o;
-        }
-        const unsigned total = __shfl_sync(kAll, incl, 31);
-        for (unsigned q0 = 0; q0 < total; q0 += 32) {
-          const unsigned q = q0 + (unsigned)lane;
-          int o = 0;  // owner: the first lane whose inclusive count exceeds q
-#pragma unroll
-          for (int b = 16; b >= 1; b >>= 1) {
-            const unsigned pv = __shfl_sync(kAll, incl, o + b - 1);
-            if (pv <= q) o += b;
-          }
-          o = o < 31 ? o : 31;
-          const unsigned on = __shfl_sync(kAll, cnt, o), oincl = __shfl_sync(kAll, incl, o);
-          const int oit = __shfl_sync(kAll, it, o), oklt = __shfl_sync(kAll, klt, o);
-          const R os = __shfl_sync(kAll, s, o), oe = __shfl_sync(kAll, end, o);
-          const R ot0 = __shfl_sync(kAll, t0, o), ov = __shfl_sync(kAll, v, o);
-          const uint32_t ocb = __shfl_sync(kAll, cbase, o);
-          double ow = 0.0;
-          float ows = 0.0f;
-          if (fp32_fixed) ows = __shfl_sync(kAll, wscale, o);
-          else ow = __shfl_sync(kAll, w, o);
-          const int bin = (oit > 0 ? oit : 0) + (int)(q - (oincl - on));
-          const bool mine = q < total;
-          const int eb = mine ? bin : 0;  // an in-range edge index for lanes without a piece
-          const R lo = eb == oit ? os : (et[eb] - ot0) * ov;
-          const R hi = eb < oklt ? (et[eb + 1] - ot0) * ov : oe;
-          stage(mine && hi > lo, ocb + (uint32_t)bin, hi - lo, ow, ows);
+      const bool any = last >= first;
+      // piece in bin `first`: from s (or its lower edge) to its upper edge (or end)
+      {
+        const R lo = first == it ? s : (et[first] - t0) * v;
+        const R hi = first < klt ? (et[first + 1] - t0) * v : end;
+        stage(any && hi > lo, gbase + cell * (uint32_t)gstride + (uint32_t)first, hi - lo);
+      }
+      if (__any_sync(kAll, last > first)) {
+        const bool two = last > first;
+        // piece in bin `last`, from its lower edge to end (or its upper edge, past the time mesh)
+        const R lo = (et[last] - t0) * v;
+        const R hi = last < klt ? (et[last + 1] - t0) * v : end;
+        stage(two && hi > lo, gbase + cell * (uint32_t)gstride + (uint32_t)last, hi - lo);
+        if (__any_sync(kAll, last > first + 1)) {
+          const bool full = last > first + 1;
+          const uint32_t db = dbase + cell * (uint32_t)dstride;
+          stage(full, db + (uint32_t)(first + 1), R(1));
+          stage(full, db + (uint32_t)last, R(-1));
         }
       }
       // advance along the walk (lane-local)

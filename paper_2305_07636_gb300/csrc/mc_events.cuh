@@ -419,10 +419,10 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 // Handles the pending event of a particle loaded from the bank; on survival it is ready to fly.
 template <typename R>
 __device__ __forceinline__ bool handle_pending(const RunParams& P, const Tab<R>& T, Part<R>& p, uint4* const* Bout,
-                                               unsigned long long* bcount, BlockCounters* bc, uint64_t bins,
+                                               unsigned long long* bcount, BlockCounters* bc, uint64_t row,
                                                uint64_t stripe_off) {
   const uint32_t pend = pk_pend(p.pk);
-  const uint64_t bbase = stripe_off + (uint64_t)(p.elem >> 16) * bins;
+  const uint64_t bbase = stripe_off + (uint64_t)(p.elem >> 16) * row;
   const bool alive = pend == PEND_COLL ? do_collision(P, T, p, Bout, bcount, bc)
                                        : do_surface(P, T, p, Bout, bcount, bc, bbase);
   if (alive) {
@@ -437,14 +437,14 @@ __device__ __forceinline__ bool handle_pending(const RunParams& P, const Tab<R>&
 // integer sum over batches of the batch totals T_b and the exact 128-bit sum of T_b^2 (integer
 // pipes only; the floating-point arithmetic happens once per bin at readback).  FP64: the sum of
 // T_b and of the batch means and their squares (inv_nbar = batches / histories).
-__device__ __forceinline__ void stats_bin_fixed(const long long* tally, uint64_t bins, int nb, int stripes, uint64_t b,
+__device__ __forceinline__ void stats_bin_fixed(const long long* tally, uint64_t row, int nb, int stripes, uint64_t b,
                                                 long long& sum, unsigned long long& sq_lo, unsigned long long& sq_hi) {
-  const uint64_t stride = (uint64_t)nb * bins;
+  const uint64_t stride = (uint64_t)nb * row;
   long long s = 0;
   unsigned long long lo = 0, hi = 0;
   for (int j = 0; j < nb; ++j) {
     long long x = 0;
-    for (int c = 0; c < stripes; ++c) x += __ldcs(tally + c * stride + (uint64_t)j * bins + b);
+    for (int c = 0; c < stripes; ++c) x += __ldcs(tally + c * stride + (uint64_t)j * row + b);
     s += x;
     const unsigned long long ux = (unsigned long long)(x < 0 ? -x : x);
     const unsigned long long plo = ux * ux, phi = __umul64hi(ux, ux);
@@ -457,13 +457,13 @@ __device__ __forceinline__ void stats_bin_fixed(const long long* tally, uint64_t
   sq_hi = hi;
 }
 
-__device__ __forceinline__ void stats_bin_fp64(const double* tally, uint64_t bins, int nb, int stripes,
+__device__ __forceinline__ void stats_bin_fp64(const double* tally, uint64_t row, int nb, int stripes,
                                                double inv_nbar, uint64_t b, double& tot, double& s1, double& s2) {
-  const uint64_t stride = (uint64_t)nb * bins;
+  const uint64_t stride = (uint64_t)nb * row;
   double t = 0.0, a = 0.0, q = 0.0;
   for (int j = 0; j < nb; ++j) {
     double x = 0.0;
-    for (int c = 0; c < stripes; ++c) x += __ldcs(tally + c * stride + (uint64_t)j * bins + b);
+    for (int c = 0; c < stripes; ++c) x += __ldcs(tally + c * stride + (uint64_t)j * row + b);
     t += x;
     const double m = x * inv_nbar;
     a += m;
@@ -472,6 +472,72 @@ __device__ __forceinline__ void stats_bin_fp64(const double* tally, uint64_t bin
   tot = t;
   s1 = a;
   s2 = q;
+}
+
+// Range-walk reconstruction of (batch j, range row r): a range row is one (tally, mesh cell, group)
+// of a tally scored by the range walk.  Its nt + 1 difference slots hold, summed over the stripes,
+// +w where a run of fully crossed time bins starts and -w one past where it ends; the running sum
+// over k is the weight of the flights that crossed bin k in full, each with the track length
+// v_g (t_{k+1} - t_k).  The warp scans the slots 32 at a time (shuffle scan with a carry) and adds
+// sum x length to bin k of stripe 0 (fixed point: rounded to the tally's scale; the sum is an exact
+// integer, so the result does not depend on the order of the atomics).  Only bins 1 .. nt - 2 can
+// be crossed in full, so a bin of infinite width never takes part.
+__device__ inline void reconstruct_warp(void* tally, const char* blob64, uint64_t row, int nb, int stripes, int fp64,
+                                        int j, uint64_t r) {
+  const TableHeader* H = reinterpret_cast<const TableHeader*>(blob64);
+  const int lane = threadIdx.x & 31;
+  int t = 0;
+  for (; t < H->n_tally; ++t) {
+    const TallyDesc& D = H->tally[t];
+    if (!D.range) continue;
+    const uint64_t rows_t = (uint64_t)D.nx * D.ny * D.nz * H->G;
+    if (r < rows_t) break;
+    r -= rows_t;
+  }
+  if (t >= H->n_tally) return;
+  const TallyDesc& D = H->tally[t];
+  const int nt = D.nt;
+  const int g = (int)(r % (uint64_t)H->G);
+  const double v = reinterpret_cast<const double*>(blob64 + H->o_v)[g];
+  const double* et = reinterpret_cast<const double*>(blob64 + D.o_et);
+  const uint64_t stride = (uint64_t)nb * row;
+  const uint64_t dslot = (uint64_t)j * row + (uint64_t)H->total_bins + (uint64_t)D.diff_offset + r * (uint64_t)(nt + 1);
+  const uint64_t bslot = (uint64_t)j * row + (uint64_t)D.bin_offset + r * (uint64_t)nt;
+  if (fp64) {
+    double* T = reinterpret_cast<double*>(tally);
+    double carry = 0.0;
+    for (int k0 = 0; k0 < nt; k0 += 32) {
+      const int k = k0 + lane;
+      double d = 0.0;
+      if (k < nt)
+        for (int c = 0; c < stripes; ++c) d += __ldcg(T + c * stride + dslot + k);
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double u = __shfl_up_sync(0xFFFFFFFFu, d, o);
+        if (lane >= o) d += u;
+      }
+      const double run = carry + d;
+      carry += __shfl_sync(0xFFFFFFFFu, d, 31);
+      if (k >= 1 && k <= nt - 2 && run != 0.0) T[bslot + k] += run * (v * (et[k + 1] - et[k]));
+    }
+  } else {
+    long long* T = reinterpret_cast<long long*>(tally);
+    long long carry = 0;
+    for (int k0 = 0; k0 < nt; k0 += 32) {
+      const int k = k0 + lane;
+      long long d = 0;
+      if (k < nt)
+        for (int c = 0; c < stripes; ++c) d += __ldcg(T + c * stride + dslot + k);
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long u = __shfl_up_sync(0xFFFFFFFFu, d, o);
+        if (lane >= o) d += u;
+      }
+      const long long run = carry + d;
+      carry += __shfl_sync(0xFFFFFFFFu, d, 31);
+      if (k >= 1 && k <= nt - 2 && run != 0) T[bslot + k] += __double2ll_rn((double)run * (v * (et[k + 1] - et[k])));
+    }
+  }
 }
 
 constexpr unsigned kWarpQ = 64;  // per-warp flight queue slots

@@ -75,7 +75,9 @@ struct mc_problem {
   int dev = 0;
   int G = 0, M = 0, n_surf = 0, n_cell = 0, n_tally = 0;
   int total_bins = 0, leak_offset = 0;
-  bool deal = false;  // some mesh tally deals its time pieces out over the warp (kernel build)
+  bool range = false;  // some mesh tally is scored by the range walk (kernel build)
+  uint64_t row = 0;    // elements of one batch row of the tallies: bins, then difference slots
+  uint64_t range_rows = 0;  // (tally, cell, group) rows scored by the range walk
   int tuned_block = 0, tuned_bps = 0;  // mc_run_tune's choice (block_size, blocks_per_sm), 0 = none
   std::vector<mcgb::HostTally> tallies;
   std::vector<uint8_t> blob[2];  // [0] FP32 tables, [1] FP64 tables

@@ -52,21 +52,22 @@ struct TallyDesc {
   int bin_offset;              // first bin of this tally in the concatenated bin space
   int n_bins;
   int o_etf;                   // time edges rounded to float (FP32 tracking)
-  int deal;                    // 1: the scoring walk deals this tally's time pieces out over the warp
+  int range;                   // 1: scored by the range walk (full time bins as difference marks)
   int est;                     // MC_EST_TRACK_LENGTH or MC_EST_TIME_CROSSING
   int nval;                    // values per (cell, group) along time: nt bins or nt + 1 points
-  int pad0, pad1;
+  int diff_offset;             // range walk: first difference slot after the batch row's bins
+  int pad0;
 };
 
-// A tally's time pieces are dealt out over the warp when its time axis is much finer than its
+// A track-length tally is scored by the range walk when its time axis is much finer than its
 // spatial mesh (flights then cross many more time edges than mesh planes).
-inline bool deals_time_pieces(int nx, int ny, int nz, int nt) { return nt >= 4 * (nx + ny + nz); }
+inline bool ranges_time_bins(int nx, int ny, int nz, int nt) { return nt >= 3 && nt >= 4 * (nx + ny + nz); }
 
 struct TableHeader {
   int G, M, n_surf, n_cell;
   int has_lat, lat_nx, lat_ny, lat_matrix;
   int n_tally, total_bins, leak_offset, real_bytes;
-  int src_pos, src_dir, pad0, pad1;
+  int src_pos, src_dir, total_diff, pad1;  // total_diff: difference slots after the bins of a row
   double t_census;
   double src_lo[3], src_hi[3], src_t0, src_t1;
   double lat_x0, lat_y0, lat_pitch, lat_r;
@@ -119,8 +120,9 @@ struct RunParams {
   int* sticky;             // first error of any run since the host last read it
   uint32_t tally_stripes;  // copies of the batch tallies; CTA b scores into copy b % stripes
   uint32_t pad_ts;
-  uint64_t stripe_stride;  // elements per copy (n_batches * total_bins)
-  void* tally;             // [n_batches][total_bins] int64 (fixed point) or double
+  uint64_t stripe_stride;  // elements per copy (n_batches * row)
+  uint64_t row;            // elements per batch row: total_bins, then total_diff difference slots
+  void* tally;             // [stripes][n_batches][row] int64 (fixed point) or double
   int tally_fp64, aggregate;
   double fixed_scale;      // 2^fixed_bits
   float fixed_scale_f;

@@ -26,7 +26,7 @@ namespace mcgb {
 constexpr unsigned kClaim = 128;
 
 // dynamic shared memory: [table blob][per-warp flight queues: warps x Lanes<R>::N x kWarpQ]
-template <typename R, int MINB, bool DEAL>
+template <typename R, int MINB, bool RANGE>
 __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
   extern __shared__ __align__(16) char smem[];
   __shared__ BlockCounters bc;
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
   Ctl* ctl = P.ctl;
   const unsigned lt = lanemask_lt();
   unsigned scored = 0;  // tally updates issued by this warp
-  const uint64_t bins = (uint64_t)T.h->total_bins;
+  const uint64_t row = P.row;  // tally elements per batch: bins, then difference slots
   // small tallies are striped over several copies so that hot bins are not one L2 address
   const uint64_t stripe_off = (uint64_t)(blockIdx.x % P.tally_stripes) * P.stripe_stride;
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t_start = globaltimer();
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
         if (item < rend) {
           if (item < nF + nS) {
             bank_load(p, Sin, item < nF ? item : P.cap_s - 1 - (item - nF));
-            ready = handle_pending(P, T, p, Bout, bcount, &bc, bins, stripe_off);
+            ready = handle_pending(P, T, p, Bout, bcount, &bc, row, stripe_off);
           } else if (item < nF + nS + nB) {
             const uint64_t j = item - nF - nS;
             bank_load(p, Bin, j);
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
       uint32_t pend = PEND_NONE;
       Hit hit;
       const bool flies = have && flight_plan(P, T, p, &bc, l, pend, hit);
-      score_segment_warp<R, DEAL>(T, P, p, l, stripe_off + (uint64_t)(p.elem >> 16) * bins, flies, stage, scored);
+      score_segment_warp<R, RANGE>(T, P, p, l, stripe_off + (uint64_t)(p.elem >> 16) * row, flies, stage, scored);
       if (flies) {
         bool alive = flight_finish(P, T, p, &bc, l, pend, hit);
         if (alive && p.k + 1 >= P.max_iter) {
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
           alive = false;
         }
         if (alive) {
-          if (drain) again = handle_pending(P, T, p, Bout, bcount, &bc, bins, stripe_off);
+          if (drain) again = handle_pending(P, T, p, Bout, bcount, &bc, row, stripe_off);
           else out = true;
         }
       }
@@ -220,19 +220,29 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
 }
 
 // ------------------------------------------------------------------------------------------ stats
-// Batch statistics of every bin of one problem (stats_bin_fixed / stats_bin_fp64 per bin).
-__global__ void k_batch_stats_fixed(const long long* tally, uint64_t bins, int nb, int stripes, long long* sum,
-                                    unsigned long long* sq_lo, unsigned long long* sq_hi) {
+// Batch statistics of every bin of one problem (stats_bin_fixed / stats_bin_fp64 per bin); batch
+// rows are `row` elements apart.
+__global__ void k_batch_stats_fixed(const long long* tally, uint64_t bins, uint64_t row, int nb, int stripes,
+                                    long long* sum, unsigned long long* sq_lo, unsigned long long* sq_hi) {
   for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < bins;
        b += (uint64_t)gridDim.x * blockDim.x)
-    stats_bin_fixed(tally, bins, nb, stripes, b, sum[b], sq_lo[b], sq_hi[b]);
+    stats_bin_fixed(tally, row, nb, stripes, b, sum[b], sq_lo[b], sq_hi[b]);
 }
 
-__global__ void k_batch_stats_fp64(const double* tally, uint64_t bins, int nb, int stripes, double inv_nbar,
-                                   double* tot, double* s1, double* s2) {
+__global__ void k_batch_stats_fp64(const double* tally, uint64_t bins, uint64_t row, int nb, int stripes,
+                                   double inv_nbar, double* tot, double* s1, double* s2) {
   for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < bins;
        b += (uint64_t)gridDim.x * blockDim.x)
-    stats_bin_fp64(tally, bins, nb, stripes, inv_nbar, b, tot[b], s1[b], s2[b]);
+    stats_bin_fp64(tally, row, nb, stripes, inv_nbar, b, tot[b], s1[b], s2[b]);
+}
+
+// Range-walk reconstruction of every batch of one problem (reconstruct_warp per (batch, row)).
+__global__ void k_reconstruct(void* tally, const char* blob64, uint64_t rows, uint64_t row, int nb, int stripes,
+                              int fp64) {
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t wi = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wi < (uint64_t)nb * rows;
+       wi += warps)
+    reconstruct_warp(tally, blob64, row, nb, stripes, fp64, (int)(wi / rows), wi % rows);
 }
 
 // L2 atomic throughput probe: 64-bit adds to pseudo-random slots of an array of `span` elements
@@ -259,25 +269,25 @@ __global__ void k_philox(uint64_t seed, const uint4* ctr, uint4* out, uint64_t n
 
 // ------------------------------------------------------------------------------------------ launchers
 // Two register budgets of the same kernel: 3 CTAs of 256 threads per SM (80 registers) or 2 CTAs
-// (128 registers, no spills); `wide` selects the second.  `deal` selects the build whose scoring
-// can deal time-bin pieces out over the warp (tallies with more than one time bin).
+// (128 registers, no spills); `wide` selects the second.  `range` selects the build with the range
+// walk of the scoring (tallies whose time axis is much finer than their mesh).
 template <typename R>
-static const void* transport_fn(bool wide, bool deal) {
-  if constexpr (sizeof(R) == 8) return deal ? (const void*)k_transport<R, 2, true> : (const void*)k_transport<R, 2, false>;
-  else if (deal) return wide ? (const void*)k_transport<R, 2, true> : (const void*)k_transport<R, 3, true>;
+static const void* transport_fn(bool wide, bool range) {
+  if constexpr (sizeof(R) == 8) return range ? (const void*)k_transport<R, 2, true> : (const void*)k_transport<R, 2, false>;
+  else if (range) return wide ? (const void*)k_transport<R, 2, true> : (const void*)k_transport<R, 3, true>;
   else return wide ? (const void*)k_transport<R, 2, false> : (const void*)k_transport<R, 3, false>;
 }
 
 template <typename R>
 cudaError_t launch_transport(const RunParams& P, int grid, int block, size_t smem, cudaStream_t s, bool wide,
-                             bool deal) {
+                             bool range) {
   void* args[] = {const_cast<RunParams*>(&P)};
-  return cudaLaunchCooperativeKernel(transport_fn<R>(wide, deal), grid, block, args, smem, s);
+  return cudaLaunchCooperativeKernel(transport_fn<R>(wide, range), grid, block, args, smem, s);
 }
 
 template <typename R>
-cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide, bool deal) {
-  const void* f = transport_fn<R>(wide, deal);
+cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide, bool range) {
+  const void* f = transport_fn<R>(wide, range);
   // opt in for the exact size: the default limit (48 KB less the kernel's static shared memory)
   // can be exceeded by a dynamic size just under 48 KB
   {
@@ -292,7 +302,17 @@ template cudaError_t launch_transport<double>(const RunParams&, int, int, size_t
 template cudaError_t transport_occupancy<float>(int, size_t, int*, bool, bool);
 template cudaError_t transport_occupancy<double>(int, size_t, int*, bool, bool);
 
-cudaError_t launch_batch_stats(const void* tally, int fp64, uint64_t bins, int nb, int stripes,
+cudaError_t launch_reconstruct(void* tally, const char* blob64, uint64_t rows, uint64_t row, int nb, int stripes,
+                               int fp64, cudaStream_t s) {
+  const uint64_t warps = (uint64_t)nb * rows;
+  uint64_t g = (warps + 7) / 8;
+  if (g > 152 * 8) g = 152 * 8;
+  if (g < 1) g = 1;
+  k_reconstruct<<<(unsigned)g, 256, 0, s>>>(tally, blob64, rows, row, nb, stripes, fp64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_stats(const void* tally, int fp64, uint64_t bins, uint64_t row, int nb, int stripes,
                                uint64_t n_hist, void* out, cudaStream_t s) {
   const int block = 256;
   uint64_t g = (bins + block - 1) / block;
@@ -300,12 +320,12 @@ cudaError_t launch_batch_stats(const void* tally, int fp64, uint64_t bins, int n
   if (g < 1) g = 1;
   if (fp64) {
     double* o = reinterpret_cast<double*>(out);
-    k_batch_stats_fp64<<<(unsigned)g, block, 0, s>>>(reinterpret_cast<const double*>(tally), bins, nb, stripes,
+    k_batch_stats_fp64<<<(unsigned)g, block, 0, s>>>(reinterpret_cast<const double*>(tally), bins, row, nb, stripes,
                                                      (double)nb / (double)n_hist, o, o + bins, o + 2 * bins);
   } else {
     char* o = reinterpret_cast<char*>(out);
     k_batch_stats_fixed<<<(unsigned)g, block, 0, s>>>(
-        reinterpret_cast<const long long*>(tally), bins, nb, stripes, reinterpret_cast<long long*>(o),
+        reinterpret_cast<const long long*>(tally), bins, row, nb, stripes, reinterpret_cast<long long*>(o),
         reinterpret_cast<unsigned long long*>(o + 8 * bins), reinterpret_cast<unsigned long long*>(o + 16 * bins));
   }
   return cudaGetLastError();
