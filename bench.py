@@ -538,7 +538,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
-    ap.add_argument("--algorithm", default="event", choices=["event", "history"])
+    ap.add_argument("--algorithm", default="auto", choices=["auto", "event", "history"],
+                    help="auto: the autotuner picks event- or history-based (identical results)")
     ap.add_argument("--no-flush", action="store_true", help="skip the L2 flush between steps")
     ap.add_argument("--no-tune", action="store_true", help="skip the kernel autotuner (library defaults)")
     ap.add_argument("--opt", action="append", default=[],
@@ -586,7 +587,9 @@ def main():
         # the kernel configuration for this problem, picked by the library's autotuner (untimed)
         t_opts, tune_ms = mc.run_tune(p.h, n, seed, opts, stream)
         tuned = {"block_size": t_opts.block_size, "blocks_per_sm": t_opts.blocks_per_sm,
-                 "candidate_ms": tune_ms}
+                 "algorithm": ["event", "history"][t_opts.algorithm], "candidate_ms": tune_ms}
+    algorithm = tuned["algorithm"] if tuned and args.algorithm == "auto" else (
+        "event" if args.algorithm == "auto" else args.algorithm)
     for w in range(args.warmup):
         flush.zero_()
         mc.run(p.h, n, seed + w, opts, stream)
@@ -656,7 +659,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "histories_per_step": n, "tracking": "fp32",
-                   "algorithm": args.algorithm, "run_opts": extra, "tuned": tuned,
+                   "algorithm": algorithm, "run_opts": extra, "tuned": tuned,
                    "tally": "int64 fixed point 2^-32", "batches": opts.n_batches,
                    "l2": "flushed (256 MB write) before every timed step"},
         "fom": {"value": fom, "unit": "1/s", "tally": "total flux (all groups and time bins)",
@@ -671,7 +674,7 @@ def main():
                                    "scores_per_flight": c["scores"] / c["flight"],
                                    "peak_kind": "measured live (mc_atomic_peak, random 64-bit adds)"}},
         "counters": {k: c[k] for k in ("flight", "collision", "surface", "census", "iterations")},
-        "algorithm": args.algorithm,
+        "algorithm": algorithm,
         "trace": {"iterations": int(len(tr_t)), "history_style_iterations": int(tr_drain.sum()),
                   "ms_in_history_style_tail": drain_ms},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -152,8 +152,10 @@ typedef enum { MC_TALLY_FIXED64 = 0, MC_TALLY_FP64 = 1 } mc_tally_mode;
 /* Event-based: every iteration advances each live particle by one event and one flight and
  * writes it back to the bank partitioned by its next event (collisions, surfaces).
  * History-based: each thread carries its particle from source to death without write-back.
- * Both draw the same random numbers per particle and give identical fixed-point tallies. */
-typedef enum { MC_ALG_EVENT = 0, MC_ALG_HISTORY = 1 } mc_algorithm;
+ * Both draw the same random numbers per particle and give identical fixed-point tallies.
+ * Auto: the algorithm mc_run_tune found faster for the problem (event-based until it has run;
+ * mc_run_tune called with MC_ALG_AUTO times both). */
+typedef enum { MC_ALG_EVENT = 0, MC_ALG_HISTORY = 1, MC_ALG_AUTO = 2 } mc_algorithm;
 
 typedef struct {
   int precision;          /* mc_precision: arithmetic of positions/directions/distances */
@@ -241,9 +243,11 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
 
 /* Autotuner of mc_run for one problem: runs n_histories with each candidate configuration (256 or
  * 128 threads per CTA; the 80-register build at 3 CTAs of 256 per SM, or the 128-register build at
- * 2), times each run with CUDA events (best of two after a warm-up) and stores the fastest in the
- * problem; later mc_run calls on it whose block_size and blocks_per_sm are both 0 use it.  tuned
- * (nullable) receives a copy of opts with those two fields set, best_ms (nullable) its time.
+ * 2; with opts->algorithm == MC_ALG_AUTO each under both algorithms), times each run with CUDA
+ * events (best of two after a warm-up) and stores the fastest in the problem; later mc_run calls
+ * on it whose block_size and blocks_per_sm are both 0 use it, and those with MC_ALG_AUTO its
+ * algorithm.  tuned (nullable) receives a copy of opts with those fields set, best_ms (nullable)
+ * its time.
  * Synchronises; the tallies left behind are those of the last candidate. */
 int mc_run_tune(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts* opts, void* stream,
                 mc_run_opts* tuned, double* best_ms);

@@ -576,6 +576,7 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
     o.block_size = p->tuned_block;  // the configuration mc_run_tune found for this problem
     o.blocks_per_sm = p->tuned_bps;
   }
+  if (o.algorithm == MC_ALG_AUTO) o.algorithm = p->tuned_alg;  // event-based until tuned
   if (o.precision != MC_FP32 && o.precision != MC_FP64) return fail(MC_ERR_INVALID, "precision");
   if (o.tally_mode != MC_TALLY_FIXED64 && o.tally_mode != MC_TALLY_FP64) return fail(MC_ERR_INVALID, "tally_mode");
   if (o.fixed_bits < 0 || o.fixed_bits > 48) return fail(MC_ERR_INVALID, "fixed_bits outside [0,48]");
@@ -704,15 +705,18 @@ int mc_run_tune(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run
     cudaEventDestroy(e0);
     return cuda_fail(ce, "cudaEventCreate");
   }
-  int best_block = 0, best_bps = 0, rc = MC_OK;
+  int best_block = 0, best_bps = 0, best_alg = MC_ALG_EVENT, rc = MC_OK;
   float best_t = 0.f;
   const int cands[4][2] = {{256, 0}, {256, 2}, {128, 0}, {128, 2}};  // 80- / 128-register builds
   p->tuned_block = 0;
-  for (int c = 0; c < 4 && rc == MC_OK; ++c) {
+  // MC_ALG_AUTO: both algorithms are candidates (their results are identical)
+  const int n_alg = o.algorithm == MC_ALG_AUTO ? 2 : 1;
+  for (int c = 0; c < 4 * n_alg && rc == MC_OK; ++c) {
     mc_run_opts k = o;
-    k.block_size = cands[c][0];
-    k.blocks_per_sm = cands[c][1] ? 2 : 3;  // 128-register build at 2 x 256 threads per SM, else 80 at 3
-    if (o.precision == MC_FP64 && cands[c][1] == 0) continue;  // FP64 tracking has one build
+    k.algorithm = o.algorithm == MC_ALG_AUTO ? (c < 4 ? MC_ALG_EVENT : MC_ALG_HISTORY) : o.algorithm;
+    k.block_size = cands[c % 4][0];
+    k.blocks_per_sm = cands[c % 4][1] ? 2 : 3;  // 128-register build at 2 x 256 threads per SM, else 80 at 3
+    if (o.precision == MC_FP64 && cands[c % 4][1] == 0) continue;  // FP64 tracking has one build
     rc = mc_run(p, n_histories, seed, &k, stream);  // warm-up
     float t = -1.f;
     for (int rep = 0; rep < 2 && rc == MC_OK; ++rep) {
@@ -729,6 +733,7 @@ int mc_run_tune(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run
     if (rc == MC_OK && (best_block == 0 || t < best_t)) {
       best_block = k.block_size;
       best_bps = k.blocks_per_sm;
+      best_alg = k.algorithm;
       best_t = t;
     }
   }
@@ -737,10 +742,12 @@ int mc_run_tune(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run
   if (rc != MC_OK) return rc;
   p->tuned_block = best_block;
   p->tuned_bps = best_bps;
+  p->tuned_alg = best_alg;
   if (tuned) {
     *tuned = o;
     tuned->block_size = best_block;
     tuned->blocks_per_sm = best_bps;
+    tuned->algorithm = best_alg;
   }
   if (best_ms) *best_ms = best_t;
   return MC_OK;
@@ -1094,6 +1101,7 @@ extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t
     return fail(MC_ERR_INVALID, "history indices must stay below 2^32");
   if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 256 || o.block_size % 32))
     return fail(MC_ERR_INVALID, "block_size must be a multiple of 32 in [32,256]");
+  if (o.algorithm == MC_ALG_AUTO) o.algorithm = p->tuned_alg;
   if (o.algorithm != MC_ALG_EVENT && o.algorithm != MC_ALG_HISTORY) return fail(MC_ERR_INVALID, "algorithm");
   if (check_implicit_opts(o) != MC_OK) return MC_ERR_INVALID;
   if (o.log_count > 0) return fail(MC_ERR_INVALID, "mc_run_static keeps no event log");

@@ -428,6 +428,7 @@ struct Hit {
   uint32_t type;
   int dir;
   uint32_t surf;
+  uint32_t chan;  // channel of a collision at the end of the flight (CHAN_*)
 };
 
 template <typename R>

@@ -153,7 +153,21 @@ __device__ bool weight_window(const RunParams& P, const Tab<R>& T, Part<R>& p, u
 }
 
 // ------------------------------------------------------------------------------------------ events
-// Handles the particle's pending collision at the end of flight k (uses the blocks of event k)
+// Channel of a collision of a particle in material m, group g, from u_channel (the second uniform
+// of block 0 of the flight that ends in it).  Analog: drawn over Sigma_t (scatter, production,
+// capture).  Implicit capture: drawn over Sigma_s + Sigma_f only; a collision whose non-capture
+// probability is 0 captures as in the analog walk.
+template <typename R>
+__device__ __forceinline__ uint32_t collision_channel(const RunParams& P, const Tab<R>& T, int m, int g, R St, R u) {
+  const int i = m * T.G + g;
+  const R keep = T.ssf[i];  // Sigma_s + Sigma_f: the part of Sigma_t that is not capture
+  R xi = u * St;
+  if (P.implicit) xi = keep > R(0) ? u * keep : rinf<R>();
+  return xi < T.ss[i] ? CHAN_SCATTER : (xi < keep ? CHAN_PRODUCTION : CHAN_CAPTURE);
+}
+
+// Handles the particle's pending collision at the end of flight k (uses the blocks of event k).
+// Its channel was drawn with the flight (a capture ends the particle there and never comes here).
 template <typename R>
 __device__ bool do_collision(const RunParams& P, const Tab<R>& T, Part<R>& p, uint4* const* Bout,
                              unsigned long long* bcount, BlockCounters* bc) {
@@ -161,23 +175,12 @@ __device__ bool do_collision(const RunParams& P, const Tab<R>& T, Part<R>& p, ui
   const int g = (int)pk_g(p.pk);
   const int m = material_of(T, p.pk, p.elem);
   const R St = T.st[m * G + g];
-  const R keep = T.ssf[m * G + g];  // Sigma_s + Sigma_f: the part of Sigma_t that is not capture
-  const R u0 = draw<R>(P.seed, p.tlo, p.thi, p.k, 0).b;
-  // analog: the channel is drawn over Sigma_t.  Implicit capture: over Sigma_s + Sigma_f, and the
-  // surviving weight takes the non-capture probability (Sigma_s + Sigma_f) / Sigma_t; a collision
-  // whose non-capture probability is 0 captures as in the analog walk
-  R xi = u0 * St;
-  double wkeep = 1.0;
-  if (P.implicit) {
-    if (keep > R(0)) {
-      xi = u0 * keep;
-      wkeep = (double)keep / (double)St;
-    } else {
-      xi = rinf<R>();
-    }
-  }
+  const R keep = T.ssf[m * G + g];
+  const uint32_t chan = pk_chan(p.pk);
+  // implicit capture: the surviving weight takes the non-capture probability (Sigma_s + Sigma_f) / Sigma_t
+  const double wkeep = (P.implicit && keep > R(0)) ? (double)keep / (double)St : 1.0;
   bump(bc, MC_C_COLLISION);
-  if (xi < T.ss[m * G + g]) {
+  if (chan == CHAN_SCATTER) {
     bump(bc, MC_C_SCATTER);
     const Pair2<R> b1 = draw<R>(P.seed, p.tlo, p.thi, p.k, 1);
     const Pair2<R> b2 = draw<R>(P.seed, p.tlo, p.thi, p.k, 2);
@@ -200,7 +203,7 @@ __device__ bool do_collision(const RunParams& P, const Tab<R>& T, Part<R>& p, ui
     }
     return weight_window(P, T, p, Bout, bcount, bc);
   }
-  if (xi < keep) {
+  if (chan == CHAN_PRODUCTION) {
     bump(bc, MC_C_PRODUCTION);
     const R u = draw<R>(P.seed, p.tlo, p.thi, p.k, 3).a;
     const int n = (int)floor(T.nu[m * G + g] + u);
@@ -289,8 +292,8 @@ __device__ bool flight_plan(const RunParams& P, const Tab<R>& T, Part<R>& p, Blo
   const int g = (int)pk_g(p.pk);
   const int m = material_of(T, p.pk, p.elem);
   const R St = T.st[m * G + g];
-  const R u = draw<R>(P.seed, p.tlo, p.thi, p.k, 0).a;
-  const R dc = St > R(0) ? -rlog(u) / St : rinf<R>();
+  const Pair2<R> b0 = draw<R>(P.seed, p.tlo, p.thi, p.k, 0);  // (u_dist, u_channel)
+  const R dc = St > R(0) ? -rlog(b0.a) / St : rinf<R>();
   const R ds = boundary_distance(T, p, hit);
   R dt = rinf<R>();
   if (T.h->has_census) {
@@ -302,6 +305,7 @@ __device__ bool flight_plan(const RunParams& P, const Tab<R>& T, Part<R>& p, Blo
   if (dc < ds && dc < dt) {
     pend = PEND_COLL;
     l = dc;
+    hit.chan = collision_channel(P, T, m, g, St, b0.b);
   } else if (ds <= dt) {
     pend = PEND_SURF;
     l = ds;
@@ -319,7 +323,7 @@ __device__ bool flight_plan(const RunParams& P, const Tab<R>& T, Part<R>& p, Blo
 }
 
 // Flight k, second half (after the segment was scored): move, advance the clock, set the pending
-// event.  Returns false if the particle ends at the census.
+// event.  Returns false if the particle ends at the census or is captured at the flight's end.
 template <typename R>
 __device__ bool flight_finish(const RunParams& P, const Tab<R>& T, Part<R>& p, BlockCounters* bc, R l,
                               uint32_t pend, const Hit& hit) {
@@ -333,7 +337,15 @@ __device__ bool flight_finish(const RunParams& P, const Tab<R>& T, Part<R>& p, B
     log_event(P, T, p, 2, 0, 0);
     return false;
   }
+  if (pend == PEND_COLL && hit.chan == CHAN_CAPTURE) {
+    // a capture ends the particle here: no bank round trip, no second draw of block 0
+    bump(bc, MC_C_COLLISION);
+    bump(bc, MC_C_CAPTURE);
+    log_event(P, T, p, 0, 2, 0);
+    return false;
+  }
   p.pk = pk_set_pending(p.pk, pend, hit.type, hit.dir, hit.surf);
+  if (pend == PEND_COLL) p.pk = pk_set_chan(p.pk, hit.chan);
   return true;
 }
 

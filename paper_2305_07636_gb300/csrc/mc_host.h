@@ -79,6 +79,7 @@ struct mc_problem {
   uint64_t row = 0;    // elements of one batch row of the tallies: bins, then difference slots
   uint64_t range_rows = 0;  // (tally, cell, group) rows scored by the range walk
   int tuned_block = 0, tuned_bps = 0;  // mc_run_tune's choice (block_size, blocks_per_sm), 0 = none
+  int tuned_alg = MC_ALG_EVENT;        // mc_run_tune's algorithm for MC_ALG_AUTO
   std::vector<mcgb::HostTally> tallies;
   std::vector<uint8_t> blob[2];  // [0] FP32 tables, [1] FP64 tables
   mcgb::DevBuf d_blob[2];

@@ -25,7 +25,9 @@ constexpr uint32_t kChildKeyXor = 0xA5A5A5A5u;
 //   bits 16-17 surface hit type: 0 cell surface, 1 lattice x wall, 2 lattice y wall, 3 pin
 //   bit  18    lattice wall direction (1 = +1, 0 = -1)
 //   bits 19-26 index of the crossed cell surface
+//   bits 27-28 channel of a pending collision (drawn with the flight): 0 scatter, 1 production
 enum : uint32_t { PEND_NONE = 0, PEND_COLL = 1, PEND_SURF = 2 };
+enum : uint32_t { CHAN_SCATTER = 0, CHAN_PRODUCTION = 1, CHAN_CAPTURE = 2 };
 enum : uint32_t { HIT_CELL = 0, HIT_LAT_X = 1, HIT_LAT_Y = 2, HIT_PIN = 3 };
 
 __host__ __device__ inline uint32_t pk_g(uint32_t w) { return w & 0x1Fu; }
@@ -35,6 +37,8 @@ __host__ __device__ inline uint32_t pk_pend(uint32_t w) { return (w >> 14) & 3u;
 __host__ __device__ inline uint32_t pk_hit(uint32_t w) { return (w >> 16) & 3u; }
 __host__ __device__ inline int pk_dir(uint32_t w) { return ((w >> 18) & 1u) ? 1 : -1; }
 __host__ __device__ inline uint32_t pk_surf(uint32_t w) { return (w >> 19) & 0xFFu; }
+__host__ __device__ inline uint32_t pk_chan(uint32_t w) { return (w >> 27) & 3u; }
+__host__ __device__ inline uint32_t pk_set_chan(uint32_t w, uint32_t c) { return (w & ~(3u << 27)) | ((c & 3u) << 27); }
 __host__ __device__ inline uint32_t pk_make(uint32_t g, uint32_t cell, uint32_t pin) {
   return (g & 0x1Fu) | ((cell & 0xFFu) << 5) | ((pin & 1u) << 13);
 }

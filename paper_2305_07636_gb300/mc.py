@@ -192,7 +192,7 @@ def run_opts(**kw) -> mc_run_opts:
         if k == "precision" and isinstance(v, str):
             v = {"fp32": MC_FP32, "fp64": MC_FP64}[v]
         if k == "algorithm" and isinstance(v, str):
-            v = {"event": 0, "history": 1}[v]
+            v = {"event": 0, "history": 1, "auto": 2}[v]
         if k == "tally_mode" and isinstance(v, str):
             v = {"fixed": MC_TALLY_FIXED64, "fp64": MC_TALLY_FP64}[v]
         setattr(o, k, v)

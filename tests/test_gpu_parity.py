@@ -368,11 +368,14 @@ def test_run_tuner_picks_a_configuration_that_changes_nothing_but_time(torch):
     p = mc.Problem(prob)
     p.run(200_000, 8, tally_stripes=1)
     ref = (p.tally_batches(0), p.counters())
-    tuned, ms = mc.run_tune(p.h, 200_000, 9)
+    tuned, ms = mc.run_tune(p.h, 200_000, 9, mc.run_opts(algorithm="auto"))
     assert (tuned.block_size, tuned.blocks_per_sm) in ((256, 3), (256, 2), (128, 3), (128, 2)) and ms > 0
-    p.run(200_000, 8, tally_stripes=1)
-    b, c = p.tally_batches(0), p.counters()
-    assert np.array_equal(b, ref[0])
-    ref[1].pop("iterations"), c.pop("iterations")
-    assert c == ref[1]
+    assert tuned.algorithm in (0, 1)
+    ref[1].pop("iterations")
+    for alg in ("event", "auto"):  # the tuned configuration, then also the tuned algorithm
+        p.run(200_000, 8, tally_stripes=1, algorithm=alg)
+        b, c = p.tally_batches(0), p.counters()
+        assert np.array_equal(b, ref[0])
+        c.pop("iterations")
+        assert c == ref[1]
     p.close()
