@@ -81,6 +81,9 @@ def workload(name):
     from paper_2305_07636_gb300 import problems as P
     if name == "config2":
         return P.config2(), 10_000_000, "config2: 7-group infinite medium pulse, 1e7 histories"
+    if name == "config2x":
+        return P.config2_crossing(), 10_000_000, ("config2x: 7-group infinite medium pulse, 1e7 histories, "
+                                                  "track-length and time-crossing tallies")
     if name == "config1":
         return P.config1(), 10_000_000, "config1: 1-group slab, 1e7 histories"
     if name == "config3":
