@@ -126,12 +126,12 @@ def oracle_batch_sample(probs, nh, threads, frac, seed):
 
 def launches_per_run(prob):
     """Kernels one mc_run launches: transport and batch statistics, plus the range-walk
-    reconstruction when a track-length tally's time axis is much finer than its mesh (the
-    library's rule: nt >= 3 and nt >= 4 (nx + ny + nz))."""
+    reconstruction when a tally's time axis is much finer than its mesh (the library's rule:
+    nt >= 3 and nt >= 4 (nx + ny + nz))."""
     n = 2
     for t in prob["tallies"]:
         nx, ny, nz, nt = (len(t[k]) - 1 for k in ("x", "y", "z", "t"))
-        if t.get("estimator", "track") == "track" and nt >= 3 and nt >= 4 * (nx + ny + nz):
+        if nt >= 3 and nt >= 4 * (nx + ny + nz):
             return n + 1
     return n
 

@@ -239,7 +239,7 @@ int validate(const mc_problem_desc* d) {
       }
     }
     bins += (uint64_t)T.nx * T.ny * T.nz * (T.nt + (crossing ? 1 : 0)) * G;
-    if (!crossing && ranges_time_bins(T.nx, T.ny, T.nz, T.nt)) bins += (uint64_t)T.nx * T.ny * T.nz * (T.nt + 1) * G;
+    if (ranges_time_bins(T.nx, T.ny, T.nz, T.nt)) bins += (uint64_t)T.nx * T.ny * T.nz * (T.nt + 2) * G;
   }
   if (bins + d->n_surfaces > (1ull << 30)) return fail(MC_ERR_INVALID, "tallies too large");
   if (!(d->t_census > 0.0)) return fail(MC_ERR_INVALID, "t_census must be > 0 (inf for steady state)");
@@ -401,9 +401,10 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
     D.est = T.estimator;
     D.nval = T.nt + (T.estimator == MC_EST_TIME_CROSSING ? 1 : 0);
     D.n_bins = T.nx * T.ny * T.nz * G * D.nval;
-    D.range = (T.estimator == MC_EST_TRACK_LENGTH && ranges_time_bins(T.nx, T.ny, T.nz, T.nt)) ? 1 : 0;
+    D.range = ranges_time_bins(T.nx, T.ny, T.nz, T.nt) ? 1 : 0;
     D.diff_offset = doff;
-    if (D.range) doff += T.nx * T.ny * T.nz * G * (T.nt + 1);
+    D.ndiff = T.nt + (T.estimator == MC_EST_TIME_CROSSING ? 2 : 1);
+    if (D.range) doff += T.nx * T.ny * T.nz * G * D.ndiff;
     off += D.n_bins;
   }
   H.leak_offset = off;
@@ -507,7 +508,7 @@ int mc_problem_create(const mc_problem_desc* d, mc_problem** out) {
     h.nval = T.nt + (T.estimator == MC_EST_TIME_CROSSING ? 1 : 0);
     const double* e[4] = {T.x, T.y, T.z, T.t};
     for (int k = 0; k < 4; ++k) h.e[k].assign(e[k], e[k] + h.n[k] + 1);
-    p->range = p->range || (T.estimator == MC_EST_TRACK_LENGTH && ranges_time_bins(T.nx, T.ny, T.nz, T.nt));
+    p->range = p->range || ranges_time_bins(T.nx, T.ny, T.nz, T.nt);
     p->tallies.push_back(h);
   }
   for (int i = 0; i < 3; ++i) p->src_center[i] = 0.5 * (d->source.lo[i] + d->source.hi[i]);

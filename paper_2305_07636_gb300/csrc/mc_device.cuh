@@ -75,6 +75,11 @@ __device__ __forceinline__ float rinf<float>() { return CUDART_INF_F; }
 template <>
 __device__ __forceinline__ double rinf<double>() { return CUDART_INF; }
 
+// a / b in the tracking precision: FP32 tracking takes the fast hardware divide (within 2 ulp; the
+// correctly rounded one is a multi-instruction sequence and the walk divides several times per
+// flight), FP64 tracking the correctly rounded one (the oracle's arithmetic, replayed to 1e-9)
+__device__ __forceinline__ float rdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double rdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float rlog(float u) { return __logf(u); }
 __device__ __forceinline__ double rlog(double u) { return log(u); }
 __device__ __forceinline__ float rsqrt_(float v) { return sqrtf(v); }
@@ -295,7 +300,7 @@ template <typename R>
 __device__ __forceinline__ R plane_dist(R pos, R u, R c, int sense) {
   const bool leaving = sense > 0 ? (u < R(0)) : (u > R(0));
   if (!leaving) return rinf<R>();
-  const R d = (c - pos) / u;
+  const R d = rdiv(c - pos, u);
   return d > R(0) ? d : R(0);
 }
 
@@ -311,7 +316,7 @@ __device__ __forceinline__ R cyl_dist(R x, R y, R ux, R uy, R x0, R y0, R r, boo
   if (inside) {
     if (disc < R(0)) disc = R(0);
     const R sq = rsqrt_(disc);
-    const R d = (b <= R(0)) ? (-b + sq) / a : -c / (b + sq);
+    const R d = (b <= R(0)) ? rdiv(-b + sq, a) : rdiv(-c, b + sq);
     return d > R(0) ? d : R(0);
   }
   if (b >= R(0) || disc <= R(0)) return rinf<R>();
@@ -320,7 +325,7 @@ __device__ __forceinline__ R cyl_dist(R x, R y, R ux, R uy, R x0, R y0, R r, boo
   // exit distance and bounce it in and out on the spot.  eps = 2e-5 cm (FP32), 1e-12 cm (FP64).
   const R sq = rsqrt_(disc);
   if (R(2) * sq < (sizeof(R) == 4 ? R(2e-5) : R(1e-12)) * a) return rinf<R>();
-  const R d = c / (-b + sq);
+  const R d = rdiv(c, -b + sq);
   return d > R(0) ? d : R(0);
 }
 
@@ -460,20 +465,20 @@ __device__ R boundary_distance(const Tab<R>& T, const Part<R>& p, Hit& hit) {
     R lbest = rinf<R>();
     Hit lh = {HIT_LAT_X, 1, 0};
     if (p.ux > R(0) && ix + 1 < T.h->lat_nx) {
-      R d = (xlo + T.lp - p.x) / p.ux;
+      R d = rdiv(xlo + T.lp - p.x, p.ux);
       d = d > R(0) ? d : R(0);
       if (d < lbest) { lbest = d; lh = {HIT_LAT_X, 1, 0}; }
     } else if (p.ux < R(0) && ix > 0) {
-      R d = (xlo - p.x) / p.ux;
+      R d = rdiv(xlo - p.x, p.ux);
       d = d > R(0) ? d : R(0);
       if (d < lbest) { lbest = d; lh = {HIT_LAT_X, -1, 0}; }
     }
     if (p.uy > R(0) && iy + 1 < T.h->lat_ny) {
-      R d = (ylo + T.lp - p.y) / p.uy;
+      R d = rdiv(ylo + T.lp - p.y, p.uy);
       d = d > R(0) ? d : R(0);
       if (d < lbest) { lbest = d; lh = {HIT_LAT_Y, 1, 0}; }
     } else if (p.uy < R(0) && iy > 0) {
-      R d = (ylo - p.y) / p.uy;
+      R d = rdiv(ylo - p.y, p.uy);
       d = d > R(0) ? d : R(0);
       if (d < lbest) { lbest = d; lh = {HIT_LAT_Y, -1, 0}; }
     }
@@ -682,7 +687,8 @@ __device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Pa
     const R* et = time_edges<R>(base, D);
     const int n[3] = {D.nx, D.ny, D.nz};
     const int nt = D.nt;
-    if (D.est == MC_EST_TIME_CROSSING) {
+    const bool crossing = D.est == MC_EST_TIME_CROSSING;
+    if (crossing && !(RANGE && D.range)) {
       // Time-crossing estimator: at every time point t_j with t0 <= t_j < t0 + l / v the particle
       // scores its weight into the mesh cell it occupies at t_j (the readback multiplies by v_g).
       // One point per lane per warp-uniform round.
@@ -737,7 +743,7 @@ __device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Pa
       for (int d = 0; d < 3; ++d) {
         const int i = bin_search(e[d], n[d], pos[d]);
         idx[d] = i;
-        inv[d] = R(1) / u[d];
+        inv[d] = rdiv(R(1), u[d]);
         if (u[d] > R(0)) {
           step[d] = 1;
           if (i >= n[d]) live = false;
@@ -752,9 +758,77 @@ __device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Pa
           if (i < 0 || i >= n[d]) live = false;
         }
       }
-      it = bin_search(et, nt, t0);  // -1 before the first edge; then D_it <= s < D_it+1
-      if (it >= nt) live = false;
-      else stn = (et[it + 1] - t0) * v;
+      if (!crossing) {
+        it = bin_search(et, nt, t0);  // -1 before the first edge; then D_it <= s < D_it+1
+        if (it >= nt) live = false;
+        else stn = (et[it + 1] - t0) * v;
+      }
+    }
+    if (crossing) {
+      // Time-crossing range walk: one mesh cell per lane per round.  The points the flight spans
+      // while in that cell, D_j in [s, end), are a run jn .. jb that all score w into the cell: one
+      // direct score for a single point, else two difference marks (+w at jn, -w at jb + 1) that
+      // the reconstruction turns into w at every point of the run.
+      int jn = 0;  // the next point: first j with D_j >= s
+      if (live) {
+        int lo = 0, hi = nt + 1;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (et[mid] < t0) lo = mid + 1;
+          else hi = mid;
+        }
+        jn = lo;
+        if (jn > nt) live = false;
+      }
+      const uint32_t cb = (uint32_t)(batch_base + (uint64_t)D.bin_offset + (uint64_t)g * D.nval);
+      const int cs = T.G * D.nval;
+      const uint32_t db = (uint32_t)(batch_base + (uint64_t)T.h->total_bins + (uint64_t)D.diff_offset +
+                                     (uint64_t)g * D.ndiff);
+      const int dstride = T.G * D.ndiff;
+      while (__any_sync(kAll, live)) {
+        R end = s;
+        int ja = 0, jb = -1;
+        uint32_t cell = 0;
+        if (live) {
+          end = fmin(fmin(fmin(sn[0], sn[1]), sn[2]), l);
+          int lo = jn - 1, hi = nt;  // the last point with D_j < end (jn - 1: none)
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((et[mid] - t0) * v < end) lo = mid;
+            else hi = mid - 1;
+          }
+          if (end > s && lo >= jn && idx[0] >= 0 && idx[0] < n[0] && idx[1] >= 0 && idx[1] < n[1] && idx[2] >= 0 &&
+              idx[2] < n[2]) {
+            ja = jn;
+            jb = lo;
+            cell = (uint32_t)((idx[2] * n[1] + idx[1]) * n[0] + idx[0]);
+          }
+          jn = lo + 1;
+        }
+        stage(jb == ja, cb + cell * (uint32_t)cs + (uint32_t)ja, R(1));
+        if (__any_sync(kAll, jb > ja)) {
+          const bool run = jb > ja;
+          const uint32_t dc = db + cell * (uint32_t)dstride;
+          stage(run, dc + (uint32_t)ja, R(1));
+          stage(run, dc + (uint32_t)(jb + 1), R(-1));
+        }
+        if (live) {
+          if (end >= l || jn > nt) {
+            live = false;  // the flight or the time points ended
+          } else {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+              if (sn[d] <= end) {
+                idx[d] += step[d];
+                if (idx[d] < 0 || idx[d] >= n[d]) live = false;  // left the mesh along this axis
+                else sn[d] = (e[d][idx[d] + (step[d] > 0 ? 1 : 0)] - pos[d]) * inv[d];
+              }
+            }
+          }
+          s = end;
+        }
+      }
+      continue;
     }
     const uint32_t gbase = (uint32_t)(batch_base + (uint64_t)D.bin_offset + (uint64_t)g * nt);
     const int gstride = T.G * nt;
@@ -797,8 +871,8 @@ __device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Pa
     // difference slots of this (group, cell): nt + 1 marks per (cell, group) after the batch row's
     // bins; mark k belongs to bin k
     const uint32_t dbase = (uint32_t)(batch_base + (uint64_t)T.h->total_bins + (uint64_t)D.diff_offset +
-                                      (uint64_t)g * (nt + 1));
-    const int dstride = T.G * (nt + 1);
+                                      (uint64_t)g * D.ndiff);
+    const int dstride = T.G * D.ndiff;
     while (__any_sync(kAll, live)) {
       // this lane's sub-segment [s, end) in mesh cell idx, and the last time edge klt before end:
       // it spans time bins max(it, 0) .. min(klt, nt - 1)

@@ -293,7 +293,7 @@ __device__ bool flight_plan(const RunParams& P, const Tab<R>& T, Part<R>& p, Blo
   const int m = material_of(T, p.pk, p.elem);
   const R St = T.st[m * G + g];
   const Pair2<R> b0 = draw<R>(P.seed, p.tlo, p.thi, p.k, 0);  // (u_dist, u_channel)
-  const R dc = St > R(0) ? -rlog(b0.a) / St : rinf<R>();
+  const R dc = St > R(0) ? rdiv(-rlog(b0.a), St) : rinf<R>();
   const R ds = boundary_distance(T, p, hit);
   R dt = rinf<R>();
   if (T.h->has_census) {
@@ -487,13 +487,14 @@ __device__ __forceinline__ void stats_bin_fp64(const double* tally, uint64_t row
 }
 
 // Range-walk reconstruction of (batch j, range row r): a range row is one (tally, mesh cell, group)
-// of a tally scored by the range walk.  Its nt + 1 difference slots hold, summed over the stripes,
-// +w where a run of fully crossed time bins starts and -w one past where it ends; the running sum
-// over k is the weight of the flights that crossed bin k in full, each with the track length
-// v_g (t_{k+1} - t_k).  The warp scans the slots 32 at a time (shuffle scan with a carry) and adds
-// sum x length to bin k of stripe 0 (fixed point: rounded to the tally's scale; the sum is an exact
-// integer, so the result does not depend on the order of the atomics).  Only bins 1 .. nt - 2 can
-// be crossed in full, so a bin of infinite width never takes part.
+// of a tally scored by the range walk.  Its difference slots hold, summed over the stripes, +w
+// where a run starts and -w one past where it ends, so the running sum over k is the weight of the
+// runs that cover k.  Track length: bin k is crossed in full by those flights, each with the track
+// length v_g (t_{k+1} - t_k), and running sum x length is added to bin k (only bins 1 .. nt - 2
+// can be crossed in full, so a bin of infinite width never takes part).  Time crossing: point k
+// scores the running sum itself.  The warp scans the slots 32 at a time (shuffle scan with a
+// carry) and adds to stripe 0; in fixed point the sums are exact integers, so the result does not
+// depend on the order of the atomics.
 __device__ inline void reconstruct_warp(void* tally, const char* blob64, uint64_t row, int nb, int stripes, int fp64,
                                         int j, uint64_t r) {
   const TableHeader* H = reinterpret_cast<const TableHeader*>(blob64);
@@ -509,19 +510,22 @@ __device__ inline void reconstruct_warp(void* tally, const char* blob64, uint64_
   if (t >= H->n_tally) return;
   const TallyDesc& D = H->tally[t];
   const int nt = D.nt;
+  const bool crossing = D.est == MC_EST_TIME_CROSSING;
+  const int nval = D.nval;                   // nt bins or nt + 1 points
+  const int k_lo = crossing ? 0 : 1, k_hi = crossing ? nt : nt - 2;  // values a run can cover
   const int g = (int)(r % (uint64_t)H->G);
   const double v = reinterpret_cast<const double*>(blob64 + H->o_v)[g];
   const double* et = reinterpret_cast<const double*>(blob64 + D.o_et);
   const uint64_t stride = (uint64_t)nb * row;
-  const uint64_t dslot = (uint64_t)j * row + (uint64_t)H->total_bins + (uint64_t)D.diff_offset + r * (uint64_t)(nt + 1);
-  const uint64_t bslot = (uint64_t)j * row + (uint64_t)D.bin_offset + r * (uint64_t)nt;
+  const uint64_t dslot = (uint64_t)j * row + (uint64_t)H->total_bins + (uint64_t)D.diff_offset + r * (uint64_t)D.ndiff;
+  const uint64_t bslot = (uint64_t)j * row + (uint64_t)D.bin_offset + r * (uint64_t)nval;
   if (fp64) {
     double* T = reinterpret_cast<double*>(tally);
     double carry = 0.0;
-    for (int k0 = 0; k0 < nt; k0 += 32) {
+    for (int k0 = 0; k0 < nval; k0 += 32) {
       const int k = k0 + lane;
       double d = 0.0;
-      if (k < nt)
+      if (k < nval)
         for (int c = 0; c < stripes; ++c) d += __ldcg(T + c * stride + dslot + k);
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -530,15 +534,16 @@ __device__ inline void reconstruct_warp(void* tally, const char* blob64, uint64_
       }
       const double run = carry + d;
       carry += __shfl_sync(0xFFFFFFFFu, d, 31);
-      if (k >= 1 && k <= nt - 2 && run != 0.0) T[bslot + k] += run * (v * (et[k + 1] - et[k]));
+      if (k >= k_lo && k <= k_hi && run != 0.0)
+        T[bslot + k] += crossing ? run : run * (v * (et[k + 1] - et[k]));
     }
   } else {
     long long* T = reinterpret_cast<long long*>(tally);
     long long carry = 0;
-    for (int k0 = 0; k0 < nt; k0 += 32) {
+    for (int k0 = 0; k0 < nval; k0 += 32) {
       const int k = k0 + lane;
       long long d = 0;
-      if (k < nt)
+      if (k < nval)
         for (int c = 0; c < stripes; ++c) d += __ldcg(T + c * stride + dslot + k);
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -547,7 +552,8 @@ __device__ inline void reconstruct_warp(void* tally, const char* blob64, uint64_
       }
       const long long run = carry + d;
       carry += __shfl_sync(0xFFFFFFFFu, d, 31);
-      if (k >= 1 && k <= nt - 2 && run != 0) T[bslot + k] += __double2ll_rn((double)run * (v * (et[k + 1] - et[k])));
+      if (k >= k_lo && k <= k_hi && run != 0)
+        T[bslot + k] += crossing ? run : __double2ll_rn((double)run * (v * (et[k + 1] - et[k])));
     }
   }
 }

@@ -60,11 +60,12 @@ struct TallyDesc {
   int est;                     // MC_EST_TRACK_LENGTH or MC_EST_TIME_CROSSING
   int nval;                    // values per (cell, group) along time: nt bins or nt + 1 points
   int diff_offset;             // range walk: first difference slot after the batch row's bins
-  int pad0;
+  int ndiff;                   // range walk: difference slots per (cell, group): nt + 1 (track
+                               // length) or nt + 2 (time crossing)
 };
 
-// A track-length tally is scored by the range walk when its time axis is much finer than its
-// spatial mesh (flights then cross many more time edges than mesh planes).
+// A tally is scored by the range walk when its time axis is much finer than its spatial mesh
+// (flights then cross many more time edges or points than mesh planes).
 inline bool ranges_time_bins(int nx, int ny, int nz, int nt) { return nt >= 3 && nt >= 4 * (nx + ny + nz); }
 
 struct TableHeader {

@@ -108,6 +108,35 @@ def test_crossing_beam_positions(torch, precision):
     p.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_range_walks_split_runs_across_cells(torch, precision):
+    """Both range walks on a mesh of several cells (40 time values over 5 cells: the tallies take
+    the range walk).  A beam particle is at x = t, so each time bin [k/8, (k+1)/8) lies in cell
+    floor(k/8) with track length e^{-t_k} - e^{-t_k+1}, and each time point t_j in cell floor(t_j)
+    with flux e^{-t_j}; every other (cell, time) value is zero (the track tally up to rounding where
+    a time edge meets a cell plane)."""
+    xe = np.linspace(0, 5, 6)
+    te = np.linspace(0, 5, 41)
+    pts = 0.0625 + 0.125 * np.arange(40)
+    prob = P.slab_problem(5.0, 1.0, 0.0, direction="beam_x", surface_source=True)
+    prob = P.with_tallies(prob, [P.mesh(x=xe, t=te), P.mesh(x=xe, t=pts, estimator="crossing")])
+    p = mc.Problem(prob)
+    p.run(2_000_000, 54, precision=precision, n_batches=256)
+    m, s = (a.reshape(5, 40) for a in p.tally(0))
+    cell = np.arange(40) // 8
+    mask = np.zeros_like(m, dtype=bool)
+    mask[cell, np.arange(40)] = True
+    assert np.all(np.abs(m[~mask]) < 1e-5 * m[mask].max())
+    check_z(exact_z(m[mask], s[mask], np.exp(-te[:-1]) - np.exp(-te[1:])), 40)
+    m, s = (a.reshape(5, 40) for a in p.tally(1))
+    cell = np.floor(pts).astype(int)
+    mask = np.zeros_like(m, dtype=bool)
+    mask[cell, np.arange(40)] = True
+    assert np.all(m[~mask] == 0.0)
+    check_z(exact_z(m[mask], s[mask], np.exp(-pts)), 40)
+    p.close()
+
+
 # ----------------------------------------------------------------------------- implicit capture
 
 
