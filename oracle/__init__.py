@@ -91,6 +91,19 @@ class OrOpts(C.Structure):
                 ("implicit_capture", C.c_int), ("wr_cutoff", C.c_double), ("wr_survival", C.c_double)]
 
 
+class OrEigenOpts(C.Structure):
+    _fields_ = [("n_per_cycle", C.c_uint64), ("seed", C.c_uint64), ("n_inactive", C.c_int),
+                ("n_active", C.c_int), ("threads", C.c_int), ("fixed_bits", C.c_int),
+                ("log_first", C.c_uint64), ("log_count", C.c_uint64),
+                ("log", C.POINTER(OrEvent)), ("log_cap", C.c_uint64),
+                ("log_n", C.POINTER(C.c_uint64))]
+
+
+class OrEigenResult(C.Structure):
+    _fields_ = [("k_cycle", C.POINTER(C.c_double)), ("sites_cycle", C.POINTER(C.c_uint64)),
+                ("tally_cycle", C.POINTER(C.c_double)), ("counters", C.c_int64 * NCOUNT)]
+
+
 class OrResult(C.Structure):
     _fields_ = [("s1", C.POINTER(C.c_double)), ("s2", C.POINTER(C.c_double)),
                 ("fixed", C.POINTER(C.c_int64)), ("counters", C.c_int64 * NCOUNT)]
@@ -103,6 +116,9 @@ def lib():
             L = C.CDLL(build())
             L.or_run.argtypes = [C.POINTER(OrProblem), C.POINTER(OrOpts), C.POINTER(OrResult)]
             L.or_run.restype = C.c_int
+            L.or_run_eigen.argtypes = [C.POINTER(OrProblem), C.POINTER(OrEigenOpts),
+                                       C.POINTER(OrEigenResult)]
+            L.or_run_eigen.restype = C.c_int
             L.or_total_bins.argtypes = [C.POINTER(OrProblem)]
             L.or_total_bins.restype = C.c_int
             L.or_philox.argtypes = [C.c_uint32, C.c_uint32, C.POINTER(C.c_uint32),
@@ -304,6 +320,62 @@ def run(prob: dict, n: int, seed: int = 1, threads: int | None = None, first: in
     if events is not None:
         ev = events_to_numpy(events, int(log_n.value))
     return Result(m.tally_shapes, n, s1, s2, fx, list(res.counters), m.n_surf, ev)
+
+
+class EigenResult:
+    """k of every cycle, the mean and standard error of k over the active cycles, sites banked per
+    cycle, and every tally's mean and standard error over the active cycles (each active cycle one
+    batch, as the paper's cycle statistics)."""
+
+    def __init__(self, shapes, n_surf, k, sites, tc, n_inactive, counters, events):
+        self.k_cycle, self.sites_cycle = k, sites
+        ka = k[n_inactive:]
+        self.k_mean = float(ka.mean())
+        self.k_std = float(ka.std(ddof=1) / math.sqrt(len(ka)))
+        self.counters = dict(zip(COUNTER_NAMES, [int(c) for c in counters]))
+        self.events = events
+        self.cycle_tallies = tc
+        mean = tc.mean(axis=0)
+        std = tc.std(axis=0, ddof=1) / math.sqrt(tc.shape[0])
+        self.tallies = []
+        off = 0
+        for shp in shapes:
+            size = int(np.prod(shp))
+            self.tallies.append((mean[off:off + size].reshape(shp), std[off:off + size].reshape(shp)))
+            off += size
+        self.leak_mean, self.leak_std = mean[off:off + n_surf], std[off:off + n_surf]
+
+
+def run_eigen(prob: dict, n: int, n_inactive: int, n_active: int, seed: int = 1,
+              threads: int | None = None, log_first: int = 0, log_count: int = 0,
+              log_cap: int = 0) -> EigenResult:
+    """k-eigenvalue power iteration of the oracle (see or_run_eigen in oracle.h)."""
+    L = lib()
+    m = Marshalled(prob)
+    nb = L.or_total_bins(C.byref(m.s))
+    nc = n_inactive + n_active
+    k = np.zeros(nc)
+    sites = np.zeros(nc, np.uint64)
+    tc = np.zeros((max(1, n_active), nb))
+    o = OrEigenOpts()
+    o.n_per_cycle, o.seed, o.n_inactive, o.n_active = n, seed, n_inactive, n_active
+    o.threads = threads if threads else (os.cpu_count() or 1)
+    o.fixed_bits = 32
+    events, log_n = None, C.c_uint64(0)
+    if log_count > 0:
+        cap = log_cap if log_cap else 64 * log_count * nc
+        events = (OrEvent * cap)()
+        o.log, o.log_cap, o.log_first, o.log_count = events, cap, log_first, log_count
+        o.log_n = C.pointer(log_n)
+    r = OrEigenResult()
+    r.k_cycle = k.ctypes.data_as(C.POINTER(C.c_double))
+    r.sites_cycle = sites.ctypes.data_as(C.POINTER(C.c_uint64))
+    r.tally_cycle = tc.ctypes.data_as(C.POINTER(C.c_double))
+    rc = L.or_run_eigen(C.byref(m.s), C.byref(o), C.byref(r))
+    if rc != 0:
+        raise RuntimeError(f"or_run_eigen failed: {rc}")
+    ev = events_to_numpy(events, int(log_n.value)) if events is not None else None
+    return EigenResult(m.tally_shapes, m.n_surf, k, sites, tc[:n_active], n_inactive, list(r.counters), ev)
 
 
 EVENT_DTYPE = np.dtype([("tag", np.uint64), ("root", np.uint64), ("k", np.uint32),

@@ -219,3 +219,23 @@ def isotropic_crossings(track_density: float, area: float) -> float:
     uniform isotropic flux of scalar value `track_density` (track length per unit volume):
     each one-way partial current is phi/4, so crossings = phi/2 per unit area."""
     return 0.5 * track_density * area
+
+
+# ------------------------------------------------------------------ k-eigenvalue, infinite medium
+
+
+def infinite_k(mat):
+    """k of an infinite homogeneous medium and its fundamental group spectrum: the dominant
+    eigenpair of A^-1 F with the removal operator A = diag(Sigma_t) - S^T (S from -> to) and the
+    production operator F = chi (nu Sigma_f)^T.  Returns (k, phi) with phi >= 0 summing to 1 (the
+    volume-integrated group flux shape)."""
+    st = np.asarray(mat["sigma_t"], dtype=np.float64)
+    S = np.asarray(mat["sigma_s"], dtype=np.float64)
+    nsf = np.asarray(mat["nu"], dtype=np.float64) * np.asarray(mat["sigma_f"], dtype=np.float64)
+    chi = np.asarray(mat["chi"], dtype=np.float64)
+    A = np.diag(st) - S.T
+    F = np.outer(chi, nsf)
+    lam, V = np.linalg.eig(np.linalg.solve(A, F))
+    i = int(np.argmax(lam.real))
+    phi = np.abs(V[:, i].real)
+    return float(lam[i].real), phi / phi.sum()

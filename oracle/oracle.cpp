@@ -95,6 +95,21 @@ struct Physics {
   double cutoff, survival;
 };
 
+// k-eigenvalue cycle state of one history: production banks fission sites for the next cycle
+// (floor(nu / k + xi) of them, k the previous cycle's estimate) instead of transporting
+// secondaries; every flight adds w l nu Sigma_f to the track-length estimate of k
+struct Site {
+  double x, y, z;
+  int g;
+};
+struct Eig {
+  double inv_k;             // 1 / k of the previous cycle
+  bool score;               // tallies are scored (active cycles)
+  std::vector<Site>* sites; // this history's sites, in the order they are produced
+  int64_t ktl;              // sum of llrint(w l nu Sigma_f 2^32) over this thread's flights: an
+                            // exact integer sum, so k does not depend on the thread count
+};
+
 struct Prob {
   int G, M;
   std::vector<double> st, ss, sf, nu, chi, v;
@@ -613,7 +628,7 @@ struct Logger {
 };
 
 void transport(const Prob& P, const Physics& ph, uint64_t seed, Particle q, std::vector<Particle>& stack,
-               Acc& acc, const Logger& lg) {
+               Acc& acc, const Logger& lg, Eig* eig = nullptr) {
   const int G = P.G;
   while (true) {
     int m = material(P, q);
@@ -641,7 +656,8 @@ void transport(const Prob& P, const Physics& ph, uint64_t seed, Particle q, std:
     acc.cnt[OR_C_FLIGHT]++;
     if (!(l < INF)) ev = OR_EV_LOST;
     if (ev != OR_EV_LOST) {
-      score_segment(P, q, l, acc);
+      if (!eig || eig->score) score_segment(P, q, l, acc);
+      if (eig) eig->ktl += (int64_t)std::llrint(q.w * l * (P.nu[m * G + q.g] * P.sf[m * G + q.g]) * 4294967296.0);
       q.x += l * q.ux;
       q.y += l * q.uy;
       q.z += l * q.uz;
@@ -681,7 +697,7 @@ void transport(const Prob& P, const Physics& ph, uint64_t seed, Particle q, std:
       if (hit.type == HIT_CELL) {
         int s = hit.idx;
         if (P.sbc[s] == OR_VACUUM) {
-          acc.add(P.total_bins + s, q.w);
+          if (!eig || eig->score) acc.add(P.total_bins + s, q.w);
           acc.cnt[OR_C_LEAK]++;
           rec.outcome = 2;
           alive = false;
@@ -748,6 +764,21 @@ void transport(const Prob& P, const Physics& ph, uint64_t seed, Particle q, std:
       } else if (xi < Ss + Sf) {
         acc.cnt[OR_C_PRODUCTION]++;
         Pair b3 = draw(seed, q.tag, k, 3);
+        if (eig) {
+          // fission sites for the next cycle: floor(nu / k + xi), group from chi, at this point
+          int n = (int)std::floor(P.nu[m * G + q.g] * eig->inv_k + b3.a);
+          for (int j = 0; j < n; ++j) {
+            uint64_t ct = child_tag(seed, q.tag, k, (uint32_t)j, CHILD_MARK);
+            Pair c2 = draw(seed, ct, SOURCE_EVENT, 2);
+            eig->sites->push_back({q.x, q.y, q.z, sample_cdf(&P.chi_cdf[m * G], G, c2.b)});
+            acc.cnt[OR_C_SECONDARY]++;
+          }
+          rec.outcome = 1;
+          rec.n_child = n;
+          alive = false;
+          if (logit) acc.log.push_back(rec);
+          return;
+        }
         int n = (int)std::floor(P.nu[m * G + q.g] + b3.a);
         for (int j = 0; j < n; ++j) {
           Particle c = q;
@@ -793,9 +824,127 @@ void run_range(const Prob& P, const Physics& ph, uint64_t seed, uint64_t h0, uin
   }
 }
 
+// k-eigenvalue power iteration (the paper's C5G7 runs, Section 3): cycle 0 starts N histories
+// from the problem's source; every later cycle starts N histories at the previous cycle's fission
+// sites, picked by systematic sampling (combing) with one random offset per cycle, so the
+// population stays N.  Sites are ordered by the source history that produced them, then in
+// production order, which fixes the order whatever the thread count.
+struct EigRun {
+  const Prob& P;
+  const Physics& ph;
+  uint64_t seed, N;
+  int threads;
+};
+
+// source particle h of cycle c >= 1 at site i of the previous cycle's bank
+Particle site_source(const Prob& P, uint64_t seed, uint64_t h, uint32_t cycle, const Site& s) {
+  Particle q{};
+  q.tag = h | ((uint64_t)cycle << 32);
+  q.root = h;
+  Pair b1 = draw(seed, q.tag, SOURCE_EVENT, 1), b2 = draw(seed, q.tag, SOURCE_EVENT, 2);
+  q.x = s.x;
+  q.y = s.y;
+  q.z = s.z;
+  isotropic(2.0 * b1.b - 1.0, b2.a, q.ux, q.uy, q.uz);
+  q.g = s.g;
+  q.t = 0.0;
+  q.w = 1.0;
+  q.k = 0;
+  q.cell = find_cell(P, q.x, q.y, q.z, -1, 0, 0.0, 0.0, 0.0);
+  q.ix = q.iy = q.in_pin = 0;
+  if (q.cell >= 0 && P.cmat[q.cell] < 0) lattice_locate(P, q);
+  return q;
+}
+
+// the combing offset of cycle c: first uniform of the counter (2^32 - 1, c, 2^32 - 1, 4)
+double comb_offset(uint64_t seed, uint32_t cycle) {
+  return draw(seed, 0xFFFFFFFFull | ((uint64_t)cycle << 32), SOURCE_EVENT, 4).a;
+}
+
 }  // namespace
 
 extern "C" {
+
+int or_run_eigen(const or_problem* p, const or_eigen_opts* o, or_eigen_result* r) {
+  Prob P = copy_problem(p);
+  Physics ph{false, 0.0, 0.0};
+  const uint64_t N = o->n_per_cycle;
+  const int n_cycles = o->n_inactive + o->n_active;
+  if (N == 0 || n_cycles <= 0 || o->n_active < 0) return -1;
+  int nt = o->threads > 0 ? o->threads : 1;
+  if ((uint64_t)nt > N) nt = (int)N;
+  const int nb = P.total_bins + P.n_surf;
+  std::vector<Site> prev, next;
+  double k_prev = 1.0;
+  for (int k = 0; k < OR_NCOUNT; ++k) r->counters[k] = 0;
+  Logger lg{o->log != nullptr, o->log_first, o->log_count};
+  std::vector<or_event> log;
+  for (int cyc = 0; cyc < n_cycles; ++cyc) {
+    const bool active = cyc >= o->n_inactive;
+    const double u0 = comb_offset(o->seed, (uint32_t)cyc);
+    std::vector<Acc> accs(nt);
+    std::vector<std::vector<Site>> sites(nt);
+    std::vector<int64_t> ktl(nt, 0);
+    std::vector<std::thread> th;
+    for (int i = 0; i < nt; ++i) {
+      accs[i].init(nb, o->fixed_bits);
+      uint64_t h0 = N * (uint64_t)i / (uint64_t)nt, h1 = N * (uint64_t)(i + 1) / (uint64_t)nt;
+      th.emplace_back([&, i, h0, h1] {
+        Eig eig{1.0 / k_prev, active, &sites[i], 0};
+        std::vector<Particle> stack;
+        for (uint64_t h = h0; h < h1; ++h) {
+          Particle q;
+          if (cyc == 0) {
+            q = source_particle(P, o->seed, h);
+          } else {
+            const uint64_t M = prev.size();
+            uint64_t idx = (uint64_t)std::floor(((double)h + u0) * (double)M / (double)N);
+            if (idx >= M) idx = M - 1;
+            q = site_source(P, o->seed, h, (uint32_t)cyc, prev[idx]);
+          }
+          accs[i].cnt[OR_C_SOURCE]++;
+          if (q.cell < 0) {
+            accs[i].cnt[OR_C_LOST]++;
+          } else {
+            transport(P, ph, o->seed, q, stack, accs[i], lg, &eig);
+          }
+          accs[i].end_history();
+        }
+        ktl[i] = eig.ktl;
+      });
+    }
+    for (auto& t : th) t.join();
+    next.clear();
+    int64_t ksum = 0;
+    for (int i = 0; i < nt; ++i) {
+      next.insert(next.end(), sites[i].begin(), sites[i].end());
+      ksum += ktl[i];
+      for (int k = 0; k < OR_NCOUNT; ++k) r->counters[k] += accs[i].cnt[k];
+      for (const or_event& e : accs[i].log) log.push_back(e);
+    }
+    const double k_cyc = (double)ksum / 4294967296.0 / (double)N;
+    if (r->k_cycle) r->k_cycle[cyc] = k_cyc;
+    if (r->sites_cycle) r->sites_cycle[cyc] = next.size();
+    if (active && r->tally_cycle) {
+      double* out = r->tally_cycle + (size_t)(cyc - o->n_inactive) * nb;
+      for (int b = 0; b < nb; ++b) {
+        double a = 0.0;
+        for (int i = 0; i < nt; ++i) a += accs[i].s1[b];
+        out[b] = a / (double)N;
+      }
+    }
+    if (next.empty()) return -2;  // no fission site: the chain died out
+    prev.swap(next);
+    k_prev = k_cyc;
+  }
+  if (o->log) {
+    uint64_t w = 0;
+    for (const or_event& e : log)
+      if (w < o->log_cap) o->log[w++] = e;
+    if (o->log_n) *o->log_n = w;
+  }
+  return 0;
+}
 
 int or_total_bins(const or_problem* p) {
   int off = 0;

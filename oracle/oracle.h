@@ -134,6 +134,36 @@ typedef struct {
 int or_total_bins(const or_problem* p);
 int or_run(const or_problem* p, const or_opts* o, or_result* r);
 
+/* k-eigenvalue power iteration (the paper's C5G7 runs, Section 3), analog: n_inactive + n_active
+ * cycles of n_per_cycle histories.  Cycle 0 starts at the problem's source; cycle c >= 1 starts
+ * history h (tag h + 2^32 c) at site floor((h + u0) M / N) of the previous cycle's M fission sites
+ * (systematic sampling; u0 = first uniform of Philox(seed, (2^32 - 1, c, 2^32 - 1, 4))), with an
+ * isotropic direction from its source draws (blocks 1, 2), the site's group, t = 0, w = 1.  A
+ * production event banks floor(nu / k + xi) sites (k = the previous cycle's estimate, 1 before
+ * cycle 0; groups from chi by each child tag's source draw) instead of transporting secondaries.
+ * Sites are ordered by producing history, then production order.  k of a cycle is the
+ * track-length estimate: sum over flights of w l nu Sigma_f, divided by N, summed in int64 fixed
+ * point at 2^-32 (llrint per flight) so that it does not depend on the thread count.  Tallies are
+ * scored in active cycles only. */
+typedef struct {
+  uint64_t n_per_cycle, seed;
+  int n_inactive, n_active, threads, fixed_bits;
+  uint64_t log_first, log_count; /* histories [log_first, +log_count) of every cycle are logged */
+  or_event* log;
+  uint64_t log_cap;
+  uint64_t* log_n;
+} or_eigen_opts;
+
+typedef struct {
+  double* k_cycle;       /* [n_inactive + n_active] */
+  uint64_t* sites_cycle; /* [n_inactive + n_active] fission sites banked in each cycle */
+  double* tally_cycle;   /* [n_active][total bins]: each active cycle's tallies per source particle */
+  int64_t counters[OR_NCOUNT]; /* summed over all cycles; OR_C_SECONDARY counts banked sites */
+} or_eigen_result;
+
+/* 0 on success; -1 for bad options; -2 if a cycle banked no fission site. */
+int or_run_eigen(const or_problem* p, const or_eigen_opts* o, or_eigen_result* r);
+
 /* unit-level entry points used by the tests */
 void or_philox(uint32_t k0, uint32_t k1, const uint32_t ctr[4], uint32_t out[4]);
 double or_u01(uint32_t a, uint32_t b);

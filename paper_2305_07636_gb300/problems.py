@@ -212,6 +212,43 @@ def config2_crossing(seed=2, G=7, n_tbins=100, side=10.0):
     return q
 
 
+def eigen_infinite_1g(sigma_t=1.0, sigma_s=0.5, sigma_f=0.2, nu=2.4, side=10.0):
+    """One-group infinite medium with fission for k-eigenvalue runs (steady state):
+    k = nu Sigma_f / (Sigma_t - Sigma_s) = 0.96."""
+    q = infinite_medium_1g(sigma_t, sigma_s, sigma_f, nu, 1.0, side=side, name="eigen1g")
+    return q
+
+
+def eigen_infinite_mg(seed=6, G=7, side=10.0):
+    """Seven-group infinite medium of one seeded fissile material (reflective cube), steady state,
+    for k-eigenvalue runs; a group-flux tally."""
+    rng = np.random.default_rng([seed, 2000])
+    mat = _lattice_materials(rng, G, True)
+    surfs, hs = box_surfaces((0, 0, 0), (side,) * 3, "reflect")
+    cells = [{"halfspaces": hs, "material": 0}]
+    src = source("box", (0, 0, 0), (side,) * 3, "iso", G, 0)
+    tal = [mesh(x=(0, side), y=(0, side), z=(0, side))]
+    return problem("eigenmg", G, log_speeds(G), [mat], surfs, cells, src, tal)
+
+
+def pin_cell(seed=7, G=7, pitch=1.26, radius=0.54, mesh_n=4):
+    """Infinite pin cell for k-eigenvalue runs (the paper's C5G7 UO2 pin-cell benchmark in shape
+    only: seeded synthetic cross sections, no C5G7 data): a fissile pin of radius 0.54 cm in a
+    1.26 cm square of a scattering moderator, reflective on all sides (z infinite), 7 groups,
+    steady state, uniform initial source; a 4 x 4 group-flux mesh."""
+    rng = np.random.default_rng([seed, 3000])
+    fuel = _lattice_materials(rng, G, True)
+    sigma_t = rng.uniform(0.3, 2.0, G)
+    moderator = material(sigma_t, seeded_scatter(rng, G, sigma_t, 0.95, 0.995))  # weakly absorbing
+    surfs, hs = box_surfaces((0, 0, 0), (pitch, pitch, 0), "reflect", axes=(0, 1))
+    cells = [{"halfspaces": hs, "material": -1}]
+    lat = {"nx": 1, "ny": 1, "x0": 0.0, "y0": 0.0, "pitch": float(pitch), "radius": float(radius),
+           "pin_material": [0], "matrix_material": 1}
+    src = source("box", (0, 0, 0), (pitch, pitch, 0), "iso", G, 0)
+    tal = [mesh(x=np.linspace(0, pitch, mesh_n + 1), y=np.linspace(0, pitch, mesh_n + 1))]
+    return problem("pincell", G, log_speeds(G), [fuel, moderator], surfs, cells, src, tal, INF, lat)
+
+
 def offspring_matrix(mat):
     """K[g][g'] = (sigma_s[g->g'] + nu sigma_f[g] chi[g']) / sigma_t[g] (mean offspring per
     collision); used only to scale the synthetic inputs."""
