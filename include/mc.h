@@ -241,6 +241,30 @@ int mc_problem_create(const mc_problem_desc* d, mc_problem** out);
 int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts* opts,
            void* stream);
 
+/* k-eigenvalue power iteration (the paper's C5G7 runs, Section 3: k-eigenvalue, inactive and active
+ * cycles), analog transport of n_inactive + n_active cycles of n_per_cycle histories each on a
+ * steady-state problem (t_census = inf) with production cross sections.
+ *   Cycle 0 starts from the problem's source.  A production event does not transport secondaries:
+ *   it banks floor(nu / k + xi) fission sites (position, group drawn from chi) for the next cycle,
+ *   k being the previous cycle's estimate (1 before cycle 0), in slots of the producing history, so
+ *   that the sites are ordered by producing history and production order whatever the schedule.
+ *   Cycle c >= 1 starts history h (particle tag h + 2^32 c) at site floor((h + u0) M / N) of the M
+ *   sites of cycle c - 1 (systematic sampling; u0 = the first uniform of Philox(seed, counter
+ *   (2^32 - 1, c, 2^32 - 1, 4))), isotropic, in the site's group, at t = 0 with weight 1.
+ *   k of a cycle is the track-length estimate: the sum over its flights of w l nu Sigma_f (summed
+ *   exactly in int64 fixed point at 2^-32), divided by N.  Tallies are scored in the active cycles
+ *   only, each active cycle being one statistical batch (mc_tally_get then gives the mean over the
+ *   active cycles per source particle and its standard error).
+ *   opts: precision, tally mode, kernel configuration, algorithm and event logging as for mc_run
+ *   (a log covers histories [log_first, +log_count) of every cycle); n_batches is replaced by
+ *   n_active; weight windows, implicit capture and first_history are rejected.
+ *   Outputs (host, nullable): k_cycle[n_inactive + n_active], sites_cycle[same], *k_mean and
+ *   *k_std_err over the active cycles.  Synchronises once per cycle (to read k).  MC_ERR_STATE if a
+ *   cycle banks no site; device errors as for mc_wait. */
+int mc_run_eigen(mc_problem* p, uint64_t n_per_cycle, int n_inactive, int n_active, uint64_t seed,
+                 const mc_run_opts* opts, void* stream, double* k_cycle, uint64_t* sites_cycle, double* k_mean,
+                 double* k_std_err);
+
 /* Autotuner of mc_run for one problem: runs n_histories with each candidate configuration (256 or
  * 128 threads per CTA; the 80-register build at 3 CTAs of 256 per SM, or the 128-register build at
  * 2; with opts->algorithm == MC_ALG_AUTO each under both algorithms), times each run with CUDA

@@ -27,6 +27,10 @@ cudaError_t launch_transport(const RunParams& P, int grid, int block, size_t sme
                              bool range);
 template <typename R>
 cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide, bool range);
+cudaError_t launch_scan_sites(const uint32_t* counts, unsigned long long* scan, unsigned long long* block_sums, uint64_t n,
+                              cudaStream_t s);
+cudaError_t launch_comb(const uint32_t* counts, const unsigned long long* scan, const uint4* sites, uint32_t nmax,
+                        uint64_t n, uint64_t seed, uint32_t next_cycle, uint4* src, int lanes, cudaStream_t s);
 cudaError_t launch_reconstruct(void* tally, const char* blob64, uint64_t rows, uint64_t row, int nb, int stripes,
                                int fp64, cudaStream_t s);
 cudaError_t launch_batch_stats(const void* tally, int fp64, uint64_t bins, uint64_t row, int nb, int stripes,
@@ -308,7 +312,7 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
     H.tc_hi = (float)d->t_census;
     H.tc_lo = (float)(d->t_census - (double)H.tc_hi);
   }
-  std::vector<R> st(M * G), ss(M * G), ssf(M * G), nu(M * G), scdf(M * G * G), chi(M * G);
+  std::vector<R> st(M * G), ss(M * G), ssf(M * G), nu(M * G), nusf(M * G), scdf(M * G * G), chi(M * G);
   std::vector<double> tmp(G);
   for (int m = 0; m < M; ++m) {
     for (int g = 0; g < G; ++g) {
@@ -319,6 +323,7 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
       ss[m * G + g] = (R)s;
       ssf[m * G + g] = (R)(s + d->sigma_f[m * G + g]);
       nu[m * G + g] = (R)d->nu[m * G + g];
+      nusf[m * G + g] = (R)(d->nu[m * G + g] * d->sigma_f[m * G + g]);
       cdf_row(row, G, tmp.data());
       for (int h = 0; h < G; ++h) scdf[(m * G + g) * G + h] = (R)tmp[h];
     }
@@ -336,6 +341,7 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
   H.o_ss = B.put(ss);
   H.o_ssf = B.put(ssf);
   H.o_nu = B.put(nu);
+  H.o_nusf = B.put(nusf);
   H.o_v = B.put(v);
   H.o_inv_v = B.put(inv_v);
   H.o_scdf = B.put(scdf);
@@ -521,6 +527,7 @@ int mc_problem_create(const mc_problem_desc* d, mc_problem** out) {
   p->total_bins = H->total_bins;
   p->leak_offset = H->leak_offset;
   p->row = (uint64_t)H->total_bins + (uint64_t)H->total_diff;
+  for (int i = 0; i < p->M * p->G; ++i) p->nu_max = std::max(p->nu_max, d->sigma_f[i] > 0.0 ? d->nu[i] : 0.0);
   for (int t = 0; t < H->n_tally; ++t)
     if (H->tally[t].range) p->range_rows += (uint64_t)H->tally[t].nx * H->tally[t].ny * H->tally[t].nz * H->G;
   rc = current_device(&p->dev);
@@ -689,6 +696,200 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   p->tally_fp64 = P.tally_fp64;
   p->stripes = stripes;
   p->fixed_scale = P.fixed_scale;
+  return MC_OK;
+}
+
+int mc_run_eigen(mc_problem* p, uint64_t n_per_cycle, int n_inactive, int n_active, uint64_t seed,
+                 const mc_run_opts* opts, void* stream, double* k_cycle, uint64_t* sites_cycle, double* k_mean,
+                 double* k_std_err) {
+  g_err.clear();
+  if (!p) return fail(MC_ERR_INVALID, "problem is NULL");
+  mc_run_opts o;
+  if (opts) o = *opts;
+  else mc_run_opts_default(&o);
+  if (o.block_size == 0 && o.blocks_per_sm == 0 && p->tuned_block) {
+    o.block_size = p->tuned_block;
+    o.blocks_per_sm = p->tuned_bps;
+  }
+  if (o.algorithm == MC_ALG_AUTO) o.algorithm = p->tuned_alg;
+  const uint64_t N = n_per_cycle;
+  const int n_cycles = n_inactive + n_active;
+  if (N < 1 || N >= (1ull << 32)) return fail(MC_ERR_INVALID, "n_per_cycle must be in [1, 2^32)");
+  if (n_inactive < 0 || n_active < 2 || n_cycles > 65535)
+    return fail(MC_ERR_INVALID, "need n_inactive >= 0, n_active >= 2, at most 65535 cycles");
+  if (o.precision != MC_FP32 && o.precision != MC_FP64) return fail(MC_ERR_INVALID, "precision");
+  if (o.tally_mode != MC_TALLY_FIXED64 && o.tally_mode != MC_TALLY_FP64) return fail(MC_ERR_INVALID, "tally_mode");
+  if (o.fixed_bits < 0 || o.fixed_bits > 48) return fail(MC_ERR_INVALID, "fixed_bits outside [0,48]");
+  if (o.block_size != 0 && (o.block_size < 32 || o.block_size > 256 || o.block_size % 32))
+    return fail(MC_ERR_INVALID, "block_size must be a multiple of 32 in [32,256]");
+  if (o.algorithm != MC_ALG_EVENT && o.algorithm != MC_ALG_HISTORY) return fail(MC_ERR_INVALID, "algorithm");
+  if (o.ww_enable || o.implicit_capture || o.first_history)
+    return fail(MC_ERR_INVALID, "k-eigenvalue cycles are analog, without weight windows or a first_history offset");
+  const TableHeader* H0 = reinterpret_cast<const TableHeader*>(p->blob[0].data());
+  if (H0->has_census) return fail(MC_ERR_INVALID, "k-eigenvalue cycles need a steady-state problem (t_census = inf)");
+  if (!(p->nu_max > 0.0)) return fail(MC_ERR_INVALID, "no material has a production cross section");
+  int dev;
+  int rc = current_device(&dev);
+  if (rc != MC_OK) return rc;
+  if (dev != p->dev) return fail(MC_ERR_STATE, "problem was created on device %d, current is %d", p->dev, dev);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int fp64 = o.precision == MC_FP64;
+  const int lanes = fp64 ? kLanesFP64 : kLanesFP32;
+  const int slanes = fp64 ? kSiteLanesFP64 : kSiteLanesFP32;
+  o.n_batches = n_active;  // every active cycle is one statistical batch
+  const int nb = n_active;
+  uint64_t cap = o.bank_capacity;
+  if (cap == 0) {
+    cap = 1ull << 16;
+    while (cap < 2 * N && cap < (1ull << 22)) cap <<= 1;
+  }
+  if (cap < 1024) return fail(MC_ERR_INVALID, "bank_capacity must be >= 1024");
+  const size_t bank_bytes = (size_t)cap * 16 * lanes;
+  rc = p->d_banks.ensure(4 * bank_bytes, p->dev);
+  if (rc != MC_OK) return rc;
+  const uint64_t bins = (uint64_t)p->total_bins, row = p->row;
+  uint32_t stripes = o.tally_stripes > 0 ? (uint32_t)o.tally_stripes : 1u;
+  if (o.tally_stripes <= 0) {
+    const double copy_bytes = (double)nb * (double)row * 8.0;
+    stripes = (uint32_t)std::max(1.0, std::min(16.0, std::floor(64.0 * 1048576.0 / copy_bytes)));
+  }
+  if ((double)stripes * nb * (double)row >= 4294967296.0)
+    return fail(MC_ERR_INVALID, "tally bins x active cycles x stripes must stay below 2^32");
+  rc = p->d_tally.ensure((size_t)stripes * nb * row * 8, p->dev);
+  if (rc == MC_OK) rc = p->d_stats.ensure((size_t)3 * bins * 8, p->dev);
+  if (rc == MC_OK) rc = p->d_counts.ensure((size_t)N * 4, p->dev);
+  if (rc == MC_OK) rc = p->d_scan.ensure((size_t)N * 8, p->dev);
+  if (rc == MC_OK) rc = p->d_blocksums.ensure((size_t)((N + 1023) / 1024) * 8, p->dev);
+  if (rc == MC_OK) rc = p->d_src.ensure((size_t)N * 16 * slanes, p->dev);
+  if (rc == MC_OK) rc = p->d_trace.ensure((size_t)3 * kTraceCap * 8, p->dev);
+  if (rc != MC_OK) return rc;
+  uint64_t log_cap = 0;
+  if (o.log_count > 0) {
+    log_cap = o.log_capacity ? o.log_capacity : 64 * o.log_count * (uint64_t)n_cycles;
+    rc = p->d_log.ensure(log_cap * sizeof(mc_event), p->dev);
+    if (rc != MC_OK) return rc;
+    CK(cudaMemsetAsync(p->d_log.ptr, 0, log_cap * sizeof(mc_event), s));
+  }
+  const int block = o.block_size ? o.block_size : 256;
+  const size_t smem = p->blob[fp64].size() + (size_t)(block / 32) * (64 * 16 * lanes + 128 * 12);
+  const bool range = p->range;
+  const bool wide = o.blocks_per_sm == 2 || (o.blocks_per_sm == 0 && range);
+  int per_sm = 0;
+  CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm, wide, range)
+          : transport_occupancy<float>(block, smem, &per_sm, wide, range));
+  if (per_sm < 1) return fail(MC_ERR_CUDA, "transport kernel does not fit on an SM (block %d, smem %zu)", block, smem);
+  if (o.blocks_per_sm > 0) per_sm = std::min(per_sm, std::max(1, o.blocks_per_sm * 256 / block));
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->dev));
+  const int grid = sms * per_sm;
+  CK(cudaMemsetAsync(p->d_tally.ptr, 0, (size_t)stripes * nb * row * 8, s));
+  std::vector<double> ks(n_cycles);
+  std::vector<unsigned long long> counters(MC_NCOUNTERS, 0ull);
+  unsigned long long log_n = 0, iterations = 0;
+  double k_prev = 1.0;
+  CK(cudaEventRecord(p->ev[0], s));
+  for (int c = 0; c < n_cycles; ++c) {
+    const double nm = std::floor(p->nu_max / k_prev * (1.0 + 1e-9)) + 2.0;
+    if (!(nm <= 64.0)) return fail(MC_ERR_INVALID, "cycle %d: k = %g leaves more than 64 sites per history", c, k_prev);
+    const uint32_t nmax = (uint32_t)nm;
+    rc = p->d_sites.ensure((size_t)N * nmax * 16 * slanes, p->dev);
+    if (rc != MC_OK) return rc;
+    RunParams P;
+    std::memset(&P, 0, sizeof(P));
+    char* banks = (char*)p->d_banks.ptr;
+    for (int side = 0; side < 2; ++side)
+      for (int l = 0; l < lanes; ++l) {
+        P.S[side][l] = (uint4*)(banks + (size_t)side * bank_bytes + (size_t)l * cap * 16);
+        P.B[side][l] = (uint4*)(banks + (size_t)(2 + side) * bank_bytes + (size_t)l * cap * 16);
+      }
+    P.cap_s = cap;
+    P.cap_b = cap;
+    fill_run_params(p, o, N, seed, stripes, P);
+    P.history_mode = o.algorithm == MC_ALG_HISTORY;
+    P.trace = (unsigned long long*)p->d_trace.ptr;
+    P.trace_cap = kTraceCap;
+    P.h_first = 0;
+    P.spin_limit = 1ull << 22;
+    P.log = o.log_count ? (mc_event*)p->d_log.ptr : nullptr;
+    P.log_cap = log_cap;
+    P.log_first = o.log_first;
+    P.log_count = o.log_count;
+    P.drain_threshold = o.drain_threshold ? o.drain_threshold : (uint64_t)2 * grid * block;
+    P.eigen = 1;
+    P.eigen_score = c >= n_inactive;
+    P.cycle = (uint32_t)c;
+    P.batch_fixed = c >= n_inactive ? (uint32_t)(c - n_inactive) : 0u;
+    P.nmax = nmax;
+    P.inv_k = 1.0 / k_prev;
+    P.src_site = (const uint4*)p->d_src.ptr;
+    P.site_next = (uint4*)p->d_sites.ptr;
+    P.count_next = (uint32_t*)p->d_counts.ptr;
+    CK(cudaMemsetAsync(p->d_ctl.ptr, 0, sizeof(Ctl), s));
+    CK(cudaMemcpyAsync((char*)p->d_ctl.ptr + offsetof(Ctl, log_n), &log_n, sizeof(log_n), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(p->d_counts.ptr, 0, (size_t)N * 4, s));
+    CK(fp64 ? launch_transport<double>(P, grid, block, smem, s, wide, range)
+            : launch_transport<float>(P, grid, block, smem, s, wide, range));
+    CK(launch_scan_sites((const uint32_t*)p->d_counts.ptr, (unsigned long long*)p->d_scan.ptr,
+                         (unsigned long long*)p->d_blocksums.ptr, N, s));
+    CK(launch_comb((const uint32_t*)p->d_counts.ptr, (const unsigned long long*)p->d_scan.ptr,
+                   (const uint4*)p->d_sites.ptr, nmax, N, seed, (uint32_t)(c + 1), (uint4*)p->d_src.ptr, slanes, s));
+    Ctl ctl;
+    unsigned long long M = 0;
+    CK(cudaMemcpyAsync(&ctl, p->d_ctl.ptr, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&M, (const char*)p->d_scan.ptr + (N - 1) * 8, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int sticky = 0;
+    CK(cudaMemcpy(&sticky, p->d_sticky.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (ctl.status != 0 || sticky != 0) {
+      CK(cudaMemset(p->d_sticky.ptr, 0, 16));
+      const int st = ctl.status ? ctl.status : sticky;
+      p->last_status = st;
+      return fail(st == MC_ERR_BANK_FULL || st == MC_ERR_TIMEOUT || st == MC_ERR_LOST ? st : MC_ERR_CUDA,
+                  "cycle %d: device status %d", c, st);
+    }
+    for (int i = 0; i < MC_NCOUNTERS; ++i) counters[i] += ctl.counters[i];
+    iterations += ctl.iterations;
+    log_n = ctl.log_n;
+    ks[c] = (double)(long long)ctl.k_acc / 4294967296.0 / (double)N;
+    if (k_cycle) k_cycle[c] = ks[c];
+    if (sites_cycle) sites_cycle[c] = M;
+    if (M == 0) return fail(MC_ERR_STATE, "cycle %d banked no fission site", c);
+    if (!(ks[c] > 0.0)) return fail(MC_ERR_STATE, "cycle %d: k estimate %g", c, ks[c]);
+    k_prev = ks[c];
+  }
+  CK(cudaEventRecord(p->ev[1], s));
+  // the run's counters over all cycles, where mc_counters_get reads them
+  {
+    Ctl ctl;
+    std::memset(&ctl, 0, sizeof(ctl));
+    for (int i = 0; i < MC_NCOUNTERS; ++i) ctl.counters[i] = counters[i];
+    ctl.iterations = iterations;
+    ctl.log_n = log_n;
+    CK(cudaMemcpyAsync(p->d_ctl.ptr, &ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  if (p->range)
+    CK(launch_reconstruct(p->d_tally.ptr, (const char*)p->d_blob[1].ptr, p->range_rows, row, nb, (int)stripes,
+                          o.tally_mode == MC_TALLY_FP64, s));
+  CK(launch_batch_stats(p->d_tally.ptr, o.tally_mode == MC_TALLY_FP64, bins, row, nb, (int)stripes, N * (uint64_t)nb,
+                        p->d_stats.ptr, s));
+  CK(cudaEventRecord(p->ev[2], s));
+  double km = 0.0, kv = 0.0;
+  for (int c = n_inactive; c < n_cycles; ++c) km += ks[c];
+  km /= n_active;
+  for (int c = n_inactive; c < n_cycles; ++c) kv += (ks[c] - km) * (ks[c] - km);
+  if (k_mean) *k_mean = km;
+  if (k_std_err) *k_std_err = std::sqrt(kv / (n_active - 1) / n_active);
+  p->has_run = 1;
+  p->batched = 0;
+  p->n_hist = N * (uint64_t)nb;
+  p->n_batches = nb;
+  p->stream = s;
+  p->log_cap = log_cap;
+  p->last_status = MC_OK;
+  p->tally_fp64 = o.tally_mode == MC_TALLY_FP64;
+  p->stripes = stripes;
+  p->fixed_scale = std::ldexp(1.0, o.fixed_bits);
   return MC_OK;
 }
 

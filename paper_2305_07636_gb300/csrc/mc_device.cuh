@@ -81,6 +81,11 @@ __device__ __forceinline__ double rinf<double>() { return CUDART_INF; }
 __device__ __forceinline__ float rdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double rdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float rlog(float u) { return __logf(u); }
+// a * b and a + b rounded separately (never contracted into one FMA), as the oracle computes them
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double rlog(double u) { return log(u); }
 __device__ __forceinline__ float rsqrt_(float v) { return sqrtf(v); }
 __device__ __forceinline__ double rsqrt_(double v) { return sqrt(v); }
@@ -92,7 +97,7 @@ __device__ __forceinline__ void sincos2pi(double u, double* s, double* c) { sinc
 template <typename R>
 struct Tab {
   const TableHeader* h;
-  const R *st, *ss, *ssf, *nu, *v, *inv_v, *scdf, *chi, *src_cdf, *scoef;
+  const R *st, *ss, *ssf, *nu, *nusf, *v, *inv_v, *scdf, *chi, *src_cdf, *scoef;
   const int *skind, *sbc, *nhs, *hs, *cmat, *lpin;
   R lx0, ly0, lp, lr;
   int G;
@@ -102,6 +107,7 @@ struct Tab {
     ss = reinterpret_cast<const R*>(base + h->o_ss);
     ssf = reinterpret_cast<const R*>(base + h->o_ssf);
     nu = reinterpret_cast<const R*>(base + h->o_nu);
+    nusf = reinterpret_cast<const R*>(base + h->o_nusf);
     v = reinterpret_cast<const R*>(base + h->o_v);
     inv_v = reinterpret_cast<const R*>(base + h->o_inv_v);
     scdf = reinterpret_cast<const R*>(base + h->o_scdf);
@@ -137,6 +143,7 @@ struct Part<float> {
   double w;
   uint32_t tlo, thi, k, pk, elem, root;
   __device__ __forceinline__ float time() const { return th + tl; }
+  __device__ __forceinline__ void zero_time() { th = tl = 0.0f; }
   __device__ __forceinline__ double time_d() const { return (double)th + (double)tl; }
   __device__ __forceinline__ void advance(float l, float v, float inv_v) {
     const float b = __fmul_rn(l, inv_v);
@@ -160,6 +167,7 @@ struct Part<double> {
   double w;
   uint32_t tlo, thi, k, pk, elem, root;
   __device__ __forceinline__ double time() const { return t; }
+  __device__ __forceinline__ void zero_time() { t = 0.0; }
   __device__ __forceinline__ double time_d() const { return t; }
   __device__ __forceinline__ void advance(double l, double v, double) { t += l / v; }
   __device__ __forceinline__ double census_distance(double tc, double, double v) const {
@@ -255,6 +263,32 @@ __device__ __forceinline__ void queue_store(const Part<R>& p, uint4* q, unsigned
   Lanes<R>::pack(p, v);
 #pragma unroll
   for (int l = 0; l < Lanes<R>::N; ++l) q[l * cap + i] = v[l];
+}
+
+// Fission sites of a k-eigenvalue cycle (position and group): FP32 one 16-byte vector (x, y, z, g),
+// FP64 two ((x, y), (z, g)), at index i of a site array
+__device__ __forceinline__ void site_store(uint4* a, uint64_t i, float x, float y, float z, int g) {
+  a[i] = make_uint4(__float_as_uint(x), __float_as_uint(y), __float_as_uint(z), (uint32_t)g);
+}
+__device__ __forceinline__ void site_store(uint4* a, uint64_t i, double x, double y, double z, int g) {
+  const unsigned long long bx = (unsigned long long)__double_as_longlong(x), by = (unsigned long long)__double_as_longlong(y),
+                           bz = (unsigned long long)__double_as_longlong(z);
+  a[2 * i] = make_uint4((uint32_t)bx, (uint32_t)(bx >> 32), (uint32_t)by, (uint32_t)(by >> 32));
+  a[2 * i + 1] = make_uint4((uint32_t)bz, (uint32_t)(bz >> 32), (uint32_t)g, 0u);
+}
+__device__ __forceinline__ void site_load(const uint4* a, uint64_t i, float& x, float& y, float& z, int& g) {
+  const uint4 v = __ldcg(a + i);
+  x = __uint_as_float(v.x);
+  y = __uint_as_float(v.y);
+  z = __uint_as_float(v.z);
+  g = (int)v.w;
+}
+__device__ __forceinline__ void site_load(const uint4* a, uint64_t i, double& x, double& y, double& z, int& g) {
+  const uint4 v = __ldcg(a + 2 * i), w = __ldcg(a + 2 * i + 1);
+  x = __longlong_as_double((long long)(((unsigned long long)v.y << 32) | v.x));
+  y = __longlong_as_double((long long)(((unsigned long long)v.w << 32) | v.z));
+  z = __longlong_as_double((long long)(((unsigned long long)w.y << 32) | w.x));
+  g = (int)w.z;
 }
 
 // Round-to-nearest double -> float on the integer pipes (positive normal weights; smaller

@@ -203,6 +203,27 @@ __device__ bool do_collision(const RunParams& P, const Tab<R>& T, Part<R>& p, ui
     }
     return weight_window(P, T, p, Bout, bcount, bc);
   }
+  if (chan == CHAN_PRODUCTION && P.eigen) {
+    // k-eigenvalue cycle: floor(nu / k + xi) fission sites for the next cycle, banked in this
+    // history's own slots (so their order does not depend on the schedule), groups from chi
+    bump(bc, MC_C_PRODUCTION);
+    const R u = draw<R>(P.seed, p.tlo, p.thi, p.k, 3).a;
+    int n = (int)floor(radd(rmul(T.nu[m * G + g], (R)P.inv_k), u));
+    if (n > (int)P.nmax) {
+      set_status(P, MC_ERR_BANK_FULL);  // cannot happen: nmax covers nu_max / k + 1
+      n = (int)P.nmax;
+    }
+    for (int j = 0; j < n; ++j) {
+      const uint2 t = child_tag(P.seed, p.tlo, p.thi, p.k, (uint32_t)j, kChildMark);
+      const Pair2<R> c2 = draw<R>(P.seed, t.x, t.y, kSourceEvent, 2);
+      const int cg = sample_cdf(T.chi + m * G, G, c2.b);
+      site_store(P.site_next, (uint64_t)p.root * P.nmax + (uint64_t)j, p.x, p.y, p.z, cg);
+    }
+    P.count_next[p.root] = (uint32_t)n;
+    if (n > 0) bump(bc, MC_C_SECONDARY, (unsigned)n);
+    log_event(P, T, p, 0, 1, n);
+    return false;
+  }
   if (chan == CHAN_PRODUCTION) {
     bump(bc, MC_C_PRODUCTION);
     const R u = draw<R>(P.seed, p.tlo, p.thi, p.k, 3).a;
@@ -240,7 +261,7 @@ __device__ bool do_surface(const RunParams& P, const Tab<R>& T, Part<R>& p, uint
     const int s = (int)pk_surf(p.pk);
     const int bcnd = T.sbc[s];
     if (bcnd == MC_BC_VACUUM) {
-      Scorer<R>(P, p.w)(batch_base + (uint64_t)(T.h->leak_offset + s), R(1));
+      if (!P.eigen || P.eigen_score) Scorer<R>(P, p.w)(batch_base + (uint64_t)(T.h->leak_offset + s), R(1));
       bump(bc, MC_C_LEAK);
       log_event(P, T, p, 1, 2, 0);
       return false;
@@ -381,9 +402,46 @@ __device__ __forceinline__ uint32_t batch_of(const RunParams& P, uint64_t h) {
   return q;
 }
 
+// k-eigenvalue: the flight's contribution w l nu Sigma_f to the track-length estimate of k, in fixed
+// point at 2^-32 (products rounded as the oracle rounds them, then to the nearest integer)
+__device__ __forceinline__ long long eigen_tl_fixed(const Tab<float>& T, const Part<float>& p, float l) {
+  const float nusf = T.nusf[material_of(T, p.pk, p.elem) * T.G + (int)pk_g(p.pk)];
+  return float_to_fixed(__fmul_rn(__fmul_rn(__fmul_rn(weight_to_float(p.w), l), nusf), 4294967296.0f));
+}
+__device__ __forceinline__ long long eigen_tl_fixed(const Tab<double>& T, const Part<double>& p, double l) {
+  const double nusf = T.nusf[material_of(T, p.pk, p.elem) * T.G + (int)pk_g(p.pk)];
+  return __double2ll_rn(__dmul_rn(__dmul_rn(__dmul_rn(p.w, l), nusf), 4294967296.0));
+}
+
+// Source particle of history h of a k-eigenvalue cycle >= 1: at its fission site (picked by the
+// systematic sampling of the previous cycle's bank), isotropic from its source draws (blocks 1, 2),
+// the site's group, t = 0, weight 1, tag (h, cycle)
+template <typename R>
+__device__ bool make_site_source(const RunParams& P, const Tab<R>& T, uint64_t h, Part<R>& p) {
+  const uint32_t tlo = (uint32_t)h, thi = P.cycle;
+  const Pair2<R> b1 = draw<R>(P.seed, tlo, thi, kSourceEvent, 1);
+  const Pair2<R> b2 = draw<R>(P.seed, tlo, thi, kSourceEvent, 2);
+  int g = 0;
+  site_load(P.src_site, h, p.x, p.y, p.z, g);
+  iso_dir(R(2) * b1.b - R(1), b2.a, p.ux, p.uy, p.uz);
+  p.zero_time();
+  p.w = 1.0;
+  p.tlo = tlo;
+  p.thi = thi;
+  p.k = 0;
+  p.root = (uint32_t)h;
+  p.elem = P.batch_fixed << 16;
+  const int c = locate_cell(T, p.x, p.y, p.z, -1, 0);
+  p.pk = pk_make((uint32_t)g, (uint32_t)(c < 0 ? 0 : c), 0u);
+  if (c < 0) return false;
+  if (T.cmat[c] < 0) lattice_locate(T, p);
+  return true;
+}
+
 // Source particle of history h (event index kSourceEvent, blocks 0..3)
 template <typename R>
 __device__ bool make_source(const RunParams& P, const Tab<R>& T, uint64_t h, Part<R>& p) {
+  if (P.eigen && P.cycle > 0) return make_site_source(P, T, h, p);
   const TableHeader* H = T.h;
   const uint32_t tlo = (uint32_t)h, thi = (uint32_t)(h >> 32);
   const Pair2<R> b0 = draw<R>(P.seed, tlo, thi, kSourceEvent, 0);
@@ -413,7 +471,7 @@ __device__ bool make_source(const RunParams& P, const Tab<R>& T, uint64_t h, Par
   p.thi = thi;
   p.k = 0;
   p.root = (uint32_t)h;
-  p.elem = batch_of(P, h) << 16;
+  p.elem = (P.eigen ? P.batch_fixed : batch_of(P, h)) << 16;
   const int c = locate_cell(T, p.x, p.y, p.z, -1, 0);
   p.pk = pk_make((uint32_t)g, (uint32_t)(c < 0 ? 0 : c), 0u);
   if (c < 0) return false;

@@ -102,4 +102,8 @@ struct mc_problem {
   double src_center[3] = {0.0, 0.0, 0.0};  // reference point of the source (box centre / surface point)
   int src_group = 0;                        // the source's most likely group
   mcgb::DevBuf d_ww;
+  // k-eigenvalue cycles: fission sites [N][nmax], sites per history, their scan and block totals,
+  // the next cycle's sources [N]; the last run's per-cycle k and its active-cycle mean and error
+  mcgb::DevBuf d_sites, d_counts, d_scan, d_blocksums, d_src;
+  double nu_max = 0.0;
 };

@@ -86,7 +86,7 @@ struct TableHeader {
   int o_src_cdf, o_skind, o_sbc, o_scoef;  // [G] Real; [n_surf] int; [n_surf] int; [n_surf][4] Real
   int o_nhs, o_hs, o_cmat, o_lpin;    // [n_cell] int; [n_cell][16] int (surf | sense<<16); [n_cell] int; [ny*nx] int
   TallyDesc tally[kMaxTallies];
-  int blob_bytes, pad2, pad3, pad4;
+  int blob_bytes, o_nusf, pad3, pad4;  // o_nusf: [M][G] Real nu Sigma_f (k-eigenvalue estimator)
 };
 
 // Factor that turns a bin's accumulated score into the tally value: v_g for a time-crossing bin
@@ -115,6 +115,7 @@ struct Ctl {
   unsigned long long log_n;
   unsigned long long iterations;
   unsigned long long t_start, t_end;  // %globaltimer at kernel start / end (ns)
+  unsigned long long k_acc;           // k-eigenvalue cycle: sum of fixed(w l nu Sigma_f 2^32)
 };
 
 struct RunParams {
@@ -153,6 +154,20 @@ struct RunParams {
   int ww_split_max;
   int implicit;            // implicit capture with a weight-cutoff roulette
   double wr_cutoff, wr_survival;
+  // k-eigenvalue cycle (eigen = 1): sources come from src_site[h] (cycle >= 1), production banks
+  // floor(nu inv_k + xi) fission sites at site_next[h * nmax + j] with count_next[h], every flight
+  // adds fixed(w l nu Sigma_f) to Ctl::k_acc, tallies are scored only when eigen_score, into batch
+  // row batch_fixed; particle tags are (h, cycle)
+  int eigen, eigen_score;
+  uint32_t cycle, batch_fixed;
+  uint32_t nmax, pad_e;
+  double inv_k;
+  const uint4* src_site;   // [N] sites of this cycle's sources (cycle >= 1)
+  uint4* site_next;        // [N * nmax] sites banked this cycle
+  uint32_t* count_next;    // [N] sites banked by each history (zeroed before the cycle)
 };
+
+// fission sites: FP32 tracking 1 x 16 B (x, y, z, g), FP64 2 x 16 B ((x, y), (z, g))
+constexpr int kSiteLanesFP32 = 1, kSiteLanesFP64 = 2;
 
 }  // namespace mcgb

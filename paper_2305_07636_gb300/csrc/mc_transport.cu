@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
   Ctl* ctl = P.ctl;
   const unsigned lt = lanemask_lt();
   unsigned scored = 0;  // tally updates issued by this warp
+  long long ktl = 0;    // k-eigenvalue cycle: this thread's track-length estimate of k (fixed point)
   const uint64_t row = P.row;  // tally elements per batch: bins, then difference slots
   // small tallies are striped over several copies so that hot bins are not one L2 address
   const uint64_t stripe_off = (uint64_t)(blockIdx.x % P.tally_stripes) * P.stripe_stride;
@@ -163,7 +164,9 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
       uint32_t pend = PEND_NONE;
       Hit hit;
       const bool flies = have && flight_plan(P, T, p, &bc, l, pend, hit);
-      score_segment_warp<R, RANGE>(T, P, p, l, stripe_off + (uint64_t)(p.elem >> 16) * row, flies, stage, scored);
+      if (P.eigen && flies) ktl += eigen_tl_fixed(T, p, l);
+      score_segment_warp<R, RANGE>(T, P, p, l, stripe_off + (uint64_t)(p.elem >> 16) * row,
+                                   flies && (!P.eigen || P.eigen_score), stage, scored);
       if (flies) {
         bool alive = flight_finish(P, T, p, &bc, l, pend, hit);
         if (alive && p.k + 1 >= P.max_iter) {
@@ -212,6 +215,10 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
     }
     grid_barrier(P, ctl, P.spin_limit);
   }
+  if (P.eigen) {
+    for (int o = 16; o > 0; o >>= 1) ktl += __shfl_xor_sync(0xFFFFFFFFu, ktl, o);
+    if ((threadIdx.x & 31) == 0 && ktl) atomicAdd(&ctl->k_acc, (unsigned long long)ktl);
+  }
   if ((threadIdx.x & 31) == 0 && scored) atomicAdd(&bc.c[MC_C_SCORES], scored);
   __syncthreads();
   if (threadIdx.x < MC_NCOUNTERS && bc.c[threadIdx.x])
@@ -243,6 +250,122 @@ __global__ void k_reconstruct(void* tally, const char* blob64, uint64_t rows, ui
   for (uint64_t wi = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wi < (uint64_t)nb * rows;
        wi += warps)
     reconstruct_warp(tally, blob64, row, nb, stripes, fp64, (int)(wi / rows), wi % rows);
+}
+
+// ------------------------------------------------------------------------------------------ k-eigenvalue
+// Inclusive scan of the sites banked per history (uint32, n entries) into uint64 offsets: per
+// block of 1024 entries (256 threads x 4), then over the block totals, then the block offsets.
+constexpr int kScanBlock = 1024;
+
+__device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long long v, unsigned long long* warp_tot,
+                                                                   unsigned long long* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0ull;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < (int)(blockDim.x >> 5)) warp_tot[lane] = w;  // inclusive warp totals
+  }
+  __syncthreads();
+  const unsigned long long before = (warp > 0 ? warp_tot[warp - 1] : 0ull) + x - v;
+  if (total) *total = warp_tot[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return before;
+}
+
+__global__ void k_scan_blocks(const uint32_t* in, unsigned long long* out, unsigned long long* block_sums, uint64_t n) {
+  __shared__ unsigned long long warp_tot[32];
+  __shared__ unsigned long long tot;
+  const uint64_t base = (uint64_t)blockIdx.x * kScanBlock + (uint64_t)threadIdx.x * 4;
+  unsigned long long v[4], s = 0;
+  for (int i = 0; i < 4; ++i) {
+    v[i] = base + i < n ? (unsigned long long)in[base + i] : 0ull;
+    s += v[i];
+  }
+  unsigned long long run = block_exclusive_scan(s, warp_tot, &tot);
+  for (int i = 0; i < 4; ++i) {
+    run += v[i];
+    if (base + i < n) out[base + i] = run;
+  }
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(unsigned long long* block_sums, uint64_t nblocks) {
+  __shared__ unsigned long long warp_tot[32];
+  __shared__ unsigned long long tot;
+  unsigned long long carry = 0;
+  for (uint64_t b0 = 0; b0 < nblocks; b0 += blockDim.x) {
+    const uint64_t b = b0 + threadIdx.x;
+    const unsigned long long v = b < nblocks ? block_sums[b] : 0ull;
+    const unsigned long long ex = block_exclusive_scan(v, warp_tot, &tot);
+    if (b < nblocks) block_sums[b] = carry + ex + v;  // inclusive
+    carry += tot;
+  }
+}
+
+__global__ void k_scan_add(unsigned long long* out, const unsigned long long* block_sums, uint64_t n) {
+  if (blockIdx.x == 0) return;
+  const unsigned long long add = block_sums[blockIdx.x - 1];
+  const uint64_t base = (uint64_t)blockIdx.x * kScanBlock;
+  for (uint64_t i = base + threadIdx.x; i < base + kScanBlock && i < n; i += blockDim.x) out[i] += add;
+}
+
+// Systematic sampling of the next cycle's N sources from the M sites banked by this cycle's N
+// histories: history h of the next cycle takes site floor((h + u0) M / N) (sites ordered by
+// producing history, then production order; u0 = the cycle's combing offset).  One thread per
+// producing history writes each of its sites to the histories that pick it: the candidates around
+// the inverse of that formula, each checked with the formula itself in FP64, so that every new
+// history gets exactly the site the formula gives it.
+template <int LANES>
+__global__ void k_comb(const uint32_t* counts, const unsigned long long* scan, const uint4* sites, uint32_t nmax,
+                       uint64_t N, uint64_t seed, uint32_t next_cycle, uint4* src) {
+  const unsigned long long M = scan[N - 1];
+  if (M == 0) return;
+  const double u0 = draw<double>(seed, 0xFFFFFFFFu, next_cycle, kSourceEvent, 4).a;
+  const double dN = (double)N, dM = (double)M;
+  for (uint64_t hp = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; hp < N; hp += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t n = counts[hp];
+    const unsigned long long o = scan[hp] - n;
+    for (uint32_t j = 0; j < n; ++j) {
+      const unsigned long long g = o + j;
+      long long lo = (long long)ceil((double)g * dN / dM - u0) - 1, hi = (long long)ceil((double)(g + 1) * dN / dM - u0);
+      if (lo < 0) lo = 0;
+      if (hi > (long long)N - 1) hi = (long long)N - 1;
+      for (long long h = lo; h <= hi; ++h) {
+        unsigned long long idx = (unsigned long long)floor(((double)h + u0) * dM / dN);
+        if (idx >= M) idx = M - 1;
+        if (idx != g) continue;
+        for (int l = 0; l < LANES; ++l) src[(uint64_t)h * LANES + l] = sites[(hp * nmax + j) * LANES + l];
+      }
+    }
+  }
+}
+
+cudaError_t launch_scan_sites(const uint32_t* counts, unsigned long long* scan, unsigned long long* block_sums, uint64_t n,
+                              cudaStream_t s) {
+  const uint64_t nblocks = (n + kScanBlock - 1) / kScanBlock;
+  k_scan_blocks<<<(unsigned)nblocks, 256, 0, s>>>(counts, scan, block_sums, n);
+  k_scan_sums<<<1, 1024, 0, s>>>(block_sums, nblocks);
+  k_scan_add<<<(unsigned)nblocks, 256, 0, s>>>(scan, block_sums, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_comb(const uint32_t* counts, const unsigned long long* scan, const uint4* sites, uint32_t nmax,
+                        uint64_t n, uint64_t seed, uint32_t next_cycle, uint4* src, int lanes, cudaStream_t s) {
+  uint64_t g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  if (lanes == 2) k_comb<2><<<(unsigned)g, 256, 0, s>>>(counts, scan, sites, nmax, n, seed, next_cycle, src);
+  else k_comb<1><<<(unsigned)g, 256, 0, s>>>(counts, scan, sites, nmax, n, seed, next_cycle, src);
+  return cudaGetLastError();
 }
 
 // L2 atomic throughput probe: 64-bit adds to pseudo-random slots of an array of `span` elements

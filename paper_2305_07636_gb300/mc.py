@@ -118,6 +118,8 @@ SIGNATURES = {
     "mc_run_opts_default": (None, [C.POINTER(mc_run_opts)]),
     "mc_problem_create": (C.c_int, [C.POINTER(mc_problem_desc), C.POINTER(C.c_void_p)]),
     "mc_run": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.POINTER(mc_run_opts), C.c_void_p]),
+    "mc_run_eigen": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, C.c_int, C.c_uint64, C.POINTER(mc_run_opts),
+                               C.c_void_p, DP, C.POINTER(C.c_uint64), DP, DP]),
     "mc_wait": (C.c_int, [C.c_void_p]),
     "mc_tally_shape": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64)]),
     "mc_tally_get": (C.c_int, [C.c_void_p, C.c_int, DP, DP, C.c_size_t]),
@@ -308,6 +310,21 @@ def run_tune(h: int, n_histories: int, seed: int, opts: mc_run_opts | None = Non
     return tuned, ms.value
 
 
+def run_eigen(h: int, n_per_cycle: int, n_inactive: int, n_active: int, seed: int,
+              opts: mc_run_opts | None = None, stream=None):
+    """mc_run_eigen: k-eigenvalue power iteration; returns (k of every cycle, fission sites banked
+    per cycle, mean k over the active cycles, its standard error).  Synchronises every cycle."""
+    nc = n_inactive + n_active
+    k = np.zeros(nc)
+    sites = np.zeros(nc, np.uint64)
+    km, ke = C.c_double(0.0), C.c_double(0.0)
+    check(lib().mc_run_eigen(C.c_void_p(h), int(n_per_cycle), int(n_inactive), int(n_active),
+                             int(seed) & (2**64 - 1), C.byref(opts) if opts is not None else None,
+                             C.c_void_p(_stream_handle(stream)), k.ctypes.data_as(DP),
+                             sites.ctypes.data_as(C.POINTER(C.c_uint64)), C.byref(km), C.byref(ke)))
+    return k, sites, km.value, ke.value
+
+
 def wait(h: int):
     check(lib().mc_wait(C.c_void_p(h)))
 
@@ -463,6 +480,10 @@ class Problem:
         self.opts = run_opts(**opts)
         run(self.h, n_histories, seed, self.opts, stream)
         return self
+
+    def run_eigen(self, n_per_cycle, n_inactive, n_active, seed=1, stream=None, **opts):
+        self.opts = run_opts(**opts)
+        return run_eigen(self.h, n_per_cycle, n_inactive, n_active, seed, self.opts, stream)
 
     def wait(self):
         wait(self.h)
