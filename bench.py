@@ -92,6 +92,10 @@ def workload(name):
         return P.config4(), 1_000_000, ("config4: 200 cm stack of 40 layers (4 seeded materials, Sigma_t "
                                         "0.5-3, c 0.3-0.95), 7 groups, cosine surface source at x=0, "
                                         "detector 198-200 cm; learned weight windows")
+    if name == "eigen":
+        return P.pin_cell(), 1_000_000, ("eigen: k-eigenvalue power iteration of a 7-group pin cell (pin r 0.54 cm, "
+                                        "pitch 1.26 cm, reflective; seeded cross sections), 50 inactive + 100 "
+                                        "active cycles of 1e6 histories")
     if name == "config5":
         probs, nh = P.config5()
         return (probs, nh), sum(nh), (f"config5: {len(probs)} independent problems (1D/2D slab, "
@@ -448,6 +452,80 @@ def timed_fom(torch, mc, p, n, seed, stream, **opts):
             "histories_per_s": n / t}
 
 
+EIGEN_CYCLES = (50, 100)  # inactive, active: the paper's C5G7 k-eigenvalue run
+
+
+def bench_eigen(args, torch, mc, prob, n, desc):
+    """One step = one whole power iteration (50 inactive + 100 active cycles of n histories, as the
+    paper's k-eigenvalue run) through mc_run_eigen, timed with CUDA events around the call (it
+    synchronises once per cycle to read k).  value = histories of all cycles / time."""
+    ni, na = EIGEN_CYCLES
+    p = mc.Problem(prob)
+    stream = torch.cuda.current_stream()
+    for w in range(args.warmup):
+        mc.run_eigen(p.h, n, 2, 2, 1000 + w, None, stream)
+    clocks = Clocks(0)
+    times, ks = [], []
+    for k in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        kc, sites, km, ke = mc.run_eigen(p.h, n, ni, na, 7 + k, None, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b) / 1000.0)
+        ks.append((km, ke))
+    clk = clocks.stop()
+    c = p.counters()
+    tr_ms, st_ms = p.timing()
+    t = sum(times) / len(times)
+    hist = n * (ni + na)
+    value = hist / t
+    km, ke = ks[-1]
+    fom = 1.0 / ((ke / km) ** 2 * t)
+    peak, peak_kind = peaks()
+    achieved = c["flight"] * BYTES_PER_FLIGHT / t / 1e9
+    # end to end: create the problem (tables host->device), iterate, read the tallies back
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    q = mc.Problem(prob)
+    mc.run_eigen(q.h, n, ni, na, 99, None, stream)
+    mean, err = q.tally(0)
+    h2d = q.table_bytes()
+    q.close()
+    e2e = hist / (time.perf_counter() - t0)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * t, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "histories_per_cycle": n, "cycles": {"inactive": ni, "active": na},
+                   "tracking": "fp32", "tally": "int64 fixed point 2^-32"},
+        "k": {"mean": km, "std_err": ke, "fom_1_per_s": fom,
+              "paper_context": "MC/DC 2563.8 s (incl. ~63 s JIT) and Shift 1020.7 s for 1e5 x 150 cycles of the "
+                               "C5G7 UO2 pin cell on LLNL Lassen (IBM POWER9), i.e. ~6.0e3 and ~1.47e4 "
+                               "source particles/s"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_transport<float>", "peak_kind": peak_kind,
+                     "note": "algorithmic bytes over the whole iteration time (per-cycle syncs included)"},
+        "counters": {k: c[k] for k in ("flight", "collision", "production", "secondary")},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 3 * 8 * mean.size},
+        "gpu_launches": (ni + na) * 5 + 2,
+        "clocks": clk,
+        "step_s": [round(x, 4) for x in times],
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        threads = os.cpu_count() or 1
+        ns = 20000
+        t0 = time.perf_counter()
+        oracle.run_eigen(prob, ns, 5, 10, seed=5, threads=threads)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": ns * 15 / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"{ns} histories x 15 cycles, FP64 C++ oracle"}
+    print(json.dumps(line), flush=True)
+    p.close()
+
+
 def bench_learned_ww(args, torch, mc):
     """Learned weight windows on the 200 cm stack: 5 refinement rounds from an analog start,
     then a measurement run with the final windows; analog and an exponential (non-learned) window
@@ -571,6 +649,10 @@ def main():
         if world > 1:
             raise SystemExit("the batched workload runs on one GPU")
         return bench_batch(args, torch, mc, prob, n, desc, world, local)
+    if args.workload == "eigen":
+        if world > 1:
+            raise SystemExit("the k-eigenvalue workload runs on one GPU")
+        return bench_eigen(args, torch, mc, prob, args.histories or n, desc)
     if args.histories:
         n = args.histories
     seed = 2
