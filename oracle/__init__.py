@@ -22,9 +22,10 @@ _lock = threading.Lock()
 _lib = None
 
 MAX_HS = 16
-NCOUNT = 14
+NCOUNT = 16
 COUNTER_NAMES = ["source", "secondary", "capture", "production", "leak", "census", "lost",
-                 "flight", "collision", "scatter", "surface", "reflect", "ww_split", "ww_kill"]
+                 "flight", "collision", "scatter", "surface", "reflect", "ww_split", "ww_kill",
+                 "pc_banked", "pc_copies"]
 KIND = {"PX": 0, "PY": 1, "PZ": 2, "CZ": 3}
 BC = {"interior": 0, "vacuum": 1, "reflect": 2}
 SRC_POS = {"box": 0, "surface_x0": 1}
@@ -104,6 +105,19 @@ class OrEigenResult(C.Structure):
                 ("tally_cycle", C.POINTER(C.c_double)), ("counters", C.c_int64 * NCOUNT)]
 
 
+class OrPcOpts(C.Structure):
+    _fields_ = [("n_histories", C.c_uint64), ("seed", C.c_uint64), ("n_batches", C.c_int),
+                ("threads", C.c_int), ("n_census", C.c_int), ("census_times", C.POINTER(C.c_double)),
+                ("log_first", C.c_uint64), ("log_count", C.c_uint64),
+                ("log", C.POINTER(OrEvent)), ("log_cap", C.c_uint64),
+                ("log_n", C.POINTER(C.c_uint64))]
+
+
+class OrPcResult(C.Structure):
+    _fields_ = [("tally_batch", C.POINTER(C.c_double)), ("banked", C.POINTER(C.c_uint64)),
+                ("counters", C.c_int64 * NCOUNT)]
+
+
 class OrResult(C.Structure):
     _fields_ = [("s1", C.POINTER(C.c_double)), ("s2", C.POINTER(C.c_double)),
                 ("fixed", C.POINTER(C.c_int64)), ("counters", C.c_int64 * NCOUNT)]
@@ -119,6 +133,8 @@ def lib():
             L.or_run_eigen.argtypes = [C.POINTER(OrProblem), C.POINTER(OrEigenOpts),
                                        C.POINTER(OrEigenResult)]
             L.or_run_eigen.restype = C.c_int
+            L.or_run_pc.argtypes = [C.POINTER(OrProblem), C.POINTER(OrPcOpts), C.POINTER(OrPcResult)]
+            L.or_run_pc.restype = C.c_int
             L.or_total_bins.argtypes = [C.POINTER(OrProblem)]
             L.or_total_bins.restype = C.c_int
             L.or_philox.argtypes = [C.c_uint32, C.c_uint32, C.POINTER(C.c_uint32),
@@ -376,6 +392,57 @@ def run_eigen(prob: dict, n: int, n_inactive: int, n_active: int, seed: int = 1,
         raise RuntimeError(f"or_run_eigen failed: {rc}")
     ev = events_to_numpy(events, int(log_n.value)) if events is not None else None
     return EigenResult(m.tally_shapes, m.n_surf, k, sites, tc[:n_active], n_inactive, list(r.counters), ev)
+
+
+class BatchResult:
+    """Mean and standard error of every tally over independent batches (per source particle)."""
+
+    def __init__(self, shapes, n_surf, tb, counters, banked, events):
+        self.batch_tallies = tb
+        self.counters = dict(zip(COUNTER_NAMES, [int(c) for c in counters]))
+        self.banked = banked
+        self.events = events
+        mean = tb.mean(axis=0)
+        std = tb.std(axis=0, ddof=1) / math.sqrt(tb.shape[0])
+        self.tallies = []
+        off = 0
+        for shp in shapes:
+            size = int(np.prod(shp))
+            self.tallies.append((mean[off:off + size].reshape(shp), std[off:off + size].reshape(shp)))
+            off += size
+        self.leak_mean, self.leak_std = mean[off:off + n_surf], std[off:off + n_surf]
+
+
+def run_pc(prob: dict, n: int, census_times, n_batches: int = 32, seed: int = 1,
+           threads: int | None = None, log_first: int = 0, log_count: int = 0,
+           log_cap: int = 0) -> BatchResult:
+    """Time-dependent run with splitting-roulette population control at the interior census times
+    (see or_run_pc in oracle.h); statistics over the independent batches."""
+    L = lib()
+    m = Marshalled(prob)
+    nb = L.or_total_bins(C.byref(m.s))
+    ct = np.ascontiguousarray(census_times, dtype=np.float64)
+    tb = np.zeros((n_batches, nb))
+    banked = np.zeros(max(1, ct.size), np.uint64)
+    o = OrPcOpts()
+    o.n_histories, o.seed, o.n_batches = n, seed, n_batches
+    o.threads = threads if threads else (os.cpu_count() or 1)
+    o.n_census = ct.size
+    o.census_times = ct.ctypes.data_as(C.POINTER(C.c_double))
+    events, log_n = None, C.c_uint64(0)
+    if log_count > 0:
+        cap = log_cap if log_cap else 256 * log_count
+        events = (OrEvent * cap)()
+        o.log, o.log_cap, o.log_first, o.log_count = events, cap, log_first, log_count
+        o.log_n = C.pointer(log_n)
+    r = OrPcResult()
+    r.tally_batch = tb.ctypes.data_as(C.POINTER(C.c_double))
+    r.banked = banked.ctypes.data_as(C.POINTER(C.c_uint64))
+    rc = L.or_run_pc(C.byref(m.s), C.byref(o), C.byref(r))
+    if rc != 0:
+        raise RuntimeError(f"or_run_pc failed: {rc}")
+    ev = events_to_numpy(events, int(log_n.value)) if events is not None else None
+    return BatchResult(m.tally_shapes, m.n_surf, tb, list(r.counters), banked[:ct.size], ev)
 
 
 EVENT_DTYPE = np.dtype([("tag", np.uint64), ("root", np.uint64), ("k", np.uint32),

@@ -622,13 +622,26 @@ bool weight_window(const Prob& P, uint64_t seed, Particle& q, uint32_t k_used,
   return true;
 }
 
+// population control interval of one batch: the census time of the interval, and where particles
+// that reach an interior census are banked
+struct PcBanked {
+  Particle q;
+  uint32_t kc;  // event index of the flight that reached the census
+};
+struct Pc {
+  double t_census;
+  bool interior;
+  std::vector<PcBanked>* bank;
+};
+
 struct Logger {
   bool on;
   uint64_t first, count;
 };
 
 void transport(const Prob& P, const Physics& ph, uint64_t seed, Particle q, std::vector<Particle>& stack,
-               Acc& acc, const Logger& lg, Eig* eig = nullptr) {
+               Acc& acc, const Logger& lg, Eig* eig = nullptr, Pc* pc = nullptr) {
+  const double t_census = pc ? pc->t_census : P.t_census;
   const int G = P.G;
   while (true) {
     int m = material(P, q);
@@ -637,8 +650,8 @@ void transport(const Prob& P, const Physics& ph, uint64_t seed, Particle q, std:
     double dc = St > 0.0 ? -std::log(b0.a) / St : INF;
     Hit hit = distance_to_boundary(P, q);
     double dt = INF;
-    if (P.t_census < INF) {
-      dt = P.v[q.g] * (P.t_census - q.t);
+    if (t_census < INF) {
+      dt = P.v[q.g] * (t_census - q.t);
       if (dt < 0.0) dt = 0.0;
     }
     int ev;
@@ -690,7 +703,12 @@ void transport(const Prob& P, const Physics& ph, uint64_t seed, Particle q, std:
       acc.cnt[OR_C_LOST]++;
       alive = false;
     } else if (ev == OR_EV_CENSUS) {
-      acc.cnt[OR_C_CENSUS]++;
+      if (pc && pc->interior) {
+        pc->bank->push_back({q, k});
+        acc.cnt[OR_C_PC_BANKED]++;
+      } else {
+        acc.cnt[OR_C_CENSUS]++;
+      }
       alive = false;
     } else if (ev == OR_EV_SURFACE) {
       acc.cnt[OR_C_SURFACE]++;
@@ -824,6 +842,54 @@ void run_range(const Prob& P, const Physics& ph, uint64_t seed, uint64_t h0, uin
   }
 }
 
+// one batch of a population-controlled run (see or_run_pc): its histories [h0, h1), interval by
+// interval, with splitting-roulette of the banked particles at every interior census
+void run_pc_batch(const Prob& P, const or_pc_opts* o, uint64_t h0, uint64_t h1, Acc& acc, const Logger& lg,
+                  std::vector<uint64_t>& banked) {
+  const Physics ph{false, 0.0, 0.0};
+  const uint64_t Nb = h1 - h0;
+  std::vector<Particle> cur, stack;
+  for (uint64_t h = h0; h < h1; ++h) {
+    Particle q = source_particle(P, o->seed, h);
+    acc.cnt[OR_C_SOURCE]++;
+    if (q.cell < 0) acc.cnt[OR_C_LOST]++;
+    else cur.push_back(q);
+  }
+  for (int i = 0; i <= o->n_census; ++i) {
+    std::vector<PcBanked> bank;
+    Pc pc{i < o->n_census ? o->census_times[i] : P.t_census, i < o->n_census, &bank};
+    for (const Particle& q : cur) {
+      stack.push_back(q);
+      while (!stack.empty()) {
+        Particle c = stack.back();
+        stack.pop_back();
+        transport(P, ph, o->seed, c, stack, acc, lg, nullptr, &pc);
+      }
+    }
+    cur.clear();
+    if (!pc.interior) break;
+    banked[i] += bank.size();
+    // splitting-roulette to the batch's N_b histories: exact fixed-point total weight
+    int64_t Wq = 0;
+    for (const PcBanked& b : bank) Wq += (int64_t)std::llrint(b.q.w * 1099511627776.0);
+    if (Wq <= 0) break;
+    const double wt = (double)Wq / 1099511627776.0 / (double)Nb;
+    for (const PcBanked& b : bank) {
+      const double xi = draw(o->seed, b.q.tag, b.kc, 1).a;
+      const int n = (int)std::floor(b.q.w / wt + xi);
+      for (int j = 0; j < n; ++j) {
+        Particle c = b.q;
+        c.tag = child_tag(o->seed, b.q.tag, b.kc, (uint32_t)j, 0x40000000u);
+        c.k = 0;
+        c.t = pc.t_census;
+        c.w = wt;
+        cur.push_back(c);
+        acc.cnt[OR_C_PC_COPIES]++;
+      }
+    }
+  }
+}
+
 // k-eigenvalue power iteration (the paper's C5G7 runs, Section 3): cycle 0 starts N histories
 // from the problem's source; every later cycle starts N histories at the previous cycle's fission
 // sites, picked by systematic sampling (combing) with one random offset per cycle, so the
@@ -864,6 +930,56 @@ double comb_offset(uint64_t seed, uint32_t cycle) {
 }  // namespace
 
 extern "C" {
+
+int or_run_pc(const or_problem* p, const or_pc_opts* o, or_pc_result* r) {
+  Prob P = copy_problem(p);
+  const uint64_t N = o->n_histories;
+  const int nb = o->n_batches;
+  if (N == 0 || nb < 1 || (uint64_t)nb > N || o->n_census < 0) return -1;
+  for (int i = 0; i < o->n_census; ++i)
+    if (!(o->census_times[i] > (i ? o->census_times[i - 1] : 0.0)) || !(o->census_times[i] < P.t_census)) return -1;
+  const int bins = P.total_bins + P.n_surf;
+  std::vector<Acc> accs(nb);
+  std::vector<std::vector<uint64_t>> banked(nb, std::vector<uint64_t>(o->n_census > 0 ? o->n_census : 1, 0));
+  Logger lg{o->log != nullptr, o->log_first, o->log_count};
+  int nt = o->threads > 0 ? o->threads : 1;
+  if (nt > nb) nt = nb;
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t) {
+    th.emplace_back([&, t] {
+      for (int b = t; b < nb; b += nt) {
+        accs[b].init(bins, 32);
+        // histories of batch b: floor(h nb / N) == b
+        const uint64_t h0 = ((uint64_t)b * N + nb - 1) / nb, h1 = ((uint64_t)(b + 1) * N + nb - 1) / nb;
+        run_pc_batch(P, o, h0, h1, accs[b], lg, banked[b]);
+        accs[b].end_history();
+      }
+    });
+  }
+  for (auto& x : th) x.join();
+  for (int k = 0; k < OR_NCOUNT; ++k) {
+    r->counters[k] = 0;
+    for (int b = 0; b < nb; ++b) r->counters[k] += accs[b].cnt[k];
+  }
+  for (int b = 0; b < nb; ++b) {
+    const uint64_t h0 = ((uint64_t)b * N + nb - 1) / nb, h1 = ((uint64_t)(b + 1) * N + nb - 1) / nb;
+    if (r->tally_batch)
+      for (int i = 0; i < bins; ++i) r->tally_batch[(size_t)b * bins + i] = accs[b].s1[i] / (double)(h1 - h0);
+  }
+  if (r->banked)
+    for (int i = 0; i < o->n_census; ++i) {
+      r->banked[i] = 0;
+      for (int b = 0; b < nb; ++b) r->banked[i] += banked[b][i];
+    }
+  if (o->log) {
+    uint64_t w = 0;
+    for (int b = 0; b < nb; ++b)
+      for (const or_event& e : accs[b].log)
+        if (w < o->log_cap) o->log[w++] = e;
+    if (o->log_n) *o->log_n = w;
+  }
+  return 0;
+}
 
 int or_run_eigen(const or_problem* p, const or_eigen_opts* o, or_eigen_result* r) {
   Prob P = copy_problem(p);

@@ -49,6 +49,8 @@ enum {
   OR_C_REFLECT,         /* reflections */
   OR_C_WW_SPLIT,        /* extra particles created by weight-window splitting */
   OR_C_WW_KILL,         /* particles removed by roulette (weight windows or weight cutoff) */
+  OR_C_PC_BANKED,       /* particles stopped at an interior census (population control) */
+  OR_C_PC_COPIES,       /* particles started after an interior census by splitting-roulette */
   OR_NCOUNT
 };
 
@@ -133,6 +135,37 @@ typedef struct {
 
 int or_total_bins(const or_problem* p);
 int or_run(const or_problem* p, const or_opts* o, or_result* r);
+
+/* Time-dependent run with population control at interior census times (the paper's Section 3
+ * feature list: time census with population control).  The histories are split into n_batches
+ * contiguous batches (history h in batch floor(h nb / N)), and each batch is an independent
+ * simulation of its N_b histories.  Interval i runs from the previous census (or the source) to
+ * census_times[i] (the problem's t_census after the last one): every particle and its secondaries
+ * are transported; one reaching an interior census is banked.  Then, per batch, splitting-roulette:
+ * W_b = sum of llrint(w 2^40) over the batch's banked particles (exact), w_t = W_b 2^-40 / N_b, and a
+ * banked particle of weight w (tag T, census flight k) becomes floor(w / w_t + xi) copies, xi = the
+ * first FP64 uniform of block 1 of event k, copy j with tag child_tag(T, k, 0x40000000 | j), weight
+ * w_t, time = the census time exactly, event index 0, the same position, direction and group.  The
+ * copies start the next interval.  Tallies are returned per batch (tally_batch[b][bin], per source
+ * particle of the batch). */
+typedef struct {
+  uint64_t n_histories, seed;
+  int n_batches, threads;
+  int n_census;
+  const double* census_times;    /* [n_census], increasing, below the problem's t_census */
+  uint64_t log_first, log_count;
+  or_event* log;
+  uint64_t log_cap;
+  uint64_t* log_n;
+} or_pc_opts;
+
+typedef struct {
+  double* tally_batch;           /* [n_batches][total bins] */
+  uint64_t* banked;              /* [n_census] particles banked at each interior census (all batches) */
+  int64_t counters[OR_NCOUNT];
+} or_pc_result;
+
+int or_run_pc(const or_problem* p, const or_pc_opts* o, or_pc_result* r);
 
 /* k-eigenvalue power iteration (the paper's C5G7 runs, Section 3), analog: n_inactive + n_active
  * cycles of n_per_cycle histories.  Cycle 0 starts at the problem's source; cycle c >= 1 starts
