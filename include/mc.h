@@ -195,6 +195,19 @@ typedef struct {
   int implicit_capture;   /* 0 = analog (default), 1 = implicit capture */
   double wr_cutoff;       /* weight cutoff (default 0.25) */
   double wr_survival;     /* survival weight of the roulette (default 0.5) */
+  /* Population control at interior census times (the paper's time census with population control,
+   * Section 3), by splitting-roulette within each statistical batch, which makes every batch an
+   * independent simulation of its N_b histories.  The run is split into intervals ending at
+   * census_times[0..n_census-1] and then at the problem's t_census.  A particle reaching an interior
+   * census is banked; then per batch W_b = the sum of llrint(w 2^40) of its banked particles (exact),
+   * w_t = W_b 2^-40 / N_b, and a banked particle of weight w becomes floor(w / w_t + xi) copies of
+   * weight w_t at the census time (xi = the first FP64 uniform of block 1 of its census flight; copy
+   * j tagged as a child with mark 0x40000000 | j), which start the next interval.  The tallies'
+   * errors come from the batches.  The array is copied during the call; times must increase and lie
+   * below t_census.  mc_run synchronises once per interval.  Not for mc_run_batch / mc_run_eigen /
+   * mc_run_static. */
+  int n_census;
+  const double* census_times;
 } mc_run_opts;
 
 /* Fills the defaults listed above. */
@@ -217,11 +230,14 @@ typedef struct {
  * weight cutoff).  MC_C_WW_HELD counts weight-window splits
  * not made because the particle store was more than half full: a split is optional (the particle
  * keeps its weight, which is unbiased), so bad windows slow a run down instead of overflowing
- * it; a run with held splits is no longer independent of the GPU's schedule. */
+ * it; a run with held splits is no longer independent of the GPU's schedule.  MC_C_PC_BANKED counts
+ * particles stopped at an interior census of population control, MC_C_PC_COPIES the particles that
+ * splitting-roulette started from them. */
 typedef enum {
   MC_C_SOURCE = 0, MC_C_SECONDARY, MC_C_CAPTURE, MC_C_PRODUCTION, MC_C_LEAK, MC_C_CENSUS,
   MC_C_LOST, MC_C_FLIGHT, MC_C_COLLISION, MC_C_SCATTER, MC_C_SURFACE, MC_C_REFLECT,
-  MC_C_WW_SPLIT, MC_C_WW_KILL, MC_C_ITERATIONS, MC_C_SCORES, MC_C_WW_HELD, MC_NCOUNTERS
+  MC_C_WW_SPLIT, MC_C_WW_KILL, MC_C_ITERATIONS, MC_C_SCORES, MC_C_WW_HELD, MC_C_PC_BANKED, MC_C_PC_COPIES,
+  MC_NCOUNTERS
 } mc_counter;
 
 /* ------------------------------------------------------------------------- entry points */

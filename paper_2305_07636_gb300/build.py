@@ -28,6 +28,18 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
+# The transport translation units round every product and sum separately (no contraction into
+# FMA): the compiler's contraction choices depend on the optimisation context of each kernel
+# build, so with contraction the 80- and 128-register builds of the walk (and the batched kernel)
+# could round a geometry expression differently and move a particle differently.  Without it every
+# build computes the same bits, and the FP64 walk rounds as the CPU reference does.
+NO_FMA = {"mc_transport.cu", "mc_batch.cu", "mc_api.cu"}
+
+
+def per_file_flags(src):
+    return ["-fmad=false"] if os.path.basename(src) in NO_FMA else []
+
+
 def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
@@ -53,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     procs, objs = [], []
     for src in sources():
         obj = os.path.join(obj_dir, os.path.basename(src) + ".o")
-        cmd = [cc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *per_file_flags(src), "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

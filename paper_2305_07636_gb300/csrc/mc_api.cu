@@ -31,6 +31,9 @@ cudaError_t launch_scan_sites(const uint32_t* counts, unsigned long long* scan, 
                               cudaStream_t s);
 cudaError_t launch_comb(const uint32_t* counts, const unsigned long long* scan, const uint4* sites, uint32_t nmax,
                         uint64_t n, uint64_t seed, uint32_t next_cycle, uint4* src, int lanes, cudaStream_t s);
+template <typename R>
+cudaError_t launch_pc(const RunParams& P, const RunParams& Q, const unsigned long long* pc_n, long long* wq,
+                      unsigned long long* out_n, unsigned long long* copies, int* status, bool split, cudaStream_t s);
 cudaError_t launch_reconstruct(void* tally, const char* blob64, uint64_t rows, uint64_t row, int nb, int stripes,
                                int fp64, cudaStream_t s);
 cudaError_t launch_batch_stats(const void* tally, int fp64, uint64_t bins, uint64_t row, int nb, int stripes,
@@ -427,11 +430,22 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
 // ------------------------------------------------------------------------------------------ ABI
 namespace mcgb {
 
+// the launch's census: the problem's t_census unless population control sets an interior one
+void set_census(RunParams& P, double t, bool interior) {
+  P.has_census = std::isfinite(t) ? 1 : 0;
+  P.tc = t;
+  P.tc_hi = P.has_census ? (float)t : 0.0f;
+  P.tc_lo = P.has_census ? (float)(t - (double)P.tc_hi) : 0.0f;
+  P.pc_interior = interior ? 1 : 0;
+}
+
 void fill_run_params(const mc_problem* p, const mc_run_opts& o, uint64_t n_histories, uint64_t seed,
                      uint32_t stripes, RunParams& P) {
   const int fp64 = o.precision == MC_FP64;
   const int nb = o.n_batches;
   const uint64_t bins = (uint64_t)p->total_bins;
+  P.n_sources = n_histories;
+  set_census(P, reinterpret_cast<const TableHeader*>(p->blob[1].data())->t_census, false);
   P.ctl = (Ctl*)p->d_ctl.ptr;
   P.sticky = (int*)p->d_sticky.ptr;
   P.tally = p->d_tally.ptr;
@@ -574,6 +588,83 @@ void mc_problem_destroy(mc_problem* p) {
   delete p;
 }
 
+// Population control: one transport launch per interval between census times.  After an interior
+// census the banked particles' batch weights are summed exactly, splitting-roulette writes the
+// copies into the next launch's birth bank, and the next launch starts from them alone.  The run's
+// counters (and the event log count) are summed over the intervals on the host and written back
+// into the control block at the end.
+int run_population_controlled(mc_problem* p, const RunParams& P0, const std::vector<double>& census, double t_final,
+                              int grid, int block, size_t smem, bool wide, bool range, int fp64, int lanes,
+                              uint64_t cap, cudaStream_t s) {
+  int rc = p->d_cbank.ensure((size_t)cap * 16 * lanes, p->dev);
+  const int nb = P0.n_batches;
+  if (rc == MC_OK) rc = p->d_pc.ensure((size_t)(nb + 4) * 8, p->dev);
+  if (rc != MC_OK) return rc;
+  long long* wq = (long long*)p->d_pc.ptr;
+  unsigned long long* out_n = (unsigned long long*)(wq + nb);
+  unsigned long long* copies = out_n + 1;
+  int* status = (int*)(copies + 1);
+  std::vector<unsigned long long> cnt(MC_NCOUNTERS, 0ull);
+  unsigned long long iterations = 0, log_n = 0;
+  RunParams prev = P0;
+  const int K = (int)census.size();
+  auto harvest = [&](int* st) -> int {  // the finished launch's counters
+    Ctl c;
+    CK(cudaMemcpyAsync(&c, p->d_ctl.ptr, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < MC_NCOUNTERS; ++i) cnt[i] += c.counters[i];
+    iterations += c.iterations;
+    log_n = c.log_n;
+    *st = c.status;
+    return MC_OK;
+  };
+  for (int i = 0; i <= K; ++i) {
+    RunParams Q = P0;
+    Q.n_sources = i == 0 ? P0.n_sources : 0;
+    set_census(Q, i < K ? census[i] : t_final, i < K);
+    char* cb = (char*)p->d_cbank.ptr;
+    for (int l = 0; l < lanes; ++l) Q.C[l] = (uint4*)(cb + (size_t)l * cap * 16);
+    Q.cap_c = cap;
+    if (i > 0) {
+      CK(cudaMemsetAsync(p->d_pc.ptr, 0, (size_t)(nb + 4) * 8, s));
+      const unsigned long long* pc_n = (const unsigned long long*)((const char*)p->d_ctl.ptr + offsetof(Ctl, pc_n));
+      CK(fp64 ? launch_pc<double>(prev, Q, pc_n, wq, out_n, copies, status, false, s)
+              : launch_pc<float>(prev, Q, pc_n, wq, out_n, copies, status, false, s));
+      CK(fp64 ? launch_pc<double>(prev, Q, pc_n, wq, out_n, copies, status, true, s)
+              : launch_pc<float>(prev, Q, pc_n, wq, out_n, copies, status, true, s));
+      int st = 0;
+      rc = harvest(&st);
+      if (rc != MC_OK) return rc;
+      unsigned long long pc_state[2] = {0ull, 0ull};  // copies, status word
+      CK(cudaMemcpy(pc_state, copies, 16, cudaMemcpyDeviceToHost));
+      cnt[MC_C_PC_COPIES] += pc_state[0];
+      if (st == 0) st = (int)(pc_state[1] & 0xFFFFFFFFu);
+      if (st != 0) {
+        p->last_status = st;
+        return fail(st, "population-control interval %d: device status %d", i - 1, st);
+      }
+      CK(cudaMemsetAsync(p->d_ctl.ptr, 0, sizeof(Ctl), s));
+      CK(cudaMemcpyAsync((char*)p->d_ctl.ptr + offsetof(Ctl, log_n), &log_n, sizeof(log_n), cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync((char*)p->d_ctl.ptr + offsetof(Ctl, birth), out_n, 8, cudaMemcpyDeviceToDevice, s));
+    }
+    CK(fp64 ? launch_transport<double>(Q, grid, block, smem, s, wide, range)
+            : launch_transport<float>(Q, grid, block, smem, s, wide, range));
+    prev = Q;
+  }
+  int st = 0;
+  rc = harvest(&st);
+  if (rc != MC_OK) return rc;
+  Ctl c;
+  std::memset(&c, 0, sizeof(c));
+  for (int i = 0; i < MC_NCOUNTERS; ++i) c.counters[i] = cnt[i];
+  c.iterations = iterations;
+  c.log_n = log_n;
+  c.status = st;
+  CK(cudaMemcpyAsync(p->d_ctl.ptr, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return MC_OK;
+}
+
 int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts* opts, void* stream) {
   g_err.clear();
   if (!p) return fail(MC_ERR_INVALID, "problem is NULL");
@@ -597,6 +688,13 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   if (o.ww_enable && !p->ww_set) return fail(MC_ERR_STATE, "weight windows enabled but no table set");
   if (o.algorithm != MC_ALG_EVENT && o.algorithm != MC_ALG_HISTORY) return fail(MC_ERR_INVALID, "algorithm");
   if (check_implicit_opts(o) != MC_OK) return MC_ERR_INVALID;
+  const double t_final = reinterpret_cast<const TableHeader*>(p->blob[1].data())->t_census;
+  if (o.n_census < 0 || o.n_census > 4096 || (o.n_census > 0 && !o.census_times))
+    return fail(MC_ERR_INVALID, "n_census outside [0, 4096] or census_times NULL");
+  std::vector<double> census(o.census_times, o.census_times + std::max(0, o.n_census));
+  for (int i = 0; i < o.n_census; ++i)
+    if (!(census[i] > (i ? census[i - 1] : 0.0)) || !(census[i] < t_final))
+      return fail(MC_ERR_INVALID, "census_times must increase, be > 0 and below t_census");
   int dev;
   int rc = current_device(&dev);
   if (rc != MC_OK) return rc;
@@ -679,8 +777,13 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   const int grid = sms * per_sm;
   P.drain_threshold = o.drain_threshold ? o.drain_threshold : (uint64_t)2 * grid * block;
   CK(cudaEventRecord(p->ev[0], s));
-  CK(fp64 ? launch_transport<double>(P, grid, block, smem, s, wide, range)
-          : launch_transport<float>(P, grid, block, smem, s, wide, range));
+  if (o.n_census == 0) {
+    CK(fp64 ? launch_transport<double>(P, grid, block, smem, s, wide, range)
+            : launch_transport<float>(P, grid, block, smem, s, wide, range));
+  } else {
+    rc = run_population_controlled(p, P, census, t_final, grid, block, smem, wide, range, fp64, lanes, cap, s);
+    if (rc != MC_OK) return rc;
+  }
   CK(cudaEventRecord(p->ev[1], s));
   if (p->range)
     CK(launch_reconstruct(P.tally, (const char*)p->d_blob[1].ptr, p->range_rows, row, nb, (int)stripes, P.tally_fp64, s));
@@ -1307,6 +1410,7 @@ extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t
   if (o.algorithm != MC_ALG_EVENT && o.algorithm != MC_ALG_HISTORY) return fail(MC_ERR_INVALID, "algorithm");
   if (check_implicit_opts(o) != MC_OK) return MC_ERR_INVALID;
   if (o.log_count > 0) return fail(MC_ERR_INVALID, "mc_run_static keeps no event log");
+  if (o.n_census > 0) return fail(MC_ERR_INVALID, "mc_run_static runs no population control");
   if (o.ww_enable && !p->ww_set) return fail(MC_ERR_STATE, "weight windows enabled but no table set");
   if (o.bank_capacity > kStaticBank)
     return fail(MC_ERR_INVALID, "bank_capacity %llu exceeds the static limit of %llu particles",
@@ -1360,6 +1464,8 @@ extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t
   P.trace = nullptr;
   P.trace_cap = 0;
   P.n_hist = n_histories;
+  P.n_sources = n_histories;
+  set_census(P, reinterpret_cast<const TableHeader*>(p->blob[1].data())->t_census, false);
   P.hist_per_batch = (n_histories + nb - 1) / nb;
   P.h_first = o.first_history;
   {

@@ -265,6 +265,13 @@ __device__ __forceinline__ void queue_store(const Part<R>& p, uint4* q, unsigned
   for (int l = 0; l < Lanes<R>::N; ++l) q[l * cap + i] = v[l];
 }
 
+// the time of a particle set to the launch's census time exactly (population-control copies)
+__device__ __forceinline__ void set_census_time(Part<float>& p, const RunParams& P) {
+  p.th = P.tc_hi;
+  p.tl = P.tc_lo;
+}
+__device__ __forceinline__ void set_census_time(Part<double>& p, const RunParams& P) { p.t = P.tc; }
+
 // Fission sites of a k-eigenvalue cycle (position and group): FP32 one 16-byte vector (x, y, z, g),
 // FP64 two ((x, y), (z, g)), at index i of a site array
 __device__ __forceinline__ void site_store(uint4* a, uint64_t i, float x, float y, float z, int g) {

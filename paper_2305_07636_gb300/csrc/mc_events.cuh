@@ -317,9 +317,9 @@ __device__ bool flight_plan(const RunParams& P, const Tab<R>& T, Part<R>& p, Blo
   const R dc = St > R(0) ? rdiv(-rlog(b0.a), St) : rinf<R>();
   const R ds = boundary_distance(T, p, hit);
   R dt = rinf<R>();
-  if (T.h->has_census) {
-    const R d = sizeof(R) == 4 ? (R)p.census_distance((R)T.h->tc_hi, (R)T.h->tc_lo, T.v[g])
-                               : (R)p.census_distance((R)T.h->t_census, R(0), T.v[g]);
+  if (P.has_census) {
+    const R d = sizeof(R) == 4 ? (R)p.census_distance((R)P.tc_hi, (R)P.tc_lo, T.v[g])
+                               : (R)p.census_distance((R)P.tc, R(0), T.v[g]);
     dt = d > R(0) ? d : R(0);
   }
   bump(bc, MC_C_FLIGHT);
@@ -354,8 +354,16 @@ __device__ bool flight_finish(const RunParams& P, const Tab<R>& T, Part<R>& p, B
   p.z += l * p.uz;
   p.advance(l, T.v[g], T.inv_v[g]);
   if (pend == PEND_NONE) {
-    bump(bc, MC_C_CENSUS);
     log_event(P, T, p, 2, 0, 0);
+    if (P.pc_interior) {
+      // interior census of population control: bank the particle (event index = its census flight)
+      const unsigned long long i = atomicAdd(&P.ctl->pc_n, 1ull);
+      if (i < P.cap_c) bank_store(p, P.C, i);
+      else set_status(P, MC_ERR_BANK_FULL);
+      bump(bc, MC_C_PC_BANKED);
+    } else {
+      bump(bc, MC_C_CENSUS);
+    }
     return false;
   }
   if (pend == PEND_COLL && hit.chan == CHAN_CAPTURE) {

@@ -105,5 +105,7 @@ struct mc_problem {
   // k-eigenvalue cycles: fission sites [N][nmax], sites per history, their scan and block totals,
   // the next cycle's sources [N]; the last run's per-cycle k and its active-cycle mean and error
   mcgb::DevBuf d_sites, d_counts, d_scan, d_blocksums, d_src;
+  // population control: the census bank, per-batch weights and split counters
+  mcgb::DevBuf d_cbank, d_pc;
   double nu_max = 0.0;
 };

@@ -116,6 +116,7 @@ struct Ctl {
   unsigned long long iterations;
   unsigned long long t_start, t_end;  // %globaltimer at kernel start / end (ns)
   unsigned long long k_acc;           // k-eigenvalue cycle: sum of fixed(w l nu Sigma_f 2^32)
+  unsigned long long pc_n;            // particles banked at this launch's interior census
 };
 
 struct RunParams {
@@ -154,6 +155,15 @@ struct RunParams {
   int ww_split_max;
   int implicit;            // implicit capture with a weight-cutoff roulette
   double wr_cutoff, wr_survival;
+  // histories this launch starts (n_hist, or 0 for a population-control interval after the first)
+  uint64_t n_sources;
+  // census of this launch: time (double and float pair), and whether it is an interior census of
+  // population control (reached particles go to the census bank C instead of ending)
+  int has_census, pc_interior;
+  float tc_hi, tc_lo;
+  double tc;
+  uint4* C[kMaxLanes];
+  uint64_t cap_c;
   // k-eigenvalue cycle (eigen = 1): sources come from src_site[h] (cycle >= 1), production banks
   // floor(nu inv_k + xi) fission sites at site_next[h * nmax + j] with count_next[h], every flight
   // adds fixed(w l nu Sigma_f) to Ctl::k_acc, tallies are scored only when eigen_score, into batch

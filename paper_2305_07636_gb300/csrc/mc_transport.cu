@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
     nF = nF < P.cap_s ? nF : P.cap_s;
     nS = nS < P.cap_s - nF ? nS : P.cap_s - nF;
     const uint64_t h0 = ld_volatile_u64(&ctl->hstart[cur]);
-    const uint64_t left = P.n_hist - h0;
+    const uint64_t left = P.n_sources - h0;
     // history-style iterations never write survivors back, so the transport bank is all room
     const uint64_t room = P.history_mode ? P.cap_s : P.cap_s - nF - nS;
     const uint64_t nBt = nB < room ? nB : room;  // births transported now; the rest wait
@@ -367,6 +367,70 @@ cudaError_t launch_comb(const uint32_t* counts, const unsigned long long* scan, 
   else k_comb<1><<<(unsigned)g, 256, 0, s>>>(counts, scan, sites, nmax, n, seed, next_cycle, src);
   return cudaGetLastError();
 }
+
+// ------------------------------------------------------------------------------------------ population control
+// Exact total weight of every batch's banked particles: sum of llrint(w 2^40) per batch.
+template <typename R>
+__global__ void k_pc_weight(const RunParams P, const unsigned long long* pc_n, long long* wq) {
+  const unsigned long long n = *pc_n < P.cap_c ? *pc_n : P.cap_c;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    Part<R> p;
+    bank_load(p, P.C, i);
+    atomicAdd(reinterpret_cast<unsigned long long*>(wq + (p.elem >> 16)),
+              (unsigned long long)__double2ll_rn(__dmul_rn(p.w, 1099511627776.0)));
+  }
+}
+
+// Splitting-roulette of the banked particles to N_b per batch: floor(w / w_t + xi) copies of weight
+// w_t = W_b 2^-40 / N_b at the census time, appended to the birth bank that the next interval's
+// launch starts from (count in *out_n); FP64 arithmetic rounded as the oracle rounds it.
+template <typename R>
+__global__ void k_pc_split(const RunParams P, const unsigned long long* pc_n, const long long* wq, const RunParams Q,
+                           unsigned long long* out_n, unsigned long long* copies, int* status) {
+  const unsigned long long n = *pc_n < P.cap_c ? *pc_n : P.cap_c;
+  const uint64_t N = P.n_hist, nb = (uint64_t)P.n_batches;
+  unsigned local = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    Part<R> p;
+    bank_load(p, P.C, i);
+    const uint64_t b = p.elem >> 16;
+    const uint64_t Nb = ((b + 1) * N + nb - 1) / nb - (b * N + nb - 1) / nb;
+    if (wq[b] <= 0 || Nb == 0) continue;
+    const double wt = __ddiv_rn(__ddiv_rn((double)wq[b], 1099511627776.0), (double)Nb);
+    const double xi = draw<double>(P.seed, p.tlo, p.thi, p.k, 1).a;
+    const int c = (int)floor(__dadd_rn(__ddiv_rn(p.w, wt), xi));
+    for (int j = 0; j < c; ++j) {
+      Part<R> q = p;
+      const uint2 t = child_tag(P.seed, p.tlo, p.thi, p.k, (uint32_t)j, 0x40000000u);
+      q.tlo = t.x;
+      q.thi = t.y;
+      q.k = 0;
+      q.w = wt;
+      q.pk = pk_set_pending(q.pk, PEND_NONE, 0, 1, 0);
+      set_census_time(q, P);
+      const unsigned long long k = atomicAdd(out_n, 1ull);
+      if (k < Q.cap_b) bank_store(q, Q.B[0], k);
+      else atomicCAS(status, 0, MC_ERR_BANK_FULL);
+    }
+    local += (unsigned)c;
+  }
+  if (local) atomicAdd(copies, (unsigned long long)local);
+}
+
+// P: the parameters of the launch that banked the particles; Q: those of the next launch (its
+// birth bank B[0] receives the copies)
+template <typename R>
+cudaError_t launch_pc(const RunParams& P, const RunParams& Q, const unsigned long long* pc_n, long long* wq,
+                      unsigned long long* out_n, unsigned long long* copies, int* status, bool split, cudaStream_t s) {
+  const unsigned g = 152 * 8;
+  if (!split) k_pc_weight<R><<<g, 256, 0, s>>>(P, pc_n, wq);
+  else k_pc_split<R><<<g, 256, 0, s>>>(P, pc_n, wq, Q, out_n, copies, status);
+  return cudaGetLastError();
+}
+template cudaError_t launch_pc<float>(const RunParams&, const RunParams&, const unsigned long long*, long long*,
+                                      unsigned long long*, unsigned long long*, int*, bool, cudaStream_t);
+template cudaError_t launch_pc<double>(const RunParams&, const RunParams&, const unsigned long long*, long long*,
+                                       unsigned long long*, unsigned long long*, int*, bool, cudaStream_t);
 
 // L2 atomic throughput probe: 64-bit adds to pseudo-random slots of an array of `span` elements
 // (the access pattern of tally scoring), `iters` per thread.

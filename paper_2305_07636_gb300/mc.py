@@ -27,7 +27,7 @@ MC_FP32, MC_FP64 = 0, 1
 MC_TALLY_FIXED64, MC_TALLY_FP64 = 0, 1
 COUNTER_NAMES = ["source", "secondary", "capture", "production", "leak", "census", "lost",
                  "flight", "collision", "scatter", "surface", "reflect", "ww_split", "ww_kill",
-                 "iterations", "scores", "ww_held"]
+                 "iterations", "scores", "ww_held", "pc_banked", "pc_copies"]
 NCOUNTERS = len(COUNTER_NAMES)
 KIND = {"PX": 0, "PY": 1, "PZ": 2, "CZ": 3}
 BC = {"interior": 0, "vacuum": 1, "reflect": 2}
@@ -93,7 +93,8 @@ class mc_run_opts(C.Structure):
                 ("log_capacity", C.c_uint64), ("first_history", C.c_uint64),
                 ("algorithm", C.c_int), ("drain_threshold", C.c_uint64),
                 ("tally_stripes", C.c_int), ("batch_unit", C.c_int),
-                ("implicit_capture", C.c_int), ("wr_cutoff", C.c_double), ("wr_survival", C.c_double)]
+                ("implicit_capture", C.c_int), ("wr_cutoff", C.c_double), ("wr_survival", C.c_double),
+                ("n_census", C.c_int), ("census_times", DP)]
 
 
 class mc_event(C.Structure):
@@ -197,6 +198,11 @@ def run_opts(**kw) -> mc_run_opts:
             v = {"event": 0, "history": 1, "auto": 2}[v]
         if k == "tally_mode" and isinstance(v, str):
             v = {"fixed": MC_TALLY_FIXED64, "fp64": MC_TALLY_FP64}[v]
+        if k == "census_times":
+            # interior census times of population control; the array lives as long as the options
+            o._census = np.ascontiguousarray(v, dtype=np.float64)
+            o.n_census = int(o._census.size)
+            v = o._census.ctypes.data_as(DP)
         setattr(o, k, v)
     return o
 
