@@ -92,6 +92,9 @@ def workload(name):
         return P.config4(), 1_000_000, ("config4: 200 cm stack of 40 layers (4 seeded materials, Sigma_t "
                                         "0.5-3, c 0.3-0.95), 7 groups, cosine surface source at x=0, "
                                         "detector 198-200 cm; learned weight windows")
+    if name == "pc":
+        return P.azurv1(), 10_000_000, ("pc: supercritical AZURV1 (c = 1.1, 20 mean free times), population control "
+                                        "by splitting-roulette at a census every 2 mean free times, 1e7 histories")
     if name == "eigen":
         return P.pin_cell(), 1_000_000, ("eigen: k-eigenvalue power iteration of a 7-group pin cell (pin r 0.54 cm, "
                                         "pitch 1.26 cm, reflective; seeded cross sections), 50 inactive + 100 "
@@ -658,7 +661,8 @@ def main():
     seed = 2
     p = mc.Problem(prob)
     extra = {k: int(v) for k, v in (o.split("=", 1) for o in args.opt)}
-    opts = mc.run_opts(first_history=rank * n, algorithm=args.algorithm, **extra)
+    census = {"census_times": np.arange(2.0, 20.0, 2.0)} if args.workload == "pc" else {}
+    opts = mc.run_opts(first_history=rank * n, algorithm=args.algorithm, **extra, **census)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
