@@ -26,7 +26,7 @@ NCOUNT = 16
 COUNTER_NAMES = ["source", "secondary", "capture", "production", "leak", "census", "lost",
                  "flight", "collision", "scatter", "surface", "reflect", "ww_split", "ww_kill",
                  "pc_banked", "pc_copies"]
-KIND = {"PX": 0, "PY": 1, "PZ": 2, "CZ": 3}
+KIND = {"PX": 0, "PY": 1, "PZ": 2, "CZ": 3, "CX": 4, "CY": 5, "SQ": 6, "GQ": 7}
 BC = {"interior": 0, "vacuum": 1, "reflect": 2}
 SRC_POS = {"box": 0, "surface_x0": 1}
 SRC_DIR = {"iso": 0, "beam_x": 1, "cos_x": 2}
@@ -143,6 +143,8 @@ def lib():
             L.or_u01.restype = C.c_double
             L.or_dist_cylinder.argtypes = [C.c_double] * 7 + [C.c_int]
             L.or_dist_cylinder.restype = C.c_double
+            L.or_dist_surface.argtypes = [C.POINTER(OrProblem), C.c_int] + [C.c_double] * 6 + [C.c_int]
+            L.or_dist_surface.restype = C.c_double
             L.or_dist_plane.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int]
             L.or_dist_plane.restype = C.c_double
             L.or_source_sample.argtypes = [C.POINTER(OrProblem), C.c_uint64, C.c_uint64,
@@ -208,7 +210,7 @@ class Marshalled:
         surfs = prob["surfaces"]
         s.n_surf = len(surfs)
         s.surf_kind = ip([KIND[x["kind"]] for x in surfs])
-        coef = np.zeros((len(surfs), 3))
+        coef = np.zeros((len(surfs), 10))
         for i, x in enumerate(surfs):
             coef[i, : len(x["coef"])] = x["coef"]
         s.surf_coef = dp(coef)
@@ -477,6 +479,13 @@ def u01(a, b):
 
 def dist_cylinder(x, y, ux, uy, x0, y0, r, inside):
     return lib().or_dist_cylinder(x, y, ux, uy, x0, y0, r, int(inside))
+
+
+def dist_surface(prob, s, pos, u, sense):
+    """Distance to surface s of the problem at which a particle at pos moving along u leaves its
+    half-space `sense`."""
+    m = Marshalled(prob)
+    return lib().or_dist_surface(C.byref(m.s), s, *[float(v) for v in pos], *[float(v) for v in u], sense)
 
 
 def dist_plane(pos, u, c, sense):

@@ -239,3 +239,56 @@ def infinite_k(mat):
     i = int(np.argmax(lam.real))
     phi = np.abs(V[:, i].real)
     return float(lam[i].real), phi / phi.sum()
+
+
+# ------------------------------------------------------------------ quadric bodies: point-source escape
+
+
+def sphere_point_escape(sigma_t, R, s):
+    """Escape probability of an isotropic point source at distance s from the centre of a purely
+    absorbing sphere of radius R: the average over directions of exp(-Sigma_t d), d the distance to
+    the surface along the direction, d(mu) = -s mu + sqrt(R^2 - s^2 (1 - mu^2))."""
+    f = lambda mu: math.exp(-sigma_t * (-s * mu + math.sqrt(R * R - s * s * (1.0 - mu * mu))))
+    return 0.5 * integrate.quad(f, -1.0, 1.0, epsabs=1e-13, epsrel=1e-12)[0]
+
+
+def cylinder_point_escape(sigma_t, R, L):
+    """Escape probability from the centre of a purely absorbing finite cylinder (radius R, length 2L):
+    with mu = |cos| of the angle to the axis, uniform on [0, 1] for an isotropic source, the distance
+    is min(L / mu, R / sqrt(1 - mu^2))."""
+    def f(mu):
+        d = min(L / mu if mu > 0 else math.inf, R / math.sqrt(1 - mu * mu) if mu < 1 else math.inf)
+        return math.exp(-sigma_t * d)
+    mu_c = L / math.sqrt(L * L + R * R)  # where the two distances meet
+    return (integrate.quad(f, 0.0, mu_c, epsabs=1e-13, epsrel=1e-12)[0]
+            + integrate.quad(f, mu_c, 1.0, epsabs=1e-13, epsrel=1e-12)[0])
+
+
+def ellipsoid_point_escape(sigma_t, a, b, c):
+    """Escape probability from the centre of a purely absorbing ellipsoid with semi-axes a, b, c:
+    d(u) = 1 / sqrt(ux^2/a^2 + uy^2/b^2 + uz^2/c^2), averaged over the sphere of directions."""
+    def f(phi, mu):
+        s = math.sqrt(1 - mu * mu)
+        ux, uy = s * math.cos(phi), s * math.sin(phi)
+        d = 1.0 / math.sqrt(ux * ux / a**2 + uy * uy / b**2 + mu * mu / c**2)
+        return math.exp(-sigma_t * d)
+    return integrate.dblquad(f, -1.0, 1.0, 0.0, 2 * math.pi, epsabs=1e-11, epsrel=1e-10)[0] / (4 * math.pi)
+
+
+def quadric_body_point_escape(sigma_t, Q, c0, p0):
+    """Escape probability of an isotropic point source at p0 inside the purely absorbing body
+    (p - c0)^T Q (p - c0) < 1 (Q symmetric positive definite): along u the distance t solves
+    t^2 u.Qu + 2 t u.Q(p0 - c0) + (p0 - c0).Q(p0 - c0) - 1 = 0 (the positive root), averaged over the
+    sphere of directions by 2-D quadrature.  Written from the matrix form, independently of any
+    expansion into the ten coefficients of a general quadric."""
+    Q = np.asarray(Q, dtype=np.float64)
+    w = np.asarray(p0, dtype=np.float64) - np.asarray(c0, dtype=np.float64)
+    cw = float(w @ Q @ w) - 1.0
+
+    def f(phi, mu):
+        s = math.sqrt(1 - mu * mu)
+        u = np.array([s * math.cos(phi), s * math.sin(phi), mu])
+        a, b = float(u @ Q @ u), float(u @ Q @ w)
+        t = (-b + math.sqrt(b * b - a * cw)) / a
+        return math.exp(-sigma_t * t)
+    return integrate.dblquad(f, -1.0, 1.0, 0.0, 2 * math.pi, epsabs=1e-11, epsrel=1e-10)[0] / (4 * math.pi)

@@ -110,6 +110,69 @@ struct Eig {
                             // exact integer sum, so k does not depend on the thread count
 };
 
+// A quadric surface written about a centre point c: with (X, Y, Z) = p - c,
+// f = A X^2 + B Y^2 + C Z^2 + D XY + E YZ + F ZX + G X + H Y + I Z + J.  Cylinders and spheres are
+// centred on their axis or centre (g = 0, J = -r^2), which keeps f well conditioned far from the
+// origin; a general quadric is taken as given, about the origin.
+struct Quad {
+  double q[10];
+  double c[3];
+};
+
+Quad quad_of(int kind, const double* k) {
+  Quad Q{};
+  switch (kind) {
+    case OR_CX: Q.q[1] = Q.q[2] = 1.0; Q.q[9] = -k[2] * k[2]; Q.c[1] = k[0]; Q.c[2] = k[1]; break;
+    case OR_CY: Q.q[0] = Q.q[2] = 1.0; Q.q[9] = -k[2] * k[2]; Q.c[0] = k[0]; Q.c[2] = k[1]; break;
+    case OR_SQ: Q.q[0] = Q.q[1] = Q.q[2] = 1.0; Q.q[9] = -k[3] * k[3]; Q.c[0] = k[0]; Q.c[1] = k[1]; Q.c[2] = k[2]; break;
+    case OR_GQ: for (int i = 0; i < 10; ++i) Q.q[i] = k[i]; break;
+    default: break;
+  }
+  return Q;
+}
+
+// the quadric along the ray p + t u: f(t) = a t^2 + b t + c
+void quad_ray(const Quad& Q, double x, double y, double z, double ux, double uy, double uz, double& a, double& b,
+              double& c) {
+  const double* q = Q.q;
+  const double X = x - Q.c[0], Y = y - Q.c[1], Z = z - Q.c[2];
+  a = q[0] * ux * ux + q[1] * uy * uy + q[2] * uz * uz + q[3] * ux * uy + q[4] * uy * uz + q[5] * uz * ux;
+  b = 2.0 * (q[0] * X * ux + q[1] * Y * uy + q[2] * Z * uz) + q[3] * (X * uy + Y * ux) + q[4] * (Y * uz + Z * uy) +
+      q[5] * (Z * ux + X * uz) + q[6] * ux + q[7] * uy + q[8] * uz;
+  c = q[0] * X * X + q[1] * Y * Y + q[2] * Z * Z + q[3] * X * Y + q[4] * Y * Z + q[5] * Z * X + q[6] * X + q[7] * Y +
+      q[8] * Z + q[9];
+}
+
+// Distance along the ray at which the particle leaves its half-space of a quadric (sense +1: f >= 0,
+// -1: f < 0): the root of f(t) where f falls (sense +1) or rises (sense -1).  A root just behind
+// counts as 0 where the particle is on the surface heading out of a convex section; a grazing
+// entry into a convex section whose chord is shorter than 1e-12 cm is no crossing.
+double dist_quadric(double a, double b, double c, int sense) {
+  const double INFD = std::numeric_limits<double>::infinity();
+  if (a == 0.0) {
+    if (b == 0.0 || (sense > 0) == (b > 0.0)) return INFD;  // f linear along the ray, not leaving
+    double t = -c / b;
+    return t > 0.0 ? t : 0.0;
+  }
+  double disc = b * b - 4.0 * a * c;
+  if (sense < 0) {  // the root where f rises: (-b + sqrt(disc)) / 2a
+    if (disc < 0.0) {
+      if (a > 0.0) disc = 0.0;  // inside a convex section: rounding
+      else return INFD;
+    }
+    double sq = std::sqrt(disc);
+    double t = b <= 0.0 ? (-b + sq) / (2.0 * a) : (-2.0 * c) / (b + sq);
+    if (!(t > 0.0)) return a > 0.0 ? 0.0 : INFD;
+    return t;
+  }
+  if (disc <= 0.0) return INFD;  // the root where f falls: (-b - sqrt(disc)) / 2a
+  double sq = std::sqrt(disc);
+  if (a > 0.0 && sq < 1e-12 * a) return INFD;
+  double t = b >= 0.0 ? (-b - sq) / (2.0 * a) : (-2.0 * c) / (b - sq);
+  if (!(t > 0.0)) return (a > 0.0 && b < 0.0) ? 0.0 : INFD;
+  return t;
+}
+
 struct Prob {
   int G, M;
   std::vector<double> st, ss, sf, nu, chi, v;
@@ -119,7 +182,8 @@ struct Prob {
   std::vector<double> src_cdf;   // [G]
   int n_surf;
   std::vector<int> skind, sbc;
-  std::vector<double> scoef;
+  std::vector<double> scoef;   // [n_surf][10] as given
+  std::vector<Quad> quad;       // surfaces other than planes and z-cylinders, as quadrics
   int n_cell;
   std::vector<int> nhs, hs_surf, hs_sense, cmat;
   bool lat;
@@ -189,7 +253,9 @@ Prob copy_problem(const or_problem* p) {
   P.n_surf = p->n_surf;
   P.skind.assign(p->surf_kind, p->surf_kind + P.n_surf);
   P.sbc.assign(p->surf_bc, p->surf_bc + P.n_surf);
-  P.scoef.assign(p->surf_coef, p->surf_coef + 3 * P.n_surf);
+  P.scoef.assign(p->surf_coef, p->surf_coef + 10 * P.n_surf);
+  P.quad.resize(P.n_surf);
+  for (int s = 0; s < P.n_surf; ++s) P.quad[s] = quad_of(P.skind[s], &P.scoef[10 * s]);
   P.n_cell = p->n_cell;
   P.nhs.assign(p->cell_nhs, p->cell_nhs + P.n_cell);
   P.hs_surf.assign(p->cell_hs_surf, p->cell_hs_surf + OR_MAX_HS * P.n_cell);
@@ -257,14 +323,19 @@ struct Particle {
 
 // surface function f(p): plane x - c (or y, z); cylinder (x-x0)^2 + (y-y0)^2 - r^2
 double surf_f(const Prob& P, int s, double x, double y, double z) {
-  const double* c = &P.scoef[3 * s];
+  const double* c = &P.scoef[10 * s];
   switch (P.skind[s]) {
     case OR_PX: return x - c[0];
     case OR_PY: return y - c[0];
     case OR_PZ: return z - c[0];
-    default: {
+    case OR_CZ: {
       double dx = x - c[0], dy = y - c[1];
       return dx * dx + dy * dy - c[2] * c[2];
+    }
+    default: {
+      double a, b, f;
+      quad_ray(P.quad[s], x, y, z, 0.0, 0.0, 0.0, a, b, f);
+      return f;
     }
   }
 }
@@ -274,26 +345,39 @@ bool sense_ok(double f, int sense) { return sense > 0 ? f >= 0.0 : f < 0.0; }
 
 // size of the terms surf_f subtracts: what its rounding error is relative to
 double surf_terms(const Prob& P, int s, double x, double y, double z) {
-  const double* c = &P.scoef[3 * s];
+  const double* c = &P.scoef[10 * s];
   switch (P.skind[s]) {
     case OR_PX: return 1.0 + std::fabs(x) + std::fabs(c[0]);
     case OR_PY: return 1.0 + std::fabs(y) + std::fabs(c[0]);
     case OR_PZ: return 1.0 + std::fabs(z) + std::fabs(c[0]);
-    default: {
+    case OR_CZ: {
       double dx = x - c[0], dy = y - c[1];
       return 1.0 + dx * dx + dy * dy + c[2] * c[2];
+    }
+    default: {
+      const Quad& Q = P.quad[s];
+      const double* q = Q.q;
+      const double X = x - Q.c[0], Y = y - Q.c[1], Z = z - Q.c[2];
+      return 1.0 + std::fabs(q[0] * X * X) + std::fabs(q[1] * Y * Y) + std::fabs(q[2] * Z * Z) +
+             std::fabs(q[3] * X * Y) + std::fabs(q[4] * Y * Z) + std::fabs(q[5] * Z * X) + std::fabs(q[6] * X) +
+             std::fabs(q[7] * Y) + std::fabs(q[8] * Z) + std::fabs(q[9]);
     }
   }
 }
 
 // normal component of the direction on surface s: which side a point on s is heading into
-double surf_dir(const Prob& P, int s, double x, double y, double ux, double uy, double uz) {
-  const double* c = &P.scoef[3 * s];
+double surf_dir(const Prob& P, int s, double x, double y, double z, double ux, double uy, double uz) {
+  const double* c = &P.scoef[10 * s];
   switch (P.skind[s]) {
     case OR_PX: return ux;
     case OR_PY: return uy;
     case OR_PZ: return uz;
-    default: return (x - c[0]) * ux + (y - c[1]) * uy;
+    case OR_CZ: return (x - c[0]) * ux + (y - c[1]) * uy;
+    default: {
+      double a, b, f;
+      quad_ray(P.quad[s], x, y, z, ux, uy, uz, a, b, f);
+      return b;  // the rate at which f changes along the direction
+    }
   }
 }
 
@@ -320,7 +404,7 @@ int find_cell(const Prob& P, double x, double y, double z, int skip_surf, int sk
           ok = (sn == skip_sense);
         } else if (pass == 0) {
           double f = surf_f(P, s, x, y, z);
-          if (f == 0.0) f = surf_dir(P, s, x, y, ux, uy, uz);
+          if (f == 0.0) f = surf_dir(P, s, x, y, z, ux, uy, uz);
           ok = sense_ok(f, sn);
         } else {
           double f = surf_f(P, s, x, y, z), tol = 1e-12 * surf_terms(P, s, x, y, z);
@@ -400,13 +484,19 @@ Hit distance_to_boundary(const Prob& P, const Particle& q) {
   int c = q.cell;
   for (int i = 0; i < P.nhs[c]; ++i) {
     int s = P.hs_surf[c * OR_MAX_HS + i], sn = P.hs_sense[c * OR_MAX_HS + i];
-    const double* cf = &P.scoef[3 * s];
+    const double* cf = &P.scoef[10 * s];
     double d;
     switch (P.skind[s]) {
       case OR_PX: d = dist_plane(q.x, q.ux, cf[0], sn); break;
       case OR_PY: d = dist_plane(q.y, q.uy, cf[0], sn); break;
       case OR_PZ: d = dist_plane(q.z, q.uz, cf[0], sn); break;
-      default: d = dist_cyl(q.x, q.y, q.ux, q.uy, cf[0], cf[1], cf[2], sn < 0); break;
+      case OR_CZ: d = dist_cyl(q.x, q.y, q.ux, q.uy, cf[0], cf[1], cf[2], sn < 0); break;
+      default: {
+        double a, b, f;
+        quad_ray(P.quad[s], q.x, q.y, q.z, q.ux, q.uy, q.uz, a, b, f);
+        d = dist_quadric(a, b, f, sn);
+        break;
+      }
     }
     if (d < h.d) h = {d, HIT_CELL, s};
   }
@@ -1127,6 +1217,23 @@ double or_u01(uint32_t a, uint32_t b) { return u01(a, b); }
 double or_dist_cylinder(double x, double y, double ux, double uy, double x0, double y0, double r,
                         int inside) {
   return dist_cyl(x, y, ux, uy, x0, y0, r, inside != 0);
+}
+
+double or_dist_surface(const or_problem* p, int s, double x, double y, double z, double ux, double uy, double uz,
+                       int sense) {
+  Prob P = copy_problem(p);
+  const double* cf = &P.scoef[10 * s];
+  switch (P.skind[s]) {
+    case OR_PX: return dist_plane(x, ux, cf[0], sense);
+    case OR_PY: return dist_plane(y, uy, cf[0], sense);
+    case OR_PZ: return dist_plane(z, uz, cf[0], sense);
+    case OR_CZ: return dist_cyl(x, y, ux, uy, cf[0], cf[1], cf[2], sense < 0);
+    default: {
+      double a, b, f;
+      quad_ray(P.quad[s], x, y, z, ux, uy, uz, a, b, f);
+      return dist_quadric(a, b, f, sense);
+    }
+  }
 }
 
 double or_dist_plane(double pos, double u, double c, int sense) {

@@ -25,7 +25,9 @@ extern "C" {
 
 #define OR_MAX_HS 16
 
-enum { OR_PX = 0, OR_PY = 1, OR_PZ = 2, OR_CZ = 3 };
+/* surfaces: planes x/y/z = c; cylinders parallel to z, x, y; spheres; general quadrics
+ * A x^2 + B y^2 + C z^2 + D xy + E yz + F zx + G x + H y + I z + J = 0 */
+enum { OR_PX = 0, OR_PY = 1, OR_PZ = 2, OR_CZ = 3, OR_CX = 4, OR_CY = 5, OR_SQ = 6, OR_GQ = 7 };
 enum { OR_INTERIOR = 0, OR_VACUUM = 1, OR_REFLECT = 2 };
 enum { OR_SRC_BOX = 0, OR_SRC_SURFACE_X0 = 1 };
 enum { OR_DIR_ISO = 0, OR_DIR_BEAM_X = 1, OR_DIR_COS_X = 2 };
@@ -64,7 +66,8 @@ typedef struct {
   const double* speed;     /* [G] */
   int n_surf;
   const int* surf_kind;    /* [n_surf] OR_PX.. */
-  const double* surf_coef; /* [n_surf][3]: plane c; or cylinder x0, y0, r */
+  const double* surf_coef; /* [n_surf][10]: plane c; z-cylinder x0, y0, r; x-cylinder y0, z0, r;
+                              y-cylinder x0, z0, r; sphere x0, y0, z0, r; quadric A..J */
   const int* surf_bc;      /* [n_surf] */
   int n_cell;
   const int* cell_nhs;     /* [n_cell] */
@@ -203,6 +206,10 @@ double or_u01(uint32_t a, uint32_t b);
 double or_dist_cylinder(double x, double y, double ux, double uy, double x0, double y0, double r,
                         int inside);
 double or_dist_plane(double pos, double u, double c, int sense);
+/* distance to surface s of the problem from (x,y,z) along (ux,uy,uz) for a particle in its
+ * half-space `sense` (the distance at which it leaves that half-space; inf if never) */
+double or_dist_surface(const or_problem* p, int s, double x, double y, double z, double ux, double uy, double uz,
+                       int sense);
 /* source sample of history h: writes x,y,z,ux,uy,uz,t and group; returns cell or -1 */
 int or_source_sample(const or_problem* p, uint64_t seed, uint64_t h, double out[7], int* g);
 /* cell of the point (x, y, z); skip >= 0: the point was reached by crossing surface `skip`,

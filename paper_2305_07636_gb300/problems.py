@@ -14,8 +14,10 @@ Problem dict layout (all lengths in cm, times in s, cross sections in 1/cm):
 
     G, speed[G]
     materials: list of {sigma_t[G], sigma_s[G][G] (from, to), sigma_f[G], nu[G], chi[G]}
-    surfaces:  list of {kind: 'PX'|'PY'|'PZ'|'CZ', coef: [c] or [x0, y0, r],
-                        bc: 'interior'|'vacuum'|'reflect'}
+    surfaces:  list of {kind: 'PX'|'PY'|'PZ'|'CZ'|'CX'|'CY'|'SQ'|'GQ', coef, bc: 'interior'|'vacuum'|'reflect'}
+               coef: plane [c]; z-cylinder [x0, y0, r]; x-cylinder [y0, z0, r]; y-cylinder [x0, z0, r];
+               sphere [x0, y0, z0, r]; general quadric [A..J] of
+               A x^2 + B y^2 + C z^2 + D xy + E yz + F zx + G x + H y + I z + J
     cells:     list of {halfspaces: [(surface, +1|-1), ...], material: m (>=0) or -1 (lattice)}
     lattice:   None or {nx, ny, x0, y0, pitch, radius, pin_material[ny*nx] (-1 = no pin),
                         matrix_material}
@@ -247,6 +249,67 @@ def pin_cell(seed=7, G=7, pitch=1.26, radius=0.54, mesh_n=4):
     src = source("box", (0, 0, 0), (pitch, pitch, 0), "iso", G, 0)
     tal = [mesh(x=np.linspace(0, pitch, mesh_n + 1), y=np.linspace(0, pitch, mesh_n + 1))]
     return problem("pincell", G, log_speeds(G), [fuel, moderator], surfs, cells, src, tal, INF, lat)
+
+
+def absorber_in_void(body, sigma_t=1.0, point=(0.0, 0.0, 0.0), half=10.0, name="body", extra_cells=()):
+    """A pure absorber (one group, Sigma_t) bounded by `body` = (surfaces, halfspaces) inside a void box
+    [-half, half]^3 with vacuum walls, isotropic point source at `point`: the leakage through the box
+    is the probability that a source particle escapes the absorber."""
+    bsurfs, bhs = body
+    box, box_hs = box_surfaces((-half,) * 3, (half,) * 3, "vacuum")
+    surfs = list(bsurfs) + box
+    nb = len(bsurfs)
+    inside = {"halfspaces": list(bhs), "material": 0}
+    cells = [inside]
+    # the void: inside the box and outside the body (one cell per bounding half-space flipped, in order)
+    for i, (s, sn) in enumerate(bhs):
+        hs = [(s2, sn2) for s2, sn2 in bhs[:i]] + [(s, -sn)] + [(b + nb, sn2) for b, sn2 in box_hs]
+        cells.append({"halfspaces": hs, "material": 1})
+    mats = [material([sigma_t], [[0.0]]), material([0.0], [[0.0]])]
+    src = source("box", point, point, "iso", 1)
+    tal = [mesh(x=(-half, half), y=(-half, half), z=(-half, half))]
+    return problem(name, 1, [1.0], mats, surfs, cells, src, tal)
+
+
+def sphere_absorber(R=1.0, sigma_t=1.0, point=(0.0, 0.0, 0.0), center=(0.0, 0.0, 0.0)):
+    s = [{"kind": "SQ", "coef": [float(c) for c in center] + [float(R)], "bc": "interior"}]
+    return absorber_in_void((s, [(0, -1)]), sigma_t, point, name="sphere")
+
+
+def xcylinder_absorber(R=1.0, L=2.0, sigma_t=1.0, axis="x"):
+    """Finite cylinder of radius R along `axis` ('x', 'y' or 'z') between the planes at -L and +L,
+    point source at the centre."""
+    kind = {"x": "CX", "y": "CY", "z": "CZ"}[axis]
+    plane = {"x": "PX", "y": "PY", "z": "PZ"}[axis]
+    s = [{"kind": kind, "coef": [0.0, 0.0, float(R)], "bc": "interior"},
+         {"kind": plane, "coef": [-float(L)], "bc": "interior"},
+         {"kind": plane, "coef": [float(L)], "bc": "interior"}]
+    return absorber_in_void((s, [(0, -1), (1, +1), (2, -1)]), sigma_t, name=f"cyl{axis}")
+
+
+def ellipsoid_matrix(a, b, c, angles):
+    """Q = R diag(1/a^2, 1/b^2, 1/c^2) R^T of an ellipsoid rotated by the z-y-x angles."""
+    az, ay, ax = angles
+    Rz = np.array([[math.cos(az), -math.sin(az), 0], [math.sin(az), math.cos(az), 0], [0, 0, 1]])
+    Ry = np.array([[math.cos(ay), 0, math.sin(ay)], [0, 1, 0], [-math.sin(ay), 0, math.cos(ay)]])
+    Rx = np.array([[1, 0, 0], [0, math.cos(ax), -math.sin(ax)], [0, math.sin(ax), math.cos(ax)]])
+    R = Rz @ Ry @ Rx
+    return R @ np.diag([1 / a**2, 1 / b**2, 1 / c**2]) @ R.T
+
+
+def ellipsoid_absorber(a=1.0, b=0.6, c=1.5, sigma_t=1.0, angles=(0.0, 0.0, 0.0), center=(0.0, 0.0, 0.0),
+                       point=None):
+    """Ellipsoid with semi-axes a, b, c, rotated by the z-y-x angles and centred at `center`, given as
+    a general quadric (all ten coefficients in use when rotated and moved), point source at the
+    centre: (p - c0)^T Q (p - c0) < 1 with Q = R diag(1/a^2, 1/b^2, 1/c^2) R^T."""
+    Q = ellipsoid_matrix(a, b, c, angles)
+    c0 = np.asarray(center, dtype=np.float64)
+    g = -2.0 * Q @ c0
+    J = float(c0 @ Q @ c0) - 1.0
+    coef = [Q[0, 0], Q[1, 1], Q[2, 2], 2 * Q[0, 1], 2 * Q[1, 2], 2 * Q[0, 2], g[0], g[1], g[2], J]
+    s = [{"kind": "GQ", "coef": [float(v) for v in coef], "bc": "interior"}]
+    p0 = c0 if point is None else np.asarray(point, dtype=np.float64)
+    return absorber_in_void((s, [(0, -1)]), sigma_t, point=tuple(float(v) for v in p0), name="ellipsoid")
 
 
 def offspring_matrix(mat):
