@@ -54,15 +54,25 @@ typedef enum {
 #define MC_MAX_TALLIES 4
 
 /* ------------------------------------------------------------------------- geometry */
-typedef enum { MC_SURF_PX = 0, MC_SURF_PY = 1, MC_SURF_PZ = 2, MC_SURF_CZ = 3 } mc_surface_kind;
+typedef enum {
+  MC_SURF_PX = 0, MC_SURF_PY = 1, MC_SURF_PZ = 2, /* planes x, y, z = coef[0] */
+  MC_SURF_CZ = 3, /* cylinder parallel to z: (x - coef[0])^2 + (y - coef[1])^2 - coef[2]^2 */
+  MC_SURF_CX = 4, /* cylinder parallel to x: (y - coef[0])^2 + (z - coef[1])^2 - coef[2]^2 */
+  MC_SURF_CY = 5, /* cylinder parallel to y: (x - coef[0])^2 + (z - coef[1])^2 - coef[2]^2 */
+  MC_SURF_SQ = 6, /* sphere: (x - coef[0])^2 + (y - coef[1])^2 + (z - coef[2])^2 - coef[3]^2 */
+  MC_SURF_GQ = 7  /* general quadric A x^2 + B y^2 + C z^2 + D xy + E yz + F zx + G x + H y + I z + J,
+                     coef = A..J */
+} mc_surface_kind;
 typedef enum { MC_BC_INTERIOR = 0, MC_BC_VACUUM = 1, MC_BC_REFLECT = 2 } mc_boundary;
 
-/* Surface f(x,y,z) = 0.  Planes: f = x - coef[0] (y, z likewise).  Cylinder parallel to z:
- * f = (x - coef[0])^2 + (y - coef[1])^2 - coef[2]^2.  Reflection is supported on planes only. */
+/* Surface f(x,y,z) = 0 of the kind's form (mc_surface_kind), the paper's quadric-surface CSG.  A
+ * particle leaves the half-space it is in at the first point ahead where f changes sign in that
+ * direction; a grazing entry into a sphere, cylinder or convex quadric whose chord is shorter than
+ * 2e-5 cm (FP32 tracking) or 1e-12 cm (FP64) is no crossing.  Reflection is supported on planes only. */
 typedef struct {
-  int kind;       /* mc_surface_kind */
-  double coef[3];
-  int bc;         /* mc_boundary */
+  int kind;        /* mc_surface_kind */
+  double coef[10]; /* as the kind says; unused entries ignored */
+  int bc;          /* mc_boundary */
 } mc_surface;
 
 /* A cell is the intersection of half-spaces; sense +1 means f >= 0, -1 means f < 0.

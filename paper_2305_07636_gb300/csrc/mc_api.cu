@@ -175,13 +175,16 @@ int validate(const mc_problem_desc* d) {
     return fail(MC_ERR_INVALID, "n_surfaces=%d outside [1,%d]", d->n_surfaces, MC_MAX_SURFACES);
   for (int s = 0; s < d->n_surfaces; ++s) {
     const mc_surface& S = d->surfaces[s];
-    if (S.kind < MC_SURF_PX || S.kind > MC_SURF_CZ) return fail(MC_ERR_INVALID, "surface %d: bad kind", s);
+    if (S.kind < MC_SURF_PX || S.kind > MC_SURF_GQ) return fail(MC_ERR_INVALID, "surface %d: bad kind", s);
     if (S.bc < MC_BC_INTERIOR || S.bc > MC_BC_REFLECT) return fail(MC_ERR_INVALID, "surface %d: bad bc", s);
-    if (S.kind == MC_SURF_CZ && S.bc == MC_BC_REFLECT)
+    if (S.kind > MC_SURF_PZ && S.bc == MC_BC_REFLECT)
       return fail(MC_ERR_INVALID, "surface %d: reflection is supported on planes only", s);
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 10; ++i)
       if (!std::isfinite(S.coef[i])) return fail(MC_ERR_INVALID, "surface %d: non-finite coefficient", s);
-    if (S.kind == MC_SURF_CZ && !(S.coef[2] > 0.0)) return fail(MC_ERR_INVALID, "surface %d: radius must be > 0", s);
+    const double radius = S.kind == MC_SURF_SQ ? S.coef[3] : S.coef[2];
+    if ((S.kind == MC_SURF_CZ || S.kind == MC_SURF_CX || S.kind == MC_SURF_CY || S.kind == MC_SURF_SQ) &&
+        !(radius > 0.0))
+      return fail(MC_ERR_INVALID, "surface %d: radius must be > 0", s);
   }
   if (d->n_cells < 1 || d->n_cells > MC_MAX_CELLS || !d->cells)
     return fail(MC_ERR_INVALID, "n_cells=%d outside [1,%d]", d->n_cells, MC_MAX_CELLS);
@@ -351,11 +354,30 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
   H.o_chi = B.put(chi);
   H.o_src_cdf = B.put(src);
   std::vector<int> skind(H.n_surf), sbc(H.n_surf);
-  std::vector<R> scoef(4 * H.n_surf, R(0));
+  // per surface kSurfStride values: [0..2] the plane / z-cylinder coefficients, [3..12] the quadric
+  // A..J about the centre [13..15] for the other kinds (cylinders and spheres centred on their axis
+  // or centre, so that their f stays well conditioned far from the origin)
+  std::vector<R> scoef(kSurfStride * H.n_surf, R(0));
   for (int s = 0; s < H.n_surf; ++s) {
-    skind[s] = d->surfaces[s].kind;
-    sbc[s] = d->surfaces[s].bc;
-    for (int i = 0; i < 3; ++i) scoef[4 * s + i] = (R)d->surfaces[s].coef[i];
+    const mc_surface& S = d->surfaces[s];
+    skind[s] = S.kind;
+    sbc[s] = S.bc;
+    R* c = &scoef[kSurfStride * s];
+    for (int i = 0; i < 3; ++i) c[i] = (R)S.coef[i];
+    double q[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, ctr[3] = {0, 0, 0};
+    switch (S.kind) {
+      case MC_SURF_CX: q[1] = q[2] = 1.0; q[9] = -S.coef[2] * S.coef[2]; ctr[1] = S.coef[0]; ctr[2] = S.coef[1]; break;
+      case MC_SURF_CY: q[0] = q[2] = 1.0; q[9] = -S.coef[2] * S.coef[2]; ctr[0] = S.coef[0]; ctr[2] = S.coef[1]; break;
+      case MC_SURF_SQ:
+        q[0] = q[1] = q[2] = 1.0;
+        q[9] = -S.coef[3] * S.coef[3];
+        for (int i = 0; i < 3; ++i) ctr[i] = S.coef[i];
+        break;
+      case MC_SURF_GQ: for (int i = 0; i < 10; ++i) q[i] = S.coef[i]; break;
+      default: break;
+    }
+    for (int i = 0; i < 10; ++i) c[3 + i] = (R)q[i];
+    for (int i = 0; i < 3; ++i) c[13 + i] = (R)ctr[i];
   }
   H.o_skind = B.put(skind);
   H.o_sbc = B.put(sbc);

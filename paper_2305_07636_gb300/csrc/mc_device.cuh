@@ -370,16 +370,64 @@ __device__ __forceinline__ R cyl_dist(R x, R y, R ux, R uy, R x0, R y0, R r, boo
   return d > R(0) ? d : R(0);
 }
 
+// A quadric surface (cylinders along x or y, spheres, general quadrics) along the ray p + t u:
+// f(t) = a t^2 + b t + c, with the quadric A..J written about its centre: (X, Y, Z) = p - centre.
+template <typename R>
+__device__ __forceinline__ void quad_ray(const R* k, R x, R y, R z, R ux, R uy, R uz, R& a, R& b, R& c) {
+  const R* q = k + 3;
+  const R X = x - k[13], Y = y - k[14], Z = z - k[15];
+  a = q[0] * ux * ux + q[1] * uy * uy + q[2] * uz * uz + q[3] * ux * uy + q[4] * uy * uz + q[5] * uz * ux;
+  b = R(2) * (q[0] * X * ux + q[1] * Y * uy + q[2] * Z * uz) + q[3] * (X * uy + Y * ux) + q[4] * (Y * uz + Z * uy) +
+      q[5] * (Z * ux + X * uz) + q[6] * ux + q[7] * uy + q[8] * uz;
+  c = q[0] * X * X + q[1] * Y * Y + q[2] * Z * Z + q[3] * X * Y + q[4] * Y * Z + q[5] * Z * X + q[6] * X + q[7] * Y +
+      q[8] * Z + q[9];
+}
+
+// Distance at which the particle leaves its half-space of a quadric (sense +1: f >= 0, -1: f < 0):
+// the root of f(t) where f falls (sense +1) or rises (sense -1).  A root just behind counts as 0
+// where the particle is on the surface heading out of a convex section; a grazing entry into a convex
+// section whose chord sqrt(disc) / a is shorter than eps (2e-5 cm FP32, 1e-12 cm FP64) is no crossing.
+template <typename R>
+__device__ __forceinline__ R dist_quadric(R a, R b, R c, int sense) {
+  if (a == R(0)) {
+    if (b == R(0) || (sense > 0) == (b > R(0))) return rinf<R>();  // f linear along the ray, not leaving
+    const R t = rdiv(-c, b);
+    return t > R(0) ? t : R(0);
+  }
+  R disc = b * b - R(4) * a * c;
+  if (sense < 0) {  // the root where f rises
+    if (disc < R(0)) {
+      if (a > R(0)) disc = R(0);  // inside a convex section: rounding
+      else return rinf<R>();
+    }
+    const R sq = rsqrt_(disc);
+    const R t = b <= R(0) ? rdiv(-b + sq, R(2) * a) : rdiv(R(-2) * c, b + sq);
+    if (!(t > R(0))) return a > R(0) ? R(0) : rinf<R>();
+    return t;
+  }
+  if (disc <= R(0)) return rinf<R>();  // the root where f falls
+  const R sq = rsqrt_(disc);
+  if (a > R(0) && sq < (sizeof(R) == 4 ? R(2e-5) : R(1e-12)) * a) return rinf<R>();
+  const R t = b >= R(0) ? rdiv(-b - sq, R(2) * a) : rdiv(R(-2) * c, b - sq);
+  if (!(t > R(0))) return (a > R(0) && b < R(0)) ? R(0) : rinf<R>();
+  return t;
+}
+
 template <typename R>
 __device__ __forceinline__ R surf_f(const Tab<R>& T, int s, R x, R y, R z) {
-  const R* c = T.scoef + 4 * s;
+  const R* c = T.scoef + kSurfStride * s;
   switch (T.skind[s]) {
     case MC_SURF_PX: return x - c[0];
     case MC_SURF_PY: return y - c[0];
     case MC_SURF_PZ: return z - c[0];
-    default: {
+    case MC_SURF_CZ: {
       const R dx = x - c[0], dy = y - c[1];
       return dx * dx + dy * dy - c[2] * c[2];
+    }
+    default: {
+      R a, b, f;
+      quad_ray(c, x, y, z, R(0), R(0), R(0), a, b, f);
+      return f;
     }
   }
 }
@@ -387,27 +435,38 @@ __device__ __forceinline__ R surf_f(const Tab<R>& T, int s, R x, R y, R z) {
 // rounding scale of surf_f at a point: the magnitude of the terms it subtracts
 template <typename R>
 __device__ __forceinline__ R surf_scale(const Tab<R>& T, int s, R x, R y, R z) {
-  const R* c = T.scoef + 4 * s;
+  const R* c = T.scoef + kSurfStride * s;
   switch (T.skind[s]) {
     case MC_SURF_PX: return R(1) + fabs(x) + fabs(c[0]);
     case MC_SURF_PY: return R(1) + fabs(y) + fabs(c[0]);
     case MC_SURF_PZ: return R(1) + fabs(z) + fabs(c[0]);
-    default: {
+    case MC_SURF_CZ: {
       const R dx = x - c[0], dy = y - c[1];
       return R(1) + dx * dx + dy * dy + c[2] * c[2];
+    }
+    default: {
+      const R* q = c + 3;
+      const R X = x - c[13], Y = y - c[14], Z = z - c[15];
+      return R(1) + fabs(q[0] * X * X) + fabs(q[1] * Y * Y) + fabs(q[2] * Z * Z) + fabs(q[3] * X * Y) +
+             fabs(q[4] * Y * Z) + fabs(q[5] * Z * X) + fabs(q[6] * X) + fabs(q[7] * Y) + fabs(q[8] * Z) + fabs(q[9]);
     }
   }
 }
 
 // normal component of the direction on surface s (the side a point on s is moving into)
 template <typename R>
-__device__ __forceinline__ R surf_dir(const Tab<R>& T, int s, R x, R y, R ux, R uy, R uz) {
-  const R* c = T.scoef + 4 * s;
+__device__ __forceinline__ R surf_dir(const Tab<R>& T, int s, R x, R y, R z, R ux, R uy, R uz) {
+  const R* c = T.scoef + kSurfStride * s;
   switch (T.skind[s]) {
     case MC_SURF_PX: return ux;
     case MC_SURF_PY: return uy;
     case MC_SURF_PZ: return uz;
-    default: return (x - c[0]) * ux + (y - c[1]) * uy;
+    case MC_SURF_CZ: return (x - c[0]) * ux + (y - c[1]) * uy;
+    default: {
+      R a, b, f;
+      quad_ray(c, x, y, z, ux, uy, uz, a, b, f);
+      return b;  // the rate at which f changes along the direction
+    }
   }
 }
 
@@ -439,7 +498,7 @@ __device__ int locate_cell(const Tab<R>& T, R x, R y, R z, int skip, int skip_se
         } else {
           const R f = surf_f(T, s, x, y, z);
           if (pass == 0) {
-            const R d = f != R(0) ? f : surf_dir(T, s, x, y, ux, uy, uz);
+            const R d = f != R(0) ? f : surf_dir(T, s, x, y, z, ux, uy, uz);
             ok = sn > 0 ? (d >= R(0)) : (d < R(0));
           } else {
             const R tol = eps * surf_scale(T, s, x, y, z);
@@ -486,13 +545,19 @@ __device__ R boundary_distance(const Tab<R>& T, const Part<R>& p, Hit& hit) {
   for (int i = 0; i < n; ++i) {
     const int e = T.hs[c * MC_MAX_HALFSPACES + i];
     const int s = e & 0xFFFF, sn = (e >> 16) ? -1 : 1;
-    const R* cf = T.scoef + 4 * s;
+    const R* cf = T.scoef + kSurfStride * s;
     R d;
     switch (T.skind[s]) {
       case MC_SURF_PX: d = plane_dist(p.x, p.ux, cf[0], sn); break;
       case MC_SURF_PY: d = plane_dist(p.y, p.uy, cf[0], sn); break;
       case MC_SURF_PZ: d = plane_dist(p.z, p.uz, cf[0], sn); break;
-      default: d = cyl_dist(p.x, p.y, p.ux, p.uy, cf[0], cf[1], cf[2], sn < 0); break;
+      case MC_SURF_CZ: d = cyl_dist(p.x, p.y, p.ux, p.uy, cf[0], cf[1], cf[2], sn < 0); break;
+      default: {
+        R a, b, f;
+        quad_ray(cf, p.x, p.y, p.z, p.ux, p.uy, p.uz, a, b, f);
+        d = dist_quadric(a, b, f, sn);
+        break;
+      }
     }
     if (d < best) {
       best = d;

@@ -8,6 +8,7 @@
 namespace mcgb {
 
 constexpr int kMaxTallies = MC_MAX_TALLIES;
+constexpr int kSurfStride = 16;   // table values per surface (plane / cylinder, quadric, centre)
 constexpr int kMaxLanes = 6;      // 16-byte state lanes per particle (FP64 layout)
 constexpr int kLanesFP32 = 4;     // 64 B per particle
 constexpr int kLanesFP64 = 6;     // 96 B per particle
@@ -83,7 +84,7 @@ struct TableHeader {
   // byte offsets
   int o_st, o_ss, o_ssf, o_nu;        // [M][G] Real: sigma_t, scatter threshold, scatter+production threshold, nu
   int o_v, o_inv_v, o_scdf, o_chi;    // [G] Real speed, 1/speed; [M][G][G] scatter CDF; [M][G] chi CDF
-  int o_src_cdf, o_skind, o_sbc, o_scoef;  // [G] Real; [n_surf] int; [n_surf] int; [n_surf][4] Real
+  int o_src_cdf, o_skind, o_sbc, o_scoef;  // [G] Real; [n_surf] int; [n_surf] int; [n_surf][16] Real
   int o_nhs, o_hs, o_cmat, o_lpin;    // [n_cell] int; [n_cell][16] int (surf | sense<<16); [n_cell] int; [ny*nx] int
   TallyDesc tally[kMaxTallies];
   int blob_bytes, o_nusf, pad3, pad4;  // o_nusf: [M][G] Real nu Sigma_f (k-eigenvalue estimator)

@@ -29,7 +29,7 @@ COUNTER_NAMES = ["source", "secondary", "capture", "production", "leak", "census
                  "flight", "collision", "scatter", "surface", "reflect", "ww_split", "ww_kill",
                  "iterations", "scores", "ww_held", "pc_banked", "pc_copies"]
 NCOUNTERS = len(COUNTER_NAMES)
-KIND = {"PX": 0, "PY": 1, "PZ": 2, "CZ": 3}
+KIND = {"PX": 0, "PY": 1, "PZ": 2, "CZ": 3, "CX": 4, "CY": 5, "SQ": 6, "GQ": 7}  # mc_surface_kind
 BC = {"interior": 0, "vacuum": 1, "reflect": 2}
 SRC_POS = {"box": 0, "surface_x0": 1}
 SRC_DIR = {"iso": 0, "beam_x": 1, "cos_x": 2}
@@ -47,7 +47,7 @@ IP = C.POINTER(C.c_int)
 
 
 class mc_surface(C.Structure):
-    _fields_ = [("kind", C.c_int), ("coef", C.c_double * 3), ("bc", C.c_int)]
+    _fields_ = [("kind", C.c_int), ("coef", C.c_double * 10), ("bc", C.c_int)]
 
 
 class mc_cell(C.Structure):

@@ -312,6 +312,33 @@ def ellipsoid_absorber(a=1.0, b=0.6, c=1.5, sigma_t=1.0, angles=(0.0, 0.0, 0.0),
     return absorber_in_void((s, [(0, -1)]), sigma_t, point=tuple(float(v) for v in p0), name="ellipsoid")
 
 
+def quadric_assembly(seed=8, G=2, half=4.0):
+    """Scattering regions bounded by quadrics in a reflective box [-4, 4]^3: a sphere, a cylinder
+    along x from wall to wall, and a rotated ellipsoid (a general quadric), each with its own seeded
+    material, in a seeded background material; uniform source, steady state, a 4 x 4 x 4 mesh."""
+    rng = np.random.default_rng([seed, 4000])
+    mats = []
+    for _ in range(4):
+        st = rng.uniform(0.3, 1.5, G)
+        mats.append(material(st, seeded_scatter(rng, G, st, 0.5, 0.9)))
+    box, box_hs = box_surfaces((-half,) * 3, (half,) * 3, "reflect")
+    Q = ellipsoid_matrix(1.0, 0.6, 1.2, (0.5, 0.3, -0.8))
+    c0 = np.array([2.2, -0.5, -1.6])
+    g = -2.0 * Q @ c0
+    gq = [Q[0, 0], Q[1, 1], Q[2, 2], 2 * Q[0, 1], 2 * Q[1, 2], 2 * Q[0, 2], g[0], g[1], g[2], float(c0 @ Q @ c0) - 1.0]
+    surfs = box + [{"kind": "SQ", "coef": [-2.0, 0.5, -1.0, 1.5], "bc": "interior"},
+                   {"kind": "CX", "coef": [0.0, 2.6, 1.0], "bc": "interior"},
+                   {"kind": "GQ", "coef": [float(v) for v in gq], "bc": "interior"}]
+    sph, cyl, ell = 6, 7, 8
+    cells = [{"halfspaces": [(sph, -1)], "material": 0},
+             {"halfspaces": [(cyl, -1), box_hs[0], box_hs[1]], "material": 1},
+             {"halfspaces": [(ell, -1)], "material": 2},
+             {"halfspaces": box_hs + [(sph, +1), (cyl, +1), (ell, +1)], "material": 3}]
+    src = source("box", (-half,) * 3, (half,) * 3, "iso", G, 0)
+    tal = [mesh(x=np.linspace(-half, half, 5), y=np.linspace(-half, half, 5), z=np.linspace(-half, half, 5))]
+    return problem("quadrics", G, log_speeds(G), mats, surfs, cells, src, tal)
+
+
 def offspring_matrix(mat):
     """K[g][g'] = (sigma_s[g->g'] + nu sigma_f[g] chi[g']) / sigma_t[g] (mean offspring per
     collision); used only to scale the synthetic inputs."""
