@@ -19,6 +19,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mc_host.h"
 
 namespace mcgb {
@@ -452,6 +454,13 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
 // ------------------------------------------------------------------------------------------ ABI
 namespace mcgb {
 
+// NVTX range over a library call or a phase of it (visible to nsys / ncu when a tool is attached;
+// header-only, no cost otherwise)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 // the launch's census: the problem's t_census unless population control sets an interior one
 void set_census(RunParams& P, double t, bool interior) {
   P.has_census = std::isfinite(t) ? 1 : 0;
@@ -641,6 +650,7 @@ int run_population_controlled(mc_problem* p, const RunParams& P0, const std::vec
     return MC_OK;
   };
   for (int i = 0; i <= K; ++i) {
+    NvtxRange interval_range("census interval");
     RunParams Q = P0;
     Q.n_sources = i == 0 ? P0.n_sources : 0;
     set_census(Q, i < K ? census[i] : t_final, i < K);
@@ -688,6 +698,7 @@ int run_population_controlled(mc_problem* p, const RunParams& P0, const std::vec
 }
 
 int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts* opts, void* stream) {
+  NvtxRange nvtx_range("mc_run");
   g_err.clear();
   if (!p) return fail(MC_ERR_INVALID, "problem is NULL");
   mc_run_opts o;
@@ -827,6 +838,7 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
 int mc_run_eigen(mc_problem* p, uint64_t n_per_cycle, int n_inactive, int n_active, uint64_t seed,
                  const mc_run_opts* opts, void* stream, double* k_cycle, uint64_t* sites_cycle, double* k_mean,
                  double* k_std_err) {
+  NvtxRange nvtx_range("mc_run_eigen");
   g_err.clear();
   if (!p) return fail(MC_ERR_INVALID, "problem is NULL");
   mc_run_opts o;
@@ -914,6 +926,7 @@ int mc_run_eigen(mc_problem* p, uint64_t n_per_cycle, int n_inactive, int n_acti
   double k_prev = 1.0;
   CK(cudaEventRecord(p->ev[0], s));
   for (int c = 0; c < n_cycles; ++c) {
+    NvtxRange cycle_range(c < n_inactive ? "inactive cycle" : "active cycle");
     const double nm = std::floor(p->nu_max / k_prev * (1.0 + 1e-9)) + 2.0;
     if (!(nm <= 64.0)) return fail(MC_ERR_INVALID, "cycle %d: k = %g leaves more than 64 sites per history", c, k_prev);
     const uint32_t nmax = (uint32_t)nm;
@@ -1117,6 +1130,7 @@ int mc_tally_shape(const mc_problem* p, int tally_id, int64_t shape[5]) {
 }
 
 int mc_tally_get(mc_problem* p, int tally_id, double* mean, double* std_err, size_t n) {
+  NvtxRange nvtx_range("mc_tally_get");
   int64_t shp[5];
   int rc = mc_tally_shape(p, tally_id, shp);
   if (rc != MC_OK) return rc;

@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "MC_OK", -1: "MC_ERR_INVALID", -2: "MC_ERR_CUDA", -3: "MC_ERR
                 -4: "MC_ERR_BANK_FULL", -5: "MC_ERR_TIMEOUT", -6: "MC_ERR_STATE",
                 -7: "MC_ERR_LOST"}
 MAX_HALFSPACES = 16
+MAX_GROUPS, MAX_SURFACES, MAX_CELLS = 32, 255, 255  # MC_MAX_* of mc.h
 MC_FP32, MC_FP64 = 0, 1
 MC_TALLY_FIXED64, MC_TALLY_FP64 = 0, 1
 COUNTER_NAMES = ["source", "secondary", "capture", "production", "leak", "census", "lost",

@@ -76,3 +76,10 @@ def test_no_gpu_means_a_loud_error_not_a_fallback():
         mc.problem_create(P.config1())
     assert e.value.code in (mc.MC_ERR_CUDA, mc.MC_ERR_OOM)
     assert math.isfinite(len(str(e.value)))
+
+
+def test_binding_limits_match_the_header():
+    text = open(os.path.join(ROOT, "include", "mc.h")).read()
+    lim = {k: int(v) for k, v in re.findall(r"#define MC_MAX_(\w+) (\d+)", text)}
+    assert (lim["GROUPS"], lim["SURFACES"], lim["CELLS"], lim["HALFSPACES"]) == (
+        mc.MAX_GROUPS, mc.MAX_SURFACES, mc.MAX_CELLS, mc.MAX_HALFSPACES)
