@@ -61,6 +61,22 @@ def source_digest(kernel):
     return h.hexdigest()[:16]
 
 
+def profiled_value(summary, kernel, key):
+    """A number recorded in a committed ncu summary under profiles/ (`key: value`), or None when the
+    summary was taken on other kernel sources than these."""
+    import re
+    try:
+        with open(os.path.join(ROOT, "profiles", summary)) as f:
+            text = f.read()
+    except OSError:
+        return None
+    m = re.search(key + r":\s*([0-9.eE+]+)", text)
+    d = re.search(r"source_digest:\s*([0-9a-f]+)", text)
+    if m and d and d.group(1) == source_digest(kernel):
+        return float(m.group(1))
+    return None
+
+
 def profiled_traffic(summary, kernel):
     """DRAM bytes (read + write) per launch from a committed ncu summary under profiles/, or None
     when the summary was taken on other kernel sources than these."""
@@ -129,6 +145,22 @@ def oracle_batch_sample(probs, nh, threads, frac, seed):
         oracle.run(q, m, seed=seed + i, threads=threads)
         n1 += m
     return n1, time.perf_counter() - t0
+
+
+def issue_roofline(workload, n, flights, kernel_ms, clk):
+    """Instruction issue of the transport kernel against the issue peak of 152 SMs x 4 warp schedulers
+    x the SM clock seen during the timed region (one warp instruction per scheduler per clock): the
+    ceiling this latency-bound kernel actually meets.  The warp instructions per flight come from the
+    committed ncu summary of the same kernel sources (None when they changed)."""
+    per_flight = profiled_value(f"k_transport_{workload}_1e7.md", "k_transport", "warp_instructions_per_flight")
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    if per_flight is None or n != 10_000_000:
+        return None
+    achieved = per_flight * flights / (kernel_ms / 1000.0)
+    peak = 152 * 4 * mhz * 1e6
+    return {"bound": "issue", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "G warp instructions/s",
+            "frac": achieved / peak, "warp_instructions_per_flight": per_flight,
+            "peak_kind": "152 SMs x 4 schedulers x SM clock sampled during the timed region"}
 
 
 def launches_per_run(prob):
@@ -761,7 +793,8 @@ def main():
                      "l2_atomic": {"achieved": atom_rate / 1e9, "peak": atom_peak / 1e9,
                                    "unit": "G atomics/s", "frac": atom_rate / atom_peak,
                                    "scores_per_flight": c["scores"] / c["flight"],
-                                   "peak_kind": "measured live (mc_atomic_peak, random 64-bit adds)"}},
+                                   "peak_kind": "measured live (mc_atomic_peak, random 64-bit adds)"},
+                     "issue": issue_roofline(args.workload, n, c["flight"], tr_ms, clk)},
         "counters": {k: c[k] for k in ("flight", "collision", "surface", "census", "iterations")},
         "algorithm": algorithm,
         "trace": {"iterations": int(len(tr_t)), "history_style_iterations": int(tr_drain.sum()),
