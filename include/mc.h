@@ -172,7 +172,8 @@ typedef struct {
   int tally_mode;         /* mc_tally_mode: int64 fixed point (deterministic) or FP64 atomics */
   int fixed_bits;         /* fixed-point scale 2^fixed_bits (default 32) */
   int n_batches;          /* statistical batches, >= 2 (default 32) */
-  uint64_t bank_capacity; /* particles in flight (0 = library default) */
+  uint64_t bank_capacity; /* particles in flight (0 = library default: the power of two >= 2 x the
+                             histories, at most 2^22, or 2^28 with census_times) */
   int block_size;         /* threads per CTA (0 = autotuned default) */
   int blocks_per_sm;      /* CTAs per SM, counted in 256-thread CTAs (the cap is blocks_per_sm x
                              256 / block_size CTAs): 2 selects the 128-register build of the kernel

@@ -737,8 +737,11 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   const int lanes = fp64 ? kLanesFP64 : kLanesFP32;
   uint64_t cap = o.bank_capacity;
   if (cap == 0) {
+    // in flight a bank is refilled in chunks, so 2^22 suffices; with census times the census bank
+    // holds every particle alive at a census and the birth bank all their copies
+    const uint64_t limit = o.n_census > 0 ? (1ull << 28) : (1ull << 22);
     cap = 1ull << 16;
-    while (cap < 2 * n_histories && cap < (1ull << 22)) cap <<= 1;
+    while (cap < 2 * n_histories && cap < limit) cap <<= 1;
   }
   if (cap < 1024) return fail(MC_ERR_INVALID, "bank_capacity must be >= 1024");
   const size_t bank_bytes = (size_t)cap * 16 * lanes;

@@ -69,9 +69,9 @@ def test_pc_fp64_replays_the_oracle(torch):
 def test_pc_azurv1_fp32_closed_forms(torch):
     prob = P.azurv1()
     ct = np.arange(2.0, 20.0, 2.0)
-    n = 1_024_000
+    n = 4_096_000  # N e^{0.2} above 2^22 particles at every census: the default bank sizing
     p = mc.Problem(prob)
-    p.run(n, 92, n_batches=256, census_times=ct, bank_capacity=1 << 22)
+    p.run(n, 92, n_batches=256, census_times=ct)
     m, s = p.tally(0)
     z = exact_z(m, s, CF.infinite_time_bins(1.0, 0.6, 0.5, 1.0, prob["tallies"][0]["t"]))
     assert z.size >= 18 and np.all(np.abs(z) < 4), z
