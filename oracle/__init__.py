@@ -61,6 +61,7 @@ class OrProblem(C.Structure):
         ("has_lattice", C.c_int), ("lat_nx", C.c_int), ("lat_ny", C.c_int),
         ("lat_x0", C.c_double), ("lat_y0", C.c_double), ("lat_pitch", C.c_double),
         ("lat_r", C.c_double), ("lat_pin_mat", C.POINTER(C.c_int)), ("lat_matrix", C.c_int),
+        ("lat_nz", C.c_int), ("lat_z0", C.c_double), ("lat_pitch_z", C.c_double),
         ("src_pos", C.c_int), ("src_dir", C.c_int),
         ("src_lo", C.c_double * 3), ("src_hi", C.c_double * 3),
         ("src_group_pdf", C.POINTER(C.c_double)), ("src_t0", C.c_double), ("src_t1", C.c_double),
@@ -234,6 +235,8 @@ class Marshalled:
             s.lat_pitch, s.lat_r = lat["pitch"], lat["radius"]
             s.lat_pin_mat = ip(lat["pin_material"])
             s.lat_matrix = lat["matrix_material"]
+            s.lat_nz = lat.get("nz", 0)
+            s.lat_z0, s.lat_pitch_z = lat.get("z0", 0.0), lat.get("pitch_z", 0.0)
         else:
             s.has_lattice = 0
             s.lat_pin_mat = ip([0])

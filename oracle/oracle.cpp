@@ -10,7 +10,7 @@
 // Section 3) -- but prints no transport equations.  The steps here are textbook analog multigroup
 // Monte Carlo, in this order per flight:
 //   1. distance to collision  d_c = -ln(xi) / Sigma_t[m][g]
-//   2. distance to the nearest bounding surface d_s (planes, z-cylinders, lattice walls)
+//   2. distance to the nearest bounding surface d_s (planes, quadrics, lattice walls and pins)
 //   3. distance to census     d_t = v[g] (t_census - t)
 //   4. l = min(...), move, score w * l into the (x, y, z, g, t) mesh (track-length estimator)
 //   5. collision: scatter (g' by CDF of the Sigma_s row, isotropic), production
@@ -187,9 +187,9 @@ struct Prob {
   int n_cell;
   std::vector<int> nhs, hs_surf, hs_sense, cmat;
   bool lat;
-  int lnx, lny, lmatrix;
-  double lx0, ly0, lp, lr;
-  std::vector<int> lpin;
+  int lnx, lny, lnz, lmatrix;  // lnz = 1: one layer, unbounded in z (no z walls)
+  double lx0, ly0, lz0, lp, lpz, lr;
+  std::vector<int> lpin;       // [lnz][lny][lnx]
   int src_pos, src_dir;
   double src_lo[3], src_hi[3], t0, t1;
   std::vector<Tally> tallies;
@@ -269,7 +269,10 @@ Prob copy_problem(const or_problem* p) {
   P.lp = p->lat_pitch;
   P.lr = p->lat_r;
   P.lmatrix = p->lat_matrix;
-  if (P.lat) P.lpin.assign(p->lat_pin_mat, p->lat_pin_mat + P.lnx * P.lny);
+  P.lnz = p->lat_nz > 1 ? p->lat_nz : 1;
+  P.lz0 = p->lat_z0;
+  P.lpz = p->lat_pitch_z;
+  if (P.lat) P.lpin.assign(p->lat_pin_mat, p->lat_pin_mat + P.lnx * P.lny * P.lnz);
   P.src_pos = p->src_pos;
   P.src_dir = p->src_dir;
   for (int i = 0; i < 3; ++i) {
@@ -318,7 +321,7 @@ struct Particle {
   double x, y, z, ux, uy, uz, t, w;
   uint64_t tag, root;
   uint32_t k;
-  int g, cell, ix, iy, in_pin;
+  int g, cell, ix, iy, iz, in_pin;
 };
 
 // surface function f(p): plane x - c (or y, z); cylinder (x-x0)^2 + (y-y0)^2 - r^2
@@ -417,10 +420,13 @@ int find_cell(const Prob& P, double x, double y, double z, int skip_surf, int sk
   return -1;
 }
 
-bool has_pin(const Prob& P, int ix, int iy) { return P.lpin[iy * P.lnx + ix] >= 0; }
+// element (ix, iy, iz) of the lattice, z layer iz outermost
+int elem_index(const Prob& P, int ix, int iy, int iz) { return (iz * P.lny + iy) * P.lnx + ix; }
+
+bool has_pin(const Prob& P, const Particle& q) { return P.lpin[elem_index(P, q.ix, q.iy, q.iz)] >= 0; }
 
 int pin_sense_inside(const Prob& P, const Particle& q) {
-  if (!has_pin(P, q.ix, q.iy)) return 0;
+  if (!has_pin(P, q)) return 0;
   double xc = P.lx0 + (q.ix + 0.5) * P.lp, yc = P.ly0 + (q.iy + 0.5) * P.lp;
   double dx = q.x - xc, dy = q.y - yc;
   return (dx * dx + dy * dy - P.lr * P.lr) < 0.0 ? 1 : 0;
@@ -431,13 +437,18 @@ void lattice_locate(const Prob& P, Particle& q) {
   int iy = (int)std::floor((q.y - P.ly0) / P.lp);
   q.ix = std::min(std::max(ix, 0), P.lnx - 1);
   q.iy = std::min(std::max(iy, 0), P.lny - 1);
+  q.iz = 0;
+  if (P.lnz > 1) {
+    int iz = (int)std::floor((q.z - P.lz0) / P.lpz);
+    q.iz = std::min(std::max(iz, 0), P.lnz - 1);
+  }
   q.in_pin = pin_sense_inside(P, q);
 }
 
 int material(const Prob& P, const Particle& q) {
   int m = P.cmat[q.cell];
   if (m >= 0) return m;
-  if (q.in_pin) return P.lpin[q.iy * P.lnx + q.ix];
+  if (q.in_pin) return P.lpin[elem_index(P, q.ix, q.iy, q.iz)];
   return P.lmatrix;
 }
 
@@ -473,7 +484,7 @@ double dist_cyl(double x, double y, double ux, double uy, double x0, double y0, 
   return d > 0.0 ? d : 0.0;
 }
 
-enum { HIT_CELL = 0, HIT_LAT_X = 1, HIT_LAT_Y = 2, HIT_PIN = 3 };
+enum { HIT_CELL = 0, HIT_LAT_X = 1, HIT_LAT_Y = 2, HIT_PIN = 3, HIT_LAT_Z = 4 };
 struct Hit {
   double d;
   int type, idx;
@@ -522,7 +533,20 @@ Hit distance_to_boundary(const Prob& P, const Particle& q) {
       d = d > 0.0 ? d : 0.0;
       if (d < l.d) l = {d, HIT_LAT_Y, -1};
     }
-    if (has_pin(P, q.ix, q.iy)) {
+    if (P.lnz > 1) {
+      // axial layers: the z walls between them
+      double zlo = P.lz0 + q.iz * P.lpz;
+      if (q.uz > 0.0 && q.iz + 1 < P.lnz) {
+        double d = (zlo + P.lpz - q.z) / q.uz;
+        d = d > 0.0 ? d : 0.0;
+        if (d < l.d) l = {d, HIT_LAT_Z, +1};
+      } else if (q.uz < 0.0 && q.iz > 0) {
+        double d = (zlo - q.z) / q.uz;
+        d = d > 0.0 ? d : 0.0;
+        if (d < l.d) l = {d, HIT_LAT_Z, -1};
+      }
+    }
+    if (has_pin(P, q)) {
       double d = dist_cyl(q.x, q.y, q.ux, q.uy, xlo + 0.5 * P.lp, ylo + 0.5 * P.lp, P.lr,
                           q.in_pin != 0);
       if (d < l.d) l = {d, HIT_PIN, 0};
@@ -671,7 +695,7 @@ Particle source_particle(const Prob& P, uint64_t seed, uint64_t h) {
   q.w = 1.0;
   q.k = 0;
   q.cell = find_cell(P, q.x, q.y, q.z, -1, 0, 0.0, 0.0, 0.0);
-  q.ix = q.iy = q.in_pin = 0;
+  q.ix = q.iy = q.iz = q.in_pin = 0;
   if (q.cell >= 0 && P.cmat[q.cell] < 0) lattice_locate(P, q);
   return q;
 }
@@ -776,7 +800,7 @@ void transport(const Prob& P, const Physics& ph, uint64_t seed, Particle q, std:
       rec.k = k;
       rec.kind = ev;
       rec.cell = q.cell;
-      rec.elem = q.iy * (P.lat ? P.lnx : 0) + q.ix;
+      rec.elem = P.lat ? elem_index(P, q.ix, q.iy, q.iz) : q.ix;
       rec.in_pin = q.in_pin;
       rec.g = q.g;
       rec.x = q.x;
@@ -829,10 +853,11 @@ void transport(const Prob& P, const Physics& ph, uint64_t seed, Particle q, std:
             if (P.cmat[nc] < 0) lattice_locate(P, q);
           }
         }
-      } else if (hit.type == HIT_LAT_X || hit.type == HIT_LAT_Y) {
+      } else if (hit.type == HIT_LAT_X || hit.type == HIT_LAT_Y || hit.type == HIT_LAT_Z) {
         rec.outcome = 3;
         if (hit.type == HIT_LAT_X) q.ix += hit.idx;
-        else q.iy += hit.idx;
+        else if (hit.type == HIT_LAT_Y) q.iy += hit.idx;
+        else q.iz += hit.idx;
         q.in_pin = pin_sense_inside(P, q);
       } else {
         rec.outcome = 4;
@@ -1007,7 +1032,7 @@ Particle site_source(const Prob& P, uint64_t seed, uint64_t h, uint32_t cycle, c
   q.w = 1.0;
   q.k = 0;
   q.cell = find_cell(P, q.x, q.y, q.z, -1, 0, 0.0, 0.0, 0.0);
-  q.ix = q.iy = q.in_pin = 0;
+  q.ix = q.iy = q.iz = q.in_pin = 0;
   if (q.cell >= 0 && P.cmat[q.cell] < 0) lattice_locate(P, q);
   return q;
 }

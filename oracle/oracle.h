@@ -6,7 +6,8 @@
  * with the CUDA path; the two meet only in the seeded problem dicts.
  *
  * What it computes: the analog history-based random walk of the paper's Section 3 problem class
- * (fixed source, multigroup, quadric CSG of planes and z-cylinders plus a square pin lattice,
+ * (fixed source, multigroup, quadric CSG -- planes, cylinders, spheres, general quadrics -- plus
+ * a square pin lattice with optional axial layers,
  * time-dependent source, time census, track-length mesh tallies, secondary production), in FP64,
  * one history at a time, with the per-history variance of every tally bin.  Two variants the
  * paper's Section 3 runs use: the time-crossing estimator of the flux at time points (the
@@ -76,8 +77,10 @@ typedef struct {
   const int* cell_mat;     /* [n_cell], -1 = filled by the lattice */
   int has_lattice, lat_nx, lat_ny;
   double lat_x0, lat_y0, lat_pitch, lat_r;
-  const int* lat_pin_mat;  /* [ny][nx], -1 = no pin */
+  const int* lat_pin_mat;  /* [nz][ny][nx] (nz = 1 when lat_nz <= 1), -1 = no pin */
   int lat_matrix;
+  int lat_nz;              /* axial layers; <= 1: one layer, unbounded in z */
+  double lat_z0, lat_pitch_z;
   int src_pos, src_dir;
   double src_lo[3], src_hi[3];
   const double* src_group_pdf; /* [G] */

@@ -19,8 +19,10 @@ Problem dict layout (all lengths in cm, times in s, cross sections in 1/cm):
                sphere [x0, y0, z0, r]; general quadric [A..J] of
                A x^2 + B y^2 + C z^2 + D xy + E yz + F zx + G x + H y + I z + J
     cells:     list of {halfspaces: [(surface, +1|-1), ...], material: m (>=0) or -1 (lattice)}
-    lattice:   None or {nx, ny, x0, y0, pitch, radius, pin_material[ny*nx] (-1 = no pin),
-                        matrix_material}
+    lattice:   None or {nx, ny, x0, y0, pitch, radius, pin_material (-1 = no pin),
+                        matrix_material[, nz, z0, pitch_z]}: elements of side `pitch` holding a
+               z-cylinder pin; with nz >= 2 axial layers of height pitch_z from z0, pin_material
+               laid out [nz][ny][nx] (else [ny][nx], one layer unbounded in z)
     source:    {pos: 'box'|'surface_x0', lo[3], hi[3], dir: 'iso'|'beam_x'|'cos_x',
                 group_pdf[G], t0, t1}
     tallies:   list of {x: edges, y: edges, z: edges, t: edges, estimator: 'track'|'crossing'}
@@ -432,6 +434,123 @@ def config3(seed=3):
     3 seeded materials (two pin fills, one matrix), production scaled to spectral radius 0.9,
     uniform volumetric source, 34x34x7x50 space-group-time mesh."""
     return lattice_problem(seed=seed)
+
+
+def absorber_material(rng, G):
+    """A strong absorber (control-rod-like): Sigma_t in [1, 3], 10% scattering, downscatter only."""
+    sigma_t = rng.uniform(1.0, 3.0, G)
+    S = np.zeros((G, G))
+    for g in range(G):
+        S[g, g:] = 0.1 * sigma_t[g] * rng.dirichlet(np.ones(G - g))
+    return material(sigma_t, S)
+
+
+def axial_lattice(n=5, nz=6, pitch=1.26, pitch_z=2.0, radius=0.54, G=7, seed=9, n_rod_layers=2,
+                  n_tbins=20, bc_z="vacuum", name="axial"):
+    """3D lattice with axial zoning (a pin-lattice assembly in the shape of the paper's 3D C5G7
+    configurations; seeded synthetic cross sections, no C5G7 data): n x n elements of pitch `pitch`,
+    nz layers of height pitch_z.  Layer 0 is a bottom reflector (moderator only); layers 1..nz-2 hold
+    fuel pins of two seeded fissile materials; absorber rods at a seeded eighth of the positions fill
+    the top reflector layer and the top `n_rod_layers` fuel layers (partially inserted rods).
+    Reflective in x and y, `bc_z` at the bottom and top; source uniform in the fuel layers, group 0,
+    t = 0; mesh of one bin per element and layer over log-spaced time bins."""
+    rng = np.random.default_rng([seed, 4000])
+    mats = config3_materials(seed, G) + [absorber_material(rng, G)]  # fuel A, fuel B, moderator, rod
+    side, height = n * pitch, nz * pitch_z
+    surfs, hs = box_surfaces((0, 0, 0), (side, side, height), "reflect", axes=(0, 1))
+    zs, zhs = box_surfaces((0, 0, 0), (side, side, height), bc_z, axes=(2,))
+    surfs += zs
+    hs += [(i + 4, sn) for i, sn in zhs]
+    cells = [{"halfspaces": hs, "material": -1}]
+    fuel = rng.integers(0, 2, n * n)
+    rods = rng.uniform(size=n * n) < 0.125
+    pins = np.full((nz, n * n), -1, dtype=int)
+    for iz in range(1, nz - 1):
+        pins[iz] = fuel
+        if iz >= nz - 1 - n_rod_layers:
+            pins[iz][rods] = 3
+    pins[nz - 1][rods] = 3
+    lat = {"nx": n, "ny": n, "x0": 0.0, "y0": 0.0, "pitch": float(pitch), "radius": float(radius),
+           "pin_material": pins.ravel().tolist(), "matrix_material": 2,
+           "nz": nz, "z0": 0.0, "pitch_z": float(pitch_z)}
+    src = source("box", (0, 0, pitch_z), (side, side, height - pitch_z), "iso", G, 0)
+    t_edges = log_time_edges(n_tbins)
+    tal = [mesh(x=np.linspace(0, side, n + 1), y=np.linspace(0, side, n + 1),
+                z=np.linspace(0, height, nz + 1), t=t_edges)]
+    return problem(name, G, log_speeds(G), mats, surfs, cells, src, tal, t_edges[-1], lat)
+
+
+def lattice_absorber_3d(n=3, nz=3, pitch=1.0, pitch_z=1.0, radius=0.35, point=(1.3, 1.7, 1.2),
+                        sigma=(0.6, 1.5, 0.3), seed=10):
+    """Purely absorbing one-group 3D lattice (n x n elements, nz layers) with vacuum walls and an
+    isotropic point source at `point`: the leakage is the escape probability.  Matrix Sigma_t =
+    sigma[0]; each element of each layer holds a pin of Sigma_t sigma[1] or sigma[2] or none (seeded),
+    so the optical depth along a ray depends on the layer it passes through."""
+    rng = np.random.default_rng([seed, 5000])
+    mats = [material([v], [[0.0]]) for v in sigma]
+    side, height = n * pitch, nz * pitch_z
+    surfs, hs = box_surfaces((0, 0, 0), (side, side, height), "vacuum")
+    cells = [{"halfspaces": hs, "material": -1}]
+    pins = rng.choice([-1, 1, 2], size=nz * n * n).astype(int)
+    lat = {"nx": n, "ny": n, "x0": 0.0, "y0": 0.0, "pitch": float(pitch), "radius": float(radius),
+           "pin_material": pins.tolist(), "matrix_material": 0,
+           "nz": nz, "z0": 0.0, "pitch_z": float(pitch_z)}
+    src = source("box", point, point, "iso", 1)
+    tal = [mesh(x=(0, side), y=(0, side), z=(0, height))]
+    return problem("lattice3d_absorber", 1, [1.0], mats, surfs, cells, src, tal, INF, lat)
+
+
+def dogleg_duct(G=2, seed=11, L=40.0, w=8.0, n_tbins=10):
+    """Streaming through a dog-leg void duct in a shield (in the shape of the paper's Kobayashi
+    duct-streaming benchmark; seeded synthetic cross sections, no benchmark data).  The box [0, L]^3
+    is cut by planes into axis-aligned boxes, each one cell: the source block [0, w]^3, a duct leg
+    along x from the source block to x = L - w, a second leg along y up to y = L - w, and shield
+    elsewhere.  Reflective on x = 0, y = 0, z = 0 (a quarter model), vacuum on the far faces.
+    Source uniform in the source block, group 0, t = 0; a mesh along the duct and beside it."""
+    rng = np.random.default_rng([seed, 6000])
+    sigma_t = rng.uniform(0.3, 0.6, G)
+    shield = material(sigma_t, seeded_scatter(rng, G, sigma_t, 0.4, 0.6))
+    void = material(np.zeros(G), np.zeros((G, G)))
+    sigma_t = rng.uniform(0.2, 0.4, G)
+    src_mat = material(sigma_t, seeded_scatter(rng, G, sigma_t, 0.5, 0.7))
+    xs = [0.0, w, L - 2 * w, L - w, L]
+    ys = [0.0, w, L - w, L]
+    zs = [0.0, w, L]
+    surfs = []
+    ids = {}
+    for axis, kind, cuts in ((0, "PX", xs), (1, "PY", ys), (2, "PZ", zs)):
+        for j, c in enumerate(cuts):
+            bc = "interior"
+            if j == 0:
+                bc = "reflect"
+            elif j == len(cuts) - 1:
+                bc = "vacuum"
+            ids[(axis, j)] = len(surfs)
+            surfs.append({"kind": kind, "coef": [float(c)], "bc": bc})
+
+    def region(ix, iy, iz):
+        if iz != 0:
+            return 0
+        if ix == 0 and iy == 0:
+            return 2  # source block
+        if iy == 0 and ix in (1, 2):
+            return 1  # first leg along x
+        if ix == 2 and iy == 1:
+            return 1  # second leg along y
+        return 0
+
+    cells = []
+    for iz in range(len(zs) - 1):
+        for iy in range(len(ys) - 1):
+            for ix in range(len(xs) - 1):
+                hs = [(ids[(0, ix)], +1), (ids[(0, ix + 1)], -1), (ids[(1, iy)], +1),
+                      (ids[(1, iy + 1)], -1), (ids[(2, iz)], +1), (ids[(2, iz + 1)], -1)]
+                cells.append({"halfspaces": hs, "material": region(ix, iy, iz)})
+    src = source("box", (0, 0, 0), (w, w, w), "iso", G, 0)
+    v = log_speeds(G)
+    t_edges = np.concatenate([[0.0], np.logspace(-8, -5, n_tbins)])
+    tal = [mesh(x=xs, y=np.linspace(0, L, 11), z=(0, w, L), t=t_edges)]
+    return problem("dogleg", G, v, [shield, void, src_mat], surfs, cells, src, tal, t_edges[-1])
 
 
 def config4_materials(seed=4, G=7, n_mat=4):
