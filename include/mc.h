@@ -3,7 +3,8 @@
  *
  * The library implements the transport method whose problem class the MC/DC paper states in
  * its Section 3: fixed-source multigroup transport on quadric-surface constructive solid geometry
- * (here planes x/y/z, z-cylinders and a square pin lattice), a time-dependent source, a time
+ * (planes, cylinders, spheres, general quadrics and a pin lattice with optional axial layers), a
+ * time-dependent source, a time
  * census and time-dependent mesh tallies scored with the track-length estimator (Section 3.1) or
  * the time-crossing estimator, with analog collisions or implicit capture (Section 3's runs).
  * Per particle the walk samples the distance to collision, compares it with the distance to the
@@ -51,6 +52,7 @@ typedef enum {
 #define MC_MAX_CELLS 255
 #define MC_MAX_HALFSPACES 16
 #define MC_MAX_LATTICE 255 /* per axis */
+#define MC_MAX_LATTICE_ELEMENTS 65536 /* nx x ny x max(nz, 1) */
 #define MC_MAX_TALLIES 4
 
 /* ------------------------------------------------------------------------- geometry */
@@ -85,14 +87,21 @@ typedef struct {
   int material;
 } mc_cell;
 
-/* Square lattice of nx x ny elements of side `pitch`, lower-left corner (x0, y0); element (i, j)
- * holds a z-cylinder of `radius` centred in it filled with pin_material[j*nx + i] (or no pin if
- * that entry is -1) inside matrix_material. */
+/* Square pin lattice (the paper's lattice geometry, Section 3): nx x ny elements of side `pitch`,
+ * lower-left corner (x0, y0).  With nz >= 2 it has nz axial layers of height pitch_z stacked from
+ * z0 (a 3D lattice: axially zoned assemblies, partially inserted rods); with nz = 0 or 1 it is one
+ * layer, unbounded in z.  Element (i, j, k) holds a z-cylinder of `radius` centred in it, filled with
+ * pin_material[(k*ny + j)*nx + i] (no pin if that entry is -1), inside matrix_material.  The lattice
+ * fills the cells whose material is -1 and must cover their extent exactly (its outer walls are
+ * the cells' own surfaces).  nx, ny, nz <= MC_MAX_LATTICE and nx*ny*max(nz,1) <= 65536; invalid
+ * sizes, pitches or materials make mc_problem_create return MC_ERR_INVALID. */
 typedef struct {
   int nx, ny;
   double x0, y0, pitch, radius;
-  const int* pin_material; /* [ny*nx] */
+  const int* pin_material; /* [max(nz,1)][ny][nx] */
   int matrix_material;
+  int nz;                  /* axial layers (0 or 1: one layer, unbounded in z) */
+  double z0, pitch_z;      /* bottom of layer 0 and the layer height (used when nz >= 2) */
 } mc_lattice;
 
 /* ------------------------------------------------------------------------- source */

@@ -202,16 +202,22 @@ int validate(const mc_problem_desc* d) {
     if (C.material == -1) uses_lattice = true;
     else if (C.material < 0 || C.material >= M) return fail(MC_ERR_INVALID, "cell %d: bad material", c);
   }
-  if (uses_lattice) {
+  if (uses_lattice || d->lattice) {
     const mc_lattice* L = d->lattice;
     if (!L) return fail(MC_ERR_INVALID, "a cell uses the lattice but no lattice is given");
-    if (L->nx < 1 || L->ny < 1 || L->nx > MC_MAX_LATTICE || L->ny > MC_MAX_LATTICE)
-      return fail(MC_ERR_INVALID, "lattice size outside [1,%d]", MC_MAX_LATTICE);
+    if (L->nx < 1 || L->ny < 1 || L->nx > MC_MAX_LATTICE || L->ny > MC_MAX_LATTICE || L->nz < 0 ||
+        L->nz > MC_MAX_LATTICE)
+      return fail(MC_ERR_INVALID, "lattice size outside [1,%d] (nz in [0,%d])", MC_MAX_LATTICE, MC_MAX_LATTICE);
+    const int nz = L->nz > 1 ? L->nz : 1;
+    if (L->nx * L->ny * nz > MC_MAX_LATTICE_ELEMENTS)
+      return fail(MC_ERR_INVALID, "lattice has more than %d elements", MC_MAX_LATTICE_ELEMENTS);
     if (!(L->pitch > 0.0) || !(L->radius > 0.0) || !(2.0 * L->radius < L->pitch) || !std::isfinite(L->x0) ||
         !std::isfinite(L->y0))
       return fail(MC_ERR_INVALID, "lattice needs pitch > 2 radius > 0");
+    if (nz > 1 && (!(L->pitch_z > 0.0) || !std::isfinite(L->pitch_z) || !std::isfinite(L->z0)))
+      return fail(MC_ERR_INVALID, "an axially layered lattice needs a finite z0 and pitch_z > 0");
     if (!L->pin_material) return fail(MC_ERR_INVALID, "lattice pin_material is NULL");
-    for (int i = 0; i < L->nx * L->ny; ++i)
+    for (int i = 0; i < L->nx * L->ny * nz; ++i)
       if (L->pin_material[i] < -1 || L->pin_material[i] >= M) return fail(MC_ERR_INVALID, "lattice pin %d: bad material", i);
     if (L->matrix_material < 0 || L->matrix_material >= M) return fail(MC_ERR_INVALID, "lattice matrix material");
   }
@@ -406,10 +412,17 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
     H.lat_y0 = L->y0;
     H.lat_pitch = L->pitch;
     H.lat_r = L->radius;
-    std::vector<int> pins(L->pin_material, L->pin_material + L->nx * L->ny);
+    H.lat_nz = L->nz > 1 ? L->nz : 1;
+    H.lat_z0 = H.lat_nz > 1 ? L->z0 : 0.0;
+    H.lat_pz = H.lat_nz > 1 ? L->pitch_z : 1.0;
+    H.lat_mx = ((1ull << 32) + (unsigned long long)L->nx - 1) / (unsigned long long)L->nx;
+    H.lat_my = ((1ull << 32) + (unsigned long long)L->ny - 1) / (unsigned long long)L->ny;
+    std::vector<int> pins(L->pin_material, L->pin_material + L->nx * L->ny * H.lat_nz);
     H.o_lpin = B.put(pins);
   } else {
     H.has_lat = 0;
+    H.lat_nz = 1;
+    H.lat_mx = H.lat_my = 1ull << 32;
     std::vector<int> none(1, -1);
     H.o_lpin = B.put(none);
   }

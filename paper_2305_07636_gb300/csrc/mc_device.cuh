@@ -99,7 +99,7 @@ struct Tab {
   const TableHeader* h;
   const R *st, *ss, *ssf, *nu, *nusf, *v, *inv_v, *scdf, *chi, *src_cdf, *scoef;
   const int *skind, *sbc, *nhs, *hs, *cmat, *lpin;
-  R lx0, ly0, lp, lr;
+  R lx0, ly0, lp, lr, lz0, lpz;
   int G;
   __device__ explicit Tab(const char* base) {
     h = reinterpret_cast<const TableHeader*>(base);
@@ -124,6 +124,8 @@ struct Tab {
     ly0 = (R)h->lat_y0;
     lp = (R)h->lat_pitch;
     lr = (R)h->lat_r;
+    lz0 = (R)h->lat_z0;
+    lpz = (R)h->lat_pz;
     G = h->G;
   }
 };
@@ -322,17 +324,27 @@ __device__ __forceinline__ long long float_to_fixed(float f) {
 }
 
 // ------------------------------------------------------------------------------------------ geometry
-__device__ __forceinline__ int lat_ix(uint32_t elem) { return (int)(elem & 0xFFu); }
-__device__ __forceinline__ int lat_iy(uint32_t elem) { return (int)((elem >> 8) & 0xFFu); }
-__device__ __forceinline__ uint32_t lat_pack(uint32_t elem, int ix, int iy) {
-  return (elem & 0xFFFF0000u) | (uint32_t)ix | ((uint32_t)iy << 8);
+// lattice element index e = (iz ny + iy) nx + ix in the low 16 bits of the elem word
+__device__ __forceinline__ uint32_t lat_e(uint32_t elem) { return elem & 0xFFFFu; }
+__device__ __forceinline__ uint32_t lat_pack(uint32_t elem, uint32_t e) { return (elem & 0xFFFF0000u) | e; }
+
+struct LatIdx {
+  int ix, iy, iz;
+};
+// (ix, iy, iz) of element e: n / d = floor(n ceil(2^32 / d) / 2^32) exactly for n < 2^16 and
+// d <= 2^16 (the rounding-up error of the reciprocal adds less than n / 2^32 < 1 / d)
+template <typename R>
+__device__ __forceinline__ LatIdx lat_split(const Tab<R>& T, uint32_t e) {
+  const uint32_t q = (uint32_t)(((unsigned long long)e * T.h->lat_mx) >> 32);
+  const uint32_t iz = (uint32_t)(((unsigned long long)q * T.h->lat_my) >> 32);
+  return {(int)(e - q * (uint32_t)T.h->lat_nx), (int)(q - iz * (uint32_t)T.h->lat_ny), (int)iz};
 }
 
 template <typename R>
 __device__ __forceinline__ int material_of(const Tab<R>& T, uint32_t pk, uint32_t elem) {
   const int m = T.cmat[pk_cell(pk)];
   if (m >= 0) return m;
-  if (pk_pin(pk)) return T.lpin[lat_iy(elem) * T.h->lat_nx + lat_ix(elem)];
+  if (pk_pin(pk)) return T.lpin[lat_e(elem)];
   return T.h->lat_matrix;
 }
 
@@ -513,8 +525,8 @@ __device__ int locate_cell(const Tab<R>& T, R x, R y, R z, int skip, int skip_se
 }
 
 template <typename R>
-__device__ __forceinline__ uint32_t pin_inside(const Tab<R>& T, R x, R y, int ix, int iy) {
-  if (T.lpin[iy * T.h->lat_nx + ix] < 0) return 0u;
+__device__ __forceinline__ uint32_t pin_inside(const Tab<R>& T, R x, R y, int ix, int iy, uint32_t e) {
+  if (T.lpin[e] < 0) return 0u;
   const R dx = x - (T.lx0 + (R(ix) + R(0.5)) * T.lp), dy = y - (T.ly0 + (R(iy) + R(0.5)) * T.lp);
   return (dx * dx + dy * dy - T.lr * T.lr) < R(0) ? 1u : 0u;
 }
@@ -522,11 +534,16 @@ __device__ __forceinline__ uint32_t pin_inside(const Tab<R>& T, R x, R y, int ix
 // lattice element and pin sense of a point inside the lattice cell
 template <typename R>
 __device__ __forceinline__ void lattice_locate(const Tab<R>& T, Part<R>& p) {
-  int ix = (int)floor((p.x - T.lx0) / T.lp), iy = (int)floor((p.y - T.ly0) / T.lp);
+  int ix = (int)floor((p.x - T.lx0) / T.lp), iy = (int)floor((p.y - T.ly0) / T.lp), iz = 0;
   ix = min(max(ix, 0), T.h->lat_nx - 1);
   iy = min(max(iy, 0), T.h->lat_ny - 1);
-  p.elem = lat_pack(p.elem, ix, iy);
-  p.pk = (p.pk & ~(1u << 13)) | (pin_inside(T, p.x, p.y, ix, iy) << 13);
+  if (T.h->lat_nz > 1) {
+    iz = (int)floor((p.z - T.lz0) / T.lpz);
+    iz = min(max(iz, 0), T.h->lat_nz - 1);
+  }
+  const uint32_t e = (uint32_t)((iz * T.h->lat_ny + iy) * T.h->lat_nx + ix);
+  p.elem = lat_pack(p.elem, e);
+  p.pk = (p.pk & ~(1u << 13)) | (pin_inside(T, p.x, p.y, ix, iy, e) << 13);
 }
 
 struct Hit {
@@ -565,30 +582,45 @@ __device__ R boundary_distance(const Tab<R>& T, const Part<R>& p, Hit& hit) {
     }
   }
   if (T.cmat[c] < 0) {
-    // lattice: inner element walls in the direction of motion, then the pin
-    const int ix = lat_ix(p.elem), iy = lat_iy(p.elem);
+    // lattice: inner element walls in the direction of motion (x, y, then z between axial
+    // layers), then the pin; the hit's surf field carries the wall's axis
+    const uint32_t e = lat_e(p.elem);
+    const LatIdx L = lat_split(T, e);
+    const int ix = L.ix, iy = L.iy;
     const R xlo = T.lx0 + R(ix) * T.lp, ylo = T.ly0 + R(iy) * T.lp;
     R lbest = rinf<R>();
-    Hit lh = {HIT_LAT_X, 1, 0};
+    Hit lh = {HIT_LAT, 1, 0};
     if (p.ux > R(0) && ix + 1 < T.h->lat_nx) {
       R d = rdiv(xlo + T.lp - p.x, p.ux);
       d = d > R(0) ? d : R(0);
-      if (d < lbest) { lbest = d; lh = {HIT_LAT_X, 1, 0}; }
+      if (d < lbest) { lbest = d; lh = {HIT_LAT, 1, 0}; }
     } else if (p.ux < R(0) && ix > 0) {
       R d = rdiv(xlo - p.x, p.ux);
       d = d > R(0) ? d : R(0);
-      if (d < lbest) { lbest = d; lh = {HIT_LAT_X, -1, 0}; }
+      if (d < lbest) { lbest = d; lh = {HIT_LAT, -1, 0}; }
     }
     if (p.uy > R(0) && iy + 1 < T.h->lat_ny) {
       R d = rdiv(ylo + T.lp - p.y, p.uy);
       d = d > R(0) ? d : R(0);
-      if (d < lbest) { lbest = d; lh = {HIT_LAT_Y, 1, 0}; }
+      if (d < lbest) { lbest = d; lh = {HIT_LAT, 1, 1}; }
     } else if (p.uy < R(0) && iy > 0) {
       R d = rdiv(ylo - p.y, p.uy);
       d = d > R(0) ? d : R(0);
-      if (d < lbest) { lbest = d; lh = {HIT_LAT_Y, -1, 0}; }
+      if (d < lbest) { lbest = d; lh = {HIT_LAT, -1, 1}; }
     }
-    if (T.lpin[iy * T.h->lat_nx + ix] >= 0) {
+    if (T.h->lat_nz > 1) {
+      const R zlo = T.lz0 + R(L.iz) * T.lpz;
+      if (p.uz > R(0) && L.iz + 1 < T.h->lat_nz) {
+        R d = rdiv(zlo + T.lpz - p.z, p.uz);
+        d = d > R(0) ? d : R(0);
+        if (d < lbest) { lbest = d; lh = {HIT_LAT, 1, 2}; }
+      } else if (p.uz < R(0) && L.iz > 0) {
+        R d = rdiv(zlo - p.z, p.uz);
+        d = d > R(0) ? d : R(0);
+        if (d < lbest) { lbest = d; lh = {HIT_LAT, -1, 2}; }
+      }
+    }
+    if (T.lpin[e] >= 0) {
       const R d = cyl_dist(p.x, p.y, p.ux, p.uy, xlo + R(0.5) * T.lp, ylo + R(0.5) * T.lp, T.lr,
                            pk_pin(p.pk) != 0);
       if (d < lbest) { lbest = d; lh = {HIT_PIN, 1, 0}; }

@@ -72,7 +72,7 @@ __device__ void log_event(const RunParams& P, const Tab<R>& T, const Part<R>& p,
   e.outcome = outcome;
   e.n_child = n_child;
   e.cell = (int)pk_cell(p.pk);
-  e.elem = T.h->has_lat ? lat_iy(p.elem) * T.h->lat_nx + lat_ix(p.elem) : 0;
+  e.elem = T.h->has_lat ? lat_e(p.elem) : 0;
   e.in_pin = (int)pk_pin(p.pk);
   e.g = (int)pk_g(p.pk);
   e.x = p.x; e.y = p.y; e.z = p.z;
@@ -295,11 +295,13 @@ __device__ bool do_surface(const RunParams& P, const Tab<R>& T, Part<R>& p, uint
     p.pk ^= (1u << 13);
   } else {
     log_event(P, T, p, 1, 3, 0);
-    int ix = lat_ix(p.elem), iy = lat_iy(p.elem);
-    if (hit == HIT_LAT_X) ix += pk_dir(p.pk);
-    else iy += pk_dir(p.pk);
-    p.elem = lat_pack(p.elem, ix, iy);
-    p.pk = (p.pk & ~(1u << 13)) | (pin_inside(T, p.x, p.y, ix, iy) << 13);
+    // a lattice wall: the next element along the wall's axis (strides 1, nx, nx ny)
+    const uint32_t axis = pk_surf(p.pk);
+    const int stride = axis == 0 ? 1 : (axis == 1 ? T.h->lat_nx : T.h->lat_nx * T.h->lat_ny);
+    const uint32_t e = (uint32_t)((int)lat_e(p.elem) + pk_dir(p.pk) * stride);
+    p.elem = lat_pack(p.elem, e);
+    const LatIdx L = lat_split(T, e);
+    p.pk = (p.pk & ~(1u << 13)) | (pin_inside(T, p.x, p.y, L.ix, L.iy, e) << 13);
   }
   return weight_window(P, T, p, Bout, bcount, bc);
 }

@@ -17,19 +17,19 @@ constexpr uint32_t kChildMark = 0x80000000u;
 constexpr uint32_t kSplitMark = 0xC0000000u;
 constexpr uint32_t kChildKeyXor = 0xA5A5A5A5u;
 
-// ---- `elem` word: bits 0-7 lattice x index, 8-15 lattice y index, 16-31 statistical batch
+// ---- `elem` word: bits 0-15 lattice element (iz ny + iy) nx + ix, 16-31 statistical batch
 // ---- packed per-particle word (lane 3 .w in FP32, lane 4 .w in FP64)
 //   bits 0-4   group (G <= 32)
 //   bits 5-12  cell index
 //   bit  13    inside the pin of the current lattice element
 //   bits 14-15 pending event: 0 none (needs a flight), 1 collision, 2 surface
-//   bits 16-17 surface hit type: 0 cell surface, 1 lattice x wall, 2 lattice y wall, 3 pin
+//   bits 16-17 surface hit type: 0 cell surface, 1 lattice wall, 3 pin
 //   bit  18    lattice wall direction (1 = +1, 0 = -1)
-//   bits 19-26 index of the crossed cell surface
+//   bits 19-26 index of the crossed cell surface, or the axis of the crossed lattice wall (0 x, 1 y, 2 z)
 //   bits 27-28 channel of a pending collision (drawn with the flight): 0 scatter, 1 production
 enum : uint32_t { PEND_NONE = 0, PEND_COLL = 1, PEND_SURF = 2 };
 enum : uint32_t { CHAN_SCATTER = 0, CHAN_PRODUCTION = 1, CHAN_CAPTURE = 2 };
-enum : uint32_t { HIT_CELL = 0, HIT_LAT_X = 1, HIT_LAT_Y = 2, HIT_PIN = 3 };
+enum : uint32_t { HIT_CELL = 0, HIT_LAT = 1, HIT_PIN = 3 };
 
 __host__ __device__ inline uint32_t pk_g(uint32_t w) { return w & 0x1Fu; }
 __host__ __device__ inline uint32_t pk_cell(uint32_t w) { return (w >> 5) & 0xFFu; }
@@ -77,15 +77,17 @@ struct TableHeader {
   double t_census;
   double src_lo[3], src_hi[3], src_t0, src_t1;
   double lat_x0, lat_y0, lat_pitch, lat_r;
+  double lat_z0, lat_pz;                  // axial layers (lat_nz >= 2): bottom and height
+  unsigned long long lat_mx, lat_my;      // ceil(2^32 / nx), ceil(2^32 / ny): element index division
   // float copies for FP32 tracking (no double->float conversion on the device)
   float src_lo_f[4], src_hi_f[4];
   float src_t0_f, src_t1_f, tc_hi, tc_lo;  // census time as the float pair hi + lo
-  int has_census, pad5, pad6, pad7;
+  int has_census, lat_nz, pad6, pad7;  // lat_nz: axial layers (1: one layer, unbounded in z)
   // byte offsets
   int o_st, o_ss, o_ssf, o_nu;        // [M][G] Real: sigma_t, scatter threshold, scatter+production threshold, nu
   int o_v, o_inv_v, o_scdf, o_chi;    // [G] Real speed, 1/speed; [M][G][G] scatter CDF; [M][G] chi CDF
   int o_src_cdf, o_skind, o_sbc, o_scoef;  // [G] Real; [n_surf] int; [n_surf] int; [n_surf][16] Real
-  int o_nhs, o_hs, o_cmat, o_lpin;    // [n_cell] int; [n_cell][16] int (surf | sense<<16); [n_cell] int; [ny*nx] int
+  int o_nhs, o_hs, o_cmat, o_lpin;    // [n_cell] int; [n_cell][16] int (surf | sense<<16); [n_cell] int; [nz][ny][nx] int
   TallyDesc tally[kMaxTallies];
   int blob_bytes, o_nusf, pad3, pad4;  // o_nusf: [M][G] Real nu Sigma_f (k-eigenvalue estimator)
 };

@@ -24,6 +24,7 @@ STATUS_NAMES = {0: "MC_OK", -1: "MC_ERR_INVALID", -2: "MC_ERR_CUDA", -3: "MC_ERR
                 -7: "MC_ERR_LOST"}
 MAX_HALFSPACES = 16
 MAX_GROUPS, MAX_SURFACES, MAX_CELLS = 32, 255, 255  # MC_MAX_* of mc.h
+MAX_LATTICE, MAX_LATTICE_ELEMENTS = 255, 65536
 MC_FP32, MC_FP64 = 0, 1
 MC_TALLY_FIXED64, MC_TALLY_FP64 = 0, 1
 COUNTER_NAMES = ["source", "secondary", "capture", "production", "leak", "census", "lost",
@@ -59,7 +60,7 @@ class mc_cell(C.Structure):
 class mc_lattice(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("x0", C.c_double), ("y0", C.c_double),
                 ("pitch", C.c_double), ("radius", C.c_double), ("pin_material", IP),
-                ("matrix_material", C.c_int)]
+                ("matrix_material", C.c_int), ("nz", C.c_int), ("z0", C.c_double), ("pitch_z", C.c_double)]
 
 
 class mc_source(C.Structure):
@@ -264,6 +265,7 @@ class _Desc:
             L.x0, L.y0, L.pitch, L.radius = lat["x0"], lat["y0"], lat["pitch"], lat["radius"]
             L.pin_material = ip(lat["pin_material"])
             L.matrix_material = lat["matrix_material"]
+            L.nz, L.z0, L.pitch_z = lat.get("nz", 0), lat.get("z0", 0.0), lat.get("pitch_z", 0.0)
             self.keep.append(L)
             d.lattice = C.pointer(L)
         src = prob["source"]

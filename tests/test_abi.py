@@ -83,3 +83,14 @@ def test_binding_limits_match_the_header():
     lim = {k: int(v) for k, v in re.findall(r"#define MC_MAX_(\w+) (\d+)", text)}
     assert (lim["GROUPS"], lim["SURFACES"], lim["CELLS"], lim["HALFSPACES"]) == (
         mc.MAX_GROUPS, mc.MAX_SURFACES, mc.MAX_CELLS, mc.MAX_HALFSPACES)
+    assert (lim["LATTICE"], lim["LATTICE_ELEMENTS"]) == (mc.MAX_LATTICE, mc.MAX_LATTICE_ELEMENTS)
+
+
+def test_lattice_index_division_by_reciprocal():
+    """The device splits a lattice element index e < 2^16 into (ix, iy, iz) with n / d =
+    floor(n * ceil(2^32 / d) / 2^32): exact for every divisor an axis can have and every index."""
+    import numpy as np
+    n = np.arange(mc.MAX_LATTICE_ELEMENTS, dtype=np.uint64)
+    for d in range(1, mc.MAX_LATTICE + 1):
+        m = np.uint64(((1 << 32) + d - 1) // d)
+        assert np.array_equal((n * m) >> np.uint64(32), n // np.uint64(d)), d
