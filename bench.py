@@ -40,7 +40,7 @@ BYTES_PER_FLIGHT = 136  # 64 B state read + 64 B state write + 8 B tally update 
 
 KERNEL_SOURCES = {
     "k_transport": ["mc_transport.cu", "mc_events.cuh", "mc_device.cuh", "mc_internal.h"],
-    "k_transport_batch": ["mc_batch.cu", "mc_events.cuh", "mc_device.cuh", "mc_internal.h", "mc_host.h"],
+    "k_transport_batch": ["mc_batch.cu", "mc_events.cuh", "mc_device.cuh", "mc_internal.h"],
 }
 
 
@@ -708,7 +708,8 @@ def main():
         # the kernel configuration for this problem, picked by the library's autotuner (untimed)
         t_opts, tune_ms = mc.run_tune(p.h, n, seed, opts, stream)
         tuned = {"block_size": t_opts.block_size, "blocks_per_sm": t_opts.blocks_per_sm,
-                 "algorithm": ["event", "history"][t_opts.algorithm], "candidate_ms": tune_ms}
+                 "algorithm": ["event", "history"][t_opts.algorithm],
+                 "drain_threshold": t_opts.drain_threshold or "default", "candidate_ms": tune_ms}
     algorithm = tuned["algorithm"] if tuned and args.algorithm == "auto" else (
         "event" if args.algorithm == "auto" else args.algorithm)
     for w in range(args.warmup):

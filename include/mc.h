@@ -304,10 +304,12 @@ int mc_run_eigen(mc_problem* p, uint64_t n_per_cycle, int n_inactive, int n_acti
 /* Autotuner of mc_run for one problem: runs n_histories with each candidate configuration (256 or
  * 128 threads per CTA; the 80-register build at 3 CTAs of 256 per SM, or the 128-register build at
  * 2; with opts->algorithm == MC_ALG_AUTO each under both algorithms), times each run with CUDA
- * events (best of two after a warm-up) and stores the fastest in the problem; later mc_run calls
- * on it whose block_size and blocks_per_sm are both 0 use it, and those with MC_ALG_AUTO its
- * algorithm.  tuned (nullable) receives a copy of opts with those fields set, best_ms (nullable)
- * its time.
+ * events (best of two after a warm-up) and stores the fastest in the problem.  When the fastest is
+ * event-based and opts->drain_threshold is 0, drain thresholds of 16 and 64 times the default
+ * (twice the resident threads) are timed at that configuration as well.  Later mc_run calls on the
+ * problem whose block_size and blocks_per_sm are both 0 use the stored configuration (and its drain
+ * threshold when theirs is 0), those with MC_ALG_AUTO its algorithm.  tuned (nullable) receives a
+ * copy of opts with those fields set (drain_threshold 0 = the default), best_ms (nullable) its time.
  * Synchronises; the tallies left behind are those of the last candidate. */
 int mc_run_tune(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts* opts, void* stream,
                 mc_run_opts* tuned, double* best_ms);

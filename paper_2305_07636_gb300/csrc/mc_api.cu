@@ -720,6 +720,7 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   if (o.block_size == 0 && o.blocks_per_sm == 0 && p->tuned_block) {
     o.block_size = p->tuned_block;  // the configuration mc_run_tune found for this problem
     o.blocks_per_sm = p->tuned_bps;
+    if (o.drain_threshold == 0) o.drain_threshold = p->tuned_drain;
   }
   if (o.algorithm == MC_ALG_AUTO) o.algorithm = p->tuned_alg;  // event-based until tuned
   if (o.precision != MC_FP32 && o.precision != MC_FP64) return fail(MC_ERR_INVALID, "precision");
@@ -1065,6 +1066,7 @@ int mc_run_tune(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run
   float best_t = 0.f;
   const int cands[4][2] = {{256, 0}, {256, 2}, {128, 0}, {128, 2}};  // 80- / 128-register builds
   p->tuned_block = 0;
+  p->tuned_drain = 0;
   // MC_ALG_AUTO: both algorithms are candidates (their results are identical)
   const int n_alg = o.algorithm == MC_ALG_AUTO ? 2 : 1;
   for (int c = 0; c < 4 * n_alg && rc == MC_OK; ++c) {
@@ -1093,17 +1095,54 @@ int mc_run_tune(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run
       best_t = t;
     }
   }
+  // Event mode: when the run turns history-style (the drain threshold) is a candidate too, at the
+  // chosen configuration.  Turning early saves grid barriers and bank round trips where histories
+  // are short and alike, and costs where they are long and uneven (lattices with production, a
+  // supercritical medium), so the default (twice the resident threads) and 16x / 64x of it are timed.
+  uint64_t best_drain = 0;
+  int sms = 0;
+  if (rc == MC_OK && best_alg == MC_ALG_EVENT && o.drain_threshold == 0) {
+    ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->dev);
+    if (ce != cudaSuccess) rc = cuda_fail(ce, "cudaDeviceGetAttribute");
+  }
+  for (int mult : {16, 64}) {
+    if (rc != MC_OK || sms == 0) break;
+    mc_run_opts k = o;
+    k.algorithm = MC_ALG_EVENT;
+    k.block_size = best_block;
+    k.blocks_per_sm = best_bps;
+    k.drain_threshold = (uint64_t)mult * 2ull * (uint64_t)sms * (uint64_t)best_bps * 256ull;
+    rc = mc_run(p, n_histories, seed, &k, stream);  // warm-up
+    float t = -1.f;
+    for (int rep = 0; rep < 2 && rc == MC_OK; ++rep) {
+      ce = cudaEventRecord(e0, s);
+      if (ce == cudaSuccess) rc = mc_run(p, n_histories, seed, &k, stream);
+      if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+      if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+      if (ce != cudaSuccess && rc == MC_OK) rc = cuda_fail(ce, "timing a candidate");
+      if (t < 0.f || ms < t) t = ms;
+    }
+    if (rc == MC_OK) rc = mc_wait(p);
+    if (rc == MC_OK && t < best_t) {
+      best_drain = k.drain_threshold;
+      best_t = t;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != MC_OK) return rc;
   p->tuned_block = best_block;
   p->tuned_bps = best_bps;
   p->tuned_alg = best_alg;
+  p->tuned_drain = best_drain;
   if (tuned) {
     *tuned = o;
     tuned->block_size = best_block;
     tuned->blocks_per_sm = best_bps;
     tuned->algorithm = best_alg;
+    tuned->drain_threshold = best_drain;
   }
   if (best_ms) *best_ms = best_t;
   return MC_OK;

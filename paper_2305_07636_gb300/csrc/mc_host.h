@@ -80,6 +80,7 @@ struct mc_problem {
   uint64_t range_rows = 0;  // (tally, cell, group) rows scored by the range walk
   int tuned_block = 0, tuned_bps = 0;  // mc_run_tune's choice (block_size, blocks_per_sm), 0 = none
   int tuned_alg = MC_ALG_EVENT;        // mc_run_tune's algorithm for MC_ALG_AUTO
+  uint64_t tuned_drain = 0;            // mc_run_tune's drain threshold (0 = the default)
   std::vector<mcgb::HostTally> tallies;
   std::vector<uint8_t> blob[2];  // [0] FP32 tables, [1] FP64 tables
   mcgb::DevBuf d_blob[2];

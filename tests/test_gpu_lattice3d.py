@@ -3,8 +3,10 @@ against the CPU oracle and closed forms:
 
 - FP64 replay: the axially zoned assembly (partially inserted rods, fission) and the dog-leg duct
   give the oracle's event sequence, element indices and counters;
-- FP32: their mesh flux agrees with the oracle within 4 sigma; point-source escape from a purely
-  absorbing 3D lattice agrees with the ray-marched quadrature;
+- FP32: their mesh flux agrees with the oracle (thousands of bins: the bar is the |z| a correct
+  walk exceeds anywhere with probability 1e-3, at least 4; GPU errors from 256 batches, so their
+  tails are normal); point-source escape from a purely absorbing 3D lattice agrees with the
+  ray-marched quadrature;
 - the batched launch gives the same fixed-point tallies as separate runs;
 - invalid lattices are rejected on the host.
 """
@@ -50,10 +52,15 @@ def replay(prob, n, seed, per_history):
     return p, ev
 
 
+def bar(n):
+    from scipy.stats import norm
+    return max(4.0, float(norm.isf(5e-4 / n)))
+
+
 def flux_z(prob, n_gpu, n_or, seed):
     o = oracle.run(prob, n_or, seed=seed, threads=THREADS)
     p = mc.Problem(prob)
-    p.run(n_gpu, seed + 1, bank_capacity=1 << 22)
+    p.run(n_gpu, seed + 1, n_batches=256, bank_capacity=1 << 22)
     mg, sg = p.tally(0)
     mo, so = o.tallies[0]
     mg, sg, mo, so = (np.asarray(a, dtype=np.float64).ravel() for a in (mg, sg, mo, so))
@@ -80,14 +87,14 @@ def test_dogleg_duct_fp64_replay(torch):
 
 
 def test_axial_lattice_fp32_against_oracle(torch):
-    z, c = flux_z(P.axial_lattice(), 2_000_000, 100_000, 87)
-    assert z.size > 300 and np.all(np.abs(z) < 4), np.abs(z).max()
+    z, c = flux_z(P.axial_lattice(), 2_048_000, 100_000, 87)
+    assert z.size > 1000 and np.all(np.abs(z) < bar(z.size)), (np.abs(z).max(), z.size)
     assert c["lost"] == 0
 
 
 def test_dogleg_duct_fp32_against_oracle(torch):
-    z, c = flux_z(P.dogleg_duct(), 4_000_000, 200_000, 88)
-    assert z.size > 100 and np.all(np.abs(z) < 4), np.abs(z).max()
+    z, c = flux_z(P.dogleg_duct(), 4_096_000, 200_000, 88)
+    assert z.size > 100 and np.all(np.abs(z) < bar(z.size)), (np.abs(z).max(), z.size)
     assert c["lost"] == 0
 
 

@@ -371,6 +371,8 @@ def test_run_tuner_picks_a_configuration_that_changes_nothing_but_time(torch):
     tuned, ms = mc.run_tune(p.h, 200_000, 9, mc.run_opts(algorithm="auto"))
     assert (tuned.block_size, tuned.blocks_per_sm) in ((256, 3), (256, 2), (128, 3), (128, 2)) and ms > 0
     assert tuned.algorithm in (0, 1)
+    base = 2 * torch.cuda.get_device_properties(0).multi_processor_count * tuned.blocks_per_sm * 256
+    assert tuned.drain_threshold in (0, 16 * base, 64 * base)
     ref[1].pop("iterations")
     for alg in ("event", "auto"):  # the tuned configuration, then also the tuned algorithm
         p.run(200_000, 8, tally_stripes=1, algorithm=alg)
@@ -378,4 +380,9 @@ def test_run_tuner_picks_a_configuration_that_changes_nothing_but_time(torch):
         assert np.array_equal(b, ref[0])
         c.pop("iterations")
         assert c == ref[1]
+    for dt in (1, 10**9):  # drain at the very end / once every history is sourced: only the schedule changes
+        p.run(200_000, 8, tally_stripes=1, algorithm="event", drain_threshold=dt)
+        c = p.counters()
+        c.pop("iterations")
+        assert np.array_equal(p.tally_batches(0), ref[0]) and c == ref[1]
     p.close()
