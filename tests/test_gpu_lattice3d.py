@@ -130,6 +130,23 @@ def test_batched_3d_lattice_equals_separate_runs(torch):
         p.close()
 
 
+@pytest.mark.parametrize("corner", ["low", "high"])
+def test_largest_lattice_fp64_replay(torch, corner):
+    """64 x 64 x 16 = 65536 elements (the most the element index holds), scattering materials, a
+    point source in the first or the last element: the walk and its element indices replay the
+    oracle's."""
+    point = (0.03, 0.03, 0.1) if corner == "low" else (6.37, 6.37, 7.9)
+    prob = P.lattice_absorber_3d(n=64, nz=16, pitch=0.1, pitch_z=0.5, radius=0.035, point=point)
+    for m in prob["materials"]:
+        m["sigma_s"] = [[0.6 * m["sigma_t"][0]]]
+    n = 500
+    p, ev = replay(prob, n, 91, 400)
+    first = ev["elem"][ev["k"] == 0]
+    assert np.all(first == (0 if corner == "low" else 65535))
+    assert len(np.unique(ev["elem"])) > 500
+    p.close()
+
+
 def test_invalid_lattices_rejected_on_the_host(torch):
     base = P.axial_lattice()
     bad = []
