@@ -273,7 +273,10 @@ int mc_problem_create(const mc_problem_desc* d, mc_problem** out);
  * the previous run are replaced.  Histories are split into opts->n_batches contiguous batches
  * whose tallies give the statistical error.  The paper's time census, track-length estimator and
  * secondary production are Section 3 features; the random walk itself is the textbook analog one.
- * Returns MC_ERR_INVALID for bad options, MC_ERR_OOM / MC_ERR_CUDA for launch failures. */
+ * Returns MC_ERR_INVALID for bad options, or when the problem's tables (per material and group
+ * cross sections and scatter CDFs, surfaces, cells, the lattice's one-byte-per-element pin map, tally
+ * edges) and the per-warp queues do not fit in one CTA's shared memory, where the kernels keep
+ * them (about 180 KB of tables at 256 threads per CTA); MC_ERR_OOM / MC_ERR_CUDA for launch failures. */
 int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts* opts,
            void* stream);
 

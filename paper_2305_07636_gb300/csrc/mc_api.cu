@@ -65,8 +65,23 @@ int fail(int code, const char* fmt, ...) {
 }
 
 int cuda_fail(cudaError_t e, const char* what) {
+  // reset the runtime's last-error state, so that a failed call (an attribute, an allocation) is not
+  // reported again by the next library call that checks cudaGetLastError after a launch
+  cudaGetLastError();
   return fail(e == cudaErrorMemoryAllocation ? MC_ERR_OOM : MC_ERR_CUDA, "%s: %s", what,
               cudaGetErrorString(e));
+}
+
+int check_shared_memory(int dev, size_t bytes, const char* what) {
+  int optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+  if (bytes > (size_t)optin)
+    return fail(MC_ERR_INVALID,
+                "%s needs %zu B of shared memory per CTA (the problem's tables and the per-warp queues); "
+                "the device allows %d B: fewer materials x groups, surfaces, cells or lattice elements",
+                what, bytes, optin);
+  return MC_OK;
 }
 
 int current_device(int* dev) {
@@ -417,13 +432,15 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
     H.lat_pz = H.lat_nz > 1 ? L->pitch_z : 1.0;
     H.lat_mx = ((1ull << 32) + (unsigned long long)L->nx - 1) / (unsigned long long)L->nx;
     H.lat_my = ((1ull << 32) + (unsigned long long)L->ny - 1) / (unsigned long long)L->ny;
-    std::vector<int> pins(L->pin_material, L->pin_material + L->nx * L->ny * H.lat_nz);
+    // one byte per element (the tables live in shared memory): material, or kNoPin
+    std::vector<uint8_t> pins((size_t)L->nx * L->ny * H.lat_nz);
+    for (size_t i = 0; i < pins.size(); ++i) pins[i] = L->pin_material[i] < 0 ? kNoPin : (uint8_t)L->pin_material[i];
     H.o_lpin = B.put(pins);
   } else {
     H.has_lat = 0;
     H.lat_nz = 1;
     H.lat_mx = H.lat_my = 1ull << 32;
-    std::vector<int> none(1, -1);
+    std::vector<uint8_t> none(1, kNoPin);
     H.o_lpin = B.put(none);
   }
   H.n_tally = d->n_tallies;
@@ -812,6 +829,8 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   const int block = o.block_size ? o.block_size : 256;
   // tables + per-warp flight queues (64 slots) + per-warp tally staging (128 x 12 B)
   const size_t smem = P.blob_bytes + (size_t)(block / 32) * (64 * 16 * lanes + 128 * 12);
+  rc = check_shared_memory(p->dev, smem, "the transport kernel");
+  if (rc != MC_OK) return rc;
   int per_sm = 0;
   // blocks_per_sm == 2 selects the 128-register build of the kernel, any other explicit value the
   // 80-register one; 0 takes the 128-register build when a tally is scored by the range walk
@@ -926,6 +945,8 @@ int mc_run_eigen(mc_problem* p, uint64_t n_per_cycle, int n_inactive, int n_acti
   }
   const int block = o.block_size ? o.block_size : 256;
   const size_t smem = p->blob[fp64].size() + (size_t)(block / 32) * (64 * 16 * lanes + 128 * 12);
+  rc = check_shared_memory(p->dev, smem, "the transport kernel");
+  if (rc != MC_OK) return rc;
   const bool range = p->range;
   const bool wide = o.blocks_per_sm == 2 || (o.blocks_per_sm == 0 && range);
   int per_sm = 0;
@@ -1589,6 +1610,8 @@ extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t
   CK(cudaMemsetAsync(base + off_tally, 0, tally_bytes, s));
   const int block = o.block_size ? o.block_size : 256;
   const size_t smem = P.blob_bytes + (size_t)(block / 32) * (64 * 16 * lanes + 128 * 12);
+  rc = check_shared_memory(p->dev, smem, "the transport kernel");
+  if (rc != MC_OK) return rc;
   int per_sm = 0;
   const bool range = p->range;
   const bool wide = o.blocks_per_sm == 2 || (o.blocks_per_sm == 0 && range);

@@ -431,6 +431,8 @@ int get_plan(int dev, int n, const BatchConfig& c, int fp64, int range, size_t s
   pl->stack_cap = stack_cap;
   const size_t wb = fp64 ? batch_warp_bytes<double>(slot) : batch_warp_bytes<float>(slot);
   pl->smem = (size_t)(c.block / 32) * wb;
+  int rc0 = check_shared_memory(dev, pl->smem, "the batched kernel");
+  if (rc0 != MC_OK) return rc0;
   int per_sm = 0;
   CK(fp64 ? batch_occupancy<double>(c.block, pl->smem, c.wide, range, &per_sm)
           : batch_occupancy<float>(c.block, pl->smem, c.wide, range, &per_sm));

@@ -98,7 +98,8 @@ template <typename R>
 struct Tab {
   const TableHeader* h;
   const R *st, *ss, *ssf, *nu, *nusf, *v, *inv_v, *scdf, *chi, *src_cdf, *scoef;
-  const int *skind, *sbc, *nhs, *hs, *cmat, *lpin;
+  const int *skind, *sbc, *nhs, *hs, *cmat;
+  const uint8_t* lpin;
   R lx0, ly0, lp, lr, lz0, lpz;
   int G;
   __device__ explicit Tab(const char* base) {
@@ -119,7 +120,7 @@ struct Tab {
     nhs = reinterpret_cast<const int*>(base + h->o_nhs);
     hs = reinterpret_cast<const int*>(base + h->o_hs);
     cmat = reinterpret_cast<const int*>(base + h->o_cmat);
-    lpin = reinterpret_cast<const int*>(base + h->o_lpin);
+    lpin = reinterpret_cast<const uint8_t*>(base + h->o_lpin);
     lx0 = (R)h->lat_x0;
     ly0 = (R)h->lat_y0;
     lp = (R)h->lat_pitch;
@@ -344,7 +345,7 @@ template <typename R>
 __device__ __forceinline__ int material_of(const Tab<R>& T, uint32_t pk, uint32_t elem) {
   const int m = T.cmat[pk_cell(pk)];
   if (m >= 0) return m;
-  if (pk_pin(pk)) return T.lpin[lat_e(elem)];
+  if (pk_pin(pk)) return (int)T.lpin[lat_e(elem)];
   return T.h->lat_matrix;
 }
 
@@ -526,7 +527,7 @@ __device__ int locate_cell(const Tab<R>& T, R x, R y, R z, int skip, int skip_se
 
 template <typename R>
 __device__ __forceinline__ uint32_t pin_inside(const Tab<R>& T, R x, R y, int ix, int iy, uint32_t e) {
-  if (T.lpin[e] < 0) return 0u;
+  if (T.lpin[e] == kNoPin) return 0u;
   const R dx = x - (T.lx0 + (R(ix) + R(0.5)) * T.lp), dy = y - (T.ly0 + (R(iy) + R(0.5)) * T.lp);
   return (dx * dx + dy * dy - T.lr * T.lr) < R(0) ? 1u : 0u;
 }
@@ -620,7 +621,7 @@ __device__ R boundary_distance(const Tab<R>& T, const Part<R>& p, Hit& hit) {
         if (d < lbest) { lbest = d; lh = {HIT_LAT, -1, 2}; }
       }
     }
-    if (T.lpin[e] >= 0) {
+    if (T.lpin[e] != kNoPin) {
       const R d = cyl_dist(p.x, p.y, p.ux, p.uy, xlo + R(0.5) * T.lp, ylo + R(0.5) * T.lp, T.lr,
                            pk_pin(p.pk) != 0);
       if (d < lbest) { lbest = d; lh = {HIT_PIN, 1, 0}; }

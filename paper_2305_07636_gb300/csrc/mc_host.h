@@ -16,6 +16,9 @@ int fail(int code, const char* fmt, ...);
 // maps a CUDA error to MC_ERR_OOM / MC_ERR_CUDA with its message
 int cuda_fail(cudaError_t e, const char* what);
 int current_device(int* dev);
+// MC_ERR_INVALID (with a message naming `what`) when `bytes` of dynamic shared memory per CTA exceed
+// the device's opt-in limit: the transport kernels keep the problem's tables in shared memory
+int check_shared_memory(int dev, size_t bytes, const char* what);
 // validates the implicit-capture fields of run options (MC_OK or MC_ERR_INVALID with a message)
 int check_implicit_opts(const mc_run_opts& o);
 

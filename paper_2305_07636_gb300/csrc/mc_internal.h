@@ -30,6 +30,7 @@ constexpr uint32_t kChildKeyXor = 0xA5A5A5A5u;
 enum : uint32_t { PEND_NONE = 0, PEND_COLL = 1, PEND_SURF = 2 };
 enum : uint32_t { CHAN_SCATTER = 0, CHAN_PRODUCTION = 1, CHAN_CAPTURE = 2 };
 enum : uint32_t { HIT_CELL = 0, HIT_LAT = 1, HIT_PIN = 3 };
+constexpr uint8_t kNoPin = 0xFF;  // pin map entry of an element without a pin (materials are < 255)
 
 __host__ __device__ inline uint32_t pk_g(uint32_t w) { return w & 0x1Fu; }
 __host__ __device__ inline uint32_t pk_cell(uint32_t w) { return (w >> 5) & 0xFFu; }
@@ -87,7 +88,8 @@ struct TableHeader {
   int o_st, o_ss, o_ssf, o_nu;        // [M][G] Real: sigma_t, scatter threshold, scatter+production threshold, nu
   int o_v, o_inv_v, o_scdf, o_chi;    // [G] Real speed, 1/speed; [M][G][G] scatter CDF; [M][G] chi CDF
   int o_src_cdf, o_skind, o_sbc, o_scoef;  // [G] Real; [n_surf] int; [n_surf] int; [n_surf][16] Real
-  int o_nhs, o_hs, o_cmat, o_lpin;    // [n_cell] int; [n_cell][16] int (surf | sense<<16); [n_cell] int; [nz][ny][nx] int
+  int o_nhs, o_hs, o_cmat, o_lpin;    // [n_cell] int; [n_cell][16] int (surf | sense<<16); [n_cell] int;
+                                      // [nz][ny][nx] uint8 pin material (kNoPin = no pin)
   TallyDesc tally[kMaxTallies];
   int blob_bytes, o_nusf, pad3, pad4;  // o_nusf: [M][G] Real nu Sigma_f (k-eigenvalue estimator)
 };

@@ -132,3 +132,22 @@ def test_invalid_problems_rejected_on_the_host(torch):
         with pytest.raises(mc.McError) as e:
             mc.Problem(q)
         assert e.value.code == mc.MC_ERR_INVALID
+
+
+def test_tables_beyond_shared_memory_rejected_and_library_still_usable(torch):
+    """The transport kernels keep the problem's tables in shared memory: 255 materials x 32 groups
+    (a 1 MB scatter table) cannot fit, and the run says so with MC_ERR_INVALID before any launch;
+    the failed attempt leaves nothing behind for the next calls (a run, an MLP)."""
+    prob = P.config2(G=mc.MAX_GROUPS, n_tbins=4)
+    prob["materials"] = prob["materials"] * 255
+    p = mc.Problem(prob)
+    with pytest.raises(mc.McError) as e:
+        p.run(10000, 110)
+    assert e.value.code == mc.MC_ERR_INVALID and "shared memory" in str(e.value)
+    p.close()
+    q = mc.Problem(P.config1())
+    q.run(100000, 111)
+    assert q.counters()["source"] == 100000
+    q.close()
+    net = mc.Mlp(P.mlp_init(seed=3))
+    net.close()
