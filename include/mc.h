@@ -307,9 +307,9 @@ int mc_run_eigen(mc_problem* p, uint64_t n_per_cycle, int n_inactive, int n_acti
 /* Autotuner of mc_run for one problem: runs n_histories with each candidate configuration (256 or
  * 128 threads per CTA; the 80-register build at 3 CTAs of 256 per SM, or the 128-register build at
  * 2; with opts->algorithm == MC_ALG_AUTO each under both algorithms), times each run with CUDA
- * events (best of two after a warm-up) and stores the fastest in the problem.  When the fastest is
- * event-based and opts->drain_threshold is 0, drain thresholds of 16 and 64 times the default
- * (twice the resident threads) are timed at that configuration as well.  Later mc_run calls on the
+ * events (best of two after a warm-up) and stores the fastest in the problem.  When
+ * opts->drain_threshold is 0, drain thresholds of 16 and 64 times the default (twice the resident
+ * threads) are timed as well, at the fastest event-based configuration.  Later mc_run calls on the
  * problem whose block_size and blocks_per_sm are both 0 use the stored configuration (and its drain
  * threshold when theirs is 0), those with MC_ALG_AUTO its algorithm.  tuned (nullable) receives a
  * copy of opts with those fields set (drain_threshold 0 = the default), best_ms (nullable) its time.

@@ -1084,7 +1084,8 @@ int mc_run_tune(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run
     return cuda_fail(ce, "cudaEventCreate");
   }
   int best_block = 0, best_bps = 0, best_alg = MC_ALG_EVENT, rc = MC_OK;
-  float best_t = 0.f;
+  int ev_block = 0, ev_bps = 0;  // fastest event-based configuration
+  float best_t = 0.f, ev_t = 0.f;
   const int cands[4][2] = {{256, 0}, {256, 2}, {128, 0}, {128, 2}};  // 80- / 128-register builds
   p->tuned_block = 0;
   p->tuned_drain = 0;
@@ -1115,14 +1116,20 @@ int mc_run_tune(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run
       best_alg = k.algorithm;
       best_t = t;
     }
+    if (rc == MC_OK && k.algorithm == MC_ALG_EVENT && (ev_block == 0 || t < ev_t)) {
+      ev_block = k.block_size;
+      ev_bps = k.blocks_per_sm;
+      ev_t = t;
+    }
   }
   // Event mode: when the run turns history-style (the drain threshold) is a candidate too, at the
-  // chosen configuration.  Turning early saves grid barriers and bank round trips where histories
-  // are short and alike, and costs where they are long and uneven (lattices with production, a
-  // supercritical medium), so the default (twice the resident threads) and 16x / 64x of it are timed.
+  // fastest event-based configuration.  Turning early saves grid barriers and bank round trips where
+  // histories are short and alike, and costs where they are long and uneven (lattices with
+  // production, a supercritical medium), so 16x and 64x the default (twice the resident threads) are
+  // timed; the result may beat the history-based candidates too.
   uint64_t best_drain = 0;
   int sms = 0;
-  if (rc == MC_OK && best_alg == MC_ALG_EVENT && o.drain_threshold == 0) {
+  if (rc == MC_OK && ev_block != 0 && o.drain_threshold == 0) {
     ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->dev);
     if (ce != cudaSuccess) rc = cuda_fail(ce, "cudaDeviceGetAttribute");
   }
@@ -1130,9 +1137,9 @@ int mc_run_tune(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run
     if (rc != MC_OK || sms == 0) break;
     mc_run_opts k = o;
     k.algorithm = MC_ALG_EVENT;
-    k.block_size = best_block;
-    k.blocks_per_sm = best_bps;
-    k.drain_threshold = (uint64_t)mult * 2ull * (uint64_t)sms * (uint64_t)best_bps * 256ull;
+    k.block_size = ev_block;
+    k.blocks_per_sm = ev_bps;
+    k.drain_threshold = (uint64_t)mult * 2ull * (uint64_t)sms * (uint64_t)ev_bps * 256ull;
     rc = mc_run(p, n_histories, seed, &k, stream);  // warm-up
     float t = -1.f;
     for (int rep = 0; rep < 2 && rc == MC_OK; ++rep) {
@@ -1147,6 +1154,9 @@ int mc_run_tune(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run
     }
     if (rc == MC_OK) rc = mc_wait(p);
     if (rc == MC_OK && t < best_t) {
+      best_block = ev_block;
+      best_bps = ev_bps;
+      best_alg = MC_ALG_EVENT;
       best_drain = k.drain_threshold;
       best_t = t;
     }
