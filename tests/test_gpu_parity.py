@@ -38,8 +38,16 @@ def combined_z(mg, sg, mo, so, rel_max=0.1):
 
 
 def check_z(z, min_bins, bar=4.0):
+    """Every bin within `bar`; also reported (shown with -s): the fractions of bins beyond 3 and 4
+    sigma and chi^2 per bin over the mesh.  On a mesh of 200 bins or more, over 2% of them beyond
+    3 sigma fails as well (0.27% for normal errors, about 0.5% with errors from 32 batches)."""
     assert z.size >= min_bins, f"only {z.size} comparable bins"
+    f3, f4 = float(np.mean(np.abs(z) > 3)), float(np.mean(np.abs(z) > 4))
+    print(f"parity: {z.size} bins, beyond 3 sigma {f3:.4f}, beyond 4 sigma {f4:.4f}, "
+          f"chi2 per bin {float(np.mean(z * z)):.3f}")
     assert np.all(np.abs(z) < bar), f"max |z| = {np.abs(z).max():.2f} over {z.size} bins"
+    if z.size >= 200:
+        assert f3 < 0.02, f"{f3:.3%} of the bins beyond 3 sigma"
 
 
 def conserved(c):
@@ -133,6 +141,32 @@ def test_fp32_tallies_match_oracle(torch, name, n_or, n_gpu, min_bins):
     if np.any(o.leak_mean > 0):
         check_z(combined_z(lg, lgs, o.leak_mean, o.leak_std), 1)
     assert conserved(p.counters())
+    p.close()
+
+
+@pytest.mark.parametrize("name,n", [("config1", 4_096_000), ("config2", 4_096_000), ("config3", 1_024_000)])
+def test_fp32_vs_fp64_tracking_bias(torch, name, n):
+    """FP32 tracking (positions, directions and distances in float, float-float clock) against FP64
+    tracking on the GPU, independent seeds: the total of every tally and each resolved bin agree
+    within the statistics; the relative difference of the totals and its error are reported
+    (shown with -s) as the FP32 tracking bias bound for the workload."""
+    prob = P.by_name(name)
+    p = mc.Problem(prob)
+    tot = {}
+    bins = {}
+    for precision, seed in (("fp32", 12), ("fp64", 13)):
+        p.run(n, seed, precision=precision, n_batches=64)
+        per_batch = p.tally_batches(0).reshape(64, -1)
+        t = per_batch.sum(axis=1)
+        tot[precision] = (t.mean(), t.std(ddof=1) / math.sqrt(64))
+        bins[precision] = p.tally(0)
+    (m32, s32), (m64, s64) = tot["fp32"], tot["fp64"]
+    rel, rel_err = (m32 - m64) / m64, math.hypot(s32, s64) / m64
+    print(f"{name}: FP32 - FP64 tracking, total tally: {rel:+.2e} +- {rel_err:.1e} (relative)")
+    assert abs(m32 - m64) < 4 * math.hypot(s32, s64)
+    z = combined_z(*bins["fp32"], *bins["fp64"])
+    from scipy.stats import norm  # many bins: the bar a correct pair exceeds anywhere with probability 1e-3
+    check_z(z, 40, bar=max(4.0, float(norm.isf(5e-4 / max(1, z.size)))))
     p.close()
 
 
