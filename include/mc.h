@@ -42,7 +42,9 @@ typedef enum {
   MC_ERR_BANK_FULL = -4, /* the secondary/birth bank overflowed during the run */
   MC_ERR_TIMEOUT = -5,   /* the device watchdog (iteration or barrier-wait budget) expired */
   MC_ERR_STATE = -6,     /* call out of order (e.g. tally read before any run) */
-  MC_ERR_LOST = -7       /* particles left the geometry (no cell contains them) */
+  MC_ERR_LOST = -7,      /* particles left the geometry (no cell contains them) */
+  MC_ERR_BOUNDS = -8     /* bounds-checked build only: an index into a table, a tally or the
+                            lattice was out of range (the access was skipped) */
 } mc_status;
 
 /* ------------------------------------------------------------------------- limits */

@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmcgb.so")
+LIB_CHECKED = os.path.join(HERE, "libmcgb_checked.so")  # every computed index checked (MC_ERR_BOUNDS)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          f"-I{os.path.join(ROOT, 'include')}"]
@@ -49,23 +50,27 @@ def headers():
             + [os.path.join(ROOT, "include", "mc.h")])
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib=LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in sources() + headers() + [__file__])
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    obj_dir = os.path.join(HERE, "_build")
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Builds libmcgb.so, or with checked=True the bounds-checked libmcgb_checked.so (the same
+    sources with -DMCGB_CHECKED, objects in their own folder)."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and up_to_date(lib):
+        return lib
+    obj_dir = os.path.join(HERE, "_build_checked" if checked else "_build")
     os.makedirs(obj_dir, exist_ok=True)
     cc = nvcc()
     procs, objs = [], []
     for src in sources():
         obj = os.path.join(obj_dir, os.path.basename(src) + ".o")
-        cmd = [cc, *ARCH, *FLAGS, *per_file_flags(src), "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *per_file_flags(src), *(["-DMCGB_CHECKED"] if checked else []), "-c", src,
+               "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -79,12 +84,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
             failed.append(src)
     if failed:
         raise RuntimeError(f"nvcc failed for {failed}")
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

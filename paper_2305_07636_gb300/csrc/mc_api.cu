@@ -1020,7 +1020,9 @@ int mc_run_eigen(mc_problem* p, uint64_t n_per_cycle, int n_inactive, int n_acti
       CK(cudaMemset(p->d_sticky.ptr, 0, 16));
       const int st = ctl.status ? ctl.status : sticky;
       p->last_status = st;
-      return fail(st == MC_ERR_BANK_FULL || st == MC_ERR_TIMEOUT || st == MC_ERR_LOST ? st : MC_ERR_CUDA,
+      return fail(st == MC_ERR_BANK_FULL || st == MC_ERR_TIMEOUT || st == MC_ERR_LOST || st == MC_ERR_BOUNDS
+                      ? st
+                      : MC_ERR_CUDA,
                   "cycle %d: device status %d", c, st);
     }
     for (int i = 0; i < MC_NCOUNTERS; ++i) counters[i] += ctl.counters[i];
@@ -1191,6 +1193,7 @@ int mc_wait(mc_problem* p) {
   if (status == MC_ERR_BANK_FULL) return fail(status, "particle bank overflowed; raise bank_capacity");
   if (status == MC_ERR_TIMEOUT) return fail(status, "device watchdog expired (iteration or barrier budget)");
   if (status == MC_ERR_LOST) return fail(status, "particles left the geometry");
+  if (status == MC_ERR_BOUNDS) return fail(status, "an index was out of range (bounds-checked build)");
   if (status != 0) return fail(MC_ERR_CUDA, "device status %d", status);
   return MC_OK;
 }
@@ -1315,7 +1318,8 @@ int mc_tally_batches(mc_problem* p, int tally_id, double* out, size_t n, int* n_
 int mc_counters_get(mc_problem* p, int64_t* counters, size_t n) {
   if (!p || !counters) return fail(MC_ERR_INVALID, "NULL argument");
   int rc = mc_wait(p);
-  if (rc != MC_OK && rc != MC_ERR_BANK_FULL && rc != MC_ERR_TIMEOUT && rc != MC_ERR_LOST) return rc;
+  if (rc != MC_OK && rc != MC_ERR_BANK_FULL && rc != MC_ERR_TIMEOUT && rc != MC_ERR_LOST && rc != MC_ERR_BOUNDS)
+    return rc;
   Ctl c;
   CK(cudaMemcpy(&c, p->d_ctl.ptr, sizeof(Ctl), cudaMemcpyDeviceToHost));
   for (size_t i = 0; i < n && i < (size_t)MC_NCOUNTERS; ++i)

@@ -93,6 +93,14 @@ __device__ __forceinline__ double rsqrt_(double v) { return sqrt(v); }
 __device__ __forceinline__ void sincos2pi(float u, float* s, float* c) { sincospif(2.0f * u, s, c); }
 __device__ __forceinline__ void sincos2pi(double u, double* s, double* c) { sincospi(2.0 * u, s, c); }
 
+// true when i < n; in the bounds-checked build a false records MC_ERR_BOUNDS (first error wins)
+__device__ __forceinline__ bool in_range(const RunParams& P, uint64_t i, uint64_t n) {
+  if (!kChecked || i < n) return true;
+  atomicCAS(&P.ctl->status, 0, MC_ERR_BOUNDS);
+  atomicCAS(P.sticky, 0, MC_ERR_BOUNDS);
+  return false;
+}
+
 // ------------------------------------------------------------------------------------------ tables
 template <typename R>
 struct Tab {
@@ -704,6 +712,7 @@ struct Scorer {
   __device__ Scorer(const RunParams& P_, double w_)
       : P(P_), w(w_), wscale(sizeof(R) == 4 ? weight_to_float(w_) * P_.fixed_scale_f : 0.0f) {}
   __device__ __forceinline__ void operator()(uint64_t slot, R len) const {
+    if (!in_range(P, slot, (uint64_t)P.tally_stripes * P.stripe_stride)) return;
     if (P.tally_fp64) {
       add_fp64(reinterpret_cast<double*>(P.tally) + slot, w * (double)len, P.aggregate != 0);
     } else {
@@ -743,6 +752,7 @@ __device__ __forceinline__ void stage_flush(const RunParams& P, const Stage& S, 
     if (i < n) {
       const uint32_t slot = S.slot[i];
       const unsigned long long v = S.val[i];
+      if (!in_range(P, slot, (uint64_t)P.tally_stripes * P.stripe_stride)) continue;
       if (P.tally_fp64)
         add_fp64(reinterpret_cast<double*>(P.tally) + slot, __longlong_as_double((long long)v), P.aggregate != 0);
       else

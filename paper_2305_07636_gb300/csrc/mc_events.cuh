@@ -185,6 +185,7 @@ __device__ bool do_collision(const RunParams& P, const Tab<R>& T, Part<R>& p, ui
     const Pair2<R> b1 = draw<R>(P.seed, p.tlo, p.thi, p.k, 1);
     const Pair2<R> b2 = draw<R>(P.seed, p.tlo, p.thi, p.k, 2);
     const int ng = sample_cdf(T.scdf + (m * G + g) * G, G, b1.a);
+    if (!in_range(P, (uint64_t)ng, (uint64_t)G)) return false;
     log_event(P, T, p, 0, 0, 0);
     p.pk = (p.pk & ~0x1Fu) | (uint32_t)ng;
     iso_dir(R(2) * b1.b - R(1), b2.a, p.ux, p.uy, p.uz);
@@ -299,6 +300,7 @@ __device__ bool do_surface(const RunParams& P, const Tab<R>& T, Part<R>& p, uint
     const uint32_t axis = pk_surf(p.pk);
     const int stride = axis == 0 ? 1 : (axis == 1 ? T.h->lat_nx : T.h->lat_nx * T.h->lat_ny);
     const uint32_t e = (uint32_t)((int)lat_e(p.elem) + pk_dir(p.pk) * stride);
+    if (!in_range(P, e, (uint64_t)T.h->lat_nx * T.h->lat_ny * T.h->lat_nz)) return false;
     p.elem = lat_pack(p.elem, e);
     const LatIdx L = lat_split(T, e);
     p.pk = (p.pk & ~(1u << 13)) | (pin_inside(T, p.x, p.y, L.ix, L.iy, e) << 13);
@@ -313,6 +315,15 @@ __device__ bool flight_plan(const RunParams& P, const Tab<R>& T, Part<R>& p, Blo
                             uint32_t& pend, Hit& hit) {
   const int G = T.G;
   const int g = (int)pk_g(p.pk);
+  if (kChecked) {
+    // the particle's cell, group, lattice element and material index the tables
+    const int c = (int)pk_cell(p.pk);
+    if (!in_range(P, (uint64_t)c, (uint64_t)T.h->n_cell) || !in_range(P, (uint64_t)g, (uint64_t)G)) return false;
+    if (T.cmat[c] < 0 &&
+        !in_range(P, lat_e(p.elem), (uint64_t)T.h->lat_nx * T.h->lat_ny * T.h->lat_nz))
+      return false;
+    if (!in_range(P, (uint64_t)(int64_t)material_of(T, p.pk, p.elem), (uint64_t)T.h->M)) return false;
+  }
   const int m = material_of(T, p.pk, p.elem);
   const R St = T.st[m * G + g];
   const Pair2<R> b0 = draw<R>(P.seed, p.tlo, p.thi, p.k, 0);  // (u_dist, u_channel)

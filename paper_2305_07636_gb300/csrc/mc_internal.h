@@ -30,7 +30,17 @@ constexpr uint32_t kChildKeyXor = 0xA5A5A5A5u;
 enum : uint32_t { PEND_NONE = 0, PEND_COLL = 1, PEND_SURF = 2 };
 enum : uint32_t { CHAN_SCATTER = 0, CHAN_PRODUCTION = 1, CHAN_CAPTURE = 2 };
 enum : uint32_t { HIT_CELL = 0, HIT_LAT = 1, HIT_PIN = 3 };
-constexpr uint8_t kNoPin = 0xFF;  // pin map entry of an element without a pin (materials are < 255)
+constexpr uint8_t kNoPin = 0xFF;
+
+// Bounds-checked build (libmcgb_checked.so, compiled with -DMCGB_CHECKED): the walk checks every
+// index it computes into the tables, the tallies and the lattice's element map before use; a bad
+// one records MC_ERR_BOUNDS in the run's status, the access is skipped and the particle ends.  It
+// stands in for a memory checker.  In the normal build the checks are constant-true.
+#ifdef MCGB_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif  // pin map entry of an element without a pin (materials are < 255)
 
 __host__ __device__ inline uint32_t pk_g(uint32_t w) { return w & 0x1Fu; }
 __host__ __device__ inline uint32_t pk_cell(uint32_t w) { return (w >> 5) & 0xFFu; }

@@ -18,10 +18,10 @@ from . import build as _build
 
 # ------------------------------------------------------------------------------ constants (mc.h)
 MC_OK, MC_ERR_INVALID, MC_ERR_CUDA, MC_ERR_OOM = 0, -1, -2, -3
-MC_ERR_BANK_FULL, MC_ERR_TIMEOUT, MC_ERR_STATE, MC_ERR_LOST = -4, -5, -6, -7
+MC_ERR_BANK_FULL, MC_ERR_TIMEOUT, MC_ERR_STATE, MC_ERR_LOST, MC_ERR_BOUNDS = -4, -5, -6, -7, -8
 STATUS_NAMES = {0: "MC_OK", -1: "MC_ERR_INVALID", -2: "MC_ERR_CUDA", -3: "MC_ERR_OOM",
                 -4: "MC_ERR_BANK_FULL", -5: "MC_ERR_TIMEOUT", -6: "MC_ERR_STATE",
-                -7: "MC_ERR_LOST"}
+                -7: "MC_ERR_LOST", -8: "MC_ERR_BOUNDS"}
 MAX_HALFSPACES = 16
 MAX_GROUPS, MAX_SURFACES, MAX_CELLS = 32, 255, 255  # MC_MAX_* of mc.h
 MAX_LATTICE, MAX_LATTICE_ELEMENTS = 255, 65536
@@ -166,11 +166,14 @@ _lock = threading.Lock()
 
 
 def lib(build_if_missing: bool = True):
-    """Loads libmcgb.so (building it with nvcc first if it is missing or stale)."""
+    """Loads libmcgb.so (building it with nvcc first if it is missing or stale); with the
+    environment variable MCGB_CHECKED=1 the bounds-checked build libmcgb_checked.so instead."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build() if build_if_missing else _build.LIB
+            checked = os.environ.get("MCGB_CHECKED") == "1"
+            path = (_build.build(checked=checked) if build_if_missing
+                    else (_build.LIB_CHECKED if checked else _build.LIB))
             L = C.CDLL(path)
             for name, (res, args) in SIGNATURES.items():
                 f = getattr(L, name)
