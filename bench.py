@@ -497,15 +497,17 @@ def bench_eigen(args, torch, mc, prob, n, desc):
     ni, na = EIGEN_CYCLES
     p = mc.Problem(prob)
     stream = torch.cuda.current_stream()
+    extra = {k: int(v) for k, v in (o.split("=", 1) for o in args.opt)}
+    opts = mc.run_opts(**extra) if extra else None
     for w in range(args.warmup):
-        mc.run_eigen(p.h, n, 2, 2, 1000 + w, None, stream)
+        mc.run_eigen(p.h, n, 2, 2, 1000 + w, opts, stream)
     clocks = Clocks(0)
     times, ks = [], []
     for k in range(args.steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         a.record(stream)
-        kc, sites, km, ke = mc.run_eigen(p.h, n, ni, na, 7 + k, None, stream)
+        kc, sites, km, ke = mc.run_eigen(p.h, n, ni, na, 7 + k, opts, stream)
         b.record(stream)
         torch.cuda.synchronize()
         times.append(a.elapsed_time(b) / 1000.0)
@@ -524,7 +526,7 @@ def bench_eigen(args, torch, mc, prob, n, desc):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     q = mc.Problem(prob)
-    mc.run_eigen(q.h, n, ni, na, 99, None, stream)
+    mc.run_eigen(q.h, n, ni, na, 99, opts, stream)
     mean, err = q.tally(0)
     h2d = q.table_bytes()
     q.close()
@@ -534,7 +536,7 @@ def bench_eigen(args, torch, mc, prob, n, desc):
         "warmup": args.warmup, "ms_per_step": 1000 * t, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "histories_per_cycle": n, "cycles": {"inactive": ni, "active": na},
-                   "tracking": "fp32", "tally": "int64 fixed point 2^-32"},
+                   "tracking": "fp32", "tally": "int64 fixed point 2^-32", "run_opts": extra},
         "k": {"mean": km, "std_err": ke, "fom_1_per_s": fom,
               "paper_context": "MC/DC 2563.8 s (incl. ~63 s JIT) and Shift 1020.7 s for 1e5 x 150 cycles of the "
                                "C5G7 UO2 pin cell on LLNL Lassen (IBM POWER9), i.e. ~6.0e3 and ~1.47e4 "

@@ -201,7 +201,8 @@ typedef struct {
   uint64_t first_history; /* history indices run are [first_history, first_history + n) */
   int algorithm;          /* mc_algorithm (default MC_ALG_EVENT) */
   uint64_t drain_threshold; /* event mode: once every history is sourced and at most this many
-                               particles remain, finish them history-style (0 = 2 per thread) */
+                               particles remain, finish them history-style (0 = 2 per thread; in
+                               mc_run_eigen 32 per thread; mc_run_tune may pick another) */
   int tally_stripes;      /* copies of the batch tallies that CTAs score into round-robin, summed
                              by the statistics (0 = up to 16 within a 64 MB budget) */
   int batch_unit;         /* mc_run_batch: histories per work unit a warp claims (0 = tuned or 128) */
