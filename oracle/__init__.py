@@ -111,7 +111,7 @@ class OrPcOpts(C.Structure):
                 ("threads", C.c_int), ("n_census", C.c_int), ("census_times", C.POINTER(C.c_double)),
                 ("log_first", C.c_uint64), ("log_count", C.c_uint64),
                 ("log", C.POINTER(OrEvent)), ("log_cap", C.c_uint64),
-                ("log_n", C.POINTER(C.c_uint64))]
+                ("log_n", C.POINTER(C.c_uint64)), ("method", C.c_int)]
 
 
 class OrPcResult(C.Structure):
@@ -420,9 +420,10 @@ class BatchResult:
 
 def run_pc(prob: dict, n: int, census_times, n_batches: int = 32, seed: int = 1,
            threads: int | None = None, log_first: int = 0, log_count: int = 0,
-           log_cap: int = 0) -> BatchResult:
-    """Time-dependent run with splitting-roulette population control at the interior census times
-    (see or_run_pc in oracle.h); statistics over the independent batches."""
+           log_cap: int = 0, method: str = "split") -> BatchResult:
+    """Time-dependent run with population control at the interior census times (see or_run_pc in
+    oracle.h): splitting-roulette ("split") or combing ("comb"); statistics over the independent
+    batches."""
     L = lib()
     m = Marshalled(prob)
     nb = L.or_total_bins(C.byref(m.s))
@@ -434,6 +435,7 @@ def run_pc(prob: dict, n: int, census_times, n_batches: int = 32, seed: int = 1,
     o.threads = threads if threads else (os.cpu_count() or 1)
     o.n_census = ct.size
     o.census_times = ct.ctypes.data_as(C.POINTER(C.c_double))
+    o.method = {"split": 0, "comb": 1}[method]
     events, log_n = None, C.c_uint64(0)
     if log_count > 0:
         cap = log_cap if log_cap else 256 * log_count
@@ -474,6 +476,16 @@ def philox(key, ctr):
     out = (C.c_uint32 * 4)()
     L.or_philox(int(key[0]) & 0xFFFFFFFF, int(key[1]) & 0xFFFFFFFF, c, out)
     return [int(v) for v in out]
+
+
+def comb_counts(weights, n_teeth: int, xi: float):
+    """Copies the population-control comb gives each weight of the list, in its order."""
+    L = lib()
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    out = np.zeros(w.size, np.int64)
+    L.or_comb_counts(w.ctypes.data_as(C.POINTER(C.c_double)), C.c_int64(w.size), C.c_uint64(n_teeth),
+                     C.c_double(xi), out.ctypes.data_as(C.POINTER(C.c_int64)))
+    return out
 
 
 def u01(a, b):

@@ -959,8 +959,17 @@ void run_range(const Prob& P, const Physics& ph, uint64_t seed, uint64_t h0, uin
 
 // one batch of a population-controlled run (see or_run_pc): its histories [h0, h1), interval by
 // interval, with splitting-roulette of the banked particles at every interior census
-void run_pc_batch(const Prob& P, const or_pc_opts* o, uint64_t h0, uint64_t h1, Acc& acc, const Logger& lg,
-                  std::vector<uint64_t>& banked) {
+// copies of banked particle j by the comb: teeth at (k + xi) W / N_b, k = 0 .. N_b - 1, counted in
+// its cumulative-weight interval [C_{j-1}, C_j) through F(C) = #{k : tooth k < C}
+int64_t comb_teeth_below(int64_t C, int64_t W, uint64_t Nb, double xi) {
+  const double x = (double)C * (double)Nb / (double)W - xi;
+  const double f = std::ceil(x);
+  if (!(f > 0.0)) return 0;
+  return f >= (double)Nb ? (int64_t)Nb : (int64_t)f;
+}
+
+void run_pc_batch(const Prob& P, const or_pc_opts* o, uint64_t b, uint64_t h0, uint64_t h1, Acc& acc,
+                  const Logger& lg, std::vector<uint64_t>& banked) {
   const Physics ph{false, 0.0, 0.0};
   const uint64_t Nb = h1 - h0;
   std::vector<Particle> cur, stack;
@@ -989,12 +998,26 @@ void run_pc_batch(const Prob& P, const or_pc_opts* o, uint64_t h0, uint64_t h1, 
     for (const PcBanked& b : bank) Wq += (int64_t)std::llrint(b.q.w * 1099511627776.0);
     if (Wq <= 0) break;
     const double wt = (double)Wq / 1099511627776.0 / (double)Nb;
-    for (const PcBanked& b : bank) {
-      const double xi = draw(o->seed, b.q.tag, b.kc, 1).a;
-      const int n = (int)std::floor(b.q.w / wt + xi);
-      for (int j = 0; j < n; ++j) {
-        Particle c = b.q;
-        c.tag = child_tag(o->seed, b.q.tag, b.kc, (uint32_t)j, 0x40000000u);
+    std::vector<int> ncopy(bank.size());
+    if (o->method == 1) {
+      // combing: the bank in tag order, one offset per batch and census
+      std::sort(bank.begin(), bank.end(), [](const PcBanked& x, const PcBanked& y) { return x.q.tag < y.q.tag; });
+      const double xi = draw(o->seed, 0xFFFFFFFEull | (b << 32), (uint32_t)i, 5).a;
+      int64_t C = 0;
+      for (size_t j = 0; j < bank.size(); ++j) {
+        const int64_t Cp = C;
+        C += (int64_t)std::llrint(bank[j].q.w * 1099511627776.0);
+        ncopy[j] = (int)(comb_teeth_below(C, Wq, Nb, xi) - comb_teeth_below(Cp, Wq, Nb, xi));
+      }
+    } else {
+      for (size_t j = 0; j < bank.size(); ++j)
+        ncopy[j] = (int)std::floor(bank[j].q.w / wt + draw(o->seed, bank[j].q.tag, bank[j].kc, 1).a);
+    }
+    for (size_t jb = 0; jb < bank.size(); ++jb) {
+      const PcBanked& bk = bank[jb];
+      for (int j = 0; j < ncopy[jb]; ++j) {
+        Particle c = bk.q;
+        c.tag = child_tag(o->seed, bk.q.tag, bk.kc, (uint32_t)j, 0x40000000u);
         c.k = 0;
         c.t = pc.t_census;
         c.w = wt;
@@ -1046,6 +1069,17 @@ double comb_offset(uint64_t seed, uint32_t cycle) {
 
 extern "C" {
 
+void or_comb_counts(const double* w, int64_t n, uint64_t Nb, double xi, int64_t* out) {
+  int64_t W = 0;
+  for (int64_t j = 0; j < n; ++j) W += (int64_t)std::llrint(w[j] * 1099511627776.0);
+  int64_t C = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    const int64_t Cp = C;
+    C += (int64_t)std::llrint(w[j] * 1099511627776.0);
+    out[j] = comb_teeth_below(C, W, Nb, xi) - comb_teeth_below(Cp, W, Nb, xi);
+  }
+}
+
 int or_run_pc(const or_problem* p, const or_pc_opts* o, or_pc_result* r) {
   Prob P = copy_problem(p);
   const uint64_t N = o->n_histories;
@@ -1066,7 +1100,7 @@ int or_run_pc(const or_problem* p, const or_pc_opts* o, or_pc_result* r) {
         accs[b].init(bins, 32);
         // histories of batch b: floor(h nb / N) == b
         const uint64_t h0 = ((uint64_t)b * N + nb - 1) / nb, h1 = ((uint64_t)(b + 1) * N + nb - 1) / nb;
-        run_pc_batch(P, o, h0, h1, accs[b], lg, banked[b]);
+        run_pc_batch(P, o, (uint64_t)b, h0, h1, accs[b], lg, banked[b]);
         accs[b].end_history();
       }
     });

@@ -153,7 +153,13 @@ int or_run(const or_problem* p, const or_opts* o, or_result* r);
  * first FP64 uniform of block 1 of event k, copy j with tag child_tag(T, k, 0x40000000 | j), weight
  * w_t, time = the census time exactly, event index 0, the same position, direction and group.  The
  * copies start the next interval.  Tallies are returned per batch (tally_batch[b][bin], per source
- * particle of the batch). */
+ * particle of the batch).
+ * method 1 combs instead (systematic sampling of the census bank): the batch's banked particles are
+ * ordered by tag, C_j = the running sum of llrint(w 2^40) up to and including particle j, W_b = C_M,
+ * and with F(C) = min(N_b, max(0, ceil(C N_b / W_b - xi_b))) (FP64, each operation rounded in this
+ * order; xi_b = the first FP64 uniform of block 5 of event i of tag 0xFFFFFFFE + 2^32 b, i the
+ * census index) particle j becomes F(C_j) - F(C_{j-1}) copies (the N_b teeth (k + xi_b) W_b / N_b
+ * that fall in its weight interval), each as above. */
 typedef struct {
   uint64_t n_histories, seed;
   int n_batches, threads;
@@ -163,6 +169,7 @@ typedef struct {
   or_event* log;
   uint64_t log_cap;
   uint64_t* log_n;
+  int method;                    /* 0 splitting-roulette, 1 combing */
 } or_pc_opts;
 
 typedef struct {
@@ -172,6 +179,10 @@ typedef struct {
 } or_pc_result;
 
 int or_run_pc(const or_problem* p, const or_pc_opts* o, or_pc_result* r);
+
+/* The comb of method 1 applied to n weights in the given order: out[j] = copies of weight j
+ * (exposed for the pins). */
+void or_comb_counts(const double* w, int64_t n, uint64_t Nb, double xi, int64_t* out);
 
 /* k-eigenvalue power iteration (the paper's C5G7 runs, Section 3), analog: n_inactive + n_active
  * cycles of n_per_cycle histories.  Cycle 0 starts at the problem's source; cycle c >= 1 starts
