@@ -231,7 +231,18 @@ typedef struct {
    * mc_run_static. */
   int n_census;
   const double* census_times;
+  /* Population-control method (mc_pc_method).  MC_PC_COMB combs instead of splitting-roulette
+   * (systematic sampling of the census bank, one of the population-control techniques the paper
+   * cites): per batch the banked particles are ordered by their 64-bit tag, C_j = the running sum of
+   * llrint(w 2^40) up to and including particle j, W_b = C_M, and particle j becomes F(C_j) - F(C_{j-1})
+   * copies with F(C) = min(N_b, max(0, ceil(C N_b / W_b - xi_b))) evaluated in FP64 in that order
+   * (xi_b = the first FP64 uniform of block 5 of event i of tag 0xFFFFFFFE + 2^32 b, i the census
+   * index): the N_b teeth (k + xi_b) W_b / N_b that fall in its weight interval.  Every census then
+   * restores exactly N_b particles per batch.  Copies as for splitting-roulette. */
+  int pc_method;
 } mc_run_opts;
+
+typedef enum { MC_PC_SPLIT_ROULETTE = 0, MC_PC_COMB = 1 } mc_pc_method;
 
 /* Fills the defaults listed above. */
 void mc_run_opts_default(mc_run_opts* o);

@@ -36,6 +36,11 @@ cudaError_t launch_comb(const uint32_t* counts, const unsigned long long* scan, 
 template <typename R>
 cudaError_t launch_pc(const RunParams& P, const RunParams& Q, const unsigned long long* pc_n, long long* wq,
                       unsigned long long* out_n, unsigned long long* copies, int* status, bool split, cudaStream_t s);
+size_t comb_scratch_bytes(uint64_t n, int nb);
+template <typename R>
+cudaError_t launch_comb_pc(const RunParams& P, const RunParams& Q, uint64_t n, const long long* wb, uint32_t census,
+                           void* scratch, size_t scratch_bytes, unsigned long long* out_n, unsigned long long* copies,
+                           int* status, cudaStream_t s);
 cudaError_t launch_reconstruct(void* tally, const char* blob64, uint64_t rows, uint64_t row, int nb, int stripes,
                                int fp64, cudaStream_t s);
 cudaError_t launch_batch_stats(const void* tally, int fp64, uint64_t bins, uint64_t row, int nb, int stripes,
@@ -644,19 +649,28 @@ void mc_problem_destroy(mc_problem* p) {
   p->d_trace.release();
   p->d_sticky.release();
   p->d_ww.release();
+  // k-eigenvalue and population-control buffers
+  p->d_sites.release();
+  p->d_counts.release();
+  p->d_scan.release();
+  p->d_blocksums.release();
+  p->d_src.release();
+  p->d_cbank.release();
+  p->d_pc.release();
+  p->d_comb.release();
   for (int i = 0; i < 3; ++i)
     if (p->ev[i]) cudaEventDestroy(p->ev[i]);
   delete p;
 }
 
 // Population control: one transport launch per interval between census times.  After an interior
-// census the banked particles' batch weights are summed exactly, splitting-roulette writes the
-// copies into the next launch's birth bank, and the next launch starts from them alone.  The run's
+// census the banked particles' batch weights are summed exactly, splitting-roulette or the comb
+// writes the copies into the next launch's birth bank, and the next launch starts from them alone.  The run's
 // counters (and the event log count) are summed over the intervals on the host and written back
 // into the control block at the end.
 int run_population_controlled(mc_problem* p, const RunParams& P0, const std::vector<double>& census, double t_final,
                               int grid, int block, size_t smem, bool wide, bool range, int fp64, int lanes,
-                              uint64_t cap, cudaStream_t s) {
+                              uint64_t cap, bool comb, cudaStream_t s) {
   int rc = p->d_cbank.ensure((size_t)cap * 16 * lanes, p->dev);
   const int nb = P0.n_batches;
   if (rc == MC_OK) rc = p->d_pc.ensure((size_t)(nb + 4) * 8, p->dev);
@@ -669,7 +683,7 @@ int run_population_controlled(mc_problem* p, const RunParams& P0, const std::vec
   unsigned long long iterations = 0, log_n = 0;
   RunParams prev = P0;
   const int K = (int)census.size();
-  auto harvest = [&](int* st) -> int {  // the finished launch's counters
+  auto harvest = [&](int* st, unsigned long long* banked) -> int {  // the finished launch's counters
     Ctl c;
     CK(cudaMemcpyAsync(&c, p->d_ctl.ptr, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -677,6 +691,7 @@ int run_population_controlled(mc_problem* p, const RunParams& P0, const std::vec
     iterations += c.iterations;
     log_n = c.log_n;
     *st = c.status;
+    *banked = c.pc_n;
     return MC_OK;
   };
   for (int i = 0; i <= K; ++i) {
@@ -692,13 +707,27 @@ int run_population_controlled(mc_problem* p, const RunParams& P0, const std::vec
       const unsigned long long* pc_n = (const unsigned long long*)((const char*)p->d_ctl.ptr + offsetof(Ctl, pc_n));
       CK(fp64 ? launch_pc<double>(prev, Q, pc_n, wq, out_n, copies, status, false, s)
               : launch_pc<float>(prev, Q, pc_n, wq, out_n, copies, status, false, s));
-      CK(fp64 ? launch_pc<double>(prev, Q, pc_n, wq, out_n, copies, status, true, s)
-              : launch_pc<float>(prev, Q, pc_n, wq, out_n, copies, status, true, s));
       int st = 0;
-      rc = harvest(&st);
+      unsigned long long banked = 0;
+      rc = harvest(&st, &banked);
       if (rc != MC_OK) return rc;
+      if (comb && st == 0) {
+        // the comb sorts the census bank first, so it needs the banked count on the host
+        const uint64_t n = banked < cap ? banked : cap;
+        const size_t bytes = comb_scratch_bytes(n, nb);
+        rc = p->d_comb.ensure(bytes, p->dev);
+        if (rc != MC_OK) return rc;
+        CK(fp64 ? launch_comb_pc<double>(prev, Q, n, wq, (uint32_t)(i - 1), p->d_comb.ptr, bytes, out_n, copies,
+                                         status, s)
+                : launch_comb_pc<float>(prev, Q, n, wq, (uint32_t)(i - 1), p->d_comb.ptr, bytes, out_n, copies,
+                                        status, s));
+      } else if (st == 0) {
+        CK(fp64 ? launch_pc<double>(prev, Q, pc_n, wq, out_n, copies, status, true, s)
+                : launch_pc<float>(prev, Q, pc_n, wq, out_n, copies, status, true, s));
+      }
       unsigned long long pc_state[2] = {0ull, 0ull};  // copies, status word
-      CK(cudaMemcpy(pc_state, copies, 16, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpyAsync(pc_state, copies, 16, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
       cnt[MC_C_PC_COPIES] += pc_state[0];
       if (st == 0) st = (int)(pc_state[1] & 0xFFFFFFFFu);
       if (st != 0) {
@@ -714,7 +743,8 @@ int run_population_controlled(mc_problem* p, const RunParams& P0, const std::vec
     prev = Q;
   }
   int st = 0;
-  rc = harvest(&st);
+  unsigned long long banked_last = 0;
+  rc = harvest(&st, &banked_last);
   if (rc != MC_OK) return rc;
   Ctl c;
   std::memset(&c, 0, sizeof(c));
@@ -753,6 +783,8 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   if (o.algorithm != MC_ALG_EVENT && o.algorithm != MC_ALG_HISTORY) return fail(MC_ERR_INVALID, "algorithm");
   if (check_implicit_opts(o) != MC_OK) return MC_ERR_INVALID;
   const double t_final = reinterpret_cast<const TableHeader*>(p->blob[1].data())->t_census;
+  if (o.pc_method != MC_PC_SPLIT_ROULETTE && o.pc_method != MC_PC_COMB)
+    return fail(MC_ERR_INVALID, "pc_method must be MC_PC_SPLIT_ROULETTE or MC_PC_COMB");
   if (o.n_census < 0 || o.n_census > 4096 || (o.n_census > 0 && !o.census_times))
     return fail(MC_ERR_INVALID, "n_census outside [0, 4096] or census_times NULL");
   std::vector<double> census(o.census_times, o.census_times + std::max(0, o.n_census));
@@ -850,7 +882,8 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
     CK(fp64 ? launch_transport<double>(P, grid, block, smem, s, wide, range)
             : launch_transport<float>(P, grid, block, smem, s, wide, range));
   } else {
-    rc = run_population_controlled(p, P, census, t_final, grid, block, smem, wide, range, fp64, lanes, cap, s);
+    rc = run_population_controlled(p, P, census, t_final, grid, block, smem, wide, range, fp64, lanes, cap,
+                                   o.pc_method == MC_PC_COMB, s);
     if (rc != MC_OK) return rc;
   }
   CK(cudaEventRecord(p->ev[1], s));

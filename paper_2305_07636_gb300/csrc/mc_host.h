@@ -111,5 +111,6 @@ struct mc_problem {
   mcgb::DevBuf d_sites, d_counts, d_scan, d_blocksums, d_src;
   // population control: the census bank, per-batch weights and split counters
   mcgb::DevBuf d_cbank, d_pc;
+  mcgb::DevBuf d_comb;  // combing: sort keys and indices, fixed-point weights and their scan, CUB scratch
   double nu_max = 0.0;
 };

@@ -96,7 +96,7 @@ class mc_run_opts(C.Structure):
                 ("algorithm", C.c_int), ("drain_threshold", C.c_uint64),
                 ("tally_stripes", C.c_int), ("batch_unit", C.c_int),
                 ("implicit_capture", C.c_int), ("wr_cutoff", C.c_double), ("wr_survival", C.c_double),
-                ("n_census", C.c_int), ("census_times", DP)]
+                ("n_census", C.c_int), ("census_times", DP), ("pc_method", C.c_int)]
 
 
 class mc_event(C.Structure):
@@ -201,6 +201,8 @@ def run_opts(**kw) -> mc_run_opts:
             v = {"fp32": MC_FP32, "fp64": MC_FP64}[v]
         if k == "algorithm" and isinstance(v, str):
             v = {"event": 0, "history": 1, "auto": 2}[v]
+        if k == "pc_method" and isinstance(v, str):
+            v = {"split": 0, "comb": 1}[v]
         if k == "tally_mode" and isinstance(v, str):
             v = {"fixed": MC_TALLY_FIXED64, "fp64": MC_TALLY_FP64}[v]
         if k == "census_times":
