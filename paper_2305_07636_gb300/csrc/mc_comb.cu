@@ -20,34 +20,51 @@ namespace mcgb {
 
 constexpr double kW40 = 1099511627776.0;  // 2^40, the fixed-point scale of census weights
 
+// Where the comb's fields sit in a banked particle (16-byte lanes): tag (x, y), batch in the high
+// half of elem, weight (FP64 bits).  FP32: tag lane 3, elem lane 1 .z, weight lane 2 (.z, .w).
+// FP64: tag lane 4, elem lane 5 .x, weight lane 3 (.z, .w).
 template <typename R>
-__global__ void k_comb_keys(const RunParams P, uint64_t n, unsigned long long* tag, uint32_t* idx) {
+struct CombLanes;
+template <>
+struct CombLanes<float> {
+  static constexpr int kTag = 3, kElem = 1, kW = 2;
+  static __device__ __forceinline__ uint32_t elem(const uint4& v) { return v.z; }
+};
+template <>
+struct CombLanes<double> {
+  static constexpr int kTag = 4, kElem = 5, kW = 3;
+  static __device__ __forceinline__ uint32_t elem(const uint4& v) { return v.x; }
+};
+
+// One pass over the census bank, three of its lanes: tag keys, identity indices, and in bank order
+// the batch and the fixed-point weight llrint(w 2^40) of every particle.
+template <typename R>
+__global__ void k_comb_keys(const RunParams P, uint64_t n, unsigned long long* tag, uint32_t* idx, uint32_t* bat0,
+                            long long* wq0) {
+  using L = CombLanes<R>;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    Part<R> p;
-    bank_load(p, P.C, i);
-    tag[i] = ((unsigned long long)p.thi << 32) | p.tlo;
+    const uint4 t = __ldcg(P.C[L::kTag] + i);
+    const uint4 e = __ldcg(P.C[L::kElem] + i);
+    const uint4 w = __ldcg(P.C[L::kW] + i);
+    tag[i] = ((unsigned long long)t.y << 32) | t.x;
     idx[i] = (uint32_t)i;
+    bat0[i] = L::elem(e) >> 16;
+    const double wd = __longlong_as_double((long long)(((unsigned long long)w.w << 32) | w.z));
+    wq0[i] = __double2ll_rn(__dmul_rn(wd, kW40));
   }
 }
 
 // batch of each particle, in tag order
-template <typename R>
-__global__ void k_comb_batch(const RunParams P, uint64_t n, const uint32_t* idx, uint32_t* batch) {
-  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (uint64_t)gridDim.x * blockDim.x) {
-    Part<R> p;
-    bank_load(p, P.C, idx[j]);
-    batch[j] = p.elem >> 16;
-  }
+__global__ void k_comb_batch(uint64_t n, const uint32_t* idx, const uint32_t* bat0, uint32_t* batch) {
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (uint64_t)gridDim.x * blockDim.x)
+    batch[j] = bat0[idx[j]];
 }
 
 // fixed-point weights in (batch, tag) order, and the first position of every batch
-template <typename R>
-__global__ void k_comb_weights(const RunParams P, uint64_t n, const uint32_t* idx, const uint32_t* batch,
+__global__ void k_comb_weights(uint64_t n, const uint32_t* idx, const uint32_t* batch, const long long* wq0,
                                long long* wq, uint32_t* start) {
   for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (uint64_t)gridDim.x * blockDim.x) {
-    Part<R> p;
-    bank_load(p, P.C, idx[j]);
-    wq[j] = __double2ll_rn(__dmul_rn(p.w, kW40));
+    wq[j] = wq0[idx[j]];
     if (j == 0 || batch[j - 1] != batch[j]) start[batch[j]] = (uint32_t)j;
   }
 }
@@ -109,7 +126,7 @@ size_t comb_scratch_bytes(uint64_t n, int nb) {
   cub::DeviceScan::InclusiveSum(nullptr, scan_tmp, (const long long*)nullptr, (long long*)nullptr, (int64_t)n);
   const size_t tmp = std::max(sort_tmp, std::max(sort2_tmp, scan_tmp));
   auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
-  return up(n * 8) * 2 + up(n * 4) * 4 + up(n * 8) * 2 + up((size_t)nb * 4) + up(tmp);
+  return up(n * 8) * 2 + up(n * 4) * 5 + up(n * 8) * 3 + up((size_t)nb * 4) + up(tmp);
 }
 
 // The comb of the n particles banked by launch P (its census bank P.C), copies into Q's birth bank.
@@ -139,18 +156,22 @@ cudaError_t launch_comb_pc(const RunParams& P, const RunParams& Q, uint64_t n, c
   c += up(n * 8);
   uint32_t* start = (uint32_t*)c;
   c += up((size_t)P.n_batches * 4);
+  uint32_t* bat0 = (uint32_t*)c;
+  c += up(n * 4);
+  long long* wq0 = (long long*)c;
+  c += up(n * 8);
   void* tmp = c;
   size_t tmp_bytes = scratch_bytes - (size_t)(c - (char*)scratch);
   const unsigned g = 152 * 8;
   int end_bit = 1;
   while ((1 << end_bit) < P.n_batches) ++end_bit;
-  k_comb_keys<R><<<g, 256, 0, s>>>(P, n, tag_a, idx_a);
+  k_comb_keys<R><<<g, 256, 0, s>>>(P, n, tag_a, idx_a, bat0, wq0);
   cudaError_t e = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, tag_a, tag_b, idx_a, idx_b, (int64_t)n, 0, 64, s);
   if (e != cudaSuccess) return e;
-  k_comb_batch<R><<<g, 256, 0, s>>>(P, n, idx_b, bat_a);
+  k_comb_batch<<<g, 256, 0, s>>>(n, idx_b, bat0, bat_a);
   e = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, bat_a, bat_b, idx_b, idx_a, (int64_t)n, 0, end_bit, s);
   if (e != cudaSuccess) return e;
-  k_comb_weights<R><<<g, 256, 0, s>>>(P, n, idx_a, bat_b, wq, start);
+  k_comb_weights<<<g, 256, 0, s>>>(n, idx_a, bat_b, wq0, wq, start);
   e = cub::DeviceScan::InclusiveSum(tmp, tmp_bytes, wq, csum, (int64_t)n, s);
   if (e != cudaSuccess) return e;
   k_comb_copies<R><<<g, 256, 0, s>>>(P, n, idx_a, bat_b, wq, csum, start, wb, census, Q, out_n, copies, status);
