@@ -804,9 +804,22 @@ __device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Pa
   const float wscale = sizeof(R) == 4 ? weight_to_float(w) * P.fixed_scale_f : 0.0f;
   const bool fp32_fixed = sizeof(R) == 4 && !P.tally_fp64;
   unsigned n_st = 0;
-  // stages one value per lane (those with emit), flushing when the buffer could overflow
+  const bool direct = !P.aggregate;  // warp-uniform
+  // stages one value per lane (those with emit), flushing when the buffer could overflow; without
+  // warp aggregation the staging buys nothing, and each lane adds its value at once (fire-and-
+  // forget atomics; integer sums do not depend on their order)
   auto stage_bits = [&](bool emit, uint32_t slot, unsigned long long val) {
     const unsigned m = __ballot_sync(kAll, emit);
+    if (direct) {
+      pieces += __popc(m);
+      if (emit && in_range(P, slot, (uint64_t)P.tally_stripes * P.stripe_stride)) {
+        if (P.tally_fp64)
+          atomicAdd(reinterpret_cast<double*>(P.tally) + slot, __longlong_as_double((long long)val));
+        else
+          atomicAdd(reinterpret_cast<unsigned long long*>(P.tally) + slot, val);
+      }
+      return;
+    }
     if (emit) {
       const unsigned i = n_st + __popc(m & lt);
       S.slot[i] = slot;
@@ -1097,7 +1110,7 @@ __device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Pa
       }
     }
   }
-  stage_flush(P, S, n_st);
+  if (n_st) stage_flush(P, S, n_st);
 }
 
 // ------------------------------------------------------------------------------------------ sampling
