@@ -317,13 +317,15 @@ def bench_batch(args, torch, mc, batch, n_total, desc, world, local):
     hs = [p.h for p in ps]
     stream = torch.cuda.current_stream()
     seed = 5
+    extra = {k: int(v) for k, v in (o.split("=", 1) for o in args.opt)}
+    bopts = mc.run_opts(**extra) if extra else None
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     t0 = time.perf_counter()
-    tuned, tune_ms = mc.batch_tune(hs, nh, seed, None, stream)
+    tuned, tune_ms = mc.batch_tune(hs, nh, seed, bopts, stream)
     tune_s = time.perf_counter() - t0
     for w in range(args.warmup):
         flush.zero_()
-        mc.run_batch(hs, nh, seed + w, None, stream)
+        mc.run_batch(hs, nh, seed + w, bopts, stream)
     torch.cuda.synchronize()
     clocks = Clocks(local)
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -332,7 +334,7 @@ def bench_batch(args, torch, mc, batch, n_total, desc, world, local):
         if not args.no_flush:
             flush.zero_()
         ev_s[k].record(stream)
-        mc.run_batch(hs, nh, seed + 100 + k, None, stream)
+        mc.run_batch(hs, nh, seed + 100 + k, bopts, stream)
         ev_e[k].record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -342,7 +344,7 @@ def bench_batch(args, torch, mc, batch, n_total, desc, world, local):
     ms_per_step = sum(step_ms) / len(step_ms)
     value = n_total / (ms_per_step / 1000.0)
     # per-problem completion times since the launch started (device clock), untimed extra step
-    wall = mc.run_batch(hs, nh, seed + 100, None, stream, wall=True)
+    wall = mc.run_batch(hs, nh, seed + 100, bopts, stream, wall=True)
     cs = [p.counters() for p in ps]
     flights = sum(c["flight"] for c in cs)
     scores = sum(c["scores"] for c in cs)

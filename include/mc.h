@@ -193,8 +193,9 @@ typedef struct {
                              when a tally deals its time pieces out over the warp and the 80-register
                              build otherwise, as many CTAs as fit */
   uint64_t max_iterations;/* watchdog: event iterations before MC_ERR_TIMEOUT (0 = 2^20) */
-  int aggregate_atomics;  /* 1 = warp-aggregated tally atomics, 0 = one atomic per score,
-                             -1 = auto (default): aggregate a small tally that is not striped */
+  int aggregate_atomics;  /* 1 = warp-aggregated tally atomics (staged per warp, same-bin scores
+                             summed before one atomic), 0 = one atomic per score at once,
+                             -1 = default (currently 0: faster on every measured workload) */
   int ww_enable;          /* 1 = apply the weight-window table set by mc_ww_set_table */
   uint64_t log_first, log_count; /* log every event of histories [log_first, +log_count) */
   uint64_t log_capacity;  /* event records kept (0 = 64 per logged history) */

@@ -519,10 +519,12 @@ void fill_run_params(const mc_problem* p, const mc_run_opts& o, uint64_t n_histo
   P.row = p->row;
   P.stripe_stride = (uint64_t)nb * p->row;
   P.tally_fp64 = o.tally_mode == MC_TALLY_FP64;
-  // auto: aggregate only a small tally that could not be striped (many lanes per hot bin)
-  P.aggregate = o.aggregate_atomics >= 0
-                    ? o.aggregate_atomics
-                    : (stripes == 1 && (double)nb * (double)bins * 8.0 < 32.0 * 1048576.0 ? 1 : 0);
+  // auto: one fire-and-forget atomic per score.  Warp aggregation (match + shuffle tree through a
+  // shared-memory stage) was the default for small unstriped tallies, i.e. the batched launch; there
+  // it measured slower (the 256-problem workload: 85 ms per launch aggregated, 69 ms direct), so it
+  // is kept only as an option for tallies with a few very hot bins.
+  (void)bins;
+  P.aggregate = o.aggregate_atomics >= 0 ? o.aggregate_atomics : 0;
   P.fixed_scale = std::ldexp(1.0, o.fixed_bits);
   P.fixed_scale_f = (float)P.fixed_scale;
   P.n_hist = n_histories;
@@ -1620,7 +1622,7 @@ extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t
   P.row = p->row;
   P.stripe_stride = (uint64_t)nb * p->row;
   P.tally_fp64 = o.tally_mode == MC_TALLY_FP64;
-  P.aggregate = o.aggregate_atomics >= 0 ? o.aggregate_atomics : 1;
+  P.aggregate = o.aggregate_atomics >= 0 ? o.aggregate_atomics : 0;  // as mc_run
   P.fixed_scale = std::ldexp(1.0, o.fixed_bits);
   P.fixed_scale_f = (float)P.fixed_scale;
   P.history_mode = o.algorithm == MC_ALG_HISTORY;
