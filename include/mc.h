@@ -430,6 +430,15 @@ int mc_mlp_train(mc_mlp* m, const float* x, const float* target, const float* wt
 int mc_ww_learn(mc_problem* p, mc_mlp* m, int tally_id, int epochs, float lr, double extrap_slope,
                 double extrap_efolds, double info[5]);
 
+/* The same with a network the problem owns (created by the first mc_ww_set_mlp, released with the
+ * problem), for callers that do not manage an mc_mlp.  mc_ww_set_mlp loads n == mc_mlp_param_count()
+ * parameters given as BF16 bit patterns (host array; the order of mc_mlp_set_params; non-finite
+ * values are MC_ERR_INVALID).  mc_ww_train runs one learning round on mesh tally tally_id of the
+ * problem's last run (mc_ww_learn steps 1, 3 and 4: no extrapolation past the resolved region), or
+ * returns MC_ERR_STATE when no weights were loaded. */
+int mc_ww_set_mlp(mc_problem* p, const uint16_t* bf16_weights, size_t n);
+int mc_ww_train(mc_problem* p, int tally_id, int epochs, float lr);
+
 /* Bytes of sampling, geometry and tally tables that mc_problem_create copied to the device
  * (both tracking precisions); 0 for NULL. */
 size_t mc_problem_table_bytes(const mc_problem* p);

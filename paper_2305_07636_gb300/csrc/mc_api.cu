@@ -660,6 +660,7 @@ void mc_problem_destroy(mc_problem* p) {
   p->d_cbank.release();
   p->d_pc.release();
   p->d_comb.release();
+  if (p->own_mlp) mc_mlp_destroy(p->own_mlp);
   for (int i = 0; i < 3; ++i)
     if (p->ev[i]) cudaEventDestroy(p->ev[i]);
   delete p;
@@ -2021,4 +2022,32 @@ extern "C" int mc_ww_learn(mc_problem* p, mc_mlp* m, int tally_id, int epochs, f
     info[4] = n_extra;
   }
   return MC_OK;
+}
+
+// The problem's own network, for callers that do not manage an mc_mlp (see mc.h).
+extern "C" int mc_ww_set_mlp(mc_problem* p, const uint16_t* bf16_weights, size_t n) {
+  g_err.clear();
+  if (!p || !bf16_weights) return fail(MC_ERR_INVALID, "NULL argument");
+  if (n != (size_t)mc_mlp_param_count())
+    return fail(MC_ERR_INVALID, "expected %d BF16 parameters, got %zu", mc_mlp_param_count(), n);
+  std::vector<double> params(n);
+  for (size_t i = 0; i < n; ++i) {
+    const uint32_t bits = (uint32_t)bf16_weights[i] << 16;  // BF16 is the top half of an FP32
+    float f;
+    std::memcpy(&f, &bits, sizeof(f));
+    if (!std::isfinite(f)) return fail(MC_ERR_INVALID, "parameter %zu is not finite", i);
+    params[i] = (double)f;
+  }
+  if (!p->own_mlp) {
+    const int rc = mc_mlp_create(&p->own_mlp);
+    if (rc != MC_OK) return rc;
+  }
+  return mc_mlp_set_params(p->own_mlp, params.data(), n);
+}
+
+extern "C" int mc_ww_train(mc_problem* p, int tally_id, int epochs, float lr) {
+  g_err.clear();
+  if (!p) return fail(MC_ERR_INVALID, "problem is NULL");
+  if (!p->own_mlp) return fail(MC_ERR_STATE, "no network: load its weights with mc_ww_set_mlp first");
+  return mc_ww_learn(p, p->own_mlp, tally_id, epochs, lr, 0.0, 0.0, nullptr);
 }

@@ -76,6 +76,7 @@ void fill_run_params(const mc_problem* p, const mc_run_opts& o, uint64_t n_histo
 
 struct mc_problem {
   int dev = 0;
+  mc_mlp* own_mlp = nullptr;  // mc_ww_set_mlp / mc_ww_train's network, released with the problem
   int G = 0, M = 0, n_surf = 0, n_cell = 0, n_tally = 0;
   int total_bins = 0, leak_offset = 0;
   bool range = false;  // some mesh tally is scored by the range walk (kernel build)

@@ -151,6 +151,8 @@ SIGNATURES = {
                                C.c_void_p, C.c_void_p]),
     "mc_ww_learn": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_float, C.c_double,
                               C.c_double, DP]),
+    "mc_ww_set_mlp": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint16), C.c_size_t]),
+    "mc_ww_train": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_float]),
     "mc_run_static": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.POINTER(mc_run_opts),
                                 C.c_void_p, C.c_void_p, C.c_void_p]),
     "mc_run_tune": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.POINTER(mc_run_opts), C.c_void_p,
@@ -598,3 +600,21 @@ def ww_learn(problem_h: int, mlp: "Mlp", tally_id: int, epochs: int, lr: float,
                             info.ctypes.data_as(DP)))
     return {"points": int(info[0]), "loss": float(info[1]), "scale": float(info[2]),
             "phi_ref": float(info[3]), "extrapolated": int(info[4])}
+
+
+def ww_set_mlp(problem_h: int, bf16_bits) -> None:
+    """mc_ww_set_mlp: load the problem's own network from BF16 bit patterns (uint16)."""
+    a = np.ascontiguousarray(np.asarray(bf16_bits, dtype=np.uint16).ravel())
+    check(lib().mc_ww_set_mlp(C.c_void_p(problem_h), a.ctypes.data_as(C.POINTER(C.c_uint16)), a.size))
+
+
+def ww_train(problem_h: int, tally_id: int, epochs: int, lr: float) -> None:
+    """mc_ww_train: one learning round of the weight windows with the problem's own network."""
+    check(lib().mc_ww_train(C.c_void_p(problem_h), int(tally_id), int(epochs), float(lr)))
+
+
+def to_bf16_bits(params) -> np.ndarray:
+    """BF16 bit patterns (round to nearest even) of FP64 parameters."""
+    f = np.asarray(params, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    rounded = (f + 0x7FFF + ((f >> 16) & 1)) >> 16
+    return rounded.astype(np.uint16)

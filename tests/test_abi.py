@@ -22,9 +22,22 @@ def declared_functions():
 
 def test_header_declares_the_entry_points():
     names = declared_functions()
-    for core in ("mc_problem_create", "mc_run", "mc_tally_get", "mc_problem_destroy",
-                 "mc_wait", "mc_counters_get", "mc_event_log", "mc_philox"):
+    # the calls of the boundary sketch, and the ones this library adds
+    for core in ("mc_problem_create", "mc_run", "mc_run_batch", "mc_tally_get", "mc_tally_shape",
+                 "mc_ww_set_mlp", "mc_ww_train", "mc_event_log", "mc_problem_destroy", "mc_last_error",
+                 "mc_wait", "mc_counters_get", "mc_philox", "mc_run_eigen", "mc_run_tune"):
         assert core in names
+
+
+def test_bf16_bit_patterns():
+    import numpy as np
+    x = np.array([1.0, -2.5, 3.140625, 1.0 + 2.0**-8, 1.0 + 3 * 2.0**-9, 0.0, 1e-30])
+    b = mc.to_bf16_bits(x)
+    back = (b.astype(np.uint32) << 16).view(np.float32)
+    assert back[0] == 1.0 and back[1] == -2.5 and back[2] == 3.140625 and back[5] == 0.0
+    assert back[3] == 1.0  # a tie rounds to even
+    assert back[4] == 1.0 + 2.0**-7  # above the tie rounds up
+    assert abs(back[6] - 1e-30) < 1e-32
 
 
 def test_library_exports_every_declared_symbol():

@@ -154,3 +154,28 @@ def conserved(c):
     started = c["source"] + c["secondary"] + c["ww_split"]
     ended = c["capture"] + c["production"] + c["leak"] + c["census"] + c["lost"] + c["ww_kill"]
     return started == ended
+
+
+def test_problem_owned_network_entry_points(torch):
+    """mc_ww_set_mlp / mc_ww_train: the problem's own network, loaded from BF16 bit patterns and
+    trained on the problem's tally, gives windows that split and roulette and keep the detector
+    estimate unbiased; training before loading is MC_ERR_STATE, a wrong count MC_ERR_INVALID."""
+    prob = P.slab_stack(thickness=10.0, n_layers=5, detector=2.0, ww_bin=1.0, name="thin")
+    p = mc.Problem(prob)
+    p.run(4_000_000, 1, tally_mode="fp64")
+    ma, sa = _detector(p, 32)
+    with pytest.raises(mc.McError) as e:
+        mc.ww_train(p.h, 1, 10, 1e-3)
+    assert e.value.code == mc.MC_ERR_STATE
+    bits = mc.to_bf16_bits(P.mlp_init(seed=4))
+    with pytest.raises(mc.McError) as e:
+        mc.ww_set_mlp(p.h, bits[:-1])
+    assert e.value.code == mc.MC_ERR_INVALID
+    mc.ww_set_mlp(p.h, bits)
+    mc.ww_train(p.h, 1, 2000, 3e-3)
+    p.run(500_000, 2, tally_mode="fp64", ww_enable=1, bank_capacity=1 << 22)
+    mw, sw = _detector(p, 32)
+    c = p.counters()
+    assert conserved(c) and c["ww_split"] > 0 and c["ww_kill"] > 0
+    assert abs(mw - ma) < 4.0 * np.hypot(sa, sw), (mw, ma, sw, sa)
+    p.close()
