@@ -45,3 +45,30 @@ def test_philox_equals_curand(tmp_path):
         assert np.array_equal(d_out.cpu().numpy().view(np.uint32), out)
         for i in range(0, n, 97):  # and the oracle's
             assert oracle.philox((seed & 0xFFFFFFFF, seed >> 32), [int(v) for v in ctr[i]]) == [int(v) for v in out[i]]
+
+
+def test_philox_uniformity_on_1e8_words():
+    """10^8 output words of the device generator (counters (i, 0, seed-derived, 0)): chi-square of a
+    1000-bin histogram and Kolmogorov-Smirnov on 10^6 of them against the uniform law, and the lag-1
+    serial correlation of consecutive words, at the 10^-3 level."""
+    import torch
+    from scipy import stats
+    n_blocks = 25_000_000  # x 4 words
+    ctr = torch.zeros((n_blocks, 4), dtype=torch.int32, device="cuda")
+    ctr[:, 0] = torch.arange(n_blocks, dtype=torch.int64, device="cuda").to(torch.int32)
+    ctr[:, 2] = 12345
+    out = torch.zeros_like(ctr)
+    mc.philox(0x243F6A8885A308D3, ctr.data_ptr(), out.data_ptr(), n_blocks)
+    torch.cuda.synchronize()
+    w = out.view(-1).to(torch.int64) & 0xFFFFFFFF  # unsigned words
+    u = (w.to(torch.float64) + 0.5) / 4294967296.0
+    hist = torch.bincount((u * 1000).to(torch.int64), minlength=1000).cpu().numpy()
+    e = u.numel() / 1000
+    chi2 = float(((hist - e) ** 2 / e).sum())
+    assert stats.chi2.sf(chi2, 999) > 1e-3, chi2
+    sample = u[:: 100].cpu().numpy()
+    assert stats.kstest(sample, "uniform").pvalue > 1e-3
+    x = u - 0.5
+    r = float((x[:-1] * x[1:]).mean() / (x * x).mean())
+    assert abs(r) < 3.3 / np.sqrt(u.numel()), r  # ~1e-3 two-sided for a correlation of 0
+    del ctr, out, w, u, x
