@@ -1,11 +1,14 @@
 #!/usr/bin/env python
 """Benchmark of the GPU random walk: particle histories per second and figure of merit.
 
-Workload (default): the 7-group infinite homogeneous medium (reflective 10 cm cube, pulse in
-group 1 at t = 0, 100 log-spaced time bins, census at 1e-3 s), 1e7 histories per step, FP32
-tracking, int64 fixed-point tallies, 32 statistical batches.  One step = one mc_run over all
-histories: source sampling, the persistent event loop (flight, track-length scoring, collision,
-surface), and the batch statistics.  Inputs are seeded synthetic cross sections.
+Workload (default): the largest single-GPU configuration, a 17 x 17 lattice of pins (r 0.54 cm,
+pitch 1.26 cm) in a reflective box, 7 groups, three seeded materials with secondary production
+scaled to spectral radius 0.9, uniform volumetric pulse source, a 34 x 34 x 7 x 50 space-group-time
+mesh tally (404,600 bins), 1e8 histories per step, FP32 tracking, int64 fixed-point tallies, 32
+statistical batches.  One step = one mc_run over all histories: source sampling, the persistent
+event loop (flight, track-length scoring, collision, surface, secondaries), and the batch
+statistics.  Inputs are seeded synthetic cross sections.  `--workload config2` (7-group infinite
+medium pulse, 1e7 histories) and the others listed in `workload()` print the same line.
 
 Our arm (default): times K steps with CUDA events on the launching stream after W warm-up steps;
 L2 is flushed (256 MB write) before every timed step, outside the timed interval.  The `e2e`
@@ -77,20 +80,13 @@ def profiled_value(summary, kernel, key):
     return None
 
 
-def profiled_traffic(summary, kernel):
-    """DRAM bytes (read + write) per launch from a committed ncu summary under profiles/, or None
-    when the summary was taken on other kernel sources than these."""
-    import re
-    try:
-        with open(os.path.join(ROOT, "profiles", summary)) as f:
-            text = f.read()
-    except OSError:
-        return None
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    d = re.search(r"source_digest:\s*([0-9a-f]+)", text)
-    if m and d and d.group(1) == source_digest(kernel):
-        return float(m.group(1))
-    return None
+def traffic_per_launch(workload, flights):
+    """DRAM bytes (read + write) of one transport launch of this run: the committed ncu summary's
+    DRAM bytes per flight (captured on a smaller case of the same workload, whose traffic grows in
+    proportion to the flights) times this launch's flights; None when the summary was taken on
+    other kernel sources than these."""
+    per_flight = profiled_value(f"k_transport_{workload}.md", "k_transport", "traffic_bytes_per_flight")
+    return None if per_flight is None else per_flight * flights
 
 
 def workload(name):
@@ -103,7 +99,8 @@ def workload(name):
     if name == "config1":
         return P.config1(), 10_000_000, "config1: 1-group slab, 1e7 histories"
     if name == "config3":
-        return P.config3(), 10_000_000, "config3: 17x17 pin lattice, 7 groups, 1e7 histories"
+        return P.config3(), 100_000_000, ("config3: 17x17 pin lattice (r 0.54, pitch 1.26 cm, reflective), 7 groups, "
+                                          "3 seeded materials, spectral radius 0.9, mesh 34x34x7x50, 1e8 histories")
     if name == "config4":
         return P.config4(), 1_000_000, ("config4: 200 cm stack of 40 layers (4 seeded materials, Sigma_t "
                                         "0.5-3, c 0.3-0.95), 7 groups, cosine surface source at x=0, "
@@ -152,9 +149,9 @@ def issue_roofline(workload, n, flights, kernel_ms, clk):
     x the SM clock seen during the timed region (one warp instruction per scheduler per clock): the
     ceiling this latency-bound kernel actually meets.  The warp instructions per flight come from the
     committed ncu summary of the same kernel sources (None when they changed)."""
-    per_flight = profiled_value(f"k_transport_{workload}_1e7.md", "k_transport", "warp_instructions_per_flight")
+    per_flight = profiled_value(f"k_transport_{workload}.md", "k_transport", "warp_instructions_per_flight")
     mhz = (clk or {}).get("sm_mhz") or 2070.0
-    if per_flight is None or n != 10_000_000:
+    if per_flight is None:
         return None
     achieved = per_flight * flights / (kernel_ms / 1000.0)
     peak = 152 * 4 * mhz * 1e6
@@ -417,7 +414,7 @@ def bench_batch(args, torch, mc, batch, n_total, desc, world, local):
                                  "launch": "one mc_run per problem, shortest first, same stream"},
                   "speedup_vs_sequential": value / seq_value},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic("k_transport_batch_config5.md", "k_transport_batch"),
+                     "frac": achieved / peak, "traffic": profiled_value("k_transport_batch_config5.md", "k_transport_batch", "traffic_bytes_per_launch"),
                      "kernel": "k_transport_batch<float>", "kernel_ms": kernel_ms,
                      "algorithmic_bytes": algo_bytes, "peak_kind": peak_kind,
                      "l2_atomic": {"achieved": scores / (kernel_ms / 1000.0) / 1e9,
@@ -650,10 +647,10 @@ def bench_learned_ww(args, torch, mc):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)  # ~0.5 s timed: enough for clock samples
+    ap.add_argument("--steps", type=int, default=20)  # ~4 s timed on the default workload
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="config2")
+    ap.add_argument("--workload", default="config3")
     ap.add_argument("--histories", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -758,9 +755,11 @@ def main():
     peak, peak_kind = peaks()
     algo_bytes = c["flight"] * BYTES_PER_FLIGHT
     achieved = algo_bytes / (tr_ms / 1000.0) / 1e9
-    # tally scoring against the L2 atomic roofline, measured live on the tally's footprint
-    tally_elems = sum(int(np.prod(mc.tally_shape(p.h, t))) for t in range(len(prob["tallies"]) + 1))
-    atom_peak = mc.atomic_peak(min(1 << 27, max(1, tally_elems * opts.n_batches * 16)))
+    # tally scoring against the L2 atomic roofline, measured live on the run's own tally footprint
+    # (stripes x batches x row elements, as the library laid it out)
+    stripes, n_batches, row = mc.tally_layout(p.h)
+    footprint = stripes * n_batches * row
+    atom_peak = mc.atomic_peak(min(1 << 27, max(1, footprint)))
     atom_rate = c["scores"] / (tr_ms / 1000.0)
 
     # end to end through the public API with host buffers
@@ -792,13 +791,15 @@ def main():
                 "rel_err_per_step": rel, "seconds_to_5pct": t_5pct},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": profiled_traffic(f"k_transport_{args.workload}_1e7.md", "k_transport") if n == 10_000_000 else None,
+                     "traffic": traffic_per_launch(args.workload, c["flight"]),
                      "kernel": "k_transport<float>", "kernel_ms": tr_ms,
                      "algorithmic_bytes": algo_bytes, "peak_kind": peak_kind,
                      "l2_atomic": {"achieved": atom_rate / 1e9, "peak": atom_peak / 1e9,
                                    "unit": "G atomics/s", "frac": atom_rate / atom_peak,
                                    "scores_per_flight": c["scores"] / c["flight"],
-                                   "peak_kind": "measured live (mc_atomic_peak, random 64-bit adds)"},
+                                   "peak_kind": "measured live (mc_atomic_peak, random 64-bit adds over the "
+                                                f"run's tally footprint: {stripes} stripes x {n_batches} "
+                                                f"batches x {row} elements)"},
                      "issue": issue_roofline(args.workload, n, c["flight"], tr_ms, clk)},
         "counters": {k: c[k] for k in ("flight", "collision", "surface", "census", "iterations")},
         "algorithm": algorithm,

@@ -370,6 +370,12 @@ int mc_trace_get(mc_problem* p, uint64_t* t_ns, uint64_t* items, uint64_t* sourc
  * the transport kernel and around the batch-statistics kernel (milliseconds).  Synchronises. */
 int mc_run_timing(mc_problem* p, double* transport_ms, double* stats_ms);
 
+/* Device layout of the last run's batch tallies (the track-length tally scoring of Section 3 writes
+ * into it): *stripes copies of *n_batches rows of *row int64 (or double) elements each, so the
+ * scoring atomics of a run spread over stripes x n_batches x row elements.  Any pointer may be
+ * NULL.  MC_ERR_STATE before the first run. */
+int mc_tally_layout(const mc_problem* p, int* stripes, int* n_batches, uint64_t* row);
+
 /* Weight windows (variance reduction for deep penetration; the paper's runs are analog or use
  * implicit capture, §3).  Sets the window-centre table w_c over an (x, y, z) mesh and all groups:
  * edges = x[nx+1], y[ny+1], z[nz+1] (increasing), centre[nz][ny][nx][G] (host arrays, copied;
@@ -453,18 +459,21 @@ const char* mc_last_error(void);
 /* Bytes of the library's static device scratch used by mc_run_static. */
 #define MC_STATIC_SCRATCH_BYTES (32u << 20)
 
-/* mc_run for callers that cannot allocate device memory: code that runs while a CUDA graph is
- * being captured (cudaMalloc is not allowed then), applications that hand all device memory to
- * their own pool or allocator up front, and allocator or memory-pressure callbacks that must not
- * re-enter the allocator.  This call takes no memory from cudaMalloc, cudaFree or any allocating
+/* mc_run for callers that cannot allocate device memory: applications that hand all device memory
+ * to their own pool or allocator up front (a further cudaMalloc fails or steals from the pool),
+ * allocator or memory-pressure callbacks that must not re-enter the allocator, and hosts that fix
+ * their device-memory budget at start-up.  This call takes no memory from cudaMalloc, cudaFree or any allocating
  * library: its control block, particle banks (32768 particles each), batch tallies and statistics
  * live in one MC_STATIC_SCRATCH_BYTES array that the library declares at file scope, reserved on
  * every GPU that loads the library until the process exits.  The paper has no counterpart; it is
  * an interface for such callers only.
  *   p            problem from mc_problem_create (created beforehand, outside the restricted code)
  *   n_histories, seed, opts   as for mc_run; opts may not ask for an event log, more than 32768
- *                particles in flight, or tally_stripes > 1 (MC_ERR_INVALID)
- *   mean, std_err  DEVICE arrays of at least the problem's total bin count (every mesh tally's
+ *                particles in flight, fewer than 1024 (a non-zero bank_capacity below 1024), or
+ *                tally_stripes > 1 (MC_ERR_INVALID)
+ *   mean, std_err  DEVICE arrays of the problem's device (8-byte aligned; host, misaligned or
+ *                other-device pointers are MC_ERR_INVALID before any launch) of at least the
+ *                problem's total bin count (every mesh tally's
  *                bins in tally order, then the leakage bins), caller-allocated; they receive the
  *                per-source-particle mean and standard error, or NaN in every entry if the run
  *                failed on the device (bank overflow, watchdog, lost particle)

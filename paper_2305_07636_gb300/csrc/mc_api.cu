@@ -810,6 +810,7 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
     while (cap < 2 * n_histories && cap < limit) cap <<= 1;
   }
   if (cap < 1024) return fail(MC_ERR_INVALID, "bank_capacity must be >= 1024");
+  if (cap >= (1ull << 32)) return fail(MC_ERR_INVALID, "bank_capacity must be below 2^32");
   const size_t bank_bytes = (size_t)cap * 16 * lanes;
   rc = p->d_banks.ensure(4 * bank_bytes, p->dev);
   if (rc != MC_OK) return rc;
@@ -953,6 +954,7 @@ int mc_run_eigen(mc_problem* p, uint64_t n_per_cycle, int n_inactive, int n_acti
     while (cap < 2 * N && cap < (1ull << 22)) cap <<= 1;
   }
   if (cap < 1024) return fail(MC_ERR_INVALID, "bank_capacity must be >= 1024");
+  if (cap >= (1ull << 32)) return fail(MC_ERR_INVALID, "bank_capacity must be below 2^32");
   const size_t bank_bytes = (size_t)cap * 16 * lanes;
   rc = p->d_banks.ensure(4 * bank_bytes, p->dev);
   if (rc != MC_OK) return rc;
@@ -1456,6 +1458,15 @@ int mc_run_timing(mc_problem* p, double* transport_ms, double* stats_ms) {
   return MC_OK;
 }
 
+int mc_tally_layout(const mc_problem* p, int* stripes, int* n_batches, uint64_t* row) {
+  if (!p) return fail(MC_ERR_INVALID, "problem is NULL");
+  if (!p->has_run) return fail(MC_ERR_STATE, "no run yet");
+  if (stripes) *stripes = (int)p->stripes;
+  if (n_batches) *n_batches = p->n_batches;
+  if (row) *row = p->row;
+  return MC_OK;
+}
+
 int mc_atomic_peak(uint64_t span, double* atomics_per_s) {
   g_err.clear();
   if (!atomics_per_s || span < 1 || span > (1ull << 27)) return fail(MC_ERR_INVALID, "span outside [1, 2^27]");
@@ -1581,11 +1592,23 @@ extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t
   if (o.bank_capacity > kStaticBank)
     return fail(MC_ERR_INVALID, "bank_capacity %llu exceeds the static limit of %llu particles",
                 (unsigned long long)o.bank_capacity, (unsigned long long)kStaticBank);
+  if (o.bank_capacity > 0 && o.bank_capacity < 1024) return fail(MC_ERR_INVALID, "bank_capacity must be >= 1024");
   if (o.tally_stripes > 1) return fail(MC_ERR_INVALID, "mc_run_static keeps a single tally copy");
   int dev;
   int rc = current_device(&dev);
   if (rc != MC_OK) return rc;
   if (dev != p->dev) return fail(MC_ERR_STATE, "problem was created on device %d, current is %d", p->dev, dev);
+  // the outputs must be 8-byte aligned device memory of this device (a runtime query, no allocation)
+  if (((uintptr_t)mean | (uintptr_t)std_err) & 7u) return fail(MC_ERR_INVALID, "mean and std_err must be 8-byte aligned");
+  for (const double* q : {mean, std_err}) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MC_ERR_INVALID, "mean and std_err must be device arrays");
+    }
+    if ((a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != dev)
+      return fail(MC_ERR_INVALID, "mean and std_err must be device arrays of device %d", dev);
+  }
   const int fp64 = o.precision == MC_FP64;
   const int lanes = fp64 ? kLanesFP64 : kLanesFP32;
   const uint64_t cap = kStaticBank;
@@ -1609,6 +1632,8 @@ extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t
   cudaStream_t s = (cudaStream_t)stream;
   RunParams P;
   std::memset(&P, 0, sizeof(P));
+  // the parameters mc_run sets, then the addresses in the static array and the settings of this call
+  fill_run_params(p, o, n_histories, seed, 1, P);
   for (int side = 0; side < 2; ++side)
     for (int l = 0; l < lanes; ++l) {
       P.S[side][l] = (uint4*)(base + off_banks + (size_t)side * bank_bytes + (size_t)l * cap * 16);
@@ -1619,46 +1644,11 @@ extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t
   P.ctl = (Ctl*)base;
   P.sticky = (int*)(base + off_sticky);
   P.tally = base + off_tally;
-  P.tally_stripes = 1;
-  P.row = p->row;
-  P.stripe_stride = (uint64_t)nb * p->row;
-  P.tally_fp64 = o.tally_mode == MC_TALLY_FP64;
-  P.aggregate = o.aggregate_atomics >= 0 ? o.aggregate_atomics : 0;  // as mc_run
-  P.fixed_scale = std::ldexp(1.0, o.fixed_bits);
-  P.fixed_scale_f = (float)P.fixed_scale;
   P.history_mode = o.algorithm == MC_ALG_HISTORY;
   P.trace = nullptr;
   P.trace_cap = 0;
-  P.n_hist = n_histories;
-  P.n_sources = n_histories;
-  set_census(P, reinterpret_cast<const TableHeader*>(p->blob[1].data())->t_census, false);
-  P.hist_per_batch = (n_histories + nb - 1) / nb;
   P.h_first = o.first_history;
-  {
-    const double mg = std::floor(4294967296.0 * (double)nb / (double)n_histories);
-    P.batch_magic = mg >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)mg;
-  }
-  P.n_batches = nb;
-  P.blob_bytes = (int)p->blob[fp64].size();
-  P.blob = (const uint4*)p->d_blob[fp64].ptr;
-  P.seed = seed;
-  P.max_iter = o.max_iterations ? o.max_iterations : (1ull << 20);
   P.spin_limit = 1ull << 22;
-  P.implicit = o.implicit_capture;
-  P.wr_cutoff = o.wr_cutoff;
-  P.wr_survival = o.wr_survival;
-  if (o.ww_enable) {
-    const double* wb = (const double*)p->d_ww.ptr;
-    P.ww_on = 1;
-    P.ww_nx = p->ww_n[0];
-    P.ww_ny = p->ww_n[1];
-    P.ww_nz = p->ww_n[2];
-    P.ww_edges = wb;
-    P.ww_center = wb + (p->ww_n[0] + 1) + (p->ww_n[1] + 1) + (p->ww_n[2] + 1);
-    P.ww_upper = 2.0;
-    P.ww_lower = 0.5;
-    P.ww_split_max = 10;
-  }
   // the array keeps the previous call's contents: clear what must start at zero
   CK(cudaMemsetAsync(base, 0, off_banks, s));
   CK(cudaMemsetAsync(base + off_tally, 0, tally_bytes, s));

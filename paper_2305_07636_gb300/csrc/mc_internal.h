@@ -122,7 +122,10 @@ __host__ __device__ inline double bin_value_factor(const char* blob, uint64_t bi
 
 // ---- device control block, one per problem
 struct Ctl {
-  unsigned long long front[3], back[3], birth[3], hstart[3];  // rotated per iteration (mod 3)
+  // rotated per iteration (mod 3): the next transport bank's fill (collision-pending particles from
+  // the front in the low 32 bits, surface-pending ones from the back in the high 32 bits; cap_s <
+  // 2^32), the birth bank's fill and the first history not yet started
+  unsigned long long fb[3], birth[3], hstart[3];
   unsigned long long next[3];                                 // dynamic item claim counters
   unsigned int bar_count, bar_gen;
   int status, pad;

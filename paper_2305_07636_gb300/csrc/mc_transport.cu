@@ -60,8 +60,10 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
     __syncthreads();
     if (s_status != 0) break;
     // the counters cannot exceed the banks (overflow stops the run above); clamp regardless
-    uint64_t nF = ld_volatile_u64(&ctl->front[cur]);
-    uint64_t nS = ld_volatile_u64(&ctl->back[cur]);
+    // the next bank's fill: collision-pending particles in the low half, surface-pending ones in the high half
+    const unsigned long long fb = ld_volatile_u64(&ctl->fb[cur]);
+    uint64_t nF = fb & 0xFFFFFFFFull;
+    uint64_t nS = fb >> 32;
     uint64_t nB = ld_volatile_u64(&ctl->birth[cur]);
     nB = nB < P.cap_b ? nB : P.cap_b;
     nF = nF < P.cap_s ? nF : P.cap_s;
@@ -85,8 +87,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
     if (threadIdx.x == 0) bc.hold_at = P.cap_b / 2 > nB - nBt ? P.cap_b / 2 - (nB - nBt) : 0ull;
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-      ctl->front[old] = 0ull;
-      ctl->back[old] = 0ull;
+      ctl->fb[old] = 0ull;
       ctl->birth[old] = 0ull;
       ctl->next[old] = 0ull;
       ctl->hstart[nxt] = h0 + nSrc;
@@ -159,11 +160,22 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
       if (have) queue_load(p, wq, kWarpQ, qn - nfly + lane);
       __syncwarp();
       qn -= nfly;
-      bool out = false, again = false;
+      bool again = false;
       R l = R(0);
       uint32_t pend = PEND_NONE;
       Hit hit;
       const bool flies = have && flight_plan(P, T, p, &bc, l, pend, hit);
+      // The particles that survive this flight into the next bank are known once it is planned:
+      // a collision other than a capture (front of the bank) or a surface crossing (back); only
+      // the watchdog below can still end one of them, and it stops the run.  Their slots are
+      // reserved now with one atomic per warp on the packed pair of counts (front in the low
+      // half, back in the high half), so the atomic's latency hides behind the scoring.
+      const bool wF = !drain && flies && pend == PEND_COLL && hit.chan != CHAN_CAPTURE;
+      const bool wS = !drain && flies && pend == PEND_SURF;
+      const unsigned mF = __ballot_sync(0xFFFFFFFFu, wF), mS = __ballot_sync(0xFFFFFFFFu, wS);
+      unsigned long long bFS = 0;
+      if (lane == 0 && (mF | mS))
+        bFS = atomicAdd(&ctl->fb[nxt], (unsigned long long)__popc(mF) | ((unsigned long long)__popc(mS) << 32));
       if (P.eigen && flies) ktl += eigen_tl_fixed(T, p, l);
       score_segment_warp<R, RANGE>(T, P, p, l, stripe_off + (uint64_t)(p.elem >> 16) * row,
                                    flies && (!P.eigen || P.eigen_score), stage, scored);
@@ -176,10 +188,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
           set_status(P, MC_ERR_TIMEOUT);
           alive = false;
         }
-        if (alive) {
-          if (drain) again = handle_pending(P, T, p, Bout, bcount, &bc, row, stripe_off);
-          else out = true;
-        }
+        if (alive && drain) again = handle_pending(P, T, p, Bout, bcount, &bc, row, stripe_off);
       }
       if (drain) {
         const unsigned m = __ballot_sync(0xFFFFFFFFu, again);
@@ -188,18 +197,10 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
         __syncwarp();
         continue;
       }
-      // append survivors, partitioned by their pending event: one atomic per warp per side
-      const bool wF = out && pk_pend(p.pk) == PEND_COLL;
-      const bool wS = out && pk_pend(p.pk) == PEND_SURF;
-      const unsigned mF = __ballot_sync(0xFFFFFFFFu, wF), mS = __ballot_sync(0xFFFFFFFFu, wS);
+      // append the survivors into the reserved slots, partitioned by their pending event
       if (mF | mS) {
-        unsigned long long bF = 0, bS = 0;
-        if (lane == 0) {
-          if (mF) bF = atomicAdd(&ctl->front[nxt], (unsigned long long)__popc(mF));
-          if (mS) bS = atomicAdd(&ctl->back[nxt], (unsigned long long)__popc(mS));
-        }
-        bF = __shfl_sync(0xFFFFFFFFu, bF, 0);
-        bS = __shfl_sync(0xFFFFFFFFu, bS, 0);
+        bFS = __shfl_sync(0xFFFFFFFFu, bFS, 0);
+        const uint64_t bF = bFS & 0xFFFFFFFFull, bS = bFS >> 32;
         // front + back <= items transported <= cap_s, so the two regions never meet
         if (wF) {
           const uint64_t i = bF + __popc(mF & lt);

@@ -131,6 +131,7 @@ SIGNATURES = {
     "mc_event_log": (C.c_int, [C.c_void_p, C.POINTER(mc_event), C.c_size_t,
                                C.POINTER(C.c_size_t)]),
     "mc_run_timing": (C.c_int, [C.c_void_p, DP, DP]),
+    "mc_tally_layout": (C.c_int, [C.c_void_p, IP, IP, C.POINTER(C.c_uint64)]),
     "mc_trace_get": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
                                C.POINTER(C.c_uint64), C.c_size_t, C.POINTER(C.c_size_t)]),
     "mc_problem_table_bytes": (C.c_size_t, [C.c_void_p]),
@@ -456,6 +457,13 @@ def run_timing(h: int):
     a, b = C.c_double(0), C.c_double(0)
     check(lib().mc_run_timing(C.c_void_p(h), C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def tally_layout(h: int):
+    """mc_tally_layout: (stripes, n_batches, row) of the last run's device tallies."""
+    st, nb, row = C.c_int(0), C.c_int(0), C.c_uint64(0)
+    check(lib().mc_tally_layout(C.c_void_p(h), C.byref(st), C.byref(nb), C.byref(row)))
+    return st.value, nb.value, row.value
 
 
 def trace_get(h: int, cap: int = 65536):

@@ -61,6 +61,64 @@ def test_forward_and_gradients_match_oracle(torch):
     net.close()
 
 
+def _magnitude_backprop(params, x, seed, H=64):
+    """Backpropagation of |seed_n| through the network with every factor taken in absolute value
+    (|W|, |h|, |1 - h^2|): element i is sum over samples and paths of the magnitudes of the products
+    that make up gradient element i.  A relative perturbation e of every rounded factor on a path
+    (BF16 activations and deltas, FP32 sums, the device tanh) moves element i by at most about
+    (rounding sites on the path) x e x this magnitude, to first order; seeding it with the residual
+    error |y_gpu - y_oracle| instead bounds what the forward pass's error does to the gradient."""
+    p = np.asarray(params, np.float64)
+    o = np.cumsum([0, H * 5, H, H * H, H, H * H, H, H, 1])
+    W1, b1, W2, b2, W3, b3, W4 = (p[o[i]:o[i + 1]] for i in range(7))
+    W1, W2, W3 = W1.reshape(H, 5), W2.reshape(H, H), W3.reshape(H, H)
+    h1 = np.tanh(x @ W1.T + b1)
+    h2 = np.tanh(h1 @ W2.T + b2)
+    h3 = np.tanh(h2 @ W3.T + b3)
+    s = np.abs(np.asarray(seed, np.float64))[:, None]
+    d3 = s * np.abs(W4)[None, :] * np.abs(1 - h3 * h3)
+    d2 = (d3 @ np.abs(W3)) * np.abs(1 - h2 * h2)
+    d1 = (d2 @ np.abs(W2)) * np.abs(1 - h1 * h1)
+    return np.concatenate([(d1.T @ np.abs(x)).ravel(), d1.sum(0), (d2.T @ np.abs(h1)).ravel(), d2.sum(0),
+                           (d3.T @ np.abs(h2)).ravel(), d3.sum(0), (s * np.abs(h3)).sum(0), [s.sum()]])
+
+
+def test_every_gradient_element_within_its_bf16_rounding_bound(torch):
+    """Element by element, every one of the 8,769 gradient entries of the tensor-core backward pass
+    lies within the first-order rounding bound of its own terms: |g - g_oracle| <= 3 x 2^-8 x M_i + F_i,
+    M_i the magnitude of the products summed into entry i (the oracle's residuals |y - t| seeding an
+    absolute-value backpropagation; six BF16 roundings on every path, each within the unit roundoff
+    2^-9, give 3 x 2^-8; FP32 sums and the device tanh add far less) and F_i the same propagation seeded with the GPU
+    forward pass's own error |y_gpu - y_oracle|.  A dropped term, a sign or an index mistake in any
+    one element moves it by about its own magnitude and fails."""
+    params = P.mlp_init(seed=11)
+    n = 200  # 12 full tiles of 16 and a ragged tail of 8
+    x, target, wt = _data(n, 3)
+    net = mc.Mlp(params)
+    dx, dt, dw = _dev(torch, x), _dev(torch, target), _dev(torch, wt)
+    dy = torch.zeros(n, device="cuda")
+    dg = torch.zeros(net.n_params, device="cuda")
+    dl = torch.zeros(1, device="cuda")
+    net.forward(dx.data_ptr(), dy.data_ptr(), n)
+    net.loss_grad(dx.data_ptr(), dt.data_ptr(), dw.data_ptr(), n, dg.data_ptr(), dl.data_ptr())
+    torch.cuda.synchronize()
+    _, y_o, g_o = oracle.mlp_loss_grad(params, x, target, wt, H=64)
+    y, g = dy.cpu().numpy().astype(np.float64), dg.cpu().numpy().astype(np.float64)
+    M = _magnitude_backprop(params, x, 2.0 * wt * (y_o - target) / n)
+    F = _magnitude_backprop(params, x, 2.0 * wt * (y - y_o) / n)
+    bound = 3.0 * 2.0**-8 * M + F + 1e-12
+    err = np.abs(g - g_o)
+    worst = int(np.argmax(err / bound))
+    assert np.all(err <= bound), (worst, g[worst], g_o[worst], bound[worst], int(np.sum(err > bound)))
+    # the bound is tight enough to matter: most entries exceed it, so replacing one of them by
+    # zero or by another entry's value fails
+    resolved = np.abs(g_o) > bound
+    assert np.mean(resolved) > 0.6, float(np.mean(resolved))
+    print(f"gradient: {g.size} entries within bound, worst ratio {float(np.max(err / bound)):.3f}, "
+          f"{float(np.mean(resolved)):.1%} of entries larger than their bound")
+    net.close()
+
+
 def test_gpu_training_fits_a_smooth_log_importance(torch):
     """Full-batch Adam on the GPU brings the loss of a smooth log-importance-like target down by
     two orders of magnitude, and the trained network's forward pass reproduces the targets."""

@@ -126,7 +126,6 @@ def test_fp64_replay_first_histories(torch, name):
 @pytest.mark.parametrize("name,n_or,n_gpu,min_bins", [
     ("config1", 400_000, 4_000_000, 45),
     ("config2", 400_000, 4_000_000, 200),
-    ("config3", 200_000, 2_000_000, 1000),
 ])
 def test_fp32_tallies_match_oracle(torch, name, n_or, n_gpu, min_bins):
     prob = P.by_name(name)
@@ -140,6 +139,41 @@ def test_fp32_tallies_match_oracle(torch, name, n_or, n_gpu, min_bins):
     lg, lgs = p.leakage()
     if np.any(o.leak_mean > 0):
         check_z(combined_z(lg, lgs, o.leak_mean, o.leak_std), 1)
+    assert conserved(p.counters())
+    p.close()
+
+
+def test_config3_mesh_parity_bin_by_bin(torch):
+    """The lattice workload's 34 x 34 x 7 x 50 space-group-time mesh (404,600 bins), GPU (FP32
+    tracking, 6.4e7 histories, 256 batches) against the oracle (6e6 histories, exact per-history
+    variance), bin by bin on every bin both sides resolve to 10%: at least a quarter of the whole
+    mesh, reaching every group (the thermal ones included), the outermost mesh cells and the late
+    time bins.  Bar: the |z| that a correct walk exceeds in some bin with probability 1e-3 (two
+    independent oracle runs of 3e6 histories stay at 4.4 against 5.8 on 149,320 bins), and at most
+    1% of the compared bins beyond 3 sigma."""
+    from scipy.stats import norm
+    prob = P.config3()
+    o = oracle.run(prob, 6_000_000, seed=3, threads=THREADS)
+    p = mc.Problem(prob)
+    p.run(64_000_000, 4, precision="fp32", n_batches=256)
+    mg, sg = (np.asarray(a, np.float64) for a in p.tally(0))
+    mo, so = (np.asarray(a, np.float64) for a in o.tallies[0])
+    shape = mg.shape  # (nz, ny, nx, G, nt)
+    ok = (sg > 0) & (so > 0) & (sg < 0.1 * np.abs(mg)) & (so < 0.1 * np.abs(mo))
+    z = (mg[ok] - mo[ok]) / np.sqrt(sg[ok] ** 2 + so[ok] ** 2)
+    frac = float(ok.mean())
+    bar = max(4.0, float(norm.isf(5e-4 / max(1, z.size))))
+    f3 = float(np.mean(np.abs(z) > 3))
+    print(f"config3 mesh: {z.size} of {ok.size} bins compared ({frac:.1%}), max |z| {np.abs(z).max():.2f} "
+          f"(bar {bar:.2f}), beyond 3 sigma {f3:.4f}, chi2 per bin {float(np.mean(z * z)):.3f}")
+    assert frac >= 0.25, frac
+    assert np.all(np.abs(z) < bar), np.abs(z).max()
+    assert f3 < 0.01, f3
+    assert 0.8 < float(np.mean(z * z)) < 1.25
+    per_group = ok.sum(axis=(0, 1, 2, 4))
+    assert np.all(per_group > 0), per_group
+    assert ok[:, :, 0].any() and ok[:, :, -1].any() and ok[:, 0].any() and ok[:, -1].any()
+    assert ok[..., shape[4] // 2:].any()
     assert conserved(p.counters())
     p.close()
 
