@@ -644,6 +644,17 @@ def bench_learned_ww(args, torch, mc):
     print(json.dumps(line), flush=True)
 
 
+def probes(torch, mc):
+    """The measured figures the design rests on (not a benchmark step): instruction throughput per SM
+    clock (mc_op_rates) and 64-bit L2 atomic rates over spans of slots from one address to a
+    footprint far beyond L2 (mc_atomic_peak)."""
+    spans = [1, 700, 22_400, 360_000, 1_000_000, 13_000_000, 100_000_000]
+    line = {"probes": "instruction and atomic rates", "op_rates_per_clk_per_sm": mc.op_rates(),
+            "l2_atomics_per_s": {str(sp): mc.atomic_peak(sp) for sp in spans},
+            "device": torch.cuda.get_device_name(0)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -676,6 +687,8 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    if args.workload == "probes":
+        return probes(torch, mc)
     prob, n, desc = workload(args.workload)
     if args.workload == "config4":
         if world > 1:
@@ -735,10 +748,20 @@ def main():
     mc.wait(p.h)
     step_ms = [ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps)]
     t_dev = sum(step_ms) / 1000.0
+    combined = None
     if dist is not None:
         t = torch.tensor([t_dev], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_dev = float(t.item())
+        # the one exchange step of sharded histories (after the timed region): every rank's exact
+        # int64 tally sums of its last run, added by one all-reduce into the sums of the union of
+        # the ranks' history ranges
+        sums, bits = mc.tally_sums(p.h, 0)
+        ts = torch.from_numpy(sums.ravel()).to("cuda")
+        dist.all_reduce(ts)
+        tot = ts.cpu().numpy()
+        combined = {"bins": int(tot.size), "fixed_bits": bits, "ranks": world,
+                    "histories": world * n, "total_flux": float(tot.sum()) / 2.0 ** bits / (world * n)}
     value = world * n * args.steps / t_dev
     ms_per_step = 1000.0 * t_dev / args.steps
 
@@ -808,6 +831,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_run(prob) * args.steps,
+        "combined_tally": combined,
         "clocks": clk,
         "wall_s": wall,
         "step_ms": [round(x, 4) for x in step_ms],

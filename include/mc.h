@@ -352,6 +352,15 @@ int mc_tally_get(mc_problem* p, int tally_id, double* mean, double* std_err, siz
  * from the spread of the batch values.  Synchronises. */
 int mc_tally_batches(mc_problem* p, int tally_id, double* out, size_t n, int* n_batches);
 
+/* Exact int64 fixed-point sums (units of 2^-fixed_bits) over all histories of the last run, one
+ * per bin of a tally (the track-length scores of Section 3 summed over batches and stripes, before
+ * any floating-point division), into sums[n >= bins]; *fixed_bits (may be NULL) receives the scale.
+ * Integer sums do not depend on the order of their terms: runs over disjoint history ranges
+ * (mc_run_opts::first_history) add up to the run over their union bit for bit, which is how
+ * histories shard across processes or GPUs and how a run cut short resumes.  MC_ERR_STATE after a
+ * run with FP64 tallies.  Synchronises. */
+int mc_tally_sums(mc_problem* p, int tally_id, int64_t* sums, size_t n, int* fixed_bits);
+
 /* Copies the MC_NCOUNTERS run counters into counters[n]. Synchronises. */
 int mc_counters_get(mc_problem* p, int64_t* counters, size_t n);
 
@@ -386,6 +395,13 @@ int mc_tally_layout(const mc_problem* p, int* stripes, int* n_batches, uint64_t*
  * use FP64 tallies (weights can span many decades). */
 int mc_ww_set_table(mc_problem* p, int nx, int ny, int nz, const double* edges, const double* centre);
 
+/* The same with time bins (the time-dependent problems of Section 3: a pulse source and a time
+ * census, where the importance of a particle depends on when it is somewhere): edges = x[nx+1],
+ * y[ny+1], z[nz+1], t[nt+1] (increasing), centre[nt][nz][ny][nx][G].  A particle takes the window of
+ * the time bin t[i] <= t < t[i+1] holding its time (outside every bin: no window).
+ * mc_ww_set_table is this call with one time bin [0, +inf). */
+int mc_ww_set_table_t(mc_problem* p, int nx, int ny, int nz, int nt, const double* edges, const double* centre);
+
 /* ------------------------------------------------------------------------- importance network */
 /* A 5 -> 64 -> 64 -> 64 -> 1 perceptron (tanh hidden units, linear output) mapping a phase-space
  * point (x, y, z, group, t, each scaled to [-1, 1]) to the log of a weight-window centre.  FP32
@@ -413,11 +429,13 @@ int mc_mlp_loss_grad(mc_mlp* m, const float* x, const float* target, const float
 int mc_mlp_train(mc_mlp* m, const float* x, const float* target, const float* wt, int n, int epochs, float lr,
                  float* last_loss, void* stream);
 /* One learning round of the weight windows from the problem's last run (synchronous):
- *   1. from mesh tally `tally_id` (its time bins summed) take the flux phi of every (cell, group)
- *      resolved to a relative error below 0.5; target = log(phi / phi_ref), phi_ref = the flux of the
- *      source point's cell in the source's main group, weight = 1 / relative variance (capped);
+ *   1. from mesh tally `tally_id` take the flux phi of every (cell, group, time bin) resolved to a
+ *      relative error below 0.5 (with one time bin, or none resolved in time: the flux summed over
+ *      time); target = log(phi / phi_ref), phi_ref = that of the source point's cell in the source's
+ *      main group (and the time bin of the source's start time), weight = 1 / relative variance
+ *      (capped); the network input is (x, y, z, group, time bin index), each scaled to [-1, 1];
  *   2. if extrap_slope > 0, continue the windows past the resolved region along x: for every x line
- *      of the mesh (fixed y, z cell) and each group with r >= 3 resolved cells, fit a
+ *      of the mesh (fixed y, z cell and time bin) and each group with r >= 3 resolved cells, fit a
  *      least-squares line to the targets of its outermost max(3, r/4) resolved cells; take the
  *      flattest of these slopes that fall away from the resolved region as the line's common
  *      slope (deep in a medium all groups decay at the common asymptotic rate); from each group's
@@ -428,9 +446,10 @@ int mc_mlp_train(mc_mlp* m, const float* x, const float* target, const float* wt
  *      bounds how far a wrong slope can take them from the flux.  (A table whose splitting
  *      overflows the bank shows as MC_ERR_BANK_FULL on the next run: learn again with less.)
  *   3. train the network on these targets on the GPU (`epochs` Adam steps at `lr`);
- *   4. evaluate it on every (cell, group) of that tally's spatial mesh and set the window centres
- *      w_c = phi_ref-normalised exp(net) as the problem's weight-window table (the forward-flux
- *      weight windows of the MAGIC method, learned instead of tabulated).
+ *   4. evaluate it on every (cell, group, time bin) of that tally's mesh and set the window centres
+ *      w_c = phi_ref-normalised exp(net) as the problem's weight-window table, with the tally's
+ *      time bins when step 1 resolved them in time (the forward-flux weight windows of the MAGIC
+ *      method, learned instead of tabulated).
  * info (host, may be NULL) receives {resolved training points, final loss, target scale, phi_ref,
  * extrapolated training points}. */
 int mc_ww_learn(mc_problem* p, mc_mlp* m, int tally_id, int epochs, float lr, double extrap_slope,
@@ -533,6 +552,13 @@ int mc_batch_tune(mc_problem* const* ps, int n, const uint64_t* n_hist, uint64_t
  * 256 threads per SM; *atomics_per_s receives adds per second.  Allocates and frees its array.
  * Used as the atomic roofline of track-length scoring. */
 int mc_atomic_peak(uint64_t span, double* atomics_per_s);
+
+/* Instruction throughput on the current GPU, in operations per SM clock per SM (a measurement tool
+ * like mc_atomic_peak; it explains why the FP32 walk keeps FP64 work off its path): out[0] FP32 FMA,
+ * [1] FP64 add, [2] 32-bit umulhi (with an add), [3] int -> float conversion, [4] float -> int64
+ * conversion, [5] __logf (with an add); four independent chains per thread, 8 CTAs of 256 threads
+ * per SM.  n >= 6.  Synchronous. */
+int mc_op_rates(double* ops_per_clk_per_sm, int n);
 
 /* Philox4x32-10 (Salmon et al., SC'11) on the device: out[i] = Philox(key = seed, ctr = ctr[i])
  * for n counters; ctr and out are DEVICE arrays of 4*n uint32 (counter words c0..c3).  This is

@@ -71,6 +71,7 @@ class OrProblem(C.Structure):
         ("ww_edges", C.POINTER(C.c_double)), ("ww_center", C.POINTER(C.c_double)),
         ("ww_upper", C.c_double), ("ww_lower", C.c_double), ("ww_split_max", C.c_int),
         ("tally_est", C.POINTER(C.c_int)),
+        ("ww_nt", C.c_int), ("ww_tedges", C.POINTER(C.c_double)),
     ]
 
 
@@ -270,6 +271,9 @@ class Marshalled:
             s.ww_nx, s.ww_ny, s.ww_nz = (len(ww[k]) - 1 for k in ("x", "y", "z"))
             s.ww_edges = dp(list(ww["x"]) + list(ww["y"]) + list(ww["z"]))
             s.ww_center = dp(ww["center"])
+            if "t" in ww:
+                s.ww_nt = len(ww["t"]) - 1
+                s.ww_tedges = dp(list(ww["t"]))
             s.ww_upper = ww.get("upper", 2.0)
             s.ww_lower = ww.get("lower", 0.5)
             s.ww_split_max = ww.get("split_max", 10)

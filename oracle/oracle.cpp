@@ -196,8 +196,8 @@ struct Prob {
   int total_bins;  // mesh bins; leakage bins follow
   double t_census;
   bool ww;
-  std::vector<double> ww_e[3];
-  int ww_n[3];
+  std::vector<double> ww_e[4];  // x, y, z and time edges
+  int ww_n[4];
   std::vector<double> ww_c;
   double ww_up, ww_lo;
   int ww_max;
@@ -308,7 +308,14 @@ Prob copy_problem(const or_problem* p) {
       P.ww_e[d].assign(we, we + P.ww_n[d] + 1);
       we += P.ww_n[d] + 1;
     }
-    P.ww_c.assign(p->ww_center, p->ww_center + P.ww_n[0] * P.ww_n[1] * P.ww_n[2] * G);
+    if (p->ww_nt > 1 && p->ww_tedges) {
+      P.ww_n[3] = p->ww_nt;
+      P.ww_e[3].assign(p->ww_tedges, p->ww_tedges + p->ww_nt + 1);
+    } else {
+      P.ww_n[3] = 1;
+      P.ww_e[3] = {0.0, std::numeric_limits<double>::infinity()};
+    }
+    P.ww_c.assign(p->ww_center, p->ww_center + (size_t)P.ww_n[0] * P.ww_n[1] * P.ww_n[2] * P.ww_n[3] * G);
     P.ww_up = p->ww_upper;
     P.ww_lo = p->ww_lower;
     P.ww_max = p->ww_split_max;
@@ -709,8 +716,10 @@ bool weight_window(const Prob& P, uint64_t seed, Particle& q, uint32_t k_used,
   const double ah = 1e-9;
   int ix = bin_of(P.ww_e[0], q.x + ah * q.ux), iy = bin_of(P.ww_e[1], q.y + ah * q.uy),
       iz = bin_of(P.ww_e[2], q.z + ah * q.uz);
-  if (ix < 0 || iy < 0 || iz < 0) return true;
-  double wc = P.ww_c[((iz * P.ww_n[1] + iy) * P.ww_n[0] + ix) * P.G + q.g];
+  // and of the time bin holding the particle's time
+  int it = bin_of(P.ww_e[3], q.t);
+  if (ix < 0 || iy < 0 || iz < 0 || it < 0) return true;
+  double wc = P.ww_c[(((it * P.ww_n[2] + iz) * P.ww_n[1] + iy) * P.ww_n[0] + ix) * P.G + q.g];
   if (!(wc > 0.0)) return true;
   if (q.w > P.ww_up * wc) {
     int n = (int)std::ceil(q.w / wc);

@@ -99,6 +99,11 @@ typedef struct {
   /* per tally: OR_EST_TRACK (nt time bins between the nt+1 edges) or OR_EST_CROSSING (values at
    * the nt+1 time points themselves); NULL means every tally is a track-length tally */
   const int* tally_est;
+  /* time bins of the weight windows: ww_center is [ww_nt][ww_nz][ww_ny][ww_nx][G] and a particle
+   * takes the window of the time bin t[i] <= t < t[i+1] holding its time; ww_nt <= 1 or NULL edges:
+   * one bin holding every time */
+  int ww_nt;
+  const double* ww_tedges; /* t[ww_nt+1] */
 } or_problem;
 
 typedef struct {

@@ -45,6 +45,8 @@ cudaError_t launch_reconstruct(void* tally, const char* blob64, uint64_t rows, u
                                int fp64, cudaStream_t s);
 cudaError_t launch_batch_stats(const void* tally, int fp64, uint64_t bins, uint64_t row, int nb, int stripes,
                                uint64_t n_hist, void* out, cudaStream_t s);
+cudaError_t launch_op_probe(int op, int grid, int iters, unsigned long long* sink, unsigned long long* clk,
+                            cudaStream_t s);
 cudaError_t launch_philox(uint64_t seed, const uint4* ctr, uint4* out, uint64_t n, cudaStream_t s);
 cudaError_t launch_atomic_probe(unsigned long long* a, unsigned long long span, int grid, int iters, unsigned salt,
                                 cudaStream_t s);
@@ -489,6 +491,12 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
 // ------------------------------------------------------------------------------------------ ABI
 namespace mcgb {
 
+// Shared memory of one warp of the transport kernel besides the tables: its flight queue (64
+// particles) and its tally staging buffer (128 x 12 B).
+size_t transport_warp_smem(int fp64) {
+  return (size_t)kWarpQ * 16 * (fp64 ? kLanesFP64 : kLanesFP32) + (size_t)kStage * 12;
+}
+
 // NVTX range over a library call or a phase of it (visible to nsys / ncu when a tool is attached;
 // header-only, no cost otherwise)
 struct NvtxRange {
@@ -547,8 +555,9 @@ void fill_run_params(const mc_problem* p, const mc_run_opts& o, uint64_t n_histo
     P.ww_nx = p->ww_n[0];
     P.ww_ny = p->ww_n[1];
     P.ww_nz = p->ww_n[2];
+    P.ww_nt = p->ww_n[3];
     P.ww_edges = base;
-    P.ww_center = base + (p->ww_n[0] + 1) + (p->ww_n[1] + 1) + (p->ww_n[2] + 1);
+    P.ww_center = base + (p->ww_n[0] + 1) + (p->ww_n[1] + 1) + (p->ww_n[2] + 1) + (p->ww_n[3] + 1);
     P.ww_upper = 2.0;
     P.ww_lower = 0.5;
     P.ww_split_max = 10;
@@ -864,7 +873,7 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   if (P.log) CK(cudaMemsetAsync(p->d_log.ptr, 0, log_cap * sizeof(mc_event), s));
   const int block = o.block_size ? o.block_size : 256;
   // tables + per-warp flight queues (64 slots) + per-warp tally staging (128 x 12 B)
-  const size_t smem = P.blob_bytes + (size_t)(block / 32) * (64 * 16 * lanes + 128 * 12);
+  const size_t smem = P.blob_bytes + (size_t)(block / 32) * transport_warp_smem(fp64);
   rc = check_shared_memory(p->dev, smem, "the transport kernel");
   if (rc != MC_OK) return rc;
   int per_sm = 0;
@@ -982,7 +991,7 @@ int mc_run_eigen(mc_problem* p, uint64_t n_per_cycle, int n_inactive, int n_acti
     CK(cudaMemsetAsync(p->d_log.ptr, 0, log_cap * sizeof(mc_event), s));
   }
   const int block = o.block_size ? o.block_size : 256;
-  const size_t smem = p->blob[fp64].size() + (size_t)(block / 32) * (64 * 16 * lanes + 128 * 12);
+  const size_t smem = p->blob[fp64].size() + (size_t)(block / 32) * transport_warp_smem(fp64);
   rc = check_shared_memory(p->dev, smem, "the transport kernel");
   if (rc != MC_OK) return rc;
   const bool range = p->range;
@@ -1260,6 +1269,23 @@ int mc_tally_shape(const mc_problem* p, int tally_id, int64_t shape[5]) {
   return MC_OK;
 }
 
+int mc_tally_sums(mc_problem* p, int tally_id, int64_t* sums, size_t n, int* fixed_bits) {
+  int64_t shp[5];
+  int rc = mc_tally_shape(p, tally_id, shp);
+  if (rc != MC_OK) return rc;
+  rc = mc_wait(p);
+  if (rc != MC_OK) return rc;
+  if (p->tally_fp64) return fail(MC_ERR_STATE, "the last run kept FP64 tallies, which have no exact sums");
+  const size_t nbins = (size_t)(shp[0] * shp[1] * shp[2] * shp[3] * shp[4]);
+  if (!sums || n < nbins) return fail(MC_ERR_INVALID, "output holds %zu of %zu bins", sums ? n : 0, nbins);
+  const TableHeader* H = reinterpret_cast<const TableHeader*>(p->blob[0].data());
+  const size_t first = tally_id == p->n_tally ? (size_t)H->leak_offset : (size_t)H->tally[tally_id].bin_offset;
+  // the batch statistics start with the exact integer sum over batches (and stripes) of every bin
+  CK(cudaMemcpy(sums, (const char*)p->d_stats.ptr + 8 * first, nbins * 8, cudaMemcpyDeviceToHost));
+  if (fixed_bits) *fixed_bits = (int)std::lround(std::log2(p->fixed_scale));
+  return MC_OK;
+}
+
 int mc_tally_get(mc_problem* p, int tally_id, double* mean, double* std_err, size_t n) {
   NvtxRange nvtx_range("mc_tally_get");
   int64_t shp[5];
@@ -1384,33 +1410,44 @@ int mc_event_log(mc_problem* p, mc_event* out, size_t cap, size_t* n_out) {
   return MC_OK;
 }
 
-int mc_ww_set_table(mc_problem* p, int nx, int ny, int nz, const double* edges, const double* centre) {
+int mc_ww_set_table_t(mc_problem* p, int nx, int ny, int nz, int nt, const double* edges, const double* centre) {
   g_err.clear();
   if (!p || !edges || !centre) return fail(MC_ERR_INVALID, "NULL argument");
-  if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny * nz > (1 << 24))
+  if (nx < 1 || ny < 1 || nz < 1 || nt < 1 || (int64_t)nx * ny * nz * nt > (1 << 24))
     return fail(MC_ERR_INVALID, "weight-window mesh size");
-  const int n[3] = {nx, ny, nz};
+  const int n[4] = {nx, ny, nz, nt};
   const double* e = edges;
-  for (int d = 0; d < 3; ++d) {
-    for (int i = 1; i <= n[d]; ++i)
-      if (!(e[i] > e[i - 1])) return fail(MC_ERR_INVALID, "weight-window edges must increase");
+  for (int d = 0; d < 4; ++d) {
+    for (int i = 0; i <= n[d]; ++i)
+      if (std::isnan(e[i]) || (i > 0 && !(e[i] > e[i - 1])))
+        return fail(MC_ERR_INVALID, "weight-window edges must increase");
     e += n[d] + 1;
   }
-  const size_t cells = (size_t)nx * ny * nz * p->G;
+  const size_t cells = (size_t)nx * ny * nz * nt * p->G;
   for (size_t i = 0; i < cells; ++i)
     if (!(centre[i] >= 0.0) || !std::isfinite(centre[i]))
       return fail(MC_ERR_INVALID, "weight-window centres must be finite and >= 0 (0 disables a cell)");
-  const size_t n_edges = (size_t)(nx + 1) + (ny + 1) + (nz + 1);
+  const size_t n_edges = (size_t)(nx + 1) + (ny + 1) + (nz + 1) + (nt + 1);
   if (p->has_run) CK(cudaStreamSynchronize(p->stream));
   int rc = p->d_ww.ensure((n_edges + cells) * sizeof(double), p->dev);
   if (rc != MC_OK) return rc;
   CK(cudaMemcpy(p->d_ww.ptr, edges, n_edges * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy((double*)p->d_ww.ptr + n_edges, centre, cells * sizeof(double), cudaMemcpyHostToDevice));
-  p->ww_n[0] = nx;
-  p->ww_n[1] = ny;
-  p->ww_n[2] = nz;
+  for (int d = 0; d < 4; ++d) p->ww_n[d] = n[d];
   p->ww_set = 1;
   return MC_OK;
+}
+
+int mc_ww_set_table(mc_problem* p, int nx, int ny, int nz, const double* edges, const double* centre) {
+  g_err.clear();
+  if (!p || !edges || !centre) return fail(MC_ERR_INVALID, "NULL argument");
+  if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny * nz > (1 << 24))
+    return fail(MC_ERR_INVALID, "weight-window mesh size");
+  // one time bin holding every time: [0, +inf)
+  std::vector<double> e(edges, edges + (nx + 1) + (ny + 1) + (nz + 1));
+  e.push_back(0.0);
+  e.push_back(std::numeric_limits<double>::infinity());
+  return mc_ww_set_table_t(p, nx, ny, nz, 1, e.data(), centre);
 }
 
 size_t mc_problem_table_bytes(const mc_problem* p) {
@@ -1495,6 +1532,46 @@ int mc_atomic_peak(uint64_t span, double* atomics_per_s) {
   buf.release();
   if (e != cudaSuccess) return cuda_fail(e, "atomic probe");
   *atomics_per_s = 3.0 * grid * 256.0 * iters / (ms * 1e-3);
+  return MC_OK;
+}
+
+int mc_op_rates(double* ops_per_clk_per_sm, int n) {
+  g_err.clear();
+  if (!ops_per_clk_per_sm || n < 6) return fail(MC_ERR_INVALID, "need room for 6 rates");
+  int dev, sms = 0;
+  int rc = current_device(&dev);
+  if (rc != MC_OK) return rc;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  DevBuf buf;
+  rc = buf.ensure(64, dev);
+  if (rc != MC_OK) return rc;
+  unsigned long long* sink = (unsigned long long*)buf.ptr;
+  unsigned long long* clk = sink + 2;
+  const int grid = sms * 8;  // 8 CTAs of 256 threads per SM
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (int op = 0; op < 6 && e == cudaSuccess; ++op) {
+    // FP64 and the int64 conversion are slow: fewer iterations
+    const int iters = (op == 1 || op == 4) ? 512 : 8192;
+    e = launch_op_probe(op, grid, iters, sink, clk, 0);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, 0);
+    if (e == cudaSuccess) e = launch_op_probe(op, grid, iters, sink, clk, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    unsigned long long c[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(c, clk, sizeof(c), cudaMemcpyDeviceToHost);
+    // operations / (launch time x SM clock x SMs); the clock is block 0's ticks per nanosecond
+    const double ops = (double)grid * 256.0 * 4.0 * iters;
+    const double ghz = c[1] > 0 ? (double)c[0] / (double)c[1] : 0.0;
+    if (e == cudaSuccess) ops_per_clk_per_sm[op] = (ms > 0.f && ghz > 0.0) ? ops / (ms * 1e6 * ghz * sms) : 0.0;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  buf.release();
+  if (e != cudaSuccess) return cuda_fail(e, "instruction probe");
   return MC_OK;
 }
 
@@ -1653,7 +1730,7 @@ extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t
   CK(cudaMemsetAsync(base, 0, off_banks, s));
   CK(cudaMemsetAsync(base + off_tally, 0, tally_bytes, s));
   const int block = o.block_size ? o.block_size : 256;
-  const size_t smem = P.blob_bytes + (size_t)(block / 32) * (64 * 16 * lanes + 128 * 12);
+  const size_t smem = P.blob_bytes + (size_t)(block / 32) * transport_warp_smem(fp64);
   rc = check_shared_memory(p->dev, smem, "the transport kernel");
   if (rc != MC_OK) return rc;
   int per_sm = 0;
@@ -1844,25 +1921,35 @@ extern "C" int mc_ww_learn(mc_problem* p, mc_mlp* m, int tally_id, int epochs, f
   rc = mc_tally_get(p, tally_id, mean.data(), err.data(), nbin);
   if (rc != MC_OK) return rc;
   const HostTally& T = p->tallies[tally_id];
+  // Windows resolved in time when the tally has several time bins: the targets are then the flux
+  // of each (cell, group, time bin), so that the windows follow the particle population in time as
+  // they follow it in space (about the same number of tracks in every bin); otherwise the flux
+  // summed over time.
+  const bool timed = nt > 1;
+  const int ntw = timed ? nt : 1;
   const size_t ncell = (size_t)nz * ny * nx * G;
-  std::vector<double> phi(ncell, 0.0), var(ncell, 0.0);
+  std::vector<double> phi(ncell * ntw, 0.0), var(ncell * ntw, 0.0);
   for (size_t c = 0; c < ncell; ++c)
     for (int it = 0; it < nt; ++it) {
-      phi[c] += mean[c * nt + it];
-      var[c] += err[c * nt + it] * err[c * nt + it];
+      const size_t k = c * ntw + (timed ? it : 0);
+      phi[k] += mean[c * nt + it];
+      var[k] += err[c * nt + it] * err[c * nt + it];
     }
   const int rx = bin_of_point(T.e[0], p->src_center[0]), ry = bin_of_point(T.e[1], p->src_center[1]),
             rz = bin_of_point(T.e[2], p->src_center[2]);
-  const double phi_ref = phi[(((size_t)rz * ny + ry) * nx + rx) * G + p->src_group];
+  const int rt = timed ? bin_of_point(T.e[3], reinterpret_cast<const TableHeader*>(p->blob[1].data())->src_t0) : 0;
+  const double phi_ref = phi[((((size_t)rz * ny + ry) * nx + rx) * G + p->src_group) * ntw + rt];
   if (!(phi_ref > 0.0)) return fail(MC_ERR_STATE, "the source cell of tally %d has no flux yet", tally_id);
   std::vector<float> xs, tg, wt, xall;
   double scale = 1.0;
-  auto point = [&](int ix, int iy, int iz, int g, float* pt) {
+  // network input: the cell centre scaled to [-1, 1] along x, y, z, the group, and the time bin
+  // (its index scaled to [-1, 1], which keeps log-spaced bins evenly apart; 0 without time bins)
+  auto point = [&](int ix, int iy, int iz, int g, int iw, float* pt) {
     pt[0] = (float)scaled_centre(T.e[0], ix);
     pt[1] = (float)scaled_centre(T.e[1], iy);
     pt[2] = (float)scaled_centre(T.e[2], iz);
     pt[3] = G > 1 ? (float)(2.0 * g / (G - 1) - 1.0) : 0.f;
-    pt[4] = 0.f;
+    pt[4] = ntw > 1 ? (float)(2.0 * iw / (ntw - 1) - 1.0) : 0.f;
   };
   auto add = [&](const float* pt, double target, double w) {
     xs.insert(xs.end(), pt, pt + 5);
@@ -1871,93 +1958,96 @@ extern "C" int mc_ww_learn(mc_problem* p, mc_mlp* m, int tally_id, int epochs, f
     scale = std::max(scale, std::fabs(target));
   };
   int n_extra = 0;
-  for (int iz = 0; iz < nz; ++iz)
-    for (int iy = 0; iy < ny; ++iy) {
-      // resolved cells of every group's x line; then one common slope per side: the flattest of
-      // the groups' fitted slopes (deep in a medium every group decays at the common asymptotic
-      // rate, which no group's near-source rate undercuts)
-      std::vector<std::vector<int>> rix(G);
-      std::vector<std::vector<double>> rt(G);
-      for (int g = 0; g < G; ++g)
-        for (int ix = 0; ix < nx; ++ix) {
-          float pt[5];
-          point(ix, iy, iz, g, pt);
-          xall.insert(xall.end(), pt, pt + 5);
-          const size_t c = (((size_t)iz * ny + iy) * nx + ix) * G + g;
-          if (!(phi[c] > 0.0)) continue;
-          const double rel = std::sqrt(var[c]) / phi[c];
-          if (!(rel < 0.5)) continue;
-          const double target = std::log(phi[c] / phi_ref);
-          add(pt, target, std::min(1.0 / std::max(rel * rel, 1e-12), 1e4));
-          rix[g].push_back(ix);
-          rt[g].push_back(target);
-        }
-      if (!(extrap_slope > 0.0)) continue;
-      for (int side = 0; side < 2; ++side) {
-        // least-squares line through the k outermost resolved cells of each group on this side
-        std::vector<double> fa(G, 0.0), fb(G, 0.0);
-        std::vector<char> fit(G, 0);
-        double common = 0.0;
-        bool any = false;
-        for (int g = 0; g < G; ++g) {
-          const int nr = (int)rix[g].size();
-          if (nr < 3) continue;
-          const int k = std::max(3, nr / 4);
-          double sx = 0, sy = 0, sxx = 0, sxy = 0;
-          bool finite = true;
-          for (int j = 0; j < k; ++j) {
-            const int q = side ? nr - 1 - j : j;
-            const double xc = 0.5 * (T.e[0][rix[g][q]] + T.e[0][rix[g][q] + 1]);
-            finite = finite && std::isfinite(xc);
-            sx += xc;
-            sy += rt[g][q];
-            sxx += xc * xc;
-            sxy += xc * rt[g][q];
-          }
-          const double den = k * sxx - sx * sx;
-          if (!finite || !(den > 0.0) || !std::isfinite(den)) continue;
-          const double a = (k * sxy - sx * sy) / den;
-          if (side ? !(a < 0.0) : !(a > 0.0)) continue;  // not falling away from the resolved cells
-          fa[g] = a;
-          fb[g] = (sy - a * sx) / k;
-          fit[g] = 1;
-          common = any ? (side ? std::max(common, a) : std::min(common, a)) : a;
-          any = true;
-        }
-        if (!any) continue;
-        // each group continues from its own outermost resolved cell with extrap_slope times the
-        // common slope until the windows have fallen by extrap_efolds, then stays constant
-        const double slope = extrap_slope * common;
-        for (int g = 0; g < G; ++g) {
-          if (!fit[g]) continue;
-          const int nr = (int)rix[g].size();
-          const int edge = side ? rix[g][nr - 1] : rix[g][0];
-          const double xe = 0.5 * (T.e[0][edge] + T.e[0][edge + 1]);
-          const double ye = fa[g] * xe + fb[g];
-          const int from = side ? edge + 1 : 0, to = side ? nx : edge;
-          for (int ix = from; ix < to; ++ix) {
-            const double xc = 0.5 * (T.e[0][ix] + T.e[0][ix + 1]);
-            if (!std::isfinite(xc)) continue;
-            const double drop = std::min(std::fabs(slope * (xc - xe)), extrap_efolds);
+  for (int iw = 0; iw < ntw; ++iw)
+    for (int iz = 0; iz < nz; ++iz)
+      for (int iy = 0; iy < ny; ++iy) {
+        // resolved cells of every group's x line; then one common slope per side: the flattest of
+        // the groups' fitted slopes (deep in a medium every group decays at the common asymptotic
+        // rate, which no group's near-source rate undercuts)
+        std::vector<std::vector<int>> rix(G);
+        std::vector<std::vector<double>> rtg(G);
+        for (int g = 0; g < G; ++g)
+          for (int ix = 0; ix < nx; ++ix) {
             float pt[5];
-            point(ix, iy, iz, g, pt);
-            add(pt, std::max(ye - drop, -700.0), 4.0);  // the weight of a 50% relative error
-            ++n_extra;
+            point(ix, iy, iz, g, iw, pt);
+            xall.insert(xall.end(), pt, pt + 5);
+            const size_t c = ((((size_t)iz * ny + iy) * nx + ix) * G + g) * ntw + iw;
+            if (!(phi[c] > 0.0)) continue;
+            const double rel = std::sqrt(var[c]) / phi[c];
+            if (!(rel < 0.5)) continue;
+            const double target = std::log(phi[c] / phi_ref);
+            add(pt, target, std::min(1.0 / std::max(rel * rel, 1e-12), 1e4));
+            rix[g].push_back(ix);
+            rtg[g].push_back(target);
+          }
+        if (!(extrap_slope > 0.0)) continue;
+        for (int side = 0; side < 2; ++side) {
+          // least-squares line through the k outermost resolved cells of each group on this side
+          std::vector<double> fa(G, 0.0), fb(G, 0.0);
+          std::vector<char> fit(G, 0);
+          double common = 0.0;
+          bool any = false;
+          for (int g = 0; g < G; ++g) {
+            const int nr = (int)rix[g].size();
+            if (nr < 3) continue;
+            const int k = std::max(3, nr / 4);
+            double sx = 0, sy = 0, sxx = 0, sxy = 0;
+            bool finite = true;
+            for (int j = 0; j < k; ++j) {
+              const int q = side ? nr - 1 - j : j;
+              const double xc = 0.5 * (T.e[0][rix[g][q]] + T.e[0][rix[g][q] + 1]);
+              finite = finite && std::isfinite(xc);
+              sx += xc;
+              sy += rtg[g][q];
+              sxx += xc * xc;
+              sxy += xc * rtg[g][q];
+            }
+            const double den = k * sxx - sx * sx;
+            if (!finite || !(den > 0.0) || !std::isfinite(den)) continue;
+            const double a = (k * sxy - sx * sy) / den;
+            if (side ? !(a < 0.0) : !(a > 0.0)) continue;  // not falling away from the resolved cells
+            fa[g] = a;
+            fb[g] = (sy - a * sx) / k;
+            fit[g] = 1;
+            common = any ? (side ? std::max(common, a) : std::min(common, a)) : a;
+            any = true;
+          }
+          if (!any) continue;
+          // each group continues from its own outermost resolved cell with extrap_slope times the
+          // common slope until the windows have fallen by extrap_efolds, then stays constant
+          const double slope = extrap_slope * common;
+          for (int g = 0; g < G; ++g) {
+            if (!fit[g]) continue;
+            const int nr = (int)rix[g].size();
+            const int edge = side ? rix[g][nr - 1] : rix[g][0];
+            const double xe = 0.5 * (T.e[0][edge] + T.e[0][edge + 1]);
+            const double ye = fa[g] * xe + fb[g];
+            const int from = side ? edge + 1 : 0, to = side ? nx : edge;
+            for (int ix = from; ix < to; ++ix) {
+              const double xc = 0.5 * (T.e[0][ix] + T.e[0][ix + 1]);
+              if (!std::isfinite(xc)) continue;
+              const double drop = std::min(std::fabs(slope * (xc - xe)), extrap_efolds);
+              float pt[5];
+              point(ix, iy, iz, g, iw, pt);
+              add(pt, std::max(ye - drop, -700.0), 4.0);  // the weight of a 50% relative error
+              ++n_extra;
+            }
           }
         }
       }
-    }
-  // xall is in [z][y][g][x] order here; the window table wants [z][y][x][g]
+  // xall is in [t][z][y][g][x] order here; the window table wants [t][z][y][x][g]
   {
     std::vector<float> re(xall.size());
-    for (int iz = 0; iz < nz; ++iz)
-      for (int iy = 0; iy < ny; ++iy)
-        for (int g = 0; g < G; ++g)
-          for (int ix = 0; ix < nx; ++ix) {
-            const size_t from = ((((size_t)iz * ny + iy) * G + g) * nx + ix) * 5;
-            const size_t to = ((((size_t)iz * ny + iy) * nx + ix) * G + g) * 5;
-            std::copy(xall.begin() + from, xall.begin() + from + 5, re.begin() + to);
-          }
+    for (int iw = 0; iw < ntw; ++iw)
+      for (int iz = 0; iz < nz; ++iz)
+        for (int iy = 0; iy < ny; ++iy)
+          for (int g = 0; g < G; ++g)
+            for (int ix = 0; ix < nx; ++ix) {
+              const size_t line = ((size_t)iw * nz + iz) * ny + iy;
+              const size_t from = ((line * G + g) * nx + ix) * 5;
+              const size_t to = ((line * nx + ix) * G + g) * 5;
+              std::copy(xall.begin() + from, xall.begin() + from + 5, re.begin() + to);
+            }
     xall.swap(re);
   }
   const int n = (int)tg.size();
@@ -1988,13 +2078,19 @@ extern "C" int mc_ww_learn(mc_problem* p, mc_mlp* m, int tally_id, int epochs, f
                m->steps, dl, 0));
   m->steps += epochs;
   CK(mlp_forward(m->wg.ptr, dall, dy, nall, 0));
-  // the window table lives on the tally's spatial mesh
-  const size_t n_edges = (size_t)(nx + 1) + (ny + 1) + (nz + 1);
+  // the window table lives on the tally's spatial mesh and, when resolved in time, its time bins
+  std::vector<double> edges;
+  for (int d = 0; d < 3; ++d) edges.insert(edges.end(), T.e[d].begin(), T.e[d].end());
+  if (timed) {
+    edges.insert(edges.end(), T.e[3].begin(), T.e[3].end());
+  } else {
+    edges.push_back(0.0);
+    edges.push_back(std::numeric_limits<double>::infinity());
+  }
+  const size_t n_edges = edges.size();
   if (p->has_run) CK(cudaStreamSynchronize(p->stream));
   rc = p->d_ww.ensure((n_edges + (size_t)nall) * sizeof(double), p->dev);
   if (rc != MC_OK) return rc;
-  std::vector<double> edges;
-  for (int d = 0; d < 3; ++d) edges.insert(edges.end(), T.e[d].begin(), T.e[d].end());
   CK(cudaMemcpy(p->d_ww.ptr, edges.data(), n_edges * sizeof(double), cudaMemcpyHostToDevice));
   // window centres relative to the source particle's weight 1 at phi_ref
   CK(mlp_centres(dy, nall, scale, -700.0, 50.0, 1.0, (double*)p->d_ww.ptr + n_edges, 0));
@@ -2003,6 +2099,7 @@ extern "C" int mc_ww_learn(mc_problem* p, mc_mlp* m, int tally_id, int epochs, f
   p->ww_n[0] = nx;
   p->ww_n[1] = ny;
   p->ww_n[2] = nz;
+  p->ww_n[3] = ntw;
   p->ww_set = 1;
   if (info) {
     info[0] = n - n_extra;

@@ -736,7 +736,6 @@ __device__ __forceinline__ const double* time_edges<double>(const char* base, co
 
 // Per-warp staging buffer of tally scores in shared memory: slot index and the score's bits
 // (int64 fixed point or double).
-constexpr unsigned kStage = 128;
 struct Stage {
   uint32_t* slot;
   unsigned long long* val;
@@ -1001,30 +1000,34 @@ __device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Pa
         R len = R(0);
         if (live) {
           const R nxt = fmin(fmin(fmin(sn[0], sn[1]), fmin(sn[2], stn)), l);
-          if (nxt > s && idx[0] >= 0 && idx[0] < n[0] && idx[1] >= 0 && idx[1] < n[1] && idx[2] >= 0 &&
-              idx[2] < n[2] && it >= 0) {
-            emit = true;
-            slot = gbase + (uint32_t)(((idx[2] * n[1] + idx[1]) * n[0] + idx[0]) * gstride + it);
-            len = nxt - s;
-          }
-          if (nxt >= l) {
-            live = false;
-          } else {
+          emit = nxt > s && idx[0] >= 0 && idx[0] < n[0] && idx[1] >= 0 && idx[1] < n[1] && idx[2] >= 0 &&
+                 idx[2] < n[2] && it >= 0;
+          slot = gbase + (uint32_t)(((idx[2] * n[1] + idx[1]) * n[0] + idx[0]) * gstride + it);
+          len = nxt - s;
+          // every axis (and the time axis) whose crossing is at nxt steps, without branches: the next
+          // crossing distance is computed for every axis (edge index clamped to the edge list) and
+          // kept only where the axis stepped; an axis stepping out of the mesh ends the walk
+          bool alive = nxt < l;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-              if (sn[d] <= nxt) {
-                idx[d] += step[d];
-                if (idx[d] < 0 || idx[d] >= n[d]) live = false;  // left the mesh along this axis
-                else sn[d] = (e[d][idx[d] + (step[d] > 0 ? 1 : 0)] - pos[d]) * inv[d];
-              }
-            }
-            if (stn <= nxt) {
-              ++it;
-              if (it >= nt) live = false;
-              else stn = (et[it + 1] - t0) * v;
-            }
-            s = nxt;
+          for (int d = 0; d < 3; ++d) {
+            const bool st = sn[d] <= nxt;
+            const int ni = idx[d] + (st ? step[d] : 0);
+            const int ei = min(max(ni + (step[d] > 0 ? 1 : 0), 0), n[d]);
+            const R nsn = (e[d][ei] - pos[d]) * inv[d];
+            alive = alive && !(st && (ni < 0 || ni >= n[d]));
+            idx[d] = ni;
+            sn[d] = st ? nsn : sn[d];
           }
+          {
+            const bool st = stn <= nxt;
+            const int ni = it + (st ? 1 : 0);
+            const R nstn = (et[min(ni + 1, nt)] - t0) * v;
+            alive = alive && ni < nt;
+            it = ni;
+            stn = st ? nstn : stn;
+          }
+          live = alive;
+          s = nxt;
         }
         stage(emit, slot, len);
       }

@@ -82,11 +82,13 @@ __device__ void log_event(const RunParams& P, const Tab<R>& T, const Part<R>& p,
 }
 
 // ------------------------------------------------------------------------------------------ counters
-// per-CTA (per-warp in the batched kernel) event counters, and the birth count above which a
-// weight-window split is held (half the birth store, less the births that wait to be stored again
-// in this iteration)
+// per-CTA (per-warp in the batched kernel) event counters and the weight-window split limit: with
+// a split counter (the persistent kernel: the iteration's count of split copies) hold_at is the
+// iteration's budget of copies (half the birth store, less the births that wait to be stored
+// again); without one, the fill of the warp's stack above which splits wait
 struct __align__(16) BlockCounters {
   unsigned int c[MC_NCOUNTERS];
+  unsigned long long* split_ctr;
   unsigned long long hold_at;
 };
 __device__ __forceinline__ void bump(BlockCounters* bc, int i, unsigned v = 1u) { atomicAdd(&bc->c[i], v); }
@@ -111,24 +113,40 @@ __device__ bool weight_window(const RunParams& P, const Tab<R>& T, Part<R>& p, u
   const double* ex = P.ww_edges;
   const double* ey = ex + P.ww_nx + 1;
   const double* ez = ey + P.ww_ny + 1;
+  const double* et = ez + P.ww_nz + 1;
   // the window of the cell the particle moves into: a particle on a window-mesh edge (e.g. just
-  // after crossing a layer plane that is also a mesh plane) is looked up 1e-9 cm ahead
+  // after crossing a layer plane that is also a mesh plane) is looked up 1e-9 cm ahead; the time
+  // bin is the one holding the particle's time
   const double ah = 1e-9;
   const int ix = bin_search(ex, P.ww_nx, (double)p.x + ah * (double)p.ux),
             iy = bin_search(ey, P.ww_ny, (double)p.y + ah * (double)p.uy),
-            iz = bin_search(ez, P.ww_nz, (double)p.z + ah * (double)p.uz);
-  if (ix < 0 || ix >= P.ww_nx || iy < 0 || iy >= P.ww_ny || iz < 0 || iz >= P.ww_nz) return true;
-  const double wc = __ldg(P.ww_center + ((size_t)(iz * P.ww_ny + iy) * P.ww_nx + ix) * T.G + pk_g(p.pk));
+            iz = bin_search(ez, P.ww_nz, (double)p.z + ah * (double)p.uz),
+            it = P.ww_nt > 1 ? bin_search(et, P.ww_nt, p.time_d()) : 0;
+  if (ix < 0 || ix >= P.ww_nx || iy < 0 || iy >= P.ww_ny || iz < 0 || iz >= P.ww_nz || it < 0 || it >= P.ww_nt)
+    return true;
+  const double wc =
+      __ldg(P.ww_center + ((((size_t)it * P.ww_nz + iz) * P.ww_ny + iy) * P.ww_nx + ix) * T.G + pk_g(p.pk));
   if (!(wc > 0.0)) return true;
   if (p.w > P.ww_upper * wc) {
-    // a split is optional: while the birth store is more than half full the particle keeps its
-    // weight (unbiased), so windows far below the flux cannot overflow the store
-    if (*reinterpret_cast<volatile unsigned long long*>(bcount) >= bc->hold_at) {
+    int n = (int)ceil(p.w / wc);
+    if (n > P.ww_split_max) n = P.ww_split_max;
+    // A split is optional: while it would overfill the split budget the particle keeps its weight
+    // (unbiased), so that windows far below the flux cannot overflow the birth store.  In the
+    // persistent kernel the n - 1 copies are first counted on the iteration's split counter (one
+    // atomic add; an attempt that would pass the budget holds, and since its count is not taken
+    // back the counter only errs towards holding), so that particles splitting at the same moment
+    // cannot overshoot the budget together; in a warp's private stack the stack's fill is compared
+    // with the limit.
+    const unsigned long long need = (unsigned long long)(n - 1);
+    if (bc->split_ctr != nullptr) {
+      if (atomicAdd(bc->split_ctr, need) + need > bc->hold_at) {
+        bump(bc, MC_C_WW_HELD);
+        return true;
+      }
+    } else if (*reinterpret_cast<volatile unsigned long long*>(bcount) >= bc->hold_at) {
       bump(bc, MC_C_WW_HELD);
       return true;
     }
-    int n = (int)ceil(p.w / wc);
-    if (n > P.ww_split_max) n = P.ww_split_max;
     p.w = p.w / n;
     for (int j = 1; j < n; ++j) {
       Part<R> c = p;
@@ -637,6 +655,5 @@ __device__ inline void reconstruct_warp(void* tally, const char* blob64, uint64_
   }
 }
 
-constexpr unsigned kWarpQ = 64;  // per-warp flight queue slots
 
 }  // namespace mcgb

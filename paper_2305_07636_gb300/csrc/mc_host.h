@@ -103,7 +103,7 @@ struct mc_problem {
   double fixed_scale = 1.0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // transport start, transport end, stats end
   // weight windows
-  int ww_set = 0, ww_n[3] = {0, 0, 0};
+  int ww_set = 0, ww_n[4] = {0, 0, 0, 0};  // window mesh: x, y, z and time bins
   double src_center[3] = {0.0, 0.0, 0.0};  // reference point of the source (box centre / surface point)
   int src_group = 0;                        // the source's most likely group
   mcgb::DevBuf d_ww;

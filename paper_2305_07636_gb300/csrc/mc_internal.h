@@ -12,6 +12,10 @@ constexpr int kSurfStride = 16;   // table values per surface (plane / cylinder,
 constexpr int kMaxLanes = 6;      // 16-byte state lanes per particle (FP64 layout)
 constexpr int kLanesFP32 = 4;     // 64 B per particle
 constexpr int kLanesFP64 = 6;     // 96 B per particle
+// per-warp shared memory of the transport kernels: flight queue slots and tally staging entries
+// (8-byte value + 4-byte slot each)
+constexpr unsigned kWarpQ = 64;
+constexpr unsigned kStage = 128;
 constexpr uint32_t kSourceEvent = 0xFFFFFFFFu;
 constexpr uint32_t kChildMark = 0x80000000u;
 constexpr uint32_t kSplitMark = 0xC0000000u;
@@ -126,6 +130,7 @@ struct Ctl {
   // the front in the low 32 bits, surface-pending ones from the back in the high 32 bits; cap_s <
   // 2^32), the birth bank's fill and the first history not yet started
   unsigned long long fb[3], birth[3], hstart[3];
+  unsigned long long splits[3];  // weight-window split copies counted in the iteration (rotated too)
   unsigned long long next[3];                                 // dynamic item claim counters
   unsigned int bar_count, bar_gen;
   int status, pad;
@@ -167,8 +172,9 @@ struct RunParams {
   uint64_t log_cap, log_first, log_count;
   // weight windows (optional)
   int ww_on, ww_nx, ww_ny, ww_nz;
-  const double* ww_edges;  // x[nx+1], y[ny+1], z[nz+1]
-  const double* ww_center; // [nz][ny][nx][G]
+  int ww_nt, pad_ww;
+  const double* ww_edges;  // x[nx+1], y[ny+1], z[nz+1], t[nt+1]
+  const double* ww_center; // [nt][nz][ny][nx][G]
   double ww_upper, ww_lower;
   int ww_split_max;
   int implicit;            // implicit capture with a weight-cutoff roulette

@@ -22,10 +22,22 @@
 
 namespace mcgb {
 
-// Items a warp claims per atomic on the iteration's work counter (processed 32 at a time).
-constexpr unsigned kClaim = 128;
+// Items a warp claims per atomic on the iteration's work counter (processed 32 at a time): kClaim
+// while more than kTailWaves claims per warp of the grid remain, kClaimTail after that, so that
+// the warps of the grid run out of work at nearly the same time and wait less at the barrier.
+#ifndef MCGB_CLAIM
+#define MCGB_CLAIM 128
+#endif
+#ifndef MCGB_CLAIM_TAIL
+#define MCGB_CLAIM_TAIL 32
+#endif
+#ifndef MCGB_TAIL_WAVES
+#define MCGB_TAIL_WAVES 2
+#endif
+constexpr unsigned kClaim = MCGB_CLAIM, kClaimTail = MCGB_CLAIM_TAIL, kTailWaves = MCGB_TAIL_WAVES;
 
 // dynamic shared memory: [table blob][per-warp flight queues: warps x Lanes<R>::N x kWarpQ]
+// [per-warp tally staging: warps x kStage x 12 B]
 template <typename R, int MINB, bool RANGE>
 __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
   extern __shared__ __align__(16) char smem[];
@@ -82,12 +94,16 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
       break;
     }
     const bool drain = P.history_mode || (nSrc == left && W <= P.drain_threshold);
-    // splits are held once the births of this iteration, with the nB - nBt waiting births that
-    // are stored again below, would fill half the birth store
-    if (threadIdx.x == 0) bc.hold_at = P.cap_b / 2 > nB - nBt ? P.cap_b / 2 - (nB - nBt) : 0ull;
+    // splits are held once the copies made in this iteration would exceed half the birth store,
+    // less the nB - nBt waiting births that are stored again below
+    if (threadIdx.x == 0) {
+      bc.split_ctr = &ctl->splits[cur];
+      bc.hold_at = P.cap_b / 2 > nB - nBt ? P.cap_b / 2 - (nB - nBt) : 0ull;
+    }
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       ctl->fb[old] = 0ull;
+      ctl->splits[old] = 0ull;
       ctl->birth[old] = 0ull;
       ctl->next[old] = 0ull;
       ctl->hstart[nxt] = h0 + nSrc;
@@ -98,6 +114,9 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
         P.trace[3 * it + 2] = nSrc | (drain ? (1ull << 63) : 0ull);
       }
     }
+    // the items left when the claims switch to the tail size (the end of the previous claimed
+    // range stands for the shared claim counter, which only grows)
+    const uint64_t tail = (uint64_t)kTailWaves * kClaim * gridDim.x * nwarp;
     uint4* const* Sin = P.S[it & 1];
     uint4* const* Sout = P.S[(it + 1) & 1];
     uint4* const* Bin = P.B[it & 1];
@@ -118,11 +137,12 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
       while (qn < 32u && !(exhausted && rbeg >= rend)) {
         if (rbeg >= rend) {
           unsigned long long b = 0;
-          if (lane == 0) b = atomicAdd(claim, (unsigned long long)kClaim);
+          const unsigned take = rend + tail < W ? kClaim : kClaimTail;
+          if (lane == 0) b = atomicAdd(claim, (unsigned long long)take);
           b = __shfl_sync(0xFFFFFFFFu, b, 0);
           rbeg = b;
-          rend = b + kClaim < W ? b + kClaim : W;
-          if (b + kClaim >= W) exhausted = true;
+          rend = b + take < W ? b + take : W;
+          if (b + take >= W) exhausted = true;
           if (rbeg >= rend) break;
         }
         const uint64_t item = rbeg + lane;
@@ -446,6 +466,81 @@ __global__ void k_atomic_probe(unsigned long long* a, unsigned long long span, i
 cudaError_t launch_atomic_probe(unsigned long long* a, unsigned long long span, int grid, int iters, unsigned salt,
                                 cudaStream_t s) {
   k_atomic_probe<<<grid, 256, 0, s>>>(a, span, iters, salt);
+  return cudaGetLastError();
+}
+
+// Instruction throughput probe: every thread runs four independent chains of `iters` operations of
+// one kind (op 0 FP32 FMA, 1 FP64 add, 2 32-bit umulhi, 3 int -> float, 4 float -> int64, 5 __logf),
+// so that throughput, not latency, bounds it; block 0 records the SM clock ticks and the global
+// nanoseconds it took (the clock rate seen by the kernel).  The result feeds a sink so that nothing
+// is optimised away.
+template <int OP>
+__global__ void k_op_probe(int iters, unsigned long long* sink, unsigned long long* clk) {
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const long long c0 = clock64();
+  unsigned long long g0 = 0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(g0));
+  unsigned long long acc = 0;
+  if (OP == 0) {
+    float a[4] = {1.0f + t * 1e-9f, 1.1f, 1.2f, 1.3f};
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) a[c] = __fmaf_rn(a[c], 0.999999f, 1e-7f);
+    acc = __float_as_uint(a[0] + a[1] + a[2] + a[3]);
+  } else if (OP == 1) {
+    double a[4] = {1.0 + t * 1e-12, 1.1, 1.2, 1.3};
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) a[c] = __dadd_rn(a[c], 1e-9);
+    acc = (unsigned long long)__double_as_longlong(a[0] + a[1] + a[2] + a[3]);
+  } else if (OP == 2) {
+    unsigned a[4] = {t | 1u, 3u, 5u, 7u};
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) a[c] = __umulhi(a[c], 0x9E3779B9u) + 0x6A09E667u;
+    acc = a[0] ^ a[1] ^ a[2] ^ a[3];
+  } else if (OP == 3) {
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    int b[4] = {(int)t, 2, 3, 4};
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        a[c] = __int2float_rn(b[c]);
+        b[c] = __float_as_int(a[c]) >> 3;
+      }
+    acc = __float_as_uint(a[0] + a[1] + a[2] + a[3]);
+  } else if (OP == 4) {
+    float a[4] = {1.5f + t, 2.5f, 3.5f, 4.5f};
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) a[c] = __int_as_float((int)(__float2ll_rn(a[c]) | 0x3F800000ll));
+    acc = __float_as_uint(a[0] + a[1] + a[2] + a[3]);
+  } else {
+    float a[4] = {1.5f + t * 1e-7f, 2.5f, 3.5f, 4.5f};
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) a[c] = __logf(a[c]) + 2.0f;
+    acc = __float_as_uint(a[0] + a[1] + a[2] + a[3]);
+  }
+  if (acc == 0x5EED5EEDull) *sink = acc;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    unsigned long long g1 = 0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(g1));
+    clk[0] = (unsigned long long)(clock64() - c0);
+    clk[1] = g1 - g0;
+  }
+}
+
+cudaError_t launch_op_probe(int op, int grid, int iters, unsigned long long* sink, unsigned long long* clk,
+                            cudaStream_t s) {
+  switch (op) {
+    case 0: k_op_probe<0><<<grid, 256, 0, s>>>(iters, sink, clk); break;
+    case 1: k_op_probe<1><<<grid, 256, 0, s>>>(iters, sink, clk); break;
+    case 2: k_op_probe<2><<<grid, 256, 0, s>>>(iters, sink, clk); break;
+    case 3: k_op_probe<3><<<grid, 256, 0, s>>>(iters, sink, clk); break;
+    case 4: k_op_probe<4><<<grid, 256, 0, s>>>(iters, sink, clk); break;
+    default: k_op_probe<5><<<grid, 256, 0, s>>>(iters, sink, clk); break;
+  }
   return cudaGetLastError();
 }
 

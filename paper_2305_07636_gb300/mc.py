@@ -132,6 +132,7 @@ SIGNATURES = {
                                C.POINTER(C.c_size_t)]),
     "mc_run_timing": (C.c_int, [C.c_void_p, DP, DP]),
     "mc_tally_layout": (C.c_int, [C.c_void_p, IP, IP, C.POINTER(C.c_uint64)]),
+    "mc_tally_sums": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.c_size_t, IP]),
     "mc_trace_get": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
                                C.POINTER(C.c_uint64), C.c_size_t, C.POINTER(C.c_size_t)]),
     "mc_problem_table_bytes": (C.c_size_t, [C.c_void_p]),
@@ -139,7 +140,9 @@ SIGNATURES = {
     "mc_last_error": (C.c_char_p, []),
     "mc_philox": (C.c_int, [C.c_uint64, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]),
     "mc_atomic_peak": (C.c_int, [C.c_uint64, DP]),
+    "mc_op_rates": (C.c_int, [DP, C.c_int]),
     "mc_ww_set_table": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, DP, DP]),
+    "mc_ww_set_table_t": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, DP, DP]),
     "mc_mlp_param_count": (C.c_int, []),
     "mc_mlp_create": (C.c_int, [C.POINTER(C.c_void_p)]),
     "mc_mlp_destroy": (None, [C.c_void_p]),
@@ -362,6 +365,16 @@ def tally_get(h: int, tally_id: int):
     return mean.reshape(shp), err.reshape(shp)
 
 
+def tally_sums(h: int, tally_id: int):
+    """mc_tally_sums: (exact int64 sums per bin, fixed_bits) of the last run's fixed-point tally."""
+    shp = tally_shape(h, tally_id)
+    out = np.zeros(int(np.prod(shp)), np.int64)
+    bits = C.c_int(0)
+    check(lib().mc_tally_sums(C.c_void_p(h), int(tally_id), out.ctypes.data_as(C.POINTER(C.c_int64)), out.size,
+                              C.byref(bits)))
+    return out.reshape(shp), bits.value
+
+
 def tally_batches(h: int, tally_id: int) -> np.ndarray:
     """mc_tally_batches: per-batch per-source-particle means, shape (n_batches, *tally shape)."""
     shp = tally_shape(h, tally_id)
@@ -437,12 +450,18 @@ def batch_tune(handles, n_hist, seed: int, opts: mc_run_opts | None = None, stre
 
 
 def ww_set_table(h: int, ww: dict):
-    """mc_ww_set_table from {x, y, z: edges, center: [nz][ny][nx][G]}."""
-    edges = np.ascontiguousarray(np.concatenate([np.asarray(ww[k], np.float64) for k in "xyz"]))
+    """mc_ww_set_table from {x, y, z: edges, center: [nz][ny][nx][G]}, or mc_ww_set_table_t when
+    the dict also has time edges t (center: [nt][nz][ny][nx][G])."""
+    axes = "xyzt" if "t" in ww else "xyz"
+    edges = np.ascontiguousarray(np.concatenate([np.asarray(ww[k], np.float64) for k in axes]))
     centre = np.ascontiguousarray(np.asarray(ww["center"], np.float64).ravel())
-    n = [len(ww[k]) - 1 for k in "xyz"]
-    check(lib().mc_ww_set_table(C.c_void_p(h), n[0], n[1], n[2], edges.ctypes.data_as(DP),
-                                centre.ctypes.data_as(DP)))
+    n = [len(ww[k]) - 1 for k in axes]
+    if "t" in ww:
+        check(lib().mc_ww_set_table_t(C.c_void_p(h), n[0], n[1], n[2], n[3], edges.ctypes.data_as(DP),
+                                      centre.ctypes.data_as(DP)))
+    else:
+        check(lib().mc_ww_set_table(C.c_void_p(h), n[0], n[1], n[2], edges.ctypes.data_as(DP),
+                                    centre.ctypes.data_as(DP)))
 
 
 def atomic_peak(span: int) -> float:
@@ -450,6 +469,14 @@ def atomic_peak(span: int) -> float:
     v = C.c_double(0)
     check(lib().mc_atomic_peak(int(span), C.byref(v)))
     return v.value
+
+
+def op_rates() -> dict:
+    """mc_op_rates: operations per SM clock per SM of the instruction kinds the walk depends on."""
+    out = np.zeros(6)
+    check(lib().mc_op_rates(out.ctypes.data_as(DP), 6))
+    return dict(zip(("fp32_fma", "fp64_add", "umulhi", "int_to_float", "float_to_int64", "logf"),
+                    (float(v) for v in out)))
 
 
 def run_timing(h: int):
@@ -520,6 +547,9 @@ class Problem:
 
     def tally_batches(self, i=0):
         return tally_batches(self.h, i)
+
+    def tally_sums(self, i=0):
+        return tally_sums(self.h, i)
 
     def leakage(self):
         return tally_get(self.h, self.n_tallies)

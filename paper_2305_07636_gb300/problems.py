@@ -564,10 +564,11 @@ def config4_materials(seed=4, G=7, n_mat=4):
 
 
 def slab_stack(thickness=200.0, n_layers=40, G=7, seed=4, detector=2.0, ww_bin=5.0,
-               name="config4"):
+               name="config4", t_edges=(0.0, INF), t_census=INF):
     """Deep-penetration x-layered slab stack (infinite in y, z), vacuum both ends, cosine
-    (isotropic-flux) surface source at x=0 in group 1; tally 0 = detector on the last
-    `detector` cm, tally 1 = coarse space-group mesh used to train weight windows."""
+    (isotropic-flux) surface source at x=0 in group 1 at t = 0; tally 0 = detector on the last
+    `detector` cm, tally 1 = coarse space-group mesh used to train weight windows; both tallies
+    take the time bins `t_edges` (one bin holding every time by default)."""
     mats = config4_materials(seed, G)
     dx = thickness / n_layers
     xs = [i * dx for i in range(n_layers + 1)]
@@ -579,9 +580,17 @@ def slab_stack(thickness=200.0, n_layers=40, G=7, seed=4, detector=2.0, ww_bin=5
              for i in range(n_layers)]
     src = source("surface_x0", (0, 0, 0), (0, 0, 0), "cos_x", G, 0)
     n_ww = max(1, int(round(thickness / ww_bin)))
-    tal = [mesh(x=(thickness - detector, thickness)),
-           mesh(x=np.linspace(0.0, thickness, n_ww + 1))]
-    return problem(name, G, log_speeds(G), mats, surfs, cells, src, tal, INF)
+    tal = [mesh(x=(thickness - detector, thickness), t=t_edges),
+           mesh(x=np.linspace(0.0, thickness, n_ww + 1), t=t_edges)]
+    return problem(name, G, log_speeds(G), mats, surfs, cells, src, tal, t_census)
+
+
+def pulse_stack(thickness=10.0, n_layers=5, n_tbins=12, t_hi=1e-4, ww_bin=1.0, seed=4, name="pulse"):
+    """The slab stack hit by a pulse: the cosine surface source fires at t = 0, the detector and the
+    window-training mesh are resolved in n_tbins time bins ({0} U logspace(1e-9, t_hi)), and the
+    census ends every history at t_hi."""
+    return slab_stack(thickness=thickness, n_layers=n_layers, seed=seed, detector=2.0, ww_bin=ww_bin, name=name,
+                      t_edges=log_time_edges(n_tbins, 1e-9, t_hi), t_census=t_hi)
 
 
 def config4(seed=4, thickness=200.0):
@@ -657,9 +666,10 @@ def _small_lattice(seed, G, name):
     return p
 
 
-def exponential_ww(prob, decay, nx=None, ref=1.0):
+def exponential_ww(prob, decay, nx=None, ref=1.0, t_edges=None, t_decay=0.0):
     """Weight-window centres w_c = ref * exp(-decay * x) on an x-mesh (edges from the problem's
-    second tally, or nx equal bins over the slab), all groups alike: a fixed, seeded-free input."""
+    second tally, or nx equal bins over the slab), all groups alike: a fixed, seeded-free input.
+    With time edges, time bin i takes w_c * exp(-t_decay * i) (center [nt][nx][G])."""
     if nx is None:
         xe = np.asarray(prob["tallies"][1]["x"], dtype=np.float64)
     else:
@@ -668,7 +678,14 @@ def exponential_ww(prob, decay, nx=None, ref=1.0):
     xc = 0.5 * (xe[:-1] + xe[1:])
     G = prob["G"]
     centre = np.repeat((ref * np.exp(-decay * xc))[:, None], G, axis=1)  # [nx][G]
-    return {"x": xe.tolist(), "y": [-INF, INF], "z": [-INF, INF], "center": centre.tolist()}
+    ww = {"x": xe.tolist(), "y": [-INF, INF], "z": [-INF, INF]}
+    if t_edges is None:
+        ww["center"] = centre.tolist()
+        return ww
+    nt = len(t_edges) - 1
+    ww["t"] = [float(v) for v in t_edges]
+    ww["center"] = (np.exp(-t_decay * np.arange(nt))[:, None, None] * centre[None]).tolist()  # [nt][nx][G]
+    return ww
 
 
 def bf16_round(a):

@@ -178,6 +178,58 @@ def test_learned_weight_windows_gain_and_stay_unbiased(torch):
     net.close()
 
 
+def test_learned_time_dependent_windows_on_a_pulse(torch):
+    """A pulse through the 10 cm stack, the detector and the training mesh resolved in 12 time bins
+    (to 1e-4 s): one analog run trains the network on (x, group, time bin) points of its own
+    time-resolved mesh tally, and the baked windows change with the particle's time.  Against
+    analog transport on the same GPU they resolve many more of the detector's (group, time) bins
+    (30 against 1 to 20%), give a larger figure of merit on the late-time detector response (the
+    last time bin, summed over groups: 2.9x), and the detector total and every bin both runs resolve
+    agree within 4 sigma.  (Windows trained on a one-time-bin mesh of the same problem do better
+    still on this detector, 10x on its total: the time-resolved targets spread the particles over
+    all time bins, the early ones included, where the detector is not reached.)"""
+    prob = P.pulse_stack(thickness=10.0, n_layers=5, n_tbins=12, t_hi=1e-4, ww_bin=1.0)
+    nb = 32
+    p = mc.Problem(prob)
+    p.run(8_000_000, 1, tally_mode="fp64")
+    p.wait()
+    t_a = p.timing()[0]
+    ba = p.tally_batches(0).reshape(nb, 7, 12)
+    mo, so = (np.asarray(a, np.float64).reshape(7, 12) for a in p.tally(0))
+    net = mc.Mlp(P.mlp_init(seed=4))
+    info = mc.ww_learn(p.h, net, 1, 3000, 3e-3)
+    # more points than the 10 x 7 (cell, group) pairs: the targets are resolved in time
+    assert info["points"] > 70, info
+    p.run(50_000, 2, tally_mode="fp64", ww_enable=1, bank_capacity=1 << 22)
+    p.wait()
+    t_w = p.timing()[0]
+    bw = p.tally_batches(0).reshape(nb, 7, 12)
+    mg, sg = (np.asarray(a, np.float64).reshape(7, 12) for a in p.tally(0))
+    c = p.counters()
+    assert conserved(c) and c["ww_split"] > 0 and c["ww_kill"] > 0
+
+    def fom(b, t):  # of the sum over groups of the last time bin, from the batch spread
+        x = b[:, :, -1].sum(axis=1)
+        return 1.0 / ((x.std(ddof=1) / np.sqrt(nb) / x.mean()) ** 2 * t), x.mean(), x.std(ddof=1) / np.sqrt(nb)
+
+    fa, xa, ea = fom(ba, t_a)
+    fw, xw, ew = fom(bw, t_w)
+    res_a = int(np.sum((so > 0) & (so < 0.2 * mo)))
+    res_w = int(np.sum((sg > 0) & (sg < 0.2 * mg)))
+    print(f"pulse stack: detector bins resolved to 20%: analog {res_a}, time-dependent windows {res_w}; "
+          f"late-time FOM analog {fa:.3g} /s, windows {fw:.3g} /s ({fw / fa:.1f}x); {info['points']} training points")
+    assert res_w >= 5 * max(res_a, 1), (res_a, res_w)
+    assert fw > 2.0 * fa, (fw, fa)
+    assert abs(xw - xa) < 4.0 * np.hypot(ea, ew), (xw, xa)
+    ta, tw = ba.sum(axis=(1, 2)), bw.sum(axis=(1, 2))
+    assert abs(tw.mean() - ta.mean()) < 4.0 * np.hypot(ta.std(ddof=1), tw.std(ddof=1)) / np.sqrt(nb)
+    ok = (sg > 0) & (so > 0) & (sg < 0.2 * mg) & (so < 0.2 * mo)
+    z = (mg[ok] - mo[ok]) / np.hypot(sg[ok], so[ok])
+    assert np.all(np.abs(z) < 4.0), z
+    p.close()
+    net.close()
+
+
 def test_extrapolated_windows_reach_an_analog_blind_detector(torch):
     """40 cm stack: the detector flux (~1e-22 per source particle) is out of analog reach.  Learned
     windows continued past the resolved depth (slope fraction 1, 20 e-folds) resolve the whole

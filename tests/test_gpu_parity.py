@@ -401,6 +401,35 @@ def test_weight_window_fp64_replay_and_unbiasedness(torch):
     p.close()
 
 
+def test_time_dependent_windows_fp64_replay_and_unbiasedness(torch):
+    """Windows that change from one time bin to the next (a pulse through a slab stack, the window
+    centre falling by e^-0.5 per time bin): the FP64 GPU walk replays the oracle's event sequence,
+    splits and roulettes included, and the FP32 windowed tallies agree with the oracle's analog
+    tallies within 4 sigma."""
+    prob = P.pulse_stack(thickness=4.0, n_layers=2, n_tbins=6, ww_bin=0.5)
+    ww = P.exponential_ww(prob, decay=0.8, t_edges=prob["tallies"][0]["t"], t_decay=0.5)
+    n = 2000
+    o = oracle.run(prob, n, seed=78, threads=THREADS, log_first=0, log_count=n, log_cap=2000 * n,
+                   ww=ww)
+    p = mc.Problem(prob)
+    p.set_weight_windows(ww)
+    p.run(n, 78, precision="fp64", tally_mode="fp64", ww_enable=1, log_first=0, log_count=n,
+          log_capacity=2000 * n, bank_capacity=1 << 20)
+    compare_logs(p.events(2000 * n), o.events)
+    c = p.counters()
+    for k in oracle.COUNTER_NAMES:
+        assert c[k] == o.counters[k], k
+    assert c["ww_split"] > 0 and c["ww_kill"] > 0
+    a = oracle.run(prob, 2_000_000, seed=5, threads=THREADS)
+    p.run(200_000, 6, tally_mode="fp64", ww_enable=1, bank_capacity=1 << 22)
+    assert conserved(p.counters()) and p.counters()["ww_held"] == 0
+    for t in (0, 1):
+        mg, sg = p.tally(t)
+        mo, so = a.tallies[t]
+        check_z(combined_z(mg, sg, mo, so), 5 if t == 0 else 60)
+    p.close()
+
+
 def test_held_splits_stay_unbiased_and_bad_windows_cannot_overflow(torch):
     """A weight-window split is optional: while the particle store is more than half full it is
     held (the particle keeps its weight).  (1) The same windows (exp(-1.1 x), close to the flux
