@@ -562,6 +562,43 @@ def bench_eigen(args, torch, mc, prob, n, desc):
     p.close()
 
 
+def time_learning_kernels(torch, mc, P, n=700, epochs=3000, reps=5):
+    """CUDA-event times of the importance network's kernels on n training points (the 200 cm stack's
+    learning rounds train on about 700): one forward pass, one loss-and-gradient pass, and full-batch
+    Adam (one launch for all epochs), per call and per epoch."""
+    rng = np.random.default_rng(1)
+    x = torch.tensor(P.bf16_round(rng.uniform(-1, 1, (n, 5))), dtype=torch.float32, device="cuda")
+    tgt = torch.tensor(rng.normal(0, 1, n), dtype=torch.float32, device="cuda")
+    wt = torch.ones(n, dtype=torch.float32, device="cuda")
+    y = torch.zeros(n, device="cuda")
+    net = mc.Mlp(P.mlp_init(seed=4))
+    g = torch.zeros(net.n_params, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+
+    def timed(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    fwd = timed(lambda: net.forward(x.data_ptr(), y.data_ptr(), n), 20 * reps)
+    grad = timed(lambda: net.loss_grad(x.data_ptr(), tgt.data_ptr(), wt.data_ptr(), n, g.data_ptr(),
+                                       loss.data_ptr()), 20 * reps)
+    train = timed(lambda: net.train(x.data_ptr(), tgt.data_ptr(), wt.data_ptr(), n, epochs, 3e-3, loss.data_ptr()),
+                  reps)
+    net.close()
+    flops_fwd = 2.0 * (5 * 64 + 2 * 64 * 64 + 64) * n
+    return {"points": n, "forward_ms": fwd, "loss_grad_ms": grad, "train_ms": train, "epochs": epochs,
+            "train_ms_per_epoch": train / epochs, "forward_tflops": flops_fwd / (fwd * 1e-3) / 1e12,
+            "note": "one cooperative launch trains for all epochs on a grid of CTAs (a warp per 16-sample "
+                    "tile, two grid barriers per epoch); the network is 8,769 parameters"}
+
+
 def bench_learned_ww(args, torch, mc):
     """Learned weight windows on the 200 cm stack: 5 refinement rounds from an analog start,
     then a measurement run with the final windows; analog and an exponential (non-learned) window
@@ -636,6 +673,7 @@ def bench_learned_ww(args, torch, mc):
                               "z_learned_vs_analog": z, "rounds": rounds2},
                 "unit": "1/s", "tally": "detector flux, last 2 cm, all groups"},
         "rounds": rounds, "learning_s": learn_total,
+        "learning_kernels": time_learning_kernels(torch, mc, P),
         "counters": {k: c[k] for k in ("flight", "ww_split", "ww_kill", "scores")},
         "gpu_launches": 2 * args.steps,
         "clocks": clk,

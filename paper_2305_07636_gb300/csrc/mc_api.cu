@@ -28,7 +28,7 @@ template <typename R>
 cudaError_t launch_transport(const RunParams& P, int grid, int block, size_t smem, cudaStream_t s, bool wide,
                              bool range);
 template <typename R>
-cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide, bool range);
+cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide, bool range, bool seg);
 cudaError_t launch_scan_sites(const uint32_t* counts, unsigned long long* scan, unsigned long long* block_sums, uint64_t n,
                               cudaStream_t s);
 cudaError_t launch_comb(const uint32_t* counts, const unsigned long long* scan, const uint4* sites, uint32_t nmax,
@@ -660,6 +660,7 @@ void mc_problem_destroy(mc_problem* p) {
   p->d_trace.release();
   p->d_sticky.release();
   p->d_ww.release();
+  p->d_seg.release();
   // k-eigenvalue and population-control buffers
   p->d_sites.release();
   p->d_counts.release();
@@ -882,14 +883,22 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   // (that walk needs the registers) and the 80-register build otherwise
   const bool range = p->range;
   const bool wide = o.blocks_per_sm == 2 || (o.blocks_per_sm == 0 && range);
-  CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm, wide, range)
-          : transport_occupancy<float>(block, smem, &per_sm, wide, range));
+  // FP32 tracking with plain-walk tallies only: segments are scored apart from their flights
+  bool seg = !fp64 && !range && p->n_tally <= 4;
+  for (const HostTally& t : p->tallies) seg = seg && t.est == MC_EST_TRACK_LENGTH;
+  CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm, wide, range, false)
+          : transport_occupancy<float>(block, smem, &per_sm, wide, range, seg));
   if (per_sm < 1) return fail(MC_ERR_CUDA, "transport kernel does not fit on an SM (block %d, smem %zu)", block, smem);
   if (o.blocks_per_sm > 0) per_sm = std::min(per_sm, std::max(1, o.blocks_per_sm * 256 / block));
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->dev));
   const int grid = sms * per_sm;
   P.drain_threshold = o.drain_threshold ? o.drain_threshold : (uint64_t)2 * grid * block;
+  if (seg) {
+    rc = p->d_seg.ensure((size_t)grid * (block / 32) * kSegLanes * kSegCap * 16, p->dev);
+    if (rc != MC_OK) return rc;
+    P.seg = (uint4*)p->d_seg.ptr;
+  }
   CK(cudaEventRecord(p->ev[0], s));
   if (o.n_census == 0) {
     CK(fp64 ? launch_transport<double>(P, grid, block, smem, s, wide, range)
@@ -997,8 +1006,8 @@ int mc_run_eigen(mc_problem* p, uint64_t n_per_cycle, int n_inactive, int n_acti
   const bool range = p->range;
   const bool wide = o.blocks_per_sm == 2 || (o.blocks_per_sm == 0 && range);
   int per_sm = 0;
-  CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm, wide, range)
-          : transport_occupancy<float>(block, smem, &per_sm, wide, range));
+  CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm, wide, range, false)
+          : transport_occupancy<float>(block, smem, &per_sm, wide, range, false));
   if (per_sm < 1) return fail(MC_ERR_CUDA, "transport kernel does not fit on an SM (block %d, smem %zu)", block, smem);
   if (o.blocks_per_sm > 0) per_sm = std::min(per_sm, std::max(1, o.blocks_per_sm * 256 / block));
   int sms = 0;
@@ -1736,8 +1745,8 @@ extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t
   int per_sm = 0;
   const bool range = p->range;
   const bool wide = o.blocks_per_sm == 2 || (o.blocks_per_sm == 0 && range);
-  CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm, wide, range)
-          : transport_occupancy<float>(block, smem, &per_sm, wide, range));
+  CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm, wide, range, false)
+          : transport_occupancy<float>(block, smem, &per_sm, wide, range, false));
   if (per_sm < 1) return fail(MC_ERR_CUDA, "transport kernel does not fit on an SM (block %d, smem %zu)", block, smem);
   if (o.blocks_per_sm > 0) per_sm = std::min(per_sm, std::max(1, o.blocks_per_sm * 256 / block));
   int sms = 0;
@@ -1765,8 +1774,9 @@ cudaError_t mlp_refresh(const float* master, void* Wg, cudaStream_t s);
 cudaError_t mlp_forward(const void* Wg, const float* x, float* y, int n, cudaStream_t s);
 cudaError_t mlp_loss_grad(const void* Wg, const float* x, const float* tgt, const float* wt, int n, float* grad,
                           float* loss, cudaStream_t s);
+size_t mlp_train_scratch_bytes();
 cudaError_t mlp_train(float* master, float* m1, float* m2, void* Wg, const float* x, const float* tgt, const float* wt,
-                      int n, int epochs, float lr, long long step0, float* last_loss, cudaStream_t s);
+                      int n, int epochs, float lr, long long step0, float* last_loss, void* scratch, cudaStream_t s);
 cudaError_t mlp_centres(const float* y, int n, double scale, double ymin, double ymax, double ref, double* centre,
                         cudaStream_t s);
 }  // namespace mcgb
@@ -1774,6 +1784,7 @@ cudaError_t mlp_centres(const float* y, int n, double scale, double ymin, double
 struct mc_mlp {
   int dev = 0;
   DevBuf master, m1, m2, wg, data, aux;
+  DevBuf train;  // the trainer's epoch gradients and grid barrier
   long long steps = 0;
 };
 
@@ -1792,6 +1803,7 @@ int mc_mlp_create(mc_mlp** out) {
   if (rc == MC_OK) rc = m->m1.ensure(np * 4, m->dev);
   if (rc == MC_OK) rc = m->m2.ensure(np * 4, m->dev);
   if (rc == MC_OK) rc = m->wg.ensure(mlp_weights_bytes(), m->dev);
+  if (rc == MC_OK) rc = m->train.ensure(mlp_train_scratch_bytes(), m->dev);
   if (rc == MC_OK) {
     cudaError_t e = cudaMemset(m->master.ptr, 0, np * 4);
     if (e == cudaSuccess) e = cudaMemset(m->m1.ptr, 0, np * 4);
@@ -1818,6 +1830,7 @@ void mc_mlp_destroy(mc_mlp* m) {
   m->wg.release();
   m->data.release();
   m->aux.release();
+  m->train.release();
   delete m;
 }
 
@@ -1874,7 +1887,7 @@ int mc_mlp_train(mc_mlp* m, const float* x, const float* target, const float* wt
   g_err.clear();
   if (!m || !x || !target || n < 1 || epochs < 0 || !(lr > 0.f)) return fail(MC_ERR_INVALID, "bad argument");
   CK(mlp_train((float*)m->master.ptr, (float*)m->m1.ptr, (float*)m->m2.ptr, m->wg.ptr, x, target, wt, n, epochs, lr,
-               m->steps, last_loss, (cudaStream_t)stream));
+               m->steps, last_loss, m->train.ptr, (cudaStream_t)stream));
   m->steps += epochs;
   return MC_OK;
 }
@@ -2075,7 +2088,7 @@ extern "C" int mc_ww_learn(mc_problem* p, mc_mlp* m, int tally_id, int epochs, f
   CK(cudaMemcpy(dw, wt.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(dall, xall.data(), (size_t)nall * 5 * 4, cudaMemcpyHostToDevice));
   CK(mlp_train((float*)m->master.ptr, (float*)m->m1.ptr, (float*)m->m2.ptr, m->wg.ptr, dx, dt, dw, n, epochs, lr,
-               m->steps, dl, 0));
+               m->steps, dl, m->train.ptr, 0));
   m->steps += epochs;
   CK(mlp_forward(m->wg.ptr, dall, dy, nall, 0));
   // the window table lives on the tally's spatial mesh and, when resolved in time, its time bins
@@ -2096,6 +2109,7 @@ extern "C" int mc_ww_learn(mc_problem* p, mc_mlp* m, int tally_id, int epochs, f
   CK(mlp_centres(dy, nall, scale, -700.0, 50.0, 1.0, (double*)p->d_ww.ptr + n_edges, 0));
   float loss = 0.f;
   CK(cudaMemcpy(&loss, dl, 4, cudaMemcpyDeviceToHost));
+  if (std::isnan(loss)) return fail(MC_ERR_TIMEOUT, "the network's training grid barrier timed out");
   p->ww_n[0] = nx;
   p->ww_n[1] = ny;
   p->ww_n[2] = nz;

@@ -769,6 +769,246 @@ static __device__ __noinline__ unsigned long long score_bits_fp64(const RunParam
   return (unsigned long long)__double2ll_rn(w * len * P.fixed_scale);
 }
 
+template <typename R>
+struct ScoreSink {
+  const RunParams& P;
+  const Stage& S;
+  unsigned& pieces;
+  unsigned n_st;
+  double w;
+  float wscale;
+  __device__ ScoreSink(const RunParams& P_, const Stage& S_, unsigned& pieces_, double w_)
+      : P(P_), S(S_), pieces(pieces_), n_st(0u), w(w_),
+        wscale(sizeof(R) == 4 ? weight_to_float(w_) * P_.fixed_scale_f : 0.0f) {}
+  __device__ __forceinline__ void add(bool emit, uint32_t slot, R len) {
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, emit);
+    unsigned long long val = 0ull;
+    if (emit) {
+      if (sizeof(R) == 4 && !P.tally_fp64) {
+        const long long qv = float_to_fixed(wscale * fabsf((float)len));
+        val = (unsigned long long)(len < R(0) ? -qv : qv);
+      } else {
+        val = score_bits_fp64(P, w, (double)len);
+      }
+    }
+    pieces += __popc(m);
+    if (!P.aggregate) {
+      if (emit && in_range(P, slot, (uint64_t)P.tally_stripes * P.stripe_stride)) {
+        if (P.tally_fp64)
+          atomicAdd(reinterpret_cast<double*>(P.tally) + slot, __longlong_as_double((long long)val));
+        else
+          atomicAdd(reinterpret_cast<unsigned long long*>(P.tally) + slot, val);
+      }
+      return;
+    }
+    if (emit) {
+      const unsigned i = n_st + __popc(m & lanemask_lt());
+      S.slot[i] = slot;
+      S.val[i] = val;
+    }
+    n_st += __popc(m);
+    if (n_st > kStage - 32) {
+      stage_flush(P, S, n_st);
+      n_st = 0;
+    }
+  }
+  __device__ __forceinline__ void flush() {
+    if (n_st) stage_flush(P, S, n_st);
+    n_st = 0;
+  }
+};
+
+// ------------------------------------------------------------------------------------------ segment scoring
+// Scoring apart from the flight (FP32 tracking, tallies of the plain walk): a flown segment is
+// written as a record to the warp's segment region, and whenever 32 wait the warp scores 32 of
+// them at once, one per lane, for at most kSegRounds rounds; a walk still live then goes back as a
+// resumed record, and a finished one comes back for the next tally, if any.  The register-heavy
+// walk thus runs outside the flight, and a long walk no longer holds 31 lanes idle.  A resumed
+// walk recomputes its crossing distances by the walk's own expressions, so every piece, slot and
+// value equals those of an uninterrupted walk.
+constexpr unsigned kSegRounds = 3;
+
+struct SegRec {
+  float pos[3], u[3], l, t0, s;
+  double w;
+  int idx[3], it, g, ti;
+  bool resumed;
+  uint32_t batch;
+};
+
+__device__ __forceinline__ void seg_store(uint4* q, unsigned i, const SegRec& r) {
+  const unsigned long long wb = (unsigned long long)__double_as_longlong(r.w);
+  __stcg(q + i, make_uint4(__float_as_uint(r.pos[0]), __float_as_uint(r.pos[1]), __float_as_uint(r.pos[2]),
+                           __float_as_uint(r.u[0])));
+  __stcg(q + kSegCap + i, make_uint4(__float_as_uint(r.u[1]), __float_as_uint(r.u[2]), __float_as_uint(r.l),
+                                     __float_as_uint(r.t0)));
+  __stcg(q + 2 * kSegCap + i, make_uint4(__float_as_uint(r.s), 0u, (uint32_t)wb, (uint32_t)(wb >> 32)));
+  __stcg(q + 3 * kSegCap + i,
+         make_uint4((uint32_t)r.idx[0], (uint32_t)r.idx[1], (uint32_t)r.idx[2],
+                    (uint32_t)(r.it + 1) | ((uint32_t)r.g << 17) | ((uint32_t)r.ti << 22) | ((r.resumed ? 1u : 0u) << 24)));
+  __stcg(q + 4 * kSegCap + i, make_uint4(r.batch, 0u, 0u, 0u));
+}
+
+__device__ __forceinline__ void seg_load(const uint4* q, unsigned i, SegRec& r) {
+  const uint4 a = __ldcg(q + i), b = __ldcg(q + kSegCap + i), c = __ldcg(q + 2 * kSegCap + i),
+              d = __ldcg(q + 3 * kSegCap + i), e = __ldcg(q + 4 * kSegCap + i);
+  r.pos[0] = __uint_as_float(a.x); r.pos[1] = __uint_as_float(a.y); r.pos[2] = __uint_as_float(a.z);
+  r.u[0] = __uint_as_float(a.w); r.u[1] = __uint_as_float(b.x); r.u[2] = __uint_as_float(b.y);
+  r.l = __uint_as_float(b.z);
+  r.t0 = __uint_as_float(b.w);
+  r.s = __uint_as_float(c.x);
+  r.w = __longlong_as_double((long long)(((unsigned long long)c.w << 32) | c.z));
+  r.idx[0] = (int)d.x; r.idx[1] = (int)d.y; r.idx[2] = (int)d.z;
+  r.it = (int)(d.w & 0x1FFFFu) - 1;
+  r.g = (int)((d.w >> 17) & 0x1Fu);
+  r.ti = (int)((d.w >> 22) & 3u);
+  r.resumed = ((d.w >> 24) & 1u) != 0u;
+  r.batch = e.x;
+}
+
+// the segment a particle is about to fly, for the first tally
+__device__ __forceinline__ void seg_push_flight(uint4* q, unsigned i, const Part<float>& p, float l) {
+  SegRec r;
+  r.pos[0] = p.x; r.pos[1] = p.y; r.pos[2] = p.z;
+  r.u[0] = p.ux; r.u[1] = p.uy; r.u[2] = p.uz;
+  r.l = l;
+  r.t0 = p.time();
+  r.s = 0.0f;
+  r.w = p.w;
+  r.idx[0] = r.idx[1] = r.idx[2] = 0;
+  r.it = 0;
+  r.g = (int)pk_g(p.pk);
+  r.ti = 0;
+  r.resumed = false;
+  r.batch = p.elem >> 16;
+  seg_store(q, i, r);
+}
+
+// Scores waiting segments, 32 at a time while 32 wait (or, with `all`, until none is left).
+// stripe_off: the CTA's tally stripe.  All 32 lanes call it.
+__device__ __forceinline__ void score_segments(const Tab<float>& T, const RunParams& P, uint4* q, unsigned& ns,
+                                               bool all, uint64_t stripe_off, const Stage& S, unsigned& pieces) {
+  constexpr unsigned kAll = 0xFFFFFFFFu;
+  const unsigned lane = threadIdx.x & 31u;
+  const char* base = reinterpret_cast<const char*>(T.h);
+  const int n_tally = T.h->n_tally;
+  while (ns >= 32u || (all && ns > 0u)) {
+    const unsigned k = ns < 32u ? ns : 32u;
+    const bool have = lane < k;
+    SegRec r;
+    if (have) seg_load(q, ns - k + lane, r);
+    else {
+      r.ti = 0;
+      r.g = 0;
+      r.w = 0.0;
+      r.batch = 0u;
+      r.t0 = r.l = r.s = 0.0f;
+      for (int d = 0; d < 3; ++d) {
+        r.pos[d] = 0.0f;
+        r.u[d] = 0.0f;
+        r.idx[d] = 0;
+      }
+      r.it = 0;
+      r.resumed = true;
+    }
+    __syncwarp();
+    ns -= k;
+    const TallyDesc& D = T.h->tally[r.ti];
+    const float* e[3] = {reinterpret_cast<const float*>(base + D.o_ex), reinterpret_cast<const float*>(base + D.o_ey),
+                         reinterpret_cast<const float*>(base + D.o_ez)};
+    const float* et = time_edges<float>(base, D);
+    const int n[3] = {D.nx, D.ny, D.nz};
+    const int nt = D.nt;
+    const float v = T.v[r.g];
+    const uint32_t gbase = (uint32_t)(stripe_off + (uint64_t)r.batch * P.row + (uint64_t)D.bin_offset + (uint64_t)r.g * nt);
+    const int gstride = T.G * nt;
+    float inv[3], sn[3], stn = rinf<float>();
+    int step[3];
+    bool live = have;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      inv[d] = rdiv(1.0f, r.u[d]);
+      step[d] = r.u[d] > 0.0f ? 1 : (r.u[d] < 0.0f ? -1 : 0);
+    }
+    if (live && !r.resumed) {
+      // a new walk: the cells and time bin of the segment's start (as score_segment_warp finds them)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int i = bin_search(e[d], n[d], r.pos[d]);
+        r.idx[d] = i;
+        if (step[d] > 0) {
+          if (i >= n[d]) live = false;
+          sn[d] = (i >= n[d]) ? rinf<float>() : (e[d][i + 1] - r.pos[d]) * inv[d];
+        } else if (step[d] < 0) {
+          if (i < 0) live = false;
+          sn[d] = (i < 0) ? rinf<float>() : (e[d][i] - r.pos[d]) * inv[d];
+        } else {
+          sn[d] = rinf<float>();
+          if (i < 0 || i >= n[d]) live = false;
+        }
+      }
+      r.it = bin_search(et, nt, r.t0);
+      if (r.it >= nt) live = false;
+      else stn = (et[r.it + 1] - r.t0) * v;
+    } else if (live) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        sn[d] = step[d] > 0 ? (e[d][r.idx[d] + 1] - r.pos[d]) * inv[d]
+                            : (step[d] < 0 ? (e[d][r.idx[d]] - r.pos[d]) * inv[d] : rinf<float>());
+      stn = (et[r.it + 1] - r.t0) * v;
+    }
+    ScoreSink<float> sink(P, S, pieces, r.w);
+    for (unsigned rounds = 0; rounds < kSegRounds && __any_sync(kAll, live); ++rounds) {
+      bool emit = false;
+      uint32_t slot = 0;
+      float len = 0.0f;
+      if (live) {
+        const float nxt = fmin(fmin(fmin(sn[0], sn[1]), fmin(sn[2], stn)), r.l);
+        emit = nxt > r.s && r.idx[0] >= 0 && r.idx[0] < n[0] && r.idx[1] >= 0 && r.idx[1] < n[1] && r.idx[2] >= 0 &&
+               r.idx[2] < n[2] && r.it >= 0;
+        slot = gbase + (uint32_t)(((r.idx[2] * n[1] + r.idx[1]) * n[0] + r.idx[0]) * gstride + r.it);
+        len = nxt - r.s;
+        bool alive = nxt < r.l;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const bool st = sn[d] <= nxt;
+          const int ni = r.idx[d] + (st ? step[d] : 0);
+          const int ei = min(max(ni + (step[d] > 0 ? 1 : 0), 0), n[d]);
+          const float nsn = (e[d][ei] - r.pos[d]) * inv[d];
+          alive = alive && !(st && (ni < 0 || ni >= n[d]));
+          r.idx[d] = ni;
+          sn[d] = st ? nsn : sn[d];
+        }
+        {
+          const bool st = stn <= nxt;
+          const int ni = r.it + (st ? 1 : 0);
+          const float nstn = (et[min(ni + 1, nt)] - r.t0) * v;
+          alive = alive && ni < nt;
+          r.it = ni;
+          stn = st ? nstn : stn;
+        }
+        live = alive;
+        r.s = nxt;
+      }
+      sink.add(emit, slot, len);
+    }
+    sink.flush();
+    // back to the region: the rest of a live walk, or the segment again for the next tally
+    const bool next_tally = have && !live && r.ti + 1 < n_tally;
+    const bool put = live || next_tally;
+    if (next_tally) {
+      r.ti += 1;
+      r.resumed = false;
+      r.s = 0.0f;
+    } else {
+      r.resumed = true;
+    }
+    const unsigned m = __ballot_sync(kAll, put);
+    if (put) seg_store(q, ns + __popc(m & lanemask_lt()), r);
+    ns += __popc(m);
+  }
+}
+
 // Track-length estimator over the segment of length l from the particle's position: score
 // w * piece length into every (mesh cell, time bin) the segment passes through.  Crossing
 // distances are measured from the segment start, so rounding does not accumulate along the walk.

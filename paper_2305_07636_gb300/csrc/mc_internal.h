@@ -16,6 +16,11 @@ constexpr int kLanesFP64 = 6;     // 96 B per particle
 // (8-byte value + 4-byte slot each)
 constexpr unsigned kWarpQ = 64;
 constexpr unsigned kStage = 128;
+// segments waiting to be scored: records per warp (31 waiting + 32 new from one flight round; a
+// scoring pass puts back at most as many as it took) of kSegLanes 16-byte lanes, in a per-warp
+// region of device memory
+constexpr unsigned kSegCap = 64;
+constexpr int kSegLanes = 5;
 constexpr uint32_t kSourceEvent = 0xFFFFFFFFu;
 constexpr uint32_t kChildMark = 0x80000000u;
 constexpr uint32_t kSplitMark = 0xC0000000u;
@@ -199,6 +204,9 @@ struct RunParams {
   const uint4* src_site;   // [N] sites of this cycle's sources (cycle >= 1)
   uint4* site_next;        // [N * nmax] sites banked this cycle
   uint32_t* count_next;    // [N] sites banked by each history (zeroed before the cycle)
+  // FP32 tracking, plain-walk tallies only: per-warp regions of segments waiting to be scored
+  // (warp w of the grid at seg + w * kSegLanes * kSegCap); nullptr: every flight is scored at once
+  uint4* seg;
 };
 
 // fission sites: FP32 tracking 1 x 16 B (x, y, z, g), FP64 2 x 16 B ((x, y), (z, g))

@@ -369,46 +369,111 @@ __global__ void k_loss_grad(const Weights* Wg, const float* x, const float* tgt,
   for (int i = threadIdx.x; i < NPARAM; i += blockDim.x) atomicAdd(grad + i, gsm[i]);
 }
 
-// Full-batch Adam on one CTA: every epoch computes the gradient of the whole set on the tensor
-// cores, updates the FP32 masters and refreshes the BF16 copies in shared memory.
+// Grid barrier of the training kernel (a cooperative launch, every CTA resident): the wait is
+// bounded; on expiry the CTA records an error, and every CTA leaves the epoch loop at its next
+// barrier, so that a stuck barrier ends the kernel instead of hanging it.
+struct TrainSync {
+  unsigned int count, gen;
+  int err, pad;
+  float loss[2];  // loss of the even / odd epochs
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ bool train_grid_sync(TrainSync* s) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned gen = ld_acquire_u32(&s->gen);
+    __threadfence();
+    if (atomicAdd(&s->count, 1u) == gridDim.x - 1) {
+      atomicExch(&s->count, 0u);
+      __threadfence();
+      atomicAdd(&s->gen, 1u);
+    } else {
+      unsigned long long polls = 0;
+      while (ld_acquire_u32(&s->gen) == gen) {
+        if (*(volatile int*)&s->err) break;
+        if (++polls > (1ull << 26)) {
+          atomicExch(&s->err, 1);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    s_ok = *(volatile int*)&s->err == 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// the BF16 weights from global memory through L2 (other CTAs rewrite them between epochs)
+__device__ __forceinline__ void load_weights_cg(Weights& dst, const Weights* src) {
+  const uint4* s = reinterpret_cast<const uint4*>(src);
+  uint4* d = reinterpret_cast<uint4*>(&dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(Weights) / 16); i += blockDim.x) d[i] = __ldcg(s + i);
+  __syncthreads();
+}
+
+// Full-batch Adam over a grid of CTAs (one cooperative launch for all epochs).  Every epoch each
+// warp of the grid computes the loss gradient of its 16-sample tiles on the tensor cores into its
+// CTA's shared gradient; the CTAs add theirs into the epoch's global gradient; after a grid
+// barrier each CTA updates its share of the FP32 masters with Adam and writes their BF16 copies;
+// after a second barrier every CTA reloads the BF16 weights.  The gradients of even and odd epochs
+// alternate between two buffers, each zeroed an epoch ahead, so two barriers per epoch suffice.
 __global__ void k_train(float* master, float* m1, float* m2, Weights* Wg, const float* x, const float* tgt,
-                        const float* wt, int n, int epochs, float lr, long long step0, float* last_loss) {
+                        const float* wt, int n, int epochs, float lr, long long step0, float* last_loss, float* gbuf,
+                        TrainSync* sync) {
   extern __shared__ __align__(16) unsigned char sm[];
   Weights& W = *reinterpret_cast<Weights*>(sm);
   float* gsm = reinterpret_cast<float*>(sm + ((sizeof(Weights) + 15) / 16) * 16);
   Stage* st = reinterpret_cast<Stage*>(reinterpret_cast<unsigned char*>(gsm) + ((NPARAM * 4 + 15) / 16) * 16);
-  __shared__ float s_loss;
-  load_weights(W, Wg);
-  const int warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+  load_weights_cg(W, Wg);
+  const int warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int gw = blockIdx.x * wpb + warp, nw = gridDim.x * wpb;
+  const int chunk = (NPARAM + gridDim.x - 1) / gridDim.x;
+  const int p0 = blockIdx.x * chunk, p1 = p0 + chunk < NPARAM ? p0 + chunk : NPARAM;
   const float beta1 = 0.9f, beta2 = 0.999f, eps = 1e-8f;
-  for (int e = 0; e < epochs; ++e) {
+  bool ok = true;
+  int e = 0;
+  for (; e < epochs && ok; ++e) {
+    float* gcur = gbuf + (e & 1) * NPARAM;
+    float* gnext = gbuf + ((e + 1) & 1) * NPARAM;
     for (int i = threadIdx.x; i < NPARAM; i += blockDim.x) gsm[i] = 0.f;
-    if (threadIdx.x == 0) s_loss = 0.f;
     __syncthreads();
     float l = 0.f;
-    for (int tile = warp; tile * 16 < n; tile += warps)
+    for (int tile = gw; tile * 16 < n; tile += nw)
       tile_loss_grad(W, st[warp], x, tgt, wt, n, tile * 16, 1.f / (float)n, gsm, &l);
     for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xFFFFFFFFu, l, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&s_loss, l);
+    if ((threadIdx.x & 31) == 0 && l != 0.f) atomicAdd(&sync->loss[e & 1], l);
     __syncthreads();
+    for (int i = threadIdx.x; i < NPARAM; i += blockDim.x)
+      if (gsm[i] != 0.f) atomicAdd(gcur + i, gsm[i]);
+    if (!(ok = train_grid_sync(sync))) break;
     const float step = (float)(step0 + e + 1);
     const float c1 = 1.f - powf(beta1, step), c2 = 1.f - powf(beta2, step);
-    for (int i = threadIdx.x; i < NPARAM; i += blockDim.x) {
-      const float gr = gsm[i];
+    for (int i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
+      const float gr = __ldcg(gcur + i);
       const float a = beta1 * m1[i] + (1.f - beta1) * gr;
       const float b = beta2 * m2[i] + (1.f - beta2) * gr * gr;
       m1[i] = a;
       m2[i] = b;
       const float p = master[i] - lr * (a / c1) / (sqrtf(b / c2) + eps);
       master[i] = p;
-      scatter_param(W, i, p);
+      scatter_param(*Wg, i, p);
+      gnext[i] = 0.f;
     }
-    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) sync->loss[(e + 1) & 1] = 0.f;
+    if (!(ok = train_grid_sync(sync))) break;
+    load_weights_cg(W, Wg);
   }
-  if (threadIdx.x == 0 && last_loss) *last_loss = s_loss;
-  const uint4* s = reinterpret_cast<const uint4*>(&W);
-  uint4* d = reinterpret_cast<uint4*>(Wg);
-  for (int i = threadIdx.x; i < (int)(sizeof(Weights) / 16); i += blockDim.x) d[i] = s[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0 && last_loss)
+    *last_loss = epochs == 0 ? 0.f : (ok ? *(volatile float*)&sync->loss[(epochs - 1) & 1] : __int_as_float(0x7FC00000));
 }
 
 // window centres from the network: centre[i] = ref * exp(scale * y[i]), y clamped to [ymin, ymax]
@@ -456,13 +521,31 @@ cudaError_t mlp_loss_grad(const void* Wg, const float* x, const float* tgt, cons
   return cudaGetLastError();
 }
 
+size_t mlp_train_scratch_bytes() { return 2 * mlp::NPARAM * 4 + sizeof(mlp::TrainSync); }
+
 cudaError_t mlp_train(float* master, float* m1, float* m2, void* Wg, const float* x, const float* tgt, const float* wt,
-                      int n, int epochs, float lr, long long step0, float* last_loss, cudaStream_t s) {
+                      int n, int epochs, float lr, long long step0, float* last_loss, void* scratch, cudaStream_t s) {
   const size_t smem = mlp::grad_smem(8);
   cudaError_t e = cudaFuncSetAttribute(mlp::k_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  mlp::k_train<<<1, 256, smem, s>>>(master, m1, m2, reinterpret_cast<mlp::Weights*>(Wg), x, tgt, wt, n, epochs, lr,
-                                    step0, last_loss);
+  // one warp per 16-sample tile where the SMs allow (one CTA of 8 warps per SM), cooperative
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp::k_train, 256, smem)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int tiles = (n + 15) / 16;
+  int grid = (tiles + 7) / 8;
+  if (grid > sms * per_sm) grid = sms * per_sm;
+  if (grid < 1) grid = 1;
+  float* gbuf = reinterpret_cast<float*>(scratch);
+  mlp::TrainSync* sync = reinterpret_cast<mlp::TrainSync*>(gbuf + 2 * mlp::NPARAM);
+  if ((e = cudaMemsetAsync(scratch, 0, mlp_train_scratch_bytes(), s)) != cudaSuccess) return e;
+  mlp::Weights* W = reinterpret_cast<mlp::Weights*>(Wg);
+  void* args[] = {&master, &m1, &m2, &W, const_cast<float**>(&x), const_cast<float**>(&tgt), const_cast<float**>(&wt),
+                  &n, &epochs, &lr, &step0, &last_loss, &gbuf, &sync};
+  e = cudaLaunchCooperativeKernel((const void*)mlp::k_train, grid, 256, args, smem, s);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -38,7 +38,7 @@ constexpr unsigned kClaim = MCGB_CLAIM, kClaimTail = MCGB_CLAIM_TAIL, kTailWaves
 
 // dynamic shared memory: [table blob][per-warp flight queues: warps x Lanes<R>::N x kWarpQ]
 // [per-warp tally staging: warps x kStage x 12 B]
-template <typename R, int MINB, bool RANGE>
+template <typename R, int MINB, bool RANGE, bool SEG>
 __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
   extern __shared__ __align__(16) char smem[];
   __shared__ BlockCounters bc;
@@ -55,6 +55,9 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
   char* stage_base = smem + P.blob_bytes + (size_t)nwarp * Lanes<R>::N * kWarpQ * 16;
   const Stage stage{reinterpret_cast<uint32_t*>(stage_base + (size_t)nwarp * kStage * 8) + warp * kStage,
                     reinterpret_cast<unsigned long long*>(stage_base) + warp * kStage};
+  // SEG: the warp's region of segments waiting to be scored, ns of them (warp-uniform)
+  uint4* const sq = SEG ? P.seg + ((size_t)blockIdx.x * nwarp + warp) * (kSegLanes * kSegCap) : nullptr;
+  unsigned ns = 0;
   Ctl* ctl = P.ctl;
   const unsigned lt = lanemask_lt();
   unsigned scored = 0;  // tally updates issued by this warp
@@ -173,6 +176,11 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
         qn += __popc(m);
         __syncwarp();
       }
+      if constexpr (SEG) {
+        // a full warp of segments whenever 32 wait, and all of them when the warp's work in this
+        // iteration is done
+        if (ns >= 32u || (qn == 0u && ns > 0u)) score_segments(T, P, sq, ns, qn == 0u, stripe_off, stage, scored);
+      }
       if (qn == 0u) break;  // the warp's items are exhausted and nothing is left to fly
       const unsigned nfly = qn < 32u ? qn : 32u;
       Part<R> p;
@@ -197,8 +205,15 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
       if (lane == 0 && (mF | mS))
         bFS = atomicAdd(&ctl->fb[nxt], (unsigned long long)__popc(mF) | ((unsigned long long)__popc(mS) << 32));
       if (P.eigen && flies) ktl += eigen_tl_fixed(T, p, l);
-      score_segment_warp<R, RANGE>(T, P, p, l, stripe_off + (uint64_t)(p.elem >> 16) * row,
-                                   flies && (!P.eigen || P.eigen_score), stage, scored);
+      if constexpr (SEG) {
+        const bool sc = flies && (!P.eigen || P.eigen_score);
+        const unsigned msc = __ballot_sync(0xFFFFFFFFu, sc);
+        if (sc) seg_push_flight(sq, ns + __popc(msc & lt), p, l);
+        ns += __popc(msc);
+      } else {
+        score_segment_warp<R, RANGE>(T, P, p, l, stripe_off + (uint64_t)(p.elem >> 16) * row,
+                                     flies && (!P.eigen || P.eigen_score), stage, scored);
+      }
       if (flies) {
         bool alive = flight_finish(P, T, p, &bc, l, pend, hit);
         if (alive && p.k + 1 >= P.max_iter) {
@@ -555,22 +570,26 @@ __global__ void k_philox(uint64_t seed, const uint4* ctr, uint4* out, uint64_t n
 // (128 registers, no spills); `wide` selects the second.  `range` selects the build with the range
 // walk of the scoring (tallies whose time axis is much finer than their mesh).
 template <typename R>
-static const void* transport_fn(bool wide, bool range) {
-  if constexpr (sizeof(R) == 8) return range ? (const void*)k_transport<R, 2, true> : (const void*)k_transport<R, 2, false>;
-  else if (range) return wide ? (const void*)k_transport<R, 2, true> : (const void*)k_transport<R, 3, true>;
-  else return wide ? (const void*)k_transport<R, 2, false> : (const void*)k_transport<R, 3, false>;
+static const void* transport_fn(bool wide, bool range, bool seg) {
+  if constexpr (sizeof(R) == 8) {
+    return range ? (const void*)k_transport<R, 2, true, false> : (const void*)k_transport<R, 2, false, false>;
+  } else {
+    if (seg) return wide ? (const void*)k_transport<R, 2, false, true> : (const void*)k_transport<R, 3, false, true>;
+    if (range) return wide ? (const void*)k_transport<R, 2, true, false> : (const void*)k_transport<R, 3, true, false>;
+    return wide ? (const void*)k_transport<R, 2, false, false> : (const void*)k_transport<R, 3, false, false>;
+  }
 }
 
 template <typename R>
 cudaError_t launch_transport(const RunParams& P, int grid, int block, size_t smem, cudaStream_t s, bool wide,
                              bool range) {
   void* args[] = {const_cast<RunParams*>(&P)};
-  return cudaLaunchCooperativeKernel(transport_fn<R>(wide, range), grid, block, args, smem, s);
+  return cudaLaunchCooperativeKernel(transport_fn<R>(wide, range, P.seg != nullptr), grid, block, args, smem, s);
 }
 
 template <typename R>
-cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide, bool range) {
-  const void* f = transport_fn<R>(wide, range);
+cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide, bool range, bool seg) {
+  const void* f = transport_fn<R>(wide, range, seg);
   // opt in for the exact size: the default limit (48 KB less the kernel's static shared memory)
   // can be exceeded by a dynamic size just under 48 KB
   {
@@ -582,8 +601,8 @@ cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide, 
 
 template cudaError_t launch_transport<float>(const RunParams&, int, int, size_t, cudaStream_t, bool, bool);
 template cudaError_t launch_transport<double>(const RunParams&, int, int, size_t, cudaStream_t, bool, bool);
-template cudaError_t transport_occupancy<float>(int, size_t, int*, bool, bool);
-template cudaError_t transport_occupancy<double>(int, size_t, int*, bool, bool);
+template cudaError_t transport_occupancy<float>(int, size_t, int*, bool, bool, bool);
+template cudaError_t transport_occupancy<double>(int, size_t, int*, bool, bool, bool);
 
 cudaError_t launch_reconstruct(void* tally, const char* blob64, uint64_t rows, uint64_t row, int nb, int stripes,
                                int fp64, cudaStream_t s) {

@@ -250,6 +250,28 @@ def test_gpu_azurv1_population(torch):
     p.close()
 
 
+@pytest.mark.parametrize("speed", [2e9, 2e3])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_census_population_closed_form(torch, speed, precision):
+    """The census decision of the walk (FP32 tracking keeps time as a float-float pair, FP64 as a
+    double): a one-group infinite medium (Sigma_t = 1, Sigma_a = 0.5) pulsed at t = 0 keeps the
+    fraction exp(-v Sigma_a t_c) of its particles alive at the census t_c (no production, analog);
+    with v Sigma_a t_c = 1.5 at particle speeds of 2e9 and 2e3 cm/s (census at 1.5e-9 s and 1.5e-3
+    s), the census count agrees with exp(-1.5) within 4 binomial sigma, and every particle ends
+    exactly once."""
+    t_c = 1.5 / (speed * 0.5)
+    prob = P.infinite_medium_1g(sigma_t=1.0, sigma_s=0.5, speed=speed, t_census=t_c)
+    n = 4_000_000 if precision == "fp32" else 400_000
+    p = mc.Problem(prob)
+    p.run(n, 29, precision=precision)
+    c = p.counters()
+    assert conserved(c)
+    frac, exact = c["census"] / n, math.exp(-1.5)
+    sig = math.sqrt(exact * (1 - exact) / n)
+    assert abs(frac - exact) < 4 * sig, (frac, exact, sig)
+    p.close()
+
+
 # ----------------------------------------------------------------------------- errors
 
 
