@@ -83,10 +83,13 @@ __device__ __forceinline__ void warp_copy16(void* dst, const void* src, size_t b
   for (size_t i = lane; i < bytes / 16; i += 32) d[i] = __ldg(s + i);
 }
 
-template <typename R, int MINB, bool RANGE>
+// SEG (FP32, plain-walk tallies only): flown segments are scored apart from their flights, 32 at a
+// time, from the warp's segment region in `segs` (score_segments); the region is emptied before
+// the warp turns to another problem, whose tables and tallies its records do not address.
+template <typename R, int MINB, bool RANGE, bool SEG>
 __global__ void __launch_bounds__(256, MINB)
     k_transport_batch(BatchHeader* bh, const BatchItem* items, unsigned long long* t_done, uint4* stacks,
-                      int slot_bytes) {
+                      int slot_bytes, uint4* segs) {
   extern __shared__ __align__(16) char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   char* wbase = smem + (size_t)warp * batch_warp_bytes<R>((size_t)slot_bytes);
@@ -99,6 +102,8 @@ __global__ void __launch_bounds__(256, MINB)
   unsigned long long* sc = reinterpret_cast<unsigned long long*>(st + kStage * 12 + sizeof(BlockCounters));
   const unsigned lt = lanemask_lt();
   const uint64_t gw = (uint64_t)blockIdx.x * nwarp + warp, nwt = (uint64_t)gridDim.x * nwarp;
+  uint4* const sq = SEG ? segs + gw * (kSegLanes * kSegCap) : nullptr;
+  unsigned ns = 0;
   const uint64_t cap = bh->stack_cap;
   const unsigned long long n_units = bh->n_units;
   const uint64_t unit = bh->unit;
@@ -195,6 +200,9 @@ __global__ void __launch_bounds__(256, MINB)
         qn += __popc(m);
       }
       __syncwarp();
+      if constexpr (SEG) {
+        if (ns >= 32u || (qn == 0u && ns > 0u)) score_segments(T, P, sq, ns, qn == 0u, 0, stage, scored);
+      }
       if (qn == 0u) break;
       // (B) fly up to 32 queued particles; survivors handle their next event and queue again
       const unsigned nfly = qn < 32u ? qn : 32u;
@@ -208,7 +216,13 @@ __global__ void __launch_bounds__(256, MINB)
       uint32_t pend = PEND_NONE;
       Hit hit;
       const bool flies = have && flight_plan(P, T, p, bc, l, pend, hit);
-      score_segment_warp<R, RANGE>(T, P, p, l, (uint64_t)(p.elem >> 16) * row, flies, stage, scored);
+      if constexpr (SEG) {
+        const unsigned msc = __ballot_sync(0xFFFFFFFFu, flies);
+        if (flies) seg_push_flight(sq, ns + __popc(msc & lt), p, l);
+        ns += __popc(msc);
+      } else {
+        score_segment_warp<R, RANGE>(T, P, p, l, (uint64_t)(p.elem >> 16) * row, flies, stage, scored);
+      }
       if (flies) {
         bool alive = flight_finish(P, T, p, bc, l, pend, hit);
         if (alive && p.k + 1 >= P.max_iter) {
@@ -297,13 +311,16 @@ __global__ void k_batch_stats_multi(const BatchHeader* bh, const BatchItem* item
 // the two register budgets of the batched kernel (FP64 tracking has only the wide one), each with
 // and without the range walk of the scoring
 template <typename R>
-static const void* batch_fn(bool wide, bool range) {
-  if constexpr (sizeof(R) == 8)
-    return range ? (const void*)k_transport_batch<R, 2, true> : (const void*)k_transport_batch<R, 2, false>;
-  else if (range)
-    return wide ? (const void*)k_transport_batch<R, 2, true> : (const void*)k_transport_batch<R, 3, true>;
-  else
-    return wide ? (const void*)k_transport_batch<R, 2, false> : (const void*)k_transport_batch<R, 3, false>;
+static const void* batch_fn(bool wide, bool range, bool seg) {
+  if constexpr (sizeof(R) == 8) {
+    return range ? (const void*)k_transport_batch<R, 2, true, false> : (const void*)k_transport_batch<R, 2, false, false>;
+  } else {
+    if (seg)
+      return wide ? (const void*)k_transport_batch<R, 2, false, true> : (const void*)k_transport_batch<R, 3, false, true>;
+    if (range)
+      return wide ? (const void*)k_transport_batch<R, 2, true, false> : (const void*)k_transport_batch<R, 3, true, false>;
+    return wide ? (const void*)k_transport_batch<R, 2, false, false> : (const void*)k_transport_batch<R, 3, false, false>;
+  }
 }
 
 }  // namespace mcgb
@@ -320,10 +337,10 @@ struct BatchConfig {
 // list and header (uploaded by every call from pinned staging), per-problem completion times,
 // and the warp stacks.
 struct BatchPlan {
-  int dev = 0, n = 0, block = 0, wide = 0, fp64 = 0, range = 0, grid = 0;
+  int dev = 0, n = 0, block = 0, wide = 0, fp64 = 0, range = 0, seg = 0, grid = 0;
   size_t slot_bytes = 0, smem = 0;
   uint64_t stack_cap = 0;
-  DevBuf d_items, d_head, d_tdone, d_stacks;
+  DevBuf d_items, d_head, d_tdone, d_stacks, d_segs;
   BatchItem* h_items = nullptr;
   BatchHeader* h_head = nullptr;
   unsigned long long* h_tdone = nullptr;
@@ -344,6 +361,7 @@ struct BatchPlan {
     d_head.release();
     d_tdone.release();
     d_stacks.release();
+    d_segs.release();
   }
 };
 
@@ -355,8 +373,8 @@ constexpr size_t kMaxPlans = 4;
 constexpr uint64_t kDefaultStack = 2048;
 
 template <typename R>
-cudaError_t batch_occupancy(int block, size_t smem, bool wide, bool range, int* per_sm) {
-  const void* f = batch_fn<R>(wide, range);
+cudaError_t batch_occupancy(int block, size_t smem, bool wide, bool range, bool seg, int* per_sm) {
+  const void* f = batch_fn<R>(wide, range, seg);
   // opt in for the exact size: the default limit (48 KB less the kernel's static shared memory)
   // can be exceeded by a dynamic size just under 48 KB
   {
@@ -373,9 +391,11 @@ int capture(BatchPlan* pl) {
   const BatchItem* items = (const BatchItem*)pl->d_items.ptr;
   unsigned long long* tdone = (unsigned long long*)pl->d_tdone.ptr;
   uint4* stacks = (uint4*)pl->d_stacks.ptr;
+  uint4* segs = (uint4*)pl->d_segs.ptr;
   int slot = (int)pl->slot_bytes;
-  const void* f = pl->fp64 ? batch_fn<double>(pl->wide, pl->range) : batch_fn<float>(pl->wide, pl->range);
-  void* args[] = {&bh, &items, &tdone, &stacks, &slot};
+  const void* f = pl->fp64 ? batch_fn<double>(pl->wide, pl->range, false)
+                           : batch_fn<float>(pl->wide, pl->range, pl->seg != 0);
+  void* args[] = {&bh, &items, &tdone, &stacks, &slot, &segs};
   CK(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
   k_batch_clear<<<dim3((unsigned)pl->n, 16), 256, 0, pl->cap_stream>>>(bh, items, tdone);
   cudaError_t e = cudaGetLastError();
@@ -403,11 +423,11 @@ int capture(BatchPlan* pl) {
 
 // The plan of a launch shape, created (and its graph captured) on first use.  Caller holds
 // g_batch_mu.
-int get_plan(int dev, int n, const BatchConfig& c, int fp64, int range, size_t slot, uint64_t stack_cap,
+int get_plan(int dev, int n, const BatchConfig& c, int fp64, int range, int seg, size_t slot, uint64_t stack_cap,
              BatchPlan** out) {
   for (auto& pl : g_plans)
     if (pl->dev == dev && pl->n == n && pl->block == c.block && pl->wide == c.wide && pl->fp64 == fp64 &&
-        pl->range == range && pl->slot_bytes == slot && pl->stack_cap == stack_cap) {
+        pl->range == range && pl->seg == seg && pl->slot_bytes == slot && pl->stack_cap == stack_cap) {
       pl->last_use = ++g_plan_clock;
       *out = pl.get();
       return MC_OK;
@@ -428,6 +448,7 @@ int get_plan(int dev, int n, const BatchConfig& c, int fp64, int range, size_t s
   pl->wide = c.wide;
   pl->fp64 = fp64;
   pl->range = range;
+  pl->seg = seg;
   pl->slot_bytes = slot;
   pl->stack_cap = stack_cap;
   const size_t wb = fp64 ? batch_warp_bytes<double>(slot) : batch_warp_bytes<float>(slot);
@@ -435,8 +456,8 @@ int get_plan(int dev, int n, const BatchConfig& c, int fp64, int range, size_t s
   int rc0 = check_shared_memory(dev, pl->smem, "the batched kernel");
   if (rc0 != MC_OK) return rc0;
   int per_sm = 0;
-  CK(fp64 ? batch_occupancy<double>(c.block, pl->smem, c.wide, range, &per_sm)
-          : batch_occupancy<float>(c.block, pl->smem, c.wide, range, &per_sm));
+  CK(fp64 ? batch_occupancy<double>(c.block, pl->smem, c.wide, range, false, &per_sm)
+          : batch_occupancy<float>(c.block, pl->smem, c.wide, range, seg != 0, &per_sm));
   if (per_sm < 1)
     return fail(MC_ERR_INVALID, "batched kernel does not fit on an SM (block %d, %zu B shared memory)", c.block,
                 pl->smem);
@@ -446,6 +467,7 @@ int get_plan(int dev, int n, const BatchConfig& c, int fp64, int range, size_t s
   const int lanes = fp64 ? kLanesFP64 : kLanesFP32;
   const uint64_t warps = (uint64_t)pl->grid * (c.block / 32);
   int rc = pl->d_stacks.ensure((size_t)lanes * warps * stack_cap * 16, dev);
+  if (rc == MC_OK && seg) rc = pl->d_segs.ensure((size_t)warps * kSegLanes * kSegCap * 16, dev);
   if (rc == MC_OK) rc = pl->d_items.ensure((size_t)n * sizeof(BatchItem), dev);
   if (rc == MC_OK) rc = pl->d_head.ensure(sizeof(BatchHeader), dev);
   if (rc == MC_OK) rc = pl->d_tdone.ensure((size_t)n * 8, dev);
@@ -528,10 +550,13 @@ int mc_run_batch(mc_problem* const* ps, int n, const uint64_t* n_hist, uint64_t 
   }
   size_t slot = 0;
   int range = 0;  // some problem has a tally scored by the range walk
+  int seg = !fp64;  // every problem's tallies take the plain walk: segments scored apart (FP32)
   for (int i = 0; i < n; ++i) {
     mc_problem* p = ps[i];
     if (!p) return fail(MC_ERR_INVALID, "problem %d is NULL", i);
     range = range || p->range;
+    seg = seg && !p->range && p->n_tally <= 4;
+    for (const HostTally& t : p->tallies) seg = seg && t.est == MC_EST_TRACK_LENGTH;
     if (p->dev != dev) return fail(MC_ERR_STATE, "problem %d was created on device %d, current is %d", i, p->dev, dev);
     if (n_hist[i] < (uint64_t)nb) return fail(MC_ERR_INVALID, "problem %d: need at least n_batches histories", i);
     if (n_hist[i] >= (1ull << 32)) return fail(MC_ERR_INVALID, "problem %d: history indices must stay below 2^32", i);
@@ -573,7 +598,7 @@ int mc_run_batch(mc_problem* const* ps, int n, const uint64_t* n_hist, uint64_t 
 
   std::lock_guard<std::mutex> lk(g_batch_mu);
   BatchPlan* pl = nullptr;
-  rc = get_plan(dev, n, c, fp64, range, slot, stack_cap, &pl);
+  rc = get_plan(dev, n, c, fp64, range, seg, slot, stack_cap, &pl);
   if (rc != MC_OK) return rc;
   CK(cudaEventSynchronize(pl->uploaded));  // the staging buffers are free again
   uint64_t units = 0;
