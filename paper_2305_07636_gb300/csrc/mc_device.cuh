@@ -679,15 +679,23 @@ __device__ __forceinline__ V peer_reduce(unsigned mask, unsigned peers, V v, uns
   return v;
 }
 
+// tally adds whose old value nobody reads: reductions (no value comes back from L2)
+__device__ __forceinline__ void red_add(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.global.add.u64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "l"(v) : "memory");
+}
+__device__ __forceinline__ void red_add(double* p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "d"(v) : "memory");
+}
+
 __device__ __forceinline__ void add_fixed(unsigned long long* dst, long long v, bool aggregate) {
   if (aggregate) {
     const unsigned mask = __activemask();
     const unsigned peers = __match_any_sync(mask, (unsigned long long)dst);
     const unsigned depth = __reduce_max_sync(mask, (unsigned)__popc(peers));
     if (depth > 1) v = peer_reduce(mask, peers, v, depth);
-    if ((peers & lanemask_lt()) == 0u) atomicAdd(dst, (unsigned long long)v);
+    if ((peers & lanemask_lt()) == 0u) red_add(dst, (unsigned long long)v);
   } else {
-    atomicAdd(dst, (unsigned long long)v);
+    red_add(dst, (unsigned long long)v);
   }
 }
 
@@ -697,9 +705,9 @@ __device__ __forceinline__ void add_fp64(double* dst, double v, bool aggregate) 
     const unsigned peers = __match_any_sync(mask, (unsigned long long)dst);
     const unsigned depth = __reduce_max_sync(mask, (unsigned)__popc(peers));
     if (depth > 1) v = peer_reduce(mask, peers, v, depth);
-    if ((peers & lanemask_lt()) == 0u) atomicAdd(dst, v);
+    if ((peers & lanemask_lt()) == 0u) red_add(dst, v);
   } else {
-    atomicAdd(dst, v);
+    red_add(dst, v);
   }
 }
 
@@ -795,9 +803,9 @@ struct ScoreSink {
     if (!P.aggregate) {
       if (emit && in_range(P, slot, (uint64_t)P.tally_stripes * P.stripe_stride)) {
         if (P.tally_fp64)
-          atomicAdd(reinterpret_cast<double*>(P.tally) + slot, __longlong_as_double((long long)val));
+          red_add(reinterpret_cast<double*>(P.tally) + slot, __longlong_as_double((long long)val));
         else
-          atomicAdd(reinterpret_cast<unsigned long long*>(P.tally) + slot, val);
+          red_add(reinterpret_cast<unsigned long long*>(P.tally) + slot, val);
       }
       return;
     }
@@ -1053,9 +1061,9 @@ __device__ void score_segment_warp(const Tab<R>& T, const RunParams& P, const Pa
       pieces += __popc(m);
       if (emit && in_range(P, slot, (uint64_t)P.tally_stripes * P.stripe_stride)) {
         if (P.tally_fp64)
-          atomicAdd(reinterpret_cast<double*>(P.tally) + slot, __longlong_as_double((long long)val));
+          red_add(reinterpret_cast<double*>(P.tally) + slot, __longlong_as_double((long long)val));
         else
-          atomicAdd(reinterpret_cast<unsigned long long*>(P.tally) + slot, val);
+          red_add(reinterpret_cast<unsigned long long*>(P.tally) + slot, val);
       }
       return;
     }

@@ -468,13 +468,14 @@ template cudaError_t launch_pc<float>(const RunParams&, const RunParams&, const 
 template cudaError_t launch_pc<double>(const RunParams&, const RunParams&, const unsigned long long*, long long*,
                                        unsigned long long*, unsigned long long*, int*, bool, cudaStream_t);
 
-// L2 atomic throughput probe: 64-bit adds to pseudo-random slots of an array of `span` elements
-// (the access pattern of tally scoring), `iters` per thread.
+// L2 atomic throughput probe: 64-bit reductions (adds whose old value is not returned, as the
+// tally scoring issues them) to pseudo-random slots of an array of `span` elements, `iters` per
+// thread.
 __global__ void k_atomic_probe(unsigned long long* a, unsigned long long span, int iters, unsigned salt) {
   unsigned long long x = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) * 2654435761ull + salt;
   for (int i = 0; i < iters; ++i) {
     x = x * 6364136223846793005ull + 1442695040888963407ull;
-    atomicAdd(a + ((x >> 20) % span), 1ull);
+    red_add(a + ((x >> 20) % span), 1ull);
   }
 }
 
