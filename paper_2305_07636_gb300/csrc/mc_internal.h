@@ -20,7 +20,7 @@ constexpr unsigned kStage = 128;
 // scoring pass puts back at most as many as it took) of kSegLanes 16-byte lanes, in a per-warp
 // region of device memory
 constexpr unsigned kSegCap = 64;
-constexpr int kSegLanes = 5;
+constexpr int kSegLanes = 4;
 constexpr uint32_t kSourceEvent = 0xFFFFFFFFu;
 constexpr uint32_t kChildMark = 0x80000000u;
 constexpr uint32_t kSplitMark = 0xC0000000u;

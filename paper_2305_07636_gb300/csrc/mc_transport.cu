@@ -177,9 +177,9 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
         __syncwarp();
       }
       if constexpr (SEG) {
-        // a full warp of segments whenever 32 wait, and all of them when the warp's work in this
-        // iteration is done
-        if (ns >= 32u || (qn == 0u && ns > 0u)) score_segments(T, P, sq, ns, qn == 0u, stripe_off, stage, scored);
+        // a full warp of segments whenever 32 wait; fewer stay in the warp's region into the next
+        // iteration (a record holds all it needs), and the rest is scored when the run ends
+        if (ns >= 32u) score_segments(T, P, sq, ns, false, stripe_off, stage, scored);
       }
       if (qn == 0u) break;  // the warp's items are exhausted and nothing is left to fly
       const unsigned nfly = qn < 32u ? qn : 32u;
@@ -250,6 +250,9 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
       }
     }
     grid_barrier(P, ctl, P.spin_limit);
+  }
+  if constexpr (SEG) {
+    if (ns > 0u) score_segments(T, P, sq, ns, true, stripe_off, stage, scored);
   }
   if (P.eigen) {
     for (int o = 16; o > 0; o >>= 1) ktl += __shfl_xor_sync(0xFFFFFFFFu, ktl, o);
