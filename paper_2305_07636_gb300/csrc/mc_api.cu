@@ -661,6 +661,7 @@ void mc_problem_destroy(mc_problem* p) {
   p->d_sticky.release();
   p->d_ww.release();
   p->d_seg.release();
+  p->d_wstack.release();
   // k-eigenvalue and population-control buffers
   p->d_sites.release();
   p->d_counts.release();
@@ -898,6 +899,19 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
     rc = p->d_seg.ensure((size_t)grid * (block / 32) * kSegLanes * kSegCap * 16, p->dev);
     if (rc != MC_OK) return rc;
     P.seg = (uint4*)p->d_seg.ptr;
+    // split run: the history-style tail flies each warp's secondaries from its own stack of up to
+    // 256, carved out of the bank capacity (a bank too small for 32 per warp runs in one launch).
+    // Runs with weight windows stay one launch: a stack keeps a lineage on its warp, and lineages
+    // that split many times over would hold a few warps busy while the grid waits, where the
+    // one-launch tail spreads every generation of copies over all warps.
+    const uint64_t nwt = (uint64_t)grid * (uint64_t)(block / 32);
+    const uint64_t wcap = std::min<uint64_t>(256, cap / nwt);
+    if (o.n_census == 0 && !o.ww_enable && wcap >= 32) {
+      rc = p->d_wstack.ensure((size_t)lanes * nwt * wcap * 16, p->dev);
+      if (rc != MC_OK) return rc;
+      for (int l = 0; l < lanes; ++l) P.WS[l] = (uint4*)p->d_wstack.ptr + (size_t)l * nwt * wcap;
+      P.ws_cap = wcap;
+    }
   }
   CK(cudaEventRecord(p->ev[0], s));
   if (o.n_census == 0) {

@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(256, MINB)
   if (lane == 0) {
     *sc = 0ull;
     bc->split_ctr = nullptr;
+    bc->local = 0u;
     bc->hold_at = cap / 2;  // weight-window splits are held while the warp's stack is half full
   }
 

@@ -85,18 +85,30 @@ __device__ void log_event(const RunParams& P, const Tab<R>& T, const Part<R>& p,
 // per-CTA (per-warp in the batched kernel) event counters and the weight-window split limit: with
 // a split counter (the persistent kernel: the iteration's count of split copies) hold_at is the
 // iteration's budget of copies (half the birth store, less the births that wait to be stored
-// again); without one, the fill of the warp's stack above which splits wait
+// again); without one, the fill of the warp's stack above which splits wait (the batched kernel)
 struct __align__(16) BlockCounters {
   unsigned int c[MC_NCOUNTERS];
   unsigned long long* split_ctr;
   unsigned long long hold_at;
+  // the tail launch of a split run: births go to the warp's own stack first (wn[w]: its fill,
+  // which runs past P.ws_cap when the stack overflowed into the birth bank)
+  unsigned int local;
+  unsigned int wn[8];
 };
 __device__ __forceinline__ void bump(BlockCounters* bc, int i, unsigned v = 1u) { atomicAdd(&bc->c[i], v); }
 
 // ------------------------------------------------------------------------------------------ births
 template <typename R>
 __device__ __forceinline__ void append_birth(const RunParams& P, uint4* const* Bout, unsigned long long* counter,
-                                             const Part<R>& c) {
+                                             BlockCounters* bc, const Part<R>& c) {
+  if (bc->local) {
+    const unsigned w = threadIdx.x >> 5;
+    const unsigned j = atomicAdd(&bc->wn[w], 1u);
+    if (j < P.ws_cap) {
+      bank_store(c, P.WS, ((uint64_t)blockIdx.x * (blockDim.x >> 5) + w) * P.ws_cap + j);
+      return;
+    }
+  }
   const unsigned long long i = atomicAdd(counter, 1ull);
   if (i >= P.cap_b) {
     set_status(P, MC_ERR_BANK_FULL);
@@ -136,7 +148,8 @@ __device__ bool weight_window(const RunParams& P, const Tab<R>& T, Part<R>& p, u
     // atomic add; an attempt that would pass the budget holds, and since its count is not taken
     // back the counter only errs towards holding), so that particles splitting at the same moment
     // cannot overshoot the budget together; in a warp's private stack the stack's fill is compared
-    // with the limit.
+    // with the limit.  (Runs with windows are never split, so no copy goes to a tail launch's
+    // stack of secondaries.)
     const unsigned long long need = (unsigned long long)(n - 1);
     if (bc->split_ctr != nullptr) {
       if (atomicAdd(bc->split_ctr, need) + need > bc->hold_at) {
@@ -155,7 +168,7 @@ __device__ bool weight_window(const RunParams& P, const Tab<R>& T, Part<R>& p, u
       c.thi = t.y;
       c.k = 0;
       c.pk = pk_set_pending(c.pk, PEND_NONE, 0, 1, 0);
-      append_birth(P, Bout, bcount, c);
+      append_birth(P, Bout, bcount, bc, c);
       bump(bc, MC_C_WW_SPLIT);
     }
   } else if (p.w < P.ww_lower * wc) {
@@ -259,7 +272,7 @@ __device__ bool do_collision(const RunParams& P, const Tab<R>& T, Part<R>& p, ui
       iso_dir(R(2) * c1.b - R(1), c2.a, c.ux, c.uy, c.uz);
       const int cg = sample_cdf(T.chi + m * G, G, c2.b);
       c.pk = pk_set_pending((c.pk & ~0x1Fu) | (uint32_t)cg, PEND_NONE, 0, 1, 0);
-      append_birth(P, Bout, bcount, c);
+      append_birth(P, Bout, bcount, bc, c);
     }
     if (n > 0) bump(bc, MC_C_SECONDARY, (unsigned)n);
     log_event(P, T, p, 0, 1, n);

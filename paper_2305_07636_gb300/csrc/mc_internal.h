@@ -145,6 +145,7 @@ struct Ctl {
   unsigned long long t_start, t_end;  // %globaltimer at kernel start / end (ns)
   unsigned long long k_acc;           // k-eigenvalue cycle: sum of fixed(w l nu Sigma_f 2^32)
   unsigned long long pc_n;            // particles banked at this launch's interior census
+  unsigned long long tail_it;         // split run: the iteration the history-style tail launch starts at
 };
 
 struct RunParams {
@@ -207,6 +208,10 @@ struct RunParams {
   // FP32 tracking, plain-walk tallies only: per-warp regions of segments waiting to be scored
   // (warp w of the grid at seg + w * kSegLanes * kSegCap); nullptr: every flight is scored at once
   uint4* seg;
+  // split run (event-based launch, then a history-style tail launch): per-warp stacks of the tail's
+  // secondaries, lane l of warp w's slot j at WS[l][w * ws_cap + j]; nullptr: one launch
+  uint4* WS[kMaxLanes];
+  unsigned long long ws_cap;
 };
 
 // fission sites: FP32 tracking 1 x 16 B (x, y, z, g), FP64 2 x 16 B ((x, y), (z, g))

@@ -38,7 +38,15 @@ constexpr unsigned kClaim = MCGB_CLAIM, kClaimTail = MCGB_CLAIM_TAIL, kTailWaves
 
 // dynamic shared memory: [table blob][per-warp flight queues: warps x Lanes<R>::N x kWarpQ]
 // [per-warp tally staging: warps x kStage x 12 B]
-template <typename R, int MINB, bool RANGE, bool SEG>
+//
+// MODE 0 runs the whole transport in one launch: event-based iterations, then history-style ones
+// once the work left is below the drain threshold.  A split run launches MODE 1, which stops where
+// MODE 0 would turn history-style (and records that iteration in ctl->tail_it), then MODE 2, which
+// runs the history-style iterations from there with per-warp stacks of secondaries: a warp flies
+// its particles' secondaries before it claims more work, so one history-style iteration ends the
+// run instead of one per generation of secondaries, and the event-based launch carries none of
+// the tail's code.
+template <typename R, int MINB, bool RANGE, bool SEG, int MODE>
 __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
   extern __shared__ __align__(16) char smem[];
   __shared__ BlockCounters bc;
@@ -46,6 +54,8 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
   for (int i = threadIdx.x; i < P.blob_bytes / 16; i += blockDim.x)
     reinterpret_cast<uint4*>(smem)[i] = P.blob[i];
   if (threadIdx.x < MC_NCOUNTERS) bc.c[threadIdx.x] = 0u;
+  if (threadIdx.x < 8) bc.wn[threadIdx.x] = 0u;
+  if (threadIdx.x == 0) bc.local = MODE == 2 && P.WS[0] != nullptr ? 1u : 0u;
   __syncthreads();
   const Tab<R> T(smem);
   const int lane = threadIdx.x & 31;
@@ -65,10 +75,14 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
   const uint64_t row = P.row;  // tally elements per batch: bins, then difference slots
   // small tallies are striped over several copies so that hot bins are not one L2 address
   const uint64_t stripe_off = (uint64_t)(blockIdx.x % P.tally_stripes) * P.stripe_stride;
-  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t_start = globaltimer();
+  if (MODE != 2 && blockIdx.x == 0 && threadIdx.x == 0) ctl->t_start = globaltimer();
 
-  for (uint64_t it = 0;; ++it) {
+  for (uint64_t it = MODE == 2 ? ld_volatile_u64(&ctl->tail_it) : 0ull;; ++it) {
     const int cur = (int)(it % 3), nxt = (int)((it + 1) % 3), old = (int)((it + 2) % 3);
+    // event-based launch of a split run: whichever way it ends (history-style turn, no work left,
+    // an error), the tail launch starts from the iteration recorded here (the counters it reads
+    // are those every CTA of this launch read)
+    if (MODE == 1 && blockIdx.x == 0 && threadIdx.x == 0) ctl->tail_it = it;
     // the status word can change at any time (another CTA may post an error): read it once per
     // CTA so that every thread of the CTA takes the same branch
     if (threadIdx.x == 0) s_status = ld_volatile_int(&ctl->status);
@@ -96,7 +110,9 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
       set_status(P, MC_ERR_TIMEOUT);
       break;
     }
-    const bool drain = P.history_mode || (nSrc == left && W <= P.drain_threshold);
+    const bool drain = MODE == 2 || P.history_mode || (nSrc == left && W <= P.drain_threshold);
+    if (MODE == 1 && drain) break;  // the tail launch takes over from this iteration
+    const bool hs = MODE == 2 || (MODE == 0 && drain);  // this iteration runs history-style
     // splits are held once the copies made in this iteration would exceed half the birth store,
     // less the nB - nBt waiting births that are stored again below
     if (threadIdx.x == 0) {
@@ -137,7 +153,24 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
     uint64_t rbeg = 0, rend = 0;  // the warp's claimed item range
     bool exhausted = false;
     while (true) {
-      while (qn < 32u && !(exhausted && rbeg >= rend)) {
+      while (qn < 32u && ((MODE == 2 && bc.wn[warp] != 0u) || !(exhausted && rbeg >= rend))) {
+        if constexpr (MODE == 2) {
+          // secondaries of this warp's particles first (depth first keeps the stack shallow)
+          const unsigned sn = bc.wn[warp] < (unsigned)P.ws_cap ? bc.wn[warp] : (unsigned)P.ws_cap;
+          if (sn != 0u) {
+            const unsigned k = sn < 32u - qn ? sn : 32u - qn;
+            if ((unsigned)lane < k) {
+              Part<R> b;
+              bank_load(b, P.WS, ((uint64_t)blockIdx.x * nwarp + warp) * P.ws_cap + sn - k + lane);
+              queue_store(b, wq, kWarpQ, qn + lane);
+            }
+            __syncwarp();
+            if (lane == 0) bc.wn[warp] = sn - k;
+            __syncwarp();
+            qn += k;
+            continue;
+          }
+        }
         if (rbeg >= rend) {
           unsigned long long b = 0;
           const unsigned take = rend + tail < W ? kClaim : kClaimTail;
@@ -159,7 +192,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
           } else if (item < nF + nS + nB) {
             const uint64_t j = item - nF - nS;
             bank_load(p, Bin, j);
-            if (j >= nBt) append_birth(P, Bout, bcount, p);  // waits for room
+            if (j >= nBt) append_birth(P, Bout, bcount, &bc, p);  // waits for room
             else ready = true;
           } else {
             const uint64_t h = P.h_first + h0 + (item - nF - nS - nB);
@@ -198,8 +231,8 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
       // the watchdog below can still end one of them, and it stops the run.  Their slots are
       // reserved now with one atomic per warp on the packed pair of counts (front in the low
       // half, back in the high half), so the atomic's latency hides behind the scoring.
-      const bool wF = !drain && flies && pend == PEND_COLL && hit.chan != CHAN_CAPTURE;
-      const bool wS = !drain && flies && pend == PEND_SURF;
+      const bool wF = !hs && flies && pend == PEND_COLL && hit.chan != CHAN_CAPTURE;
+      const bool wS = !hs && flies && pend == PEND_SURF;
       const unsigned mF = __ballot_sync(0xFFFFFFFFu, wF), mS = __ballot_sync(0xFFFFFFFFu, wS);
       unsigned long long bFS = 0;
       if (lane == 0 && (mF | mS))
@@ -223,9 +256,9 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
           set_status(P, MC_ERR_TIMEOUT);
           alive = false;
         }
-        if (alive && drain) again = handle_pending(P, T, p, Bout, bcount, &bc, row, stripe_off);
+        if (alive && hs) again = handle_pending(P, T, p, Bout, bcount, &bc, row, stripe_off);
       }
-      if (drain) {
+      if (hs) {
         const unsigned m = __ballot_sync(0xFFFFFFFFu, again);
         if (again) queue_store(p, wq, kWarpQ, qn + __popc(m & lt));
         qn += __popc(m);
@@ -572,35 +605,58 @@ __global__ void k_philox(uint64_t seed, const uint4* ctr, uint4* out, uint64_t n
 // ------------------------------------------------------------------------------------------ launchers
 // Two register budgets of the same kernel: 3 CTAs of 256 threads per SM (80 registers) or 2 CTAs
 // (128 registers, no spills); `wide` selects the second.  `range` selects the build with the range
-// walk of the scoring (tallies whose time axis is much finer than their mesh).
+// walk of the scoring (tallies whose time axis is much finer than their mesh), `seg` the build that
+// scores segments apart from their flights, `mode` the launch of a split run (1: event-based part,
+// 2: history-style tail; only the segment builds are split).
 template <typename R>
-static const void* transport_fn(bool wide, bool range, bool seg) {
+static const void* transport_fn(bool wide, bool range, bool seg, int mode = 0) {
   if constexpr (sizeof(R) == 8) {
-    return range ? (const void*)k_transport<R, 2, true, false> : (const void*)k_transport<R, 2, false, false>;
+    return range ? (const void*)k_transport<R, 2, true, false, 0> : (const void*)k_transport<R, 2, false, false, 0>;
   } else {
-    if (seg) return wide ? (const void*)k_transport<R, 2, false, true> : (const void*)k_transport<R, 3, false, true>;
-    if (range) return wide ? (const void*)k_transport<R, 2, true, false> : (const void*)k_transport<R, 3, true, false>;
-    return wide ? (const void*)k_transport<R, 2, false, false> : (const void*)k_transport<R, 3, false, false>;
+    if (seg) {
+      if (mode == 1) return wide ? (const void*)k_transport<R, 2, false, true, 1> : (const void*)k_transport<R, 3, false, true, 1>;
+      if (mode == 2) return wide ? (const void*)k_transport<R, 2, false, true, 2> : (const void*)k_transport<R, 3, false, true, 2>;
+      return wide ? (const void*)k_transport<R, 2, false, true, 0> : (const void*)k_transport<R, 3, false, true, 0>;
+    }
+    if (range) return wide ? (const void*)k_transport<R, 2, true, false, 0> : (const void*)k_transport<R, 3, true, false, 0>;
+    return wide ? (const void*)k_transport<R, 2, false, false, 0> : (const void*)k_transport<R, 3, false, false, 0>;
   }
 }
 
+// A run with per-warp stacks (P.WS) of a segment build is split into the event-based launch and
+// the history-style tail launch, back to back on the stream; any other run is one launch.
 template <typename R>
 cudaError_t launch_transport(const RunParams& P, int grid, int block, size_t smem, cudaStream_t s, bool wide,
                              bool range) {
   void* args[] = {const_cast<RunParams*>(&P)};
-  return cudaLaunchCooperativeKernel(transport_fn<R>(wide, range, P.seg != nullptr), grid, block, args, smem, s);
+  const bool seg = P.seg != nullptr;
+  if (sizeof(R) == 4 && seg && P.WS[0] != nullptr) {
+    cudaError_t e = cudaLaunchCooperativeKernel(transport_fn<R>(wide, range, true, 1), grid, block, args, smem, s);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel(transport_fn<R>(wide, range, true, 2), grid, block, args, smem, s);
+  }
+  return cudaLaunchCooperativeKernel(transport_fn<R>(wide, range, seg), grid, block, args, smem, s);
 }
 
 template <typename R>
 cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide, bool range, bool seg) {
-  const void* f = transport_fn<R>(wide, range, seg);
-  // opt in for the exact size: the default limit (48 KB less the kernel's static shared memory)
-  // can be exceeded by a dynamic size just under 48 KB
-  {
+  // every mode of a build has the same register budget; the split launches need the grid to fit
+  // for each of them, so the least occupancy of the modes is taken
+  const int n_modes = (sizeof(R) == 4 && seg) ? 3 : 1;
+  int best = 1 << 30;
+  for (int mode = 0; mode < n_modes; ++mode) {
+    const void* f = transport_fn<R>(wide, range, seg, mode);
+    // opt in for the exact size: the default limit (48 KB less the kernel's static shared memory)
+    // can be exceeded by a dynamic size just under 48 KB
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, block, smem);
+    if (e != cudaSuccess) return e;
+    best = n < best ? n : best;
   }
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, f, block, smem);
+  *per_sm = best;
+  return cudaSuccess;
 }
 
 template cudaError_t launch_transport<float>(const RunParams&, int, int, size_t, cudaStream_t, bool, bool);
