@@ -42,7 +42,8 @@ BYTES_PER_FLIGHT = 136  # 64 B state read + 64 B state write + 8 B tally update 
 
 
 KERNEL_SOURCES = {
-    "k_transport": ["mc_transport.cu", "mc_events.cuh", "mc_device.cuh", "mc_internal.h"],
+    "k_transport": ["mc_transport.cuh", "mc_transport.cu", "mc_transport_seg.cu", "mc_transport_range.cu",
+                    "mc_events.cuh", "mc_device.cuh", "mc_internal.h"],
     "k_transport_batch": ["mc_batch.cu", "mc_events.cuh", "mc_device.cuh", "mc_internal.h"],
 }
 

@@ -34,7 +34,7 @@ def nvcc() -> str:
 # build, so with contraction the 80- and 128-register builds of the walk (and the batched kernel)
 # could round a geometry expression differently and move a particle differently.  Without it every
 # build computes the same bits, and the FP64 walk rounds as the CPU reference does.
-NO_FMA = {"mc_transport.cu", "mc_batch.cu", "mc_api.cu"}
+NO_FMA = {"mc_transport.cu", "mc_transport_seg.cu", "mc_transport_range.cu", "mc_batch.cu", "mc_api.cu"}
 
 
 def per_file_flags(src):

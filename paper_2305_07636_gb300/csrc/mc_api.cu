@@ -899,6 +899,8 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
     rc = p->d_seg.ensure((size_t)grid * (block / 32) * kSegLanes * kSegCap * 16, p->dev);
     if (rc != MC_OK) return rc;
     P.seg = (uint4*)p->d_seg.ptr;
+  }
+  if (seg || (range && !fp64)) {
     // split run: the history-style tail flies each warp's secondaries from its own stack of up to
     // 256, carved out of the bank capacity (a bank too small for 32 per warp runs in one launch).
     // Runs with weight windows stay one launch: a stack keeps a lineage on its warp, and lineages
