@@ -184,14 +184,20 @@ typedef struct {
   int fixed_bits;         /* fixed-point scale 2^fixed_bits (default 32) */
   int n_batches;          /* statistical batches, >= 2 (default 32) */
   uint64_t bank_capacity; /* particles in flight (0 = library default: the power of two >= 2 x the
-                             histories, at most 2^22, or 2^28 with census_times) */
-  int block_size;         /* threads per CTA (0 = autotuned default) */
+                             histories, at most 2^22, or 2^28 with census_times); FP32 mc_run runs
+                             without census_times or weight windows also keep, for the
+                             history-style tail, a stack of min(256, bank_capacity / warps)
+                             secondaries per warp (none below 32: the run is then one launch) */
+  int block_size;         /* threads per CTA (0 = mc_run_tune's choice if it ran, else 128 for
+                             the 96-register build above and 256 otherwise) */
   int blocks_per_sm;      /* CTAs per SM, counted in 256-thread CTAs (the cap is blocks_per_sm x
                              256 / block_size CTAs): 2 selects the 128-register build of the kernel
                              (2 x 256 threads per SM), another value the 80-register build (3 x 256
-                             fit); 0 = mc_run_tune's choice if it ran, else the 128-register build
-                             when a tally deals its time pieces out over the warp and the 80-register
-                             build otherwise, as many CTAs as fit */
+                             fit; FP32 runs whose tallies all take the plain track-length walk use
+                             a 96-register build at 128 threads per CTA, 5 CTAs per SM); 0 =
+                             mc_run_tune's choice if it ran, else the 128-register build when a
+                             tally deals its time pieces out over the warp and the 80- or
+                             96-register build otherwise, as many CTAs as fit */
   uint64_t max_iterations;/* watchdog: event iterations before MC_ERR_TIMEOUT (0 = 2^20) */
   int aggregate_atomics;  /* 1 = warp-aggregated tally atomics (staged per warp, same-bin scores
                              summed before one atomic), 0 = one atomic per score at once,
@@ -203,7 +209,10 @@ typedef struct {
   int algorithm;          /* mc_algorithm (default MC_ALG_EVENT) */
   uint64_t drain_threshold; /* event mode: once every history is sourced and at most this many
                                particles remain, finish them history-style (0 = 2 per thread; in
-                               mc_run_eigen 32 per thread; mc_run_tune may pick another) */
+                               mc_run_eigen 32 per thread; mc_run_tune may pick another).  FP32
+                               mc_run runs without census_times or weight windows do this in a
+                               second launch, in which each warp flies its secondaries from its
+                               own stack; the results equal those of one launch */
   int tally_stripes;      /* copies of the batch tallies that CTAs score into round-robin, summed
                              by the statistics (0 = up to 16 within a 64 MB budget) */
   int batch_unit;         /* mc_run_batch: histories per work unit a warp claims (0 = tuned or 128) */

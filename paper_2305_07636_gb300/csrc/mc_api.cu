@@ -873,20 +873,22 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   CK(cudaMemsetAsync(p->d_ctl.ptr, 0, sizeof(Ctl), s));
   CK(cudaMemsetAsync(p->d_tally.ptr, 0, (size_t)stripes * nb * row * 8, s));
   if (P.log) CK(cudaMemsetAsync(p->d_log.ptr, 0, log_cap * sizeof(mc_event), s));
-  const int block = o.block_size ? o.block_size : 256;
-  // tables + per-warp flight queues (64 slots) + per-warp tally staging (128 x 12 B)
-  const size_t smem = P.blob_bytes + (size_t)(block / 32) * transport_warp_smem(fp64);
-  rc = check_shared_memory(p->dev, smem, "the transport kernel");
-  if (rc != MC_OK) return rc;
-  int per_sm = 0;
   // blocks_per_sm == 2 selects the 128-register build of the kernel, any other explicit value the
-  // 80-register one; 0 takes the 128-register build when a tally is scored by the range walk
-  // (that walk needs the registers) and the 80-register build otherwise
+  // 80-register one (96 registers for a segment build at 128 threads per CTA); 0 takes the
+  // 128-register build when a tally is scored by the range walk (that walk needs the registers) and
+  // the 80- or 96-register build otherwise
   const bool range = p->range;
   const bool wide = o.blocks_per_sm == 2 || (o.blocks_per_sm == 0 && range);
   // FP32 tracking with plain-walk tallies only: segments are scored apart from their flights
   bool seg = !fp64 && !range && p->n_tally <= 4;
   for (const HostTally& t : p->tallies) seg = seg && t.est == MC_EST_TRACK_LENGTH;
+  // default CTA size: 128 threads for the segment build's 96-register budget, else 256
+  const int block = o.block_size ? o.block_size : (seg && !wide ? 128 : 256);
+  // tables + per-warp flight queues (64 slots) + per-warp tally staging (128 x 12 B)
+  const size_t smem = P.blob_bytes + (size_t)(block / 32) * transport_warp_smem(fp64);
+  rc = check_shared_memory(p->dev, smem, "the transport kernel");
+  if (rc != MC_OK) return rc;
+  int per_sm = 0;
   CK(fp64 ? transport_occupancy<double>(block, smem, &per_sm, wide, range, false)
           : transport_occupancy<float>(block, smem, &per_sm, wide, range, seg));
   if (per_sm < 1) return fail(MC_ERR_CUDA, "transport kernel does not fit on an SM (block %d, smem %zu)", block, smem);

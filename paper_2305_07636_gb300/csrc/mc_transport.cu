@@ -313,16 +313,17 @@ __global__ void k_philox(uint64_t seed, const uint4* ctr, uint4* out, uint64_t n
 
 // ------------------------------------------------------------------------------------------ launchers
 // Two register budgets of the same kernel: 3 CTAs of 256 threads per SM (80 registers) or 2 CTAs
-// (128 registers, no spills); `wide` selects the second.  `range` selects the build with the range
-// walk of the scoring (tallies whose time axis is much finer than their mesh), `seg` the build that
-// scores segments apart from their flights, `mode` the launch of a split run (1: event-based part,
-// 2: history-style tail; the FP32 segment and range-walk builds are split).
+// (128 registers, no spills); `wide` selects the second (the segment builds at 128 threads per CTA
+// take a third, 96 registers at 5 CTAs per SM, instead of 80).  `range` selects the build with the
+// range walk of the scoring (tallies whose time axis is much finer than their mesh), `seg` the
+// build that scores segments apart from their flights, `mode` the launch of a split run (1:
+// event-based part, 2: history-style tail; the FP32 segment and range-walk builds are split).
 template <typename R>
-static const void* transport_fn(bool wide, bool range, bool seg, int mode = 0) {
+static const void* transport_fn(bool wide, bool range, bool seg, int block, int mode = 0) {
   if constexpr (sizeof(R) == 8) {
     return range ? (const void*)k_transport<R, 2, true, false, 0> : (const void*)k_transport<R, 2, false, false, 0>;
   } else {
-    if (seg) return transport_fn_seg(wide, mode);
+    if (seg) return transport_fn_seg(wide, block, mode);
     if (range) return transport_fn_range(wide, mode);
     return wide ? (const void*)k_transport<R, 2, false, false, 0> : (const void*)k_transport<R, 3, false, false, 0>;
   }
@@ -337,11 +338,11 @@ cudaError_t launch_transport(const RunParams& P, int grid, int block, size_t sme
   void* args[] = {const_cast<RunParams*>(&P)};
   const bool seg = P.seg != nullptr;
   if (sizeof(R) == 4 && (seg || range) && P.WS[0] != nullptr) {
-    cudaError_t e = cudaLaunchCooperativeKernel(transport_fn<R>(wide, range, seg, 1), grid, block, args, smem, s);
+    cudaError_t e = cudaLaunchCooperativeKernel(transport_fn<R>(wide, range, seg, block, 1), grid, block, args, smem, s);
     if (e != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel(transport_fn<R>(wide, range, seg, 2), grid, block, args, smem, s);
+    return cudaLaunchCooperativeKernel(transport_fn<R>(wide, range, seg, block, 2), grid, block, args, smem, s);
   }
-  return cudaLaunchCooperativeKernel(transport_fn<R>(wide, range, seg), grid, block, args, smem, s);
+  return cudaLaunchCooperativeKernel(transport_fn<R>(wide, range, seg, block), grid, block, args, smem, s);
 }
 
 template <typename R>
@@ -351,7 +352,7 @@ cudaError_t transport_occupancy(int block, size_t smem, int* per_sm, bool wide, 
   const int n_modes = (sizeof(R) == 4 && (seg || range)) ? 3 : 1;
   int best = 1 << 30;
   for (int mode = 0; mode < n_modes; ++mode) {
-    const void* f = transport_fn<R>(wide, range, seg, mode);
+    const void* f = transport_fn<R>(wide, range, seg, block, mode);
     // opt in for the exact size: the default limit (48 KB less the kernel's static shared memory)
     // can be exceeded by a dynamic size just under 48 KB
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

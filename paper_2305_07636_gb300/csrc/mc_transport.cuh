@@ -53,8 +53,11 @@ constexpr unsigned kClaim = MCGB_CLAIM, kClaimTail = MCGB_CLAIM_TAIL, kTailWaves
 // its particles' secondaries before it claims more work, so one history-style iteration ends the
 // run instead of one per generation of secondaries, and the event-based launch carries none of
 // the tail's code.
+//
+// MINB sets the register budget: 2 or 3 CTAs of 256 threads per SM (128 or 80 registers), or 5 CTAs
+// of 128 threads (96 registers, the segment builds at 128 threads per CTA).
 template <typename R, int MINB, bool RANGE, bool SEG, int MODE>
-__global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
+__global__ void __launch_bounds__(MINB == 5 ? 128 : 256, MINB) k_transport(RunParams P) {
   extern __shared__ __align__(16) char smem[];
   __shared__ BlockCounters bc;
   __shared__ int s_status;
@@ -305,9 +308,10 @@ __global__ void __launch_bounds__(256, MINB) k_transport(RunParams P) {
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t_end = globaltimer();
 }
 
-// the kernel of one build family: `wide` the 128-register build (else 80), `mode` 0 for one
-// launch, 1 / 2 for the event-based part and the tail of a split run
-const void* transport_fn_seg(bool wide, int mode);    // FP32, segments scored apart
-const void* transport_fn_range(bool wide, int mode);  // FP32, range walk
+// the kernel of one build family: `wide` the 128-register build (else 80, or for the segment
+// builds at 128 threads per CTA 96), `mode` 0 for one launch, 1 / 2 for the event-based part and
+// the tail of a split run
+const void* transport_fn_seg(bool wide, int block, int mode);  // FP32, segments scored apart
+const void* transport_fn_range(bool wide, int mode);           // FP32, range walk
 
 }  // namespace mcgb
