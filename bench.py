@@ -161,18 +161,6 @@ def issue_roofline(workload, n, flights, kernel_ms, clk):
             "peak_kind": "152 SMs x 4 schedulers x SM clock sampled during the timed region"}
 
 
-def launches_per_run(prob):
-    """Kernels one mc_run launches: transport and batch statistics, plus the range-walk
-    reconstruction when a tally's time axis is much finer than its mesh (the library's rule:
-    nt >= 3 and nt >= 4 (nx + ny + nz))."""
-    n = 2
-    for t in prob["tallies"]:
-        nx, ny, nz, nt = (len(t[k]) - 1 for k in ("x", "y", "z", "t"))
-        if nt >= 3 and nt >= 4 * (nx + ny + nz):
-            return n + 1
-    return n
-
-
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -869,7 +857,7 @@ def main():
                   "ms_in_history_style_tail": drain_ms},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches_per_run(prob) * args.steps,
+        "gpu_launches": p.launches() * args.steps,  # counted by the library for the last run
         "combined_tally": combined,
         "clocks": clk,
         "wall_s": wall,

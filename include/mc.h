@@ -388,6 +388,15 @@ int mc_trace_get(mc_problem* p, uint64_t* t_ns, uint64_t* items, uint64_t* sourc
  * the transport kernel and around the batch-statistics kernel (milliseconds).  Synchronises. */
 int mc_run_timing(mc_problem* p, double* transport_ms, double* stats_ms);
 
+/* Kernels the last mc_run of p launched on its stream: the transport (one launch, or two for a
+ * split run: FP32 tracking without census times or weight windows runs its event-based iterations
+ * and its history-style tail as two launches), the range-walk reconstruction when a tally is
+ * scored by the range walk, and the batch statistics.  *n receives the count.  MC_ERR_STATE when
+ * p has not run, or when its last run was not a plain mc_run (census times, mc_run_batch,
+ * mc_run_eigen), whose launches are not counted; mc_run_static leaves the count of p's last
+ * run as it was.  Does not synchronise. */
+int mc_run_launches(const mc_problem* p, int* n);
+
 /* Device layout of the last run's batch tallies (the track-length tally scoring of Section 3 writes
  * into it): *stripes copies of *n_batches rows of *row int64 (or double) elements each, so the
  * scoring atomics of a run spread over stripes x n_batches x row elements.  Any pointer may be

@@ -918,9 +918,13 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
     }
   }
   CK(cudaEventRecord(p->ev[0], s));
+  p->launches = 0;
   if (o.n_census == 0) {
     CK(fp64 ? launch_transport<double>(P, grid, block, smem, s, wide, range)
             : launch_transport<float>(P, grid, block, smem, s, wide, range));
+    // a split run (see launch_transport) is two launches
+    const bool split = !fp64 && (seg || range) && P.WS[0] != nullptr;
+    p->launches = (split ? 2 : 1) + (p->range ? 1 : 0) + 1;
   } else {
     rc = run_population_controlled(p, P, census, t_final, grid, block, smem, wide, range, fp64, lanes, cap,
                                    o.pc_method == MC_PC_COMB, s);
@@ -1137,6 +1141,7 @@ int mc_run_eigen(mc_problem* p, uint64_t n_per_cycle, int n_inactive, int n_acti
   if (k_mean) *k_mean = km;
   if (k_std_err) *k_std_err = std::sqrt(kv / (n_active - 1) / n_active);
   p->has_run = 1;
+  p->launches = 0;  // not counted
   p->batched = 0;
   p->n_hist = N * (uint64_t)nb;
   p->n_batches = nb;
@@ -1498,6 +1503,14 @@ int mc_trace_get(mc_problem* p, uint64_t* t_ns, uint64_t* items, uint64_t* sourc
     if (sources) sources[i] = buf[3 * i + 2];
   }
   *n_out = n;
+  return MC_OK;
+}
+
+int mc_run_launches(const mc_problem* p, int* n) {
+  if (!p || !n) return fail(MC_ERR_INVALID, "problem or output is NULL");
+  if (!p->has_run) return fail(MC_ERR_STATE, "no run yet");
+  if (p->batched || p->launches == 0) return fail(MC_ERR_STATE, "the last run's launches are not counted");
+  *n = p->launches;
   return MC_OK;
 }
 

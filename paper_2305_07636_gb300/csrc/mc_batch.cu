@@ -635,6 +635,7 @@ int mc_run_batch(mc_problem* const* ps, int n, const uint64_t* n_hist, uint64_t 
   for (int i = 0; i < n; ++i) {
     mc_problem* p = ps[i];
     p->has_run = 1;
+    p->launches = 0;  // not counted
     p->batched = 1;
     p->n_hist = n_hist[i];
     p->n_batches = nb;

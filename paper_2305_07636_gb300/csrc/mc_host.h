@@ -94,6 +94,7 @@ struct mc_problem {
   mcgb::DevBuf d_sticky;  // first device error of any run since the last mc_wait (not reset by mc_run)
   // last run
   int has_run = 0;
+  int launches = 0;  // kernels the last plain mc_run launched (0: not counted)
   int batched = 0;  // the last run was part of mc_run_batch (timing from the device clock)
   uint64_t n_hist = 0;
   int n_batches = 0;

@@ -131,6 +131,7 @@ SIGNATURES = {
     "mc_event_log": (C.c_int, [C.c_void_p, C.POINTER(mc_event), C.c_size_t,
                                C.POINTER(C.c_size_t)]),
     "mc_run_timing": (C.c_int, [C.c_void_p, DP, DP]),
+    "mc_run_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "mc_tally_layout": (C.c_int, [C.c_void_p, IP, IP, C.POINTER(C.c_uint64)]),
     "mc_tally_sums": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.c_size_t, IP]),
     "mc_trace_get": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
@@ -493,6 +494,13 @@ def tally_layout(h: int):
     return st.value, nb.value, row.value
 
 
+def run_launches(h: int) -> int:
+    """mc_run_launches: kernels the last plain mc_run launched."""
+    n = C.c_int(0)
+    check(lib().mc_run_launches(C.c_void_p(h), C.byref(n)))
+    return n.value
+
+
 def trace_get(h: int, cap: int = 65536):
     """mc_trace_get: per-iteration (t_ns, items, sources, drain) arrays of the last run."""
     t = np.zeros(cap, np.uint64)
@@ -565,6 +573,9 @@ class Problem:
 
     def timing(self):
         return run_timing(self.h)
+
+    def launches(self):
+        return run_launches(self.h)
 
     def events(self, cap):
         return event_log(self.h, cap)

@@ -5,11 +5,12 @@ depend on the order of their adds.
 
 - The lattice (production, so secondaries in every generation of the tail) and the 1D slab: a
   default run (split), a run whose bank is too small for stacks (one launch), history-based runs
-  (the whole run in the tail launch), and tails that start early (16x and 64x the default drain
-  threshold) give equal tallies and counters.
+  (the whole run in the tail launch), and tails that start early (16x the default drain threshold,
+  and a threshold above the whole run) give equal tallies and counters.
 - A run that ends inside the event-based launch (no history-style iteration left) adds nothing in
   the tail launch: the leakage of a purely absorbing slab is the E3 closed form, and the counters
   match a one-launch run.
+- mc_run_launches counts each kind of run's kernels.
 """
 import numpy as np
 import pytest
@@ -63,3 +64,20 @@ def test_run_ending_in_the_event_launch(torch):
     assert np.array_equal(p.tally_batches(0), t_split)
     assert c_split["source"] == 2_000_000
     p.close()
+
+
+def test_launch_count_of_each_kind_of_run(torch):
+    """mc_run_launches: a split run is two transport launches, a one-launch run one; the range
+    walk adds its reconstruction and every run its batch statistics."""
+    p = mc.Problem(P.config3())
+    p.run(100_000, 44)
+    assert p.launches() == 3  # event-based part, tail, statistics
+    p.run(100_000, 44, bank_capacity=1 << 16)
+    assert p.launches() == 2  # too small a bank for stacks: one transport launch
+    p.run(100_000, 44, precision="fp64")
+    assert p.launches() == 2  # FP64 tracking is not split
+    p.close()
+    q = mc.Problem(P.config2())
+    q.run(1_000_000, 45)
+    assert q.launches() == 4  # event-based part, tail, range-walk reconstruction, statistics
+    q.close()
