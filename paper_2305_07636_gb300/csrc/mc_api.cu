@@ -660,7 +660,6 @@ void mc_problem_destroy(mc_problem* p) {
   p->d_trace.release();
   p->d_sticky.release();
   p->d_ww.release();
-  p->d_seg.release();
   p->d_wstack.release();
   // k-eigenvalue and population-control buffers
   p->d_sites.release();
@@ -884,8 +883,10 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   for (const HostTally& t : p->tallies) seg = seg && t.est == MC_EST_TRACK_LENGTH;
   // default CTA size: 128 threads for the segment build's 96-register budget, else 256
   const int block = o.block_size ? o.block_size : (seg && !wide ? 128 : 256);
-  // tables + per-warp flight queues (64 slots) + per-warp tally staging (128 x 12 B)
-  const size_t smem = P.blob_bytes + (size_t)(block / 32) * transport_warp_smem(fp64);
+  // tables + per-warp flight queues (64 slots) + per-warp tally staging (128 x 12 B) + per-warp
+  // segment regions (64 records of 64 B)
+  const size_t smem = P.blob_bytes + (size_t)(block / 32) * (transport_warp_smem(fp64) +
+                                                             (seg ? (size_t)kSegLanes * kSegCap * 16 : 0));
   rc = check_shared_memory(p->dev, smem, "the transport kernel");
   if (rc != MC_OK) return rc;
   int per_sm = 0;
@@ -897,11 +898,7 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->dev));
   const int grid = sms * per_sm;
   P.drain_threshold = o.drain_threshold ? o.drain_threshold : (uint64_t)2 * grid * block;
-  if (seg) {
-    rc = p->d_seg.ensure((size_t)grid * (block / 32) * kSegLanes * kSegCap * 16, p->dev);
-    if (rc != MC_OK) return rc;
-    P.seg = (uint4*)p->d_seg.ptr;
-  }
+  P.seg = seg ? 1 : 0;
   if (seg || (range && !fp64)) {
     // split run: the history-style tail flies each warp's secondaries from its own stack of up to
     // 256, carved out of the bank capacity (a bank too small for 32 per warp runs in one launch).

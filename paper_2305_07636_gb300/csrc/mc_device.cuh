@@ -846,19 +846,19 @@ struct SegRec {
 
 __device__ __forceinline__ void seg_store(uint4* q, unsigned i, const SegRec& r) {
   const unsigned long long wb = (unsigned long long)__double_as_longlong(r.w);
-  __stcg(q + i, make_uint4(__float_as_uint(r.pos[0]), __float_as_uint(r.pos[1]), __float_as_uint(r.pos[2]),
+  q[i] = (make_uint4(__float_as_uint(r.pos[0]), __float_as_uint(r.pos[1]), __float_as_uint(r.pos[2]),
                            __float_as_uint(r.u[0])));
-  __stcg(q + kSegCap + i, make_uint4(__float_as_uint(r.u[1]), __float_as_uint(r.u[2]), __float_as_uint(r.l),
+  q[kSegCap + i] = (make_uint4(__float_as_uint(r.u[1]), __float_as_uint(r.u[2]), __float_as_uint(r.l),
                                      __float_as_uint(r.t0)));
-  __stcg(q + 2 * kSegCap + i, make_uint4(__float_as_uint(r.s), r.batch, (uint32_t)wb, (uint32_t)(wb >> 32)));
-  __stcg(q + 3 * kSegCap + i,
+  q[2 * kSegCap + i] = (make_uint4(__float_as_uint(r.s), r.batch, (uint32_t)wb, (uint32_t)(wb >> 32)));
+  q[3 * kSegCap + i] = (
          make_uint4((uint32_t)r.idx[0], (uint32_t)r.idx[1], (uint32_t)r.idx[2],
                     (uint32_t)(r.it + 1) | ((uint32_t)r.g << 17) | ((uint32_t)r.ti << 22) | ((r.resumed ? 1u : 0u) << 24)));
 }
 
 __device__ __forceinline__ void seg_load(const uint4* q, unsigned i, SegRec& r) {
-  const uint4 a = __ldcg(q + i), b = __ldcg(q + kSegCap + i), c = __ldcg(q + 2 * kSegCap + i),
-              d = __ldcg(q + 3 * kSegCap + i);
+  const uint4 a = q[i], b = q[kSegCap + i], c = q[2 * kSegCap + i],
+              d = q[3 * kSegCap + i];
   r.pos[0] = __uint_as_float(a.x); r.pos[1] = __uint_as_float(a.y); r.pos[2] = __uint_as_float(a.z);
   r.u[0] = __uint_as_float(a.w); r.u[1] = __uint_as_float(b.x); r.u[2] = __uint_as_float(b.y);
   r.l = __uint_as_float(b.z);

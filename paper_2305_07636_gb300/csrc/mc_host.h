@@ -90,7 +90,6 @@ struct mc_problem {
   mcgb::DevBuf d_blob[2];
   mcgb::DevBuf d_ctl, d_tally, d_stats, d_log, d_banks, d_trace;
   mcgb::DevBuf d_wstack;  // per-warp stacks of secondaries of a split run's tail launch
-  mcgb::DevBuf d_seg;  // per-warp regions of segments waiting to be scored (FP32 tracking)
   mcgb::DevBuf d_sticky;  // first device error of any run since the last mc_wait (not reset by mc_run)
   // last run
   int has_run = 0;

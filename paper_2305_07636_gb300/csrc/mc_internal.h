@@ -18,7 +18,7 @@ constexpr unsigned kWarpQ = 64;
 constexpr unsigned kStage = 128;
 // segments waiting to be scored: records per warp (31 waiting + 32 new from one flight round; a
 // scoring pass puts back at most as many as it took) of kSegLanes 16-byte lanes, in a per-warp
-// region of device memory
+// region of shared memory (the persistent kernel) or device memory (the batched kernel)
 constexpr unsigned kSegCap = 64;
 constexpr int kSegLanes = 4;
 constexpr uint32_t kSourceEvent = 0xFFFFFFFFu;
@@ -205,9 +205,9 @@ struct RunParams {
   const uint4* src_site;   // [N] sites of this cycle's sources (cycle >= 1)
   uint4* site_next;        // [N * nmax] sites banked this cycle
   uint32_t* count_next;    // [N] sites banked by each history (zeroed before the cycle)
-  // FP32 tracking, plain-walk tallies only: per-warp regions of segments waiting to be scored
-  // (warp w of the grid at seg + w * kSegLanes * kSegCap); nullptr: every flight is scored at once
-  uint4* seg;
+  // FP32 tracking, plain-walk tallies only: 1 = flown segments wait in a per-warp region of shared
+  // memory and are scored 32 at a time; 0: every flight is scored at once
+  int seg, pad_seg;
   // split run (event-based launch, then a history-style tail launch): per-warp stacks of the tail's
   // secondaries, lane l of warp w's slot j at WS[l][w * ws_cap + j]; nullptr: one launch
   uint4* WS[kMaxLanes];

@@ -336,7 +336,7 @@ template <typename R>
 cudaError_t launch_transport(const RunParams& P, int grid, int block, size_t smem, cudaStream_t s, bool wide,
                              bool range) {
   void* args[] = {const_cast<RunParams*>(&P)};
-  const bool seg = P.seg != nullptr;
+  const bool seg = P.seg != 0;
   if (sizeof(R) == 4 && (seg || range) && P.WS[0] != nullptr) {
     cudaError_t e = cudaLaunchCooperativeKernel(transport_fn<R>(wide, range, seg, block, 1), grid, block, args, smem, s);
     if (e != cudaSuccess) return e;

@@ -44,7 +44,8 @@ namespace mcgb {
 constexpr unsigned kClaim = MCGB_CLAIM, kClaimTail = MCGB_CLAIM_TAIL, kTailWaves = MCGB_TAIL_WAVES;
 
 // dynamic shared memory: [table blob][per-warp flight queues: warps x Lanes<R>::N x kWarpQ]
-// [per-warp tally staging: warps x kStage x 12 B]
+// [per-warp tally staging: warps x kStage x 12 B][SEG: per-warp segment regions: warps x
+// kSegLanes x kSegCap x 16 B]
 //
 // MODE 0 runs the whole transport in one launch: event-based iterations, then history-style ones
 // once the work left is below the drain threshold.  A split run launches MODE 1, which stops where
@@ -76,7 +77,9 @@ __global__ void __launch_bounds__(MINB == 5 ? 128 : 256, MINB) k_transport(RunPa
   const Stage stage{reinterpret_cast<uint32_t*>(stage_base + (size_t)nwarp * kStage * 8) + warp * kStage,
                     reinterpret_cast<unsigned long long*>(stage_base) + warp * kStage};
   // SEG: the warp's region of segments waiting to be scored, ns of them (warp-uniform)
-  uint4* const sq = SEG ? P.seg + ((size_t)blockIdx.x * nwarp + warp) * (kSegLanes * kSegCap) : nullptr;
+  // SEG: the warp's region of segments waiting to be scored, after the staging buffers
+  uint4* const sq = SEG ? reinterpret_cast<uint4*>(stage_base + (size_t)nwarp * kStage * 12) + warp * (kSegLanes * kSegCap)
+                        : nullptr;
   unsigned ns = 0;
   Ctl* ctl = P.ctl;
   const unsigned lt = lanemask_lt();
