@@ -492,9 +492,9 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
 namespace mcgb {
 
 // Shared memory of one warp of the transport kernel besides the tables: its flight queue (64
-// particles) and its tally staging buffer (128 x 12 B).
-size_t transport_warp_smem(int fp64) {
-  return (size_t)kWarpQ * 16 * (fp64 ? kLanesFP64 : kLanesFP32) + (size_t)kStage * 12;
+// particles) and, where the tally adds are warp-aggregated, its tally staging buffer (128 x 12 B).
+size_t transport_warp_smem(int fp64, bool aggregate) {
+  return (size_t)kWarpQ * 16 * (fp64 ? kLanesFP64 : kLanesFP32) + (aggregate ? (size_t)kStage * 12 : 0);
 }
 
 // NVTX range over a library call or a phase of it (visible to nsys / ncu when a tool is attached;
@@ -883,9 +883,9 @@ int mc_run(mc_problem* p, uint64_t n_histories, uint64_t seed, const mc_run_opts
   for (const HostTally& t : p->tallies) seg = seg && t.est == MC_EST_TRACK_LENGTH;
   // default CTA size: 128 threads for the segment build's 96-register budget, else 256
   const int block = o.block_size ? o.block_size : (seg && !wide ? 128 : 256);
-  // tables + per-warp flight queues (64 slots) + per-warp tally staging (128 x 12 B) + per-warp
-  // segment regions (64 records of 64 B)
-  const size_t smem = P.blob_bytes + (size_t)(block / 32) * (transport_warp_smem(fp64) +
+  // tables + per-warp flight queues (64 slots) + per-warp tally staging (128 x 12 B, warp-aggregated
+  // tally adds only) + per-warp segment regions (64 records of 64 B)
+  const size_t smem = P.blob_bytes + (size_t)(block / 32) * (transport_warp_smem(fp64, P.aggregate != 0) +
                                                              (seg ? (size_t)kSegLanes * kSegCap * 16 : 0));
   rc = check_shared_memory(p->dev, smem, "the transport kernel");
   if (rc != MC_OK) return rc;
@@ -1019,7 +1019,7 @@ int mc_run_eigen(mc_problem* p, uint64_t n_per_cycle, int n_inactive, int n_acti
     CK(cudaMemsetAsync(p->d_log.ptr, 0, log_cap * sizeof(mc_event), s));
   }
   const int block = o.block_size ? o.block_size : 256;
-  const size_t smem = p->blob[fp64].size() + (size_t)(block / 32) * transport_warp_smem(fp64);
+  const size_t smem = p->blob[fp64].size() + (size_t)(block / 32) * transport_warp_smem(fp64, o.aggregate_atomics > 0);
   rc = check_shared_memory(p->dev, smem, "the transport kernel");
   if (rc != MC_OK) return rc;
   const bool range = p->range;
@@ -1767,7 +1767,7 @@ extern "C" int mc_run_static(const mc_problem* p, uint64_t n_histories, uint64_t
   CK(cudaMemsetAsync(base, 0, off_banks, s));
   CK(cudaMemsetAsync(base + off_tally, 0, tally_bytes, s));
   const int block = o.block_size ? o.block_size : 256;
-  const size_t smem = P.blob_bytes + (size_t)(block / 32) * transport_warp_smem(fp64);
+  const size_t smem = P.blob_bytes + (size_t)(block / 32) * transport_warp_smem(fp64, P.aggregate != 0);
   rc = check_shared_memory(p->dev, smem, "the transport kernel");
   if (rc != MC_OK) return rc;
   int per_sm = 0;

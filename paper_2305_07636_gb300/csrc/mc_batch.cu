@@ -27,6 +27,8 @@
 #include <numeric>
 #include <vector>
 
+// this kernel's weight-window test out of line (see weight_window)
+#define MCGB_WW_OUT_OF_LINE 1
 #include "mc_events.cuh"
 #include "mc_host.h"
 

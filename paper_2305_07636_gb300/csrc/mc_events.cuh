@@ -57,10 +57,12 @@ __device__ inline void grid_barrier(const RunParams& P, Ctl* ctl, unsigned long 
 }
 
 // ------------------------------------------------------------------------------------------ logging
+// The event-log write is compiled out of line (the log is off in every timed run, and its code
+// would otherwise sit inline at each of the walk's event sites); only the test for an open log
+// stays inline.
 template <typename R>
-__device__ void log_event(const RunParams& P, const Tab<R>& T, const Part<R>& p, int kind,
-                          int outcome, int n_child) {
-  if (P.log == nullptr) return;
+__device__ __noinline__ void log_event_write(const RunParams& P, const Tab<R>& T, const Part<R>& p, int kind,
+                                             int outcome, int n_child) {
   if ((uint64_t)p.root < P.log_first || (uint64_t)p.root >= P.log_first + P.log_count) return;
   const unsigned long long i = atomicAdd(&P.ctl->log_n, 1ull);
   if (i >= P.log_cap) return;
@@ -79,6 +81,12 @@ __device__ void log_event(const RunParams& P, const Tab<R>& T, const Part<R>& p,
   e.ux = p.ux; e.uy = p.uy; e.uz = p.uz;
   e.t = p.time_d(); e.w = p.w;
   P.log[i] = e;
+}
+
+template <typename R>
+__device__ __forceinline__ void log_event(const RunParams& P, const Tab<R>& T, const Part<R>& p, int kind,
+                                          int outcome, int n_child) {
+  if (P.log != nullptr) log_event_write(P, T, p, kind, outcome, n_child);
 }
 
 // ------------------------------------------------------------------------------------------ counters
@@ -117,11 +125,17 @@ __device__ __forceinline__ void append_birth(const RunParams& P, uint4* const* B
   bank_store(c, Bout, i);
 }
 
-// weight-window test after a collision or surface event (split above, roulette below)
+// Weight-window test after a collision or surface event (split above, roulette below).  Where
+// MCGB_WW_OUT_OF_LINE is 1 (the batched kernel's translation unit) it is compiled out of line, so
+// that the walk's hot loop carries only the test of P.ww_on: that kernel's warps run different
+// problems at different points of the walk, and it is bound by instruction fetch.  The persistent
+// kernel keeps it inline (a run with windows splits and roulettes at many of its events).
+#ifndef MCGB_WW_OUT_OF_LINE
+#define MCGB_WW_OUT_OF_LINE 0
+#endif
 template <typename R>
-__device__ bool weight_window(const RunParams& P, const Tab<R>& T, Part<R>& p, uint4* const* Bout,
-                              unsigned long long* bcount, BlockCounters* bc) {
-  if (!P.ww_on) return true;
+__device__ __forceinline__ bool weight_window_body(const RunParams& P, const Tab<R>& T, Part<R>& p, uint4* const* Bout,
+                                                   unsigned long long* bcount, BlockCounters* bc) {
   const double* ex = P.ww_edges;
   const double* ey = ex + P.ww_nx + 1;
   const double* ez = ey + P.ww_ny + 1;
@@ -183,6 +197,20 @@ __device__ bool weight_window(const RunParams& P, const Tab<R>& T, Part<R>& p, u
   return true;
 }
 
+template <typename R>
+__device__ __noinline__ bool weight_window_apply(const RunParams& P, const Tab<R>& T, Part<R>& p, uint4* const* Bout,
+                                                 unsigned long long* bcount, BlockCounters* bc) {
+  return weight_window_body(P, T, p, Bout, bcount, bc);
+}
+
+template <typename R>
+__device__ bool weight_window(const RunParams& P, const Tab<R>& T, Part<R>& p, uint4* const* Bout,
+                              unsigned long long* bcount, BlockCounters* bc) {
+  if (!P.ww_on) return true;
+  if (MCGB_WW_OUT_OF_LINE) return weight_window_apply(P, T, p, Bout, bcount, bc);
+  return weight_window_body(P, T, p, Bout, bcount, bc);
+}
+
 // ------------------------------------------------------------------------------------------ events
 // Channel of a collision of a particle in material m, group g, from u_channel (the second uniform
 // of block 0 of the flight that ends in it).  Analog: drawn over Sigma_t (scatter, production,
@@ -195,6 +223,32 @@ __device__ __forceinline__ uint32_t collision_channel(const RunParams& P, const 
   R xi = u * St;
   if (P.implicit) xi = keep > R(0) ? u * keep : rinf<R>();
   return xi < T.ss[i] ? CHAN_SCATTER : (xi < keep ? CHAN_PRODUCTION : CHAN_CAPTURE);
+}
+
+// k-eigenvalue cycle, a production collision in material m: floor(nu / k + xi) fission sites for
+// the next cycle, banked in this history's own slots (so their order does not depend on the
+// schedule), groups from chi.  Out of line: fixed-source runs never come here.
+template <typename R>
+__device__ __noinline__ void bank_fission_sites(const RunParams& P, const Tab<R>& T, const Part<R>& p, int m,
+                                                BlockCounters* bc) {
+  const int G = T.G;
+  const int g = (int)pk_g(p.pk);
+  bump(bc, MC_C_PRODUCTION);
+  const R u = draw<R>(P.seed, p.tlo, p.thi, p.k, 3).a;
+  int n = (int)floor(radd(rmul(T.nu[m * G + g], (R)P.inv_k), u));
+  if (n > (int)P.nmax) {
+    set_status(P, MC_ERR_BANK_FULL);  // cannot happen: nmax covers nu_max / k + 1
+    n = (int)P.nmax;
+  }
+  for (int j = 0; j < n; ++j) {
+    const uint2 t = child_tag(P.seed, p.tlo, p.thi, p.k, (uint32_t)j, kChildMark);
+    const Pair2<R> c2 = draw<R>(P.seed, t.x, t.y, kSourceEvent, 2);
+    const int cg = sample_cdf(T.chi + m * G, G, c2.b);
+    site_store(P.site_next, (uint64_t)p.root * P.nmax + (uint64_t)j, p.x, p.y, p.z, cg);
+  }
+  P.count_next[p.root] = (uint32_t)n;
+  if (n > 0) bump(bc, MC_C_SECONDARY, (unsigned)n);
+  log_event(P, T, p, 0, 1, n);
 }
 
 // Handles the particle's pending collision at the end of flight k (uses the blocks of event k).
@@ -236,24 +290,7 @@ __device__ bool do_collision(const RunParams& P, const Tab<R>& T, Part<R>& p, ui
     return weight_window(P, T, p, Bout, bcount, bc);
   }
   if (chan == CHAN_PRODUCTION && P.eigen) {
-    // k-eigenvalue cycle: floor(nu / k + xi) fission sites for the next cycle, banked in this
-    // history's own slots (so their order does not depend on the schedule), groups from chi
-    bump(bc, MC_C_PRODUCTION);
-    const R u = draw<R>(P.seed, p.tlo, p.thi, p.k, 3).a;
-    int n = (int)floor(radd(rmul(T.nu[m * G + g], (R)P.inv_k), u));
-    if (n > (int)P.nmax) {
-      set_status(P, MC_ERR_BANK_FULL);  // cannot happen: nmax covers nu_max / k + 1
-      n = (int)P.nmax;
-    }
-    for (int j = 0; j < n; ++j) {
-      const uint2 t = child_tag(P.seed, p.tlo, p.thi, p.k, (uint32_t)j, kChildMark);
-      const Pair2<R> c2 = draw<R>(P.seed, t.x, t.y, kSourceEvent, 2);
-      const int cg = sample_cdf(T.chi + m * G, G, c2.b);
-      site_store(P.site_next, (uint64_t)p.root * P.nmax + (uint64_t)j, p.x, p.y, p.z, cg);
-    }
-    P.count_next[p.root] = (uint32_t)n;
-    if (n > 0) bump(bc, MC_C_SECONDARY, (unsigned)n);
-    log_event(P, T, p, 0, 1, n);
+    bank_fission_sites(P, T, p, m, bc);
     return false;
   }
   if (chan == CHAN_PRODUCTION) {
@@ -387,6 +424,16 @@ __device__ bool flight_plan(const RunParams& P, const Tab<R>& T, Part<R>& p, Blo
   return true;
 }
 
+// Interior census of population control: banks the particle (event index = its census flight).
+// Out of line: runs without census times never come here.
+template <typename R>
+__device__ __noinline__ void bank_census(const RunParams& P, const Part<R>& p, BlockCounters* bc) {
+  const unsigned long long i = atomicAdd(&P.ctl->pc_n, 1ull);
+  if (i < P.cap_c) bank_store(p, P.C, i);
+  else set_status(P, MC_ERR_BANK_FULL);
+  bump(bc, MC_C_PC_BANKED);
+}
+
 // Flight k, second half (after the segment was scored): move, advance the clock, set the pending
 // event.  Returns false if the particle ends at the census or is captured at the flight's end.
 template <typename R>
@@ -399,15 +446,8 @@ __device__ bool flight_finish(const RunParams& P, const Tab<R>& T, Part<R>& p, B
   p.advance(l, T.v[g], T.inv_v[g]);
   if (pend == PEND_NONE) {
     log_event(P, T, p, 2, 0, 0);
-    if (P.pc_interior) {
-      // interior census of population control: bank the particle (event index = its census flight)
-      const unsigned long long i = atomicAdd(&P.ctl->pc_n, 1ull);
-      if (i < P.cap_c) bank_store(p, P.C, i);
-      else set_status(P, MC_ERR_BANK_FULL);
-      bump(bc, MC_C_PC_BANKED);
-    } else {
-      bump(bc, MC_C_CENSUS);
-    }
+    if (P.pc_interior) bank_census(P, p, bc);
+    else bump(bc, MC_C_CENSUS);
     return false;
   }
   if (pend == PEND_COLL && hit.chan == CHAN_CAPTURE) {
@@ -469,7 +509,7 @@ __device__ __forceinline__ long long eigen_tl_fixed(const Tab<double>& T, const 
 // systematic sampling of the previous cycle's bank), isotropic from its source draws (blocks 1, 2),
 // the site's group, t = 0, weight 1, tag (h, cycle)
 template <typename R>
-__device__ bool make_site_source(const RunParams& P, const Tab<R>& T, uint64_t h, Part<R>& p) {
+__device__ __noinline__ bool make_site_source(const RunParams& P, const Tab<R>& T, uint64_t h, Part<R>& p) {
   const uint32_t tlo = (uint32_t)h, thi = P.cycle;
   const Pair2<R> b1 = draw<R>(P.seed, tlo, thi, kSourceEvent, 1);
   const Pair2<R> b2 = draw<R>(P.seed, tlo, thi, kSourceEvent, 2);

@@ -44,8 +44,8 @@ namespace mcgb {
 constexpr unsigned kClaim = MCGB_CLAIM, kClaimTail = MCGB_CLAIM_TAIL, kTailWaves = MCGB_TAIL_WAVES;
 
 // dynamic shared memory: [table blob][per-warp flight queues: warps x Lanes<R>::N x kWarpQ]
-// [per-warp tally staging: warps x kStage x 12 B][SEG: per-warp segment regions: warps x
-// kSegLanes x kSegCap x 16 B]
+// [per-warp tally staging, with warp-aggregated tally adds only: warps x kStage x 12 B][SEG:
+// per-warp segment regions: warps x kSegLanes x kSegCap x 16 B]
 //
 // MODE 0 runs the whole transport in one launch: event-based iterations, then history-style ones
 // once the work left is below the drain threshold.  A split run launches MODE 1, which stops where
@@ -72,13 +72,15 @@ __global__ void __launch_bounds__(MINB == 5 ? 128 : 256, MINB) k_transport(RunPa
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   uint4* wq = reinterpret_cast<uint4*>(smem + P.blob_bytes) + warp * (Lanes<R>::N * kWarpQ);
-  // per-warp tally staging buffers follow the queues: values (8 B) then slots (4 B)
+  // per-warp tally staging buffers follow the queues: values (8 B) then slots (4 B); only runs
+  // that warp-aggregate their tally adds stage scores, the others have no staging region
+  const unsigned kst = P.aggregate ? kStage : 0u;
   char* stage_base = smem + P.blob_bytes + (size_t)nwarp * Lanes<R>::N * kWarpQ * 16;
-  const Stage stage{reinterpret_cast<uint32_t*>(stage_base + (size_t)nwarp * kStage * 8) + warp * kStage,
-                    reinterpret_cast<unsigned long long*>(stage_base) + warp * kStage};
-  // SEG: the warp's region of segments waiting to be scored, ns of them (warp-uniform)
-  // SEG: the warp's region of segments waiting to be scored, after the staging buffers
-  uint4* const sq = SEG ? reinterpret_cast<uint4*>(stage_base + (size_t)nwarp * kStage * 12) + warp * (kSegLanes * kSegCap)
+  const Stage stage{reinterpret_cast<uint32_t*>(stage_base + (size_t)nwarp * kst * 8) + warp * kst,
+                    reinterpret_cast<unsigned long long*>(stage_base) + warp * kst};
+  // SEG: the warp's region of segments waiting to be scored (ns of them, warp-uniform), after the
+  // staging buffers
+  uint4* const sq = SEG ? reinterpret_cast<uint4*>(stage_base + (size_t)nwarp * kst * 12) + warp * (kSegLanes * kSegCap)
                         : nullptr;
   unsigned ns = 0;
   Ctl* ctl = P.ctl;
