@@ -317,6 +317,36 @@ struct Blob {
   TableHeader* hdr() { return reinterpret_cast<TableHeader*>(b.data()); }
 };
 
+// First-guess parameters of a bin search over float edges e[0..n] (see TallyDesc::gkind): equal
+// spacing, or geometric spacing from edge 1 on (log-spaced time bins after a first bin [0, e1]);
+// any other axis is searched by bisection.  Only the search's cost depends on them.
+void bin_guess_params(const std::vector<float>& e, int& kind, float& a, float& b) {
+  kind = 0;
+  a = b = 0.0f;
+  const int n = (int)e.size() - 1;
+  if (n < 4) return;
+  const double w = (double)e[n] - (double)e[0];
+  bool lin = w > 0.0;
+  for (int k = 1; k < n && lin; ++k)
+    lin = std::fabs((double)e[k] - ((double)e[0] + w * k / n)) <= 1e-3 * w / n;
+  if (lin) {
+    kind = 1;
+    a = e[0];
+    b = (float)(n / w);
+    return;
+  }
+  if (!(e[1] > 0.0f) || !(e[n] > e[1])) return;
+  const double r = std::log2((double)e[n] / (double)e[1]) / (n - 1);
+  bool geo = r > 0.0;
+  for (int k = 2; k < n && geo; ++k)
+    geo = std::fabs(std::log2((double)e[k] / (double)e[1]) - r * (k - 1)) <= 1e-3 * r;
+  if (geo) {
+    kind = 2;
+    a = (float)(1.0 / (double)e[1]);
+    b = (float)(1.0 / r);
+  }
+}
+
 template <typename R>
 std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
   const int G = d->n_groups, M = d->n_materials;
@@ -467,6 +497,11 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
     D.o_ez = B.put(ez);
     D.o_et = B.put(et);
     D.o_etf = B.put(etf);
+    {
+      const std::vector<float> exf(T.x, T.x + T.nx + 1), eyf(T.y, T.y + T.ny + 1), ezf(T.z, T.z + T.nz + 1);
+      const std::vector<float>* axes[4] = {&exf, &eyf, &ezf, &etf};
+      for (int a = 0; a < 4; ++a) bin_guess_params(*axes[a], D.gkind[a], D.ga[a], D.gb[a]);
+    }
     D.bin_offset = off;
     D.est = T.estimator;
     D.nval = T.nt + (T.estimator == MC_EST_TIME_CROSSING ? 1 : 0);

@@ -27,8 +27,10 @@
 #include <numeric>
 #include <vector>
 
-// this kernel's weight-window test out of line (see weight_window)
+// this kernel's weight-window test out of line (see weight_window), its segment walks started by
+// bisection (see bin_find)
 #define MCGB_WW_OUT_OF_LINE 1
+#define MCGB_BIN_GUESS 0
 #include "mc_events.cuh"
 #include "mc_host.h"
 

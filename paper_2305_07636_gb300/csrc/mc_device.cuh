@@ -656,6 +656,28 @@ __device__ __forceinline__ int bin_search(const E* e, int n, X x) {
   return lo;
 }
 
+// The same bin as bin_search, from a first guess along an axis of equal (kind 1) or geometric
+// (kind 2, from edge 1 on) spacing, corrected against the edges: the guess lands within a bin of
+// the answer, and the walk to e[i] <= x < e[i+1] settles the rounding of the guess.  Kind 0 is
+// plain bisection.  The segment walk of the persistent kernel starts with it; the batched
+// kernel's translation unit sets MCGB_BIN_GUESS to 0 and keeps bisection (that kernel is bound by
+// instruction fetch, and the guess's code measured slower there).
+#ifndef MCGB_BIN_GUESS
+#define MCGB_BIN_GUESS 1
+#endif
+__device__ __forceinline__ int bin_find(const float* e, int n, float x, int kind, float a, float b) {
+  if (kind == 0) return bin_search(e, n, x);
+  if (!(x >= e[0])) return -1;
+  if (!(x < e[n])) return n;
+  int i;
+  if (kind == 1) i = __float2int_rd(__fmul_rn(__fsub_rn(x, a), b));
+  else i = x < e[1] ? 0 : 1 + __float2int_rd(__fmul_rn(__log2f(__fmul_rn(x, a)), b));
+  i = min(max(i, 0), n - 1);
+  while (i > 0 && x < e[i]) --i;
+  while (i < n - 1 && !(x < e[i + 1])) ++i;
+  return i;
+}
+
 // ------------------------------------------------------------------------------------------ tally atomics
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
@@ -941,7 +963,8 @@ __device__ __forceinline__ void score_segments(const Tab<float>& T, const RunPar
       // a new walk: the cells and time bin of the segment's start (as score_segment_warp finds them)
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const int i = bin_search(e[d], n[d], r.pos[d]);
+        const int i = MCGB_BIN_GUESS ? bin_find(e[d], n[d], r.pos[d], D.gkind[d], D.ga[d], D.gb[d])
+                                     : bin_search(e[d], n[d], r.pos[d]);
         r.idx[d] = i;
         if (step[d] > 0) {
           if (i >= n[d]) live = false;
@@ -954,7 +977,7 @@ __device__ __forceinline__ void score_segments(const Tab<float>& T, const RunPar
           if (i < 0 || i >= n[d]) live = false;
         }
       }
-      r.it = bin_search(et, nt, r.t0);
+      r.it = MCGB_BIN_GUESS ? bin_find(et, nt, r.t0, D.gkind[3], D.ga[3], D.gb[3]) : bin_search(et, nt, r.t0);
       if (r.it >= nt) live = false;
       else stn = (et[r.it + 1] - r.t0) * v;
     } else if (live) {

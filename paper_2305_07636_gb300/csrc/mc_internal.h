@@ -83,6 +83,12 @@ struct TallyDesc {
   int diff_offset;             // range walk: first difference slot after the batch row's bins
   int ndiff;                   // range walk: difference slots per (cell, group): nt + 1 (track
                                // length) or nt + 2 (time crossing)
+  // First guess of a segment's starting bin along x, y, z, t from the float edges (FP32 walk):
+  // kind 0 none (bisection); 1 equal spacing, bin floor((u - a) b); 2 geometric from edge 1 on,
+  // bin 1 + floor(log2(u a) b) (bin 0 below edge 1).  The guess is corrected against the edges,
+  // so the bin found is the one bisection finds whatever the spacing.
+  int gkind[4];
+  float ga[4], gb[4];
 };
 
 // A tally is scored by the range walk when its time axis is much finer than its spatial mesh
