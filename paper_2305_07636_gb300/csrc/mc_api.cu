@@ -454,6 +454,24 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
   H.o_nhs = B.put(nhs);
   H.o_hs = B.put(hs);
   H.o_cmat = B.put(cmat);
+  // box cells: the walk takes the one plane per axis that the direction of motion can leave by
+  std::vector<int> cbox((size_t)H.n_cell * 7, -1);
+  for (int c = 0; c < H.n_cell; ++c) {
+    const mc_cell& C = d->cells[c];
+    int* b = &cbox[(size_t)c * 7];
+    b[0] = 1;
+    for (int i = 0; i < C.n_halfspaces && b[0]; ++i) {
+      const int s = C.surface[i], k = d->surfaces[s].kind;
+      if (k != MC_SURF_PX && k != MC_SURF_PY && k != MC_SURF_PZ) {
+        b[0] = 0;
+        break;
+      }
+      int& slot = b[1 + 2 * k + (C.sense[i] > 0 ? 0 : 1)];  // sense +1: the plane bounds from below
+      if (slot != -1) b[0] = 0;
+      else slot = s | (i << 16);
+    }
+  }
+  H.o_cbox = B.put(cbox);
   if (d->lattice) {
     const mc_lattice* L = d->lattice;
     H.has_lat = 1;

@@ -106,7 +106,7 @@ template <typename R>
 struct Tab {
   const TableHeader* h;
   const R *st, *ss, *ssf, *nu, *nusf, *v, *inv_v, *scdf, *chi, *src_cdf, *scoef;
-  const int *skind, *sbc, *nhs, *hs, *cmat;
+  const int *skind, *sbc, *nhs, *hs, *cmat, *cbox;
   const uint8_t* lpin;
   R lx0, ly0, lp, lr, lz0, lpz;
   int G;
@@ -128,6 +128,7 @@ struct Tab {
     nhs = reinterpret_cast<const int*>(base + h->o_nhs);
     hs = reinterpret_cast<const int*>(base + h->o_hs);
     cmat = reinterpret_cast<const int*>(base + h->o_cmat);
+    cbox = reinterpret_cast<const int*>(base + h->o_cbox);
     lpin = reinterpret_cast<const uint8_t*>(base + h->o_lpin);
     lx0 = (R)h->lat_x0;
     ly0 = (R)h->lat_y0;
@@ -562,12 +563,38 @@ struct Hit {
   uint32_t chan;  // channel of a collision at the end of the flight (CHAN_*)
 };
 
+// Cells bounded by axis-aligned planes only take a shortcut of the surface loop (the same
+// distances and choice); the batched kernel's translation unit sets MCGB_BOX_CELLS to 0.
+#ifndef MCGB_BOX_CELLS
+#define MCGB_BOX_CELLS 1
+#endif
 template <typename R>
 __device__ R boundary_distance(const Tab<R>& T, const Part<R>& p, Hit& hit) {
   R best = rinf<R>();
   hit = {HIT_CELL, 1, 0};
   const int c = (int)pk_cell(p.pk);
-  const int n = T.nhs[c];
+  const int n = MCGB_BOX_CELLS && T.cbox[7 * c] ? 0 : T.nhs[c];
+  if (MCGB_BOX_CELLS && n == 0) {
+    // a box cell: per axis only the plane the motion can leave by, with the generic loop's
+    // distance expression and its choice among equal distances (the earliest in the cell's list)
+    const int* bx = T.cbox + 7 * c + 1;
+    const R pos[3] = {p.x, p.y, p.z}, u[3] = {p.ux, p.uy, p.uz};
+    int bo = 1 << 30;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int e = u[a] > R(0) ? bx[2 * a + 1] : (u[a] < R(0) ? bx[2 * a] : -1);
+      if (e >= 0) {
+        const int s = e & 0xFFFF, o = e >> 16;
+        R d = rdiv(T.scoef[kSurfStride * s] - pos[a], u[a]);
+        d = d > R(0) ? d : R(0);
+        if (d < best || (d == best && d < rinf<R>() && o < bo)) {
+          best = d;
+          bo = o;
+          hit = {HIT_CELL, 1, (uint32_t)s};
+        }
+      }
+    }
+  }
   for (int i = 0; i < n; ++i) {
     const int e = T.hs[c * MC_MAX_HALFSPACES + i];
     const int s = e & 0xFFFF, sn = (e >> 16) ? -1 : 1;

@@ -116,7 +116,10 @@ struct TableHeader {
   int o_nhs, o_hs, o_cmat, o_lpin;    // [n_cell] int; [n_cell][16] int (surf | sense<<16); [n_cell] int;
                                       // [nz][ny][nx] uint8 pin material (kNoPin = no pin)
   TallyDesc tally[kMaxTallies];
-  int blob_bytes, o_nusf, pad3, pad4;  // o_nusf: [M][G] Real nu Sigma_f (k-eigenvalue estimator)
+  int blob_bytes, o_nusf, o_cbox, pad4;  // o_nusf: [M][G] Real nu Sigma_f (k-eigenvalue estimator)
+  // o_cbox: [n_cell][7] int: 1 for a cell bounded by axis-aligned planes only, at most one lower
+  // and one upper plane per axis; then per axis its lower and upper plane as surface | (position
+  // in the cell's halfspace list << 16), or -1
 };
 
 // Factor that turns a bin's accumulated score into the tally value: v_g for a time-crossing bin
