@@ -564,7 +564,7 @@ struct Hit {
 };
 
 // Cells bounded by axis-aligned planes only take a shortcut of the surface loop (the same
-// distances and choice); the batched kernel's translation unit sets MCGB_BOX_CELLS to 0.
+// distances and choice); a translation unit that sets MCGB_BOX_CELLS to 0 compiles the loop alone.
 #ifndef MCGB_BOX_CELLS
 #define MCGB_BOX_CELLS 1
 #endif
