@@ -22,6 +22,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "mc_host.h"
+#include "mc_tables.h"
 
 namespace mcgb {
 template <typename R>
@@ -317,36 +318,6 @@ struct Blob {
   TableHeader* hdr() { return reinterpret_cast<TableHeader*>(b.data()); }
 };
 
-// First-guess parameters of a bin search over float edges e[0..n] (see TallyDesc::gkind): equal
-// spacing, or geometric spacing from edge 1 on (log-spaced time bins after a first bin [0, e1]);
-// any other axis is searched by bisection.  Only the search's cost depends on them.
-void bin_guess_params(const std::vector<float>& e, int& kind, float& a, float& b) {
-  kind = 0;
-  a = b = 0.0f;
-  const int n = (int)e.size() - 1;
-  if (n < 4) return;
-  const double w = (double)e[n] - (double)e[0];
-  bool lin = w > 0.0;
-  for (int k = 1; k < n && lin; ++k)
-    lin = std::fabs((double)e[k] - ((double)e[0] + w * k / n)) <= 1e-3 * w / n;
-  if (lin) {
-    kind = 1;
-    a = e[0];
-    b = (float)(n / w);
-    return;
-  }
-  if (!(e[1] > 0.0f) || !(e[n] > e[1])) return;
-  const double r = std::log2((double)e[n] / (double)e[1]) / (n - 1);
-  bool geo = r > 0.0;
-  for (int k = 2; k < n && geo; ++k)
-    geo = std::fabs(std::log2((double)e[k] / (double)e[1]) - r * (k - 1)) <= 1e-3 * r;
-  if (geo) {
-    kind = 2;
-    a = (float)(1.0 / (double)e[1]);
-    b = (float)(1.0 / r);
-  }
-}
-
 template <typename R>
 std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
   const int G = d->n_groups, M = d->n_materials;
@@ -456,21 +427,7 @@ std::vector<uint8_t> build_blob(const mc_problem_desc* d) {
   H.o_cmat = B.put(cmat);
   // box cells: the walk takes the one plane per axis that the direction of motion can leave by
   std::vector<int> cbox((size_t)H.n_cell * 7, -1);
-  for (int c = 0; c < H.n_cell; ++c) {
-    const mc_cell& C = d->cells[c];
-    int* b = &cbox[(size_t)c * 7];
-    b[0] = 1;
-    for (int i = 0; i < C.n_halfspaces && b[0]; ++i) {
-      const int s = C.surface[i], k = d->surfaces[s].kind;
-      if (k != MC_SURF_PX && k != MC_SURF_PY && k != MC_SURF_PZ) {
-        b[0] = 0;
-        break;
-      }
-      int& slot = b[1 + 2 * k + (C.sense[i] > 0 ? 0 : 1)];  // sense +1: the plane bounds from below
-      if (slot != -1) b[0] = 0;
-      else slot = s | (i << 16);
-    }
-  }
+  for (int c = 0; c < H.n_cell; ++c) box_cell_entry(d->cells[c], d->surfaces, &cbox[(size_t)c * 7]);
   H.o_cbox = B.put(cbox);
   if (d->lattice) {
     const mc_lattice* L = d->lattice;
